@@ -1,0 +1,201 @@
+/*
+ * wrf.h - C ABI of the B300 (sm_103a) spectrum-synthesis library.
+ *
+ * Implements the spectrum-synthesis path of SwiftWRF, "Deformable 2D Gaussian
+ * Splatting for Efficient Wireless Radiance Field Rendering" (arXiv 2506.12787):
+ * the problem F: R^3 -> spectrum (Sec. 3.3.2) solved by a deformation MLP over
+ * 2D Gaussians (Sec. 4.2, Eqs. 12-15) followed by tile rasterisation of the
+ * order-free Gaussian sum (Sec. 4.1, Eqs. 8-9, 13).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *device* are CUDA device pointers; they are owned by the
+ *     caller and must stay valid until the work queued on `stream` finishes.
+ *     The library never allocates device memory: scratch space is passed in
+ *     as `ws` (size from the matching *_workspace_size call), 256-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *     only enqueues work and returns; nothing synchronises the host.
+ *   - Argument errors are detected on the host and returned before any work
+ *     is queued (WRF_EINVAL / WRF_EUNSUPPORTED).  A failed launch returns
+ *     WRF_ECUDA.  Conditions only the device can see (key-capacity overflow,
+ *     a bounded wait that ran out) are recorded in a library-global device
+ *     status word that wrf_status_read() returns (and clears).
+ *   - wrf_last_error() returns a thread-local message for the last non-OK
+ *     status returned on the calling thread.
+ *   - Spectrum layout: FP32 [Q][H][W] row-major; row y = elevation index,
+ *     column x = azimuth index (Sec. 3.1, Eq. 5: 90 rows x 360 columns at
+ *     1 degree).  Pixel (x, y) is sampled at integer coordinates (x, y).
+ *   - One channel (C = 1) is supported: the scalar signal response.
+ */
+#ifndef WRF_H
+#define WRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WRF_OK = 0,
+    WRF_EINVAL = -1,       /* bad argument (null pointer, size, alignment)       */
+    WRF_ENOSPC = -2,       /* key capacity too small; required count reported    */
+    WRF_ECUDA = -3,        /* a CUDA launch or runtime call failed               */
+    WRF_ETIMEOUT = -4,     /* a bounded device-side wait gave up                 */
+    WRF_EUNSUPPORTED = -5  /* valid request outside what the kernels implement   */
+} wrf_status;
+
+enum { WRF_FP32 = 0, WRF_BF16 = 1 };
+enum { WRF_MAX_LAYERS = 8, WRF_HIDDEN = 128, WRF_OUT = 5 };
+
+/* Reference-frame Gaussians G^0 (Sec. 4.2, Eq. 10-12), structure of arrays,
+ * FP32, device.  Per Gaussian: centre mean[2] in pixels (x, y); log_scale[2]
+ * = natural log of the two principal standard deviations in pixels; rot =
+ * angle of the first principal axis (radians); opacity_logit a with
+ * attenuation delta = sigmoid(a) (Sec. 4.1); amp = scalar response psi. */
+typedef struct {
+    int32_t n;                   /* number of Gaussians N (>= 0)              */
+    int32_t channels;            /* must be 1                                 */
+    const float *mean;           /* [N][2] device                             */
+    const float *log_scale;      /* [N][2] device                             */
+    const float *rot;            /* [N]    device                             */
+    const float *opacity_logit;  /* [N]    device                             */
+    const float *amp;            /* [N]    device                             */
+} wrf_scene;
+
+/* Deformation MLP F_theta (Sec. 4.2, Eq. 14): input [gamma(mean/(W,H)),
+ * gamma((tx - room_min)/room_size)] with gamma from Eq. 15 (L_mean and L_tx
+ * frequency bands), n_layers Linear layers with ReLU between them, output
+ * (dx, dy, drot, dlog_scale1, dlog_scale2).  Weights are FP32, device,
+ * W[l] is [dims[l+1]][dims[l]] row-major, b[l] is [dims[l+1]].
+ * Supported: dims[0] = 2(2 L_mean + 1) + 3(2 L_tx + 1), hidden widths 128,
+ * 2 <= n_layers <= 8, output width 5.  precision = WRF_BF16 runs the hidden
+ * layers on tcgen05 tensor cores with BF16 operands and FP32 accumulation;
+ * WRF_FP32 runs everything in FP32 on the CUDA cores. */
+typedef struct {
+    int32_t n_layers;
+    int32_t dims[WRF_MAX_LAYERS + 1];
+    const float *W[WRF_MAX_LAYERS];
+    const float *b[WRF_MAX_LAYERS];
+    int32_t L_mean, L_tx;
+    float room_min[3], room_size[3];
+    int32_t precision;           /* WRF_FP32 or WRF_BF16                      */
+} wrf_mlp;
+
+/* Spectrum grid and tiling.  A Gaussian contributes to pixel p only where
+ * q = d^T Sigma^-1 d <= q_cut (d = p - centre); q_cut = +inf disables the
+ * cutoff.  Tiles are tile_w x tile_h pixels, numbered row-major; the last
+ * tile row/column may be partial.  Supported tile shapes: 8x8, 16x8, 16x16,
+ * 32x8, 32x16 (w x h). */
+typedef struct {
+    int32_t H, W;
+    int32_t tile_w, tile_h;
+    float q_cut;
+} wrf_grid;
+
+/* Projected record of one deformed Gaussian for one query: 8 floats, 32-byte
+ * aligned, [Q][N][8]:
+ *   [0] mx, [1] my     deformed centre (pixels)
+ *   [2] a, [3] b, [4] c  inverse covariance scaled by log2(e)/2, so that
+ *                      exp(-q/2) = exp2(-(a dx^2 + 2 b dx dy + c dy^2))
+ *   [5] w              sigmoid(opacity_logit) * amp
+ *   [6] rx, [7] ry     sqrt(q_cut Sigma_xx), sqrt(q_cut Sigma_yy): axis
+ *                      half-widths of the q <= q_cut ellipse                 */
+enum { WRF_REC_FLOATS = 8 };
+
+/* ---------------------------------------------------------------------- */
+/* Deformation: residuals for every (query, Gaussian) row, Sec. 4.2 Eq. 14
+ * (with the positional encoding of Eq. 15).
+ *   tx     [Q][3] device, TX positions in metres.
+ *   resid  [Q][N][5] device output (dx, dy, drot, dls1, dls2).
+ *   ws     workspace of wrf_deform_workspace_size(N, Q, mlp) bytes.        */
+size_t wrf_deform_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp);
+wrf_status wrf_deform(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                      const float *tx, int32_t Q, float *resid, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* Deform + project: Eq. 12-13 applied to every (query, Gaussian) row, giving
+ * the projected record (layout above) and, if tile_count is non-NULL, the
+ * number of tiles its footprint rectangle covers.
+ *   resid      [Q][N][5] device, or NULL for no deformation (Q copies of G^0).
+ *   rec        [Q][N][8] device output, 32-byte aligned.
+ *   tile_count [Q][N] device output or NULL.                                */
+wrf_status wrf_project(const wrf_scene *scene, const float *resid, int32_t Q,
+                       const wrf_grid *grid, float *rec, uint32_t *tile_count, void *stream);
+
+/* Fused deformation + projection: the MLP epilogue writes records directly
+ * (no [Q][N][5] residual round trip through HBM).  Same outputs as
+ * wrf_deform followed by wrf_project, up to FP32 rounding order.            */
+wrf_status wrf_deform_project(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                              const float *tx, int32_t Q, float *rec, uint32_t *tile_count,
+                              void *ws, size_t ws_bytes, void *stream);
+
+/* Tile binning (Sec. 4.1: the spectrum is partitioned into tiles processed
+ * in parallel).  For every query q and tile t, lists the ids n of the
+ * Gaussians whose footprint rectangle covers t, ascending in n: a stable
+ * one-digit radix (counting) sort of keys (q, t, n) on the digit (q, t).
+ * The footprint rectangle of a record covers pixels ceil(mx - rx) ..
+ * floor(mx + rx) (x) and ceil(my - ry) .. floor(my + ry) (y), clipped to the
+ * grid, computed in FP32.
+ *   gids          [key_capacity] device output: n of every key, (q,t)-major.
+ *   n_keys_out    device int64: total number of keys (always written).
+ *   tile_offsets  [Q*T + 1] device output (CSR): keys of (q, t) are
+ *                 gids[tile_offsets[q*T+t] .. tile_offsets[q*T+t+1]).
+ * If the total exceeds key_capacity (or 2^32-1) no gids are written, the
+ * device status word records WRF_ENOSPC and *n_keys_out holds the required
+ * count; wrf_render then produces zeros for those queries.                */
+size_t wrf_bin_workspace_size(int32_t n, int32_t Q, const wrf_grid *grid);
+wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid, uint32_t *gids,
+                   int64_t key_capacity, int64_t *n_keys_out, uint32_t *tile_offsets, void *ws,
+                   size_t ws_bytes, void *stream);
+
+/* Rasterisation, Eq. 9 / Eq. 13: A_q(y, x) = sum over the Gaussians listed
+ * for the pixel's tile, ascending n, of [q <= q_cut] w exp(-q/2).  No depth
+ * order, no transmittance, no clamping (order-free accumulation).
+ *   spectra  [Q][H][W] device output (fully overwritten).
+ *   n_keys / key_capacity as produced/used by wrf_bin.                     */
+wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *tile_offsets,
+                      const int64_t *n_keys, int64_t key_capacity, int32_t n, int32_t Q,
+                      const wrf_grid *grid, float *spectra, void *stream);
+
+/* Backward of wrf_render: from dL/dA [Q][H][W] to d_rec [Q][N][6] =
+ * dL/d(mx, my, A, B, C, w) where (A, B, C) is the unscaled inverse
+ * covariance (Eq. 8).  Per-pixel weights are recomputed from the records
+ * and tile lists (nothing is stored by the forward).  d_rec is accumulated
+ * with atomic adds and must be zeroed by the caller.                        */
+wrf_status wrf_render_backward(const float *rec, const uint32_t *gids,
+                               const uint32_t *tile_offsets, const int64_t *n_keys,
+                               int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
+                               const float *dL_dspectra, float *d_rec, void *stream);
+
+/* Backward of wrf_project: from d_rec [Q][N][6] to d_resid [Q][N][5] and the
+ * reference-frame gradients summed over queries.  Outputs are overwritten
+ * (d_mean [N][2], d_log_scale [N][2], d_rot, d_opacity, d_amp [N]);
+ * d_resid may be NULL when resid is NULL.                                   */
+wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int32_t Q,
+                                const float *d_rec, float *d_resid, float *d_mean,
+                                float *d_log_scale, float *d_rot, float *d_opacity, float *d_amp,
+                                void *stream);
+
+/* Backward of wrf_deform (MLP back-propagation, Sec. 4.4): from d_resid
+ * [Q][N][5] to dW[l], db[l] (same shapes as the weights; overwritten) and,
+ * unless stop_grad_mean is non-zero, adds the derivative through
+ * gamma(mean) into d_mean [N][2] (the paper freezes position gradients in
+ * its fine stage; the flag reproduces that).                                */
+size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp);
+wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                               const float *tx, int32_t Q, const float *d_resid, float *const *dW,
+                               float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
+                               size_t ws_bytes, void *stream);
+
+/* Device status word: returns the first device-side error recorded since the
+ * last call (WRF_OK if none) after synchronising `stream`, and clears it.    */
+wrf_status wrf_status_read(void *stream);
+
+const char *wrf_last_error(void);
+int32_t wrf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WRF_H */

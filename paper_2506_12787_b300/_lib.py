@@ -1,0 +1,97 @@
+"""ctypes view of the C ABI in include/wrf.h (argument marshalling only).
+
+The shared library ``libwrf.so`` is built in-tree by ``build.py``.  Loading
+fails loudly when it is missing: there is no CPU or PyTorch fallback for any
+step of the path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwrf.so")
+
+WRF_OK, WRF_EINVAL, WRF_ENOSPC, WRF_ECUDA, WRF_ETIMEOUT, WRF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+WRF_FP32, WRF_BF16 = 0, 1
+MAX_LAYERS = 8
+REC_FLOATS = 8
+
+STATUS_NAMES = {0: "WRF_OK", -1: "WRF_EINVAL", -2: "WRF_ENOSPC", -3: "WRF_ECUDA",
+                -4: "WRF_ETIMEOUT", -5: "WRF_EUNSUPPORTED"}
+
+# Every symbol include/wrf.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "wrf_deform_workspace_size", "wrf_deform", "wrf_project", "wrf_deform_project",
+    "wrf_bin_workspace_size", "wrf_bin", "wrf_render", "wrf_render_backward",
+    "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
+    "wrf_status_read", "wrf_last_error", "wrf_version",
+)
+
+
+class WrfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Scene(C.Structure):
+    _fields_ = [("n", C.c_int32), ("channels", C.c_int32), ("mean", C.c_void_p),
+                ("log_scale", C.c_void_p), ("rot", C.c_void_p), ("opacity_logit", C.c_void_p),
+                ("amp", C.c_void_p)]
+
+
+class Mlp(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.c_int32 * (MAX_LAYERS + 1)),
+                ("W", C.c_void_p * MAX_LAYERS), ("b", C.c_void_p * MAX_LAYERS),
+                ("L_mean", C.c_int32), ("L_tx", C.c_int32), ("room_min", C.c_float * 3),
+                ("room_size", C.c_float * 3), ("precision", C.c_int32)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("tile_w", C.c_int32),
+                ("tile_h", C.c_int32), ("q_cut", C.c_float)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwrf.so and declare every entry point's signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with "
+                          "`python -m paper_2506_12787_b300.build` (nvcc, sm_103a)")
+    L = C.CDLL(path)
+    P, S, I32, I64, F = C.c_void_p, C.c_size_t, C.c_int32, C.c_int64, C.c_float
+    sp, mp, gp = C.POINTER(Scene), C.POINTER(Mlp), C.POINTER(Grid)
+    sig = {
+        "wrf_deform_workspace_size": (S, [I32, I32, mp]),
+        "wrf_deform": (I32, [sp, mp, gp, P, I32, P, P, S, P]),
+        "wrf_project": (I32, [sp, P, I32, gp, P, P, P]),
+        "wrf_deform_project": (I32, [sp, mp, gp, P, I32, P, P, P, S, P]),
+        "wrf_bin_workspace_size": (S, [I32, I32, gp]),
+        "wrf_bin": (I32, [P, I32, I32, gp, P, I64, P, P, P, S, P]),
+        "wrf_render": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
+        "wrf_render_backward": (I32, [P, P, P, P, I64, I32, I32, gp, P, P, P]),
+        "wrf_project_backward": (I32, [sp, P, I32, P, P, P, P, P, P, P, P]),
+        "wrf_deform_backward_workspace_size": (S, [I32, I32, mp]),
+        "wrf_deform_backward": (I32, [sp, mp, gp, P, I32, P, P, P, P, I32, P, S, P]),
+        "wrf_status_read": (I32, [P]),
+        "wrf_last_error": (C.c_char_p, []),
+        "wrf_version": (I32, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def check(status: int) -> None:
+    if status != WRF_OK:
+        msg = load().wrf_last_error().decode(errors="replace")
+        raise WrfError(int(status), msg)

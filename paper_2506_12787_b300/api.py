@@ -1,0 +1,310 @@
+"""Python binding of the C ABI: the same entry points, taking torch tensors.
+
+PyTorch supplies device memory and streams only; every step of the path runs
+in the library's CUDA kernels.  Functions return their outputs as tensors
+(allocated with torch when not passed in) and raise WrfError on a non-OK
+status.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import math
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import WRF_BF16, WRF_FP32, WrfError
+
+__all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
+           "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
+           "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
+           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16"]
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _f32(a, device):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=device, dtype=torch.float32).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device)
+
+
+@dataclasses.dataclass
+class DeviceScene:
+    """Reference-frame Gaussians resident on the device (FP32, SoA)."""
+    mean: torch.Tensor           # [N,2]
+    log_scale: torch.Tensor      # [N,2]
+    rot: torch.Tensor            # [N]
+    opacity_logit: torch.Tensor  # [N]
+    amp: torch.Tensor            # [N]
+
+    @classmethod
+    def from_host(cls, s, device="cuda"):
+        return cls(*(_f32(getattr(s, k), device) for k in
+                     ("mean", "log_scale", "rot", "opacity_logit", "amp")))
+
+    @property
+    def n(self) -> int:
+        return int(self.mean.shape[0])
+
+    def c(self) -> _lib.Scene:
+        return _lib.Scene(self.n, 1, self.mean.data_ptr(), self.log_scale.data_ptr(),
+                          self.rot.data_ptr(), self.opacity_logit.data_ptr(),
+                          self.amp.data_ptr())
+
+
+@dataclasses.dataclass
+class DeviceMLP:
+    """Deformation MLP weights resident on the device (FP32 masters)."""
+    W: list
+    b: list
+    L_mean: int = 6
+    L_tx: int = 10
+    room_min: tuple = (0.0, 0.0, 0.0)
+    room_size: tuple = (5.0, 5.0, 3.0)
+    precision: int = WRF_FP32
+
+    @classmethod
+    def from_host(cls, m, device="cuda", precision=WRF_FP32):
+        return cls([_f32(w, device) for w in m.W], [_f32(b, device) for b in m.b], m.L_mean,
+                   m.L_tx, tuple(m.room_min), tuple(m.room_size), precision)
+
+    @property
+    def dims(self):
+        return [int(self.W[0].shape[1])] + [int(w.shape[0]) for w in self.W]
+
+    def with_precision(self, precision):
+        return dataclasses.replace(self, precision=precision)
+
+    def c(self) -> _lib.Mlp:
+        m = _lib.Mlp()
+        m.n_layers = len(self.W)
+        for i, d in enumerate(self.dims):
+            m.dims[i] = d
+        for i, (w, b) in enumerate(zip(self.W, self.b)):
+            m.W[i] = w.data_ptr()
+            m.b[i] = b.data_ptr()
+        m.L_mean, m.L_tx = self.L_mean, self.L_tx
+        for i in range(3):
+            m.room_min[i] = self.room_min[i]
+            m.room_size[i] = self.room_size[i]
+        m.precision = self.precision
+        return m
+
+
+def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0) -> _lib.Grid:
+    return _lib.Grid(H, W, tile_w, tile_h, float(q_cut))
+
+
+def tiles_of(grid) -> int:
+    return ((grid.W + grid.tile_w - 1) // grid.tile_w) * ((grid.H + grid.tile_h - 1) // grid.tile_h)
+
+
+def _ws(nbytes, device):
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def wrf_deform(scene: DeviceScene, mlp: DeviceMLP, grid, tx, resid=None, ws=None, stream=None):
+    """Residuals [Q,N,5] (Eq. 14)."""
+    L = _lib.load()
+    Q, dev = int(tx.shape[0]), tx.device
+    mc = mlp.c()
+    if resid is None:
+        resid = torch.empty((Q, scene.n, 5), dtype=torch.float32, device=dev)
+    need = L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_deform(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q, _p(resid),
+                            _p(ws), ws.numel(), _stream(stream)))
+    return resid
+
+
+def wrf_project(scene: DeviceScene, resid, Q: int, grid, rec=None, tile_count=None, stream=None):
+    """Records [Q,N,8] and tile counts [Q,N] (Eq. 12-13)."""
+    L = _lib.load()
+    dev = scene.mean.device
+    if rec is None:
+        rec = torch.empty((Q, scene.n, 8), dtype=torch.float32, device=dev)
+    if tile_count is None:
+        tile_count = torch.empty((Q, scene.n), dtype=torch.int32, device=dev)
+    _lib.check(L.wrf_project(C.byref(scene.c()), _p(resid), Q, C.byref(grid), _p(rec),
+                             _p(tile_count), _stream(stream)))
+    return rec, tile_count
+
+
+def wrf_deform_project(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rec=None, tile_count=None,
+                       ws=None, stream=None):
+    L = _lib.load()
+    Q, dev = int(tx.shape[0]), tx.device
+    mc = mlp.c()
+    if rec is None:
+        rec = torch.empty((Q, scene.n, 8), dtype=torch.float32, device=dev)
+    need = L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_deform_project(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
+                                    _p(rec), _p(tile_count), _p(ws), ws.numel(), _stream(stream)))
+    return rec, tile_count
+
+
+def wrf_bin(rec, n: int, Q: int, grid, key_capacity: int, gids=None, n_keys=None, offsets=None,
+            ws=None, stream=None):
+    """Tile lists: gids [cap] (uint32 stored as int32), n_keys [1] int64, offsets [Q*T+1]."""
+    L = _lib.load()
+    dev = rec.device
+    T = tiles_of(grid)
+    if gids is None:
+        gids = torch.empty(max(int(key_capacity), 1), dtype=torch.int32, device=dev)
+    if n_keys is None:
+        n_keys = torch.empty(1, dtype=torch.int64, device=dev)
+    if offsets is None:
+        offsets = torch.empty(Q * T + 1, dtype=torch.int32, device=dev)
+    need = L.wrf_bin_workspace_size(n, Q, C.byref(grid))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_bin(_p(rec), n, Q, C.byref(grid), _p(gids), int(key_capacity), _p(n_keys),
+                         _p(offsets), _p(ws), ws.numel(), _stream(stream)))
+    return gids, n_keys, offsets
+
+
+def wrf_render(rec, gids, offsets, n_keys, key_capacity: int, n: int, Q: int, grid, out=None,
+               stream=None):
+    L = _lib.load()
+    if out is None:
+        out = torch.empty((Q, grid.H, grid.W), dtype=torch.float32, device=offsets.device)
+    _lib.check(L.wrf_render(_p(rec), _p(gids), _p(offsets), _p(n_keys), int(key_capacity), n, Q,
+                            C.byref(grid), _p(out), _stream(stream)))
+    return out
+
+
+def wrf_render_backward(rec, gids, offsets, n_keys, key_capacity: int, n: int, Q: int, grid,
+                        dA, d_rec=None, stream=None):
+    L = _lib.load()
+    if d_rec is None:
+        d_rec = torch.zeros((Q, n, 6), dtype=torch.float32, device=dA.device)
+    _lib.check(L.wrf_render_backward(_p(rec), _p(gids), _p(offsets), _p(n_keys),
+                                     int(key_capacity), n, Q, C.byref(grid), _p(dA.contiguous()),
+                                     _p(d_rec), _stream(stream)))
+    return d_rec
+
+
+def wrf_project_backward(scene: DeviceScene, resid, Q: int, d_rec, d_resid=None, stream=None):
+    L = _lib.load()
+    dev, N = scene.mean.device, scene.n
+    if d_resid is None and resid is not None:
+        d_resid = torch.empty((Q, N, 5), dtype=torch.float32, device=dev)
+    g = dict(d_mean=torch.empty((N, 2), device=dev), d_log_scale=torch.empty((N, 2), device=dev),
+             d_rot=torch.empty(N, device=dev), d_opacity=torch.empty(N, device=dev),
+             d_amp=torch.empty(N, device=dev))
+    _lib.check(L.wrf_project_backward(C.byref(scene.c()), _p(resid), Q, _p(d_rec), _p(d_resid),
+                                      _p(g["d_mean"]), _p(g["d_log_scale"]), _p(g["d_rot"]),
+                                      _p(g["d_opacity"]), _p(g["d_amp"]), _stream(stream)))
+    g["d_resid"] = d_resid
+    return g
+
+
+def wrf_deform_backward(scene: DeviceScene, mlp: DeviceMLP, grid, tx, d_resid, d_mean=None,
+                        stop_grad_mean=False, ws=None, stream=None):
+    """dW, db (lists) and d_mean accumulated through gamma(mean) (unless stopped)."""
+    L = _lib.load()
+    dev, Q = tx.device, int(tx.shape[0])
+    mc = mlp.c()
+    dW = [torch.empty_like(w) for w in mlp.W]
+    db = [torch.empty_like(b) for b in mlp.b]
+    if d_mean is None:
+        d_mean = torch.zeros((scene.n, 2), dtype=torch.float32, device=dev)
+    arr = C.c_void_p * len(dW)
+    pW = arr(*[w.data_ptr() for w in dW])
+    pb = arr(*[b.data_ptr() for b in db])
+    need = L.wrf_deform_backward_workspace_size(scene.n, Q, C.byref(mc))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_deform_backward(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
+                                     _p(d_resid), pW, pb, _p(d_mean), int(bool(stop_grad_mean)),
+                                     _p(ws), ws.numel(), _stream(stream)))
+    return dW, db, d_mean
+
+
+def wrf_status_read(stream=None) -> int:
+    """First device-side status recorded since the last read (synchronises)."""
+    return int(_lib.load().wrf_status_read(_stream(stream)))
+
+
+class Renderer:
+    """The forward path (deform+project -> bin -> render) with reusable
+    workspaces and a key capacity that grows when binning reports overflow.
+
+    The tile lists and records of the last call are kept for the backward.
+    """
+
+    def __init__(self, grid, device="cuda", key_capacity: int = 0, fused: bool = True):
+        self.grid = grid
+        self.device = torch.device(device)
+        self.cap = int(key_capacity)
+        self.fused = fused
+        self._ws = {}
+
+    def _buf(self, name, nbytes):
+        b = self._ws.get(name)
+        if b is None or b.numel() < nbytes:
+            b = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.device)
+            self._ws[name] = b
+        return b
+
+    def _tensor(self, name, shape, dtype):
+        numel = int(np.prod(shape))
+        nbytes = numel * torch.empty((), dtype=dtype).element_size()
+        return self._buf(name, nbytes)[:nbytes].view(dtype)[:numel].view(shape)
+
+    def project(self, scene: DeviceScene, mlp, tx, stream=None):
+        L = _lib.load()
+        Q = int(tx.shape[0])
+        rec = self._tensor("rec", (Q, scene.n, 8), torch.float32)
+        if mlp is None:
+            wrf_project(scene, None, Q, self.grid, rec=rec, tile_count=None, stream=stream)
+            return rec, None
+        mc = mlp.c()
+        ws = self._buf("dws", L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc)))
+        if self.fused:
+            wrf_deform_project(scene, mlp, self.grid, tx, rec=rec, ws=ws, stream=stream)
+            return rec, None
+        resid = self._tensor("resid", (Q, scene.n, 5), torch.float32)
+        wrf_deform(scene, mlp, self.grid, tx, resid=resid, ws=ws, stream=stream)
+        wrf_project(scene, resid, Q, self.grid, rec=rec, tile_count=None, stream=stream)
+        return rec, resid
+
+    def bin_and_render(self, rec, n, Q, stream=None, out=None):
+        L = _lib.load()
+        T = tiles_of(self.grid)
+        if self.cap <= 0:
+            self.cap = max(1 << 16, Q * n * 6)
+        while True:
+            gids = self._tensor("gids", (self.cap,), torch.int32)
+            n_keys = self._tensor("nk", (1,), torch.int64)
+            offs = self._tensor("offs", (Q * T + 1,), torch.int32)
+            bws = self._buf("bws", L.wrf_bin_workspace_size(n, Q, C.byref(self.grid)))
+            wrf_bin(rec, n, Q, self.grid, self.cap, gids=gids, n_keys=n_keys, offsets=offs,
+                    ws=bws, stream=stream)
+            need = int(n_keys.item())
+            if need <= self.cap:
+                break
+            wrf_status_read(stream)  # clear the recorded overflow
+            self.cap = int(need * 1.25) + 1024
+        out = wrf_render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out,
+                         stream=stream)
+        self.last = dict(rec=rec, gids=gids, offs=offs, n_keys=n_keys, n=n, Q=Q)
+        return out
+
+    def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None):
+        Q = int(tx.shape[0])
+        rec, resid = self.project(scene, mlp, tx, stream=stream)
+        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out)
+        self.last["resid"] = resid
+        return out

@@ -1,0 +1,348 @@
+// C ABI entry points (include/wrf.h): argument checks, workspace carve-up and
+// kernel launches.  No entry point allocates device memory or synchronises,
+// except wrf_status_read which is documented to synchronise its stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "kernels.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+__device__ int g_status;  // first device-side error since the last read
+
+wrf_status fail(wrf_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+wrf_status cuda_fail(cudaError_t e, const char *where) {
+    return fail(WRF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+// Device address of g_status for the current device (looked up once per
+// device; the first call on a device should happen outside stream capture).
+int *status_ptr() {
+    static int *ptrs[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+        ptrs[dev] = static_cast<int *>(p);
+    }
+    return ptrs[dev];
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+wrf_status check_scene(const wrf_scene *s) {
+    if (!s) return fail(WRF_EINVAL, "scene is NULL");
+    if (s->n < 0) return fail(WRF_EINVAL, "scene.n < 0");
+    if (s->channels != 1) return fail(WRF_EUNSUPPORTED, "only channels == 1 is supported");
+    if (s->n > 0 && (!s->mean || !s->log_scale || !s->rot || !s->opacity_logit || !s->amp))
+        return fail(WRF_EINVAL, "scene array is NULL");
+    if (s->n > 0 && (!aligned(s->mean, 8) || !aligned(s->log_scale, 8)))
+        return fail(WRF_EINVAL, "scene.mean / log_scale must be 8-byte aligned");
+    return WRF_OK;
+}
+
+wrf_status check_grid(const wrf_grid *g, wrf::GridView *v) {
+    if (!g) return fail(WRF_EINVAL, "grid is NULL");
+    if (g->H < 1 || g->W < 1 || g->H > 65536 || g->W > 65536)
+        return fail(WRF_EINVAL, "grid H/W out of range");
+    if (!wrf::render_config_supported(g->tile_w, g->tile_h))
+        return fail(WRF_EUNSUPPORTED, "tile %dx%d not supported", g->tile_w, g->tile_h);
+    if (!(g->q_cut > 0.f)) return fail(WRF_EINVAL, "q_cut must be > 0 (or +inf)");
+    v->H = g->H;
+    v->W = g->W;
+    v->tw = g->tile_w;
+    v->th = g->tile_h;
+    v->ntx = (g->W + g->tile_w - 1) / g->tile_w;
+    v->nty = (g->H + g->tile_h - 1) / g->tile_h;
+    v->T = v->ntx * v->nty;
+    v->q_cut = g->q_cut;
+    if (v->T > 3000) return fail(WRF_EUNSUPPORTED, "more than 3000 tiles");
+    return WRF_OK;
+}
+
+wrf_status check_mlp(const wrf_mlp *m, wrf::MlpView *v) {
+    if (!m) return fail(WRF_EINVAL, "mlp is NULL");
+    if (m->n_layers < 2 || m->n_layers > WRF_MAX_LAYERS)
+        return fail(WRF_EUNSUPPORTED, "n_layers must be in [2, 8]");
+    if (m->L_mean < 0 || m->L_mean > 15 || m->L_tx < 0 || m->L_tx > 15)
+        return fail(WRF_EUNSUPPORTED, "frequency bands must be in [0, 15]");
+    const int dm = 2 * (2 * m->L_mean + 1), dt = 3 * (2 * m->L_tx + 1);
+    if (m->dims[0] != dm + dt) return fail(WRF_EINVAL, "dims[0] != 2(2L_mean+1)+3(2L_tx+1)");
+    for (int l = 1; l < m->n_layers; ++l)
+        if (m->dims[l] != WRF_HIDDEN) return fail(WRF_EUNSUPPORTED, "hidden widths must be 128");
+    if (m->dims[m->n_layers] != WRF_OUT) return fail(WRF_EUNSUPPORTED, "output width must be 5");
+    for (int l = 0; l < m->n_layers; ++l)
+        if (!m->W[l] || !m->b[l]) return fail(WRF_EINVAL, "weight %d is NULL", l);
+    for (int i = 0; i < 3; ++i)
+        if (!(m->room_size[i] > 0.f)) return fail(WRF_EINVAL, "room_size must be > 0");
+    if (m->precision != WRF_FP32 && m->precision != WRF_BF16)
+        return fail(WRF_EINVAL, "unknown precision");
+    if (m->precision == WRF_BF16 && m->n_layers > 5)
+        return fail(WRF_EUNSUPPORTED, "BF16 tensor-core path keeps <= 3 hidden layers resident");
+    v->n_layers = m->n_layers;
+    v->dm = dm;
+    v->dt = dt;
+    v->L_mean = m->L_mean;
+    v->L_tx = m->L_tx;
+    for (int i = 0; i < 3; ++i) {
+        v->room_min[i] = m->room_min[i];
+        v->room_size[i] = m->room_size[i];
+    }
+    v->W0 = m->W[0];
+    v->b0 = m->b[0];
+    for (int l = 0; l < 8; ++l) {
+        v->Wh[l] = (l + 1 < m->n_layers - 1) ? m->W[l + 1] : nullptr;
+        v->bh[l] = (l + 1 < m->n_layers - 1) ? m->b[l + 1] : nullptr;
+    }
+    v->Wo = m->W[m->n_layers - 1];
+    v->bo = m->b[m->n_layers - 1];
+    return WRF_OK;
+}
+
+wrf::SceneView view(const wrf_scene *s) {
+    return wrf::SceneView{s->n, s->mean, s->log_scale, s->rot, s->opacity_logit, s->amp};
+}
+
+bool rows_ok(int n, int Q) { return static_cast<long long>(n) * Q < (1ll << 31); }
+
+}  // namespace
+
+extern "C" {
+
+int32_t wrf_version(void) { return 1; }
+
+const char *wrf_last_error(void) { return g_err; }
+
+wrf_status wrf_status_read(void *stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int *p = status_ptr();
+    if (!p) return fail(WRF_ECUDA, "status word unavailable");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, p, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "wrf_status_read");
+    if (h != 0) {
+        int z = 0;
+        e = cudaMemcpyAsync(p, &z, sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "wrf_status_read");
+        return fail(static_cast<wrf_status>(h), "device status %d", h);
+    }
+    return WRF_OK;
+}
+
+size_t wrf_deform_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp) {
+    int nl = mlp ? mlp->n_layers : 5;
+    return wrf::deform_ws_layout(n < 0 ? 0 : n, Q < 0 ? 0 : Q, nl, nullptr, nullptr);
+}
+
+static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                                const float *tx, int32_t Q, int mode, float *resid, float *rec,
+                                uint32_t *tile_count, void *ws, size_t ws_bytes, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    wrf::MlpView m{};
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if ((s = check_mlp(mlp, &m)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    if (Q > 0 && !tx) return fail(WRF_EINVAL, "tx is NULL");
+    if (mode == 0 && Q > 0 && scene->n > 0 && !resid) return fail(WRF_EINVAL, "resid is NULL");
+    if (mode == 1 && Q > 0 && scene->n > 0 && (!rec || !aligned(rec, 16)))
+        return fail(WRF_EINVAL, "rec must be non-NULL and 16-byte aligned");
+    size_t need = wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    if (Q == 0 || scene->n == 0) return WRF_OK;
+    wrf::DeformWs w{};
+    wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, &w, static_cast<char *>(ws));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wrf::SceneView sv = view(scene);
+    int *status = status_ptr();
+    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, mlp->precision == WRF_BF16, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prep");
+    if (mlp->precision == WRF_BF16)
+        e = wrf::launch_mlp_tc(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
+                               tile_count, status, st);
+    else
+        e = wrf::launch_mlp_f32(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
+                                tile_count, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp");
+    return WRF_OK;
+}
+
+wrf_status wrf_deform(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                      const float *tx, int32_t Q, float *resid, void *ws, size_t ws_bytes,
+                      void *stream) {
+    return deform_common(scene, mlp, grid, tx, Q, 0, resid, nullptr, nullptr, ws, ws_bytes,
+                         stream);
+}
+
+wrf_status wrf_deform_project(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                              const float *tx, int32_t Q, float *rec, uint32_t *tile_count,
+                              void *ws, size_t ws_bytes, void *stream) {
+    return deform_common(scene, mlp, grid, tx, Q, 1, nullptr, rec, tile_count, ws, ws_bytes,
+                         stream);
+}
+
+wrf_status wrf_project(const wrf_scene *scene, const float *resid, int32_t Q,
+                       const wrf_grid *grid, float *rec, uint32_t *tile_count, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    if (Q == 0 || scene->n == 0) return WRF_OK;
+    if (!rec || !aligned(rec, 16)) return fail(WRF_EINVAL, "rec must be 16-byte aligned");
+    cudaError_t e = wrf::launch_project(view(scene), resid, Q, g, reinterpret_cast<float4 *>(rec),
+                                        tile_count, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "project");
+    return WRF_OK;
+}
+
+size_t wrf_bin_workspace_size(int32_t n, int32_t Q, const wrf_grid *grid) {
+    wrf::GridView g{};
+    if (!grid || check_grid(grid, &g) != WRF_OK) return 0;
+    return wrf::bin_ws_layout(n < 0 ? 0 : n, Q < 0 ? 0 : Q, g, nullptr, nullptr);
+}
+
+wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid, uint32_t *gids,
+                   int64_t key_capacity, int64_t *n_keys_out, uint32_t *tile_offsets, void *ws,
+                   size_t ws_bytes, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n < 0 || Q < 0 || key_capacity < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (!rows_ok(n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    if (!n_keys_out || !tile_offsets) return fail(WRF_EINVAL, "n_keys_out / tile_offsets NULL");
+    if (n > 0 && Q > 0 && (!rec || !aligned(rec, 16))) return fail(WRF_EINVAL, "rec alignment");
+    if (key_capacity > 0 && !gids) return fail(WRF_EINVAL, "gids is NULL");
+    size_t need = wrf::bin_ws_layout(n, Q, g, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    if (Q == 0) return WRF_OK;
+    wrf::BinWs w{};
+    wrf::bin_ws_layout(n, Q, g, &w, static_cast<char *>(ws));
+    cudaError_t e = wrf::launch_bin(reinterpret_cast<const float4 *>(rec), n, Q, g, gids,
+                                    key_capacity, reinterpret_cast<long long *>(n_keys_out),
+                                    tile_offsets, w, status_ptr(), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "bin");
+    return WRF_OK;
+}
+
+wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *tile_offsets,
+                      const int64_t *n_keys, int64_t key_capacity, int32_t n, int32_t Q,
+                      const wrf_grid *grid, float *spectra, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n < 0 || Q < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (Q == 0) return WRF_OK;
+    if (!tile_offsets || !n_keys || !spectra) return fail(WRF_EINVAL, "NULL pointer");
+    if (!aligned(spectra, 16) || (n > 0 && !aligned(rec, 16)))
+        return fail(WRF_EINVAL, "spectra / rec must be 16-byte aligned");
+    cudaError_t e = wrf::launch_render(reinterpret_cast<const float4 *>(rec), gids, tile_offsets,
+                                       reinterpret_cast<const long long *>(n_keys), key_capacity,
+                                       n, Q, g, spectra, status_ptr(),
+                                       static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render");
+    return WRF_OK;
+}
+
+wrf_status wrf_render_backward(const float *rec, const uint32_t *gids,
+                               const uint32_t *tile_offsets, const int64_t *n_keys,
+                               int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
+                               const float *dL_dspectra, float *d_rec, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n < 0 || Q < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (Q == 0 || n == 0) return WRF_OK;
+    if (!rec || !tile_offsets || !n_keys || !dL_dspectra || !d_rec)
+        return fail(WRF_EINVAL, "NULL pointer");
+    cudaError_t e = wrf::launch_render_bwd(reinterpret_cast<const float4 *>(rec), gids,
+                                           tile_offsets,
+                                           reinterpret_cast<const long long *>(n_keys),
+                                           key_capacity, n, Q, g, dL_dspectra, d_rec,
+                                           status_ptr(), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render_backward");
+    return WRF_OK;
+}
+
+wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int32_t Q,
+                                const float *d_rec, float *d_resid, float *d_mean,
+                                float *d_log_scale, float *d_rot, float *d_opacity, float *d_amp,
+                                void *stream) {
+    wrf_status s;
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    if (scene->n == 0) return WRF_OK;
+    if ((Q > 0 && !d_rec) || !d_mean || !d_log_scale || !d_rot || !d_opacity || !d_amp)
+        return fail(WRF_EINVAL, "NULL pointer");
+    cudaError_t e = wrf::launch_project_bwd(view(scene), resid, Q, d_rec, d_resid, d_mean,
+                                            d_log_scale, d_rot, d_opacity, d_amp,
+                                            static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "project_backward");
+    return WRF_OK;
+}
+
+size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp) {
+    wrf::MlpView m{};
+    if (!mlp || check_mlp(mlp, &m) != WRF_OK) return 0;
+    return wrf::deform_bwd_ws_layout(n < 0 ? 0 : n, Q < 0 ? 0 : Q, m, nullptr, nullptr, nullptr);
+}
+
+wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                               const float *tx, int32_t Q, const float *d_resid, float *const *dW,
+                               float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
+                               size_t ws_bytes, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    wrf::MlpView m{};
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if ((s = check_mlp(mlp, &m)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    if (!dW || !db) return fail(WRF_EINVAL, "dW / db NULL");
+    for (int l = 0; l < mlp->n_layers; ++l)
+        if (!dW[l] || !db[l]) return fail(WRF_EINVAL, "dW[%d] / db[%d] NULL", l, l);
+    if (!stop_grad_mean && scene->n > 0 && !d_mean) return fail(WRF_EINVAL, "d_mean NULL");
+    if (Q > 0 && (!tx || !d_resid)) return fail(WRF_EINVAL, "tx / d_resid NULL");
+    size_t need = wrf::deform_bwd_ws_layout(scene->n, Q, m, nullptr, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    wrf::DeformWs fw{};
+    wrf::DeformBwdWs bw{};
+    wrf::deform_bwd_ws_layout(scene->n, Q, m, &fw, &bw, static_cast<char *>(ws));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wrf::SceneView sv = view(scene);
+    cudaError_t e = cudaSuccess;
+    if (Q > 0 && scene->n > 0) {
+        e = wrf::launch_prep(sv, m, g, tx, Q, fw, false, st);
+        if (e != cudaSuccess) return cuda_fail(e, "prep");
+    }
+    e = wrf::launch_mlp_bwd(sv, m, g, Q, fw, bw, d_resid, dW, db, d_mean, stop_grad_mean, st);
+    if (e != cudaSuccess) return cuda_fail(e, "mlp_backward");
+    return WRF_OK;
+}
+
+}  // extern "C"

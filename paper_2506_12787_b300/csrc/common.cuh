@@ -1,0 +1,161 @@
+// Shared device helpers for the spectrum-synthesis kernels (sm_103a).
+//
+// Contents: status codes, bounded waits, PTX wrappers for mbarriers and bulk
+// (TMA) copies, the per-Gaussian projection (Sec. 4.2 Eq. 12-13 with the
+// residual head dx, dy, drot, dls1, dls2) and the footprint tile rectangle.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/wrf.h"
+
+namespace wrf {
+
+// log2(e)/2: exp(-q/2) == exp2(-q * kHalfLog2e).
+constexpr float kHalfLog2e = 0.72134752044448170368f;
+
+// Bounded waits give up after this many nanoseconds of %globaltimer.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+struct GridView {
+    int H, W, tw, th, ntx, nty, T;
+    float q_cut;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void record_status(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---------------------------------------------------------------- mbarrier
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of `bar` to complete; gives up after kWaitLimitNs,
+// records WRF_ETIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            record_status(status, WRF_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ------------------------------------------------------------ bulk copies
+// Non-tensor bulk copy global -> shared, completion counted in bytes on
+// `bar`.  Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------- footprint rectangle
+// Tiles covered by a record's footprint: pixels ceil(mx-rx)..floor(mx+rx)
+// (and likewise in y) clipped to the grid, divided by the tile size.  Every
+// step is an exactly rounded FP32 operation so the result is a fixed integer
+// function of the stored record.
+__device__ __forceinline__ bool tile_rect(float mx, float my, float rx, float ry,
+                                          const GridView &g, int &tx0, int &tx1, int &ty0,
+                                          int &ty1) {
+    float xlo = __fsub_rn(mx, rx), xhi = __fadd_rn(mx, rx);
+    float ylo = __fsub_rn(my, ry), yhi = __fadd_rn(my, ry);
+    float wm = static_cast<float>(g.W - 1), hm = static_cast<float>(g.H - 1);
+    if (!(xhi >= 0.f) || !(xlo <= wm) || !(yhi >= 0.f) || !(ylo <= hm)) return false;
+    float ax = ceilf(fmaxf(xlo, 0.f)), bx = floorf(fminf(xhi, wm));
+    float ay = ceilf(fmaxf(ylo, 0.f)), by = floorf(fminf(yhi, hm));
+    if (ax > bx || ay > by) return false;
+    tx0 = static_cast<int>(ax) / g.tw;
+    tx1 = static_cast<int>(bx) / g.tw;
+    ty0 = static_cast<int>(ay) / g.th;
+    ty1 = static_cast<int>(by) / g.th;
+    return true;
+}
+
+// ------------------------------------------------------------- projection
+struct SceneView {
+    int n;
+    const float *mean, *log_scale, *rot, *opacity_logit, *amp;
+};
+
+// Deform Gaussian n by its residual (Eq. 12) and project it to a record:
+// centre, log2(e)/2-scaled inverse covariance of R(th) diag(s1^2, s2^2) R^T,
+// weight sigmoid(a) * amp (Sec. 4.1) and footprint half-widths.
+__device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float d0, float d1,
+                                                float d2, float d3, float d4, const GridView &g,
+                                                float4 &r0, float4 &r1) {
+    float2 m = reinterpret_cast<const float2 *>(s.mean)[n];
+    float2 ls = reinterpret_cast<const float2 *>(s.log_scale)[n];
+    float mx = m.x + d0, my = m.y + d1;
+    float th = s.rot[n] + d2;
+    float l1 = ls.x + d3, l2 = ls.y + d4;
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    float v1 = expf(2.f * l1), v2 = expf(2.f * l2);
+    float i1 = expf(-2.f * l1), i2 = expf(-2.f * l2);
+    float cc = cs * cs, ss = sn * sn, csn = cs * sn;
+    float sxx = cc * v1 + ss * v2, syy = ss * v1 + cc * v2;
+    float A = cc * i1 + ss * i2, B = csn * (i1 - i2), C = ss * i1 + cc * i2;
+    float w = s.amp[n] / (1.f + expf(-s.opacity_logit[n]));
+    float rx = sqrtf(g.q_cut * sxx), ry = sqrtf(g.q_cut * syy);
+    r0 = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
+    r1 = make_float4(C * kHalfLog2e, w, rx, ry);
+    int a, b, c, d;
+    if (!tile_rect(mx, my, rx, ry, g, a, b, c, d)) return 0u;
+    return static_cast<uint32_t>((b - a + 1) * (d - c + 1));
+}
+
+// ------------------------------------------------------ positional encoding
+// Eq. 15 for one component x at band k: sin(2^k pi x), cos(2^k pi x).
+// 2^k * x is exact in FP32, and sincospif reduces the argument exactly.
+__device__ __forceinline__ void pe_band(float x, int k, float &s, float &c) {
+    sincospif(ldexpf(x, k), &s, &c);
+}
+
+}  // namespace wrf

@@ -1,0 +1,90 @@
+// Internal launcher declarations shared by the kernel files and the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace wrf {
+
+// Weight images prepared once per call from the caller's FP32 weights.
+struct MlpView {
+    int n_layers;          // Linear layers (>= 2)
+    int dm, dt;            // widths of gamma(mean) and gamma(tx)
+    int L_mean, L_tx;
+    float room_min[3], room_size[3];
+    const float *W0;       // [128][dm+dt] (caller's first layer)
+    const float *b0;       // [128]
+    const float *Wh[8];    // hidden layers 1..n_layers-2: [128][128]
+    const float *bh[8];
+    const float *Wo;       // output layer [5][128]
+    const float *bo;       // [5]
+};
+
+// Workspace carve-up for deformation (all offsets 256-byte aligned).
+struct DeformWs {
+    float *U;              // [N][128]  W0[:, :dm] gamma(mean_n)
+    float *V;              // [Q][128]  W0[:, dm:] gamma(tx_q) + b0
+    float *wt_f32;         // hidden layers transposed [l][k=128][j=128], FP32
+    float *wo_f32;         // output layer transposed [k=128][8] (cols 5..7 zero)
+    uint16_t *w_bf16;      // tcgen05 operand images of hidden + output layers
+};
+
+size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base);
+
+cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
+                        int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st);
+
+// mode 0: write residuals [Q][N][5]; mode 1: project and write records.
+cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                           const DeformWs &ws, int mode, float *resid, float4 *rec,
+                           uint32_t *count, cudaStream_t st);
+cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                          const DeformWs &ws, int mode, float *resid, float4 *rec,
+                          uint32_t *count, int *status, cudaStream_t st);
+
+cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
+                           float4 *rec, uint32_t *count, cudaStream_t st);
+
+// Binning.
+struct BinWs {
+    uint32_t *chunk_counts;  // [Q][T][C]
+    unsigned long long *block_sums;
+    int C;                   // chunks of kBinChunk Gaussians per query
+    long long M;             // Q*T*C
+    int nblocks;
+};
+constexpr int kBinChunk = 1024;
+size_t bin_ws_layout(int n, int Q, const GridView &g, BinWs *ws, char *base);
+cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint32_t *gids,
+                       long long cap, long long *n_keys, uint32_t *offsets, const BinWs &ws,
+                       int *status, cudaStream_t st);
+
+// Rasteriser.
+cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
+                          const long long *n_keys, long long cap, int n, int Q,
+                          const GridView &g, float *out, int *status, cudaStream_t st);
+cudaError_t launch_render_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
+                              const long long *n_keys, long long cap, int n, int Q,
+                              const GridView &g, const float *dA, float *d_rec, int *status,
+                              cudaStream_t st);
+cudaError_t launch_project_bwd(const SceneView &s, const float *resid, int Q, const float *d_rec,
+                               float *d_resid, float *d_mean, float *d_ls, float *d_rot,
+                               float *d_op, float *d_amp, cudaStream_t st);
+
+// MLP backward.
+struct DeformBwdWs {
+    float *partials;   // [nblocks][P] per-block parameter-gradient partials
+    int nblocks;
+    int P;             // parameter count
+};
+size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, DeformBwdWs *bw,
+                            char *base);
+cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                           const DeformWs &fw, const DeformBwdWs &bw, const float *d_resid,
+                           float *const *dW, float *const *db, float *d_mean, int stop_grad_mean,
+                           cudaStream_t st);
+
+bool render_config_supported(int tw, int th);
+
+}  // namespace wrf

@@ -1,0 +1,166 @@
+// Preparation for the deformation MLP (Sec. 4.2, Eqs. 14-15).
+//
+// The first Linear layer acts on [gamma(mean_n), gamma(tx_q)], so its
+// pre-activation splits exactly into a per-Gaussian part and a per-query
+// part:  W0 [gamma(mu_n); gamma(s_q)] + b0 = U[n] + V[q] with
+//   U[n] = W0[:, :dm] gamma(mu_n),   V[q] = W0[:, dm:] gamma(s_q) + b0.
+// U costs N*128*dm FMAs and V Q*128*dt, instead of Q*N*128*(dm+dt); the MLP
+// kernels then start every row from ReLU(U[n] + V[q]).
+//
+// This file also builds the weight images the MLP kernels read: FP32
+// transposed copies for the CUDA-core path and BF16 K-major 128-byte-swizzled
+// operand images for the tcgen05 path.
+#include <cuda_bf16.h>
+
+#include "kernels.h"
+
+namespace wrf {
+
+namespace {
+
+constexpr int kMaxPe = 3 * (2 * 15 + 1);  // d(2L+1) for d <= 3, L <= 15
+
+// gamma(x) of Eq. 15 for a d-vector, written to out[d(2L+1)] in the order
+// [x, sin band 0 (all d), ..., sin band L-1, cos band 0, ..., cos band L-1].
+__device__ void encode(const float *x, int d, int L, float *out) {
+    for (int i = 0; i < d; ++i) out[i] = x[i];
+    for (int k = 0; k < L; ++k)
+        for (int i = 0; i < d; ++i) {
+            float s, c;
+            pe_band(x[i], k, s, c);
+            out[d + k * d + i] = s;
+            out[d + L * d + k * d + i] = c;
+        }
+}
+
+// U[n][j] for 32 Gaussians per block; thread j owns output column j.
+__global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, GridView g,
+                                                      float *U) {
+    __shared__ float gam[32][kMaxPe];
+    const int n0 = blockIdx.x * 32;
+    const int din = m.dm + m.dt;
+    if (threadIdx.x < 32) {
+        int n = n0 + threadIdx.x;
+        if (n < s.n) {
+            float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
+            float x[2] = {mu.x / static_cast<float>(g.W), mu.y / static_cast<float>(g.H)};
+            encode(x, 2, m.L_mean, gam[threadIdx.x]);
+        }
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    const float *wrow = m.W0 + static_cast<size_t>(j) * din;
+    float w[kMaxPe];
+#pragma unroll 4
+    for (int k = 0; k < m.dm; ++k) w[k] = wrow[k];
+    for (int r = 0; r < 32 && n0 + r < s.n; ++r) {
+        float acc = 0.f;
+        for (int k = 0; k < m.dm; ++k) acc = fmaf(w[k], gam[r][k], acc);
+        U[static_cast<size_t>(n0 + r) * WRF_HIDDEN + j] = acc;
+    }
+}
+
+// V[q][j] for 32 queries per block.
+__global__ void __launch_bounds__(128) pe_tx_kernel(MlpView m, const float *tx, int Q, float *V) {
+    __shared__ float gam[32][kMaxPe];
+    const int q0 = blockIdx.x * 32;
+    const int din = m.dm + m.dt;
+    if (threadIdx.x < 32) {
+        int q = q0 + threadIdx.x;
+        if (q < Q) {
+            float x[3];
+            for (int i = 0; i < 3; ++i)
+                x[i] = (tx[3 * q + i] - m.room_min[i]) / m.room_size[i];
+            encode(x, 3, m.L_tx, gam[threadIdx.x]);
+        }
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    const float *wrow = m.W0 + static_cast<size_t>(j) * din + m.dm;
+    const float bj = m.b0[j];
+    for (int r = 0; r < 32 && q0 + r < Q; ++r) {
+        float acc = 0.f;
+        for (int k = 0; k < m.dt; ++k) acc = fmaf(wrow[k], gam[r][k], acc);
+        V[static_cast<size_t>(q0 + r) * WRF_HIDDEN + j] = acc + bj;
+    }
+}
+
+// Byte offset of element (row n, col k) in a K-major, 128-byte-swizzled
+// tcgen05 operand image with `rows` rows and 128 columns of BF16: two
+// 64-column halves of rows x 128 B; inside a row the 16-byte chunk index
+// (k % 64) / 8 is XORed with n % 8.
+__device__ __forceinline__ uint32_t sw128_offset(int n, int k, int rows) {
+    int half = k >> 6, kk = k & 63;
+    return static_cast<uint32_t>(half * rows * 128 + n * 128 + ((((kk >> 3) ^ (n & 7))) << 4) +
+                                 ((kk & 7) << 1));
+}
+
+// One thread per (layer, row, col) of every hidden layer and the output
+// layer: FP32 transposes and BF16 swizzled images.
+__global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
+    const int nh = m.n_layers - 2;
+    const long long per = WRF_HIDDEN * WRF_HIDDEN;
+    const long long total = nh * per + 16 * WRF_HIDDEN;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (i < nh * per) {
+            int l = static_cast<int>(i / per);
+            int r = static_cast<int>(i % per);
+            int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // W[j][k]
+            float v = m.Wh[l][r];
+            ws.wt_f32[l * per + k * WRF_HIDDEN + j] = v;
+            if (want_bf16) {
+                char *img = reinterpret_cast<char *>(ws.w_bf16) + l * per * 2;
+                *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(j, k, WRF_HIDDEN)) =
+                    __float2bfloat16_rn(v);
+            }
+        } else {
+            int r = static_cast<int>(i - nh * per);
+            int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // output row j (< 16)
+            float v = j < WRF_OUT ? m.Wo[j * WRF_HIDDEN + k] : 0.f;
+            if (j < 8) ws.wo_f32[k * 8 + j] = v;
+            if (want_bf16) {
+                char *img = reinterpret_cast<char *>(ws.w_bf16) + nh * per * 2;
+                *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(j, k, 16)) =
+                    __float2bfloat16_rn(v);
+            }
+        }
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+}  // namespace
+
+size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off = align256(off + bytes);
+        return p;
+    };
+    int nh = n_layers - 2 > 0 ? n_layers - 2 : 0;
+    DeformWs w{};
+    w.U = reinterpret_cast<float *>(take(static_cast<size_t>(n) * WRF_HIDDEN * 4));
+    w.V = reinterpret_cast<float *>(take(static_cast<size_t>(Q) * WRF_HIDDEN * 4));
+    w.wt_f32 = reinterpret_cast<float *>(take(static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 4));
+    w.wo_f32 = reinterpret_cast<float *>(take(WRF_HIDDEN * 8 * 4));
+    w.w_bf16 = reinterpret_cast<uint16_t *>(
+        take(static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 2 + 16 * WRF_HIDDEN * 2));
+    if (ws) *ws = w;
+    return off;
+}
+
+cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
+                        int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st) {
+    if (s.n > 0) pe_mean_kernel<<<(s.n + 31) / 32, 128, 0, st>>>(s, m, g, ws.U);
+    if (Q > 0) pe_tx_kernel<<<(Q + 31) / 32, 128, 0, st>>>(m, tx, Q, ws.V);
+    long long total = static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
+                      16 * WRF_HIDDEN;
+    int blocks = static_cast<int>((total + 255) / 256);
+    if (blocks > 1184) blocks = 1184;
+    weights_kernel<<<blocks, 256, 0, st>>>(m, ws, want_bf16 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace wrf

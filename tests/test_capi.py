@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library builds, loads, and exports every
+entry point include/wrf.h declares; host-side argument validation runs
+without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wrf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(wrf_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_12787_b300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2506_12787_b300 import _lib
+    names = _declared()
+    assert len(names) >= 14
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(_lib.EXPORTS)
+
+
+def test_version_and_error_string(lib):
+    assert lib.wrf_version() >= 1
+    assert isinstance(lib.wrf_last_error(), bytes)
+
+
+def test_host_validation_rejects_bad_arguments(lib):
+    """Argument errors are caught on the host before any launch."""
+    from paper_2506_12787_b300 import _lib
+    g = _lib.Grid(90, 360, 12, 16, 9.0)  # unsupported tile shape
+    st = lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None)
+    assert st == _lib.WRF_EUNSUPPORTED
+    assert b"tile" in lib.wrf_last_error()
+    g = _lib.Grid(90, 360, 16, 16, -1.0)
+    assert lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None) == _lib.WRF_EINVAL
+    g = _lib.Grid(90, 360, 16, 16, 9.0)
+    # NULL outputs with Q > 0
+    assert lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None) == _lib.WRF_EINVAL
+    s = _lib.Scene(10, 2, None, None, None, None, None)  # two channels: unsupported
+    assert lib.wrf_project(C.byref(s), None, 1, C.byref(g), None, None, None) == _lib.WRF_EUNSUPPORTED
+    m = _lib.Mlp()
+    m.n_layers = 5
+    m.L_mean, m.L_tx = 6, 10
+    for i, d in enumerate([89, 128, 128, 128, 100, 5]):
+        m.dims[i] = d
+    assert lib.wrf_deform_workspace_size(10, 2, C.byref(m)) > 0
+    s = _lib.Scene(0, 1, None, None, None, None, None)
+    st = lib.wrf_deform(C.byref(s), C.byref(m), C.byref(g), None, 0, None, None, 0, None)
+    assert st == _lib.WRF_EUNSUPPORTED  # hidden width 100
+
+
+def test_workspace_sizes_are_monotone(lib):
+    from paper_2506_12787_b300 import _lib
+    g = _lib.Grid(90, 360, 16, 16, 9.0)
+    a = lib.wrf_bin_workspace_size(20000, 16, C.byref(g))
+    b = lib.wrf_bin_workspace_size(20000, 256, C.byref(g))
+    assert 0 < a < b
+
+
+def test_product_path_does_not_import_the_oracle():
+    """The library package never references the oracle or a CPU fallback."""
+    pkg = os.path.join(ROOT, "paper_2506_12787_b300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "liboracle" not in txt, f
