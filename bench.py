@@ -1,0 +1,413 @@
+"""Spectrum-synthesis benchmark: spectra/s of the batched forward on one B300.
+
+Workload (default, `batched`): 20,000 2D Gaussians (means uniform over the
+grid, log-scales ~ N(ln 3 px, 0.3^2), rotation U[0, pi), opacity
+sigmoid(N(0,1)), amplitude U(0,1)), a 360 x 90 FP32 spectrum, 256 TX
+positions uniform in a 5 x 5 x 3 m room per step, deformation MLP 89 ->
+4 x 128 ReLU -> 5 (Xavier x 0.1) on tensor cores with BF16 operands and FP32
+accumulation.  A step is one whole forward: positional encoding + MLP +
+deform + project (fused), tile binning, rasterisation.  Synthetic data
+stands in for the paper's indoor scenes (360 x 90 spectra, ~10k Gaussians).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launching stream; a 256 MB buffer (> 126 MB L2) is rewritten between steps.
+Multi-GPU (torchrun): every rank runs its own batch (independent replicas,
+weak scaling); rank 0 reports total spectra over the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    # name: (N, H, W, Q, ls_mean, ls_std)
+    "batched": (20000, 90, 360, 256, math.log(3.0), 0.3),
+    "large": (200000, 180, 720, 1024, math.log(2.0), 0.5),
+    "plain": (1024, 90, 360, 1, math.log(3.0), 0.3),
+}
+Q_CUT = 9.0
+MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
+RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
+BIN_BYTES_PER_REC = 32   # each record read once
+BIN_BYTES_PER_KEY = 4    # each Gaussian id written once
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
+    p.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--cpu-sample", type=int, default=192, help="queries timed on the CPU oracle")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(workload, rank):
+    N, H, W, Q, lsm, lss = WORKLOADS[workload]
+    sc = synth.make_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
+    m = synth.make_mlp(seed=0)
+    tx = synth.make_tx(Q, seed=1 + rank)
+    return sc, m, tx, (N, H, W, Q)
+
+
+def config_of(args, shape, extra=None):
+    N, H, W, Q = shape
+    c = {"workload": f"{args.workload}: {N} Gaussians, {W}x{H} FP32 spectrum, {Q} TX per step",
+         "gaussians": N, "H": H, "W": W, "queries_per_step": Q,
+         "mlp": "89-128x4-5 ReLU, " + ("BF16 tcgen05 / FP32 acc" if args.precision == "bf16"
+                                       else "FP32 CUDA cores"),
+         "q_cut": Q_CUT, "tile": args.tile, "l2": "256 MB buffer rewritten between timed steps",
+         "parallelism": f"replicas x{args.gpus}"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        # samples are ~100 ms apart; keep the ones taken under load (the top
+        # half of power draw) -- the timed region is the only sustained load
+        def fnum(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        pw = [fnum(r[3]) for r in rows]
+        thr = statistics.median(pw) if len(pw) > 2 else -1
+        load = [r for r, p in zip(rows, pw) if p >= thr] or rows
+        sm = [fnum(r[1]) for r in load]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in load for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": fnum(load[0][2]),
+                "reasons": reasons, "samples": len(load)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18):
+    """Number of (pixel, record) pairs with q <= q_cut over all records
+    [Q,N,8]: the evaluations the order-free sum needs (Eq. 9), counted per
+    record row by row from the ellipse's exact x-interval (torch, device).
+    Measurement helper: runs once, outside every timed region."""
+    import torch
+    flat = rec.reshape(-1, 8)
+    k = 0.5 / math.log(2.0)
+    total = 0
+    ys_rel = None
+    for s in range(0, flat.shape[0], chunk):
+        r = flat[s:s + chunk].double()
+        mx, my = r[:, 0], r[:, 1]
+        a, b, c = r[:, 2] / k, r[:, 3] / k, r[:, 4] / k
+        ry = r[:, 7]
+        y0 = torch.clamp(torch.ceil(my - ry), min=0)
+        y1 = torch.clamp(torch.floor(my + ry), max=H - 1)
+        nrow = int(torch.clamp(y1 - y0 + 1, min=0).max().item()) if r.shape[0] else 0
+        if nrow <= 0:
+            continue
+        ys_rel = torch.arange(nrow, device=r.device, dtype=torch.float64)
+        y = y0[:, None] + ys_rel[None, :]
+        valid = y <= y1[:, None]
+        dy = y - my[:, None]
+        # a dx^2 + 2 b dx dy + c dy^2 <= q_cut  ->  dx in [(-b dy - s)/a, (-b dy + s)/a]
+        disc = (b[:, None] * dy) ** 2 - a[:, None] * (c[:, None] * dy * dy - q_cut)
+        ok = valid & (disc >= 0)
+        sq = torch.sqrt(torch.clamp(disc, min=0))
+        lo = mx[:, None] + (-b[:, None] * dy - sq) / a[:, None]
+        hi = mx[:, None] + (-b[:, None] * dy + sq) / a[:, None]
+        lo = torch.clamp(torch.ceil(lo), min=0)
+        hi = torch.clamp(torch.floor(hi), max=W - 1)
+        cnt = torch.where(ok, torch.clamp(hi - lo + 1, min=0), torch.zeros_like(lo))
+        total += int(cnt.sum().item())
+    return total
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm, on a bounded sample."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    sc, m, tx, shape = make_inputs(args.workload, 0)
+    N, H, W, Q = shape
+    S = max(1, min(Q, 4))
+    for i in range(args.warmup):
+        oracle.forward(sc, m, tx[(i * S) % Q:(i * S) % Q + S], H, W, Q_CUT)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        j = (i * S) % Q
+        oracle.forward(sc, m, tx[j:j + S], H, W, Q_CUT)
+    dt = time.perf_counter() - t0
+    val = S * args.steps / dt
+    line = {"impl": "reference", "metric": "spectra/s", "value": val, "unit": "spectra/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, shape, {"sample": f"{S} of {Q} queries per step"}),
+            "cpu_baseline": {"value": val, "unit": "spectra/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{S} of {Q} TX queries per step, {N} Gaussians, "
+                                       f"{W}x{H}, FP64 C oracle (OpenMP)"},
+            "e2e": {"value": val, "unit": "spectra/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(args, sc, m, tx, shape):
+    import oracle
+    N, H, W, Q = shape
+    S = max(1, min(Q, args.cpu_sample))
+    oracle.forward(sc, m, tx[:1], H, W, Q_CUT)  # build + page in
+    t0 = time.perf_counter()
+    oracle.forward(sc, m, tx[:S], H, W, Q_CUT)
+    dt = time.perf_counter() - t0
+    return {"value": S / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {S} of {Q} TX queries of the workload, {N} Gaussians, {W}x{H}, "
+                      f"FP64 C oracle (OpenMP), {dt:.1f} s"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_12787_b300 import api
+    from paper_2506_12787_b300.batched import BatchedForward
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, m, tx_np, shape = make_inputs(args.workload, rank)
+    N, H, W, Q = shape
+    tw, th = (int(v) for v in args.tile.split("x"))
+    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
+    ds = api.DeviceScene.from_host(sc, dev)
+    dm = api.DeviceMLP.from_host(m, dev, precision=prec)
+    tx = torch.as_tensor(tx_np, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    fw = BatchedForward(ds, dm, grid, Q, dev)
+    with torch.cuda.stream(stream):
+        n_keys = fw.reserve(tx, stream)
+        fw.check(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # per-stage events (on the launching stream) inside every timed step
+    def step(evs=None):
+        if evs is None:
+            fw.run(tx, stream)
+            return
+        evs[0].record(stream)
+        fw.deform_project(tx, stream)
+        evs[1].record(stream)
+        fw.bin(stream)
+        evs[2].record(stream)
+        fw.render(stream)
+        evs[3].record(stream)
+
+    graph = fw.graph(tx, stream) if args.graph else None
+
+    def replay():
+        if graph is not None:
+            graph.replay()
+        else:
+            fw.run(tx, stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            replay()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    K = args.steps
+    # (1) whole-step timing
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            replay()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = sum(step_ms) / 1e3
+    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_max = float(t.item())
+    value = Q * K * ws / total_max
+
+    # (2) per-stage timing of the same step (eager launches, same stream)
+    KS = max(3, min(K, 50))
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(KS)]
+    with torch.cuda.stream(stream):
+        for i in range(KS):
+            flush.fill_(i & 255)
+            step(sev[i])
+    torch.cuda.synchronize()
+    stage = {name: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in sev)
+             for j, name in enumerate(("deform_project", "bin", "render"))}
+    clk = clocks.stop()
+    fw.check(stream)
+
+    # (3) end-to-end through host buffers: pinned TX in, pinned spectra out
+    tx_host = torch.as_tensor(tx_np).pin_memory()
+    out_host = torch.empty((Q, H, W), dtype=torch.float32).pin_memory()
+    KE = max(3, min(K, 50))
+    eev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(KE)]
+    with torch.cuda.stream(stream):
+        for i in range(KE):
+            flush.fill_(i & 255)
+            eev[i][0].record(stream)
+            tx.copy_(tx_host, non_blocking=True)
+            replay()
+            out_host.copy_(fw.out, non_blocking=True)
+            eev[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in eev) / 1e3
+    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_val = Q * KE * ws / float(te.item())
+
+    # roofline of the dominant stage
+    peaks, peak_src = measured_peaks()
+    dom = max(stage, key=stage.get)
+    if dom == "render":
+        E = count_in_cutoff(fw.rec, H, W, Q_CUT)
+        fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        roof = {"kernel": "render_kernel", "bound": "alu",
+                "achieved": RAST_FLOP_PER_EVAL * E / (stage["render"] * 1e-3) / 1e12,
+                "peak": fp32_peak, "unit": "TFLOP/s",
+                "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
+                "evals_in_cutoff": E}
+    elif dom == "deform_project":
+        rows = Q * N
+        pk = peaks["bf16_tflops"] if prec == api.WRF_BF16 else \
+            148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        roof = {"kernel": "mlp_tc_kernel" if prec == api.WRF_BF16 else "mlp_f32_kernel",
+                "bound": "tensor" if prec == api.WRF_BF16 else "alu",
+                "achieved": rows * MLP_FLOP_PER_ROW / (stage["deform_project"] * 1e-3) / 1e12,
+                "peak": pk, "unit": "TFLOP/s",
+                "peak_source": f"bf16_tflops ({peak_src})" if prec == api.WRF_BF16 else
+                               "FP32 148 SM x 128 lanes x 2 x max SM clock"}
+    else:
+        nbytes = BIN_BYTES_PER_REC * Q * N + BIN_BYTES_PER_KEY * n_keys + 4 * (Q * fw.T + 1)
+        roof = {"kernel": "bin (count+scan+scatter)", "bound": "hbm",
+                "achieved": nbytes / (stage["bin"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["stage_ms"] = stage
+
+    line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == api.WRF_BF16 else "f32", "data": "synthetic",
+            "config": config_of(args, shape, {"keys_per_step": n_keys,
+                                              "cuda_graph": bool(args.graph)}),
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": "spectra/s", "h2d_bytes_per_step": Q * 3 * 4,
+                    "d2h_bytes_per_step": Q * H * W * 4},
+            "gpu_launches": fw.launches_per_run * K,
+            "roofline": roof}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, sc, m, tx_np, shape)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

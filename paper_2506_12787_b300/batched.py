@@ -1,0 +1,108 @@
+"""Batched spectrum synthesis with preallocated device buffers.
+
+One ``BatchedForward`` holds everything a batch of Q queries over one
+resident scene needs (records, tile lists, workspaces, output) so that a
+forward is a fixed sequence of library calls on one stream with no host
+synchronisation: deform+project (Eq. 12-15) -> bin -> render (Eq. 9/13).
+Because nothing is allocated or read back inside ``run``, the sequence can be
+captured once into a CUDA graph and replayed.
+
+Key capacity: the number of (query, tile, Gaussian) keys depends on the
+queries.  ``reserve`` sizes the capacity from one measured forward plus a
+margin; if a later batch needs more, the library records WRF_ENOSPC in its
+status word and renders zeros, and ``check`` raises so the caller can
+``reserve`` again and rerun (the capacity never shrinks).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from .api import (DeviceMLP, DeviceScene, _p, _stream, tiles_of, wrf_bin, wrf_deform_project,
+                  wrf_render, wrf_status_read)
+
+
+class BatchedForward:
+    def __init__(self, scene: DeviceScene, mlp: DeviceMLP, grid, Q: int, device="cuda",
+                 key_capacity: int = 0, margin: float = 1.25):
+        self.scene, self.mlp, self.grid, self.Q = scene, mlp, grid, int(Q)
+        self.device = torch.device(device)
+        self.margin = margin
+        L = _lib.load()
+        n = scene.n
+        self.T = tiles_of(grid)
+        self._mc = mlp.c()
+        self.rec = torch.empty((self.Q, n, 8), dtype=torch.float32, device=self.device)
+        self.dws = torch.empty(max(256, L.wrf_deform_workspace_size(n, self.Q, C.byref(self._mc))),
+                               dtype=torch.uint8, device=self.device)
+        self.bws = torch.empty(max(256, L.wrf_bin_workspace_size(n, self.Q, C.byref(grid))),
+                               dtype=torch.uint8, device=self.device)
+        self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.offs = torch.empty(self.Q * self.T + 1, dtype=torch.int32, device=self.device)
+        self.out = torch.empty((self.Q, grid.H, grid.W), dtype=torch.float32, device=self.device)
+        self.cap = 0
+        self.gids = None
+        self._alloc_keys(int(key_capacity))
+
+    # kernels one run() launches: PE(mean), PE(tx), weight images, MLP;
+    # bin count, scan reduce, scan top, scan down-sweep, scatter; render
+    launches_per_run = 10
+
+    def _alloc_keys(self, cap: int):
+        cap = max(int(cap), 1024)
+        if cap > self.cap:
+            self.gids = torch.empty(cap, dtype=torch.int32, device=self.device)
+            self.cap = cap
+
+    def deform_project(self, tx, stream=None):
+        wrf_deform_project(self.scene, self.mlp, self.grid, tx, rec=self.rec, ws=self.dws,
+                           stream=stream)
+
+    def bin(self, stream=None):
+        wrf_bin(self.rec, self.scene.n, self.Q, self.grid, self.cap, gids=self.gids,
+                n_keys=self.n_keys, offsets=self.offs, ws=self.bws, stream=stream)
+
+    def render(self, stream=None, out=None):
+        return wrf_render(self.rec, self.gids, self.offs, self.n_keys, self.cap, self.scene.n,
+                          self.Q, self.grid, out=self.out if out is None else out, stream=stream)
+
+    def run(self, tx, stream=None, out=None):
+        """Enqueue one forward for tx [Q,3] (device) on `stream`; no sync."""
+        assert tx.shape[0] == self.Q
+        self.deform_project(tx, stream)
+        self.bin(stream)
+        return self.render(stream, out)
+
+    def reserve(self, tx, stream=None) -> int:
+        """Run once, read the key count and grow the capacity to count*margin."""
+        self.run(tx, stream)
+        st = stream or torch.cuda.current_stream()
+        st.synchronize()
+        need = int(self.n_keys.item())
+        wrf_status_read(stream)  # clear an overflow recorded by this sizing run
+        if need > self.cap:
+            self._alloc_keys(int(need * self.margin) + 1024)
+            self.run(tx, stream)
+            st.synchronize()
+        return need
+
+    def check(self, stream=None):
+        """Raise WrfError if the device recorded an error (e.g. key overflow)."""
+        s = wrf_status_read(stream)
+        if s != 0:
+            raise _lib.WrfError(s, f"device status (n_keys={int(self.n_keys.item())}, "
+                                   f"capacity={self.cap})")
+
+    def graph(self, tx, stream=None):
+        """Capture run(tx) into a CUDA graph (tx must stay at the same address)."""
+        g = torch.cuda.CUDAGraph()
+        s = stream or torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(tx, s)  # warm the path on the capture stream
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g, stream=s):
+            self.run(tx, s)
+        return g

@@ -3,12 +3,6 @@
 
 namespace wrf {
 
-cudaError_t launch_mlp_tc(const SceneView &, const MlpView &, const GridView &, int,
-                          const DeformWs &, int, float *, float4 *, uint32_t *, int *,
-                          cudaStream_t) {
-    return cudaErrorNotSupported;
-}
-
 size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, DeformBwdWs *bw,
                             char *base) {
     size_t s = deform_ws_layout(n, Q, m.n_layers, fw, base);

@@ -55,6 +55,20 @@ __device__ __forceinline__ void fence_async_smem() {
 __device__ __forceinline__ void named_bar(int id, int count) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
+// Barrier over the 128 threads of one warpgroup that also ORs `pred` across
+// them, so every thread of the warpgroup takes the same branch afterwards.
+__device__ __forceinline__ bool wg_bar_any(int id, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<uint32_t>(pred)), "r"(id)
+        : "memory");
+    return r != 0;
+}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
 // 8-row core-matrix groups 1024 bytes apart (stride byte offset), start
@@ -129,7 +143,10 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
 }
 
 // Wait on an mbarrier phase; gives up (returning false) when another thread
-// has flagged an abort or after kWaitLimitNs, flagging it.
+// has flagged an abort or after kWaitLimitNs, flagging it.  Threads never
+// leave a tile early on an abort: they finish it (on garbage) so that every
+// named barrier of the tile is reached by all 128 threads, and the tile loop
+// ends at the next uniform check.
 __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
                                               volatile int *abort_flag, int *status) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -221,7 +238,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
 
     for (int tile = blockIdx.x * 2 + wg; tile < a.ntiles; tile += gridDim.x * 2) {
-        if (*abort_flag) break;
+        // uniform per warpgroup: a timed-out wait anywhere ends the loop for
+        // all 128 threads together (no thread is left at a named barrier)
+        if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
         const long long row0 = static_cast<long long>(tile) * kTileRows;
         // ---- layer 1: h1 = ReLU(U[n] + V[q]) -> BF16 swizzled tile.
         // Warp wq fills rows 32wq..32wq+31; lane covers K columns 4*lane..4*lane+3.
@@ -283,9 +302,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             tc_fence_before();
             fence_async_smem();
             named_bar(1 + wg, 128);
-            if (*abort_flag) break;
         }
-        if (*abort_flag) break;
 
         // ---- output layer (N = 16, columns 0..4 used)
         if (leader) {
