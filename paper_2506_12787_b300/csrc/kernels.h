@@ -23,12 +23,16 @@ struct MlpView {
 
 // Workspace carve-up for deformation (all offsets 256-byte aligned).
 struct DeformWs {
-    float *U;              // [N][128]  W0[:, :dm] gamma(mean_n)
+    float *U;              // [N][128]  W0[:, :dm] gamma(mean_n)            (FP32 path)
+    uint16_t *G;           // [N][k1]   gamma(mean_n) in BF16, zero-padded  (BF16 path)
     float *V;              // [Q][128]  W0[:, dm:] gamma(tx_q) + b0
     float *wt_f32;         // hidden layers transposed [l][k=128][j=128], FP32
     float *wo_f32;         // output layer transposed [k=128][8] (cols 5..7 zero)
-    uint16_t *w_bf16;      // tcgen05 operand images of hidden + output layers
+    uint16_t *w_bf16;      // tcgen05 operand images: W1m, hidden layers, output
 };
+
+// K of the tensor-core layer-1 MMA: gamma(mean) width dm padded to 32 or 64.
+inline __host__ __device__ int mlp_k1(int dm) { return dm <= 32 ? 32 : 64; }
 
 size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base);
 

@@ -1,23 +1,28 @@
 // Deformation MLP on the 5th-generation tensor cores (tcgen05), BF16
 // operands with FP32 accumulation in tensor memory (Sec. 4.2, Eq. 14).
 //
-// Rows are the (query, Gaussian) pairs, flattened as row = q*N + n and cut
-// into tiles of 128 rows (one tcgen05 M=128 tile; TMEM lane = row).  A CTA
-// has two warpgroups that each own a tile at a time and run independently,
-// so one warpgroup's epilogue on the CUDA cores overlaps the other's MMAs on
-// the tensor core.  Per tile and warpgroup:
-//   1. layer 1 activation h1 = ReLU(U[n] + V[q]) (FP32, see prep.cu) is
-//      rounded to BF16 into a 128x128 K-major, 128-byte-swizzled smem tile;
-//   2. for every hidden layer: one elected thread issues 8 MMAs
-//      (128x128x16, kind::f16) reading the activation tile and the layer's
-//      resident weight image, and commits them to an mbarrier; the 128
-//      threads then read their row from TMEM (tcgen05.ld 32x32b), add the
-//      bias, apply ReLU, round to BF16 and write the next activation tile;
-//   3. the output layer is one 128x16x128 MMA chain (5 useful columns);
-//      its epilogue adds the bias and either stores the residual row or
+// Rows are the (query, Gaussian) pairs.  A tile is 128 consecutive Gaussians
+// of one query (one tcgen05 M=128 tile; TMEM lane = row); the last tile of a
+// query is partial.  A CTA runs three warpgroups that each own one tile at a
+// time and run independently, so the tensor core works on one warpgroup's
+// layer while the others run their epilogues on the CUDA cores.  Per tile:
+//   1. layer 1 splits exactly into a per-Gaussian and a per-query part:
+//      W1 [gamma(mean_n); gamma(s_q)] + b1 = W1m gamma(mean_n) + V[q], with
+//      V[q] = W1s gamma(s_q) + b1 computed once per query in FP32
+//      (prep.cu).  The per-Gaussian part runs on the tensor core: the
+//      thread of row n copies the BF16 row gamma(mean_n) (K = 32 or 64
+//      columns, prefetched during the previous tile) into the A tile, and
+//      one thread issues the K/16 MMAs against the resident W1m image;
+//   2. every layer's epilogue: the 128 threads read their row from TMEM
+//      (tcgen05.ld 32x32b), add the bias (V[q] for layer 1), apply ReLU and
+//      round to BF16 (one cvt.rn.relu.bf16x2 per pair) into the 128x128
+//      K-major, 128-byte-swizzled A tile of the next layer;
+//   3. hidden layers: 8 MMAs of 128x128x16 each, committed to an mbarrier;
+//   4. the output layer is one 128x16x128 MMA chain (5 useful columns)
+//      whose epilogue adds the bias and either stores the residual row or
 //      deforms and projects the Gaussian (fused Eq. 12-13) into its record.
-// All weights (<= 3 hidden layers + output, <= 100 KB of BF16) are copied
-// into shared memory once per CTA with bulk (TMA) copies.
+// All weights (W1m, <= 3 hidden layers, output; <= 116 KB of BF16) are
+// copied into shared memory once per CTA with bulk (TMA) copies.
 #include "kernels.h"
 
 namespace wrf {
@@ -25,11 +30,13 @@ namespace wrf {
 namespace {
 
 constexpr int kTileRows = 128;
-constexpr int kThreads = 256;             // two warpgroups
+constexpr int kWG = 3;                    // warpgroups per CTA
+constexpr int kThreads = 128 * kWG;
 constexpr uint32_t kLayerBytes = 128 * 128 * 2;
+constexpr uint32_t kW1Bytes = 128 * 128;  // W1m image: 128 rows x 128 B (K <= 64)
 constexpr uint32_t kOutBytes = 16 * 128 * 2;
 constexpr uint32_t kActBytes = 128 * 128 * 2;
-constexpr uint32_t kTmemCols = 512;       // 2 x (128 hidden + 16 output), rounded to a power of 2
+constexpr uint32_t kTmemCols = 512;       // kWG x 128 accumulator columns, power of 2
 
 // ------------------------------------------------------------ tcgen05 PTX
 __device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols) {
@@ -141,6 +148,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));  // a -> low half
     return r;
 }
+// BF16 pair of (max(a, 0), max(b, 0)), a in the low half: ReLU folded into
+// the conversion (same result as rounding after the ReLU).
+__device__ __forceinline__ uint32_t pack_bf16_relu(float a, float b) {
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
 
 // Wait on an mbarrier phase; gives up (returning false) when another thread
 // has flagged an abort or after kWaitLimitNs, flagging it.  Threads never
@@ -166,13 +180,14 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t *bar, uint32_t parity,
 struct TcArgs {
     SceneView s;
     GridView g;
-    const float *U, *V;
-    const uint16_t *w_img;   // BF16 images: hidden layers then output layer
+    const uint16_t *G;       // [N][k1] BF16 gamma(mean) rows, zero-padded
+    const float *V;          // [Q][128] FP32 per-query layer-1 term (incl. b1)
+    const uint16_t *w_img;   // BF16 images: W1m, hidden layers, output layer
     const float *bh[3];
     const float *bo;
     int nh;                  // hidden 128x128 layers (0..3)
-    int Q;
-    long long rows;
+    int k1;                  // layer-1 K: 32 or 64
+    int Q, N, tpq;           // tiles per query
     int ntiles;
     int mode;
     float *resid;
@@ -181,26 +196,31 @@ struct TcArgs {
     int *status;
 };
 
+constexpr size_t smem_bytes(int nh) {
+    return 1024 + kW1Bytes + nh * kLayerBytes + kOutBytes + kWG * kActBytes +
+           (nh * 128 + 16) * 4 + kWG * 128 * 4 + (1 + kWG) * 8 + 16;
+}
+
 __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned base (128-byte swizzle atoms must be 1024-aligned)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    const uint32_t w_bytes = a.nh * kLayerBytes + kOutBytes;
+    const uint32_t w_bytes = kW1Bytes + a.nh * kLayerBytes + kOutBytes;
     uint8_t *wsm = base;
-    uint8_t *act[2] = {base + w_bytes, base + w_bytes + kActBytes};
-    float *bias = reinterpret_cast<float *>(base + w_bytes + 2 * kActBytes);  // [nh*128 + 16]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(bias + a.nh * 128 + 16);    // wbar, mbar[2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 3);
+    uint8_t *act0 = base + w_bytes;
+    float *bias = reinterpret_cast<float *>(act0 + kWG * kActBytes);  // [nh*128 + 16]
+    float *vbuf = bias + a.nh * 128 + 16;                             // [kWG][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(vbuf + kWG * 128);  // wbar, mbar[kWG]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 1 + kWG);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int wg = warp >> 2, wq = warp & 3;  // warpgroup, warp within warpgroup
+    const int wt = tid & 127;                 // thread within the warpgroup
 
     if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int i = 0; i < 1 + kWG; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
         *abort_flag = 0;
     }
@@ -219,81 +239,89 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             bulk_g2s(wsm + off, src + off, len, &bars[0]);
         }
     }
-    bool ok = wait_or_abort(&bars[0], 0, abort_flag, a.status);
-    (void)ok;
+    wait_or_abort(&bars[0], 0, abort_flag, a.status);
     __syncthreads();
 
     uint64_t *mbar = &bars[1 + wg];
     uint32_t phase = 0;
-    uint8_t *A = act[wg];
+    uint8_t *A = act0 + wg * kActBytes;
+    float *vb = vbuf + wg * 128;
     const uint32_t a_addr = smem_u32(A);
-    const uint32_t w_addr = smem_u32(wsm);
-    const uint32_t t_hid = tmem_base + static_cast<uint32_t>(wg * 256);
-    const uint32_t t_out = t_hid + 128u;
+    const uint32_t w1_addr = smem_u32(wsm);
+    const uint32_t wh_addr = w1_addr + kW1Bytes;
+    const uint32_t t_acc = tmem_base + static_cast<uint32_t>(wg * 128);
     const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;  // TMEM lane field
     const int my_row = wq * 32 + lane;                               // row within the tile
-    const bool leader = (tid & 127) == 0;
-    const float4 *U4 = reinterpret_cast<const float4 *>(a.U);
-    const float4 *V4 = reinterpret_cast<const float4 *>(a.V);
+    const bool leader = wt == 0;
     const uint32_t id128 = idesc_bf16(128, 128), id16 = idesc_bf16(128, 16);
+    const int nch = a.k1 >> 3;  // 16-byte chunks of a gamma(mean) row (4 or 8)
+    const int stride = gridDim.x * kWG;
 
-    for (int tile = blockIdx.x * 2 + wg; tile < a.ntiles; tile += gridDim.x * 2) {
+    // prefetch of this thread's gamma(mean) row for its next tile
+    uint4 gpre[8];
+    auto load_g = [&](int tile) {
+        const int nb = tile % a.tpq;
+        const int n = nb * kTileRows + my_row;
+        const bool ok = tile < a.ntiles && n < a.N;
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.G + static_cast<size_t>(ok ? n : 0) * a.k1);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            gpre[c] = (ok && c < nch) ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
+    };
+    int tile = blockIdx.x * kWG + wg;
+    load_g(tile);
+
+    for (; tile < a.ntiles; tile += stride) {
         // uniform per warpgroup: a timed-out wait anywhere ends the loop for
         // all 128 threads together (no thread is left at a named barrier)
         if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
-        const long long row0 = static_cast<long long>(tile) * kTileRows;
-        // ---- layer 1: h1 = ReLU(U[n] + V[q]) -> BF16 swizzled tile.
-        // Warp wq fills rows 32wq..32wq+31; lane covers K columns 4*lane..4*lane+3.
-        {
-            const int half = lane >> 4, chunk = (lane & 15) >> 1, sub = (lane & 1) * 8;
-            for (int rr = 0; rr < 32; ++rr) {
-                const int r = wq * 32 + rr;
-                const long long row = row0 + r;
-                uint2 packed = make_uint2(0u, 0u);
-                if (row < a.rows) {
-                    const int q = static_cast<int>(row / a.s.n);
-                    const int n = static_cast<int>(row - static_cast<long long>(q) * a.s.n);
-                    const float4 u = U4[static_cast<size_t>(n) * 32 + lane];
-                    const float4 v = V4[static_cast<size_t>(q) * 32 + lane];
-                    packed.x = pack_bf16(fmaxf(u.x + v.x, 0.f), fmaxf(u.y + v.y, 0.f));
-                    packed.y = pack_bf16(fmaxf(u.z + v.z, 0.f), fmaxf(u.w + v.w, 0.f));
-                }
-                *reinterpret_cast<uint2 *>(A + half * 16384 + r * 128 +
-                                           ((chunk ^ (r & 7)) << 4) + sub) = packed;
-            }
-        }
+        const int q = tile / a.tpq;
+        const int n = (tile % a.tpq) * kTileRows + my_row;
+        // ---- layer 1 operand: gamma(mean_n) row -> A columns 0..k1-1
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (c < nch)
+                *reinterpret_cast<uint4 *>(A + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = gpre[c];
+        vb[wt] = __ldg(a.V + static_cast<size_t>(q) * 128 + wt);
+        load_g(tile + stride);
         fence_async_smem();
         named_bar(1 + wg, 128);
 
-        // ---- hidden layers
-        for (int l = 0; l < a.nh; ++l) {
+        // ---- layers: 0 = layer 1 (K = k1, bias V[q]), 1..nh = hidden
+        for (int l = 0; l <= a.nh; ++l) {
             if (leader) {
                 tc_fence_after();
-                const uint32_t wl = w_addr + l * kLayerBytes;
+                if (l == 0) {
+                    for (int k = 0; k < (a.k1 >> 4); ++k)
+                        mma_bf16(t_acc, sw128_desc(a_addr + k * 32u), sw128_desc(w1_addr + k * 32u),
+                                 id128, k > 0 ? 1u : 0u);
+                } else {
+                    const uint32_t wl = wh_addr + (l - 1) * kLayerBytes;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const uint32_t koff = (k >> 2) * 16384u + (k & 3) * 32u;
-                    mma_bf16(t_hid, sw128_desc(a_addr + koff), sw128_desc(wl + koff), id128,
-                             k > 0 ? 1u : 0u);
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t koff = (k >> 2) * 16384u + (k & 3) * 32u;
+                        mma_bf16(t_acc, sw128_desc(a_addr + koff), sw128_desc(wl + koff), id128,
+                                 k > 0 ? 1u : 0u);
+                    }
                 }
                 mma_commit(mbar);
             }
             wait_or_abort(mbar, phase, abort_flag, a.status);
             phase ^= 1u;
             tc_fence_after();
-            const float *bl = bias + l * 128;
+            const float *bl = l == 0 ? vb : bias + (l - 1) * 128;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float v[32];
-                tmem_ld32(t_hid + lane_off + c * 32, v);
+                tmem_ld32(t_acc + lane_off + c * 32, v);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     uint4 p;
                     const float *b = bl + c * 32 + j * 8;
-                    p.x = pack_bf16(fmaxf(v[j * 8 + 0] + b[0], 0.f), fmaxf(v[j * 8 + 1] + b[1], 0.f));
-                    p.y = pack_bf16(fmaxf(v[j * 8 + 2] + b[2], 0.f), fmaxf(v[j * 8 + 3] + b[3], 0.f));
-                    p.z = pack_bf16(fmaxf(v[j * 8 + 4] + b[4], 0.f), fmaxf(v[j * 8 + 5] + b[5], 0.f));
-                    p.w = pack_bf16(fmaxf(v[j * 8 + 6] + b[6], 0.f), fmaxf(v[j * 8 + 7] + b[7], 0.f));
+                    p.x = pack_bf16_relu(v[j * 8 + 0] + b[0], v[j * 8 + 1] + b[1]);
+                    p.y = pack_bf16_relu(v[j * 8 + 2] + b[2], v[j * 8 + 3] + b[3]);
+                    p.z = pack_bf16_relu(v[j * 8 + 4] + b[4], v[j * 8 + 5] + b[5]);
+                    p.w = pack_bf16_relu(v[j * 8 + 6] + b[6], v[j * 8 + 7] + b[7]);
                     const int kc = c * 4 + j;  // 16-byte chunk 0..15 along K
                     *reinterpret_cast<uint4 *>(A + (kc >> 3) * 16384 + my_row * 128 +
                                                (((kc & 7) ^ (my_row & 7)) << 4)) = p;
@@ -304,15 +332,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             named_bar(1 + wg, 128);
         }
 
-        // ---- output layer (N = 16, columns 0..4 used)
+        // ---- output layer (N = 16, columns 0..4 used), into the same columns
         if (leader) {
             tc_fence_after();
-            const uint32_t wo = w_addr + a.nh * kLayerBytes;
+            const uint32_t wo = wh_addr + a.nh * kLayerBytes;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t ka = (k >> 2) * 16384u + (k & 3) * 32u;
                 const uint32_t kb = (k >> 2) * 2048u + (k & 3) * 32u;
-                mma_bf16(t_out, sw128_desc(a_addr + ka), sw128_desc(wo + kb), id16,
+                mma_bf16(t_acc, sw128_desc(a_addr + ka), sw128_desc(wo + kb), id16,
                          k > 0 ? 1u : 0u);
             }
             mma_commit(mbar);
@@ -321,10 +349,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         phase ^= 1u;
         tc_fence_after();
         float o[16];
-        tmem_ld16(t_out + lane_off, o);
+        tmem_ld16(t_acc + lane_off, o);
         tc_fence_before();
-        const long long row = row0 + my_row;
-        if (row < a.rows && !*abort_flag) {
+        if (n < a.N && !*abort_flag) {
+            const long long row = static_cast<long long>(q) * a.N + n;
             const float *bo = bias + a.nh * 128;
             const float d0 = o[0] + bo[0], d1 = o[1] + bo[1], d2 = o[2] + bo[2],
                         d3 = o[3] + bo[3], d4 = o[4] + bo[4];
@@ -336,7 +364,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 dst[3] = d3;
                 dst[4] = d4;
             } else {
-                const int n = static_cast<int>(row % a.s.n);
                 float4 r0, r1;
                 uint32_t c = project_one(a.s, n, d0, d1, d2, d3, d4, a.g, r0, r1);
                 a.rec[2 * row] = r0;
@@ -344,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 if (a.count) a.count[row] = c;
             }
         }
-        named_bar(1 + wg, 128);  // TMEM output columns and the tile are free again
+        named_bar(1 + wg, 128);  // TMEM columns, A tile and vbuf are free again
     }
     tc_fence_before();
     __syncthreads();
@@ -362,33 +389,36 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
     const long long rows = static_cast<long long>(Q) * s.n;
     if (rows == 0) return cudaSuccess;
     const int nh = m.n_layers - 2;
-    if (nh < 0 || nh > 3) return cudaErrorInvalidValue;
+    if (nh < 0 || nh > 3 || m.dm > 64) return cudaErrorInvalidValue;
     TcArgs a{};
     a.s = s;
     a.g = g;
-    a.U = ws.U;
+    a.G = ws.G;
     a.V = ws.V;
     a.w_img = ws.w_bf16;
     for (int l = 0; l < 3; ++l) a.bh[l] = l < nh ? m.bh[l] : nullptr;
     a.bo = m.bo;
     a.nh = nh;
+    a.k1 = mlp_k1(m.dm);
     a.Q = Q;
-    a.rows = rows;
-    a.ntiles = static_cast<int>((rows + kTileRows - 1) / kTileRows);
+    a.N = s.n;
+    a.tpq = (s.n + kTileRows - 1) / kTileRows;
+    const long long nt = static_cast<long long>(a.tpq) * Q;
+    if (nt >= (1ll << 31)) return cudaErrorInvalidValue;
+    a.ntiles = static_cast<int>(nt);
     a.mode = mode;
     a.resid = resid;
     a.rec = rec;
     a.count = count;
     a.status = status;
-    const size_t smem = 1024 + nh * kLayerBytes + kOutBytes + 2 * kActBytes +
-                        (nh * 128 + 16) * 4 + 3 * 8 + 8 + 64;
+    const size_t smem = smem_bytes(nh);
     cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int grid = (a.ntiles + 1) / 2;
+    int grid = (a.ntiles + kWG - 1) / kWG;
     if (grid > sms) grid = sms;
     mlp_tc_kernel<<<grid, kThreads, smem, st>>>(a);
     return cudaGetLastError();

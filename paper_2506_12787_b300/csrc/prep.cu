@@ -19,6 +19,7 @@ namespace wrf {
 namespace {
 
 constexpr int kMaxPe = 3 * (2 * 15 + 1);  // d(2L+1) for d <= 3, L <= 15
+constexpr size_t kW1ImageBytes = WRF_HIDDEN * 128;  // 128 rows x 64 BF16 columns
 
 // gamma(x) of Eq. 15 for a d-vector, written to out[d(2L+1)] in the order
 // [x, sin band 0 (all d), ..., sin band L-1, cos band 0, ..., cos band L-1].
@@ -33,9 +34,12 @@ __device__ void encode(const float *x, int d, int L, float *out) {
         }
 }
 
-// U[n][j] for 32 Gaussians per block; thread j owns output column j.
+// Per-Gaussian part of layer 1 for 32 Gaussians per block.  FP32 path:
+// U[n][j] = W0[j, :dm] . gamma(mean_n), thread j owns column j.  BF16 path:
+// the row gamma(mean_n) itself in BF16, zero-padded to k1 columns, which the
+// tensor-core kernel multiplies by the W1m image.
 __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, GridView g,
-                                                      float *U) {
+                                                      float *U, uint16_t *G, int k1) {
     __shared__ float gam[32][kMaxPe];
     const int n0 = blockIdx.x * 32;
     const int din = m.dm + m.dt;
@@ -48,6 +52,15 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
         }
     }
     __syncthreads();
+    if (G) {
+        for (int e = threadIdx.x; e < 32 * k1; e += blockDim.x) {
+            const int r = e / k1, k = e % k1, n = n0 + r;
+            if (n < s.n)
+                reinterpret_cast<__nv_bfloat16 *>(G)[static_cast<size_t>(n) * k1 + k] =
+                    __float2bfloat16_rn(k < m.dm ? gam[r][k] : 0.f);
+        }
+        return;
+    }
     const int j = threadIdx.x;
     const float *wrow = m.W0 + static_cast<size_t>(j) * din;
     float w[kMaxPe];
@@ -60,29 +73,43 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
     }
 }
 
-// V[q][j] for 32 queries per block.
+// V[q][j] for 4 queries per block: the 4 x dt features of Eq. 15 are
+// computed one per thread, then thread j forms output column j of each query.
+constexpr int kTxPerBlock = 4;
 __global__ void __launch_bounds__(128) pe_tx_kernel(MlpView m, const float *tx, int Q, float *V) {
-    __shared__ float gam[32][kMaxPe];
-    const int q0 = blockIdx.x * 32;
+    __shared__ float gam[kTxPerBlock][kMaxPe];
+    const int q0 = blockIdx.x * kTxPerBlock;
     const int din = m.dm + m.dt;
-    if (threadIdx.x < 32) {
-        int q = q0 + threadIdx.x;
-        if (q < Q) {
-            float x[3];
-            for (int i = 0; i < 3; ++i)
-                x[i] = (tx[3 * q + i] - m.room_min[i]) / m.room_size[i];
-            encode(x, 3, m.L_tx, gam[threadIdx.x]);
+    const int L = m.L_tx;
+    for (int e = threadIdx.x; e < kTxPerBlock * m.dt; e += blockDim.x) {
+        const int r = e / m.dt, f = e % m.dt, q = q0 + r;
+        if (q >= Q) continue;
+        // feature f: [x (3), sin band k (3 each), cos band k (3 each)]
+        const int i = f % 3, grp = f / 3;
+        const float x = (tx[3 * q + i] - m.room_min[i]) / m.room_size[i];
+        float val = x;
+        if (grp >= 1) {
+            float sn, cs;
+            pe_band(x, (grp - 1) % L, sn, cs);
+            val = grp <= L ? sn : cs;
         }
+        gam[r][f] = val;
     }
     __syncthreads();
     const int j = threadIdx.x;
     const float *wrow = m.W0 + static_cast<size_t>(j) * din + m.dm;
     const float bj = m.b0[j];
-    for (int r = 0; r < 32 && q0 + r < Q; ++r) {
-        float acc = 0.f;
-        for (int k = 0; k < m.dt; ++k) acc = fmaf(wrow[k], gam[r][k], acc);
-        V[static_cast<size_t>(q0 + r) * WRF_HIDDEN + j] = acc + bj;
+    float acc[kTxPerBlock];
+#pragma unroll
+    for (int r = 0; r < kTxPerBlock; ++r) acc[r] = 0.f;
+    for (int k = 0; k < m.dt; ++k) {
+        const float w = wrow[k];
+#pragma unroll
+        for (int r = 0; r < kTxPerBlock; ++r) acc[r] = fmaf(w, gam[r][k], acc[r]);
     }
+#pragma unroll
+    for (int r = 0; r < kTxPerBlock; ++r)
+        if (q0 + r < Q) V[static_cast<size_t>(q0 + r) * WRF_HIDDEN + j] = acc[r] + bj;
 }
 
 // Byte offset of element (row n, col k) in a K-major, 128-byte-swizzled
@@ -96,34 +123,44 @@ __device__ __forceinline__ uint32_t sw128_offset(int n, int k, int rows) {
 }
 
 // One thread per (layer, row, col) of every hidden layer and the output
-// layer: FP32 transposes and BF16 swizzled images.
+// layer: FP32 transposes and BF16 swizzled images.  The BF16 image starts
+// with W1m = W0[:, :dm] as a 128 x 64 K-major image (columns >= dm zero).
 __global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
     const int nh = m.n_layers - 2;
     const long long per = WRF_HIDDEN * WRF_HIDDEN;
-    const long long total = nh * per + 16 * WRF_HIDDEN;
+    const long long w1 = want_bf16 ? WRF_HIDDEN * 64 : 0;
+    const long long total = w1 + nh * per + 16 * WRF_HIDDEN;
+    char *img = reinterpret_cast<char *>(ws.w_bf16);
+    const int din = m.dm + m.dt;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
-        if (i < nh * per) {
-            int l = static_cast<int>(i / per);
-            int r = static_cast<int>(i % per);
+        if (i < w1) {
+            const int j = static_cast<int>(i / 64), k = static_cast<int>(i % 64);
+            const float v = k < m.dm ? m.W0[static_cast<size_t>(j) * din + k] : 0.f;
+            *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(j, k, WRF_HIDDEN)) =
+                __float2bfloat16_rn(v);
+            continue;
+        }
+        const long long ii = i - w1;
+        if (ii < nh * per) {
+            int l = static_cast<int>(ii / per);
+            int r = static_cast<int>(ii % per);
             int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // W[j][k]
             float v = m.Wh[l][r];
             ws.wt_f32[l * per + k * WRF_HIDDEN + j] = v;
-            if (want_bf16) {
-                char *img = reinterpret_cast<char *>(ws.w_bf16) + l * per * 2;
-                *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(j, k, WRF_HIDDEN)) =
+            if (want_bf16)
+                *reinterpret_cast<__nv_bfloat16 *>(img + kW1ImageBytes + l * per * 2 +
+                                                   sw128_offset(j, k, WRF_HIDDEN)) =
                     __float2bfloat16_rn(v);
-            }
         } else {
-            int r = static_cast<int>(i - nh * per);
+            int r = static_cast<int>(ii - nh * per);
             int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // output row j (< 16)
             float v = j < WRF_OUT ? m.Wo[j * WRF_HIDDEN + k] : 0.f;
             if (j < 8) ws.wo_f32[k * 8 + j] = v;
-            if (want_bf16) {
-                char *img = reinterpret_cast<char *>(ws.w_bf16) + nh * per * 2;
-                *reinterpret_cast<__nv_bfloat16 *>(img + sw128_offset(j, k, 16)) =
+            if (want_bf16)
+                *reinterpret_cast<__nv_bfloat16 *>(img + kW1ImageBytes + nh * per * 2 +
+                                                   sw128_offset(j, k, 16)) =
                     __float2bfloat16_rn(v);
-            }
         }
     }
 }
@@ -142,20 +179,25 @@ size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
     int nh = n_layers - 2 > 0 ? n_layers - 2 : 0;
     DeformWs w{};
     w.U = reinterpret_cast<float *>(take(static_cast<size_t>(n) * WRF_HIDDEN * 4));
+    w.G = reinterpret_cast<uint16_t *>(take(static_cast<size_t>(n) * 64 * 2));
     w.V = reinterpret_cast<float *>(take(static_cast<size_t>(Q) * WRF_HIDDEN * 4));
     w.wt_f32 = reinterpret_cast<float *>(take(static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 4));
     w.wo_f32 = reinterpret_cast<float *>(take(WRF_HIDDEN * 8 * 4));
     w.w_bf16 = reinterpret_cast<uint16_t *>(
-        take(static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 2 + 16 * WRF_HIDDEN * 2));
+        take(kW1ImageBytes + static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 2 +
+             16 * WRF_HIDDEN * 2));
     if (ws) *ws = w;
     return off;
 }
 
 cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
                         int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st) {
-    if (s.n > 0) pe_mean_kernel<<<(s.n + 31) / 32, 128, 0, st>>>(s, m, g, ws.U);
-    if (Q > 0) pe_tx_kernel<<<(Q + 31) / 32, 128, 0, st>>>(m, tx, Q, ws.V);
-    long long total = static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
+    if (s.n > 0)
+        pe_mean_kernel<<<(s.n + 31) / 32, 128, 0, st>>>(s, m, g, ws.U, want_bf16 ? ws.G : nullptr,
+                                                        mlp_k1(m.dm));
+    if (Q > 0) pe_tx_kernel<<<(Q + kTxPerBlock - 1) / kTxPerBlock, 128, 0, st>>>(m, tx, Q, ws.V);
+    long long total = (want_bf16 ? WRF_HIDDEN * 64 : 0) +
+                      static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
                       16 * WRF_HIDDEN;
     int blocks = static_cast<int>((total + 255) / 256);
     if (blocks > 1184) blocks = 1184;

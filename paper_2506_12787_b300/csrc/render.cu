@@ -1,15 +1,21 @@
 // Tile rasteriser for the order-free Gaussian sum (Sec. 4.1 Eq. 8-9,
 // Sec. 4.2 Eq. 13) and its backward.
 //
-// Forward: one CTA per (tile, query).  The tile's Gaussian list (ascending
-// id) is streamed through shared memory in batches of NT records: every
-// thread issues one 32-byte cp.async.bulk (TMA bulk copy) for one record,
-// completion is counted in bytes on an mbarrier, and two buffers alternate so
-// the next batch lands while the current one is evaluated.  Each thread owns
-// a column of PPT consecutive pixels and walks them with an incremental
-// quadratic form (two adds per pixel); a warp skips a Gaussian whose bounding
-// box misses the warp's pixel block, and a pixel adds w * 2^(-q') only when
-// q <= q_cut.  The finished tile goes through shared memory to float4 stores.
+// Forward: one CTA per (tile, query), one thread per pixel; warp w owns an
+// 8 x 4 pixel block of the tile.  The tile's Gaussian list (ascending id) is
+// streamed through shared memory in batches of one record per thread: every
+// thread issues one 32-byte cp.async.bulk (TMA bulk copy), completion is
+// counted in bytes on an mbarrier, and two landing buffers alternate so the
+// next batch is in flight while the current one is evaluated.  Once per
+// (tile, Gaussian) a thread turns the record into the polynomial
+//   -q'(lx, ly) = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
+// in the pixel's offset (lx, ly) from the tile centre (q' = q log2(e)/2), and
+// a bitmask of the warp blocks its footprint rectangle touches.  Each warp
+// then compacts (ballot + popc) the batch into its own list, ascending, and
+// evaluates only those: 5 FMAs, one compare, one ex2 and one FMA per pixel.
+// Every pixel adds its contributions in ascending Gaussian id, so a query's
+// spectrum does not depend on the other queries in the launch.  The finished
+// tile goes through shared memory to float4 stores.
 //
 // Backward: one CTA per (tile, query); the tile's dL/dA is staged in shared
 // memory and each thread takes one Gaussian of the list, walks the pixels of
@@ -22,34 +28,45 @@ namespace wrf {
 
 namespace {
 
-template <int TW, int TH, int PPT>
-__global__ void __launch_bounds__(TW *TH / PPT) render_kernel(
+// Shared-memory carve-up of the forward kernel for a tile of NT pixels
+// (one thread per pixel, a batch of B = NT records).
+template <int NT>
+struct FwdSmem {
+    static constexpr int B = NT, NW = NT / 32;
+    static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
+    static constexpr size_t coef = raw + 2 * B * 32;           // [B][2] float4, per-tile polynomial
+    static constexpr size_t mask = coef + B * 32;              // [B] u32, warp blocks touched
+    static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
+    static constexpr size_t bytes = lists + NW * B * 2;
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW *TH) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
-    GridView g, float cut_s, float *__restrict__ out, int *status) {
-    constexpr int NT = TW * TH / PPT;
-    constexpr int B = NT;
-    __shared__ __align__(128) float4 srec[2][B][2];
-    __shared__ __align__(16) float stile[TH][TW];
+    GridView g, float ncut, float *__restrict__ out, int *status) {
+    constexpr int NT = TW * TH, B = NT, NW = NT / 32;
+    constexpr int NSX = TW / 8;  // warp blocks of 8 x 4 pixels: NSX across, TH/4 down
+    static_assert(NW == NSX * (TH / 4), "one 8x4 pixel block per warp");
+    using L = FwdSmem<NT>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
+    float4 *coef = reinterpret_cast<float4 *>(smem + L::coef);
+    uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
+    uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int abort_flag;
+    __shared__ __align__(16) float stile[TH][TW];
 
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.x, q = blockIdx.y;
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
-    const int lx = threadIdx.x % TW, ly = (threadIdx.x / TW) * PPT;
-    const float px = static_cast<float>(x0 + lx), py = static_cast<float>(y0 + ly);
-    // pixel block of this warp (used to skip Gaussians that cannot reach it)
-    const int tid0 = threadIdx.x & ~31, tid1 = tid0 + 31;
-    float wx0, wx1;
-    if (TW >= 32) {
-        wx0 = static_cast<float>(x0 + tid0 % TW);
-        wx1 = wx0 + 31.f;
-    } else {
-        wx0 = static_cast<float>(x0);
-        wx1 = static_cast<float>(x0 + TW - 1);
-    }
-    const float wy0 = static_cast<float>(y0 + (tid0 / TW) * PPT);
-    const float wy1 = static_cast<float>(y0 + (tid1 / TW) * PPT + PPT - 1);
+    // this thread's pixel (tile-local), and its offset from the tile centre
+    const int pxl = (warp % NSX) * 8 + (lane & 7);
+    const int pyl = (warp / NSX) * 4 + (lane >> 3);
+    const float lx = static_cast<float>(pxl - TW / 2), ly = static_cast<float>(pyl - TH / 2);
+    const float lx2 = lx * lx, lxy = lx * ly, ly2 = ly * ly;  // exact (small integers)
+    const float xcen = static_cast<float>(x0 + TW / 2), ycen = static_cast<float>(y0 + TH / 2);
 
     uint32_t s0 = 0, s1 = 0;
     if (*n_keys <= cap) {
@@ -60,7 +77,7 @@ __global__ void __launch_bounds__(TW *TH / PPT) render_kernel(
     const int nb = (total + B - 1) / B;
     const float4 *qrec = rec + static_cast<size_t>(q) * n * 2;
 
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
@@ -70,62 +87,91 @@ __global__ void __launch_bounds__(TW *TH / PPT) render_kernel(
     }
     __syncthreads();
     for (int b = 0; b < 2 && b < nb; ++b) {
-        int i = threadIdx.x;
-        if (i < total - b * B) {
-            uint32_t gid = gids[s0 + b * B + i];
-            bulk_g2s(&srec[b][i][0], qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
+        if (tid < total - b * B) {
+            const uint32_t gid = gids[s0 + b * B + tid];
+            bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
         }
     }
 
-    float acc[PPT];
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) acc[j] = 0.f;
-    const float ncut = -cut_s;
+    float acc = 0.f;
+    uint16_t *mylist = lists + warp * B;
     int b = 0;
     for (; b < nb; ++b) {
         const int buf = b & 1;
-        if (!mbar_wait(&bar[buf], (b >> 1) & 1, status)) abort_flag = 1;
         const int cnt = min(B, total - b * B);
-        for (int i = 0; i < cnt; ++i) {
-            const float4 r0 = srec[buf][i][0];
-            const float4 r1 = srec[buf][i][1];
-            if (r0.x + r1.z < wx0 || r0.x - r1.z > wx1 || r0.y + r1.w < wy0 ||
-                r0.y - r1.w > wy1)
-                continue;
-            const float dx = px - r0.x, dy = py - r0.y;
-            float nq = -(dx * fmaf(r0.z, dx, 2.f * r0.w * dy) + r1.x * dy * dy);
-            float step = -(2.f * fmaf(r0.w, dx, r1.x * dy) + r1.x);
-            const float step2 = -2.f * r1.x;
-#pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                if (nq >= ncut) acc[j] = fmaf(r1.y, ex2_approx(nq), acc[j]);
-                nq += step;
-                step += step2;
+        if (!mbar_wait(&bar[buf], (b >> 1) & 1, status)) abort_flag = 1;
+        if (tid == 0 && b + 2 < nb)
+            mbar_arrive_expect_tx(&bar[buf],
+                                  static_cast<uint32_t>(min(B, total - (b + 2) * B)) * 32u);
+        // ---- per-record set-up, once per (tile, Gaussian):
+        // -q'(p) for p = tile centre + (lx, ly) as a polynomial in lx, ly:
+        //   dx = lx - ux, dy = ly - uy, u = centre - tile centre,
+        //   -q' = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
+        // and the mask of 8x4 warp blocks its footprint rectangle touches.
+        if (tid < cnt) {
+            const float4 r0 = raw[(buf * B + tid) * 2], r1 = raw[(buf * B + tid) * 2 + 1];
+            const float ux = r0.x - xcen, uy = r0.y - ycen;
+            const float h1 = fmaf(r0.z, ux, r0.w * uy), h2 = fmaf(r0.w, ux, r1.x * uy);
+            const float c0 = -fmaf(ux, h1, uy * h2);
+            coef[tid * 2] = make_float4(c0, 2.f * h1, 2.f * h2, r1.y);
+            coef[tid * 2 + 1] = make_float4(-r0.z, -2.f * r0.w, -r1.x, 0.f);
+            uint32_t mk = 0;
+            const float xlo = ceilf(__fsub_rn(r0.x, r1.z)) - static_cast<float>(x0);
+            const float xhi = floorf(__fadd_rn(r0.x, r1.z)) - static_cast<float>(x0);
+            const float ylo = ceilf(__fsub_rn(r0.y, r1.w)) - static_cast<float>(y0);
+            const float yhi = floorf(__fadd_rn(r0.y, r1.w)) - static_cast<float>(y0);
+            if (xhi >= 0.f && xlo <= TW - 1.f && yhi >= 0.f && ylo <= TH - 1.f) {
+                const int bx0 = static_cast<int>(fmaxf(xlo, 0.f)) >> 3;
+                const int bx1 = static_cast<int>(fminf(xhi, TW - 1.f)) >> 3;
+                const int by0 = static_cast<int>(fmaxf(ylo, 0.f)) >> 2;
+                const int by1 = static_cast<int>(fminf(yhi, TH - 1.f)) >> 2;
+                const uint32_t row = (2u << bx1) - (1u << bx0);
+                for (int by = by0; by <= by1; ++by) mk |= row << (by * NSX);
             }
+            mask[tid] = mk;
         }
-        if (threadIdx.x == 0 && b + 2 < nb)
-            mbar_arrive_expect_tx(&bar[buf], static_cast<uint32_t>(min(B, total - (b + 2) * B)) * 32u);
         __syncthreads();
-        if (abort_flag) break;
-        if (b + 2 < nb) {
-            int i = threadIdx.x;
-            if (i < total - (b + 2) * B) {
-                uint32_t gid = gids[s0 + (b + 2) * B + i];
-                bulk_g2s(&srec[buf][i][0], qrec + 2 * static_cast<size_t>(gid), 32, &bar[buf]);
-            }
+        // raw[buf] is consumed: the copies of batch b+2 can land there now
+        if (b + 2 < nb && tid < total - (b + 2) * B) {
+            const uint32_t gid = gids[s0 + (b + 2) * B + tid];
+            bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[buf]);
         }
+        // ---- this warp's list: records touching its block, ascending index
+        int m = 0;
+        for (int base = 0; base < cnt; base += 32) {
+            const int i = base + lane;
+            const bool hit = i < cnt && ((mask[i] >> warp) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+            if (hit) mylist[m + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i);
+            m += __popc(bal);
+        }
+        __syncwarp();
+        // ---- accumulate: w * 2^(-q') where q <= q_cut (Eq. 8-9)
+#pragma unroll 4
+        for (int j = 0; j < m; ++j) {
+            const int i = mylist[j];
+            const float4 k0 = coef[i * 2], k1 = coef[i * 2 + 1];
+            float nq = fmaf(k0.y, lx, k0.x);
+            nq = fmaf(k0.z, ly, nq);
+            nq = fmaf(k1.x, lx2, nq);
+            nq = fmaf(k1.y, lxy, nq);
+            nq = fmaf(k1.z, ly2, nq);
+            if (nq >= ncut) acc = fmaf(k0.w, ex2_approx(nq), acc);
+        }
+        __syncthreads();  // coef / mask / lists are rewritten by the next batch
+        if (abort_flag) break;
     }
     if (abort_flag) {
-        // drain copies still in flight (batches b and b+1; bounded) before the CTA exits
-        for (int bb = b; bb < nb && bb <= b + 1; ++bb) mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
+        // drain copies still in flight (bounded waits) before the CTA exits
+        for (int bb = b; bb < nb && bb <= b + 2; ++bb)
+            mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
         return;
     }
-#pragma unroll
-    for (int j = 0; j < PPT; ++j) stile[ly + j][lx] = acc[j];
+    stile[pyl][pxl] = acc;
     __syncthreads();
     float *oq = out + static_cast<size_t>(q) * g.H * g.W;
     const bool vec = (g.W & 3) == 0;
-    for (int i = threadIdx.x; i < TH * TW / 4; i += NT) {
+    for (int i = tid; i < TH * TW / 4; i += NT) {
         const int r = i / (TW / 4), c4 = (i % (TW / 4)) * 4;
         const int y = y0 + r, x = x0 + c4;
         if (y >= g.H || x >= g.W) continue;
@@ -196,13 +242,18 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     }
 }
 
-template <int TW, int TH, int PPT>
+template <int TW, int TH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        float *out, int *status, cudaStream_t st) {
+    const size_t smem = FwdSmem<TW * TH>::bytes;
+    cudaError_t e = cudaFuncSetAttribute(render_kernel<TW, TH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
     dim3 grid(g.T, Q);
-    render_kernel<TW, TH, PPT><<<grid, TW * TH / PPT, 0, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                                               g.q_cut * kHalfLog2e, out, status);
+    render_kernel<TW, TH><<<grid, TW * TH, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
+                                                       -g.q_cut * kHalfLog2e, out, status);
     return cudaGetLastError();
 }
 
@@ -227,11 +278,11 @@ cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_
                           const long long *n_keys, long long cap, int n, int Q,
                           const GridView &g, float *out, int *status, cudaStream_t st) {
     if (Q == 0) return cudaSuccess;
-    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8, 2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8, 2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16, 4>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8, 2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16, 4>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
     return cudaErrorInvalidValue;
 }
 

@@ -46,16 +46,17 @@ def bf16(x):
 
 
 def emulate_bf16_mlp(sc, m, tx, H, W):
-    """Residuals [Q,N,5] with the kernel's rounding points: layer 1 in FP32
-    from gamma(mean) and gamma(tx) (split exactly, Eq. 14-15), every hidden
-    activation and weight rounded to BF16, sums in FP64, biases FP32."""
+    """Residuals [Q,N,5] with the kernel's rounding points.  Layer 1 splits
+    exactly (Eq. 14-15) into W1m gamma(mean) -- BF16 operands -- plus the
+    per-query term W1s gamma(tx) + b1 kept in FP32; every hidden activation
+    and weight is rounded to BF16; sums in FP64; biases FP32."""
     N, Q = sc.n, tx.shape[0]
     gm = np.stack([oracle.pe(np.array([x / W, y / H]), m.L_mean) for x, y in sc.mean])
     s = (np.asarray(tx, np.float64) - np.asarray(m.room_min)) / np.asarray(m.room_size)
     gt = np.stack([oracle.pe(v, m.L_tx) for v in s])
     W0 = np.asarray(m.W[0], np.float64)
     dm = gm.shape[1]
-    U = (gm @ W0[:, :dm].T).astype(np.float32)
+    U = (bf16(gm) @ bf16(W0[:, :dm]).T).astype(np.float32)
     V = (gt @ W0[:, dm:].T + m.b[0]).astype(np.float32)
     h = bf16(np.maximum(U[None, :, :] + V[:, None, :], 0).reshape(Q * N, -1))
     for l in range(1, len(m.W) - 1):
