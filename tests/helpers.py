@@ -17,8 +17,9 @@ def oracle_proj_to_records(proj):
 
 def spectrum_error(gpu, ref, slack, rel_tol):
     """Per-query check |gpu - ref| <= rel_tol * peak_q + slack (slack = the
-    oracle's sum over Gaussians within the FP32/FP64 cutoff band).
-    Returns (ok, worst error / peak, pixels that needed slack)."""
+    oracle's sum over Gaussians whose q lies in the FP32/FP64 cutoff band,
+    where either decision is correct).  Returns (ok, worst error / peak net of
+    the band slack, pixels whose difference needed the slack)."""
     gpu = np.asarray(gpu, np.float64)
     Q = ref.shape[0]
     worst, used, ok = 0.0, 0, True
@@ -26,9 +27,9 @@ def spectrum_error(gpu, ref, slack, rel_tol):
         peak = max(float(np.abs(ref[q]).max()), 1e-30)
         d = np.abs(gpu[q] - ref[q])
         tol = rel_tol * peak
-        bad = d > tol
-        used += int(np.count_nonzero(bad & (d <= tol + slack[q])))
+        used += int(np.count_nonzero((d > tol) & (d <= tol + slack[q])))
         if np.any(d > tol + slack[q]):
             ok = False
-        worst = max(worst, float((d - np.where(bad, slack[q], 0)).max()) / peak)
+        worst = max(worst, float(np.maximum(d - slack[q], 0.0).max()) / peak)
     return ok, worst, used
+

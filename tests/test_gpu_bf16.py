@@ -194,3 +194,20 @@ def test_bf16_batched_workload_sampled(api):
     print(f"batched bf16 20k x 256 (sampled {idx}): max err/peak {worst:.2e}, slack px {used}")
     assert ok
     assert np.all(np.isfinite(out)) and np.all(out.reshape(Q, -1).max(1) > 0)
+
+
+def test_bf16_deform_is_repeatable(api):
+    """Each row of the tensor-core MLP depends only on its own inputs, so
+    repeated calls give bit-identical residuals (a read of TMEM results
+    before they land, or any other ordering race, shows up here)."""
+    H, W = 90, 360
+    sc = synth.make_scene(20000, H, W, seed=21)
+    m = api.DeviceMLP.from_host(synth.make_mlp(gain=1.0, bias_std=0.05, seed=21), dev(),
+                                precision=api.WRF_BF16)
+    tx = T(synth.make_tx(256, seed=21))
+    ds = api.DeviceScene.from_host(sc, dev())
+    grid = api.make_grid(H, W)
+    first = api.wrf_deform(ds, m, grid, tx).clone()
+    for _ in range(4):
+        again = api.wrf_deform(ds, m, grid, tx)
+        assert torch.equal(first, again)
