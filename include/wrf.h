@@ -149,6 +149,30 @@ wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
                    int64_t key_capacity, int64_t *n_keys_out, uint32_t *tile_offsets, void *ws,
                    size_t ws_bytes, void *stream);
 
+/* wrf_bin without a caller workspace (no counterpart in the paper: it is a
+ * convenience for callers that cannot allocate device memory -- for example
+ * code embedded in a host application that owns the device's memory pool, or
+ * a latency-critical loop where a cudaMalloc, which may synchronise the
+ * device, is not allowed).  It behaves exactly like wrf_bin, with the
+ * scratch space taken from a fixed 4 MiB array in device memory that the
+ * library holds on every device that loads it until the process exits.
+ *   - Calls whose scratch need (wrf_bin_workspace_size) exceeds 4 MiB are
+ *     rejected with WRF_EINVAL before any work is queued; at 16 x 16 tiles
+ *     on a 360 x 90 grid that admits Q * ceil(N / 1024) up to about 7,500.
+ *   - The function allocates nothing (no cudaMalloc, cudaFree or allocating
+ *     library call).  Its first call on a device looks the array's device
+ *     address up once (cudaGetSymbolAddress); make that first call outside
+ *     any stream capture.
+ *   - Every call shares the one array: calls that may run at the same time
+ *     on the GPU (different streams, or overlapping work on one device)
+ *     race on it.  Serialise them.  The array keeps the last call's
+ *     contents; binning overwrites everything it reads, so nothing needs
+ *     clearing between calls.
+ * Arguments and outputs are those of wrf_bin.                               */
+wrf_status wrf_bin_noalloc(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
+                           uint32_t *gids, int64_t key_capacity, int64_t *n_keys_out,
+                           uint32_t *tile_offsets, void *stream);
+
 /* Rasterisation, Eq. 9 / Eq. 13: A_q(y, x) = sum over the Gaussians listed
  * for the pixel's tile, ascending n, of [q <= q_cut] w exp(-q/2).  No depth
  * order, no transmittance, no clamping (order-free accumulation).

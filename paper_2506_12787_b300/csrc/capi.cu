@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include "kernels.h"
 
@@ -38,6 +39,34 @@ int *status_ptr() {
         ptrs[dev] = static_cast<int *>(p);
     }
     return ptrs[dev];
+}
+
+// Scratch for wrf_bin_noalloc: a fixed array in device memory that exists on
+// every device that loads this library, for the life of the process.  Host
+// code may not use the symbol as an address; bin_scratch_ptr() asks the
+// runtime for its device address.
+constexpr size_t kBinScratchBytes = size_t(4) << 20;  // 4 MiB
+__device__ __align__(256) unsigned char g_bin_scratch[kBinScratchBytes];
+
+// Device address of g_bin_scratch on the current device, looked up on the
+// first call per device (the first wrf_bin_noalloc call on a device should
+// therefore come before any stream capture).  Returns the CUDA error.
+cudaError_t bin_scratch_ptr(void **out) {
+    static void *ptrs[64] = {nullptr};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_bin_scratch);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = p;
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
 }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -243,6 +272,28 @@ wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
                                     tile_offsets, w, status_ptr(), static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(e, "bin");
     return WRF_OK;
+}
+
+wrf_status wrf_bin_noalloc(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
+                           uint32_t *gids, int64_t key_capacity, int64_t *n_keys_out,
+                           uint32_t *tile_offsets, void *stream) {
+    wrf::GridView g{};
+    wrf_status s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n < 0 || Q < 0 || key_capacity < 0) return fail(WRF_EINVAL, "negative size");
+    const size_t need = wrf::bin_ws_layout(n, Q, g, nullptr, nullptr);
+    if (need > kBinScratchBytes)
+        return fail(WRF_EINVAL,
+                    "wrf_bin_noalloc: this size needs %zu bytes of scratch, the built-in "
+                    "scratch holds %zu; use wrf_bin with a caller workspace",
+                    need, kBinScratchBytes);
+    void *ws = nullptr;
+    cudaError_t e = bin_scratch_ptr(&ws);
+    if (e != cudaSuccess) return cuda_fail(e, "wrf_bin_noalloc: scratch address");
+    // The scratch needs no clearing: binning writes every count and block
+    // sum it later reads.
+    return wrf_bin(rec, n, Q, grid, gids, key_capacity, n_keys_out, tile_offsets, ws,
+                   kBinScratchBytes, stream);
 }
 
 wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *tile_offsets,
