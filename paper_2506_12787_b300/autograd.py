@@ -1,0 +1,79 @@
+"""Differentiable spectrum synthesis: a torch.autograd.Function over the C ABI.
+
+forward  (Sec. 4.2 Eq. 12-15, Sec. 4.1 Eq. 8-9): residuals of the deformation
+         MLP (wrf_deform), projection (wrf_project), tile binning (wrf_bin)
+         and the order-free rasteriser (wrf_render).
+backward (Sec. 4.4: all parameters are fitted by back-propagation):
+         wrf_render_backward recomputes every per-pixel weight from the
+         records and tile lists (nothing per pixel is stored by the forward),
+         wrf_project_backward maps record gradients to the residual and
+         reference-frame gradients, wrf_deform_backward back-propagates
+         through the MLP and (unless stop_grad_mean) through gamma(mean).
+
+PyTorch provides memory and the stream only; every step runs in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import api
+
+
+@dataclasses.dataclass
+class SpectrumConfig:
+    grid: object                 # api.make_grid(...)
+    L_mean: int = 6
+    L_tx: int = 10
+    room_min: tuple = (0.0, 0.0, 0.0)
+    room_size: tuple = (5.0, 5.0, 3.0)
+    stop_grad_mean: bool = False  # the paper's fine stage freezes position gradients
+    renderer: object = None       # reusable api.Renderer (created on first use)
+
+
+class SpectrumFunction(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, cfg, tx, mean, log_scale, rot, opacity_logit, amp, *params):
+        dev = tx.device
+        scene = api.DeviceScene(mean.detach().contiguous(), log_scale.detach().contiguous(),
+                                rot.detach().contiguous(), opacity_logit.detach().contiguous(),
+                                amp.detach().contiguous())
+        W = [p.detach().contiguous() for p in params[0::2]]
+        b = [p.detach().contiguous() for p in params[1::2]]
+        mlp = api.DeviceMLP(W, b, cfg.L_mean, cfg.L_tx, tuple(cfg.room_min),
+                            tuple(cfg.room_size), api.WRF_FP32)
+        if cfg.renderer is None:
+            cfg.renderer = api.Renderer(cfg.grid, dev, fused=False)
+        r = cfg.renderer
+        txc = tx.detach().contiguous()
+        out = r.forward(scene, mlp, txc).clone()
+        last = r.last
+        ctx.cfg, ctx.scene, ctx.mlp, ctx.tx = cfg, scene, mlp, txc
+        ctx.saved = dict(rec=last["rec"].clone(), gids=last["gids"].clone(),
+                         offs=last["offs"].clone(), n_keys=last["n_keys"].clone(),
+                         resid=last["resid"].clone(), cap=r.cap)
+        ctx.n_params = len(params)
+        return out
+
+    @staticmethod
+    def backward(ctx, dA):
+        cfg, scene, mlp, sv = ctx.cfg, ctx.scene, ctx.mlp, ctx.saved
+        Q, N = int(ctx.tx.shape[0]), scene.n
+        d_rec = api.wrf_render_backward(sv["rec"], sv["gids"], sv["offs"], sv["n_keys"],
+                                        sv["cap"], N, Q, cfg.grid, dA.contiguous())
+        g = api.wrf_project_backward(scene, sv["resid"], Q, d_rec)
+        dW, db, d_mean = api.wrf_deform_backward(scene, mlp, cfg.grid, ctx.tx, g["d_resid"],
+                                                 d_mean=g["d_mean"],
+                                                 stop_grad_mean=cfg.stop_grad_mean)
+        grads = [None, None, d_mean, g["d_log_scale"], g["d_rot"], g["d_opacity"], g["d_amp"]]
+        for w, b in zip(dW, db):
+            grads += [w, b]
+        return tuple(grads)
+
+
+def render_spectra(cfg: SpectrumConfig, tx, mean, log_scale, rot, opacity_logit, amp, params):
+    """Spectra [Q,H,W] for TX positions tx [Q,3], differentiable in the
+    Gaussians and the MLP parameters (params = [W0, b0, W1, b1, ...])."""
+    return SpectrumFunction.apply(cfg, tx, mean, log_scale, rot, opacity_logit, amp, *params)

@@ -391,7 +391,7 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
         e = wrf::launch_prep(sv, m, g, tx, Q, fw, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "prep");
     }
-    e = wrf::launch_mlp_bwd(sv, m, g, Q, fw, bw, d_resid, dW, db, d_mean, stop_grad_mean, st);
+    e = wrf::launch_mlp_bwd(sv, m, g, tx, Q, fw, bw, d_resid, dW, db, d_mean, stop_grad_mean, st);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_backward");
     return WRF_OK;
 }

@@ -163,10 +163,32 @@ __device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float
 }
 
 // ------------------------------------------------------ positional encoding
-// Eq. 15 for one component x at band k: sin(2^k pi x), cos(2^k pi x).
-// 2^k * x is exact in FP32, and sincospif reduces the argument exactly.
-__device__ __forceinline__ void pe_band(float x, int k, float &s, float &c) {
-    sincospif(ldexpf(x, k), &s, &c);
+// Eq. 15 applies sin and cos to 2^k pi x for k up to L-1 (2^9 pi at L = 10):
+// a rounding of x by one FP32 ulp would move the phase of the top band by
+// ~1e-4.  x = (a - b) / d is therefore carried as an unevaluated sum
+// hi + lo of two FP32 numbers (TwoSum for a - b, the exact FMA remainder for
+// the division), and the phase 2^k (hi + lo) is reduced modulo 2 exactly
+// before sincospif, so every band keeps FP32 accuracy.
+struct PeArg {
+    float hi, lo;
+};
+__device__ __forceinline__ PeArg pe_arg(float a, float b, float d) {
+    const float t = __fsub_rn(a, b);
+    const float nb = -b;
+    const float bb = __fsub_rn(t, a);  // TwoSum: a + nb = t + e exactly
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bb)), __fsub_rn(nb, bb));
+    const float hi = __fdiv_rn(t, d);
+    const float r = fmaf(-hi, d, t);  // t - hi d, exact
+    return PeArg{hi, __fdiv_rn(__fadd_rn(r, e), d)};
+}
+__device__ __forceinline__ float pe_value(PeArg x) { return __fadd_rn(x.hi, x.lo); }
+// sin(2^k pi x), cos(2^k pi x): 2^k hi is exact, and so is its reduction by
+// the nearest even integer (Sterbenz), leaving |phase| <= 1 plus 2^k lo.
+__device__ __forceinline__ void pe_band(PeArg x, int k, float &s, float &c) {
+    const float h = ldexpf(x.hi, k);
+    const float n2 = 2.f * rintf(0.5f * h);
+    const float red = __fadd_rn(__fsub_rn(h, n2), ldexpf(x.lo, k));
+    sincospif(red, &s, &c);
 }
 
 }  // namespace wrf

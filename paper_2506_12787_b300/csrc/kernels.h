@@ -76,18 +76,20 @@ cudaError_t launch_project_bwd(const SceneView &s, const float *resid, int Q, co
                                float *d_resid, float *d_mean, float *d_ls, float *d_rot,
                                float *d_op, float *d_amp, cudaStream_t st);
 
-// MLP backward.
+// MLP backward (row chunks; see mlp_bwd.cu).
 struct DeformBwdWs {
-    float *partials;   // [nblocks][P] per-block parameter-gradient partials
-    int nblocks;
-    int P;             // parameter count
+    float *cb_H0;       // [chunk][din]  first-layer inputs
+    float *cb_Hh[7];    // [chunk][128]  hidden activations (inputs of layers 1..L-1)
+    float *cb_G[8];     // [chunk][dout] pre-activation gradients of layers 0..L-1
+    float *gam_m;       // [N][dm] gamma(mean)
+    float *gam_t;       // [Q][dt] gamma(tx)
 };
 size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, DeformBwdWs *bw,
                             char *base);
-cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g, int Q,
-                           const DeformWs &fw, const DeformBwdWs &bw, const float *d_resid,
-                           float *const *dW, float *const *db, float *d_mean, int stop_grad_mean,
-                           cudaStream_t st);
+cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g,
+                           const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
+                           const float *d_resid, float *const *dW, float *const *db,
+                           float *d_mean, int stop_grad_mean, cudaStream_t st);
 
 bool render_config_supported(int tw, int th);
 

@@ -23,8 +23,8 @@ constexpr size_t kW1ImageBytes = WRF_HIDDEN * 128;  // 128 rows x 64 BF16 column
 
 // gamma(x) of Eq. 15 for a d-vector, written to out[d(2L+1)] in the order
 // [x, sin band 0 (all d), ..., sin band L-1, cos band 0, ..., cos band L-1].
-__device__ void encode(const float *x, int d, int L, float *out) {
-    for (int i = 0; i < d; ++i) out[i] = x[i];
+__device__ void encode(const PeArg *x, int d, int L, float *out) {
+    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
     for (int k = 0; k < L; ++k)
         for (int i = 0; i < d; ++i) {
             float s, c;
@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
         int n = n0 + threadIdx.x;
         if (n < s.n) {
             float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
-            float x[2] = {mu.x / static_cast<float>(g.W), mu.y / static_cast<float>(g.H)};
+            const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
+                                pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
             encode(x, 2, m.L_mean, gam[threadIdx.x]);
         }
     }
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(128) pe_tx_kernel(MlpView m, const float *tx, 
         if (q >= Q) continue;
         // feature f: [x (3), sin band k (3 each), cos band k (3 each)]
         const int i = f % 3, grp = f / 3;
-        const float x = (tx[3 * q + i] - m.room_min[i]) / m.room_size[i];
-        float val = x;
+        const PeArg x = pe_arg(tx[3 * q + i], m.room_min[i], m.room_size[i]);
+        float val = pe_value(x);
         if (grp >= 1) {
             float sn, cs;
             pe_band(x, (grp - 1) % L, sn, cs);

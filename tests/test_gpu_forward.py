@@ -218,7 +218,7 @@ def test_deform_fp32_residuals(api):
                          api.make_grid(H, W), T(tx)).cpu().numpy()
     err = np.abs(got - ref).max() / np.abs(ref).max()
     print(f"deform fp32 max err / max|resid| = {err:.2e}")
-    assert err < 2e-5
+    assert err < 5e-6  # the encoding phase is reduced exactly (no 2^k-amplified rounding)
 
 
 def test_zero_mlp_is_identity_on_gpu(api):

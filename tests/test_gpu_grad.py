@@ -1,0 +1,221 @@
+"""GPU gradients (render backward, project backward, MLP backward and the
+autograd.Function over all of them) against the FP64 oracle's analytic
+gradient, which the CPU suite pins to central finite differences.
+
+Tolerance: relative error <= 1e-3 per parameter group, measured norm-wise,
+||g_gpu - g_oracle|| / ||g_oracle|| (an element-wise ratio is undefined where
+a gradient component is ~0).  Every comparison prints its error.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2506_12787_b300 import api, build
+    build.build()
+    assert torch.cuda.is_available()
+    return api
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device=dev())
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def params_of(m):
+    out = []
+    for W, b in zip(m.W, m.b):
+        out += [T(W).requires_grad_(), T(b).requires_grad_()]
+    return out
+
+
+def run_autograd(api, sc, m, tx, H, W, q_cut, dA, stop_grad_mean=False, tile=(16, 16)):
+    from paper_2506_12787_b300.autograd import SpectrumConfig, render_spectra
+    cfg = SpectrumConfig(api.make_grid(H, W, tile[0], tile[1], q_cut),
+                         stop_grad_mean=stop_grad_mean)
+    leaves = [T(a).requires_grad_() for a in sc.arrays()]
+    ps = params_of(m)
+    out = render_spectra(cfg, T(tx), *leaves, ps)
+    out.backward(T(dA))
+    names = ["d_mean", "d_log_scale", "d_rot", "d_opacity", "d_amp"]
+    g = {k: v.grad.cpu().numpy() for k, v in zip(names, leaves)}
+    g["d_W"] = [p.grad.cpu().numpy() for p in ps[0::2]]
+    g["d_b"] = [p.grad.cpu().numpy() for p in ps[1::2]]
+    return out.detach().cpu().numpy(), g
+
+
+def compare(g, ref, tag):
+    worst = 0.0
+    for k in ["d_mean", "d_log_scale", "d_rot", "d_opacity", "d_amp"]:
+        e = rel(g[k], ref[k])
+        worst = max(worst, e)
+        print(f"{tag} {k}: rel {e:.2e}")
+    for l, (a, b) in enumerate(zip(g["d_W"], ref["d_W"])):
+        worst = max(worst, rel(a, b))
+    for l, (a, b) in enumerate(zip(g["d_b"], ref["d_b"])):
+        worst = max(worst, rel(a, b))
+    print(f"{tag} worst rel over all groups incl. MLP weights/biases: {worst:.2e}")
+    return worst
+
+
+def test_render_backward_matches_oracle(api):
+    H, W = 90, 360
+    sc = synth.make_scene(600, H, W, ls_std=0.4, seed=40)
+    Q = 2
+    tx = synth.make_tx(Q, seed=40)
+    dA = synth.rng(40).normal(size=(Q, H, W))
+    ref = oracle.grad(sc, None, tx, H, W, 9.0, dA)
+    grid = api.make_grid(H, W, 16, 16, 9.0)
+    ds = api.DeviceScene.from_host(sc, dev())
+    r = api.Renderer(grid, dev())
+    r.forward(ds, None, T(tx))
+    L = r.last
+    d_rec = api.wrf_render_backward(L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, sc.n, Q,
+                                    grid, T(dA)).cpu().numpy()
+    e = rel(d_rec, ref["d_proj"])
+    print(f"render backward d(mx,my,A,B,C,w): rel {e:.2e}")
+    assert e <= REL
+
+
+def test_project_backward_matches_oracle(api):
+    H, W = 90, 360
+    sc = synth.make_scene(500, H, W, seed=41)
+    Q = 3
+    resid = synth.rng(41).normal(0, 0.3, size=(Q, sc.n, 5))
+    d_proj = synth.rng(42).normal(size=(Q, sc.n, 6))
+    # oracle chain rule of the projection only: feed d_proj through or_project_grad
+    import ctypes as C
+    L = oracle.lib()
+    arrs = [oracle._d(a) for a in sc.arrays()]
+    dres = np.zeros((Q, sc.n, 5)); dm = np.zeros((sc.n, 2)); dls = np.zeros((sc.n, 2))
+    drot = np.zeros(sc.n); dop = np.zeros(sc.n); damp = np.zeros(sc.n)
+    r64, pr = oracle._d(resid)
+    dp, pdp = oracle._d(d_proj)
+    D = oracle.D
+    L.or_project_grad(sc.n, arrs[1][1], arrs[2][1], arrs[3][1], arrs[4][1], Q, pr, pdp,
+                      dres.ctypes.data_as(D), dm.ctypes.data_as(D), dls.ctypes.data_as(D),
+                      drot.ctypes.data_as(D), dop.ctypes.data_as(D), damp.ctypes.data_as(D))
+    g = api.wrf_project_backward(api.DeviceScene.from_host(sc, dev()), T(resid), Q, T(d_proj))
+    for k, ref in [("d_resid", dres), ("d_mean", dm), ("d_log_scale", dls), ("d_rot", drot),
+                   ("d_opacity", dop), ("d_amp", damp)]:
+        e = rel(g[k].cpu().numpy(), ref)
+        print(f"project backward {k}: rel {e:.2e}")
+        assert e <= REL, k
+
+
+@pytest.mark.parametrize("stop", [False, True])
+def test_deform_backward_matches_oracle(api, stop):
+    H, W = 90, 360
+    sc = synth.make_scene(700, H, W, seed=43)
+    m = synth.make_mlp(gain=1.0, bias_std=0.05, seed=43)
+    Q = 3
+    tx = synth.make_tx(Q, seed=43)
+    d_resid = synth.rng(44).normal(size=(Q, sc.n, 5))
+    dims, params = oracle.flat_params(m)
+    dparams = np.zeros_like(params)
+    dmean = np.zeros((sc.n, 2))
+    mean, pm = oracle._d(sc.mean)
+    txd, pt = oracle._d(tx)
+    rmin, prm = oracle._d(m.room_min)
+    rsz, prs = oracle._d(m.room_size)
+    pp = oracle._d(params)
+    dr = oracle._d(d_resid)
+    D = oracle.D
+    rc = oracle.lib().or_mlp_grad(sc.n, pm, H, W, Q, pt, m.L_mean, m.L_tx, prm, prs, len(m.W),
+                                  dims.ctypes.data_as(oracle.I), pp[1], dr[1], int(stop),
+                                  dparams.ctypes.data_as(D), dmean.ctypes.data_as(D))
+    assert rc == 0
+    dW_ref, db_ref = oracle.unflat_params(m, dparams)
+    dW, db, d_mean = api.wrf_deform_backward(api.DeviceScene.from_host(sc, dev()),
+                                             api.DeviceMLP.from_host(m, dev()),
+                                             api.make_grid(H, W), T(tx), T(d_resid),
+                                             stop_grad_mean=stop)
+    for l in range(len(m.W)):
+        ew, eb = rel(dW[l].cpu().numpy(), dW_ref[l]), rel(db[l].cpu().numpy(), db_ref[l])
+        print(f"deform backward layer {l}: dW rel {ew:.2e}, db rel {eb:.2e}")
+        assert ew <= REL and eb <= REL
+    if stop:
+        assert np.all(d_mean.cpu().numpy() == 0)
+    else:
+        e = rel(d_mean.cpu().numpy(), dmean)
+        print(f"deform backward d_mean through gamma(mean): rel {e:.2e}")
+        assert e <= REL
+
+
+@pytest.mark.parametrize("case", ["64x32x16", "800x90x360"])
+def test_autograd_matches_oracle(api, case):
+    n, H, W = (int(v) for v in case.split("x"))
+    sc = synth.make_scene(n, H, W, ls_mean=math.log(2.0 if n == 64 else 3.0), seed=n)
+    m = synth.make_mlp(gain=0.5, bias_std=0.02, seed=n)
+    Q = 2
+    tx = synth.make_tx(Q, seed=n)
+    dA = synth.rng(n + 1).normal(size=(Q, H, W))
+    out, g = run_autograd(api, sc, m, tx, H, W, 9.0, dA)
+    ref = oracle.grad(sc, m, tx, H, W, 9.0, dA)
+    assert compare(g, ref, f"autograd {case}") <= REL
+
+
+def test_autograd_stop_grad_mean(api):
+    H, W = 16, 32
+    sc = synth.make_scene(64, H, W, ls_mean=math.log(2.0), seed=5)
+    m = synth.make_mlp(gain=0.5, bias_std=0.02, seed=5)
+    tx = synth.make_tx(2, seed=5)
+    dA = synth.rng(6).normal(size=(2, H, W))
+    _, g = run_autograd(api, sc, m, tx, H, W, 9.0, dA, stop_grad_mean=True)
+    ref = oracle.grad(sc, m, tx, H, W, 9.0, dA, stop_grad_mean=True)
+    assert compare(g, ref, "autograd stop-grad") <= REL
+
+
+def test_training_step_workload(api):
+    """The training-step workload: 20k Gaussians, 64 TX, 360x90; targets
+    rendered by the oracle from a copy with means jittered by N(0, 2 px);
+    mean L1 loss.  Gradients of 2 of the queries against the oracle, then one
+    gradient step on all 64 must lower the loss."""
+    from paper_2506_12787_b300.autograd import SpectrumConfig, render_spectra
+    H, W, N, Q = 90, 360, 20000, 64
+    sc = synth.make_scene(N, H, W, seed=0)
+    m = synth.make_mlp(seed=0)
+    tx = synth.make_tx(Q, seed=3)
+    tgt_scene = synth.jitter_means(sc, 2.0, seed=4)
+    A_tgt, _, _, _ = oracle.forward(tgt_scene, m, tx, H, W, 9.0)
+    A_tgt_t = T(A_tgt)
+    # gradient parity on 2 queries (L1 sign from the GPU forward)
+    sub = [0, 37]
+    out, _ = run_autograd(api, sc, m, tx[sub], H, W, 9.0, np.zeros((2, H, W)))
+    dA = np.sign(out - A_tgt[sub]) / (2 * H * W)
+    _, g = run_autograd(api, sc, m, tx[sub], H, W, 9.0, dA)
+    ref = oracle.grad(sc, m, tx[sub], H, W, 9.0, dA)
+    assert compare(g, ref, "training step (2 queries)") <= REL
+    # full step: loss decreases after a small step along -grad of the Gaussians
+    cfg = SpectrumConfig(api.make_grid(H, W, 16, 16, 9.0))
+    leaves = [T(a).requires_grad_() for a in sc.arrays()]
+    ps = params_of(m)
+    loss0 = (render_spectra(cfg, T(tx), *leaves, ps) - A_tgt_t).abs().mean()
+    loss0.backward()
+    with torch.no_grad():
+        for v in leaves + ps:
+            assert torch.all(torch.isfinite(v.grad))
+        stepped = [v - 1e-2 * v.grad / (v.grad.abs().max() + 1e-30) for v in leaves]
+        loss1 = (render_spectra(cfg, T(tx), *stepped, [p.detach() for p in ps]) - A_tgt_t).abs().mean()
+    print(f"training step: L1 {float(loss0):.6f} -> {float(loss1):.6f}")
+    assert float(loss1) < float(loss0)
