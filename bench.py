@@ -62,6 +62,10 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=192, help="queries timed on the CPU oracle")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
+    p.add_argument("--serving", type=int, default=1, help="also run the serving workload")
+    p.add_argument("--rate", type=float, default=50000.0, help="serving arrivals per second")
+    p.add_argument("--serve-seconds", type=float, default=10.0)
+    p.add_argument("--serve-warmup", type=float, default=1.0)
     return p.parse_args()
 
 
@@ -240,6 +244,39 @@ def cpu_baseline(args, sc, m, tx, shape):
                       f"FP64 C oracle (OpenMP), {dt:.1f} s"}
 
 
+def run_serving(args, dev):
+    """Serving workload: Poisson stream (mean args.rate queries/s) of single
+    TX queries over 8 resident scenes (5k..120k Gaussians, 360x90), scene
+    uniform per query; continuous batching vs one query per launch on the
+    same arrivals.  Latency = arrival -> spectrum in pinned host memory."""
+    from paper_2506_12787_b300 import api, serving
+    sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
+    grid = api.make_grid(90, 360, 16, 16, Q_CUT)
+    mlp = synth.make_mlp(seed=0)
+    scenes = [serving.ResidentScene(i, synth.make_scene(n, 90, 360, seed=200 + i), mlp, grid, dev)
+              for i, n in enumerate(sizes)]
+    warm, dur = args.serve_warmup, args.serve_seconds
+    t, sc = synth.poisson_arrivals(args.rate, warm + dur, len(sizes), seed=0)
+    arr = list(zip(t.tolist(), sc.tolist()))
+    txs = synth.make_tx(len(arr), seed=9)
+    out = {"config": f"Poisson {args.rate:.0f} q/s over 8 resident scenes {list(sizes)}, "
+                     f"{dur:.0f} s measured after {warm:.0f} s warm-up, BF16 MLP, 360x90"}
+    srv = serving.Server(scenes, n_streams=4, buckets=(1, 4, 16, 64, 128))
+    srv.prepare()
+    cb, _ = serving.run_stream(srv, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
+                               warmup_s=warm)
+    cb["overflow_reruns"] = srv.overflows
+    plain = serving.PlainServer(scenes)
+    plain.prepare()
+    pl, _ = serving.run_stream(plain, arr, lambda i: txs[i], window_s=warm + dur, drain_s=1.0,
+                               warmup_s=warm)
+    for d in (cb, pl):
+        # p99 over all offered requests is undefined once >1% were never served
+        d["p99_ms_all"] = d["p99_ms"] if d["unserved"] <= 0.01 * max(1, d["offered"]) else None
+    out["continuous"], out["plain"] = cb, pl
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -400,6 +437,8 @@ def main():
                     "d2h_bytes_per_step": Q * H * W * 4},
             "gpu_launches": fw.launches_per_run * K,
             "roofline": roof}
+    if args.serving and ws == 1:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, sc, m, tx_np, shape)
     if rank == 0:

@@ -1,0 +1,369 @@
+"""Continuous-batching spectrum server over resident scenes (one GPU).
+
+Requests are single TX positions for one of several resident scenes (each
+scene's Gaussians and deformation MLP stay in HBM).  The server keeps a queue
+per scene and, whenever a batch slot is free, launches the oldest waiting
+requests of a scene as one batched forward (deform+project -> bin -> render,
+replayed from a CUDA graph captured for that slot) on one of K streams;
+requests that arrive while other batches are on the GPU are admitted as
+slots free up, so work of several scenes and batches overlaps on the device.
+Slots are created on demand and admitted by memory: the device bytes of all
+slots together stay within an HBM budget.  A request completes when its
+batch's spectra are back in pinned host memory, where they are handed to the
+caller's on_result callback; its latency is measured from arrival to the poll
+that sees the batch's completion event.
+
+``PlainServer`` is the baseline: one query per launch, in arrival order, on
+one stream.
+
+The spectrum of a query does not depend on the other queries of its batch
+(every stage treats queries independently), so a result served in a mix
+equals the result of the query served alone.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+import torch
+
+from . import api
+from .batched import BatchedForward
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    scene: int
+    tx: np.ndarray          # [3] metres
+    t_arrival: float        # host seconds (time.perf_counter)
+    t_done: float = -1.0
+    result: np.ndarray = None  # set by callers that keep results (see keep_results)
+
+
+class ResidentScene:
+    """One scene kept in HBM: Gaussians, BF16 deformation MLP and the key
+    count per query measured once at registration."""
+
+    def __init__(self, sid, scene_host, mlp_host, grid, device, precision=api.WRF_BF16,
+                 probe_tx=None):
+        self.sid = sid
+        self.grid = grid
+        self.device = torch.device(device)
+        self.scene = api.DeviceScene.from_host(scene_host, self.device)
+        self.mlp = api.DeviceMLP.from_host(mlp_host, self.device, precision=precision)
+        self.n = self.scene.n
+        probe = np.asarray(probe_tx if probe_tx is not None else
+                           [[2.5, 2.5, 1.5], [0.5, 4.5, 2.5], [4.5, 0.5, 0.5], [1.0, 1.0, 1.0]],
+                           np.float32)
+        fw = BatchedForward(self.scene, self.mlp, grid, probe.shape[0], self.device)
+        need = fw.reserve(torch.as_tensor(probe, device=self.device))
+        self.keys_per_query = need / probe.shape[0]
+        del fw
+
+
+class Slot:
+    """Device buffers + captured graph of one batched forward of Q queries of
+    one scene, with pinned host staging for its inputs and outputs."""
+
+    def __init__(self, rs: ResidentScene, Q: int, stream, margin=1.6):
+        self.rs, self.Q, self.stream = rs, Q, stream
+        dev = rs.device
+        cap = int(rs.keys_per_query * Q * margin) + 4096
+        self.fw = BatchedForward(rs.scene, rs.mlp, rs.grid, Q, dev, key_capacity=cap)
+        self.tx_dev = torch.zeros((Q, 3), dtype=torch.float32, device=dev)
+        self.tx_host = torch.zeros((Q, 3), dtype=torch.float32).pin_memory()
+        # two pinned output buffers, alternating per batch: a batch's results
+        # are handed out at its completion, before the slot's next-but-one
+        # batch can reuse the buffer
+        self.out_ring = [torch.empty((Q, rs.grid.H, rs.grid.W), dtype=torch.float32).pin_memory()
+                         for _ in range(2)]
+        self.nbatch = 0
+        self.out_host = self.out_ring[0]
+        self.nk_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+        self.done = torch.cuda.Event()
+        self.graph = self.fw.graph(self.tx_dev, stream)
+        self.reqs = []
+        self.busy = False
+        self.nbytes = sum(int(t.numel() * t.element_size()) for t in
+                          (self.fw.rec, self.fw.gids, self.fw.offs, self.fw.out, self.fw.dws,
+                           self.fw.bws))
+
+    def launch(self, reqs):
+        self.reqs = reqs
+        self.busy = True
+        txs = np.stack([r.tx for r in reqs]).astype(np.float32)
+        if len(reqs) < self.Q:  # pad the bucket with the first query (results dropped)
+            txs = np.concatenate([txs, np.repeat(txs[:1], self.Q - len(reqs), 0)])
+        self.tx_host.numpy()[:] = txs
+        self.out_host = self.out_ring[self.nbatch & 1]
+        self.nbatch += 1
+        with torch.cuda.stream(self.stream):
+            self.tx_dev.copy_(self.tx_host, non_blocking=True)
+            self.graph.replay()
+            self.out_host.copy_(self.fw.out, non_blocking=True)
+            self.nk_host.copy_(self.fw.n_keys, non_blocking=True)
+            self.done.record(self.stream)
+
+    def rerun_eager(self):
+        """After a key-capacity overflow: grow the capacity, rerun without
+        the graph (synchronously) and recapture for later batches."""
+        need = int(self.nk_host.item())
+        api.wrf_status_read(self.stream)
+        self.fw._alloc_keys(int(need * 1.5) + 4096)
+        with torch.cuda.stream(self.stream):
+            self.fw.run(self.tx_dev, self.stream)
+            self.out_host.copy_(self.fw.out, non_blocking=True)
+        self.stream.synchronize()
+        self.graph = self.fw.graph(self.tx_dev, self.stream)
+
+
+class Server:
+    """Continuous batching over resident scenes."""
+
+    def __init__(self, scenes, n_streams=4, buckets=(1, 2, 4, 8, 16, 32, 64, 128),
+                 hbm_budget=32 << 30, max_batch=128, on_result=None):
+        """on_result(request, spectrum) is called at completion with a view
+        of the spectrum in pinned host memory that stays valid during the
+        call; copy it to keep it."""
+        self.scenes = scenes
+        self.on_result = on_result
+        self.buckets = tuple(b for b in buckets if b <= max_batch)
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.next_stream = 0
+        self.budget = int(hbm_budget)
+        self.used = 0
+        self.slots = collections.defaultdict(list)  # (scene, bucket) -> [Slot]
+        self.queues = collections.defaultdict(collections.deque)
+        self.inflight = []
+        self.completed = []
+        self.overflows = 0
+        self.admission_waits = 0
+        self.evictions = 0
+        self.slot_order = []  # (scene, bucket) keys, oldest first
+
+    def _bucket(self, n):
+        for b in self.buckets:
+            if b >= n:
+                return b
+        return self.buckets[-1]
+
+    def _slot(self, sid, b):
+        for s in self.slots[(sid, b)]:
+            if not s.busy:
+                return s
+        # admit a new slot only within the HBM budget: free idle slots of
+        # other (scene, bucket) pairs, oldest first, to make room; if the
+        # memory is held by batches in flight, the requests wait
+        rs = self.scenes[sid]
+        est = b * rs.n * 32 + int(rs.keys_per_query * b * 1.6) * 4 + b * rs.grid.H * rs.grid.W * 4
+        if self.used + est > self.budget and self.used > 0:
+            for key in list(self.slot_order):
+                if self.used + est <= self.budget or self.used == 0:
+                    break
+                victim = next((x for x in self.slots[key] if not x.busy), None)
+                if victim is None or key == (sid, b):
+                    continue
+                self.slots[key].remove(victim)
+                if not self.slots[key]:
+                    self.slot_order.remove(key)
+                self.used -= victim.nbytes
+                self.evictions += 1
+                del victim
+        if self.used + est > self.budget and self.used > 0:
+            self.admission_waits += 1
+            return None
+        st = self.streams[self.next_stream % len(self.streams)]
+        self.next_stream += 1
+        s = Slot(rs, b, st)
+        self.used += s.nbytes
+        self.slots[(sid, b)].append(s)
+        if (sid, b) not in self.slot_order:
+            self.slot_order.append((sid, b))
+        return s
+
+    def prepare(self, sids=None, buckets=None, per_bucket=2):
+        """Create (and capture) per_bucket slots per (scene, bucket) ahead of
+        time, so that no graph is captured while requests are served."""
+        for sid in (sids if sids is not None else range(len(self.scenes))):
+            for b in (buckets or self.buckets):
+                made = []
+                for _ in range(per_bucket):
+                    s = self._slot(sid, b)
+                    if s is None:
+                        break
+                    s.busy = True  # so the next call makes another one
+                    made.append(s)
+                for s in made:
+                    s.busy = False
+        torch.cuda.synchronize()
+
+    def submit(self, req: Request):
+        self.queues[req.scene].append(req)
+
+    def poll(self):
+        now = None
+        still = []
+        for s in self.inflight:
+            if s.done.query():
+                now = now or time.perf_counter()
+                if int(s.nk_host.item()) > s.fw.cap:
+                    self.overflows += 1
+                    s.rerun_eager()
+                    now = time.perf_counter()
+                out = s.out_host.numpy()
+                for i, r in enumerate(s.reqs):
+                    r.t_done = now
+                    if self.on_result is not None:
+                        self.on_result(r, out[i])  # view valid during the call
+                self.completed.extend(s.reqs)
+                s.reqs = []
+                s.busy = False
+            else:
+                still.append(s)
+        self.inflight = still
+
+    def schedule(self):
+        # oldest-first over scenes: launch every scene that has waiting requests
+        order = sorted((q[0].t_arrival, sid) for sid, q in self.queues.items() if q)
+        for _, sid in order:
+            q = self.queues[sid]
+            while q:
+                b = self._bucket(len(q))
+                s = next((x for x in self.slots[(sid, b)] if not x.busy), None)
+                if s is None:
+                    # the largest free smaller bucket of this scene
+                    for bb in reversed(self.buckets):
+                        if bb < b:
+                            s = next((x for x in self.slots[(sid, bb)] if not x.busy), None)
+                            if s is not None:
+                                b = bb
+                                break
+                if s is None and not any(self.slots[(sid, bb)] for bb in self.buckets):
+                    # the scene holds no slot at all: create one if the HBM
+                    # budget admits it (otherwise wait for slots to free up;
+                    # new slots are never captured while the scene has some)
+                    s = self._slot(sid, b)
+                if s is None:
+                    break
+                take = [q.popleft() for _ in range(min(b, len(q)))]
+                s.launch(take)
+                self.inflight.append(s)
+
+    def pending(self):
+        return sum(len(q) for q in self.queues.values()) + sum(len(s.reqs) for s in self.inflight)
+
+
+class PlainServer:
+    """Baseline: one query per launch, in arrival order, on one stream."""
+
+    def __init__(self, scenes, on_result=None):
+        self.scenes = scenes
+        self.on_result = on_result
+        self.stream = torch.cuda.Stream()
+        self.slots = {}
+        self.queue = collections.deque()
+        self.completed = []
+        self.inflight = None
+
+    def prepare(self):
+        for sid, rs in enumerate(self.scenes):
+            self.slots[sid] = PlainSlot(rs, self.stream)
+        torch.cuda.synchronize()
+
+    def submit(self, req):
+        self.queue.append(req)
+
+    def poll(self):
+        if self.inflight is not None and self.inflight.done.query():
+            s = self.inflight
+            now = time.perf_counter()
+            r = s.req
+            r.t_done = now
+            if self.on_result is not None:
+                self.on_result(r, s.out_host.numpy()[0])
+            self.completed.append(r)
+            self.inflight = None
+
+    def schedule(self):
+        if self.inflight is None and self.queue:
+            r = self.queue.popleft()
+            s = self.slots[r.scene]
+            s.launch(r)
+            self.inflight = s
+
+    def pending(self):
+        return len(self.queue) + (1 if self.inflight is not None else 0)
+
+
+class PlainSlot:
+    """One-query forward through the public calls, launched eagerly."""
+
+    def __init__(self, rs, stream):
+        self.rs, self.stream = rs, stream
+        self.fw = BatchedForward(rs.scene, rs.mlp, rs.grid, 1, rs.device,
+                                 key_capacity=int(rs.keys_per_query * 2) + 4096)
+        self.tx_dev = torch.zeros((1, 3), dtype=torch.float32, device=rs.device)
+        self.tx_host = torch.zeros((1, 3), dtype=torch.float32).pin_memory()
+        self.out_host = torch.empty((1, rs.grid.H, rs.grid.W), dtype=torch.float32).pin_memory()
+        self.done = torch.cuda.Event()
+        self.req = None
+
+    def launch(self, r):
+        self.req = r
+        self.tx_host.numpy()[0] = r.tx
+        with torch.cuda.stream(self.stream):
+            self.tx_dev.copy_(self.tx_host, non_blocking=True)
+            self.fw.run(self.tx_dev, self.stream)
+            self.out_host.copy_(self.fw.out, non_blocking=True)
+            self.done.record(self.stream)
+
+
+def run_stream(server, arrivals, tx_of, window_s, drain_s=2.0, warmup_s=0.0):
+    """Drive `server` with requests (t_offset seconds, scene) from `arrivals`
+    in real time.  Requests arriving within [0, window_s) are offered; the
+    loop then drains for at most drain_s.  Requests that arrive before
+    warmup_s are served but excluded from the statistics.  Returns a stats
+    dict and the list of completed requests."""
+    t0 = time.perf_counter()
+    i, rid = 0, 0
+    reqs = []
+    n = len(arrivals)
+    while True:
+        now = time.perf_counter() - t0
+        while i < n and arrivals[i][0] <= now and arrivals[i][0] < window_s:
+            toff, sid = arrivals[i]
+            r = Request(rid, int(sid), tx_of(i), t0 + toff)
+            reqs.append(r)
+            server.submit(r)
+            i += 1
+            rid += 1
+        server.poll()
+        server.schedule()
+        if now >= window_s and (server.pending() == 0 or now >= window_s + drain_s):
+            break
+        if i >= n and now >= window_s and server.pending() == 0:
+            break
+    torch.cuda.synchronize()
+    server.poll()
+    t_end = time.perf_counter()
+    done = [r for r in reqs if r.t_done > 0]
+    meas = [r for r in done if r.t_arrival - t0 >= warmup_s]
+    lat = np.array([r.t_done - r.t_arrival for r in meas]) * 1e3
+    offered = [r for r in reqs if r.t_arrival - t0 >= warmup_s]
+    span = max(1e-9, (max((r.t_done for r in meas), default=t_end) - (t0 + warmup_s)))
+    stats = {
+        "offered": len(offered), "completed": len(meas), "unserved": len(offered) - len(meas),
+        "spectra_per_s": len(meas) / span,
+        "p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+        "mean_ms": float(lat.mean()) if len(lat) else None,
+    }
+    return stats, done
+
+
+def keep_results(req, spectrum):
+    """on_result callback that stores a copy of each spectrum on its request."""
+    req.result = spectrum.copy()
