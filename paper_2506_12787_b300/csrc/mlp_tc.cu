@@ -11,10 +11,12 @@
 //      V[q] = W1s gamma(s_q) + b1 computed once per query in FP32
 //      (prep.cu).  The per-Gaussian part runs on the tensor core: the
 //      thread of row n copies the BF16 row gamma(mean_n) (K = 32 or 64
-//      columns, prefetched during the previous tile) into the A tile, and
+//      columns; it and V[q] are prefetched during the previous tile) into
+//      the A tile, and
 //      one thread issues the K/16 MMAs against the resident W1m image;
 //   2. every layer's epilogue: the 128 threads read their row from TMEM
-//      (tcgen05.ld 32x32b), add the bias (V[q] for layer 1), apply ReLU and
+//      (tcgen05.ld 32x32b, 64 columns per load), add the bias (V[q] for
+//      layer 1), apply ReLU and
 //      round to BF16 (one cvt.rn.relu.bf16x2 per pair) into the 128x128
 //      K-major, 128-byte-swizzled A tile of the next layer;
 //   3. hidden layers: 8 MMAs of 128x128x16 each, committed to an mbarrier;
@@ -140,6 +142,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v) {
                  : "memory");
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float *v) {
+    uint32_t r[64];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31]), "+r"(r[32]), "+r"(r[33]), "+r"(r[34]), "+r"(r[35]), "+r"(r[36]), "+r"(r[37]), "+r"(r[38]), "+r"(r[39]), "+r"(r[40]), "+r"(r[41]), "+r"(r[42]), "+r"(r[43]), "+r"(r[44]), "+r"(r[45]), "+r"(r[46]), "+r"(r[47]), "+r"(r[48]), "+r"(r[49]), "+r"(r[50]), "+r"(r[51]), "+r"(r[52]), "+r"(r[53]), "+r"(r[54]), "+r"(r[55]), "+r"(r[56]), "+r"(r[57]), "+r"(r[58]), "+r"(r[59]), "+r"(r[60]), "+r"(r[61]), "+r"(r[62]), "+r"(r[63])
+                 :
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
@@ -277,10 +294,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
 
     // prefetch of this thread's gamma(mean) row for its next tile
     uint4 gpre[8];
+    float vpre = 0.f;  // this thread's column of V[q] for the next tile
     auto load_g = [&](int tile) {
         const int nb = tile % a.tpq;
         const int n = nb * kTileRows + my_row;
         const bool ok = tile < a.ntiles && n < a.N;
+        if (tile < a.ntiles) vpre = __ldg(a.V + static_cast<size_t>(tile / a.tpq) * 128 + wt);
         const uint4 *src = reinterpret_cast<const uint4 *>(a.G + static_cast<size_t>(ok ? n : 0) * a.k1);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -300,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         for (int c = 0; c < 8; ++c)
             if (c < nch)
                 *reinterpret_cast<uint4 *>(A + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = gpre[c];
-        vb[wt] = __ldg(a.V + static_cast<size_t>(q) * 128 + wt);
+        vb[wt] = vpre;
         load_g(tile + stride);
         fence_async_smem();
         named_bar(1 + wg, 128);
@@ -329,18 +348,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             tc_fence_after();
             const float *bl = l == 0 ? vb : bias + (l - 1) * 128;
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                float v[32];
-                tmem_ld32(t_acc + lane_off + c * 32, v);
+            for (int c = 0; c < 2; ++c) {
+                float v[64];
+                tmem_ld64(t_acc + lane_off + c * 64, v);
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     uint4 p;
-                    const float *b = bl + c * 32 + j * 8;
+                    const float *b = bl + c * 64 + j * 8;
                     p.x = pack_bf16_relu(v[j * 8 + 0] + b[0], v[j * 8 + 1] + b[1]);
                     p.y = pack_bf16_relu(v[j * 8 + 2] + b[2], v[j * 8 + 3] + b[3]);
                     p.z = pack_bf16_relu(v[j * 8 + 4] + b[4], v[j * 8 + 5] + b[5]);
                     p.w = pack_bf16_relu(v[j * 8 + 6] + b[6], v[j * 8 + 7] + b[7]);
-                    const int kc = c * 4 + j;  // 16-byte chunk 0..15 along K
+                    const int kc = c * 8 + j;  // 16-byte chunk 0..15 along K
                     *reinterpret_cast<uint4 *>(A + (kc >> 3) * 16384 + my_row * 128 +
                                                (((kc & 7) ^ (my_row & 7)) << 4)) = p;
                 }

@@ -232,16 +232,15 @@ class Server:
             q = self.queues[sid]
             while q:
                 b = self._bucket(len(q))
-                s = next((x for x in self.slots[(sid, b)] if not x.busy), None)
-                if s is None:
-                    # the largest free smaller bucket of this scene
-                    for bb in reversed(self.buckets):
-                        if bb < b:
-                            s = next((x for x in self.slots[(sid, bb)] if not x.busy), None)
-                            if s is not None:
-                                b = bb
-                                break
-                if s is None and not any(self.slots[(sid, bb)] for bb in self.buckets):
+                # a free slot of this scene: the smallest that holds the whole
+                # queue, else the largest free one
+                free = [x for bb in self.buckets for x in self.slots.get((sid, bb), ()) if not x.busy]
+                fit = [x for x in free if x.Q >= len(q)]
+                s = min(fit, key=lambda x: x.Q) if fit else (max(free, key=lambda x: x.Q)
+                                                              if free else None)
+                if s is not None:
+                    b = s.Q
+                if s is None and not any(self.slots.get((sid, bb)) for bb in self.buckets):
                     # the scene holds no slot at all: create one if the HBM
                     # budget admits it (otherwise wait for slots to free up;
                     # new slots are never captured while the scene has some)
