@@ -58,8 +58,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    p.add_argument("--tile", default="16x16")
-    p.add_argument("--cpu-sample", type=int, default=192, help="queries timed on the CPU oracle")
+    p.add_argument("--tile", default="auto", help="WxH, or auto (autotuned, cached)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="approximate CPU-oracle time of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
     p.add_argument("--serving", type=int, default=1, help="also run the serving workload")
@@ -232,10 +233,14 @@ def run_reference(args):
 
 
 def cpu_baseline(args, sc, m, tx, shape):
+    """The FP64 oracle on the host cores over a bounded sample of the
+    workload's queries (sized from one timed query to ~args.cpu_seconds)."""
     import oracle
     N, H, W, Q = shape
-    S = max(1, min(Q, args.cpu_sample))
-    oracle.forward(sc, m, tx[:1], H, W, Q_CUT)  # build + page in
+    t0 = time.perf_counter()
+    oracle.forward(sc, m, tx[:1], H, W, Q_CUT)  # builds, pages in, and times one query
+    t1 = time.perf_counter() - t0
+    S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-3)))))
     t0 = time.perf_counter()
     oracle.forward(sc, m, tx[:S], H, W, Q_CUT)
     dt = time.perf_counter() - t0
@@ -294,12 +299,18 @@ def main():
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = make_inputs(args.workload, rank)
     N, H, W, Q = shape
-    tw, th = (int(v) for v in args.tile.split("x"))
-    grid = api.make_grid(H, W, tw, th, Q_CUT)
     prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
     ds = api.DeviceScene.from_host(sc, dev)
     dm = api.DeviceMLP.from_host(m, dev, precision=prec)
     tx = torch.as_tensor(tx_np, device=dev)
+    tune_ms = None
+    if args.tile == "auto":
+        from paper_2506_12787_b300 import autotune
+        (tw, th), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT)
+    else:
+        tw, th = (int(v) for v in args.tile.split("x"))
+    args.tile = f"{tw}x{th}"
+    grid = api.make_grid(H, W, tw, th, Q_CUT)
     stream = torch.cuda.Stream(device=dev)
     fw = BatchedForward(ds, dm, grid, Q, dev)
     with torch.cuda.stream(stream):
@@ -431,13 +442,14 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if prec == api.WRF_BF16 else "f32", "data": "synthetic",
             "config": config_of(args, shape, {"keys_per_step": n_keys,
-                                              "cuda_graph": bool(args.graph)}),
+                                              "cuda_graph": bool(args.graph),
+                                              "autotune_ms_per_step": tune_ms}),
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "spectra/s", "h2d_bytes_per_step": Q * 3 * 4,
                     "d2h_bytes_per_step": Q * H * W * 4},
             "gpu_launches": fw.launches_per_run * K,
             "roofline": roof}
-    if args.serving and ws == 1:
+    if args.serving and ws == 1 and args.workload == "batched":
         line["serving"] = run_serving(args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, sc, m, tx_np, shape)
