@@ -77,6 +77,23 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(seconds_local, units_local, dist=None):
+    """Whole-job throughput over ranks: every rank processed units_local in
+    seconds_local of device time; the job took the slowest rank's time and
+    processed the sum of the units.  Returns (max seconds, total units,
+    units per second).  dist: an initialised torch.distributed (or None)."""
+    import torch
+    t = torch.tensor([float(seconds_local)], dtype=torch.float64)
+    u = torch.tensor([float(units_local)], dtype=torch.float64)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        if dist.get_backend() == "nccl":
+            t, u = t.cuda(), u.cuda()
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    tmax, utot = float(t.item()), float(u.item())
+    return tmax, utot, utot / tmax
+
+
 def make_inputs(workload, rank):
     N, H, W, Q, lsm, lss = WORKLOADS[workload]
     sc = synth.make_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
@@ -367,11 +384,7 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_s = sum(step_ms) / 1e3
-    t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_max = float(t.item())
-    value = Q * K * ws / total_max
+    total_max, _, value = aggregate(total_s, Q * K, dist if ws > 1 else None)
 
     # (2) per-stage timing of the same step (eager launches, same stream)
     KS = max(3, min(K, 50))
@@ -402,10 +415,7 @@ def main():
             eev[i][1].record(stream)
     torch.cuda.synchronize()
     e2e_s = sum(a.elapsed_time(b) for a, b in eev) / 1e3
-    te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_val = Q * KE * ws / float(te.item())
+    _, _, e2e_val = aggregate(e2e_s, Q * KE, dist if ws > 1 else None)
 
     # roofline of the dominant stage
     peaks, peak_src = measured_peaks()
