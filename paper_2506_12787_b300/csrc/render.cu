@@ -13,6 +13,9 @@
 // a bitmask of the warp blocks its footprint rectangle touches.  Each warp
 // then compacts (ballot + popc) the batch into its own list, ascending, and
 // evaluates only those: 5 FMAs, one compare, one ex2 and one FMA per pixel.
+// (Set-up stores, per tile row y, alpha(y) and beta(y) with
+//   -q'(lx, y) = alpha(y) + beta(y) lx + c3 lx^2,
+// so a pixel costs two FMAs, one compare, one ex2 and one FMA.)
 // Every pixel adds its contributions in ascending Gaussian id, so a query's
 // spectrum does not depend on the other queries in the launch.  The finished
 // tile goes through shared memory to float4 stores.
@@ -30,12 +33,17 @@ namespace {
 
 // Shared-memory carve-up of the forward kernel for a tile of NT pixels
 // (one thread per pixel, a batch of B = NT records).
-template <int NT>
+// Records staged per batch: half the threads, so that a CTA's shared memory
+// stays small enough for ~7 CTAs per SM to overlap their record gathers.
+constexpr int fwd_batch(int NT) { return NT >= 64 ? NT / 2 : NT; }
+
+template <int NT, int TH>
 struct FwdSmem {
-    static constexpr int B = NT, NW = NT / 32;
+    static constexpr int B = fwd_batch(NT), NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
-    static constexpr size_t coef = raw + 2 * B * 32;           // [B][2] float4, per-tile polynomial
-    static constexpr size_t mask = coef + B * 32;              // [B] u32, warp blocks touched
+    static constexpr size_t rowc = raw + 2 * B * 32;           // [TH][RS] float2 (alpha, beta)
+    static constexpr size_t gc = rowc + TH * RS * 8;           // [B] float2 (c3, w)
+    static constexpr size_t mask = gc + B * 8;                 // [B] u32, warp blocks touched
     static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
     static constexpr size_t bytes = lists + NW * B * 2;
 };
@@ -45,13 +53,14 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status) {
-    constexpr int NT = TW * TH, B = NT, NW = NT / 32;
+    constexpr int NT = TW * TH, B = fwd_batch(NT), NW = NT / 32;
     constexpr int NSX = TW / 8;  // warp blocks of 8 x 4 pixels: NSX across, TH/4 down
     static_assert(NW == NSX * (TH / 4), "one 8x4 pixel block per warp");
-    using L = FwdSmem<NT>;
+    using L = FwdSmem<NT, TH>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
-    float4 *coef = reinterpret_cast<float4 *>(smem + L::coef);
+    float2 *rowc = reinterpret_cast<float2 *>(smem + L::rowc);
+    float2 *gcoef = reinterpret_cast<float2 *>(smem + L::gc);
     uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
     __shared__ __align__(8) uint64_t bar[2];
@@ -65,7 +74,6 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
     const int pxl = (warp % NSX) * 8 + (lane & 7);
     const int pyl = (warp / NSX) * 4 + (lane >> 3);
     const float lx = static_cast<float>(pxl - TW / 2), ly = static_cast<float>(pyl - TH / 2);
-    const float lx2 = lx * lx, lxy = lx * ly, ly2 = ly * ly;  // exact (small integers)
     const float xcen = static_cast<float>(x0 + TW / 2), ycen = static_cast<float>(y0 + TH / 2);
 
     uint32_t s0 = 0, s1 = 0;
@@ -87,7 +95,7 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
     }
     __syncthreads();
     for (int b = 0; b < 2 && b < nb; ++b) {
-        if (tid < total - b * B) {
+        if (tid < B && tid < total - b * B) {
             const uint32_t gid = gids[s0 + b * B + tid];
             bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
         }
@@ -113,8 +121,14 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
             const float ux = r0.x - xcen, uy = r0.y - ycen;
             const float h1 = fmaf(r0.z, ux, r0.w * uy), h2 = fmaf(r0.w, ux, r1.x * uy);
             const float c0 = -fmaf(ux, h1, uy * h2);
-            coef[tid * 2] = make_float4(c0, 2.f * h1, 2.f * h2, r1.y);
-            coef[tid * 2 + 1] = make_float4(-r0.z, -2.f * r0.w, -r1.x, 0.f);
+            const float c1 = 2.f * h1, c2 = 2.f * h2, c4 = -2.f * r0.w, c5 = -r1.x;
+            // per tile row: -q'(lx) = alpha + beta lx + c3 lx^2
+#pragma unroll
+            for (int r = 0; r < TH; ++r) {
+                const float ly = static_cast<float>(r - TH / 2);
+                rowc[r * L::RS + tid] = make_float2(fmaf(fmaf(c5, ly, c2), ly, c0), fmaf(c4, ly, c1));
+            }
+            gcoef[tid] = make_float2(-r0.z, r1.y);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(r0.x, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(r0.x, r1.z)) - static_cast<float>(x0);
@@ -132,7 +146,7 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
         }
         __syncthreads();
         // raw[buf] is consumed: the copies of batch b+2 can land there now
-        if (b + 2 < nb && tid < total - (b + 2) * B) {
+        if (b + 2 < nb && tid < B && tid < total - (b + 2) * B) {
             const uint32_t gid = gids[s0 + (b + 2) * B + tid];
             bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[buf]);
         }
@@ -147,16 +161,14 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
         }
         __syncwarp();
         // ---- accumulate: w * 2^(-q') where q <= q_cut (Eq. 8-9)
+        const float2 *myrow = rowc + pyl * L::RS;
 #pragma unroll 4
         for (int j = 0; j < m; ++j) {
             const int i = mylist[j];
-            const float4 k0 = coef[i * 2], k1 = coef[i * 2 + 1];
-            float nq = fmaf(k0.y, lx, k0.x);
-            nq = fmaf(k0.z, ly, nq);
-            nq = fmaf(k1.x, lx2, nq);
-            nq = fmaf(k1.y, lxy, nq);
-            nq = fmaf(k1.z, ly2, nq);
-            if (nq >= ncut) acc = fmaf(k0.w, ex2_approx(nq), acc);
+            const float2 ab = myrow[i];  // this pixel row's alpha, beta
+            const float2 cw = gcoef[i];  // c3, w
+            const float nq = fmaf(fmaf(cw.x, lx, ab.y), lx, ab.x);
+            if (nq >= ncut) acc = fmaf(cw.y, ex2_approx(nq), acc);
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
         if (abort_flag) break;
@@ -246,7 +258,7 @@ template <int TW, int TH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        float *out, int *status, cudaStream_t st) {
-    const size_t smem = FwdSmem<TW * TH>::bytes;
+    const size_t smem = FwdSmem<TW * TH, TH>::bytes;
     cudaError_t e = cudaFuncSetAttribute(render_kernel<TW, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
