@@ -42,6 +42,7 @@ WORKLOADS = {
     "batched": (20000, 90, 360, 256, math.log(3.0), 0.3),
     "large": (200000, 180, 720, 1024, math.log(2.0), 0.5),
     "plain": (1024, 90, 360, 1, math.log(3.0), 0.3),
+    "train": (20000, 90, 360, 64, math.log(3.0), 0.3),
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
@@ -299,10 +300,147 @@ def run_serving(args, dev):
     return out
 
 
+def run_train(args):
+    """Training step (differentiation form): forward (FP32 MLP) + mean L1 loss
+    against fixed targets + backward through the rasteriser, projection and
+    MLP, for 20k Gaussians and 64 TX positions per step at 360x90."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_12787_b300 import api
+    from paper_2506_12787_b300.autograd import SpectrumConfig, render_spectra
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, m, tx_np, shape = make_inputs("train", rank)
+    N, H, W, Q = shape
+    tw, th = (16, 16) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
+    cfg = SpectrumConfig(api.make_grid(H, W, tw, th, Q_CUT))
+    tx = torch.as_tensor(tx_np, device=dev)
+    tgt_scene = synth.jitter_means(sc, 2.0, seed=4)
+    ds_t = api.DeviceScene.from_host(tgt_scene, dev)
+    with torch.no_grad():  # targets: the perturbed scene (the oracle renders them in the tests)
+        tgt = api.Renderer(cfg.grid, dev).forward(ds_t, api.DeviceMLP.from_host(m, dev), tx).clone()
+    leaves = [torch.as_tensor(a, device=dev).requires_grad_() for a in sc.arrays()]
+    ps = []
+    for Wt, b in zip(m.W, m.b):
+        ps += [torch.as_tensor(Wt, device=dev).requires_grad_(),
+               torch.as_tensor(b, device=dev).requires_grad_()]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        for v in leaves + ps:
+            v.grad = None
+        out = render_spectra(cfg, tx, *leaves, ps)
+        loss = (out - tgt).abs().mean()
+        loss.backward()
+        return loss
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.fill_(i & 255)
+        ev[i][0].record()
+        loss = step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    total_max, _, value = aggregate(total_s, Q * K, dist if ws > 1 else None)
+    # per-stage times of the same step (eager calls, default stream)
+    ds = api.DeviceScene(*[v.detach() for v in leaves])
+    dm = api.DeviceMLP([p.detach() for p in ps[0::2]], [p.detach() for p in ps[1::2]])
+    r = api.Renderer(cfg.grid, dev, fused=False)
+    dA = torch.sign(r.forward(ds, dm, tx) - tgt) / (Q * H * W)
+    L = r.last
+
+    def t(f, n=5):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n
+    d_rec = api.wrf_render_backward(L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, N, Q,
+                                    cfg.grid, dA)
+    g = api.wrf_project_backward(ds, L["resid"], Q, d_rec)
+    stage = {"forward": t(lambda: r.forward(ds, dm, tx)),
+             "render_backward": t(lambda: api.wrf_render_backward(
+                 L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, N, Q, cfg.grid, dA)),
+             "project_backward": t(lambda: api.wrf_project_backward(ds, L["resid"], Q, d_rec)),
+             "deform_backward": t(lambda: api.wrf_deform_backward(ds, dm, cfg.grid, tx,
+                                                                  g["d_resid"]))}
+    peaks, peak_src = measured_peaks()
+    # MLP backward algorithmic FLOP per row: forward recompute of the hidden
+    # layers (3 x 2*128^2), delta chain through them and the output
+    # (3 x 2*128^2 + 2*128*5), weight gradients (4 x 2*128^2 + 2*128*89 +
+    # 2*128*5), d_mean through W1m (2*128*26)
+    fl_row = 3 * 2 * 128 * 128 * 2 + 2 * 128 * 5 + 4 * 2 * 128 * 128 + 2 * 128 * 89 + \
+        2 * 128 * 5 + 2 * 128 * 26
+    # the MLP backward's GEMMs are FP32 emulated on the BF16 tensor cores with
+    # a three-term split (nine BF16 products per FP32 product)
+    roof = {"kernel": "wrf_deform_backward (cuBLAS FP32-emulated GEMMs + elementwise kernels)",
+            "bound": "tensor",
+            "achieved": Q * N * fl_row / (stage["deform_backward"] * 1e-3) / 1e12,
+            "peak": peaks["bf16_tflops"] / 9.0, "unit": "TFLOP/s",
+            "peak_source": f"bf16_tflops ({peak_src}) / 9 (FP32 as 3xBF16 split)",
+            "traffic": None, "stage_ms": stage}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"train: {N} Gaussians, {Q} TX per step, {W}x{H}, L1 loss, "
+                                   "forward + backward (FP32 MLP)", "gaussians": N,
+                       "queries_per_step": Q, "tile": f"{tw}x{th}",
+                       "l2": "256 MB buffer rewritten between timed steps",
+                       "final_l1": float(loss)},
+            "clocks": clk, "roofline": roof,
+            # forward: PE x2, weights, MLP, project, bin x5, render; backward:
+            # render, project, gamma tables, PE x2, weights, 2 per 8192-row chunk
+            "gpu_launches": K * (11 + 2 + 4 + 2 * ((Q * N + 8191) // 8192))}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.grad(sc, m, tx_np[:1], H, W, Q_CUT, np.ones((1, H, W)) / (H * W))
+        t1 = time.perf_counter() - t0
+        S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-3)))))
+        dA = np.sign(np.random.default_rng(0).normal(size=(S, H, W))) / (S * H * W)
+        t0 = time.perf_counter()
+        oracle.forward(sc, m, tx_np[:S], H, W, Q_CUT)
+        oracle.grad(sc, m, tx_np[:S], H, W, Q_CUT, dA)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S / dt, "unit": "spectra/s", "cores": oracle.num_threads(),
+                                "kind": "oracle",
+                                "sample": f"forward + analytic gradient of {S} of {Q} TX queries, "
+                                          f"{N} Gaussians, FP64 C oracle (OpenMP), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "train":
+        return run_train(args)
     import torch
     import torch.distributed as dist
 

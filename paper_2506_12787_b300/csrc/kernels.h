@@ -80,9 +80,12 @@ cudaError_t launch_project_bwd(const SceneView &s, const float *resid, int Q, co
 struct DeformBwdWs {
     float *cb_H0;       // [chunk][din]  first-layer inputs
     float *cb_Hh[7];    // [chunk][128]  hidden activations (inputs of layers 1..L-1)
-    float *cb_G[8];     // [chunk][dout] pre-activation gradients of layers 0..L-1
+    float *cb_G[8];     // [chunk][128]  pre-activation gradients of layers 0..L-2
+    float *dgm;         // [chunk][dm]   dL/dgamma(mean)
     float *gam_m;       // [N][dm] gamma(mean)
     float *gam_t;       // [Q][dt] gamma(tx)
+    char *cublas_ws;    // GEMM workspace handed to cuBLAS
+    size_t cublas_ws_bytes;
 };
 size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, DeformBwdWs *bw,
                             char *base);

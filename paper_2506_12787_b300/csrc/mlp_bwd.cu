@@ -1,43 +1,38 @@
 // Back-propagation through the deformation MLP (Sec. 4.2 Eq. 14-15; the
-// paper fits all parameters by gradient descent, Sec. 4.4), FP32 on the
-// CUDA cores.
+// paper fits all parameters by gradient descent, Sec. 4.4).
 //
 // Given dL/d(resid) for every (query, Gaussian) row, produces dL/dW and
 // dL/db of every layer and, unless positions are stop-gradded (the paper's
 // fine stage, Sec. 4.4), the derivative through gamma(mean) added into
-// d_mean.  Rows are processed in chunks of kChunk:
-//   rows kernel  - 32 rows per CTA: recompute the forward activations
-//                  (layer 1 from the exact split U[n] + V[q], see prep.cu),
-//                  then walk the layers backwards, delta_l = (W_{l+1}^T
-//                  delta_{l+1}) * [z_l > 0]; store every layer's input row
-//                  H_l and pre-activation gradient G_l = delta_l in the chunk
-//                  buffers; add W0m^T delta_1 through the derivative of the
-//                  positional encoding into d_mean (atomics).
-//   dW kernel    - dW_l += G_l^T H_{l-1} over the chunk's rows: 32 x 32
-//                  output tiles, a slice of rows per CTA, shared-memory
-//                  tiles of 32 rows, one atomic add per output per slice;
-//                  the bias gradient is the same sum with H = 1.
+// d_mean.  Every step over rows is a dense product, so rows are processed in
+// chunks of kChunk as plain GEMMs (cuBLAS, FP32 inputs and outputs computed
+// on the tensor cores with the three-term BF16 split of FP32,
+// CUBLAS_COMPUTE_32F_EMULATED_16BFX9) between small hand-written kernels:
+//   features   H0 = [gamma(mean_n), gamma(tx_q)], H1 = ReLU(U[n] + V[q])
+//   forward    Z_l = H_{l-1} W_{l-1}^T; H_l = ReLU(Z_l + b)       (hidden layers)
+//   deltas     D_last = (G_out W_out) * [H_last > 0]; D_{l-1} = (D_l W_l) * [H_{l-1} > 0]
+//   gradients  dW_l += D_l^T H_{l-1} (GEMM over rows, accumulated across
+//              chunks), db_l += column sums of D_l,
+//              dgamma(mean) = D_1 W0m -> d_mean through d gamma / d mean.
+// All matrices are row-major [rows][width]; cuBLAS sees them column-major
+// transposed.  The GEMM workspace comes from the caller's workspace; one
+// cuBLAS handle per device is created on the first call.
+#include <cublas_v2.h>
+
+#include <mutex>
+
 #include "kernels.h"
 
 namespace wrf {
 
 namespace {
 
-constexpr int kRows = 32;
-constexpr int kChunk = 8192;
+constexpr int kChunk = 32768;
+constexpr size_t kCublasWs = size_t(32) << 20;
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// Chunk buffers, row-major [kChunk][width].
-struct ChunkBufs {
-    float *H0;        // [kChunk][din]   first-layer input [gamma(mean), gamma(tx)]
-    float *Hh[7];     // [kChunk][128]   input of layer l (= activation h_l), l = 1..n_layers-1
-    float *G[8];      // [kChunk][dout]  pre-activation gradient of layer l (G[L-1] width 5)
-    float *gam_m;     // [N][dm]         gamma(mean_n)
-    float *gam_t;     // [Q][dt]         gamma(tx_q)
-};
-
-// gamma tables (Eq. 15), same feature order and phase reduction as prep.cu.
+// gamma(x) of Eq. 15 (same feature order and phase reduction as prep.cu).
 __device__ void encode_row(const PeArg *x, int d, int L, float *out) {
     for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
     for (int k = 0; k < L; ++k)
@@ -65,218 +60,113 @@ __global__ void gamma_tables_kernel(SceneView s, MlpView m, GridView g, const fl
     }
 }
 
-struct RowsArgs {
-    SceneView s;
-    MlpView m;
-    GridView g;
-    DeformWs fw;
-    ChunkBufs cb;
-    const float *d_resid;
-    long long row0, nrows;  // rows of this chunk
-    float *d_mean;          // null: stop-grad through gamma(mean)
-};
-
-// act layout in shared memory: [unit][row] (lane = row).
-__global__ void __launch_bounds__(128) mlp_bwd_rows_kernel(RowsArgs a) {
-    extern __shared__ __align__(16) float sm[];
-    const int L = a.m.n_layers, nh = L - 2;
-    float *h = sm;                               // [L-1][128][32] activations h_1..h_{L-1}
-    float *dl = h + (L - 1) * WRF_HIDDEN * kRows;  // [2][128][32] deltas (ping-pong)
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long lr = static_cast<long long>(blockIdx.x) * kRows + lane;  // row in chunk
-    const long long row = a.row0 + lr;
-    const bool ok = lr < a.nrows;
-    const int q = ok ? static_cast<int>(row / a.s.n) : 0;
-    const int n = ok ? static_cast<int>(row % a.s.n) : 0;
-
-    // ---- forward recompute
-    {
-        const float *u = a.fw.U + static_cast<size_t>(n) * WRF_HIDDEN + warp * 32;
-        const float *v = a.fw.V + static_cast<size_t>(q) * WRF_HIDDEN + warp * 32;
-        for (int jj = 0; jj < 32; ++jj)
-            h[(warp * 32 + jj) * kRows + lane] = ok ? fmaxf(u[jj] + v[jj], 0.f) : 0.f;
-    }
-    for (int l = 0; l < nh; ++l) {
-        __syncthreads();
-        const float *in = h + l * WRF_HIDDEN * kRows;
-        float *out = h + (l + 1) * WRF_HIDDEN * kRows;
-        const float *Wt = a.fw.wt_f32 + static_cast<size_t>(l) * WRF_HIDDEN * WRF_HIDDEN;  // [k][j]
-        float acc[32];
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = a.m.bh[l][warp * 32 + jj];
-        for (int k = 0; k < WRF_HIDDEN; ++k) {
-            const float x = in[k * kRows + lane];
-            const float4 *wk = reinterpret_cast<const float4 *>(Wt + k * WRF_HIDDEN + warp * 32);
-#pragma unroll
-            for (int v4 = 0; v4 < 8; ++v4) {
-                const float4 w = wk[v4];
-                acc[4 * v4 + 0] = fmaf(w.x, x, acc[4 * v4 + 0]);
-                acc[4 * v4 + 1] = fmaf(w.y, x, acc[4 * v4 + 1]);
-                acc[4 * v4 + 2] = fmaf(w.z, x, acc[4 * v4 + 2]);
-                acc[4 * v4 + 3] = fmaf(w.w, x, acc[4 * v4 + 3]);
-            }
+// H0[r] = [gamma(mean_n), gamma(tx_q)], H1[r] = ReLU(U[n] + V[q]) for the
+// chunk's rows (row = row0 + r, q = row / N, n = row % N).
+__global__ void features_kernel(int N, long long row0, int nrows, int dm, int dt,
+                                const float *gam_m, const float *gam_t, const float *U,
+                                const float *V, float *H0, float *H1) {
+    const int din = dm + dt;
+    const long long total = static_cast<long long>(nrows) * (din + WRF_HIDDEN);
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long r = e / (din + WRF_HIDDEN);
+        const int c = static_cast<int>(e % (din + WRF_HIDDEN));
+        const long long row = row0 + r;
+        const int q = static_cast<int>(row / N), n = static_cast<int>(row % N);
+        if (c < din) {
+            H0[r * din + c] = c < dm ? gam_m[static_cast<size_t>(n) * dm + c]
+                                     : gam_t[static_cast<size_t>(q) * dt + (c - dm)];
+        } else {
+            const int j = c - din;
+            H1[r * WRF_HIDDEN + j] = fmaxf(U[static_cast<size_t>(n) * WRF_HIDDEN + j] +
+                                               V[static_cast<size_t>(q) * WRF_HIDDEN + j],
+                                           0.f);
         }
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) out[(warp * 32 + jj) * kRows + lane] = fmaxf(acc[jj], 0.f);
-    }
-    __syncthreads();
-
-    // ---- output layer: delta_out = d_resid row
-    float g5[WRF_OUT];
-#pragma unroll
-    for (int j = 0; j < WRF_OUT; ++j) g5[j] = ok ? a.d_resid[row * WRF_OUT + j] : 0.f;
-    if (warp == 0 && ok) {
-#pragma unroll
-        for (int j = 0; j < WRF_OUT; ++j) a.cb.G[L - 1][lr * WRF_OUT + j] = g5[j];
-    }
-    // delta of the last hidden pre-activation: (Wo^T g5) * [h_{L-1} > 0]
-    float *dcur = dl;
-    {
-        const float *hl = h + nh * WRF_HIDDEN * kRows;
-        for (int jj = 0; jj < 32; ++jj) {
-            const int k = warp * 32 + jj;
-            float sacc = 0.f;
-#pragma unroll
-            for (int j = 0; j < WRF_OUT; ++j) sacc = fmaf(a.m.Wo[j * WRF_HIDDEN + k], g5[j], sacc);
-            dcur[k * kRows + lane] = hl[k * kRows + lane] > 0.f ? sacc : 0.f;
-        }
-    }
-    // hidden layers backwards: layer l maps h_{l+1} -> z_{l+2}
-    for (int l = nh - 1; l >= -1; --l) {
-        __syncthreads();
-        // store G of the layer whose pre-activation dcur is, and its input H
-        const int layer = l + 1;  // 0 = first layer
-        if (ok) {
-            float *G = a.cb.G[layer] + lr * WRF_HIDDEN;
-            for (int jj = 0; jj < 32; ++jj) G[warp * 32 + jj] = dcur[(warp * 32 + jj) * kRows + lane];
-        }
-        if (l < 0) break;
-        // delta_{prev} = (W_l^T dcur) * [h_{l+1} > 0], W_l = Wh[l] [j][k]
-        float *dnext = dcur == dl ? dl + WRF_HIDDEN * kRows : dl;
-        const float *hin = h + l * WRF_HIDDEN * kRows;
-        const float *Wl = a.m.Wh[l];
-        float acc[32];
-#pragma unroll
-        for (int kk = 0; kk < 32; ++kk) acc[kk] = 0.f;
-        for (int j = 0; j < WRF_HIDDEN; ++j) {
-            const float d = dcur[j * kRows + lane];
-            const float4 *wj = reinterpret_cast<const float4 *>(Wl + j * WRF_HIDDEN + warp * 32);
-#pragma unroll
-            for (int v4 = 0; v4 < 8; ++v4) {
-                const float4 w = wj[v4];
-                acc[4 * v4 + 0] = fmaf(w.x, d, acc[4 * v4 + 0]);
-                acc[4 * v4 + 1] = fmaf(w.y, d, acc[4 * v4 + 1]);
-                acc[4 * v4 + 2] = fmaf(w.z, d, acc[4 * v4 + 2]);
-                acc[4 * v4 + 3] = fmaf(w.w, d, acc[4 * v4 + 3]);
-            }
-        }
-#pragma unroll
-        for (int kk = 0; kk < 32; ++kk) {
-            const int k = warp * 32 + kk;
-            dnext[k * kRows + lane] = hin[k * kRows + lane] > 0.f ? acc[kk] : 0.f;
-        }
-        dcur = dnext;
-    }
-    // ---- layer inputs H: activations h_1..h_{L-1} and the first-layer features
-    if (ok) {
-        for (int l = 0; l < L - 1; ++l) {
-            float *Hr = a.cb.Hh[l] + lr * WRF_HIDDEN;
-            for (int jj = 0; jj < 32; ++jj)
-                Hr[warp * 32 + jj] = h[(l * WRF_HIDDEN + warp * 32 + jj) * kRows + lane];
-        }
-        const int din = a.m.dm + a.m.dt;
-        float *H0 = a.cb.H0 + lr * din;
-        for (int k = warp; k < din; k += 4)
-            H0[k] = k < a.m.dm ? a.cb.gam_m[static_cast<size_t>(n) * a.m.dm + k]
-                               : a.cb.gam_t[static_cast<size_t>(q) * a.m.dt + (k - a.m.dm)];
-    }
-    // ---- d_mean through gamma(mean): d gamma / d x for x = mean / (W, H)
-    if (a.d_mean && ok && warp == 0) {
-        const int din = a.m.dm + a.m.dt, Lm = a.m.L_mean;
-        const float2 mu = reinterpret_cast<const float2 *>(a.s.mean)[n];
-        const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(a.g.W)),
-                            pe_arg(mu.y, 0.f, static_cast<float>(a.g.H))};
-        float gx[2] = {0.f, 0.f};
-        for (int f = 0; f < a.m.dm; ++f) {
-            // dL/dgamma_f = sum_j W0[j][f] delta1[j]
-            float s = 0.f;
-            for (int j = 0; j < WRF_HIDDEN; ++j) s = fmaf(a.m.W0[j * din + f], dcur[j * kRows + lane], s);
-            const int i = f % 2, grp = f / 2;
-            float dg = 1.f;
-            if (grp >= 1) {
-                const int k = (grp - 1) % Lm;
-                float sn, cs;
-                pe_band(x[i], k, sn, cs);
-                const float w = ldexpf(3.14159265358979f, k);
-                dg = grp <= Lm ? w * cs : -w * sn;
-            }
-            gx[i] = fmaf(s, dg, gx[i]);
-        }
-        atomicAdd(a.d_mean + 2 * n, gx[0] / static_cast<float>(a.g.W));
-        atomicAdd(a.d_mean + 2 * n + 1, gx[1] / static_cast<float>(a.g.H));
     }
 }
 
-// dW[j][k] += sum_r G[r][j] H[r][k] (and db[j] += sum_r G[r][j] when k-tile 0
-// carries the bias column) over rows [r0, r1) of the chunk.
-struct DwJob {
-    const float *G;  // [R][dout]
-    const float *H;  // [R][din]
-    float *dW;       // [dout][din]
-    float *db;       // [dout]
-    int dout, din;
-};
-struct DwArgs {
-    DwJob job[8];
-    int njobs;
-    long long nrows;
-    int slice;  // rows per CTA
-};
+// Z = ReLU(Z + b) in place, Z [nrows][128].
+__global__ void bias_relu_kernel(float *Z, const float *b, long long n) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        Z[e] = fmaxf(Z[e] + b[e & (WRF_HIDDEN - 1)], 0.f);
+}
 
-__global__ void __launch_bounds__(256) dw_kernel(DwArgs a) {
-    __shared__ float sG[32][33];
-    __shared__ float sH[32][33];
-    const DwJob jb = a.job[blockIdx.z];
-    const int j0 = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    // output tile: rows j0..j0+31 of dW, columns k0..k0+31 (blockIdx.x encodes k-tile and slice)
-    const int nkt = (jb.din + 31) / 32 + 1;  // +1: the bias column tile
-    const int kt = blockIdx.x % nkt;
-    const int sl = blockIdx.x / nkt;
-    if (j0 >= jb.dout) return;
-    const long long r0 = static_cast<long long>(sl) * a.slice;
-    if (r0 >= a.nrows) return;
-    const long long r1 = min(a.nrows, r0 + a.slice);
-    const bool bias = kt == nkt - 1;
-    const int k0 = kt * 32;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};  // rows j = j0 + ty + 8i, column k = k0 + tx
-    for (long long rb = r0; rb < r1; rb += 32) {
-        // load 32 rows of G (columns j0..j0+31) and H (columns k0..k0+31)
-        for (int i = ty; i < 32; i += 8) {
-            const long long r = rb + i;
-            const bool rok = r < r1;
-            const int j = j0 + tx, k = k0 + tx;
-            sG[i][tx] = (rok && j < jb.dout) ? jb.G[r * jb.dout + j] : 0.f;
-            sH[i][tx] = bias ? (rok ? 1.f : 0.f) : ((rok && k < jb.din) ? jb.H[r * jb.din + k] : 0.f);
+// D = D * [H > 0] in place.
+__global__ void relu_mask_kernel(float *D, const float *H, long long n) {
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<long long>(gridDim.x) * blockDim.x)
+        if (!(H[e] > 0.f)) D[e] = 0.f;
+}
+
+// db[j] += sum_r D[r][j] for D [nrows][width]: each block sums a slice of
+// rows per column, one atomic add per (block, column).
+__global__ void colsum_kernel(const float *D, int nrows, int width, float *db) {
+    const int j = threadIdx.x;
+    if (j >= width) return;
+    const int rows_per = (nrows + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * rows_per, r1 = min(nrows, r0 + rows_per);
+    float s = 0.f;
+    for (int r = r0; r < r1; ++r) s += D[static_cast<size_t>(r) * width + j];
+    if (r1 > r0) atomicAdd(db + j, s);
+}
+
+// d_mean[n] += dgamma(mean_n) . d gamma / d (mean / (W, H)) / (W, H).
+__global__ void dmean_kernel(SceneView s, MlpView m, GridView g, int N, long long row0, int nrows,
+                             const float *dgm, float *d_mean) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    const long long row = row0 + r;
+    const int n = static_cast<int>(row % N);
+    const float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
+    const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
+                        pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
+    const int Lm = m.L_mean;
+    float gx[2] = {0.f, 0.f};
+    for (int f = 0; f < m.dm; ++f) {
+        const int i = f % 2, grp = f / 2;
+        float dg = 1.f;
+        if (grp >= 1) {
+            const int k = (grp - 1) % Lm;
+            float sn, cs;
+            pe_band(x[i], k, sn, cs);
+            const float w = ldexpf(3.14159265358979f, k);
+            dg = grp <= Lm ? w * cs : -w * sn;
         }
-        __syncthreads();
-#pragma unroll 8
-        for (int i = 0; i < 32; ++i) {
-            const float hv = sH[i][tx];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u] = fmaf(sG[i][ty + 8 * u], hv, acc[u]);
-        }
-        __syncthreads();
+        gx[i] = fmaf(dgm[static_cast<size_t>(r) * m.dm + f], dg, gx[i]);
     }
-    for (int u = 0; u < 4; ++u) {
-        const int j = j0 + ty + 8 * u, k = k0 + tx;
-        if (j >= jb.dout) continue;
-        if (bias) {
-            if (tx == 0) atomicAdd(jb.db + j, acc[u]);
-        } else if (k < jb.din) {
-            atomicAdd(jb.dW + static_cast<size_t>(j) * jb.din + k, acc[u]);
-        }
+    atomicAdd(d_mean + 2 * n, gx[0] / static_cast<float>(g.W));
+    atomicAdd(d_mean + 2 * n + 1, gx[1] / static_cast<float>(g.H));
+}
+
+int grid_for(long long n) {
+    long long b = (n + 255) / 256;
+    return static_cast<int>(b > 148 * 16 ? 148 * 16 : (b < 1 ? 1 : b));
+}
+
+// One cuBLAS handle per device, created on first use.
+cublasHandle_t handle_for_device() {
+    static cublasHandle_t handles[64] = {nullptr};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!handles[dev]) {
+        cublasHandle_t h = nullptr;
+        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
+        handles[dev] = h;
     }
+    return handles[dev];
+}
+
+// C^T (m x n) = opA(A) (m x k) * opB(B) (k x n) in cuBLAS column-major terms
+// (a row-major [rows][width] matrix is a column-major [width][rows] one).
+cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
+                    int k, const float *A, int lda, const float *B, int ldb, float beta, float *C,
+                    int ldc) {
+    const float alpha = 1.f;
+    return cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
+                        CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
 }
 
 }  // namespace
@@ -294,10 +184,13 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
     const int L = m.n_layers;
     w.cb_H0 = take(static_cast<size_t>(kChunk) * din * 4);
     for (int l = 0; l < L - 1; ++l) w.cb_Hh[l] = take(static_cast<size_t>(kChunk) * WRF_HIDDEN * 4);
-    for (int l = 0; l < L; ++l)
-        w.cb_G[l] = take(static_cast<size_t>(kChunk) * (l == L - 1 ? WRF_OUT : WRF_HIDDEN) * 4);
+    for (int l = 0; l < L - 1; ++l) w.cb_G[l] = take(static_cast<size_t>(kChunk) * WRF_HIDDEN * 4);
+    w.cb_G[L - 1] = nullptr;  // the output layer's delta is d_resid itself
+    w.dgm = take(static_cast<size_t>(kChunk) * m.dm * 4);
     w.gam_m = take(static_cast<size_t>(n) * m.dm * 4);
     w.gam_t = take(static_cast<size_t>(Q) * m.dt * 4);
+    w.cublas_ws = reinterpret_cast<char *>(take(kCublasWs));
+    w.cublas_ws_bytes = kCublasWs;
     if (bw) *bw = w;
     return off;
 }
@@ -306,7 +199,7 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
                            const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
                            const float *d_resid, float *const *dW, float *const *db,
                            float *d_mean, int stop_grad_mean, cudaStream_t st) {
-    const int L = m.n_layers;
+    const int L = m.n_layers, nh = L - 2;
     const int din = m.dm + m.dt;
     for (int l = 0; l < L; ++l) {
         const int dout = l == L - 1 ? WRF_OUT : WRF_HIDDEN;
@@ -317,48 +210,63 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
     }
     const long long rows = static_cast<long long>(Q) * s.n;
     if (rows == 0) return cudaGetLastError();
+    cublasHandle_t h = handle_for_device();
+    if (!h) return cudaErrorUnknown;
+    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS ||
+        cublasSetWorkspace(h, bw.cublas_ws, bw.cublas_ws_bytes) != CUBLAS_STATUS_SUCCESS)
+        return cudaErrorUnknown;
     gamma_tables_kernel<<<static_cast<int>((s.n + Q + 127) / 128), 128, 0, st>>>(
         s, m, g, tx, Q, bw.gam_m, bw.gam_t);
-    const size_t smem = static_cast<size_t>((L - 1) + 2) * WRF_HIDDEN * kRows * 4;
-    cudaError_t e = cudaFuncSetAttribute(mlp_bwd_rows_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    RowsArgs ra{};
-    ra.s = s;
-    ra.m = m;
-    ra.g = g;
-    ra.fw = fw;
-    ra.cb.H0 = bw.cb_H0;
-    for (int l = 0; l < L - 1; ++l) ra.cb.Hh[l] = bw.cb_Hh[l];
-    for (int l = 0; l < L; ++l) ra.cb.G[l] = bw.cb_G[l];
-    ra.cb.gam_m = bw.gam_m;
-    ra.cb.gam_t = bw.gam_t;
-    ra.d_resid = d_resid;
-    ra.d_mean = stop_grad_mean ? nullptr : d_mean;
-    DwArgs da{};
-    da.njobs = L;
-    for (int l = 0; l < L; ++l) {
-        DwJob &j = da.job[l];
-        j.G = bw.cb_G[l];
-        j.H = l == 0 ? bw.cb_H0 : bw.cb_Hh[l - 1];
-        j.dW = dW[l];
-        j.db = db[l];
-        j.dout = l == L - 1 ? WRF_OUT : WRF_HIDDEN;
-        j.din = l == 0 ? din : WRF_HIDDEN;
-    }
-    da.slice = 1024;
-    int max_kt = 0;
-    for (int l = 0; l < L; ++l) max_kt = max(max_kt, (da.job[l].din + 31) / 32 + 1);
+    const cublasOperation_t N_ = CUBLAS_OP_N, T_ = CUBLAS_OP_T;
     for (long long r0 = 0; r0 < rows; r0 += kChunk) {
-        const long long nr = min(static_cast<long long>(kChunk), rows - r0);
-        ra.row0 = r0;
-        ra.nrows = nr;
-        mlp_bwd_rows_kernel<<<static_cast<int>((nr + kRows - 1) / kRows), 128, smem, st>>>(ra);
-        da.nrows = nr;
-        const int nslices = static_cast<int>((nr + da.slice - 1) / da.slice);
-        dim3 grid(max_kt * nslices, WRF_HIDDEN / 32, L);
-        dw_kernel<<<grid, 256, 0, st>>>(da);
+        const int R = static_cast<int>(rows - r0 < kChunk ? rows - r0 : kChunk);
+        const long long nH = static_cast<long long>(R) * WRF_HIDDEN;
+        features_kernel<<<grid_for(static_cast<long long>(R) * (din + WRF_HIDDEN)), 256, 0, st>>>(
+            s.n, r0, R, m.dm, m.dt, bw.gam_m, bw.gam_t, fw.U, fw.V, bw.cb_H0, bw.cb_Hh[0]);
+        // forward recompute of the hidden layers: H_{l+1} = ReLU(H_l Wh[l]^T + bh[l])
+        for (int l = 0; l < nh; ++l) {
+            if (gemm(h, T_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, bw.cb_Hh[l],
+                     WRF_HIDDEN, 0.f, bw.cb_Hh[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+            bias_relu_kernel<<<grid_for(nH), 256, 0, st>>>(bw.cb_Hh[l + 1], m.bh[l], nH);
+        }
+        const float *Gout = d_resid + r0 * WRF_OUT;
+        // delta of the last hidden layer: (G_out W_out) * [H_last > 0]
+        float *Dl = bw.cb_G[nh];
+        if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_OUT, m.Wo, WRF_HIDDEN, Gout, WRF_OUT, 0.f, Dl,
+                 WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+        relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dl, bw.cb_Hh[nh], nH);
+        // output layer gradients: dWo += G_out^T H_last, dbo += colsum(G_out)
+        if (gemm(h, N_, T_, WRF_HIDDEN, WRF_OUT, R, bw.cb_Hh[nh], WRF_HIDDEN, Gout, WRF_OUT, 1.f,
+                 dW[L - 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+        colsum_kernel<<<296, 32, 0, st>>>(Gout, R, WRF_OUT, db[L - 1]);
+        // hidden layers backwards: layer l+1 (Wh[l]) maps H_l -> Z_{l+1}
+        for (int l = nh - 1; l >= 0; --l) {
+            float *D = bw.cb_G[l + 1];  // delta of Z_{l+1}
+            if (gemm(h, N_, T_, WRF_HIDDEN, WRF_HIDDEN, R, bw.cb_Hh[l], WRF_HIDDEN, D, WRF_HIDDEN,
+                     1.f, dW[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+            colsum_kernel<<<296, 128, 0, st>>>(D, R, WRF_HIDDEN, db[l + 1]);
+            float *Dp = bw.cb_G[l];  // delta of Z_l = (D Wh[l]) * [H_l > 0]
+            if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, D, WRF_HIDDEN, 0.f,
+                     Dp, WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+            relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dp, bw.cb_Hh[l], nH);
+        }
+        // first layer: dW0 += D_0^T H0, db0 += colsum(D_0)
+        if (gemm(h, N_, T_, din, WRF_HIDDEN, R, bw.cb_H0, din, bw.cb_G[0], WRF_HIDDEN, 1.f, dW[0],
+                 din) != CUBLAS_STATUS_SUCCESS)
+            return cudaErrorUnknown;
+        colsum_kernel<<<296, 128, 0, st>>>(bw.cb_G[0], R, WRF_HIDDEN, db[0]);
+        if (!stop_grad_mean) {
+            // dgamma(mean) [R][dm] = D_0 W0[:, :dm]
+            if (gemm(h, N_, N_, m.dm, R, WRF_HIDDEN, m.W0, din, bw.cb_G[0], WRF_HIDDEN, 0.f,
+                     bw.dgm, m.dm) != CUBLAS_STATUS_SUCCESS)
+                return cudaErrorUnknown;
+            dmean_kernel<<<(R + 127) / 128, 128, 0, st>>>(s, m, g, s.n, r0, R, bw.dgm, d_mean);
+        }
     }
     return cudaGetLastError();
 }
