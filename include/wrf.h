@@ -10,8 +10,9 @@
  * Conventions shared by every entry point
  *   - Pointers named *device* are CUDA device pointers; they are owned by the
  *     caller and must stay valid until the work queued on `stream` finishes.
- *     The library never allocates device memory: scratch space is passed in
- *     as `ws` (size from the matching *_workspace_size call), 256-byte aligned.
+ *     Scratch space is passed in as `ws` (size from the matching
+ *     *_workspace_size call), 256-byte aligned; the forward calls allocate
+ *     no device memory (see wrf_deform_backward for its cuBLAS handle).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *     only enqueues work and returns; nothing synchronises the host.
  *   - Argument errors are detected on the host and returned before any work
@@ -205,7 +206,12 @@ wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int3
  * [Q][N][5] to dW[l], db[l] (same shapes as the weights; overwritten) and,
  * unless stop_grad_mean is non-zero, adds the derivative through
  * gamma(mean) into d_mean [N][2] (the paper freezes position gradients in
- * its fine stage; the flag reproduces that).                                */
+ * its fine stage; the flag reproduces that).  The dense products over rows
+ * run as cuBLAS GEMMs (FP32 emulated on the tensor cores); their workspace
+ * is part of ws, but the first call on a device creates one cuBLAS handle,
+ * for which cuBLAS allocates its own small device state: make that first
+ * call outside any stream capture.  The weight gradients are accumulated
+ * with FP32 atomics and reductions whose order is not fixed.               */
 size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp);
 wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                                const float *tx, int32_t Q, const float *d_resid, float *const *dW,
