@@ -135,17 +135,26 @@ struct SceneView {
     const float *mean, *log_scale, *rot, *opacity_logit, *amp;
 };
 
-// Deform Gaussian n by its residual (Eq. 12) and project it to a record:
+// Reference-frame parameters of one Gaussian.
+struct GaussParams {
+    float mx, my, rot, ls1, ls2, op, amp;
+};
+__device__ __forceinline__ GaussParams load_params(const SceneView &s, int n) {
+    const float2 m = reinterpret_cast<const float2 *>(s.mean)[n];
+    const float2 ls = reinterpret_cast<const float2 *>(s.log_scale)[n];
+    return GaussParams{m.x, m.y, s.rot[n], ls.x, ls.y, s.opacity_logit[n], s.amp[n]};
+}
+
+// Deform a Gaussian by its residual (Eq. 12) and project it to a record:
 // centre, log2(e)/2-scaled inverse covariance of R(th) diag(s1^2, s2^2) R^T,
-// weight sigmoid(a) * amp (Sec. 4.1) and footprint half-widths.
-__device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float d0, float d1,
-                                                float d2, float d3, float d4, const GridView &g,
-                                                float4 &r0, float4 &r1) {
-    float2 m = reinterpret_cast<const float2 *>(s.mean)[n];
-    float2 ls = reinterpret_cast<const float2 *>(s.log_scale)[n];
-    float mx = m.x + d0, my = m.y + d1;
-    float th = s.rot[n] + d2;
-    float l1 = ls.x + d3, l2 = ls.y + d4;
+// weight sigmoid(a) * amp (Sec. 4.1) and footprint half-widths; returns the
+// number of tiles its footprint rectangle covers.
+__device__ __forceinline__ uint32_t project_params(const GaussParams &p, float d0, float d1,
+                                                   float d2, float d3, float d4,
+                                                   const GridView &g, float4 &r0, float4 &r1) {
+    float mx = p.mx + d0, my = p.my + d1;
+    float th = p.rot + d2;
+    float l1 = p.ls1 + d3, l2 = p.ls2 + d4;
     float sn, cs;
     sincosf(th, &sn, &cs);
     float v1 = expf(2.f * l1), v2 = expf(2.f * l2);
@@ -153,13 +162,19 @@ __device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float
     float cc = cs * cs, ss = sn * sn, csn = cs * sn;
     float sxx = cc * v1 + ss * v2, syy = ss * v1 + cc * v2;
     float A = cc * i1 + ss * i2, B = csn * (i1 - i2), C = ss * i1 + cc * i2;
-    float w = s.amp[n] / (1.f + expf(-s.opacity_logit[n]));
+    float w = p.amp / (1.f + expf(-p.op));
     float rx = sqrtf(g.q_cut * sxx), ry = sqrtf(g.q_cut * syy);
     r0 = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
     r1 = make_float4(C * kHalfLog2e, w, rx, ry);
     int a, b, c, d;
     if (!tile_rect(mx, my, rx, ry, g, a, b, c, d)) return 0u;
     return static_cast<uint32_t>((b - a + 1) * (d - c + 1));
+}
+
+__device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float d0, float d1,
+                                                float d2, float d3, float d4, const GridView &g,
+                                                float4 &r0, float4 &r1) {
+    return project_params(load_params(s, n), d0, d1, d2, d3, d4, g, r0, r1);
 }
 
 // ------------------------------------------------------ positional encoding

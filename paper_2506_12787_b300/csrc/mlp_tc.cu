@@ -11,7 +11,8 @@
 //      V[q] = W1s gamma(s_q) + b1 computed once per query in FP32
 //      (prep.cu).  The per-Gaussian part runs on the tensor core: the
 //      thread of row n copies the BF16 row gamma(mean_n) (K = 32 or 64
-//      columns; it and V[q] are prefetched during the previous tile) into
+//      columns; it, V[q] and the row's Gaussian parameters for the
+//      projection epilogue are prefetched during the previous tile) into
 //      the A tile, and
 //      one thread issues the K/16 MMAs against the resident W1m image;
 //   2. every layer's epilogue: the 128 threads read their row from TMEM
@@ -294,12 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
 
     // prefetch of this thread's gamma(mean) row for its next tile
     uint4 gpre[8];
-    float vpre = 0.f;  // this thread's column of V[q] for the next tile
+    float vpre = 0.f;     // this thread's column of V[q] for the next tile
+    GaussParams ppre{};  // this thread's Gaussian for the next tile (projection epilogue)
     auto load_g = [&](int tile) {
         const int nb = tile % a.tpq;
         const int n = nb * kTileRows + my_row;
         const bool ok = tile < a.ntiles && n < a.N;
         if (tile < a.ntiles) vpre = __ldg(a.V + static_cast<size_t>(tile / a.tpq) * 128 + wt);
+        if (ok && a.mode == 1) ppre = load_params(a.s, n);
         const uint4 *src = reinterpret_cast<const uint4 *>(a.G + static_cast<size_t>(ok ? n : 0) * a.k1);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -320,6 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             if (c < nch)
                 *reinterpret_cast<uint4 *>(A + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = gpre[c];
         vb[wt] = vpre;
+        const GaussParams pcur = ppre;
         load_g(tile + stride);
         fence_async_smem();
         named_bar(1 + wg, 128);
@@ -402,7 +406,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 dst[4] = d4;
             } else {
                 float4 r0, r1;
-                uint32_t c = project_one(a.s, n, d0, d1, d2, d3, d4, a.g, r0, r1);
+                uint32_t c = project_params(pcur, d0, d1, d2, d3, d4, a.g, r0, r1);
                 a.rec[2 * row] = r0;
                 a.rec[2 * row + 1] = r1;
                 if (a.count) a.count[row] = c;
