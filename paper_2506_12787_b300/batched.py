@@ -95,14 +95,67 @@ class BatchedForward:
             raise _lib.WrfError(s, f"device status (n_keys={int(self.n_keys.item())}, "
                                    f"capacity={self.cap})")
 
-    def graph(self, tx, stream=None):
-        """Capture run(tx) into a CUDA graph (tx must stay at the same address)."""
+    def graph(self, tx, stream=None, out=None):
+        """Capture run(tx) into a CUDA graph (tx, and out if given, must stay
+        at the same addresses)."""
         g = torch.cuda.CUDAGraph()
         s = stream or torch.cuda.Stream(device=self.device)
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
-            self.run(tx, s)  # warm the path on the capture stream
+            self.run(tx, s, out)  # warm the path on the capture stream
         torch.cuda.current_stream().wait_stream(s)
         with torch.cuda.graph(g, stream=s):
-            self.run(tx, s)
+            self.run(tx, s, out)
         return g
+
+
+class HostPipeline:
+    """Spectra for TX batches held in host memory, with the copies overlapped
+    with compute: step i's TX upload and forward run on the compute stream
+    into device buffer i % 2 while step i-1's spectra are read back to pinned
+    host memory on a copy stream.  Each of the two buffer sets has its own
+    captured graph.  Results land in a ring of two pinned host buffers: a
+    step's spectra are valid until the step two later completes."""
+
+    def __init__(self, fw: BatchedForward):
+        self.fw = fw
+        dev = fw.device
+        self.compute = torch.cuda.Stream(device=dev)
+        self.copy = torch.cuda.Stream(device=dev)
+        self.tx_dev = [torch.zeros((fw.Q, 3), dtype=torch.float32, device=dev) for _ in range(2)]
+        self.out_dev = [fw.out, torch.empty_like(fw.out)]
+        self.out_host = [torch.empty(tuple(fw.out.shape), dtype=torch.float32).pin_memory()
+                         for _ in range(2)]
+        self.graphs = [fw.graph(self.tx_dev[k], self.compute, self.out_dev[k]) for k in range(2)]
+        self.done = [torch.cuda.Event() for _ in range(2)]   # forward k finished
+        self.freed = [torch.cuda.Event() for _ in range(2)]  # read-back of buffer k finished
+        self.i = 0
+
+    @property
+    def h2d_bytes(self):
+        return self.fw.Q * 3 * 4
+
+    @property
+    def d2h_bytes(self):
+        return int(self.fw.out.numel()) * 4
+
+    def step(self, tx_host):
+        """Enqueue one step for tx_host [Q,3] (pinned FP32); returns the
+        pinned host tensor its spectra will land in."""
+        k = self.i & 1
+        with torch.cuda.stream(self.compute):
+            if self.i >= 2:
+                self.compute.wait_event(self.freed[k])  # buffer k read back
+            self.tx_dev[k].copy_(tx_host, non_blocking=True)
+            self.graphs[k].replay()
+            self.done[k].record(self.compute)
+        with torch.cuda.stream(self.copy):
+            self.copy.wait_event(self.done[k])
+            self.out_host[k].copy_(self.out_dev[k], non_blocking=True)
+            self.freed[k].record(self.copy)
+        self.i += 1
+        return self.out_host[k]
+
+    def sync(self):
+        self.copy.synchronize()
+        self.compute.synchronize()
