@@ -218,6 +218,14 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
                                float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
                                size_t ws_bytes, void *stream);
 
+/* Diagnostic of the bounded device-side waits (no paper counterpart): one
+ * GPU thread waits, with the same bounded wait the kernels use, on an
+ * mbarrier phase that nothing completes.  The wait gives up after limit_ns
+ * (0 < limit_ns <= 2e9) and records WRF_ETIMEOUT in the status word; the
+ * kernel then returns normally and *completed (device int) is set to 0.
+ * Read the outcome with wrf_status_read.                                      */
+wrf_status wrf_selftest_wait(int64_t limit_ns, int32_t *completed, void *stream);
+
 /* Device status word: returns the first device-side error recorded since the
  * last call (WRF_OK if none) after synchronising `stream`, and clears it.    */
 wrf_status wrf_status_read(void *stream);

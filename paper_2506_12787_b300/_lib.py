@@ -25,7 +25,7 @@ EXPORTS = (
     "wrf_deform_workspace_size", "wrf_deform", "wrf_project", "wrf_deform_project",
     "wrf_bin_workspace_size", "wrf_bin", "wrf_bin_noalloc", "wrf_render", "wrf_render_backward",
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
-    "wrf_status_read", "wrf_last_error", "wrf_version",
+    "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait",
 )
 
 
@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "wrf_status_read": (I32, [P]),
         "wrf_last_error": (C.c_char_p, []),
         "wrf_version": (I32, []),
+        "wrf_selftest_wait": (I32, [I64, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

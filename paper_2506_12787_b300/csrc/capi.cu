@@ -146,11 +146,36 @@ wrf::SceneView view(const wrf_scene *s) {
 
 bool rows_ok(int n, int Q) { return static_cast<long long>(n) * Q < (1ll << 31); }
 
+// One thread waits, with the library's bounded wait, on an mbarrier phase
+// that never completes (arrival count 2, one arrival): the wait gives up
+// after limit_ns and records WRF_ETIMEOUT.  Nothing faults or hangs.
+__global__ void selftest_wait_kernel(unsigned long long limit_ns, int *status, int *waited) {
+    __shared__ __align__(8) uint64_t bar;
+    wrf::mbar_init(&bar, 2);
+    wrf::fence_mbar_init();
+    wrf::mbar_arrive(&bar);
+    const bool ok = wrf::mbar_wait(&bar, 0, status, limit_ns);
+    *waited = ok ? 1 : 0;
+}
+
 }  // namespace
 
 extern "C" {
 
 int32_t wrf_version(void) { return 1; }
+
+wrf_status wrf_selftest_wait(int64_t limit_ns, int32_t *completed, void *stream) {
+    if (limit_ns <= 0 || limit_ns > 2000000000ll)
+        return fail(WRF_EINVAL, "limit_ns must be in (0, 2e9]");
+    if (!completed) return fail(WRF_EINVAL, "completed is NULL");
+    int *st = status_ptr();
+    if (!st) return fail(WRF_ECUDA, "status word unavailable");
+    selftest_wait_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(
+        static_cast<unsigned long long>(limit_ns), st, completed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "wrf_selftest_wait");
+    return WRF_OK;
+}
 
 const char *wrf_last_error(void) { return g_err; }
 
