@@ -28,8 +28,20 @@ struct DeformWs {
     float *V;              // [Q][128]  W0[:, dm:] gamma(tx_q) + b0
     float *wt_f32;         // hidden layers transposed [l][k=128][j=128], FP32
     float *wo_f32;         // output layer transposed [k=128][8] (cols 5..7 zero)
-    uint16_t *w_bf16;      // tcgen05 operand images: W1m, hidden layers, output
+    uint16_t *w_bf16;      // tcgen05 operand images: W1m, hidden layers, output,
+                           // bias image, bias selectors
 };
+
+// Biases enter the tensor-core MLP as one extra K = 16 MMA per layer.  The
+// bias image is a no-swizzle K-major B operand of 128 rows x 8 BF16 columns
+// (16 row groups of 8 rows x 16 B, 128 B apart; row n at (n/8)*128 + (n%8)*16):
+// columns 2l, 2l+1 hold hidden layer l's bias b split as hi = bf16(b),
+// lo = bf16(b - hi); columns 6, 7 the output bias.  A selector is an A
+// operand whose every row has ones in columns 2p, 2p+1 (one 8-row core
+// matrix, repeated with row-group stride 0, and a zero core matrix for
+// K = 8..15), so A_sel(p) B_bias adds hi + lo of pair p to every row.
+constexpr size_t kBiasImageBytes = 2048;
+constexpr size_t kSelImageBytes = 4 * 256;
 
 // K of the tensor-core layer-1 MMA: gamma(mean) width dm padded to 32 or 64.
 inline __host__ __device__ int mlp_k1(int dm) { return dm <= 32 ? 32 : 64; }

@@ -15,17 +15,23 @@
 //      projection epilogue are prefetched during the previous tile) into
 //      the A tile, and
 //      one thread issues the K/16 MMAs against the resident W1m image;
-//   2. every layer's epilogue: the 128 threads read their row from TMEM
-//      (tcgen05.ld 32x32b, 64 columns per load), add the bias (V[q] for
-//      layer 1), apply ReLU and
-//      round to BF16 (one cvt.rn.relu.bf16x2 per pair) into the 128x128
-//      K-major, 128-byte-swizzled A tile of the next layer;
-//   3. hidden layers: 8 MMAs of 128x128x16 each, committed to an mbarrier;
-//   4. the output layer is one 128x16x128 MMA chain (5 useful columns)
-//      whose epilogue adds the bias and either stores the residual row or
-//      deforms and projects the Gaussian (fused Eq. 12-13) into its record.
-// All weights (W1m, <= 3 hidden layers, output; <= 116 KB of BF16) are
-// copied into shared memory once per CTA with bulk (TMA) copies.
+//   2. biases are added by the tensor core: every layer starts with one
+//      K = 16 MMA of a selector A (ones in two columns) against a bias
+//      image B holding the bias split into BF16 hi + lo (kernels.h); for
+//      layer 1 the bias image is the warpgroup's own 128 x 8 image of V[q]
+//      (hi, lo), written by the 128 threads with the tile's other operand;
+//   3. every layer's epilogue: the 128 threads read their row from TMEM
+//      (tcgen05.ld 32x32b, 64 columns per load), apply ReLU and round to
+//      BF16 in one cvt.rn.relu.bf16x2 per pair, into the 128x128 K-major,
+//      128-byte-swizzled A tile of the next layer;
+//   4. hidden layers: bias MMA + 8 MMAs of 128x128x16, committed to an
+//      mbarrier;
+//   5. the output layer is one 128x16x128 MMA chain (5 useful columns)
+//      whose epilogue either stores the residual row or deforms and
+//      projects the Gaussian (fused Eq. 12-13) into its record.
+// All weights (W1m, <= 3 hidden layers, output, bias image and selectors;
+// <= 119 KB of BF16) are copied into shared memory once per CTA with bulk
+// (TMA) copies.
 #include "kernels.h"
 
 namespace wrf {
@@ -39,6 +45,8 @@ constexpr uint32_t kLayerBytes = 128 * 128 * 2;
 constexpr uint32_t kW1Bytes = 128 * 128;  // W1m image: 128 rows x 128 B (K <= 64)
 constexpr uint32_t kOutBytes = 16 * 128 * 2;
 constexpr uint32_t kActBytes = 128 * 128 * 2;
+constexpr uint32_t kAugBytes = static_cast<uint32_t>(kBiasImageBytes + kSelImageBytes);
+constexpr uint32_t kVImgBytes = 2048;     // per warpgroup: V[q] hi/lo, 128 rows x 16 B
 constexpr uint32_t kTmemCols = 512;       // kWG x 128 accumulator columns, power of 2
 
 // ------------------------------------------------------------ tcgen05 PTX
@@ -90,6 +98,19 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
     d |= static_cast<uint64_t>(1) << 46;                 // version
     d |= static_cast<uint64_t>(2) << 61;                 // SWIZZLE_128B
+    return d;
+}
+
+// Shared-memory matrix descriptor without swizzling: K-major core matrices
+// of 8 rows x 16 bytes; lbo = byte distance between the two core matrices
+// along K (K = 0..7, 8..15), sbo = byte distance between 8-row groups.  A
+// distance of 0 repeats the same core matrix.
+__device__ __forceinline__ uint64_t plain_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;                 // version; layout 0 = no swizzle
     return d;
 }
 
@@ -219,8 +240,6 @@ struct TcArgs {
     const uint16_t *G;       // [N][k1] BF16 gamma(mean) rows, zero-padded
     const float *V;          // [Q][128] FP32 per-query layer-1 term (incl. b1)
     const uint16_t *w_img;   // BF16 images: W1m, hidden layers, output layer
-    const float *bh[3];
-    const float *bo;
     int nh;                  // hidden 128x128 layers (0..3)
     int k1;                  // layer-1 K: 32 or 64
     int Q, N, tpq;           // tiles per query
@@ -233,21 +252,23 @@ struct TcArgs {
 };
 
 constexpr size_t smem_bytes(int nh) {
-    return 1024 + kW1Bytes + nh * kLayerBytes + kOutBytes + kWG * kActBytes +
-           (nh * 128 + 16) * 4 + kWG * 128 * 4 + (1 + kWG) * 8 + 16;
+    return 1024 + kW1Bytes + nh * kLayerBytes + kOutBytes + kAugBytes + kWG * kActBytes +
+           kWG * kVImgBytes + (1 + kWG) * 8 + 16;
 }
+static_assert(smem_bytes(3) <= 227 * 1024, "shared memory of one CTA");
 
 __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned base (128-byte swizzle atoms must be 1024-aligned)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    const uint32_t w_bytes = kW1Bytes + a.nh * kLayerBytes + kOutBytes;
+    // weights (W1m, hidden, output, bias image, selectors): a multiple of
+    // 1024 bytes, so the activation tiles after them stay 1024-aligned
+    const uint32_t w_bytes = kW1Bytes + a.nh * kLayerBytes + kOutBytes + kAugBytes;
     uint8_t *wsm = base;
     uint8_t *act0 = base + w_bytes;
-    float *bias = reinterpret_cast<float *>(act0 + kWG * kActBytes);  // [nh*128 + 16]
-    float *vbuf = bias + a.nh * 128 + 16;                             // [kWG][128]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(vbuf + kWG * 128);  // wbar, mbar[kWG]
+    uint8_t *vimg0 = act0 + kWG * kActBytes;                               // [kWG][2048]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(vimg0 + kWG * kVImgBytes);  // wbar, mbar[kWG]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 1 + kWG);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
@@ -260,8 +281,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         fence_mbar_init();
         *abort_flag = 0;
     }
-    for (int i = tid; i < a.nh * 128; i += kThreads) bias[i] = a.bh[i >> 7][i & 127];
-    if (tid < 16) bias[a.nh * 128 + tid] = tid < WRF_OUT ? a.bo[tid] : 0.f;
     if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
     tc_fence_before();
     __syncthreads();
@@ -281,10 +300,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     uint64_t *mbar = &bars[1 + wg];
     uint32_t phase = 0;
     uint8_t *A = act0 + wg * kActBytes;
-    float *vb = vbuf + wg * 128;
+    uint8_t *vimg = vimg0 + wg * kVImgBytes;
     const uint32_t a_addr = smem_u32(A);
     const uint32_t w1_addr = smem_u32(wsm);
     const uint32_t wh_addr = w1_addr + kW1Bytes;
+    const uint32_t aug_addr = wh_addr + a.nh * kLayerBytes + kOutBytes;
+    const uint32_t sel_addr = aug_addr + static_cast<uint32_t>(kBiasImageBytes);
+    // bias operands: B = bias image (row groups 128 B apart, K 8..15 repeat
+    // K 0..7 and meet the selector's zero core matrix); A = selector p
+    const uint64_t d_bias = plain_desc(aug_addr, 0u, 128u);
+    const uint64_t d_vimg = plain_desc(smem_u32(vimg), 0u, 128u);
     const uint32_t t_acc = tmem_base + static_cast<uint32_t>(wg * 128);
     const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;  // TMEM lane field
     const int my_row = wq * 32 + lane;                               // row within the tile
@@ -322,7 +347,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         for (int c = 0; c < 8; ++c)
             if (c < nch)
                 *reinterpret_cast<uint4 *>(A + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = gpre[c];
-        vb[wt] = vpre;
+        {
+            // V[q] column wt as BF16 hi + lo, K columns 0 and 1 of row wt
+            const uint32_t hi = pack_bf16(vpre, 0.f) & 0xFFFFu;
+            const float hif = __uint_as_float(hi << 16);
+            const uint32_t lo = pack_bf16(__fsub_rn(vpre, hif), 0.f) & 0xFFFFu;
+            *reinterpret_cast<uint4 *>(vimg + (wt >> 3) * 128 + (wt & 7) * 16) =
+                make_uint4(hi | (lo << 16), 0u, 0u, 0u);
+        }
         const GaussParams pcur = ppre;
         load_g(tile + stride);
         fence_async_smem();
@@ -333,16 +365,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             if (leader) {
                 tc_fence_after();
                 if (l == 0) {
+                    // D = V[q] (hi + lo), then += W1m gamma(mean)
+                    mma_bf16(t_acc, plain_desc(sel_addr, 128u, 0u), d_vimg, id128, 0u);
                     for (int k = 0; k < (a.k1 >> 4); ++k)
                         mma_bf16(t_acc, sw128_desc(a_addr + k * 32u), sw128_desc(w1_addr + k * 32u),
-                                 id128, k > 0 ? 1u : 0u);
+                                 id128, 1u);
                 } else {
+                    // D = b_l (hi + lo, selector pair l-1), then += W_l h
+                    mma_bf16(t_acc, plain_desc(sel_addr + (l - 1) * 256u, 128u, 0u), d_bias, id128,
+                             0u);
                     const uint32_t wl = wh_addr + (l - 1) * kLayerBytes;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const uint32_t koff = (k >> 2) * 16384u + (k & 3) * 32u;
-                        mma_bf16(t_acc, sw128_desc(a_addr + koff), sw128_desc(wl + koff), id128,
-                                 k > 0 ? 1u : 0u);
+                        mma_bf16(t_acc, sw128_desc(a_addr + koff), sw128_desc(wl + koff), id128, 1u);
                     }
                 }
                 mma_commit(mbar);
@@ -350,7 +386,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             wait_or_abort(mbar, phase, abort_flag, a.status);
             phase ^= 1u;
             tc_fence_after();
-            const float *bl = l == 0 ? vb : bias + (l - 1) * 128;
 #pragma unroll 1
             for (int c = 0; c < 2; ++c) {
                 float v[64];
@@ -358,11 +393,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     uint4 p;
-                    const float *b = bl + c * 64 + j * 8;
-                    p.x = pack_bf16_relu(v[j * 8 + 0] + b[0], v[j * 8 + 1] + b[1]);
-                    p.y = pack_bf16_relu(v[j * 8 + 2] + b[2], v[j * 8 + 3] + b[3]);
-                    p.z = pack_bf16_relu(v[j * 8 + 4] + b[4], v[j * 8 + 5] + b[5]);
-                    p.w = pack_bf16_relu(v[j * 8 + 6] + b[6], v[j * 8 + 7] + b[7]);
+                    p.x = pack_bf16_relu(v[j * 8 + 0], v[j * 8 + 1]);
+                    p.y = pack_bf16_relu(v[j * 8 + 2], v[j * 8 + 3]);
+                    p.z = pack_bf16_relu(v[j * 8 + 4], v[j * 8 + 5]);
+                    p.w = pack_bf16_relu(v[j * 8 + 6], v[j * 8 + 7]);
                     const int kc = c * 8 + j;  // 16-byte chunk 0..15 along K
                     *reinterpret_cast<uint4 *>(A + (kc >> 3) * 16384 + my_row * 128 +
                                                (((kc & 7) ^ (my_row & 7)) << 4)) = p;
@@ -377,12 +411,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         if (leader) {
             tc_fence_after();
             const uint32_t wo = wh_addr + a.nh * kLayerBytes;
+            // D = b_out (selector pair 3), then += W_out h
+            mma_bf16(t_acc, plain_desc(sel_addr + 3 * 256u, 128u, 0u), d_bias, id16, 0u);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t ka = (k >> 2) * 16384u + (k & 3) * 32u;
                 const uint32_t kb = (k >> 2) * 2048u + (k & 3) * 32u;
-                mma_bf16(t_acc, sw128_desc(a_addr + ka), sw128_desc(wo + kb), id16,
-                         k > 0 ? 1u : 0u);
+                mma_bf16(t_acc, sw128_desc(a_addr + ka), sw128_desc(wo + kb), id16, 1u);
             }
             mma_commit(mbar);
         }
@@ -394,9 +429,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         tc_fence_before();
         if (n < a.N && !*abort_flag) {
             const long long row = static_cast<long long>(q) * a.N + n;
-            const float *bo = bias + a.nh * 128;
-            const float d0 = o[0] + bo[0], d1 = o[1] + bo[1], d2 = o[2] + bo[2],
-                        d3 = o[3] + bo[3], d4 = o[4] + bo[4];
+            const float d0 = o[0], d1 = o[1], d2 = o[2], d3 = o[3], d4 = o[4];
             if (a.mode == 0) {
                 float *dst = a.resid + row * WRF_OUT;
                 dst[0] = d0;
@@ -412,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 if (a.count) a.count[row] = c;
             }
         }
-        named_bar(1 + wg, 128);  // TMEM columns, A tile and vbuf are free again
+        named_bar(1 + wg, 128);  // TMEM columns, A tile and V image are free again
     }
     tc_fence_before();
     __syncthreads();
@@ -437,8 +470,6 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
     a.G = ws.G;
     a.V = ws.V;
     a.w_img = ws.w_bf16;
-    for (int l = 0; l < 3; ++l) a.bh[l] = l < nh ? m.bh[l] : nullptr;
-    a.bo = m.bo;
     a.nh = nh;
     a.k1 = mlp_k1(m.dm);
     a.Q = Q;

@@ -125,16 +125,41 @@ __device__ __forceinline__ uint32_t sw128_offset(int n, int k, int rows) {
 
 // One thread per (layer, row, col) of every hidden layer and the output
 // layer: FP32 transposes and BF16 swizzled images.  The BF16 image starts
-// with W1m = W0[:, :dm] as a 128 x 64 K-major image (columns >= dm zero).
+// with W1m = W0[:, :dm] as a 128 x 64 K-major image (columns >= dm zero) and
+// ends with the bias image and the four bias selectors (layout in kernels.h).
 __global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
     const int nh = m.n_layers - 2;
     const long long per = WRF_HIDDEN * WRF_HIDDEN;
     const long long w1 = want_bf16 ? WRF_HIDDEN * 64 : 0;
-    const long long total = w1 + nh * per + 16 * WRF_HIDDEN;
+    const long long mats = w1 + nh * per + 16 * WRF_HIDDEN;
+    const long long total = mats + (want_bf16 ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
     char *img = reinterpret_cast<char *>(ws.w_bf16);
     const int din = m.dm + m.dt;
+    const size_t aug_off = kW1ImageBytes + static_cast<size_t>(nh) * per * 2 + 16 * WRF_HIDDEN * 2;
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (i >= mats) {
+            // bias image (1024 elements), then selectors (4 x 128 elements)
+            const int e = static_cast<int>(i - mats);
+            float v = 0.f;
+            if (e < 1024) {
+                const int n = e >> 3, col = e & 7, pair = col >> 1;
+                float b = 0.f;
+                if (pair < 3 && pair < nh) b = m.bh[pair][n];
+                if (pair == 3 && n < WRF_OUT) b = m.bo[n];
+                const float hi = __bfloat162float(__float2bfloat16_rn(b));
+                v = (col & 1) ? b - hi : hi;
+                *reinterpret_cast<__nv_bfloat16 *>(img + aug_off + (n >> 3) * 128 + (n & 7) * 16 +
+                                                   col * 2) = __float2bfloat16_rn(v);
+            } else {
+                const int s2 = e - 1024, p = s2 >> 7, within = s2 & 127;  // 128 elements each
+                const int col = within & 7;                                // core 0: rows x 8
+                if (within < 64 && (col >> 1) == p) v = 1.f;
+                *reinterpret_cast<__nv_bfloat16 *>(img + aug_off + kBiasImageBytes + p * 256 +
+                                                   within * 2) = __float2bfloat16_rn(v);
+            }
+            continue;
+        }
         if (i < w1) {
             const int j = static_cast<int>(i / 64), k = static_cast<int>(i % 64);
             const float v = k < m.dm ? m.W0[static_cast<size_t>(j) * din + k] : 0.f;
@@ -186,7 +211,7 @@ size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
     w.wo_f32 = reinterpret_cast<float *>(take(WRF_HIDDEN * 8 * 4));
     w.w_bf16 = reinterpret_cast<uint16_t *>(
         take(kW1ImageBytes + static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 2 +
-             16 * WRF_HIDDEN * 2));
+             16 * WRF_HIDDEN * 2 + kBiasImageBytes + kSelImageBytes));
     if (ws) *ws = w;
     return off;
 }
@@ -199,7 +224,7 @@ cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g,
     if (Q > 0) pe_tx_kernel<<<(Q + kTxPerBlock - 1) / kTxPerBlock, 128, 0, st>>>(m, tx, Q, ws.V);
     long long total = (want_bf16 ? WRF_HIDDEN * 64 : 0) +
                       static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
-                      16 * WRF_HIDDEN;
+                      16 * WRF_HIDDEN + (want_bf16 ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
     int blocks = static_cast<int>((total + 255) / 256);
     if (blocks > 1184) blocks = 1184;
     weights_kernel<<<blocks, 256, 0, st>>>(m, ws, want_bf16 ? 1 : 0);
