@@ -1,8 +1,9 @@
 // Tile rasteriser for the order-free Gaussian sum (Sec. 4.1 Eq. 8-9,
 // Sec. 4.2 Eq. 13) and its backward.
 //
-// Forward: one CTA per (tile, query), one thread per pixel; warp w owns an
-// 8 x 4 pixel block of the tile.  The tile's Gaussian list (ascending id) is
+// Forward: one CTA per (tile, query), one thread per two pixels; warp w owns
+// an 8 x 8 pixel block of the tile and lane l the pixels (l % 8, l / 8) and
+// (l % 8, l / 8 + 4) of it.  The tile's Gaussian list (ascending id) is
 // streamed through shared memory in batches of one record per thread: every
 // thread issues one 32-byte cp.async.bulk (TMA bulk copy), completion is
 // counted in bytes on an mbarrier, and two landing buffers alternate so the
@@ -12,10 +13,11 @@
 // in the pixel's offset (lx, ly) from the tile centre (q' = q log2(e)/2), and
 // a bitmask of the warp blocks its footprint rectangle touches.  Each warp
 // then compacts (ballot + popc) the batch into its own list, ascending, and
-// evaluates only those: 5 FMAs, one compare, one ex2 and one FMA per pixel.
-// (Set-up stores, per tile row y, alpha(y) and beta(y) with
+// evaluates only those.  Set-up stores, per tile row y, alpha(y) and beta(y)
+// with
 //   -q'(lx, y) = alpha(y) + beta(y) lx + c3 lx^2,
-// so a pixel costs two FMAs, one compare, one ex2 and one FMA.)
+// so a pixel costs two FMAs, one compare, one ex2 and one FMA, and one list
+// entry and (c3, w) serve both pixels of a thread.
 // Every pixel adds its contributions in ascending Gaussian id, so a query's
 // spectrum does not depend on the other queries in the launch.  The finished
 // tile goes through shared memory to float4 stores.
@@ -31,15 +33,11 @@ namespace wrf {
 
 namespace {
 
-// Shared-memory carve-up of the forward kernel for a tile of NT pixels
-// (one thread per pixel, a batch of B = NT records).
-// Records staged per batch: half the threads, so that a CTA's shared memory
-// stays small enough for ~7 CTAs per SM to overlap their record gathers.
-constexpr int fwd_batch(int NT) { return NT >= 64 ? NT / 2 : NT; }
-
+// Shared-memory carve-up of the forward kernel for a tile with NT threads
+// (two pixels each) and TH rows: a batch holds B = NT records, one per thread.
 template <int NT, int TH>
 struct FwdSmem {
-    static constexpr int B = fwd_batch(NT), NW = NT / 32, RS = B + 1;  // RS: bank spread
+    static constexpr int B = NT, NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
     static constexpr size_t rowc = raw + 2 * B * 32;           // [TH][RS] float2 (alpha, beta)
     static constexpr size_t gc = rowc + TH * RS * 8;           // [B] float2 (c3, w)
@@ -49,13 +47,13 @@ struct FwdSmem {
 };
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH) render_kernel(
+__global__ void __launch_bounds__(TW *TH / 2) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status) {
-    constexpr int NT = TW * TH, B = fwd_batch(NT), NW = NT / 32;
-    constexpr int NSX = TW / 8;  // warp blocks of 8 x 4 pixels: NSX across, TH/4 down
-    static_assert(NW == NSX * (TH / 4), "one 8x4 pixel block per warp");
+    constexpr int NT = TW * TH / 2, B = NT, NW = NT / 32;
+    constexpr int NSX = TW / 8;  // warp blocks of 8 x 8 pixels: NSX across, TH/8 down
+    static_assert(NW == NSX * (TH / 8), "one 8x8 pixel block per warp");
     using L = FwdSmem<NT, TH>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
@@ -70,10 +68,11 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.x, q = blockIdx.y;
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
-    // this thread's pixel (tile-local), and its offset from the tile centre
+    // this thread's pixels (tile-local): column pxl, rows pyl and pyl + 4;
+    // lx = the column's offset from the tile centre
     const int pxl = (warp % NSX) * 8 + (lane & 7);
-    const int pyl = (warp / NSX) * 4 + (lane >> 3);
-    const float lx = static_cast<float>(pxl - TW / 2), ly = static_cast<float>(pyl - TH / 2);
+    const int pyl = (warp / NSX) * 8 + (lane >> 3);
+    const float lx = static_cast<float>(pxl - TW / 2);
     const float xcen = static_cast<float>(x0 + TW / 2), ycen = static_cast<float>(y0 + TH / 2);
 
     uint32_t s0 = 0, s1 = 0;
@@ -95,13 +94,13 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
     }
     __syncthreads();
     for (int b = 0; b < 2 && b < nb; ++b) {
-        if (tid < B && tid < total - b * B) {
+        if (tid < total - b * B) {
             const uint32_t gid = gids[s0 + b * B + tid];
             bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
         }
     }
 
-    float acc = 0.f;
+    float acc0 = 0.f, acc1 = 0.f;
     uint16_t *mylist = lists + warp * B;
     int b = 0;
     for (; b < nb; ++b) {
@@ -115,7 +114,7 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
         // -q'(p) for p = tile centre + (lx, ly) as a polynomial in lx, ly:
         //   dx = lx - ux, dy = ly - uy, u = centre - tile centre,
         //   -q' = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
-        // and the mask of 8x4 warp blocks its footprint rectangle touches.
+        // and the mask of 8x8 warp blocks its footprint rectangle touches.
         if (tid < cnt) {
             const float4 r0 = raw[(buf * B + tid) * 2], r1 = raw[(buf * B + tid) * 2 + 1];
             const float ux = r0.x - xcen, uy = r0.y - ycen;
@@ -137,8 +136,8 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
             if (xhi >= 0.f && xlo <= TW - 1.f && yhi >= 0.f && ylo <= TH - 1.f) {
                 const int bx0 = static_cast<int>(fmaxf(xlo, 0.f)) >> 3;
                 const int bx1 = static_cast<int>(fminf(xhi, TW - 1.f)) >> 3;
-                const int by0 = static_cast<int>(fmaxf(ylo, 0.f)) >> 2;
-                const int by1 = static_cast<int>(fminf(yhi, TH - 1.f)) >> 2;
+                const int by0 = static_cast<int>(fmaxf(ylo, 0.f)) >> 3;
+                const int by1 = static_cast<int>(fminf(yhi, TH - 1.f)) >> 3;
                 const uint32_t row = (2u << bx1) - (1u << bx0);
                 for (int by = by0; by <= by1; ++by) mk |= row << (by * NSX);
             }
@@ -146,7 +145,7 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
         }
         __syncthreads();
         // raw[buf] is consumed: the copies of batch b+2 can land there now
-        if (b + 2 < nb && tid < B && tid < total - (b + 2) * B) {
+        if (b + 2 < nb && tid < total - (b + 2) * B) {
             const uint32_t gid = gids[s0 + (b + 2) * B + tid];
             bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[buf]);
         }
@@ -161,14 +160,16 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
         }
         __syncwarp();
         // ---- accumulate: w * 2^(-q') where q <= q_cut (Eq. 8-9)
-        const float2 *myrow = rowc + pyl * L::RS;
+        const float2 *row0 = rowc + pyl * L::RS, *row1 = row0 + 4 * L::RS;
 #pragma unroll 4
         for (int j = 0; j < m; ++j) {
             const int i = mylist[j];
-            const float2 ab = myrow[i];  // this pixel row's alpha, beta
-            const float2 cw = gcoef[i];  // c3, w
-            const float nq = fmaf(fmaf(cw.x, lx, ab.y), lx, ab.x);
-            if (nq >= ncut) acc = fmaf(cw.y, ex2_approx(nq), acc);
+            const float2 ab0 = row0[i], ab1 = row1[i];  // the two rows' alpha, beta
+            const float2 cw = gcoef[i];                 // c3, w
+            const float nq0 = fmaf(fmaf(cw.x, lx, ab0.y), lx, ab0.x);
+            const float nq1 = fmaf(fmaf(cw.x, lx, ab1.y), lx, ab1.x);
+            if (nq0 >= ncut) acc0 = fmaf(cw.y, ex2_approx(nq0), acc0);
+            if (nq1 >= ncut) acc1 = fmaf(cw.y, ex2_approx(nq1), acc1);
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
         if (abort_flag) break;
@@ -179,7 +180,8 @@ __global__ void __launch_bounds__(TW *TH) render_kernel(
             mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
         return;
     }
-    stile[pyl][pxl] = acc;
+    stile[pyl][pxl] = acc0;
+    stile[pyl + 4][pxl] = acc1;
     __syncthreads();
     float *oq = out + static_cast<size_t>(q) * g.H * g.W;
     const bool vec = (g.W & 3) == 0;
@@ -258,13 +260,13 @@ template <int TW, int TH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        float *out, int *status, cudaStream_t st) {
-    const size_t smem = FwdSmem<TW * TH, TH>::bytes;
+    const size_t smem = FwdSmem<TW * TH / 2, TH>::bytes;
     cudaError_t e = cudaFuncSetAttribute(render_kernel<TW, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     dim3 grid(g.T, Q);
-    render_kernel<TW, TH><<<grid, TW * TH, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
+    render_kernel<TW, TH><<<grid, TW * TH / 2, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
                                                        -g.q_cut * kHalfLog2e, out, status);
     return cudaGetLastError();
 }
