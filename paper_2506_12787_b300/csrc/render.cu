@@ -16,8 +16,9 @@
 // evaluates only those.  Set-up stores, per tile row y, alpha(y) and beta(y)
 // with
 //   -q'(lx, y) = alpha(y) + beta(y) lx + c3 lx^2,
-// so a pixel costs two FMAs, one compare, one ex2 and one FMA, and one list
-// entry and (c3, w) serve both pixels of a thread.
+// the rows y and y + 4 of a thread side by side in one 16-byte entry, so a
+// pixel costs two FMAs, one compare, one ex2 and one FMA, and one list entry,
+// one 16-byte (alpha, beta) load and (c3, w) serve both pixels of a thread.
 // Every pixel adds its contributions in ascending Gaussian id, so a query's
 // spectrum does not depend on the other queries in the launch.  The finished
 // tile goes through shared memory to float4 stores.
@@ -39,8 +40,8 @@ template <int NT, int TH>
 struct FwdSmem {
     static constexpr int B = NT, NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
-    static constexpr size_t rowc = raw + 2 * B * 32;           // [TH][RS] float2 (alpha, beta)
-    static constexpr size_t gc = rowc + TH * RS * 8;           // [B] float2 (c3, w)
+    static constexpr size_t rowc = raw + 2 * B * 32;           // [TH/2][RS] float4, row pairs
+    static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float2 (c3, w)
     static constexpr size_t mask = gc + B * 8;                 // [B] u32, warp blocks touched
     static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
     static constexpr size_t bytes = lists + NW * B * 2;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
     using L = FwdSmem<NT, TH>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
-    float2 *rowc = reinterpret_cast<float2 *>(smem + L::rowc);
+    float4 *rowc = reinterpret_cast<float4 *>(smem + L::rowc);
     float2 *gcoef = reinterpret_cast<float2 *>(smem + L::gc);
     uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
@@ -121,11 +122,15 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
             const float h1 = fmaf(r0.z, ux, r0.w * uy), h2 = fmaf(r0.w, ux, r1.x * uy);
             const float c0 = -fmaf(ux, h1, uy * h2);
             const float c1 = 2.f * h1, c2 = 2.f * h2, c4 = -2.f * r0.w, c5 = -r1.x;
-            // per tile row: -q'(lx) = alpha + beta lx + c3 lx^2
+            // per tile row: -q'(lx) = alpha + beta lx + c3 lx^2; entry p of
+            // the record holds rows y(p) and y(p) + 4, y(p) = 8 (p / 4) + p % 4
 #pragma unroll
-            for (int r = 0; r < TH; ++r) {
-                const float ly = static_cast<float>(r - TH / 2);
-                rowc[r * L::RS + tid] = make_float2(fmaf(fmaf(c5, ly, c2), ly, c0), fmaf(c4, ly, c1));
+            for (int pr = 0; pr < TH / 2; ++pr) {
+                const float ly0 = static_cast<float>((pr >> 2) * 8 + (pr & 3) - TH / 2);
+                const float ly1 = ly0 + 4.f;
+                rowc[pr * L::RS + tid] =
+                    make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(c4, ly0, c1),
+                                fmaf(fmaf(c5, ly1, c2), ly1, c0), fmaf(c4, ly1, c1));
             }
             gcoef[tid] = make_float2(-r0.z, r1.y);
             uint32_t mk = 0;
@@ -155,17 +160,21 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
             const int i = base + lane;
             const bool hit = i < cnt && ((mask[i] >> warp) & 1u);
             const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            if (hit) mylist[m + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i);
+            // entries are byte offsets i * 8 into the (c3, w) array
+            if (hit) mylist[m + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i * 8);
             m += __popc(bal);
         }
         __syncwarp();
         // ---- accumulate: w * 2^(-q') where q <= q_cut (Eq. 8-9)
-        const float2 *row0 = rowc + pyl * L::RS, *row1 = row0 + 4 * L::RS;
+        const char *mypair = reinterpret_cast<const char *>(
+            rowc + ((pyl >> 3) * 4 + (pyl & 3)) * L::RS);
+        const char *gcb = reinterpret_cast<const char *>(gcoef);
 #pragma unroll 4
         for (int j = 0; j < m; ++j) {
-            const int i = mylist[j];
-            const float2 ab0 = row0[i], ab1 = row1[i];  // the two rows' alpha, beta
-            const float2 cw = gcoef[i];                 // c3, w
+            const int o = mylist[j];  // = record index * 8
+            const float4 ab = *reinterpret_cast<const float4 *>(mypair + 2 * o);  // alpha, beta x 2
+            const float2 cw = *reinterpret_cast<const float2 *>(gcb + o);        // c3, w
+            const float2 ab0 = make_float2(ab.x, ab.y), ab1 = make_float2(ab.z, ab.w);
             const float nq0 = fmaf(fmaf(cw.x, lx, ab0.y), lx, ab0.x);
             const float nq1 = fmaf(fmaf(cw.x, lx, ab1.y), lx, ab1.x);
             if (nq0 >= ncut) acc0 = fmaf(cw.y, ex2_approx(nq0), acc0);
