@@ -16,9 +16,11 @@
 // evaluates only those.  Set-up stores, per tile row y, alpha(y) and beta(y)
 // with
 //   -q'(lx, y) = alpha(y) + beta(y) lx + c3 lx^2,
-// the rows y and y + 4 of a thread side by side in one 16-byte entry, so a
-// pixel costs two FMAs, one compare, one ex2 and one FMA, and one list entry,
-// one 16-byte (alpha, beta) load and (c3, w) serve both pixels of a thread.
+// the rows y and y + 4 of a thread side by side in one 16-byte entry
+// (alpha(y), alpha(y+4), beta(y), beta(y+4)), so a pixel costs two FMAs (one
+// two-lane fma.rn.f32x2 each for both pixels), one compare, one ex2 and one
+// FMA, and one list entry, one (alpha, beta) load and one (c3, w) load serve
+// both pixels of a thread.
 // Every pixel adds its contributions in ascending Gaussian id, so a query's
 // spectrum does not depend on the other queries in the launch.  The finished
 // tile goes through shared memory to float4 stores.
@@ -34,6 +36,21 @@ namespace wrf {
 
 namespace {
 
+// d = a * b + c on two FP32 lanes in one instruction (fma.rn.f32x2); each
+// lane rounds exactly like fmaf.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
 // Shared-memory carve-up of the forward kernel for a tile with NT threads
 // (two pixels each) and TH rows: a batch holds B = NT records, one per thread.
 template <int NT, int TH>
@@ -41,14 +58,14 @@ struct FwdSmem {
     static constexpr int B = NT, NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
     static constexpr size_t rowc = raw + 2 * B * 32;           // [TH/2][RS] float4, row pairs
-    static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float2 (c3, w)
-    static constexpr size_t mask = gc + B * 8;                 // [B] u32, warp blocks touched
+    static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float4 (c3, c3, w, 0)
+    static constexpr size_t mask = gc + B * 16;                // [B] u32, warp blocks touched
     static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
     static constexpr size_t bytes = lists + NW * B * 2;
 };
 
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW *TH / 2) render_kernel(
+__global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status) {
@@ -59,7 +76,7 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
     float4 *rowc = reinterpret_cast<float4 *>(smem + L::rowc);
-    float2 *gcoef = reinterpret_cast<float2 *>(smem + L::gc);
+    float4 *gcoef = reinterpret_cast<float4 *>(smem + L::gc);
     uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
     __shared__ __align__(8) uint64_t bar[2];
@@ -129,10 +146,10 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
                 const float ly0 = static_cast<float>((pr >> 2) * 8 + (pr & 3) - TH / 2);
                 const float ly1 = ly0 + 4.f;
                 rowc[pr * L::RS + tid] =
-                    make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(c4, ly0, c1),
-                                fmaf(fmaf(c5, ly1, c2), ly1, c0), fmaf(c4, ly1, c1));
+                    make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
+                                fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[tid] = make_float2(-r0.z, r1.y);
+            gcoef[tid] = make_float4(-r0.z, -r0.z, r1.y, 0.f);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(r0.x, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(r0.x, r1.z)) - static_cast<float>(x0);
@@ -160,8 +177,8 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
             const int i = base + lane;
             const bool hit = i < cnt && ((mask[i] >> warp) & 1u);
             const uint32_t bal = __ballot_sync(0xffffffffu, hit);
-            // entries are byte offsets i * 8 into the (c3, w) array
-            if (hit) mylist[m + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i * 8);
+            // entries are byte offsets i * 16 into the (c3, c3, w, 0) array
+            if (hit) mylist[m + __popc(bal & ((1u << lane) - 1u))] = static_cast<uint16_t>(i * 16);
             m += __popc(bal);
         }
         __syncwarp();
@@ -169,16 +186,16 @@ __global__ void __launch_bounds__(TW *TH / 2) render_kernel(
         const char *mypair = reinterpret_cast<const char *>(
             rowc + ((pyl >> 3) * 4 + (pyl & 3)) * L::RS);
         const char *gcb = reinterpret_cast<const char *>(gcoef);
+        const float2 lx2 = make_float2(lx, lx);
 #pragma unroll 4
         for (int j = 0; j < m; ++j) {
-            const int o = mylist[j];  // = record index * 8
-            const float4 ab = *reinterpret_cast<const float4 *>(mypair + 2 * o);  // alpha, beta x 2
-            const float2 cw = *reinterpret_cast<const float2 *>(gcb + o);        // c3, w
-            const float2 ab0 = make_float2(ab.x, ab.y), ab1 = make_float2(ab.z, ab.w);
-            const float nq0 = fmaf(fmaf(cw.x, lx, ab0.y), lx, ab0.x);
-            const float nq1 = fmaf(fmaf(cw.x, lx, ab1.y), lx, ab1.x);
-            if (nq0 >= ncut) acc0 = fmaf(cw.y, ex2_approx(nq0), acc0);
-            if (nq1 >= ncut) acc1 = fmaf(cw.y, ex2_approx(nq1), acc1);
+            const int o = mylist[j];  // = record index * 16
+            const float4 ab = *reinterpret_cast<const float4 *>(mypair + o);  // alpha x 2, beta x 2
+            const float4 cw = *reinterpret_cast<const float4 *>(gcb + o);    // c3, c3, w, 0
+            const float2 t = fma2(make_float2(cw.x, cw.y), lx2, make_float2(ab.z, ab.w));
+            const float2 nq = fma2(t, lx2, make_float2(ab.x, ab.y));
+            if (nq.x >= ncut) acc0 = fmaf(cw.z, ex2_approx(nq.x), acc0);
+            if (nq.y >= ncut) acc1 = fmaf(cw.z, ex2_approx(nq.y), acc1);
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
         if (abort_flag) break;
