@@ -117,6 +117,9 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
         }
     }
+    // this thread's Gaussian id of batch b + 2, loaded one batch early so the
+    // copy is issued without waiting on the index load
+    uint32_t gnext = tid < total - 2 * B ? gids[s0 + 2 * B + tid] : 0u;
 
     float acc0 = 0.f, acc1 = 0.f;
     uint16_t *mylist = lists + warp * B;
@@ -168,8 +171,8 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         __syncthreads();
         // raw[buf] is consumed: the copies of batch b+2 can land there now
         if (b + 2 < nb && tid < total - (b + 2) * B) {
-            const uint32_t gid = gids[s0 + (b + 2) * B + tid];
-            bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[buf]);
+            bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gnext), 32, &bar[buf]);
+            if (tid < total - (b + 3) * B) gnext = gids[s0 + (b + 3) * B + tid];
         }
         // ---- this warp's list: records touching its block, ascending index
         int m = 0;
