@@ -46,6 +46,11 @@ WORKLOADS = {
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
+# ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, tile_w, tile_h)
+NCU_TRAFFIC = {
+    ("render_kernel", 20000, 256, 90, 360, 32, 8): 263.144192e6 + 28.133632e6,
+    ("mlp_tc_kernel", 20000, 256, 90, 360, 32, 8): 2.128896e6 + 103.981312e6,
+}
 RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
 BIN_BYTES_PER_REC = 32   # each record read once
 BIN_BYTES_PER_KEY = 4    # each Gaussian id written once
@@ -584,7 +589,14 @@ def main():
                 "achieved": nbytes / (stage["bin"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    # one ncu capture of this kernel on this exact workload and tile shape
+    # (profiles/render_batched.txt, profiles/mlp_tc_batched.txt); null for any
+    # other configuration
+    tkey = (roof["kernel"], N, Q, H, W, tw, th)
+    roof["traffic"] = NCU_TRAFFIC.get(tkey)
+    if roof["traffic"] is not None:
+        roof["traffic_unit"] = "bytes per launch (ncu)"
     roof["stage_ms"] = stage
 
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
