@@ -17,6 +17,9 @@ Function -> paper:
   render        Sec. 4.1 Eq. 9, Sec. 4.2 Eq. 13 (order-free truncated sum)
   bin_f32       tile lists, Sec. 4.1 ("spectrum domain partitioned into tiles")
   grad          derivatives of the above (Sec. 4.4 training by back-propagation)
+  rssi          Sec. 7.2 (RSSI head: global average pool of the rendered map) with
+                RSSI as the spectrum magnitude averaged over azimuth and elevation
+                (Sec. 6.6)
 """
 from __future__ import annotations
 
@@ -164,6 +167,16 @@ def forward(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4):
     proj = project(scene, resid, q_cut, Q=tx.shape[0])
     A, slack = render(proj, H, W, q_cut, band)
     return A, slack, proj, resid
+
+
+def rssi(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4):
+    """RSSI head of Sec. 7.2: each query's H x W map (Eq. 9/13) reduced by a
+    global average pool of its magnitude (Sec. 6.6 averages the spectrum
+    magnitude over azimuth and elevation; one real channel, so the magnitude is
+    |A|).  Returns the pooled values [Q] and the pooled cutoff-band slack [Q]:
+    a pooled GPU value is correct within tol + slack."""
+    A, slack, _, _ = forward(scene, mlp, tx, H, W, q_cut, band)
+    return np.abs(A).mean(axis=(1, 2)), slack.mean(axis=(1, 2))
 
 
 def tiles(H: int, W: int, tw: int, th: int):

@@ -369,3 +369,42 @@ def test_stop_grad_mean_drops_only_the_encoding_path():
     assert not np.allclose(g["d_mean"], g["d_mean_direct"])
     for a, b in zip(g["d_W"], gs["d_W"]):
         np.testing.assert_array_equal(a, b)
+
+
+# ---------------------------------------------------------------- rssi ----
+@pytest.mark.parametrize("sigma", [1.5, 2.5])
+def test_rssi_closed_form(sigma):
+    """RSSI head (Sec. 7.2): the pooled map of one untruncated isotropic
+    Gaussian far from the edges is its lattice sum 2 pi sigma^2 w over the
+    H W pixels; with the zero MLP the residuals are exactly 0."""
+    sc = _one(32.0, 31.0, math.log(sigma), o=0.4, amp=0.7)
+    w = 0.7 / (1 + math.exp(-0.4))
+    mlp = synth.zero_mlp()
+    r, slack = oracle.rssi(sc, mlp, synth.make_tx(2, seed=3), 64, 64, math.inf)
+    want = 2 * math.pi * sigma ** 2 * w / (64 * 64)
+    assert r.shape == (2,) and slack.shape == (2,)
+    assert r == pytest.approx([want, want], rel=1e-9)
+
+
+def test_rssi_is_the_mean_magnitude():
+    """Pooling is linear in the amplitudes, adds over disjoint scenes with
+    non-negative maps, and takes the magnitude (Sec. 6.6): negating every
+    amplitude leaves the RSSI unchanged while the map changes sign."""
+    sc = synth.make_scene(40, 16, 16, seed=5)
+    mlp = synth.make_mlp(seed=2, bias_std=0.05)
+    tx = synth.make_tx(3, seed=4)
+    r, _ = oracle.rssi(sc, mlp, tx, 16, 16, 9.0)
+    A, _, _, _ = oracle.forward(sc, mlp, tx, 16, 16, 9.0)
+    assert np.all(r > 0)
+    k = synth.Scene(sc.mean, sc.log_scale, sc.rot, sc.opacity_logit, sc.amp.astype(np.float64) * 2.5)
+    rk, _ = oracle.rssi(k, mlp, tx, 16, 16, 9.0)
+    assert rk == pytest.approx(2.5 * r, rel=1e-12)
+    neg = synth.Scene(sc.mean, sc.log_scale, sc.rot, sc.opacity_logit, -sc.amp.astype(np.float64))
+    An, _, _, _ = oracle.forward(neg, mlp, tx, 16, 16, 9.0)
+    rn, _ = oracle.rssi(neg, mlp, tx, 16, 16, 9.0)
+    assert np.allclose(An, -A, rtol=0, atol=1e-15) and rn == pytest.approx(r, rel=1e-12)
+    s1 = synth.Scene(*(a[:20] for a in sc.arrays()))
+    s2 = synth.Scene(*(a[20:] for a in sc.arrays()))
+    r1, _ = oracle.rssi(s1, mlp, tx, 16, 16, 9.0)
+    r2, _ = oracle.rssi(s2, mlp, tx, 16, 16, 9.0)
+    assert r1 + r2 == pytest.approx(r, rel=1e-12)
