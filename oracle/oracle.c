@@ -184,8 +184,9 @@ static int pixel_range(double centre, double r, int size, int *lo, int *hi)
 
 /* Eq. 9 / 13: A(y, x) = sum_n [q_n <= q_cut] w_n exp(-q_n / 2), summed per
  * pixel in ascending n.  `slack` (optional) receives, per pixel, the sum of
- * w exp(-q/2) over the Gaussians whose q lies within band*q_cut of q_cut,
- * where an FP32 evaluation may legitimately fall on the other side. */
+ * |w| exp(-q/2) over the Gaussians whose q lies within band*q_cut of q_cut,
+ * where an FP32 evaluation may legitimately fall on the other side: a bound
+ * on the magnitude of what either decision adds, whatever the sign of w. */
 int or_render(int Q, int N, const double *proj, int H, int W, double q_cut, double band,
               double *out, double *slack)
 {
@@ -208,7 +209,7 @@ int or_render(int Q, int N, const double *proj, int H, int W, double q_cut, doub
                     double qq = p[2] * dx * dx + 2.0 * p[3] * dx * dy + p[4] * dy * dy;
                     double e = p[5] * exp(-0.5 * qq);
                     if (qq <= q_cut) A[(size_t)y * W + x] += e;
-                    if (S && fabs(qq - q_cut) <= band * q_cut) S[(size_t)y * W + x] += e;
+                    if (S && fabs(qq - q_cut) <= band * q_cut) S[(size_t)y * W + x] += fabs(e);
                 }
         }
     }
