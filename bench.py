@@ -43,6 +43,8 @@ WORKLOADS = {
     "large": (200000, 180, 720, 1024, math.log(2.0), 0.5),
     "plain": (1024, 90, 360, 1, math.log(3.0), 0.3),
     "train": (20000, 90, 360, 64, math.log(3.0), 0.3),
+    # RSSI head (Sec. 7.2): 50 Gaussians, 16 x 16 map, pooled; 4096 TX per step
+    "rssi": (50, 16, 16, 4096, math.log(1.5), 0.3),
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
@@ -231,25 +233,27 @@ def run_reference(args):
     import oracle
     sc, m, tx, shape = make_inputs(args.workload, 0)
     N, H, W, Q = shape
-    S = max(1, min(Q, 4))
+    S = max(1, min(Q, 4 if args.workload != "rssi" else 256))
+    run = oracle.rssi if args.workload == "rssi" else oracle.forward
+    unit = "rssi/s" if args.workload == "rssi" else "spectra/s"
     for i in range(args.warmup):
-        oracle.forward(sc, m, tx[(i * S) % Q:(i * S) % Q + S], H, W, Q_CUT)
+        run(sc, m, tx[(i * S) % Q:(i * S) % Q + S], H, W, Q_CUT)
     t0 = time.perf_counter()
     for i in range(args.steps):
         j = (i * S) % Q
-        oracle.forward(sc, m, tx[j:j + S], H, W, Q_CUT)
+        run(sc, m, tx[j:j + S], H, W, Q_CUT)
     dt = time.perf_counter() - t0
     val = S * args.steps / dt
-    line = {"impl": "reference", "metric": "spectra/s", "value": val, "unit": "spectra/s",
+    line = {"impl": "reference", "metric": unit, "value": val, "unit": unit,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, shape, {"sample": f"{S} of {Q} queries per step"}),
-            "cpu_baseline": {"value": val, "unit": "spectra/s", "cores": oracle.num_threads(),
+            "cpu_baseline": {"value": val, "unit": unit, "cores": oracle.num_threads(),
                              "kind": "oracle",
                              "sample": f"{S} of {Q} TX queries per step, {N} Gaussians, "
                                        f"{W}x{H}, FP64 C oracle (OpenMP)"},
-            "e2e": {"value": val, "unit": "spectra/s", "h2d_bytes_per_step": 0,
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -440,10 +444,153 @@ def run_train(args):
     return 0
 
 
+def run_rssi(args):
+    """RSSI head (Sec. 7.2): 50 Gaussians, 16 x 16 map, global average pool,
+    FP32 MLP, fused one-CTA-per-query kernel.  value = RSSI values per second
+    at 4096 TX per step (CUDA graph); also the latency of one query."""
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_12787_b300 import api
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, m, tx_np, shape = make_inputs("rssi", rank)
+    N, H, W, Q = shape
+    grid = api.make_grid(H, W, 16, 16, Q_CUT)
+    ds, dm = api.DeviceScene.from_host(sc, dev), api.DeviceMLP.from_host(m, dev, precision=api.WRF_FP32)
+    L = __import__("paper_2506_12787_b300._lib", fromlist=["load"]).load()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def make(q):
+        tx = torch.as_tensor(tx_np[:q], device=dev)
+        out = torch.empty(q, dtype=torch.float32, device=dev)
+        need = L.wrf_deform_workspace_size(N, q, C.byref(dm.c()))
+        wsb = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)  # 512-B aligned blocks
+        with torch.cuda.stream(stream):
+            api.wrf_rssi(ds, dm, grid, tx, rssi=out, ws=wsb, stream=stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            api.wrf_rssi(ds, dm, grid, tx, rssi=out, ws=wsb, stream=stream)
+        return g, tx, out, wsb
+
+    g, tx, out, wsb = make(Q)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            g.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            g.replay()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_max, _, value = aggregate(sum(step_ms) / 1e3, Q * K, dist if ws > 1 else None)
+    # latency of one query (graph of prep + fused kernel), L2 warm
+    g1, _, _, _ = make(1)
+    lat = []
+    with torch.cuda.stream(stream):
+        for _ in range(20):
+            g1.replay()
+        for _ in range(200):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g1.replay()
+            b.record(stream)
+            b.synchronize()
+            lat.append(a.elapsed_time(b) * 1e3)
+    lat.sort()
+    # end to end: pinned host TX in, pinned host RSSI out, every step
+    hx = torch.as_tensor(tx_np, dtype=torch.float32).pin_memory()
+    hout = torch.empty(Q, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for i in range(K):
+            tx.copy_(hx, non_blocking=True)
+            g.replay()
+            hout.copy_(out, non_blocking=True)
+        e1.record(stream)
+    e1.synchronize()
+    _, _, e2e_val = aggregate(e0.elapsed_time(e1) / 1e3, Q * K, dist if ws > 1 else None)
+    # roofline: FP32 work per query (factorised layer 1 add, hidden layers,
+    # output layer, every pixel x Gaussian at 12 FLOP) over the step time
+    peaks, _ = measured_peaks()
+    nh = len(m.W) - 2
+    fl_q = N * (128 + nh * 2 * 128 * 128 + 2 * 128 * 5) + H * W * N * 12
+    fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    t_step = statistics.median(step_ms) * 1e-3
+    roof = {"kernel": "rssi_kernel (+ PE / weight prep)", "bound": "alu",
+            "achieved": Q * fl_q / t_step / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+            "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
+            "flop_per_query": fl_q, "traffic": None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": "rssi/s", "value": value, "unit": "rssi/s", "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rssi: {N} Gaussians, {W}x{H} map, global average pool, "
+                                   f"{Q} TX per step (Sec. 7.2)", "gaussians": N, "H": H, "W": W,
+                       "queries_per_step": Q, "mlp": "89-128x4-5 ReLU, FP32 CUDA cores",
+                       "q_cut": Q_CUT, "cuda_graph": True,
+                       "l2": "256 MB buffer rewritten between timed steps",
+                       "parallelism": f"replicas x{args.gpus}"},
+            "clocks": clk,
+            "latency_one_query_us": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * len(lat))],
+                                     "what": "graph replay of wrf_rssi for Q = 1, events on the "
+                                             "stream, L2 warm"},
+            "e2e": {"value": e2e_val, "unit": "rssi/s", "h2d_bytes_per_step": 12 * Q,
+                    "d2h_bytes_per_step": 4 * Q,
+                    "api": "api.wrf_rssi graph with pinned host TX in and pinned host RSSI out"},
+            "roofline": roof,
+            "gpu_launches": K * 4}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.rssi(sc, m, tx_np[:64], H, W, Q_CUT)
+        t1 = (time.perf_counter() - t0) / 64
+        S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-6)))))
+        t0 = time.perf_counter()
+        oracle.rssi(sc, m, tx_np[:S], H, W, Q_CUT)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S / dt, "unit": "rssi/s", "cores": oracle.num_threads(),
+                                "kind": "oracle",
+                                "sample": f"first {S} of {Q} TX queries, {N} Gaussians, {W}x{H}, "
+                                          f"FP64 C oracle (OpenMP), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "rssi" and args.impl != "reference":
+        return run_rssi(args)
     if args.workload == "train":
         return run_train(args)
     import torch

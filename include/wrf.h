@@ -183,6 +183,27 @@ wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *ti
                       const int64_t *n_keys, int64_t key_capacity, int32_t n, int32_t Q,
                       const wrf_grid *grid, float *spectra, void *stream);
 
+/* RSSI head (Sec. 7.2): for each query the map of wrf_deform_project +
+ * wrf_render, reduced by a global average pool of its magnitude,
+ *   rssi[q] = (1 / (H W)) sum_pixels |A_q(pixel)|
+ * (Sec. 6.6 defines RSSI as the spectrum magnitude averaged over azimuth and
+ * elevation).  The paper's setting is 50 Gaussians on a 16 x 16 map, a
+ * latency-bound size, so the whole path runs fused, one CTA per query, with
+ * the MLP in FP32 (mlp->precision is ignored) and every pixel tested against
+ * every Gaussian (the tile fields of grid are ignored).
+ *   scene  n <= 64 Gaussians (WRF_EUNSUPPORTED above).
+ *   grid   H W <= 65536 pixels, q_cut as for wrf_render.
+ *   tx     [Q][3] device, TX positions in metres.
+ *   rssi   [Q] device output.
+ *   map    [Q][H][W] device output of the un-pooled map, or NULL.
+ *   ws     workspace of wrf_deform_workspace_size(n, Q, mlp) bytes, 256-byte
+ *          aligned (the factorised layer-1 terms and FP32 weight images).
+ * n == 0 gives rssi = 0.  Pooling sums in a fixed order, so a query's value
+ * does not depend on the other queries of the call.                        */
+wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                    const float *tx, int32_t Q, float *rssi, float *map, void *ws,
+                    size_t ws_bytes, void *stream);
+
 /* Backward of wrf_render: from dL/dA [Q][H][W] to d_rec [Q][N][6] =
  * dL/d(mx, my, A, B, C, w) where (A, B, C) is the unscaled inverse
  * covariance (Eq. 8).  Per-pixel weights are recomputed from the records

@@ -25,7 +25,7 @@ EXPORTS = (
     "wrf_deform_workspace_size", "wrf_deform", "wrf_project", "wrf_deform_project",
     "wrf_bin_workspace_size", "wrf_bin", "wrf_bin_noalloc", "wrf_render", "wrf_render_backward",
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
-    "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait",
+    "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
 )
 
 
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
         "wrf_last_error": (C.c_char_p, []),
         "wrf_version": (I32, []),
         "wrf_selftest_wait": (I32, [I64, P, P]),
+        "wrf_rssi": (I32, [sp, mp, gp, P, I32, P, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

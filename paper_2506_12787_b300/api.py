@@ -156,6 +156,22 @@ def wrf_deform_project(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rec=None, t
     return rec, tile_count
 
 
+def wrf_rssi(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rssi=None, map_out=None, ws=None,
+             stream=None):
+    """RSSI head (Sec. 7.2): pooled map magnitude per query, rssi [Q]; the
+    un-pooled maps go to map_out [Q,H,W] when it is given."""
+    L = _lib.load()
+    Q, dev = int(tx.shape[0]), tx.device
+    mc = mlp.c()
+    if rssi is None:
+        rssi = torch.empty(Q, dtype=torch.float32, device=dev)
+    need = L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_rssi(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q, _p(rssi),
+                          _p(map_out), _p(ws), ws.numel(), _stream(stream)))
+    return rssi
+
+
 def wrf_bin(rec, n: int, Q: int, grid, key_capacity: int, gids=None, n_keys=None, offsets=None,
             ws=None, stream=None):
     """Tile lists: gids [cap] (uint32 stored as int32), n_keys [1] int64, offsets [Q*T+1]."""

@@ -252,6 +252,45 @@ wrf_status wrf_deform_project(const wrf_scene *scene, const wrf_mlp *mlp, const 
                          stream);
 }
 
+wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                    const float *tx, int32_t Q, float *rssi, float *map, void *ws,
+                    size_t ws_bytes, void *stream) {
+    wrf_status s;
+    wrf::MlpView m{};
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if ((s = check_mlp(mlp, &m)) != WRF_OK) return s;
+    if (!grid) return fail(WRF_EINVAL, "grid is NULL");
+    if (grid->H < 1 || grid->W < 1 ||
+        static_cast<long long>(grid->H) * grid->W > wrf::kRssiMaxPixels)
+        return fail(WRF_EUNSUPPORTED, "RSSI head: H*W must be in [1, %d]", wrf::kRssiMaxPixels);
+    if (!(grid->q_cut > 0.f)) return fail(WRF_EINVAL, "q_cut must be > 0 (or +inf)");
+    if (scene->n > wrf::kRssiMaxN)
+        return fail(WRF_EUNSUPPORTED, "RSSI head: at most %d Gaussians", wrf::kRssiMaxN);
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (Q > 0 && (!tx || !rssi)) return fail(WRF_EINVAL, "tx / rssi is NULL");
+    size_t need = wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    if (Q == 0) return WRF_OK;
+    wrf::GridView g{};
+    g.H = grid->H;
+    g.W = grid->W;
+    g.tw = g.th = 16;
+    g.ntx = (g.W + 15) / 16;
+    g.nty = (g.H + 15) / 16;
+    g.T = g.ntx * g.nty;
+    g.q_cut = grid->q_cut;
+    wrf::DeformWs w{};
+    wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, &w, static_cast<char *>(ws));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wrf::SceneView sv = view(scene);
+    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, false, st);
+    if (e != cudaSuccess) return cuda_fail(e, "prep");
+    e = wrf::launch_rssi(sv, m, g, Q, w, rssi, map, st);
+    if (e != cudaSuccess) return cuda_fail(e, "rssi");
+    return WRF_OK;
+}
+
 wrf_status wrf_project(const wrf_scene *scene, const float *resid, int32_t Q,
                        const wrf_grid *grid, float *rec, uint32_t *tile_count, void *stream) {
     wrf_status s;

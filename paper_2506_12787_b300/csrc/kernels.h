@@ -62,6 +62,13 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
 cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
                            float4 *rec, uint32_t *count, cudaStream_t st);
 
+// RSSI head: one CTA per query, whole path fused (rssi.cu); U, V and the
+// FP32 weight images come from launch_prep(..., want_bf16 = false).
+constexpr int kRssiMaxN = 64;
+constexpr int kRssiMaxPixels = 65536;
+cudaError_t launch_rssi(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                        const DeformWs &ws, float *rssi, float *map, cudaStream_t st);
+
 // Binning.
 struct BinWs {
     uint32_t *chunk_counts;  // [Q][T][C]
