@@ -6,10 +6,14 @@
 // In this tiny-N regime the whole path is latency-bound, so one CTA per query
 // runs every step in one launch, with nothing in HBM between them:
 //   1. layer 1 from the factorised terms U[n] + V[q] (prep.cu, FP32), ReLU;
-//   2. hidden layers in FP32 on the CUDA cores: thread (j, half) owns output
-//      column j of the rows n = half, half + 2, ...; weights stream from the
-//      transposed FP32 image (coalesced over j, L1/L2 resident), activations
-//      are read from shared memory as broadcasts;
+//   2. hidden layers in FP32 on the CUDA cores as a register-tiled product:
+//      the scene's rows are padded to 64, activations are kept transposed
+//      ([input k][row]) in shared memory, and thread t owns the 4 x 8 output
+//      tile rows 4 (t % 16) .. +3, columns 8 (t / 16) .. +7, so each input k
+//      costs one 16-byte activation load and two 16-byte weight loads for 32
+//      independent FMAs; the layer's transposed FP32 weights are staged into
+//      shared memory 64 inputs (32 KB) at a time with coalesced 16-byte loads.
+//      Each output still sums bias + w_k h_k in ascending k;
 //   3. the output layer and the deform + project step (Eq. 12-13) per
 //      Gaussian, records kept in shared memory;
 //   4. every pixel against every Gaussian in ascending id with the q <= q_cut
@@ -24,6 +28,9 @@ namespace wrf {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kKChunk = 64;  // weight rows (inputs) staged per pass: 32 KB
+constexpr int kRows = kRssiMaxN;       // rows padded to 64
+constexpr int kPitch = kRows + 4;      // floats per input of the transposed activations
 
 struct RssiArgs {
     SceneView s;
@@ -39,52 +46,77 @@ struct RssiArgs {
 };
 
 __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
-    extern __shared__ float hbuf[];  // [2][N][128] activations
+    // [kKChunk][128] staged weights, then two [128][kPitch] transposed activations
+    extern __shared__ __align__(16) float smem[];
+    float *wbuf = smem;
+    float *hin = smem + kKChunk * WRF_HIDDEN, *hout = hin + WRF_HIDDEN * kPitch;
     __shared__ float4 recs[kRssiMaxN][2];
     __shared__ float dout[kRssiMaxN][8];
     __shared__ float red[kThreads];
     const int q = blockIdx.x, tid = threadIdx.x, N = a.s.n;
-    float *hin = hbuf, *hout = hbuf + N * WRF_HIDDEN;
 
-    // 1. layer 1: relu(U[n] + V[q])
+    // 1. layer 1: h[r][j] = relu(U[r][j] + V[q][j]), stored as hin[j][r]
+    //    (rows >= N are zero; loads unrolled so they are in flight together)
     const float *vq = a.V + static_cast<size_t>(q) * WRF_HIDDEN;
-    for (int e = tid; e < N * WRF_HIDDEN; e += kThreads)
-        hin[e] = fmaxf(a.U[e] + vq[e & (WRF_HIDDEN - 1)], 0.f);
-    // 2. hidden layers
-    const int j = tid & (WRF_HIDDEN - 1), half = tid >> 7;
+    const float vj = vq[tid & (WRF_HIDDEN - 1)];
+#pragma unroll
+    for (int c = 0; c < kRows * WRF_HIDDEN / kThreads; ++c) {
+        const int e = tid + c * kThreads, r = e >> 7, j = e & (WRF_HIDDEN - 1);
+        hin[j * kPitch + r] = r < N ? fmaxf(__ldg(a.U + e) + vj, 0.f) : 0.f;
+    }
+    // 2. hidden layers: thread tile rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7
+    const int rg = tid & 15, cg = tid >> 4;
     for (int l = 0; l < a.nh; ++l) {
-        __syncthreads();
-        const float bj = a.m.bh[l][j];
-        float acc[kRssiMaxN / 2];
+        float acc[4][8];
 #pragma unroll
-        for (int i = 0; i < kRssiMaxN / 2; ++i) acc[i] = bj;
-        const float *w = a.wt + static_cast<size_t>(l) * WRF_HIDDEN * WRF_HIDDEN + j;
-#pragma unroll 2
-        for (int k = 0; k < WRF_HIDDEN; ++k) {
-            const float wk = __ldg(w + k * WRF_HIDDEN);
+        for (int c = 0; c < 8; ++c) {
+            const float b = a.m.bh[l][8 * cg + c];
 #pragma unroll
-            for (int i = 0; i < kRssiMaxN / 2; ++i) {
-                const int r = 2 * i + half;
-                if (r < N) acc[i] = fmaf(wk, hin[r * WRF_HIDDEN + k], acc[i]);
+            for (int r = 0; r < 4; ++r) acc[r][c] = b;
+        }
+        const float4 *wl = reinterpret_cast<const float4 *>(
+            a.wt + static_cast<size_t>(l) * WRF_HIDDEN * WRF_HIDDEN);
+        for (int k0 = 0; k0 < WRF_HIDDEN; k0 += kKChunk) {
+            __syncthreads();  // the previous chunk (or layer's outputs) is done with
+#pragma unroll
+            for (int c = 0; c < kKChunk * WRF_HIDDEN / 4 / kThreads; ++c) {
+                const int i = tid + c * kThreads;
+                reinterpret_cast<float4 *>(wbuf)[i] = __ldg(wl + k0 * (WRF_HIDDEN / 4) + i);
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int k = 0; k < kKChunk; ++k) {
+                const float4 hv = *reinterpret_cast<const float4 *>(hin + (k0 + k) * kPitch + 4 * rg);
+                const float4 wa = *reinterpret_cast<const float4 *>(wbuf + k * WRF_HIDDEN + 8 * cg);
+                const float4 wb = *reinterpret_cast<const float4 *>(wbuf + k * WRF_HIDDEN + 8 * cg + 4);
+                const float h[4] = {hv.x, hv.y, hv.z, hv.w};
+                const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(w[c], h[r], acc[r][c]);
             }
         }
 #pragma unroll
-        for (int i = 0; i < kRssiMaxN / 2; ++i) {
-            const int r = 2 * i + half;
-            if (r < N) hout[r * WRF_HIDDEN + j] = fmaxf(acc[i], 0.f);
-        }
+        for (int c = 0; c < 8; ++c)
+            *reinterpret_cast<float4 *>(hout + (8 * cg + c) * kPitch + 4 * rg) =
+                make_float4(fmaxf(acc[0][c], 0.f), fmaxf(acc[1][c], 0.f), fmaxf(acc[2][c], 0.f),
+                            fmaxf(acc[3][c], 0.f));
         float *t = hin;
         hin = hout;
         hout = t;
     }
     __syncthreads();
-    // 3. output layer (5 residuals per Gaussian), then deform + project
+    // 3. output layer (5 residuals per Gaussian; its 4 KB transposed weights
+    //    staged in shared memory first), then deform + project
+    for (int i = tid; i < WRF_HIDDEN * 8 / 4; i += kThreads)
+        reinterpret_cast<float4 *>(wbuf)[i] = __ldg(reinterpret_cast<const float4 *>(a.wo) + i);
+    __syncthreads();
     for (int e = tid; e < N * 8; e += kThreads) {
         const int r = e >> 3, o = e & 7;
         if (o < WRF_OUT) {
             float acc = a.m.bo[o];
-            const float *h = hin + r * WRF_HIDDEN;
-            for (int k = 0; k < WRF_HIDDEN; ++k) acc = fmaf(__ldg(a.wo + k * 8 + o), h[k], acc);
+            for (int k = 0; k < WRF_HIDDEN; ++k) acc = fmaf(wbuf[k * 8 + o], hin[k * kPitch + r], acc);
             dout[r][o] = acc;
         }
     }
@@ -142,7 +174,7 @@ cudaError_t launch_rssi(const SceneView &s, const MlpView &m, const GridView &g,
     a.nh = m.n_layers - 2;
     a.rssi = rssi;
     a.map = map;
-    const size_t smem = static_cast<size_t>(2) * (s.n > 0 ? s.n : 1) * WRF_HIDDEN * 4;
+    const size_t smem = (static_cast<size_t>(kKChunk) * WRF_HIDDEN + 2 * WRF_HIDDEN * kPitch) * 4;
     cudaError_t e = cudaFuncSetAttribute(rssi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
