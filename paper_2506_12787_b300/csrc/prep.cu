@@ -62,16 +62,20 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
         }
         return;
     }
+    // thread j: 32 independent row sums, each over k in ascending order
     const int j = threadIdx.x;
     const float *wrow = m.W0 + static_cast<size_t>(j) * din;
-    float w[kMaxPe];
-#pragma unroll 4
-    for (int k = 0; k < m.dm; ++k) w[k] = wrow[k];
-    for (int r = 0; r < 32 && n0 + r < s.n; ++r) {
-        float acc = 0.f;
-        for (int k = 0; k < m.dm; ++k) acc = fmaf(w[k], gam[r][k], acc);
-        U[static_cast<size_t>(n0 + r) * WRF_HIDDEN + j] = acc;
+    float acc[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+    for (int k = 0; k < m.dm; ++k) {
+        const float w = __ldg(wrow + k);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) acc[r] = fmaf(w, gam[r][k], acc[r]);
     }
+#pragma unroll
+    for (int r = 0; r < 32; ++r)
+        if (n0 + r < s.n) U[static_cast<size_t>(n0 + r) * WRF_HIDDEN + j] = acc[r];
 }
 
 // V[q][j] for 4 queries per block: the 4 x dt features of Eq. 15 are

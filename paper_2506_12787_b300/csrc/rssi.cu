@@ -64,8 +64,19 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
         const int e = tid + c * kThreads, r = e >> 7, j = e & (WRF_HIDDEN - 1);
         hin[j * kPitch + r] = r < N ? fmaxf(__ldg(a.U + e) + vj, 0.f) : 0.f;
     }
-    // 2. hidden layers: thread tile rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7
+    // 2. hidden layers: thread tile rows 4 rg .. 4 rg + 3, columns 8 cg .. 8 cg + 7;
+    //    the next 32 KB weight chunk is loaded into registers while the
+    //    current one is used
     const int rg = tid & 15, cg = tid >> 4;
+    constexpr int kPer = kKChunk * WRF_HIDDEN / 4 / kThreads;  // float4 per thread per chunk
+    float4 pre[kPer];
+    auto load_chunk = [&](int l, int k0) {
+        const float4 *src = reinterpret_cast<const float4 *>(
+            a.wt + static_cast<size_t>(l) * WRF_HIDDEN * WRF_HIDDEN) + k0 * (WRF_HIDDEN / 4);
+#pragma unroll
+        for (int c = 0; c < kPer; ++c) pre[c] = __ldg(src + tid + c * kThreads);
+    };
+    if (a.nh > 0) load_chunk(0, 0);
     for (int l = 0; l < a.nh; ++l) {
         float acc[4][8];
 #pragma unroll
@@ -74,16 +85,16 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[r][c] = b;
         }
-        const float4 *wl = reinterpret_cast<const float4 *>(
-            a.wt + static_cast<size_t>(l) * WRF_HIDDEN * WRF_HIDDEN);
         for (int k0 = 0; k0 < WRF_HIDDEN; k0 += kKChunk) {
             __syncthreads();  // the previous chunk (or layer's outputs) is done with
 #pragma unroll
-            for (int c = 0; c < kKChunk * WRF_HIDDEN / 4 / kThreads; ++c) {
-                const int i = tid + c * kThreads;
-                reinterpret_cast<float4 *>(wbuf)[i] = __ldg(wl + k0 * (WRF_HIDDEN / 4) + i);
-            }
+            for (int c = 0; c < kPer; ++c)
+                reinterpret_cast<float4 *>(wbuf)[tid + c * kThreads] = pre[c];
             __syncthreads();
+            if (k0 + kKChunk < WRF_HIDDEN)
+                load_chunk(l, k0 + kKChunk);
+            else if (l + 1 < a.nh)
+                load_chunk(l + 1, 0);
 #pragma unroll 4
             for (int k = 0; k < kKChunk; ++k) {
                 const float4 hv = *reinterpret_cast<const float4 *>(hin + (k0 + k) * kPitch + 4 * rg);
