@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
     float acc[32];
 #pragma unroll
     for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+#pragma unroll 8
     for (int k = 0; k < m.dm; ++k) {
         const float w = __ldg(wrow + k);
 #pragma unroll
@@ -107,6 +108,7 @@ __global__ void __launch_bounds__(128) pe_tx_kernel(MlpView m, const float *tx, 
     float acc[kTxPerBlock];
 #pragma unroll
     for (int r = 0; r < kTxPerBlock; ++r) acc[r] = 0.f;
+    #pragma unroll 16
     for (int k = 0; k < m.dt; ++k) {
         const float w = wrow[k];
 #pragma unroll
