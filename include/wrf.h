@@ -183,6 +183,42 @@ wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *ti
                       const int64_t *n_keys, int64_t key_capacity, int32_t n, int32_t Q,
                       const wrf_grid *grid, float *spectra, void *stream);
 
+/* Training loss of Sec. 4.4, Eq. 16, over a batch of Q maps:
+ *   L = lambda1 mean|pred - target| + (1 - lambda1) (1 - mean_q SSIM(pred_q, target_q)),
+ * the SSIM index in its standard form (local means, variances and covariance
+ * under an 11 x 11 Gaussian window with sigma 1.5 and weights summing to 1,
+ * zero outside the map; C1 = 0.01^2, C2 = 0.03^2, i.e. data range 1; the
+ * per-pixel index averaged over the map).  The paper uses lambda1 = 0.7.
+ *   pred, target  [Q][H][W] device FP32.
+ *   out           [1 + Q] device output: L, then SSIM of each map.
+ *   d_pred        [Q][H][W] device output dL/dpred (sign(0) = 0 for the L1
+ *                 term), or NULL to compute the loss only.
+ *   ws            wrf_loss_workspace_size(Q, H, W) bytes, 256-byte aligned.
+ * Sums run in a fixed order: results do not vary from run to run.          */
+size_t wrf_loss_workspace_size(int32_t Q, int32_t H, int32_t W);
+wrf_status wrf_loss(const float *pred, const float *target, int32_t Q, int32_t H, int32_t W,
+                    float lambda1, float *out, float *d_pred, void *ws, size_t ws_bytes,
+                    void *stream);
+
+/* One Adam step (Kingma & Ba; the paper trains with PyTorch's Adam, learning
+ * rates in its Table I: 1e-2 for the Gaussians, 8e-3 for the MLP) over up to
+ * 32 parameter tensors in one launch:
+ *   m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *   param -= lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * groups is a host array; every pointer in it is a device FP32 array of n
+ * elements, m and v the caller's optimizer state (zero before step 1).
+ * step >= 1.                                                               */
+typedef struct {
+    float *param;
+    const float *grad;
+    float *m;
+    float *v;
+    int64_t n;
+    float lr;
+} wrf_adam_group;
+wrf_status wrf_adam(const wrf_adam_group *groups, int32_t n_groups, int32_t step, float beta1,
+                    float beta2, float eps, void *stream);
+
 /* RSSI head (Sec. 7.2): for each query the map of wrf_deform_project +
  * wrf_render, reduced by a global average pool of its magnitude,
  *   rssi[q] = (1 / (H W)) sum_pixels |A_q(pixel)|

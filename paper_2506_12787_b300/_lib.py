@@ -26,6 +26,7 @@ EXPORTS = (
     "wrf_bin_workspace_size", "wrf_bin", "wrf_bin_noalloc", "wrf_render", "wrf_render_backward",
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
+    "wrf_loss_workspace_size", "wrf_loss", "wrf_adam",
 )
 
 
@@ -46,6 +47,11 @@ class Mlp(C.Structure):
                 ("W", C.c_void_p * MAX_LAYERS), ("b", C.c_void_p * MAX_LAYERS),
                 ("L_mean", C.c_int32), ("L_tx", C.c_int32), ("room_min", C.c_float * 3),
                 ("room_size", C.c_float * 3), ("precision", C.c_int32)]
+
+
+class AdamGroup(C.Structure):
+    _fields_ = [("param", C.c_void_p), ("grad", C.c_void_p), ("m", C.c_void_p),
+                ("v", C.c_void_p), ("n", C.c_int64), ("lr", C.c_float)]
 
 
 class Grid(C.Structure):
@@ -85,6 +91,9 @@ def load(path: str = LIB_PATH):
         "wrf_version": (I32, []),
         "wrf_selftest_wait": (I32, [I64, P, P]),
         "wrf_rssi": (I32, [sp, mp, gp, P, I32, P, P, P, S, P]),
+        "wrf_loss_workspace_size": (S, [I32, I32, I32]),
+        "wrf_loss": (I32, [P, P, I32, I32, I32, F, P, P, P, S, P]),
+        "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

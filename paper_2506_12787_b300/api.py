@@ -20,7 +20,7 @@ from ._lib import WRF_BF16, WRF_FP32, WrfError
 __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
-           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16"]
+           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam"]
 
 
 def _p(t):
@@ -154,6 +154,37 @@ def wrf_deform_project(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rec=None, t
     _lib.check(L.wrf_deform_project(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
                                     _p(rec), _p(tile_count), _p(ws), ws.numel(), _stream(stream)))
     return rec, tile_count
+
+
+def wrf_loss(pred, target, lambda1: float = 0.7, want_grad: bool = True, out=None, d_pred=None,
+             ws=None, stream=None):
+    """Eq. 16 loss over a batch of maps [Q,H,W]: out [1+Q] = (L, SSIM_q...) and,
+    if want_grad, d_pred = dL/dpred [Q,H,W]."""
+    L = _lib.load()
+    Q, H, W = (int(v) for v in pred.shape)
+    dev = pred.device
+    if out is None:
+        out = torch.empty(1 + Q, dtype=torch.float32, device=dev)
+    if want_grad and d_pred is None:
+        d_pred = torch.empty_like(pred)
+    ws = _ws(L.wrf_loss_workspace_size(Q, H, W), dev) if ws is None else ws
+    _lib.check(L.wrf_loss(_p(pred), _p(target), Q, H, W, float(lambda1), _p(out),
+                          _p(d_pred) if want_grad else None, _p(ws), ws.numel(), _stream(stream)))
+    return out, (d_pred if want_grad else None)
+
+
+def wrf_adam(groups, step: int, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+             stream=None):
+    """One Adam step; groups = [(param, grad, m, v, lr), ...] of contiguous FP32
+    device tensors (m, v: optimizer state, zero before step 1)."""
+    L = _lib.load()
+    arr = (_lib.AdamGroup * len(groups))()
+    for i, (p, g, m, v, lr) in enumerate(groups):
+        for t in (p, g, m, v):
+            assert t.is_contiguous() and t.dtype == torch.float32 and t.numel() == p.numel()
+        arr[i] = _lib.AdamGroup(_p(p), _p(g), _p(m), _p(v), p.numel(), float(lr))
+    _lib.check(L.wrf_adam(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
+                          _stream(stream)))
 
 
 def wrf_rssi(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rssi=None, map_out=None, ws=None,

@@ -40,10 +40,12 @@ class SpectrumFunction(torch.autograd.Function):
         scene = api.DeviceScene(mean.detach().contiguous(), log_scale.detach().contiguous(),
                                 rot.detach().contiguous(), opacity_logit.detach().contiguous(),
                                 amp.detach().contiguous())
-        W = [p.detach().contiguous() for p in params[0::2]]
-        b = [p.detach().contiguous() for p in params[1::2]]
-        mlp = api.DeviceMLP(W, b, cfg.L_mean, cfg.L_tx, tuple(cfg.room_min),
-                            tuple(cfg.room_size), api.WRF_FP32)
+        mlp = None  # no MLP parameters: the reference frame G^0 for every query
+        if params:
+            W = [p.detach().contiguous() for p in params[0::2]]
+            b = [p.detach().contiguous() for p in params[1::2]]
+            mlp = api.DeviceMLP(W, b, cfg.L_mean, cfg.L_tx, tuple(cfg.room_min),
+                                tuple(cfg.room_size), api.WRF_FP32)
         if cfg.renderer is None:
             cfg.renderer = api.Renderer(cfg.grid, dev, fused=False)
         r = cfg.renderer
@@ -53,7 +55,8 @@ class SpectrumFunction(torch.autograd.Function):
         ctx.cfg, ctx.scene, ctx.mlp, ctx.tx = cfg, scene, mlp, txc
         ctx.saved = dict(rec=last["rec"].clone(), gids=last["gids"].clone(),
                          offs=last["offs"].clone(), n_keys=last["n_keys"].clone(),
-                         resid=last["resid"].clone(), cap=r.cap)
+                         resid=last["resid"].clone() if last["resid"] is not None else None,
+                         cap=r.cap)
         ctx.n_params = len(params)
         return out
 
@@ -64,6 +67,9 @@ class SpectrumFunction(torch.autograd.Function):
         d_rec = api.wrf_render_backward(sv["rec"], sv["gids"], sv["offs"], sv["n_keys"],
                                         sv["cap"], N, Q, cfg.grid, dA.contiguous())
         g = api.wrf_project_backward(scene, sv["resid"], Q, d_rec)
+        if mlp is None:
+            return (None, None, g["d_mean"], g["d_log_scale"], g["d_rot"], g["d_opacity"],
+                    g["d_amp"])
         dW, db, d_mean = api.wrf_deform_backward(scene, mlp, cfg.grid, ctx.tx, g["d_resid"],
                                                  d_mean=g["d_mean"],
                                                  stop_grad_mean=cfg.stop_grad_mean)
@@ -75,5 +81,29 @@ class SpectrumFunction(torch.autograd.Function):
 
 def render_spectra(cfg: SpectrumConfig, tx, mean, log_scale, rot, opacity_logit, amp, params):
     """Spectra [Q,H,W] for TX positions tx [Q,3], differentiable in the
-    Gaussians and the MLP parameters (params = [W0, b0, W1, b1, ...])."""
+    Gaussians and the MLP parameters (params = [W0, b0, W1, b1, ...]; an empty
+    list renders the reference frame without deformation)."""
     return SpectrumFunction.apply(cfg, tx, mean, log_scale, rot, opacity_logit, amp, *params)
+
+
+class SpectrumLossFunction(torch.autograd.Function):
+    """Eq. 16: lambda_1 mean|pred - target| + (1 - lambda_1) (1 - mean SSIM),
+    value and gradient from wrf_loss in one call."""
+
+    @staticmethod
+    def forward(ctx, pred, target, lambda1):
+        out, d = api.wrf_loss(pred.detach().contiguous(), target.detach().contiguous(), lambda1,
+                              want_grad=pred.requires_grad)
+        ctx.save_for_backward(d if d is not None else out)
+        ctx.has_grad = d is not None
+        return out[0]
+
+    @staticmethod
+    def backward(ctx, gL):
+        (d,) = ctx.saved_tensors
+        return (gL * d if ctx.has_grad else None), None, None
+
+
+def spectrum_loss(pred, target, lambda1: float = 0.7):
+    """Eq. 16 loss of a batch of spectra [Q,H,W] (differentiable in pred)."""
+    return SpectrumLossFunction.apply(pred, target, lambda1)

@@ -252,6 +252,50 @@ wrf_status wrf_deform_project(const wrf_scene *scene, const wrf_mlp *mlp, const 
                          stream);
 }
 
+size_t wrf_loss_workspace_size(int32_t Q, int32_t H, int32_t W) {
+    if (Q < 0 || H < 1 || W < 1) return 0;
+    return wrf::loss_ws_layout(Q, H, W, nullptr, nullptr);
+}
+
+wrf_status wrf_loss(const float *pred, const float *target, int32_t Q, int32_t H, int32_t W,
+                    float lambda1, float *out, float *d_pred, void *ws, size_t ws_bytes,
+                    void *stream) {
+    if (Q < 0 || H < 1 || W < 1) return fail(WRF_EINVAL, "loss: Q >= 0, H >= 1, W >= 1");
+    if (static_cast<long long>(Q) * H * W >= (1ll << 31))
+        return fail(WRF_EUNSUPPORTED, "loss: Q*H*W must be < 2^31");
+    if (!(lambda1 >= 0.f && lambda1 <= 1.f)) return fail(WRF_EINVAL, "lambda1 must be in [0, 1]");
+    if (Q == 0) return WRF_OK;
+    if (!pred || !target || !out) return fail(WRF_EINVAL, "pred / target / out is NULL");
+    const size_t need = wrf::loss_ws_layout(Q, H, W, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    cudaError_t e = wrf::launch_loss(pred, target, Q, H, W, lambda1, out, d_pred,
+                                     static_cast<char *>(ws), static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "loss");
+    return WRF_OK;
+}
+
+wrf_status wrf_adam(const wrf_adam_group *groups, int32_t n_groups, int32_t step, float beta1,
+                    float beta2, float eps, void *stream) {
+    if (n_groups < 1 || n_groups > wrf::kAdamGroups || !groups)
+        return fail(WRF_EINVAL, "adam: 1..%d groups", wrf::kAdamGroups);
+    if (step < 1) return fail(WRF_EINVAL, "adam: step >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps > 0.f))
+        return fail(WRF_EINVAL, "adam: betas in [0, 1), eps > 0");
+    wrf::AdamGroup g[wrf::kAdamGroups];
+    for (int i = 0; i < n_groups; ++i) {
+        const wrf_adam_group &a = groups[i];
+        if (a.n < 0) return fail(WRF_EINVAL, "adam: group %d has n < 0", i);
+        if (a.n > 0 && (!a.param || !a.grad || !a.m || !a.v))
+            return fail(WRF_EINVAL, "adam: group %d has a NULL array", i);
+        g[i] = wrf::AdamGroup{a.param, a.grad, a.m, a.v, static_cast<long long>(a.n), a.lr};
+    }
+    cudaError_t e = wrf::launch_adam(g, n_groups, step, beta1, beta2, eps,
+                                     static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "adam");
+    return WRF_OK;
+}
+
 wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                     const float *tx, int32_t Q, float *rssi, float *map, void *ws,
                     size_t ws_bytes, void *stream) {

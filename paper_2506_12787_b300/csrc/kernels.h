@@ -62,6 +62,21 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
 cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
                            float4 *rec, uint32_t *count, cudaStream_t st);
 
+// Training protocol (train.cu): Eq. 16 loss with SSIM, and Adam.
+size_t loss_ws_layout(int Q, int H, int W, float **coef, float **part);
+cudaError_t launch_loss(const float *pred, const float *target, int Q, int H, int W, float lam,
+                        float *out, float *d_pred, char *ws, cudaStream_t st);
+struct AdamGroup {
+    float *param;
+    const float *grad;
+    float *m, *v;
+    long long n;
+    float lr;
+};
+constexpr int kAdamGroups = 32;
+cudaError_t launch_adam(const AdamGroup *groups, int n, int step, float beta1, float beta2,
+                        float eps, cudaStream_t st);
+
 // RSSI head: one CTA per query, whole path fused (rssi.cu); U, V and the
 // FP32 weight images come from launch_prep(..., want_bf16 = false).
 constexpr int kRssiMaxN = 64;

@@ -1,0 +1,126 @@
+"""Training protocol of Sec. 4.4 on the library's kernels.
+
+* Coarse stage: only the Gaussians (mean, log-scale, rotation, opacity,
+  amplitude) are fitted, to all training spectra, with the deformation MLP
+  frozen and not applied: every query renders the reference frame G^0.
+* Fine stage: the MLP is activated and fitted together with the Gaussians,
+  except their positions, whose gradients are frozen.  The TX position fed to
+  the MLP's encoding carries the anneal-smoothing noise of Eq. 17-18,
+    n_i = gamma N3(0,1) (2 / cbrt(N_s)) (1 - i / tau)  for i < tau, else 0,
+  on the position normalised to the room's unit cube (i counts fine-stage
+  iterations; N_s is the number of training positions).
+* Loss: Eq. 16 (wrf_loss: L1 + SSIM), optimiser: Adam (wrf_adam) with the
+  learning rates of Table I (1e-2 for the Gaussians, 8e-3 for the MLP).
+
+Readings where the paper is silent: one Adam state per parameter that runs
+on across the stages (its step count is the number of updates that parameter
+has had); PyTorch's Adam defaults beta = (0.9, 0.999), eps = 1e-8; the
+minibatch of TX positions drawn uniformly with replacement every iteration.
+Random draws come from a torch.Generator the caller seeds, or are passed in.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import torch
+
+from . import api
+from .autograd import SpectrumConfig, render_spectra, spectrum_loss
+
+GAUSS_FIELDS = ("mean", "log_scale", "rot", "opacity_logit", "amp")
+
+
+@dataclasses.dataclass
+class TrainConfig:
+    lambda1: float = 0.7       # Table I: L1 weight of Eq. 16
+    lr_gauss: float = 1e-2     # Table I
+    lr_mlp: float = 8e-3       # Table I
+    gamma: float = 1.0         # Table I: anneal smoothing weight
+    tau: int = 10000           # Table I: anneal smoothing threshold
+    coarse_iters: int = 1000
+    batch: int = 64
+    beta1: float = 0.9
+    beta2: float = 0.999
+    eps: float = 1e-8
+
+
+def anneal_noise(normals: torch.Tensor, i: int, n_positions: int, gamma: float, tau: int):
+    """Eq. 18 on the unit-cube position: normals [..., 3] are N3(0,1) draws."""
+    if i >= tau:
+        return torch.zeros_like(normals)
+    return normals * (gamma * (2.0 / n_positions ** (1.0 / 3.0)) * (1.0 - i / tau))
+
+
+class Trainer:
+    """Coarse-to-fine fitting of a scene and its deformation MLP to measured
+    spectra (Sec. 4.4).
+
+    gauss: dict of device FP32 tensors mean [N,2], log_scale [N,2], rot [N],
+    opacity_logit [N], amp [N] (updated in place); mlp_params: [W0, b0, W1, b1,
+    ...] device FP32 tensors (updated in place); tx_train [N_s,3] metres and
+    targets [N_s,H,W] on the device."""
+
+    def __init__(self, gauss: dict, mlp_params: list, spec: SpectrumConfig, tx_train, targets,
+                 cfg: TrainConfig = TrainConfig(), generator: torch.Generator | None = None):
+        self.g = {k: gauss[k] for k in GAUSS_FIELDS}
+        self.mlp = list(mlp_params)
+        self.spec, self.cfg = spec, cfg
+        self.tx_train, self.targets = tx_train, targets
+        self.gen = generator
+        self.room_size = torch.tensor(spec.room_size, dtype=torch.float32, device=tx_train.device)
+        self.state = {id(p): [torch.zeros_like(p), torch.zeros_like(p), 0]
+                      for p in list(self.g.values()) + self.mlp}
+        self.it = 0
+
+    @property
+    def coarse(self) -> bool:
+        return self.it < self.cfg.coarse_iters
+
+    def noise(self, Qb: int, normals=None):
+        """Metres added to the MLP's TX input at this fine-stage iteration."""
+        if normals is None:
+            normals = torch.randn(Qb, 3, generator=self.gen).to(self.tx_train.device)
+        i = self.it - self.cfg.coarse_iters
+        return anneal_noise(normals, i, self.tx_train.shape[0], self.cfg.gamma,
+                            self.cfg.tau) * self.room_size
+
+    def step(self, idx=None, normals=None):
+        """One iteration; idx [B] (training positions) and normals [B,3] may be
+        given, else they are drawn.  Returns the loss (0-dim tensor)."""
+        c = self.cfg
+        if idx is None:
+            idx = torch.randint(self.tx_train.shape[0], (c.batch,), generator=self.gen)
+        idx = idx.to(self.tx_train.device)
+        tx, tgt = self.tx_train[idx], self.targets[idx]
+        coarse = self.coarse
+        if not coarse:
+            tx = tx + self.noise(int(idx.numel()), normals)
+        self.spec.stop_grad_mean = not coarse
+        leaves = {k: v.detach().requires_grad_(coarse or k != "mean") for k, v in self.g.items()}
+        params = [] if coarse else [p.detach().requires_grad_() for p in self.mlp]
+        out = render_spectra(self.spec, tx.contiguous(), leaves["mean"], leaves["log_scale"],
+                             leaves["rot"], leaves["opacity_logit"], leaves["amp"], params)
+        loss = spectrum_loss(out, tgt, c.lambda1)
+        loss.backward()
+        groups = []
+        for k in GAUSS_FIELDS:
+            if leaves[k].grad is not None:
+                groups.append((self.g[k], leaves[k].grad, c.lr_gauss))
+        for p, lp in zip(self.mlp, params):
+            groups.append((p, lp.grad, c.lr_mlp))
+        self._adam(groups)
+        self.it += 1
+        return loss.detach()
+
+    def _adam(self, groups):
+        # one launch per distinct step count (all equal except around the
+        # stage change, when the MLP starts at step 1)
+        by_step = {}
+        for p, g, lr in groups:
+            st = self.state[id(p)]
+            st[2] += 1
+            by_step.setdefault(st[2], []).append((p, g.contiguous(), st[0], st[1], lr))
+        for step, gs in by_step.items():
+            for i in range(0, len(gs), 32):
+                api.wrf_adam(gs[i:i + 32], step, self.cfg.beta1, self.cfg.beta2, self.cfg.eps)
