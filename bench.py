@@ -310,14 +310,17 @@ def run_serving(args, dev):
 
 
 def run_train(args):
-    """Training step (differentiation form): forward (FP32 MLP) + mean L1 loss
-    against fixed targets + backward through the rasteriser, projection and
-    MLP, for 20k Gaussians and 64 TX positions per step at 360x90."""
+    """Training iteration of Sec. 4.4, fine stage: anneal-smoothed TX positions
+    (Eq. 17-18), forward (FP32 MLP), Eq. 16 loss (L1 + SSIM) against fixed
+    targets, backward through the rasteriser, projection and MLP (position
+    gradients stopped), Adam update of the Gaussians (positions frozen) and
+    the MLP; 20k Gaussians and 64 TX positions per step at 360x90."""
     import torch
     import torch.distributed as dist
 
     from paper_2506_12787_b300 import api
-    from paper_2506_12787_b300.autograd import SpectrumConfig, render_spectra
+    from paper_2506_12787_b300.autograd import SpectrumConfig
+    from paper_2506_12787_b300.train import Trainer, TrainConfig
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -333,20 +336,18 @@ def run_train(args):
     ds_t = api.DeviceScene.from_host(tgt_scene, dev)
     with torch.no_grad():  # targets: the perturbed scene (the oracle renders them in the tests)
         tgt = api.Renderer(cfg.grid, dev).forward(ds_t, api.DeviceMLP.from_host(m, dev), tx).clone()
-    leaves = [torch.as_tensor(a, device=dev).requires_grad_() for a in sc.arrays()]
-    ps = []
+    gauss = dict(zip(("mean", "log_scale", "rot", "opacity_logit", "amp"),
+                     [torch.as_tensor(a, device=dev).contiguous() for a in sc.arrays()]))
+    mlp_p = []
     for Wt, b in zip(m.W, m.b):
-        ps += [torch.as_tensor(Wt, device=dev).requires_grad_(),
-               torch.as_tensor(b, device=dev).requires_grad_()]
+        mlp_p += [torch.as_tensor(Wt, device=dev), torch.as_tensor(b, device=dev)]
+    tcfg = TrainConfig(coarse_iters=0, batch=Q)
+    trainer = Trainer(gauss, mlp_p, cfg, tx, tgt, tcfg, torch.Generator().manual_seed(rank))
+    all_idx = torch.arange(Q)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
     def step():
-        for v in leaves + ps:
-            v.grad = None
-        out = render_spectra(cfg, tx, *leaves, ps)
-        loss = (out - tgt).abs().mean()
-        loss.backward()
-        return loss
+        return trainer.step(idx=all_idx)
 
     for _ in range(args.warmup):
         step()
@@ -369,11 +370,15 @@ def run_train(args):
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     total_max, _, value = aggregate(total_s, Q * K, dist if ws > 1 else None)
     # per-stage times of the same step (eager calls, default stream)
-    ds = api.DeviceScene(*[v.detach() for v in leaves])
-    dm = api.DeviceMLP([p.detach() for p in ps[0::2]], [p.detach() for p in ps[1::2]])
+    ds = api.DeviceScene(*[gauss[k] for k in ("mean", "log_scale", "rot", "opacity_logit",
+                                               "amp")])
+    dm = api.DeviceMLP(mlp_p[0::2], mlp_p[1::2])
     r = api.Renderer(cfg.grid, dev, fused=False)
-    dA = torch.sign(r.forward(ds, dm, tx) - tgt) / (Q * H * W)
+    pred = r.forward(ds, dm, tx).clone()
+    _, dA = api.wrf_loss(pred, tgt, tcfg.lambda1)
     L = r.last
+    adam_state = [(p, torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p))
+                  for p in list(gauss.values())[1:] + mlp_p]
 
     def t(f, n=5):
         f()
@@ -389,11 +394,15 @@ def run_train(args):
                                     cfg.grid, dA)
     g = api.wrf_project_backward(ds, L["resid"], Q, d_rec)
     stage = {"forward": t(lambda: r.forward(ds, dm, tx)),
+             "loss_l1_ssim": t(lambda: api.wrf_loss(pred, tgt, tcfg.lambda1)),
              "render_backward": t(lambda: api.wrf_render_backward(
                  L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, N, Q, cfg.grid, dA)),
              "project_backward": t(lambda: api.wrf_project_backward(ds, L["resid"], Q, d_rec)),
              "deform_backward": t(lambda: api.wrf_deform_backward(ds, dm, cfg.grid, tx,
-                                                                  g["d_resid"]))}
+                                                                  g["d_resid"],
+                                                                  stop_grad_mean=True)),
+             "adam": t(lambda: api.wrf_adam([(p.clone(), gg, m_, v_, 1e-3)
+                                             for p, gg, m_, v_ in adam_state], 1))}
     peaks, peak_src = measured_peaks()
     # MLP backward algorithmic FLOP per row: forward recompute of the hidden
     # layers (3 x 2*128^2), delta chain through them and the output
@@ -413,30 +422,38 @@ def run_train(args):
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"train: {N} Gaussians, {Q} TX per step, {W}x{H}, L1 loss, "
-                                   "forward + backward (FP32 MLP)", "gaussians": N,
+            "config": {"workload": f"train: {N} Gaussians, {Q} TX per step, {W}x{H}, fine stage "
+                                   "of Sec. 4.4: anneal noise, forward (FP32 MLP), Eq. 16 loss "
+                                   "(L1 + SSIM), backward, Adam", "gaussians": N,
                        "queries_per_step": Q, "tile": f"{tw}x{th}",
                        "l2": "256 MB buffer rewritten between timed steps",
-                       "final_l1": float(loss)},
+                       "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
-            # forward: PE x2, weights, MLP, project, bin x5, render; backward:
-            # render, project, gamma tables, PE x2, weights, 2 per 8192-row chunk
-            "gpu_launches": K * (11 + 2 + 4 + 2 * ((Q * N + 8191) // 8192))}
+            # forward: PE x2, weights, MLP, project, bin x5, render; loss: 3;
+            # backward: render, project, gamma tables, PE x2, weights, 2 per
+            # 8192-row chunk; Adam: 2 launches (the MLP and the Gaussians run
+            # on separate step counts only at the stage change)
+            "gpu_launches": K * (11 + 3 + 2 + 4 + 2 * ((Q * N + 8191) // 8192) + 1)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
         oracle.grad(sc, m, tx_np[:1], H, W, Q_CUT, np.ones((1, H, W)) / (H * W))
         t1 = time.perf_counter() - t0
         S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-3)))))
-        dA = np.sign(np.random.default_rng(0).normal(size=(S, H, W))) / (S * H * W)
+        from oracle import train as otrain
+        tg = np.asarray(tgt[:S].cpu(), np.float64)
         t0 = time.perf_counter()
-        oracle.forward(sc, m, tx_np[:S], H, W, Q_CUT)
-        oracle.grad(sc, m, tx_np[:S], H, W, Q_CUT, dA)
+        A, _, _, _ = oracle.forward(sc, m, tx_np[:S], H, W, Q_CUT)
+        dA = otrain.loss_grad(A, tg, tcfg.lambda1)
+        gr = oracle.grad(sc, m, tx_np[:S], H, W, Q_CUT, dA, stop_grad_mean=True)
+        for a, ga in ((sc.log_scale, gr["d_log_scale"]), (sc.rot, gr["d_rot"])):
+            otrain.adam(np.asarray(a, np.float64), ga, 0 * ga, 0 * ga, 1, tcfg.lr_gauss)
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": S / dt, "unit": "spectra/s", "cores": oracle.num_threads(),
                                 "kind": "oracle",
-                                "sample": f"forward + analytic gradient of {S} of {Q} TX queries, "
-                                          f"{N} Gaussians, FP64 C oracle (OpenMP), {dt:.1f} s"}
+                                "sample": f"forward, Eq. 16 loss gradient, analytic gradient and "
+                                          f"Adam of {S} of {Q} TX queries, {N} Gaussians, FP64 "
+                                          f"oracle (C with OpenMP + numpy), {dt:.1f} s"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
