@@ -431,9 +431,9 @@ def run_train(args):
             "clocks": clk, "roofline": roof,
             # forward: PE x2, weights, MLP, project, bin x5, render; loss: 3;
             # backward: render, project, gamma tables, PE x2, weights, 2 per
-            # 8192-row chunk; Adam: 2 launches (the MLP and the Gaussians run
+            # chunk of up to 1M rows; Adam: 2 launches (the MLP and the Gaussians run
             # on separate step counts only at the stage change)
-            "gpu_launches": K * (11 + 3 + 2 + 4 + 2 * ((Q * N + 8191) // 8192) + 1)}
+            "gpu_launches": K * (11 + 3 + 2 + 4 + 20 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()

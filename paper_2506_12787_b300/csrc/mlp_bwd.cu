@@ -5,7 +5,7 @@
 // dL/db of every layer and, unless positions are stop-gradded (the paper's
 // fine stage, Sec. 4.4), the derivative through gamma(mean) added into
 // d_mean.  Every step over rows is a dense product, so rows are processed in
-// chunks of kChunk as plain GEMMs (cuBLAS, FP32 inputs and outputs computed
+// chunks of up to kChunk as plain GEMMs (cuBLAS, FP32 inputs and outputs computed
 // on the tensor cores with the three-term BF16 split of FP32,
 // CUBLAS_COMPUTE_32F_EMULATED_16BFX9) between small hand-written kernels:
 //   features   H0 = [gamma(mean_n), gamma(tx_q)], H1 = ReLU(U[n] + V[q])
@@ -27,7 +27,16 @@ namespace wrf {
 
 namespace {
 
-constexpr int kChunk = 32768;
+// Rows per chunk: large chunks keep the launch count low and the weight-
+// gradient GEMMs (a reduction over the chunk's rows) long; the buffers take
+// ~8.2 KB per row of the chunk (1M rows: 8.6 GB of workspace).
+constexpr long long kChunk = 1 << 20;
+
+// Rows per chunk for a problem of Q x n rows.
+inline long long chunk_rows(int n, int Q) {
+    const long long rows = static_cast<long long>(Q) * n;
+    return rows < kChunk ? (rows > 0 ? rows : 1) : kChunk;
+}
 constexpr size_t kCublasWs = size_t(32) << 20;
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -182,11 +191,12 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
     DeformBwdWs w{};
     const int din = m.dm + m.dt;
     const int L = m.n_layers;
-    w.cb_H0 = take(static_cast<size_t>(kChunk) * din * 4);
-    for (int l = 0; l < L - 1; ++l) w.cb_Hh[l] = take(static_cast<size_t>(kChunk) * WRF_HIDDEN * 4);
-    for (int l = 0; l < L - 1; ++l) w.cb_G[l] = take(static_cast<size_t>(kChunk) * WRF_HIDDEN * 4);
+    const size_t C = static_cast<size_t>(chunk_rows(n, Q));
+    w.cb_H0 = take(C * din * 4);
+    for (int l = 0; l < L - 1; ++l) w.cb_Hh[l] = take(C * WRF_HIDDEN * 4);
+    for (int l = 0; l < L - 1; ++l) w.cb_G[l] = take(C * WRF_HIDDEN * 4);
     w.cb_G[L - 1] = nullptr;  // the output layer's delta is d_resid itself
-    w.dgm = take(static_cast<size_t>(kChunk) * m.dm * 4);
+    w.dgm = take(C * m.dm * 4);
     w.gam_m = take(static_cast<size_t>(n) * m.dm * 4);
     w.gam_t = take(static_cast<size_t>(Q) * m.dt * 4);
     w.cublas_ws = reinterpret_cast<char *>(take(kCublasWs));
@@ -218,8 +228,9 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
     gamma_tables_kernel<<<static_cast<int>((s.n + Q + 127) / 128), 128, 0, st>>>(
         s, m, g, tx, Q, bw.gam_m, bw.gam_t);
     const cublasOperation_t N_ = CUBLAS_OP_N, T_ = CUBLAS_OP_T;
-    for (long long r0 = 0; r0 < rows; r0 += kChunk) {
-        const int R = static_cast<int>(rows - r0 < kChunk ? rows - r0 : kChunk);
+    const long long CH = chunk_rows(s.n, Q);
+    for (long long r0 = 0; r0 < rows; r0 += CH) {
+        const int R = static_cast<int>(rows - r0 < CH ? rows - r0 : CH);
         const long long nH = static_cast<long long>(R) * WRF_HIDDEN;
         features_kernel<<<grid_for(static_cast<long long>(R) * (din + WRF_HIDDEN)), 256, 0, st>>>(
             s.n, r0, R, m.dm, m.dt, bw.gam_m, bw.gam_t, fw.U, fw.V, bw.cb_H0, bw.cb_Hh[0]);
