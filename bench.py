@@ -429,11 +429,12 @@ def run_train(args):
                        "l2": "256 MB buffer rewritten between timed steps",
                        "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
-            # forward: PE x2, weights, MLP, project, bin x5, render; loss: 3;
-            # backward: render, project, gamma tables, PE x2, weights, 2 per
-            # chunk of up to 1M rows; Adam: 2 launches (the MLP and the Gaussians run
-            # on separate step counts only at the stage change)
-            "gpu_launches": K * (11 + 3 + 2 + 4 + 20 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
+            # this library's kernels only (cuBLAS GEMM kernels not counted):
+            # forward: PE x2, weights, MLP, project, bin x5, render (11); loss: 3;
+            # backward: render, project, gamma tables, then per row chunk of up
+            # to 1M rows features, 3 bias-ReLU, 4 ReLU masks, 5 column sums
+            # (13); Adam: 1
+            "gpu_launches": K * (11 + 3 + 3 + 13 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
