@@ -17,6 +17,12 @@ Function -> paper:
   render        Sec. 4.1 Eq. 9, Sec. 4.2 Eq. 13 (order-free truncated sum)
   bin_f32       tile lists, Sec. 4.1 ("spectrum domain partitioned into tiles")
   grad          derivatives of the above (Sec. 4.4 training by back-propagation)
+  wrap          optional azimuth periodicity (0 and W columns the same direction:
+                every sum runs over the images mx + m W of each Gaussian, the tile
+                lists cover columns modulo W)
+  forward_complex  two channels (real and imaginary amplitude): Sec. 6.1 renders
+                them as separate channels and decomposes the result into
+                magnitude and phase
   rssi          Sec. 7.2 (RSSI head: global average pool of the rendered map) with
                 RSSI as the spectrum magnitude averaged over azimuth and elevation
                 (Sec. 6.6)
@@ -66,6 +72,12 @@ def lib():
         L.or_bin_f32.argtypes = [C.c_int, C.c_int, F, C.c_int, C.c_int, C.c_int, C.c_int, U32,
                                  U32, C.c_int64, I64, U32]
         L.or_render_grad.argtypes = [C.c_int, C.c_int, D, C.c_int, C.c_int, C.c_double, D, D]
+        L.or_render_w.argtypes = [C.c_int, C.c_int, D, C.c_int, C.c_int, C.c_double, C.c_double,
+                                  C.c_int, D, D]
+        L.or_bin_f32_w.argtypes = [C.c_int, C.c_int, F, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_int, U32, U32, C.c_int64, I64, U32]
+        L.or_render_grad_w.argtypes = [C.c_int, C.c_int, D, C.c_int, C.c_int, C.c_double,
+                                       C.c_int, D, D]
         L.or_project_grad.argtypes = [C.c_int, D, D, D, D, C.c_int, D, D, D, D, D, D, D, D]
         L.or_project_grad.restype = None
         L.or_mlp_grad.argtypes = [C.c_int, D, C.c_int, C.c_int, C.c_int, D, C.c_int, C.c_int, D,
@@ -147,26 +159,46 @@ def project(scene, resid, q_cut: float, Q: int | None = None) -> np.ndarray:
     return out
 
 
-def render(proj, H: int, W: int, q_cut: float, band: float = 1e-4, with_slack: bool = True):
+def render(proj, H: int, W: int, q_cut: float, band: float = 1e-4, with_slack: bool = True,
+           wrap: bool = False):
     """Spectra [Q,H,W] (Eq. 9/13) and the per-pixel cutoff-band slack."""
     proj, pp = _d(proj)
     Q, N = proj.shape[0], proj.shape[1]
     out = np.zeros((Q, H, W))
     slack = np.zeros((Q, H, W)) if with_slack else None
-    rc = lib().or_render(Q, N, pp, H, W, float(q_cut), float(band), out.ctypes.data_as(D),
-                         slack.ctypes.data_as(D) if with_slack else _null(D))
+    rc = lib().or_render_w(Q, N, pp, H, W, float(q_cut), float(band), int(wrap),
+                           out.ctypes.data_as(D), slack.ctypes.data_as(D) if with_slack else _null(D))
     if rc != 0:
         raise ValueError(f"or_render failed ({rc})")
     return out, slack
 
 
-def forward(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4):
+def forward(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4,
+            wrap: bool = False):
     """Full path: deform -> project -> render. mlp=None skips the MLP."""
     tx = np.atleast_2d(tx)
     resid = deform(scene, mlp, tx, H, W) if mlp is not None else None
     proj = project(scene, resid, q_cut, Q=tx.shape[0])
-    A, slack = render(proj, H, W, q_cut, band)
+    A, slack = render(proj, H, W, q_cut, band, wrap=wrap)
     return A, slack, proj, resid
+
+
+def forward_complex(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4,
+                    wrap: bool = False):
+    """Two channels: scene.amp [N, 2] holds the real and imaginary amplitude.
+    The geometry (deformation, projection, footprint) is shared; each channel
+    is the order-free sum with its own weight sigmoid(opacity) * amp_c (Eq.
+    9/13), and the result is decomposed into magnitude |A| and phase arg A
+    (Sec. 6.1; arg 0 = 0).  Returns (re, im, magnitude, phase, slack), slack
+    the larger of the two channels' cutoff-band slacks."""
+    amp = np.asarray(scene.amp, np.float64)
+    parts = []
+    for c in range(2):
+        sc = type(scene)(scene.mean, scene.log_scale, scene.rot, scene.opacity_logit,
+                         np.ascontiguousarray(amp[:, c]))
+        parts.append(forward(sc, mlp, tx, H, W, q_cut, band, wrap=wrap))
+    re, im = parts[0][0], parts[1][0]
+    return re, im, np.hypot(re, im), np.arctan2(im, re), np.maximum(parts[0][1], parts[1][1])
 
 
 def rssi(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4):
@@ -183,7 +215,7 @@ def tiles(H: int, W: int, tw: int, th: int):
     return (W + tw - 1) // tw, (H + th - 1) // th
 
 
-def bin_f32(rec32, H: int, W: int, tw: int, th: int, cap: int | None = None):
+def bin_f32(rec32, H: int, W: int, tw: int, th: int, cap: int | None = None, wrap: bool = False):
     """Tile lists from FP32 records [Q,N,8]: (counts [Q,N], gids [K], offsets [Q*T+1])."""
     rec32 = np.ascontiguousarray(rec32, dtype=np.float32)
     Q, N = rec32.shape[0], rec32.shape[1]
@@ -194,14 +226,14 @@ def bin_f32(rec32, H: int, W: int, tw: int, th: int, cap: int | None = None):
     nk = C.c_int64(0)
     if cap is None:
         cap = 0
-        lib().or_bin_f32(Q, N, rec32.ctypes.data_as(F), H, W, tw, th,
-                         counts.ctypes.data_as(U32), _null(U32), 0, C.byref(nk),
-                         offsets.ctypes.data_as(U32))
+        lib().or_bin_f32_w(Q, N, rec32.ctypes.data_as(F), H, W, tw, th, int(wrap),
+                           counts.ctypes.data_as(U32), _null(U32), 0, C.byref(nk),
+                           offsets.ctypes.data_as(U32))
         cap = int(nk.value)
     gids = np.zeros(max(cap, 1), np.uint32)
-    rc = lib().or_bin_f32(Q, N, rec32.ctypes.data_as(F), H, W, tw, th,
-                          counts.ctypes.data_as(U32), gids.ctypes.data_as(U32), int(cap),
-                          C.byref(nk), offsets.ctypes.data_as(U32))
+    rc = lib().or_bin_f32_w(Q, N, rec32.ctypes.data_as(F), H, W, tw, th, int(wrap),
+                            counts.ctypes.data_as(U32), gids.ctypes.data_as(U32), int(cap),
+                            C.byref(nk), offsets.ctypes.data_as(U32))
     if rc == -2:
         return counts, None, offsets, int(nk.value)
     if rc != 0:
@@ -209,7 +241,8 @@ def bin_f32(rec32, H: int, W: int, tw: int, th: int, cap: int | None = None):
     return counts, gids[: int(nk.value)], offsets, int(nk.value)
 
 
-def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool = False):
+def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool = False,
+         wrap: bool = False):
     """Analytic FP64 gradient of L given dL/dA [Q,H,W].
 
     Returns a dict with d_mean [N,2], d_log_scale [N,2], d_rot [N],
@@ -223,7 +256,7 @@ def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool 
     dA, pdA = _d(dA)
     N = proj.shape[1]
     dproj = np.zeros((Q, N, 6))
-    lib().or_render_grad(Q, N, pp, H, W, float(q_cut), pdA, dproj.ctypes.data_as(D))
+    lib().or_render_grad_w(Q, N, pp, H, W, float(q_cut), int(wrap), pdA, dproj.ctypes.data_as(D))
     arrs = [_d(a) for a in scene.arrays()]
     dresid = np.zeros((Q, N, 5))
     d_mean = np.zeros((N, 2)); d_ls = np.zeros((N, 2)); d_rot = np.zeros(N)

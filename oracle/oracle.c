@@ -187,10 +187,30 @@ static int pixel_range(double centre, double r, int size, int *lo, int *hi)
  * |w| exp(-q/2) over the Gaussians whose q lies within band*q_cut of q_cut,
  * where an FP32 evaluation may legitimately fall on the other side: a bound
  * on the magnitude of what either decision adds, whatever the sign of w. */
+/* Images of a Gaussian along the azimuth axis: with wrap (0 and W columns
+ * the same direction) the sum runs over the centres mx + m W whose extent
+ * +- r meets [0, W-1]; without wrap only m = 0.  r must be finite with wrap. */
+static void image_range(double mx, double r, int W, int wrap, int *m_lo, int *m_hi)
+{
+    if (!wrap) { *m_lo = 0; *m_hi = 0; return; }
+    *m_lo = (int)ceil((-r - mx) / W);
+    *m_hi = (int)floor((W - 1 + r - mx) / W);
+}
+
+int or_render_w(int Q, int N, const double *proj, int H, int W, double q_cut, double band,
+                int wrap, double *out, double *slack);
+
 int or_render(int Q, int N, const double *proj, int H, int W, double q_cut, double band,
               double *out, double *slack)
 {
+    return or_render_w(Q, N, proj, H, W, q_cut, band, 0, out, slack);
+}
+
+int or_render_w(int Q, int N, const double *proj, int H, int W, double q_cut, double band,
+                int wrap, double *out, double *slack)
+{
     if (H < 1 || W < 1) return OR_EINVAL;
+    if (wrap && isinf(q_cut)) return OR_EINVAL;
     double widen = sqrt(1.0 + band);
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < Q; ++q) {
@@ -200,17 +220,22 @@ int or_render(int Q, int N, const double *proj, int H, int W, double q_cut, doub
         if (S) memset(S, 0, sizeof(double) * H * W);
         for (int n = 0; n < N; ++n) {
             const double *p = proj + ((size_t)q * N + n) * 8;
-            int x0, x1, y0, y1;
-            if (!pixel_range(p[0], p[6] * widen, W, &x0, &x1)) continue;
+            int m_lo, m_hi, y0, y1;
             if (!pixel_range(p[1], p[7] * widen, H, &y0, &y1)) continue;
-            for (int y = y0; y <= y1; ++y)
-                for (int x = x0; x <= x1; ++x) {
-                    double dx = x - p[0], dy = y - p[1];
-                    double qq = p[2] * dx * dx + 2.0 * p[3] * dx * dy + p[4] * dy * dy;
-                    double e = p[5] * exp(-0.5 * qq);
-                    if (qq <= q_cut) A[(size_t)y * W + x] += e;
-                    if (S && fabs(qq - q_cut) <= band * q_cut) S[(size_t)y * W + x] += fabs(e);
-                }
+            image_range(p[0], p[6] * widen, W, wrap, &m_lo, &m_hi);
+            for (int m = m_lo; m <= m_hi; ++m) {
+                double cx = p[0] + (double)m * W;
+                int x0, x1;
+                if (!pixel_range(cx, p[6] * widen, W, &x0, &x1)) continue;
+                for (int y = y0; y <= y1; ++y)
+                    for (int x = x0; x <= x1; ++x) {
+                        double dx = x - cx, dy = y - p[1];
+                        double qq = p[2] * dx * dx + 2.0 * p[3] * dx * dy + p[4] * dy * dy;
+                        double e = p[5] * exp(-0.5 * qq);
+                        if (qq <= q_cut) A[(size_t)y * W + x] += e;
+                        if (S && fabs(qq - q_cut) <= band * q_cut) S[(size_t)y * W + x] += fabs(e);
+                    }
+            }
         }
     }
     return OR_OK;
@@ -240,8 +265,56 @@ static int rect_f32(const float *r, int H, int W, int tw, int th, int *tx0, int 
  * Q*T+1 entries (CSR); counts[q*N+n] = number of tiles of (q, n).  When the
  * total exceeds `cap`, no ids are written and OR_ENOSPC is returned with
  * *n_keys set to the required total. */
+/* With azimuth wrap: the column pixels ceil(mx-rx)..floor(mx+rx) (FP32)
+ * taken modulo W, as the tile intervals [a0, a1] and [b0, b1] (the second
+ * empty, b0 > b1, unless the footprint crosses the 0 / W seam); rows as
+ * without wrap.  Returns 0 for an empty footprint. */
+static int rect_f32_wrap(const float *r, int H, int W, int tw, int th, int *a0, int *a1, int *b0,
+                         int *b1, int *ty0, int *ty1)
+{
+    float mx = r[0], my = r[1], rx = r[6], ry = r[7];
+    float ylo = my - ry, yhi = my + ry, hm = (float)(H - 1);
+    if (!(yhi >= 0.0f) || !(ylo <= hm)) return 0;
+    float ay = ceilf(fmaxf(ylo, 0.0f)), by = floorf(fminf(yhi, hm));
+    if (ay > by) return 0;
+    float lo = ceilf(mx - rx), hi = floorf(mx + rx);
+    if (!(lo <= hi)) return 0;
+    int ntx = (W + tw - 1) / tw;
+    *ty0 = (int)ay / th; *ty1 = (int)by / th;
+    *b0 = 1; *b1 = 0;
+    if (hi - lo + 1.0f >= (float)W) { *a0 = 0; *a1 = ntx - 1; return 1; }
+    long c0 = (long)lo, c1 = (long)hi;
+    long a = ((c0 % W) + W) % W, b = ((c1 % W) + W) % W;
+    if (a <= b) { *a0 = (int)(a / tw); *a1 = (int)(b / tw); return 1; }
+    int ta = (int)(a / tw), tb = (int)(b / tw);
+    if (ta <= tb) { *a0 = 0; *a1 = ntx - 1; return 1; }  /* both pieces in one tile */
+    *a0 = 0; *a1 = tb; *b0 = ta; *b1 = ntx - 1;
+    return 1;
+}
+
+/* Column tile intervals of a record: [a0,a1] and [b0,b1] (b empty unless
+ * wrapped); returns 0 when the footprint is empty. */
+static int rect_any(const float *r, int H, int W, int tw, int th, int wrap, int *a0, int *a1,
+                    int *b0, int *b1, int *ty0, int *ty1)
+{
+    if (wrap) return rect_f32_wrap(r, H, W, tw, th, a0, a1, b0, b1, ty0, ty1);
+    *b0 = 1; *b1 = 0;
+    return rect_f32(r, H, W, tw, th, a0, a1, ty0, ty1);
+}
+
+int or_bin_f32_w(int Q, int N, const float *rec, int H, int W, int tw, int th, int wrap,
+                 uint32_t *counts, uint32_t *gids, int64_t cap, int64_t *n_keys,
+                 uint32_t *offsets);
+
 int or_bin_f32(int Q, int N, const float *rec, int H, int W, int tw, int th, uint32_t *counts,
                uint32_t *gids, int64_t cap, int64_t *n_keys, uint32_t *offsets)
+{
+    return or_bin_f32_w(Q, N, rec, H, W, tw, th, 0, counts, gids, cap, n_keys, offsets);
+}
+
+int or_bin_f32_w(int Q, int N, const float *rec, int H, int W, int tw, int th, int wrap,
+                 uint32_t *counts, uint32_t *gids, int64_t cap, int64_t *n_keys,
+                 uint32_t *offsets)
 {
     if (tw < 1 || th < 1 || H < 1 || W < 1) return OR_EINVAL;
     int ntx = (W + tw - 1) / tw, nty = (H + th - 1) / th, T = ntx * nty;
@@ -249,10 +322,13 @@ int or_bin_f32(int Q, int N, const float *rec, int H, int W, int tw, int th, uin
     if (!cnt) return OR_EINVAL;
     for (int q = 0; q < Q; ++q)
         for (int n = 0; n < N; ++n) {
-            int a, b, c, d, k = 0;
-            if (rect_f32(rec + ((size_t)q * N + n) * 8, H, W, tw, th, &a, &b, &c, &d)) {
-                for (int ty = c; ty <= d; ++ty)
+            int a, b, a2, b2, c, d, k = 0;
+            if (rect_any(rec + ((size_t)q * N + n) * 8, H, W, tw, th, wrap, &a, &b, &a2, &b2, &c,
+                         &d)) {
+                for (int ty = c; ty <= d; ++ty) {
                     for (int tx = a; tx <= b; ++tx) { cnt[(size_t)q * T + ty * ntx + tx]++; ++k; }
+                    for (int tx = a2; tx <= b2; ++tx) { cnt[(size_t)q * T + ty * ntx + tx]++; ++k; }
+                }
             }
             if (counts) counts[(size_t)q * N + n] = (uint32_t)k;
         }
@@ -268,10 +344,14 @@ int or_bin_f32(int Q, int N, const float *rec, int H, int W, int tw, int th, uin
     if ((int64_t)run > cap || run > 0xffffffffull) { free(cnt); return OR_ENOSPC; }
     for (int q = 0; q < Q; ++q)
         for (int n = 0; n < N; ++n) {
-            int a, b, c, d;
-            if (!rect_f32(rec + ((size_t)q * N + n) * 8, H, W, tw, th, &a, &b, &c, &d)) continue;
-            for (int ty = c; ty <= d; ++ty)
+            int a, b, a2, b2, c, d;
+            if (!rect_any(rec + ((size_t)q * N + n) * 8, H, W, tw, th, wrap, &a, &b, &a2, &b2, &c,
+                          &d))
+                continue;
+            for (int ty = c; ty <= d; ++ty) {
                 for (int tx = a; tx <= b; ++tx) gids[cnt[(size_t)q * T + ty * ntx + tx]++] = n;
+                for (int tx = a2; tx <= b2; ++tx) gids[cnt[(size_t)q * T + ty * ntx + tx]++] = n;
+            }
         }
     free(cnt);
     return OR_OK;
@@ -280,9 +360,19 @@ int or_bin_f32(int Q, int N, const float *rec, int H, int W, int tw, int th, uin
 /* -------------------------------------------------------- gradients ---- */
 /* d/d(proj) of L given dL/dA: dproj row = [dmx, dmy, dA, dB, dC, dw].  The
  * cutoff indicator is piecewise constant and contributes no derivative. */
+int or_render_grad_w(int Q, int N, const double *proj, int H, int W, double q_cut, int wrap,
+                     const double *dA, double *dproj);
+
 int or_render_grad(int Q, int N, const double *proj, int H, int W, double q_cut,
                    const double *dA, double *dproj)
 {
+    return or_render_grad_w(Q, N, proj, H, W, q_cut, 0, dA, dproj);
+}
+
+int or_render_grad_w(int Q, int N, const double *proj, int H, int W, double q_cut, int wrap,
+                     const double *dA, double *dproj)
+{
+    if (wrap && isinf(q_cut)) return OR_EINVAL;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int q = 0; q < Q; ++q) {
         const double *G = dA + (size_t)q * H * W;
@@ -290,23 +380,28 @@ int or_render_grad(int Q, int N, const double *proj, int H, int W, double q_cut,
             const double *p = proj + ((size_t)q * N + n) * 8;
             double *g = dproj + ((size_t)q * N + n) * 6;
             for (int i = 0; i < 6; ++i) g[i] = 0.0;
-            int x0, x1, y0, y1;
-            if (!pixel_range(p[0], p[6], W, &x0, &x1)) continue;
+            int m_lo, m_hi, y0, y1;
             if (!pixel_range(p[1], p[7], H, &y0, &y1)) continue;
-            for (int y = y0; y <= y1; ++y)
-                for (int x = x0; x <= x1; ++x) {
-                    double dx = x - p[0], dy = y - p[1];
-                    double qq = p[2] * dx * dx + 2.0 * p[3] * dx * dy + p[4] * dy * dy;
-                    if (!(qq <= q_cut)) continue;
-                    double e = exp(-0.5 * qq), gp = G[(size_t)y * W + x];
-                    double gw = gp * p[5] * e;
-                    g[0] += gw * (p[2] * dx + p[3] * dy);
-                    g[1] += gw * (p[3] * dx + p[4] * dy);
-                    g[2] += -0.5 * gw * dx * dx;
-                    g[3] += -gw * dx * dy;
-                    g[4] += -0.5 * gw * dy * dy;
-                    g[5] += gp * e;
-                }
+            image_range(p[0], p[6], W, wrap, &m_lo, &m_hi);
+            for (int m = m_lo; m <= m_hi; ++m) {
+                double cx = p[0] + (double)m * W;
+                int x0, x1;
+                if (!pixel_range(cx, p[6], W, &x0, &x1)) continue;
+                for (int y = y0; y <= y1; ++y)
+                    for (int x = x0; x <= x1; ++x) {
+                        double dx = x - cx, dy = y - p[1];
+                        double qq = p[2] * dx * dx + 2.0 * p[3] * dx * dy + p[4] * dy * dy;
+                        if (!(qq <= q_cut)) continue;
+                        double e = exp(-0.5 * qq), gp = G[(size_t)y * W + x];
+                        double gw = gp * p[5] * e;
+                        g[0] += gw * (p[2] * dx + p[3] * dy);
+                        g[1] += gw * (p[3] * dx + p[4] * dy);
+                        g[2] += -0.5 * gw * dx * dx;
+                        g[3] += -gw * dx * dy;
+                        g[4] += -0.5 * gw * dy * dy;
+                        g[5] += gp * e;
+                    }
+            }
         }
     }
     return OR_OK;

@@ -408,3 +408,100 @@ def test_rssi_is_the_mean_magnitude():
     r1, _ = oracle.rssi(s1, mlp, tx, 16, 16, 9.0)
     r2, _ = oracle.rssi(s2, mlp, tx, 16, 16, 9.0)
     assert r1 + r2 == pytest.approx(r, rel=1e-12)
+
+
+# --------------------------------------------------- azimuth wrap, 2 channels ----
+def test_wrap_is_cyclic():
+    """With wrap the map is periodic in azimuth: moving every Gaussian by k
+    columns rolls the map by k columns (exactly, integer moves)."""
+    H, W = 20, 48
+    sc = synth.make_scene(60, H, W, seed=11)
+    A, _, _, _ = oracle.forward(sc, None, np.zeros((1, 3)), H, W, 9.0, wrap=True)
+    for k in (5, 31):
+        m = sc.mean.astype(np.float64).copy()
+        m[:, 0] = (m[:, 0] + k) % W
+        sk = synth.Scene(m, sc.log_scale, sc.rot, sc.opacity_logit, sc.amp)
+        Ak, _, _, _ = oracle.forward(sk, None, np.zeros((1, 3)), H, W, 9.0, wrap=True)
+        assert np.allclose(Ak, np.roll(A, k, axis=2), rtol=0, atol=1e-12)
+
+
+def test_wrap_seam_integral_and_interior():
+    """A Gaussian on the 0 / W seam keeps its whole lattice sum 2 pi sigma^2 w
+    with wrap (q_cut = 60: truncation e^-30) and loses about half without;
+    away from the seam wrap changes nothing."""
+    sigma = 2.0
+    seam = _one(0.4, 30.0, math.log(sigma), amp=1.0)
+    Aw, _, _, _ = oracle.forward(seam, None, np.zeros((1, 3)), 60, 72, 60.0, wrap=True)
+    An, _, _, _ = oracle.forward(seam, None, np.zeros((1, 3)), 60, 72, 60.0)
+    assert Aw.sum() == pytest.approx(2 * math.pi * sigma ** 2, rel=1e-9)
+    assert 0.5 < An.sum() / Aw.sum() < 0.8  # centre at column 0.4: a bit over half at x >= 0
+    mid = _one(36.2, 30.0, math.log(sigma), amp=0.5)
+    Bw, _, _, _ = oracle.forward(mid, None, np.zeros((1, 3)), 60, 72, 9.0, wrap=True)
+    Bn, _, _, _ = oracle.forward(mid, None, np.zeros((1, 3)), 60, 72, 9.0)
+    assert np.array_equal(Bw, Bn)
+
+
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (32, 8)])
+def test_bin_wrap_matches_brute_force(tile):
+    """Tile lists with wrap: a Gaussian lists tile t when a column of t is
+    congruent mod W to a pixel column of ceil(mx-rx)..floor(mx+rx) (FP32) and
+    t's rows meet the clamped row range; W = 72 is not a multiple of 32."""
+    tw, th = tile
+    H, W = 24, 72
+    rng = np.random.default_rng(12)
+    Nn = 80
+    rec = np.zeros((2, Nn, 8), np.float32)
+    rec[..., 0] = rng.uniform(-5, W + 5, (2, Nn))
+    rec[..., 1] = rng.uniform(-3, H + 3, (2, Nn))
+    rec[..., 6] = rng.uniform(0.2, 12, (2, Nn))
+    rec[..., 7] = rng.uniform(0.2, 6, (2, Nn))
+    rec[0, 0, 6] = 40.0  # spans more than W - 1 columns: every column tile
+    counts, gids, offs, nk = oracle.bin_f32(rec, H, W, tw, th, wrap=True)
+    ntx, nty = oracle.tiles(H, W, tw, th)
+    want = [[[] for _ in range(ntx * nty)] for _ in range(2)]
+    for q in range(2):
+        for n in range(Nn):
+            mx, my, rx, ry = (np.float32(v) for v in rec[q, n, [0, 1, 6, 7]])
+            lo, hi = np.ceil(np.float32(mx - rx)), np.floor(np.float32(mx + rx))
+            ylo = np.ceil(max(np.float32(my - ry), np.float32(0)))
+            yhi = np.floor(min(np.float32(my + ry), np.float32(H - 1)))
+            if lo > hi or ylo > yhi:
+                continue
+            cols = set(int(c) % W for c in np.arange(lo, hi + 1)) if hi - lo + 1 < W else set(range(W))
+            ct = sorted(set(c // tw for c in cols))
+            for ty in range(int(ylo) // th, int(yhi) // th + 1):
+                for tx in ct:
+                    want[q][ty * ntx + tx].append(n)
+    for q in range(2):
+        for t in range(ntx * nty):
+            got = list(gids[offs[q * ntx * nty + t]:offs[q * ntx * nty + t + 1]])
+            assert got == want[q][t], (q, t)
+    assert nk == sum(len(l) for w in want for l in w)
+
+
+def test_two_channels_magnitude_and_phase():
+    """One Gaussian of complex amplitude r e^{i phi}: magnitude
+    r sigmoid(o) exp(-q/2), phase phi inside the footprint; opposite
+    amplitudes at the same place cancel; a zero imaginary part gives the
+    one-channel map's magnitude."""
+    r, phi, o = 0.9, 2.3, 0.5
+    sc = synth.Scene(np.array([[20.0, 11.0]]), np.array([[math.log(2.5)] * 2]), np.array([0.0]),
+                     np.array([o]), np.array([[r * math.cos(phi), r * math.sin(phi)]]))
+    re, im, mag, ph, _ = oracle.forward_complex(sc, None, np.zeros((1, 3)), 24, 40, 9.0)
+    w = r / (1 + math.exp(-o))
+    y, x = np.mgrid[0:24, 0:40]
+    qq = ((x - 20.0) ** 2 + (y - 11.0) ** 2) / 2.5 ** 2
+    inside = qq <= 9.0
+    assert np.allclose(mag[0][inside], w * np.exp(-qq[inside] / 2), rtol=1e-12, atol=0)
+    assert np.all(mag[0][~inside] == 0)
+    assert np.allclose(ph[0][inside], phi, rtol=0, atol=1e-12)
+    two = synth.Scene(np.array([[20.0, 11.0], [20.0, 11.0]]), np.array([[1.0, 1.0], [1.0, 1.0]]),
+                      np.zeros(2), np.zeros(2), np.array([[0.3, -0.2], [-0.3, 0.2]]))
+    _, _, mag2, _, _ = oracle.forward_complex(two, None, np.zeros((1, 3)), 24, 40, 9.0)
+    assert np.all(np.abs(mag2) <= 1e-15)
+    sc3 = synth.make_scene(30, 24, 40, seed=13)
+    amp2 = np.stack([sc3.amp.astype(np.float64), np.zeros(30)], 1)
+    c3 = synth.Scene(sc3.mean, sc3.log_scale, sc3.rot, sc3.opacity_logit, amp2)
+    A, _, _, _ = oracle.forward(sc3, None, np.zeros((1, 3)), 24, 40, 9.0)
+    _, _, mag3, _, _ = oracle.forward_complex(c3, None, np.zeros((1, 3)), 24, 40, 9.0)
+    assert np.array_equal(mag3, np.abs(A))
