@@ -87,11 +87,19 @@ typedef struct {
  * q = d^T Sigma^-1 d <= q_cut (d = p - centre); q_cut = +inf disables the
  * cutoff.  Tiles are tile_w x tile_h pixels, numbered row-major; the last
  * tile row/column may be partial.  Supported tile shapes: 8x8, 16x8, 16x16,
- * 32x8, 32x16 (w x h). */
+ * 32x8, 32x16 (w x h).
+ * wrap_x = 1 makes the azimuth axis periodic (columns 0 and W the same
+ * direction, as for a 0-360 degree spectrum): every Gaussian also acts through
+ * its images centre + k W, tile lists cover columns modulo W, and each tile is
+ * rendered with the image nearest to it; this needs q_cut finite and every
+ * footprint narrower than W - tile_w pixels (2 rx < W - tile_w), else the
+ * device status word records WRF_EUNSUPPORTED.  wrap_x = 0: a flat plane
+ * clipped at the edges. */
 typedef struct {
     int32_t H, W;
     int32_t tile_w, tile_h;
     float q_cut;
+    int32_t wrap_x;
 } wrf_grid;
 
 /* Projected record of one deformed Gaussian for one query: 8 floats, 32-byte

@@ -201,13 +201,13 @@ def forward_complex(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 
     return re, im, np.hypot(re, im), np.arctan2(im, re), np.maximum(parts[0][1], parts[1][1])
 
 
-def rssi(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4):
+def rssi(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4, wrap: bool = False):
     """RSSI head of Sec. 7.2: each query's H x W map (Eq. 9/13) reduced by a
     global average pool of its magnitude (Sec. 6.6 averages the spectrum
     magnitude over azimuth and elevation; one real channel, so the magnitude is
     |A|).  Returns the pooled values [Q] and the pooled cutoff-band slack [Q]:
     a pooled GPU value is correct within tol + slack."""
-    A, slack, _, _ = forward(scene, mlp, tx, H, W, q_cut, band)
+    A, slack, _, _ = forward(scene, mlp, tx, H, W, q_cut, band, wrap=wrap)
     return np.abs(A).mean(axis=(1, 2)), slack.mean(axis=(1, 2))
 
 

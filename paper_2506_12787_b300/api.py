@@ -102,8 +102,9 @@ class DeviceMLP:
         return m
 
 
-def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0) -> _lib.Grid:
-    return _lib.Grid(H, W, tile_w, tile_h, float(q_cut))
+def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0, wrap=False) -> _lib.Grid:
+    """Spectrum grid; wrap=True makes the azimuth axis periodic (0 = 360 degrees)."""
+    return _lib.Grid(H, W, tile_w, tile_h, float(q_cut), int(bool(wrap)))
 
 
 def tiles_of(grid) -> int:

@@ -21,8 +21,8 @@ TILE_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 8), (32, 16))
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 
-def workload_key(n, H, W, Q, precision, q_cut):
-    return f"n{n}_h{H}_w{W}_q{Q}_p{precision}_c{q_cut:g}"
+def workload_key(n, H, W, Q, precision, q_cut, wrap=False):
+    return f"n{n}_h{H}_w{W}_q{Q}_p{precision}_c{q_cut:g}" + ("_wrap" if wrap else "")
 
 
 def time_step(fw, tx, stream, reps):
@@ -39,11 +39,11 @@ def time_step(fw, tx, stream, reps):
 
 
 def tune(scene: api.DeviceScene, mlp: api.DeviceMLP, H: int, W: int, tx, q_cut=9.0, reps=5,
-         cache_path: str | None = DEFAULT_CACHE, shapes=TILE_SHAPES, verbose=False):
+         cache_path: str | None = DEFAULT_CACHE, shapes=TILE_SHAPES, verbose=False, wrap=False):
     """Best (tile_w, tile_h) for this workload and the timings of all shapes
     (ms per step).  tx: device tensor [Q,3] of representative TX positions."""
     Q = int(tx.shape[0])
-    key = workload_key(scene.n, H, W, Q, mlp.precision, q_cut)
+    key = workload_key(scene.n, H, W, Q, mlp.precision, q_cut, wrap)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         try:
@@ -57,7 +57,7 @@ def tune(scene: api.DeviceScene, mlp: api.DeviceMLP, H: int, W: int, tx, q_cut=9
     stream = torch.cuda.Stream(device=tx.device)
     times = {}
     for tw, th in shapes:
-        grid = api.make_grid(H, W, tw, th, q_cut)
+        grid = api.make_grid(H, W, tw, th, q_cut, wrap)
         fw = BatchedForward(scene, mlp, grid, Q, tx.device)
         with torch.cuda.stream(stream):
             fw.reserve(tx, stream)

@@ -30,7 +30,7 @@ constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;  // 4096
 
 __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n, GridView g,
-                                                        int C, uint32_t *counts) {
+                                                        int C, uint32_t *counts, int *status) {
     extern __shared__ uint32_t hist[];
     const int c = blockIdx.x, q = blockIdx.y;
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) hist[t] = 0;
@@ -40,10 +40,16 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
         if (id >= n) break;
         size_t r = static_cast<size_t>(q) * n + id;
         float4 a = rec[2 * r], b = rec[2 * r + 1];
-        int tx0, tx1, ty0, ty1;
-        if (!tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, ty0, ty1)) continue;
-        for (int ty = ty0; ty <= ty1; ++ty)
+        int tx0, tx1, tx2, tx3, ty0, ty1;
+        if (!tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1)) continue;
+        // with wrap a tile is rendered with the Gaussian's image nearest to
+        // it, which needs every footprint narrower than W - tile width
+        if (g.wrap && !(__fmul_rn(2.f, b.z) < static_cast<float>(g.W - g.tw)))
+            record_status(status, WRF_EUNSUPPORTED);
+        for (int ty = ty0; ty <= ty1; ++ty) {
             for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * g.ntx + tx], 1u);
+            for (int tx = tx2; tx <= tx3; ++tx) atomicAdd(&hist[ty * g.ntx + tx], 1u);
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < g.T; t += blockDim.x)
@@ -153,15 +159,16 @@ __global__ void __launch_bounds__(1024) bin_scatter_kernel(const float4 *rec, in
     const int c = blockIdx.x, q = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int id = c * kBinChunk + threadIdx.x;
-    int tx0 = 0, tx1 = -1, ty0 = 0, ty1 = -1;
+    int tx0 = 0, tx1 = -1, tx2 = 1, tx3 = 0, ty0 = 0, ty1 = -1;
     bool valid = false;
     if (id < n) {
         size_t r = static_cast<size_t>(q) * n + id;
         float4 a = rec[2 * r], b = rec[2 * r + 1];
-        valid = tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, ty0, ty1);
+        valid = tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
     }
     for (int tx = 0; tx < g.ntx; ++tx) {
-        uint32_t m = __ballot_sync(0xffffffffu, valid && tx >= tx0 && tx <= tx1);
+        uint32_t m = __ballot_sync(0xffffffffu, valid && ((tx >= tx0 && tx <= tx1) ||
+                                                          (tx >= tx2 && tx <= tx3)));
         if (lane == 0) colmask[w * g.ntx + tx] = m;
     }
     for (int ty = 0; ty < g.nty; ++ty) {
@@ -183,11 +190,14 @@ __global__ void __launch_bounds__(1024) bin_scatter_kernel(const float4 *rec, in
     const uint32_t below = (1u << lane) - 1u;
     for (int ty = ty0; ty <= ty1; ++ty) {
         uint32_t rm = rowmask[w * g.nty + ty];
-        for (int tx = tx0; tx <= tx1; ++tx) {
-            int t = ty * g.ntx + tx;
-            uint32_t mk = colmask[w * g.ntx + tx] & rm;
-            const uint32_t pos = base[t] + woff[w * g.T + t] + __popc(mk & below);
-            if (pos < cap) gids[pos] = static_cast<uint32_t>(id);
+        for (int part = 0; part < 2; ++part) {
+            const int a = part == 0 ? tx0 : tx2, b = part == 0 ? tx1 : tx3;
+            for (int tx = a; tx <= b; ++tx) {
+                int t = ty * g.ntx + tx;
+                uint32_t mk = colmask[w * g.ntx + tx] & rm;
+                const uint32_t pos = base[t] + woff[w * g.T + t] + __popc(mk & below);
+                if (pos < cap) gids[pos] = static_cast<uint32_t>(id);
+            }
         }
     }
 }
@@ -224,7 +234,7 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
     if (Q == 0) return cudaSuccess;
     if (n > 0) {
         dim3 grid(ws.C, Q);
-        bin_count_kernel<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts);
+        bin_count_kernel<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts, status);
     } else {
         cudaError_t e = cudaMemsetAsync(ws.chunk_counts, 0, static_cast<size_t>(ws.M) * 4, st);
         if (e != cudaSuccess) return e;

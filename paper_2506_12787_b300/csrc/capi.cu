@@ -97,6 +97,9 @@ wrf_status check_grid(const wrf_grid *g, wrf::GridView *v) {
     v->nty = (g->H + g->tile_h - 1) / g->tile_h;
     v->T = v->ntx * v->nty;
     v->q_cut = g->q_cut;
+    if (g->wrap_x != 0 && g->wrap_x != 1) return fail(WRF_EINVAL, "wrap_x must be 0 or 1");
+    if (g->wrap_x && !(g->q_cut < INFINITY)) return fail(WRF_EINVAL, "wrap_x needs a finite q_cut");
+    v->wrap = g->wrap_x;
     if (v->T > 3000) return fail(WRF_EUNSUPPORTED, "more than 3000 tiles");
     return WRF_OK;
 }
@@ -324,6 +327,10 @@ wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *
     g.nty = (g.H + 15) / 16;
     g.T = g.ntx * g.nty;
     g.q_cut = grid->q_cut;
+    if (grid->wrap_x != 0 && grid->wrap_x != 1) return fail(WRF_EINVAL, "wrap_x must be 0 or 1");
+    if (grid->wrap_x && !(grid->q_cut < INFINITY))
+        return fail(WRF_EINVAL, "wrap_x needs a finite q_cut");
+    g.wrap = grid->wrap_x;
     wrf::DeformWs w{};
     wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, &w, static_cast<char *>(ws));
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -20,6 +20,7 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 struct GridView {
     int H, W, tw, th, ntx, nty, T;
     float q_cut;
+    int wrap;  // azimuth wrap: columns 0 and W are the same direction
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -109,25 +110,74 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 // ------------------------------------------------------- footprint rectangle
-// Tiles covered by a record's footprint: pixels ceil(mx-rx)..floor(mx+rx)
-// (and likewise in y) clipped to the grid, divided by the tile size.  Every
-// step is an exactly rounded FP32 operation so the result is a fixed integer
-// function of the stored record.
+// Tiles covered by a record's footprint: pixels ceil(my-ry)..floor(my+ry)
+// clipped to the grid, divided by the tile height; columns ceil(mx-rx)..
+// floor(mx+rx) clipped to the grid, or, with azimuth wrap (0 and W the same
+// direction), taken modulo W, divided by the tile width.  The columns come as
+// up to two tile intervals [tx0, tx1] and [tx2, tx3] (the second empty,
+// tx2 > tx3, unless a wrapped footprint crosses the seam).  Every step is an
+// exactly rounded FP32 operation so the result is a fixed integer function of
+// the stored record.
 __device__ __forceinline__ bool tile_rect(float mx, float my, float rx, float ry,
-                                          const GridView &g, int &tx0, int &tx1, int &ty0,
-                                          int &ty1) {
-    float xlo = __fsub_rn(mx, rx), xhi = __fadd_rn(mx, rx);
-    float ylo = __fsub_rn(my, ry), yhi = __fadd_rn(my, ry);
-    float wm = static_cast<float>(g.W - 1), hm = static_cast<float>(g.H - 1);
-    if (!(xhi >= 0.f) || !(xlo <= wm) || !(yhi >= 0.f) || !(ylo <= hm)) return false;
-    float ax = ceilf(fmaxf(xlo, 0.f)), bx = floorf(fminf(xhi, wm));
-    float ay = ceilf(fmaxf(ylo, 0.f)), by = floorf(fminf(yhi, hm));
-    if (ax > bx || ay > by) return false;
-    tx0 = static_cast<int>(ax) / g.tw;
-    tx1 = static_cast<int>(bx) / g.tw;
+                                          const GridView &g, int &tx0, int &tx1, int &tx2,
+                                          int &tx3, int &ty0, int &ty1) {
+    tx2 = 1;
+    tx3 = 0;
+    const float ylo = __fsub_rn(my, ry), yhi = __fadd_rn(my, ry);
+    const float hm = static_cast<float>(g.H - 1);
+    if (!(yhi >= 0.f) || !(ylo <= hm)) return false;
+    const float ay = ceilf(fmaxf(ylo, 0.f)), by = floorf(fminf(yhi, hm));
+    if (ay > by) return false;
     ty0 = static_cast<int>(ay) / g.th;
     ty1 = static_cast<int>(by) / g.th;
+    const float xlo = __fsub_rn(mx, rx), xhi = __fadd_rn(mx, rx);
+    if (!g.wrap) {
+        const float wm = static_cast<float>(g.W - 1);
+        if (!(xhi >= 0.f) || !(xlo <= wm)) return false;
+        const float ax = ceilf(fmaxf(xlo, 0.f)), bx = floorf(fminf(xhi, wm));
+        if (ax > bx) return false;
+        tx0 = static_cast<int>(ax) / g.tw;
+        tx1 = static_cast<int>(bx) / g.tw;
+        return true;
+    }
+    const float lo = ceilf(xlo), hi = floorf(xhi);
+    if (!(lo <= hi)) return false;
+    if (__fadd_rn(__fsub_rn(hi, lo), 1.f) >= static_cast<float>(g.W)) {
+        tx0 = 0;
+        tx1 = g.ntx - 1;
+        return true;
+    }
+    const long long c0 = static_cast<long long>(lo), c1 = static_cast<long long>(hi);
+    const int a = static_cast<int>(((c0 % g.W) + g.W) % g.W);
+    const int b = static_cast<int>(((c1 % g.W) + g.W) % g.W);
+    if (a <= b) {
+        tx0 = a / g.tw;
+        tx1 = b / g.tw;
+        return true;
+    }
+    const int ta = a / g.tw, tb = b / g.tw;
+    tx0 = 0;
+    if (ta <= tb) {  // both pieces of the wrapped footprint meet in one tile
+        tx1 = g.ntx - 1;
+        return true;
+    }
+    tx1 = tb;
+    tx2 = ta;
+    tx3 = g.ntx - 1;
     return true;
+}
+
+// Column tiles covered (both intervals of tile_rect).
+__device__ __forceinline__ int tile_cols(int tx0, int tx1, int tx2, int tx3) {
+    return (tx1 - tx0 + 1) + (tx3 >= tx2 ? tx3 - tx2 + 1 : 0);
+}
+
+// Centre x of the image of a Gaussian nearest to column position xc (azimuth
+// wrap: the images are mx + k W); mx itself without wrap.
+__device__ __forceinline__ float nearest_image_x(float mx, float xc, const GridView &g) {
+    if (!g.wrap) return mx;
+    const float W = static_cast<float>(g.W);
+    return __fsub_rn(mx, W * rintf(__fdiv_rn(__fsub_rn(mx, xc), W)));
 }
 
 // ------------------------------------------------------------- projection
@@ -167,9 +217,9 @@ __device__ __forceinline__ uint32_t project_params(const GaussParams &p, float d
     float rx = sqrtf(g.q_cut * sxx), ry = sqrtf(g.q_cut * syy);
     r0 = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
     r1 = make_float4(C * kHalfLog2e, w, rx, ry);
-    int a, b, c, d;
-    if (!tile_rect(mx, my, rx, ry, g, a, b, c, d)) return 0u;
-    return static_cast<uint32_t>((b - a + 1) * (d - c + 1));
+    int a, b, a2, b2, c, d;
+    if (!tile_rect(mx, my, rx, ry, g, a, b, a2, b2, c, d)) return 0u;
+    return static_cast<uint32_t>(tile_cols(a, b, a2, b2) * (d - c + 1));
 }
 
 __device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float d0, float d1,

@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         // and the mask of 8x8 warp blocks its footprint rectangle touches.
         if (tid < cnt) {
             const float4 r0 = raw[(buf * B + tid) * 2], r1 = raw[(buf * B + tid) * 2 + 1];
-            const float ux = r0.x - xcen, uy = r0.y - ycen;
+            // with azimuth wrap, the image of the Gaussian nearest to this tile
+            const float mx = nearest_image_x(r0.x, xcen, g);
+            const float ux = mx - xcen, uy = r0.y - ycen;
             const float h1 = fmaf(r0.z, ux, r0.w * uy), h2 = fmaf(r0.w, ux, r1.x * uy);
             const float c0 = -fmaf(ux, h1, uy * h2);
             const float c1 = 2.f * h1, c2 = 2.f * h2, c4 = -2.f * r0.w, c5 = -r1.x;
@@ -154,8 +156,8 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             }
             gcoef[tid] = make_float4(-r0.z, -r0.z, r1.y, 0.f);
             uint32_t mk = 0;
-            const float xlo = ceilf(__fsub_rn(r0.x, r1.z)) - static_cast<float>(x0);
-            const float xhi = floorf(__fadd_rn(r0.x, r1.z)) - static_cast<float>(x0);
+            const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
+            const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
             const float ylo = ceilf(__fsub_rn(r0.y, r1.w)) - static_cast<float>(y0);
             const float yhi = floorf(__fadd_rn(r0.y, r1.w)) - static_cast<float>(y0);
             if (xhi >= 0.f && xlo <= TW - 1.f && yhi >= 0.f && ylo <= TH - 1.f) {
@@ -251,7 +253,10 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
         const uint32_t gid = gids[i];
         const size_t r = static_cast<size_t>(q) * n + gid;
-        const float4 r0 = rec[2 * r], r1 = rec[2 * r + 1];
+        float4 r0 = rec[2 * r];
+        const float4 r1 = rec[2 * r + 1];
+        // with azimuth wrap, the image of the Gaussian nearest to this tile
+        r0.x = nearest_image_x(r0.x, static_cast<float>(x0) + 0.5f * TW, g);
         int xa = max(x0, static_cast<int>(ceilf(fmaxf(r0.x - r1.z, static_cast<float>(x0)))));
         int xb = min(xe, static_cast<int>(floorf(fminf(r0.x + r1.z, static_cast<float>(xe)))));
         int ya = max(y0, static_cast<int>(ceilf(fmaxf(r0.y - r1.w, static_cast<float>(y0)))));

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
         float acc = 0.f;
         for (int n = 0; n < N; ++n) {
             const float4 r0 = recs[n][0], r1 = recs[n][1];
-            const float dx = x - r0.x, dy = y - r0.y;
+            float dx = x - r0.x;
+            const float dy = y - r0.y;
+            if (a.g.wrap) dx -= static_cast<float>(a.g.W) * rintf(dx / static_cast<float>(a.g.W));
             const float t = fmaf(r0.z, dx, 2.f * r0.w * dy);
             const float nq = -fmaf(dx, t, r1.x * dy * dy);
             if (nq >= ncut) acc = fmaf(r1.y, ex2_approx(nq), acc);
