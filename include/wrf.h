@@ -56,12 +56,12 @@ enum { WRF_MAX_LAYERS = 8, WRF_HIDDEN = 128, WRF_OUT = 5 };
  * attenuation delta = sigmoid(a) (Sec. 4.1); amp = scalar response psi. */
 typedef struct {
     int32_t n;                   /* number of Gaussians N (>= 0)              */
-    int32_t channels;            /* must be 1                                 */
+    int32_t channels;            /* 1, or 2: real and imaginary amplitude     */
     const float *mean;           /* [N][2] device                             */
     const float *log_scale;      /* [N][2] device                             */
     const float *rot;            /* [N]    device                             */
     const float *opacity_logit;  /* [N]    device                             */
-    const float *amp;            /* [N]    device                             */
+    const float *amp;            /* [N][channels] device                      */
 } wrf_scene;
 
 /* Deformation MLP F_theta (Sec. 4.2, Eq. 14): input [gamma(mean/(W,H)),
@@ -107,9 +107,14 @@ typedef struct {
  *   [0] mx, [1] my     deformed centre (pixels)
  *   [2] a, [3] b, [4] c  inverse covariance scaled by log2(e)/2, so that
  *                      exp(-q/2) = exp2(-(a dx^2 + 2 b dx dy + c dy^2))
- *   [5] w              sigmoid(opacity_logit) * amp
+ *   [5] w              sigmoid(opacity_logit) * amp (amp[n][0])
  *   [6] rx, [7] ry     sqrt(q_cut Sigma_xx), sqrt(q_cut Sigma_yy): axis
- *                      half-widths of the q <= q_cut ellipse                 */
+ *                      half-widths of the q <= q_cut ellipse
+ * With a 2-channel scene (real and imaginary amplitude, Sec. 6.1) the record
+ * buffer holds Q x N x 8 floats followed by Q x N imaginary weights
+ * sigmoid(opacity_logit) * amp[n][1] ([Q][N]): the writers (wrf_project,
+ * wrf_deform_project) fill both and the caller allocates Q x N x 9 floats;
+ * wrf_bin reads the records only, wrf_render_complex both parts.            */
 enum { WRF_REC_FLOATS = 8 };
 
 /* ---------------------------------------------------------------------- */
@@ -247,6 +252,18 @@ wrf_status wrf_adam(const wrf_adam_group *groups, int32_t n_groups, int32_t step
 wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                     const float *tx, int32_t Q, float *rssi, float *map, void *ws,
                     size_t ws_bytes, void *stream);
+
+/* Two-channel rasterisation (Sec. 6.1: the real and imaginary parts of the
+ * spectrum are rasterised as separate channels and decomposed into magnitude
+ * and phase): per pixel re = the sum of wrf_render with the records' w, im =
+ * the same sum with the imaginary weights that follow the records (see the
+ * record layout), one exp per pixel and Gaussian for both; out
+ * [Q][2][H][W] = |re + i im|, arg(re + i im) (atan2, arg 0 = 0).  Other
+ * arguments as wrf_render.  The backward entry points take one channel.    */
+wrf_status wrf_render_complex(const float *rec, const uint32_t *gids,
+                              const uint32_t *tile_offsets, const int64_t *n_keys,
+                              int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
+                              float *out, void *stream);
 
 /* Backward of wrf_render: from dL/dA [Q][H][W] to d_rec [Q][N][6] =
  * dL/d(mx, my, A, B, C, w) where (A, B, C) is the unscaled inverse

@@ -207,6 +207,9 @@ def rssi(scene, mlp, tx, H: int, W: int, q_cut: float, band: float = 1e-4, wrap:
     magnitude over azimuth and elevation; one real channel, so the magnitude is
     |A|).  Returns the pooled values [Q] and the pooled cutoff-band slack [Q]:
     a pooled GPU value is correct within tol + slack."""
+    if np.asarray(scene.amp).ndim == 2:  # two channels: the complex map's magnitude
+        _, _, mag, _, slack = forward_complex(scene, mlp, tx, H, W, q_cut, band, wrap=wrap)
+        return mag.mean(axis=(1, 2)), slack.mean(axis=(1, 2))
     A, slack, _, _ = forward(scene, mlp, tx, H, W, q_cut, band, wrap=wrap)
     return np.abs(A).mean(axis=(1, 2)), slack.mean(axis=(1, 2))
 

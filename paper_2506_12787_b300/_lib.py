@@ -26,7 +26,7 @@ EXPORTS = (
     "wrf_bin_workspace_size", "wrf_bin", "wrf_bin_noalloc", "wrf_render", "wrf_render_backward",
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
-    "wrf_loss_workspace_size", "wrf_loss", "wrf_adam",
+    "wrf_loss_workspace_size", "wrf_loss", "wrf_adam", "wrf_render_complex",
 )
 
 
@@ -94,6 +94,7 @@ def load(path: str = LIB_PATH):
         "wrf_loss_workspace_size": (S, [I32, I32, I32]),
         "wrf_loss": (I32, [P, P, I32, I32, I32, F, P, P, P, S, P]),
         "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
+        "wrf_render_complex": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

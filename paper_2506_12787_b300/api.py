@@ -20,7 +20,7 @@ from ._lib import WRF_BF16, WRF_FP32, WrfError
 __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
-           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam"]
+           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail"]
 
 
 def _p(t):
@@ -46,7 +46,7 @@ class DeviceScene:
     log_scale: torch.Tensor      # [N,2]
     rot: torch.Tensor            # [N]
     opacity_logit: torch.Tensor  # [N]
-    amp: torch.Tensor            # [N]
+    amp: torch.Tensor            # [N], or [N,2]: real and imaginary amplitude
 
     @classmethod
     def from_host(cls, s, device="cuda"):
@@ -57,10 +57,28 @@ class DeviceScene:
     def n(self) -> int:
         return int(self.mean.shape[0])
 
+    @property
+    def channels(self) -> int:
+        return 2 if self.amp.dim() == 2 else 1
+
     def c(self) -> _lib.Scene:
-        return _lib.Scene(self.n, 1, self.mean.data_ptr(), self.log_scale.data_ptr(),
+        return _lib.Scene(self.n, self.channels, self.mean.data_ptr(), self.log_scale.data_ptr(),
                           self.rot.data_ptr(), self.opacity_logit.data_ptr(),
                           self.amp.data_ptr())
+
+
+def alloc_records(Q: int, n: int, channels: int, device):
+    """Record buffer [Q,N,8]; with 2 channels the view of a Q*N*9-float
+    buffer whose last Q*N floats hold the imaginary weights."""
+    if channels == 1:
+        return torch.empty((Q, n, 8), dtype=torch.float32, device=device)
+    return torch.empty(Q * n * 9, dtype=torch.float32, device=device)[: Q * n * 8].view(Q, n, 8)
+
+
+def record_tail(rec, Q: int, n: int):
+    """The imaginary weights [Q,N] that follow a 2-channel record buffer."""
+    base = rec.reshape(-1)
+    return torch.as_strided(base, (Q, n), (n, 1), base.storage_offset() + Q * n * 8)
 
 
 @dataclasses.dataclass
@@ -135,7 +153,7 @@ def wrf_project(scene: DeviceScene, resid, Q: int, grid, rec=None, tile_count=No
     L = _lib.load()
     dev = scene.mean.device
     if rec is None:
-        rec = torch.empty((Q, scene.n, 8), dtype=torch.float32, device=dev)
+        rec = alloc_records(Q, scene.n, scene.channels, dev)
     if tile_count is None:
         tile_count = torch.empty((Q, scene.n), dtype=torch.int32, device=dev)
     _lib.check(L.wrf_project(C.byref(scene.c()), _p(resid), Q, C.byref(grid), _p(rec),
@@ -149,7 +167,7 @@ def wrf_deform_project(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rec=None, t
     Q, dev = int(tx.shape[0]), tx.device
     mc = mlp.c()
     if rec is None:
-        rec = torch.empty((Q, scene.n, 8), dtype=torch.float32, device=dev)
+        rec = alloc_records(Q, scene.n, scene.channels, dev)
     need = L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc))
     ws = _ws(need, dev) if ws is None else ws
     _lib.check(L.wrf_deform_project(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
@@ -230,6 +248,17 @@ def wrf_render(rec, gids, offsets, n_keys, key_capacity: int, n: int, Q: int, gr
         out = torch.empty((Q, grid.H, grid.W), dtype=torch.float32, device=offsets.device)
     _lib.check(L.wrf_render(_p(rec), _p(gids), _p(offsets), _p(n_keys), int(key_capacity), n, Q,
                             C.byref(grid), _p(out), _stream(stream)))
+    return out
+
+
+def wrf_render_complex(rec, gids, offsets, n_keys, key_capacity: int, n: int, Q: int, grid,
+                       out=None, stream=None):
+    """Two channels: out [Q,2,H,W] = magnitude, phase (records with their tail)."""
+    L = _lib.load()
+    if out is None:
+        out = torch.empty((Q, 2, grid.H, grid.W), dtype=torch.float32, device=offsets.device)
+    _lib.check(L.wrf_render_complex(_p(rec), _p(gids), _p(offsets), _p(n_keys), int(key_capacity),
+                                    n, Q, C.byref(grid), _p(out), _stream(stream)))
     return out
 
 
@@ -314,7 +343,9 @@ class Renderer:
     def project(self, scene: DeviceScene, mlp, tx, stream=None):
         L = _lib.load()
         Q = int(tx.shape[0])
-        rec = self._tensor("rec", (Q, scene.n, 8), torch.float32)
+        # 2 channels: the imaginary weights follow the Q x N records
+        buf = self._buf("rec", Q * scene.n * (8 + (scene.channels == 2)) * 4)
+        rec = buf[: Q * scene.n * 32].view(torch.float32).view(Q, scene.n, 8)
         if mlp is None:
             wrf_project(scene, None, Q, self.grid, rec=rec, tile_count=None, stream=stream)
             return rec, None
@@ -328,7 +359,7 @@ class Renderer:
         wrf_project(scene, resid, Q, self.grid, rec=rec, tile_count=None, stream=stream)
         return rec, resid
 
-    def bin_and_render(self, rec, n, Q, stream=None, out=None):
+    def bin_and_render(self, rec, n, Q, stream=None, out=None, channels=1):
         L = _lib.load()
         T = tiles_of(self.grid)
         if self.cap <= 0:
@@ -345,14 +376,14 @@ class Renderer:
                 break
             wrf_status_read(stream)  # clear the recorded overflow
             self.cap = int(need * 1.25) + 1024
-        out = wrf_render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out,
-                         stream=stream)
+        render = wrf_render_complex if channels == 2 else wrf_render
+        out = render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out, stream=stream)
         self.last = dict(rec=rec, gids=gids, offs=offs, n_keys=n_keys, n=n, Q=Q)
         return out
 
     def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None):
         Q = int(tx.shape[0])
         rec, resid = self.project(scene, mlp, tx, stream=stream)
-        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out)
+        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out, channels=scene.channels)
         self.last["resid"] = resid
         return out

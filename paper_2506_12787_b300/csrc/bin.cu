@@ -29,6 +29,7 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;  // 4096
 
+template <bool WRAP>
 __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n, GridView g,
                                                         int C, uint32_t *counts, int *status) {
     extern __shared__ uint32_t hist[];
@@ -41,14 +42,15 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
         size_t r = static_cast<size_t>(q) * n + id;
         float4 a = rec[2 * r], b = rec[2 * r + 1];
         int tx0, tx1, tx2, tx3, ty0, ty1;
-        if (!tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1)) continue;
+        if (!tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1)) continue;
         // with wrap a tile is rendered with the Gaussian's image nearest to
         // it, which needs every footprint narrower than W - tile width
-        if (g.wrap && !(__fmul_rn(2.f, b.z) < static_cast<float>(g.W - g.tw)))
+        if (WRAP && !(__fmul_rn(2.f, b.z) < static_cast<float>(g.W - g.tw)))
             record_status(status, WRF_EUNSUPPORTED);
         for (int ty = ty0; ty <= ty1; ++ty) {
             for (int tx = tx0; tx <= tx1; ++tx) atomicAdd(&hist[ty * g.ntx + tx], 1u);
-            for (int tx = tx2; tx <= tx3; ++tx) atomicAdd(&hist[ty * g.ntx + tx], 1u);
+            if (WRAP)
+                for (int tx = tx2; tx <= tx3; ++tx) atomicAdd(&hist[ty * g.ntx + tx], 1u);
         }
     }
     __syncthreads();
@@ -147,7 +149,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(
     if (blockIdx.x == 0 && threadIdx.x == 0) offsets[QT] = static_cast<uint32_t>(*n_keys);
 }
 
-__global__ void __launch_bounds__(1024) bin_scatter_kernel(const float4 *rec, int n, GridView g,
+template <bool WRAP>
+__global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec, int n, GridView g,
                                                            int C, const uint32_t *excl,
                                                            uint32_t *gids, long long cap,
                                                            const long long *n_keys) {
@@ -164,11 +167,11 @@ __global__ void __launch_bounds__(1024) bin_scatter_kernel(const float4 *rec, in
     if (id < n) {
         size_t r = static_cast<size_t>(q) * n + id;
         float4 a = rec[2 * r], b = rec[2 * r + 1];
-        valid = tile_rect(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
+        valid = tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
     }
     for (int tx = 0; tx < g.ntx; ++tx) {
         uint32_t m = __ballot_sync(0xffffffffu, valid && ((tx >= tx0 && tx <= tx1) ||
-                                                          (tx >= tx2 && tx <= tx3)));
+                                                          (WRAP && tx >= tx2 && tx <= tx3)));
         if (lane == 0) colmask[w * g.ntx + tx] = m;
     }
     for (int ty = 0; ty < g.nty; ++ty) {
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(1024) bin_scatter_kernel(const float4 *rec, in
     const uint32_t below = (1u << lane) - 1u;
     for (int ty = ty0; ty <= ty1; ++ty) {
         uint32_t rm = rowmask[w * g.nty + ty];
-        for (int part = 0; part < 2; ++part) {
+        for (int part = 0; part < (WRAP ? 2 : 1); ++part) {
             const int a = part == 0 ? tx0 : tx2, b = part == 0 ? tx1 : tx3;
             for (int tx = a; tx <= b; ++tx) {
                 int t = ty * g.ntx + tx;
@@ -234,7 +237,12 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
     if (Q == 0) return cudaSuccess;
     if (n > 0) {
         dim3 grid(ws.C, Q);
-        bin_count_kernel<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts, status);
+        if (g.wrap)
+            bin_count_kernel<true><<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts,
+                                                               status);
+        else
+            bin_count_kernel<false><<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts,
+                                                                status);
     } else {
         cudaError_t e = cudaMemsetAsync(ws.chunk_counts, 0, static_cast<size_t>(ws.M) * 4, st);
         if (e != cudaSuccess) return e;
@@ -246,13 +254,12 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
                                                          static_cast<long long>(Q) * g.T, n_keys);
     if (n > 0) {
         size_t smem = scatter_smem(g);
-        cudaError_t e = cudaFuncSetAttribute(bin_scatter_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        auto kern = g.wrap ? bin_scatter_kernel<true> : bin_scatter_kernel<false>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
         dim3 grid(ws.C, Q);
-        bin_scatter_kernel<<<grid, 1024, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap,
-                                                     n_keys);
+        kern<<<grid, 1024, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap, n_keys);
     }
     return cudaGetLastError();
 }

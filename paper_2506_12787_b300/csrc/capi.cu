@@ -74,7 +74,8 @@ bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) %
 wrf_status check_scene(const wrf_scene *s) {
     if (!s) return fail(WRF_EINVAL, "scene is NULL");
     if (s->n < 0) return fail(WRF_EINVAL, "scene.n < 0");
-    if (s->channels != 1) return fail(WRF_EUNSUPPORTED, "only channels == 1 is supported");
+    if (s->channels != 1 && s->channels != 2)
+        return fail(WRF_EUNSUPPORTED, "channels must be 1 or 2");
     if (s->n > 0 && (!s->mean || !s->log_scale || !s->rot || !s->opacity_logit || !s->amp))
         return fail(WRF_EINVAL, "scene array is NULL");
     if (s->n > 0 && (!aligned(s->mean, 8) || !aligned(s->log_scale, 8)))
@@ -144,7 +145,8 @@ wrf_status check_mlp(const wrf_mlp *m, wrf::MlpView *v) {
 }
 
 wrf::SceneView view(const wrf_scene *s) {
-    return wrf::SceneView{s->n, s->mean, s->log_scale, s->rot, s->opacity_logit, s->amp};
+    return wrf::SceneView{s->n, s->mean, s->log_scale, s->rot, s->opacity_logit, s->amp,
+                          s->channels};
 }
 
 bool rows_ok(int n, int Q) { return static_cast<long long>(n) * Q < (1ll << 31); }
@@ -431,6 +433,27 @@ wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *ti
     return WRF_OK;
 }
 
+wrf_status wrf_render_complex(const float *rec, const uint32_t *gids,
+                              const uint32_t *tile_offsets, const int64_t *n_keys,
+                              int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
+                              float *out, void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n < 0 || Q < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (Q == 0) return WRF_OK;
+    if (!tile_offsets || !n_keys || !out) return fail(WRF_EINVAL, "NULL pointer");
+    if (!aligned(out, 16) || (n > 0 && !aligned(rec, 16)))
+        return fail(WRF_EINVAL, "out / rec must be 16-byte aligned");
+    cudaError_t e = wrf::launch_render_complex(
+        reinterpret_cast<const float4 *>(rec), gids, tile_offsets,
+        reinterpret_cast<const long long *>(n_keys), key_capacity, n, Q, g, out, status_ptr(),
+        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "render_complex");
+    return WRF_OK;
+}
+
 wrf_status wrf_render_backward(const float *rec, const uint32_t *gids,
                                const uint32_t *tile_offsets, const int64_t *n_keys,
                                int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
@@ -458,6 +481,8 @@ wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int3
                                 void *stream) {
     wrf_status s;
     if ((s = check_scene(scene)) != WRF_OK) return s;
+    if (scene->channels != 1)
+        return fail(WRF_EUNSUPPORTED, "the backward takes one channel");
     if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
     if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
     if (scene->n == 0) return WRF_OK;
@@ -484,6 +509,8 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
     wrf::GridView g{};
     wrf::MlpView m{};
     if ((s = check_scene(scene)) != WRF_OK) return s;
+    if (scene->channels != 1)
+        return fail(WRF_EUNSUPPORTED, "the backward takes one channel");
     if ((s = check_mlp(mlp, &m)) != WRF_OK) return s;
     if ((s = check_grid(grid, &g)) != WRF_OK) return s;
     if (Q < 0) return fail(WRF_EINVAL, "Q < 0");

@@ -118,9 +118,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // tx2 > tx3, unless a wrapped footprint crosses the seam).  Every step is an
 // exactly rounded FP32 operation so the result is a fixed integer function of
 // the stored record.
+// WRAP: whether g.wrap is set, as a compile-time flag for the binning
+// kernels (the general form below reads it at run time).
+template <bool WRAP>
+__device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float ry,
+                                            const GridView &g, int &tx0, int &tx1, int &tx2,
+                                            int &tx3, int &ty0, int &ty1);
+
 __device__ __forceinline__ bool tile_rect(float mx, float my, float rx, float ry,
                                           const GridView &g, int &tx0, int &tx1, int &tx2,
                                           int &tx3, int &ty0, int &ty1) {
+    return g.wrap ? tile_rect_t<true>(mx, my, rx, ry, g, tx0, tx1, tx2, tx3, ty0, ty1)
+                  : tile_rect_t<false>(mx, my, rx, ry, g, tx0, tx1, tx2, tx3, ty0, ty1);
+}
+
+template <bool WRAP>
+__device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float ry,
+                                            const GridView &g, int &tx0, int &tx1, int &tx2,
+                                            int &tx3, int &ty0, int &ty1) {
     tx2 = 1;
     tx3 = 0;
     const float ylo = __fsub_rn(my, ry), yhi = __fadd_rn(my, ry);
@@ -131,7 +146,7 @@ __device__ __forceinline__ bool tile_rect(float mx, float my, float rx, float ry
     ty0 = static_cast<int>(ay) / g.th;
     ty1 = static_cast<int>(by) / g.th;
     const float xlo = __fsub_rn(mx, rx), xhi = __fadd_rn(mx, rx);
-    if (!g.wrap) {
+    if (!WRAP) {
         const float wm = static_cast<float>(g.W - 1);
         if (!(xhi >= 0.f) || !(xlo <= wm)) return false;
         const float ax = ceilf(fmaxf(xlo, 0.f)), bx = floorf(fminf(xhi, wm));
@@ -183,17 +198,26 @@ __device__ __forceinline__ float nearest_image_x(float mx, float xc, const GridV
 // ------------------------------------------------------------- projection
 struct SceneView {
     int n;
-    const float *mean, *log_scale, *rot, *opacity_logit, *amp;
+    const float *mean, *log_scale, *rot, *opacity_logit, *amp;  // amp [n][channels]
+    int channels;  // 1, or 2 (real and imaginary amplitude)
 };
 
-// Reference-frame parameters of one Gaussian.
+// Reference-frame parameters of one Gaussian (amp_im = 0 with one channel).
 struct GaussParams {
-    float mx, my, rot, ls1, ls2, op, amp;
+    float mx, my, rot, ls1, ls2, op, amp, amp_im;
 };
 __device__ __forceinline__ GaussParams load_params(const SceneView &s, int n) {
     const float2 m = reinterpret_cast<const float2 *>(s.mean)[n];
     const float2 ls = reinterpret_cast<const float2 *>(s.log_scale)[n];
-    return GaussParams{m.x, m.y, s.rot[n], ls.x, ls.y, s.opacity_logit[n], s.amp[n]};
+    const float *a = s.amp + static_cast<size_t>(n) * s.channels;
+    return GaussParams{m.x, m.y, s.rot[n], ls.x, ls.y, s.opacity_logit[n], a[0],
+                       s.channels == 2 ? a[1] : 0.f};
+}
+
+// Weight of the second (imaginary) channel: sigmoid(a) * amp_im, stored by
+// the record writers in the tail after the Q x N records ([Q][N] floats).
+__device__ __forceinline__ float weight_im(const GaussParams &p) {
+    return p.amp_im / (1.f + expf(-p.op));
 }
 
 // Deform a Gaussian by its residual (Eq. 12) and project it to a record:

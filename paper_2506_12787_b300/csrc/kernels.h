@@ -102,6 +102,12 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
 cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                           const long long *n_keys, long long cap, int n, int Q,
                           const GridView &g, float *out, int *status, cudaStream_t st);
+// Two channels (records followed by [Q][N] imaginary weights): out
+// [Q][2][H][W] = magnitude, phase.
+cudaError_t launch_render_complex(const float4 *rec, const uint32_t *gids,
+                                  const uint32_t *offsets, const long long *n_keys, long long cap,
+                                  int n, int Q, const GridView &g, float *out, int *status,
+                                  cudaStream_t st);
 cudaError_t launch_render_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                               const long long *n_keys, long long cap, int n, int Q,
                               const GridView &g, const float *dA, float *d_rec, int *status,

@@ -16,7 +16,8 @@ constexpr int kRows = 32;
 
 __global__ void __launch_bounds__(128) mlp_f32_kernel(SceneView s, MlpView m, GridView g, int Q,
                                                       DeformWs ws, int mode, float *resid,
-                                                      float4 *rec, uint32_t *count) {
+                                                      float4 *rec, uint32_t *count,
+                                                      float *rec_im) {
     extern __shared__ __align__(16) float smem[];
     float *act0 = smem;                                   // [128][32]
     float *act1 = act0 + WRF_HIDDEN * kRows;              // [128][32]
@@ -98,9 +99,11 @@ __global__ void __launch_bounds__(128) mlp_f32_kernel(SceneView s, MlpView m, Gr
     } else {
         int n = static_cast<int>(row % s.n);
         float4 a, b;
-        uint32_t c = project_one(s, n, o[0], o[1], o[2], o[3], o[4], g, a, b);
+        const GaussParams p = load_params(s, n);
+        uint32_t c = project_params(p, o[0], o[1], o[2], o[3], o[4], g, a, b);
         rec[2 * row] = a;
         rec[2 * row + 1] = b;
+        if (rec_im) rec_im[row] = weight_im(p);
         if (count) count[row] = c;
     }
 }
@@ -117,8 +120,11 @@ cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView 
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     long long blocks = (rows + kRows - 1) / kRows;
+    // two channels: the imaginary weights follow the Q x N records
+    float *rec_im = (mode == 1 && s.channels == 2) ? reinterpret_cast<float *>(rec + 2 * rows)
+                                                   : nullptr;
     mlp_f32_kernel<<<static_cast<unsigned>(blocks), 128, smem, st>>>(s, m, g, Q, ws, mode, resid,
-                                                                     rec, count);
+                                                                     rec, count, rec_im);
     return cudaGetLastError();
 }
 

@@ -248,6 +248,7 @@ struct TcArgs {
     float *resid;
     float4 *rec;
     uint32_t *count;
+    float *rec_im;           // two channels: imaginary weights after the records
     int *status;
 };
 
@@ -442,6 +443,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 uint32_t c = project_params(pcur, d0, d1, d2, d3, d4, a.g, r0, r1);
                 a.rec[2 * row] = r0;
                 a.rec[2 * row + 1] = r1;
+                if (a.rec_im) a.rec_im[row] = weight_im(pcur);
                 if (a.count) a.count[row] = c;
             }
         }
@@ -482,6 +484,7 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
     a.resid = resid;
     a.rec = rec;
     a.count = count;
+    a.rec_im = (mode == 1 && s.channels == 2) ? reinterpret_cast<float *>(rec + 2 * rows) : nullptr;
     a.status = status;
     const size_t smem = smem_bytes(nh);
     cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

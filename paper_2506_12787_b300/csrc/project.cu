@@ -7,7 +7,7 @@ namespace wrf {
 namespace {
 
 __global__ void project_kernel(SceneView s, const float *resid, int Q, GridView g, float4 *rec,
-                               uint32_t *count) {
+                               uint32_t *count, float *rec_im) {
     const long long rows = static_cast<long long>(Q) * s.n;
     for (long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; r < rows;
          r += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -18,9 +18,11 @@ __global__ void project_kernel(SceneView s, const float *resid, int Q, GridView 
             for (int j = 0; j < 5; ++j) d[j] = resid[r * 5 + j];
         }
         float4 a, b;
-        uint32_t c = project_one(s, n, d[0], d[1], d[2], d[3], d[4], g, a, b);
+        const GaussParams p = load_params(s, n);
+        uint32_t c = project_params(p, d[0], d[1], d[2], d[3], d[4], g, a, b);
         rec[2 * r] = a;
         rec[2 * r + 1] = b;
+        if (rec_im) rec_im[r] = weight_im(p);
         if (count) count[r] = c;
     }
 }
@@ -92,7 +94,10 @@ cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const 
     if (rows == 0) return cudaSuccess;
     long long blocks = (rows + 255) / 256;
     if (blocks > 148 * 64) blocks = 148 * 64;
-    project_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(s, resid, Q, g, rec, count);
+    // two channels: the imaginary weights follow the Q x N records
+    float *rec_im = s.channels == 2 ? reinterpret_cast<float *>(rec + 2 * rows) : nullptr;
+    project_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(s, resid, Q, g, rec, count,
+                                                                  rec_im);
     return cudaGetLastError();
 }
 

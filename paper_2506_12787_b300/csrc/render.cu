@@ -64,11 +64,14 @@ struct FwdSmem {
     static constexpr size_t bytes = lists + NW * B * 2;
 };
 
-template <int TW, int TH>
+// CH = 1: one channel, out [Q][H][W].  CH = 2: real and imaginary channels
+// (weights w from the records, w_im from rec_im [Q][N]) summed with one ex2
+// per pixel and Gaussian, out [Q][2][H][W] = magnitude, phase (Sec. 6.1).
+template <int TW, int TH, int CH, bool WRAP>
 __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
-    GridView g, float ncut, float *__restrict__ out, int *status) {
+    GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im) {
     constexpr int NT = TW * TH / 2, B = NT, NW = NT / 32;
     constexpr int NSX = TW / 8;  // warp blocks of 8 x 8 pixels: NSX across, TH/8 down
     static_assert(NW == NSX * (TH / 8), "one 8x8 pixel block per warp");
@@ -82,6 +85,7 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int abort_flag;
     __shared__ __align__(16) float stile[TH][TW];
+    __shared__ __align__(16) float stile_im[CH == 2 ? TH : 1][CH == 2 ? TW : 1];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.x, q = blockIdx.y;
@@ -101,6 +105,8 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     const int total = static_cast<int>(s1 - s0);
     const int nb = (total + B - 1) / B;
     const float4 *qrec = rec + static_cast<size_t>(q) * n * 2;
+    const float *qim = CH == 2 ? rec_im + static_cast<size_t>(q) * n : nullptr;
+    float wim0 = 0.f, wim1 = 0.f;  // imaginary weights of this thread's record, per buffer
 
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -115,13 +121,14 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         if (tid < total - b * B) {
             const uint32_t gid = gids[s0 + b * B + tid];
             bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
+            if (CH == 2) (b == 0 ? wim0 : wim1) = qim[gid];
         }
     }
     // this thread's Gaussian id of batch b + 2, loaded one batch early so the
     // copy is issued without waiting on the index load
     uint32_t gnext = tid < total - 2 * B ? gids[s0 + 2 * B + tid] : 0u;
 
-    float acc0 = 0.f, acc1 = 0.f;
+    float acc0 = 0.f, acc1 = 0.f, acc0i = 0.f, acc1i = 0.f;
     uint16_t *mylist = lists + warp * B;
     int b = 0;
     for (; b < nb; ++b) {
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         if (tid < cnt) {
             const float4 r0 = raw[(buf * B + tid) * 2], r1 = raw[(buf * B + tid) * 2 + 1];
             // with azimuth wrap, the image of the Gaussian nearest to this tile
-            const float mx = nearest_image_x(r0.x, xcen, g);
+            const float mx = WRAP ? nearest_image_x(r0.x, xcen, g) : r0.x;
             const float ux = mx - xcen, uy = r0.y - ycen;
             const float h1 = fmaf(r0.z, ux, r0.w * uy), h2 = fmaf(r0.w, ux, r1.x * uy);
             const float c0 = -fmaf(ux, h1, uy * h2);
@@ -154,7 +161,7 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
                     make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
                                 fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[tid] = make_float4(-r0.z, -r0.z, r1.y, 0.f);
+            gcoef[tid] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim1 : wim0) : 0.f);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
@@ -174,6 +181,7 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         // raw[buf] is consumed: the copies of batch b+2 can land there now
         if (b + 2 < nb && tid < total - (b + 2) * B) {
             bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gnext), 32, &bar[buf]);
+            if (CH == 2) (buf ? wim1 : wim0) = qim[gnext];
             if (tid < total - (b + 3) * B) gnext = gids[s0 + (b + 3) * B + tid];
         }
         // ---- this warp's list: records touching its block, ascending index
@@ -199,8 +207,21 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             const float4 cw = *reinterpret_cast<const float4 *>(gcb + o);    // c3, c3, w, 0
             const float2 t = fma2(make_float2(cw.x, cw.y), lx2, make_float2(ab.z, ab.w));
             const float2 nq = fma2(t, lx2, make_float2(ab.x, ab.y));
-            if (nq.x >= ncut) acc0 = fmaf(cw.z, ex2_approx(nq.x), acc0);
-            if (nq.y >= ncut) acc1 = fmaf(cw.z, ex2_approx(nq.y), acc1);
+            if (CH == 1) {
+                if (nq.x >= ncut) acc0 = fmaf(cw.z, ex2_approx(nq.x), acc0);
+                if (nq.y >= ncut) acc1 = fmaf(cw.z, ex2_approx(nq.y), acc1);
+            } else {
+                if (nq.x >= ncut) {
+                    const float e = ex2_approx(nq.x);
+                    acc0 = fmaf(cw.z, e, acc0);
+                    acc0i = fmaf(cw.w, e, acc0i);
+                }
+                if (nq.y >= ncut) {
+                    const float e = ex2_approx(nq.y);
+                    acc1 = fmaf(cw.z, e, acc1);
+                    acc1i = fmaf(cw.w, e, acc1i);
+                }
+            }
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
         if (abort_flag) break;
@@ -211,22 +232,34 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
         return;
     }
-    stile[pyl][pxl] = acc0;
-    stile[pyl + 4][pxl] = acc1;
+    if (CH == 1) {
+        stile[pyl][pxl] = acc0;
+        stile[pyl + 4][pxl] = acc1;
+    } else {
+        // magnitude and phase of re + i im (arg 0 = 0)
+        stile[pyl][pxl] = sqrtf(fmaf(acc0, acc0, acc0i * acc0i));
+        stile[pyl + 4][pxl] = sqrtf(fmaf(acc1, acc1, acc1i * acc1i));
+        stile_im[pyl][pxl] = atan2f(acc0i, acc0);
+        stile_im[pyl + 4][pxl] = atan2f(acc1i, acc1);
+    }
     __syncthreads();
-    float *oq = out + static_cast<size_t>(q) * g.H * g.W;
+    const size_t plane = static_cast<size_t>(g.H) * g.W;
     const bool vec = (g.W & 3) == 0;
-    for (int i = tid; i < TH * TW / 4; i += NT) {
-        const int r = i / (TW / 4), c4 = (i % (TW / 4)) * 4;
-        const int y = y0 + r, x = x0 + c4;
-        if (y >= g.H || x >= g.W) continue;
-        const float4 v = *reinterpret_cast<const float4 *>(&stile[r][c4]);
-        float *dst = oq + static_cast<size_t>(y) * g.W + x;
-        if (vec) {
-            *reinterpret_cast<float4 *>(dst) = v;
-        } else {
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-            for (int k = 0; k < 4 && x + k < g.W; ++k) dst[k] = vv[k];
+    for (int c = 0; c < CH; ++c) {
+        float *oq = out + (static_cast<size_t>(q) * CH + c) * plane;
+        float(*st)[TW] = c == 0 ? stile : reinterpret_cast<float(*)[TW]>(stile_im);
+        for (int i = tid; i < TH * TW / 4; i += NT) {
+            const int r = i / (TW / 4), c4 = (i % (TW / 4)) * 4;
+            const int y = y0 + r, x = x0 + c4;
+            if (y >= g.H || x >= g.W) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(&st[r][c4]);
+            float *dst = oq + static_cast<size_t>(y) * g.W + x;
+            if (vec) {
+                *reinterpret_cast<float4 *>(dst) = v;
+            } else {
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+                for (int k = 0; k < 4 && x + k < g.W; ++k) dst[k] = vv[k];
+            }
         }
     }
 }
@@ -290,19 +323,35 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int CH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        float *out, int *status, cudaStream_t st) {
     const size_t smem = FwdSmem<TW * TH / 2, TH>::bytes;
-    cudaError_t e = cudaFuncSetAttribute(render_kernel<TW, TH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto kern = g.wrap ? render_kernel<TW, TH, CH, true> : render_kernel<TW, TH, CH, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     dim3 grid(g.T, Q);
-    render_kernel<TW, TH><<<grid, TW * TH / 2, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                                       -g.q_cut * kHalfLog2e, out, status);
+    // two channels: the imaginary weights follow the Q x N records
+    const float *rec_im =
+        CH == 2 ? reinterpret_cast<const float *>(rec + 2 * static_cast<size_t>(Q) * n) : nullptr;
+    kern<<<grid, TW * TH / 2, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
+                                          -g.q_cut * kHalfLog2e, out, status, rec_im);
     return cudaGetLastError();
+}
+
+template <int CH>
+cudaError_t launch_any(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
+                       const long long *n_keys, long long cap, int n, int Q, const GridView &g,
+                       float *out, int *status, cudaStream_t st) {
+    if (Q == 0) return cudaSuccess;
+    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    return cudaErrorInvalidValue;
 }
 
 template <int TW, int TH>
@@ -325,13 +374,14 @@ bool render_config_supported(int tw, int th) {
 cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                           const long long *n_keys, long long cap, int n, int Q,
                           const GridView &g, float *out, int *status, cudaStream_t st) {
-    if (Q == 0) return cudaSuccess;
-    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    return cudaErrorInvalidValue;
+    return launch_any<1>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+}
+
+cudaError_t launch_render_complex(const float4 *rec, const uint32_t *gids,
+                                  const uint32_t *offsets, const long long *n_keys, long long cap,
+                                  int n, int Q, const GridView &g, float *out, int *status,
+                                  cudaStream_t st) {
+    return launch_any<2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
 }
 
 cudaError_t launch_render_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
     float *wbuf = smem;
     float *hin = smem + kKChunk * WRF_HIDDEN, *hout = hin + WRF_HIDDEN * kPitch;
     __shared__ float4 recs[kRssiMaxN][2];
+    __shared__ float wims[kRssiMaxN];  // imaginary weights (two channels)
     __shared__ float dout[kRssiMaxN][8];
     __shared__ float red[kThreads];
     const int q = blockIdx.x, tid = threadIdx.x, N = a.s.n;
@@ -134,10 +135,12 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
     __syncthreads();
     if (tid < N) {
         float4 r0, r1;
-        project_params(load_params(a.s, tid), dout[tid][0], dout[tid][1], dout[tid][2],
-                       dout[tid][3], dout[tid][4], a.g, r0, r1);
+        const GaussParams p = load_params(a.s, tid);
+        project_params(p, dout[tid][0], dout[tid][1], dout[tid][2], dout[tid][3], dout[tid][4],
+                       a.g, r0, r1);
         recs[tid][0] = r0;
         recs[tid][1] = r1;
+        wims[tid] = weight_im(p);
     }
     __syncthreads();
     // 4. every pixel against every Gaussian (ascending id), footprint test
@@ -147,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
     float part = 0.f;
     for (int p = tid; p < HW; p += kThreads) {
         const float x = static_cast<float>(p % a.g.W), y = static_cast<float>(p / a.g.W);
-        float acc = 0.f;
+        float acc = 0.f, acc_im = 0.f;
         for (int n = 0; n < N; ++n) {
             const float4 r0 = recs[n][0], r1 = recs[n][1];
             float dx = x - r0.x;
@@ -155,10 +158,16 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
             if (a.g.wrap) dx -= static_cast<float>(a.g.W) * rintf(dx / static_cast<float>(a.g.W));
             const float t = fmaf(r0.z, dx, 2.f * r0.w * dy);
             const float nq = -fmaf(dx, t, r1.x * dy * dy);
-            if (nq >= ncut) acc = fmaf(r1.y, ex2_approx(nq), acc);
+            if (nq >= ncut) {
+                const float e = ex2_approx(nq);
+                acc = fmaf(r1.y, e, acc);
+                acc_im = fmaf(wims[n], e, acc_im);
+            }
         }
-        if (a.map) a.map[static_cast<size_t>(q) * HW + p] = acc;
-        part += fabsf(acc);
+        // magnitude of the (one- or two-channel) value
+        const float mag = a.s.channels == 2 ? sqrtf(fmaf(acc, acc, acc_im * acc_im)) : fabsf(acc);
+        if (a.map) a.map[static_cast<size_t>(q) * HW + p] = a.s.channels == 2 ? mag : acc;
+        part += mag;
     }
     // 5. fixed-order reduction
     red[tid] = part;

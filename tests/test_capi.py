@@ -49,8 +49,10 @@ def test_host_validation_rejects_bad_arguments(lib):
     g = _lib.Grid(90, 360, 16, 16, 9.0)
     # NULL outputs with Q > 0
     assert lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None) == _lib.WRF_EINVAL
-    s = _lib.Scene(10, 2, None, None, None, None, None)  # two channels: unsupported
+    s = _lib.Scene(10, 3, None, None, None, None, None)  # three channels: unsupported
     assert lib.wrf_project(C.byref(s), None, 1, C.byref(g), None, None, None) == _lib.WRF_EUNSUPPORTED
+    s = _lib.Scene(10, 2, None, None, None, None, None)  # two channels, NULL arrays
+    assert lib.wrf_project(C.byref(s), None, 1, C.byref(g), None, None, None) == _lib.WRF_EINVAL
     m = _lib.Mlp()
     m.n_layers = 5
     m.L_mean, m.L_tx = 6, 10
