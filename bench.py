@@ -72,6 +72,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--graph", type=int, default=1, help="replay the step as a CUDA graph")
     p.add_argument("--serving", type=int, default=1, help="also run the serving workload")
+    p.add_argument("--wrap", action="store_true", help="azimuth wrap (0 = 360 degrees)")
+    p.add_argument("--channels", type=int, default=1, choices=[1, 2],
+                   help="2: real and imaginary amplitude, magnitude/phase output")
     p.add_argument("--rate", type=float, default=50000.0, help="serving arrivals per second")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--serve-warmup", type=float, default=1.0)
@@ -102,9 +105,11 @@ def aggregate(seconds_local, units_local, dist=None):
     return tmax, utot, utot / tmax
 
 
-def make_inputs(workload, rank):
+def make_inputs(workload, rank, channels=1):
     N, H, W, Q, lsm, lss = WORKLOADS[workload]
     sc = synth.make_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
+    if channels == 2:
+        sc = synth.complex_amplitudes(sc, seed=0)
     m = synth.make_mlp(seed=0)
     tx = synth.make_tx(Q, seed=1 + rank)
     return sc, m, tx, (N, H, W, Q)
@@ -117,7 +122,9 @@ def config_of(args, shape, extra=None):
          "mlp": "89-128x4-5 ReLU, " + ("BF16 tcgen05 / FP32 acc" if args.precision == "bf16"
                                        else "FP32 CUDA cores"),
          "q_cut": Q_CUT, "tile": args.tile, "l2": "256 MB buffer rewritten between timed steps",
-         "parallelism": f"replicas x{args.gpus}"}
+         "parallelism": f"replicas x{args.gpus}", "wrap": bool(args.wrap),
+         "channels": args.channels,
+         "output": "magnitude and phase [Q,2,H,W]" if args.channels == 2 else "spectra [Q,H,W]"}
     if extra:
         c.update(extra)
     return c
@@ -188,7 +195,7 @@ def measured_peaks():
                 "sm_max_mhz": 2032.0}, "fallback"
 
 
-def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18):
+def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18, wrap=False):
     """Number of (pixel, record) pairs with q <= q_cut over all records
     [Q,N,8]: the evaluations the order-free sum needs (Eq. 9), counted per
     record row by row from the ellipse's exact x-interval (torch, device).
@@ -218,9 +225,13 @@ def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18):
         sq = torch.sqrt(torch.clamp(disc, min=0))
         lo = mx[:, None] + (-b[:, None] * dy - sq) / a[:, None]
         hi = mx[:, None] + (-b[:, None] * dy + sq) / a[:, None]
-        lo = torch.clamp(torch.ceil(lo), min=0)
-        hi = torch.clamp(torch.floor(hi), max=W - 1)
-        cnt = torch.where(ok, torch.clamp(hi - lo + 1, min=0), torch.zeros_like(lo))
+        if wrap:  # columns modulo W
+            cnt = torch.clamp(torch.floor(hi) - torch.ceil(lo) + 1, min=0, max=W)
+        else:
+            lo = torch.clamp(torch.ceil(lo), min=0)
+            hi = torch.clamp(torch.floor(hi), max=W - 1)
+            cnt = torch.clamp(hi - lo + 1, min=0)
+        cnt = torch.where(ok, cnt, torch.zeros_like(cnt))
         total += int(cnt.sum().item())
     return total
 
@@ -231,10 +242,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    sc, m, tx, shape = make_inputs(args.workload, 0)
+    sc, m, tx, shape = make_inputs(args.workload, 0, args.channels)
     N, H, W, Q = shape
     S = max(1, min(Q, 4 if args.workload != "rssi" else 256))
-    run = oracle.rssi if args.workload == "rssi" else oracle.forward
+    if args.workload == "rssi":
+        run = oracle.rssi
+    else:
+        f = oracle.forward_complex if args.channels == 2 else oracle.forward
+
+        def run(sc_, m_, tx_, H_, W_, q_):
+            return f(sc_, m_, tx_, H_, W_, q_, wrap=args.wrap)
     unit = "rssi/s" if args.workload == "rssi" else "spectra/s"
     for i in range(args.warmup):
         run(sc, m, tx[(i * S) % Q:(i * S) % Q + S], H, W, Q_CUT)
@@ -265,11 +282,12 @@ def cpu_baseline(args, sc, m, tx, shape):
     import oracle
     N, H, W, Q = shape
     t0 = time.perf_counter()
-    oracle.forward(sc, m, tx[:1], H, W, Q_CUT)  # builds, pages in, and times one query
+    fwd = oracle.forward_complex if args.channels == 2 else oracle.forward
+    fwd(sc, m, tx[:1], H, W, Q_CUT, wrap=args.wrap)  # builds, pages in, and times one query
     t1 = time.perf_counter() - t0
     S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-3)))))
     t0 = time.perf_counter()
-    oracle.forward(sc, m, tx[:S], H, W, Q_CUT)
+    fwd(sc, m, tx[:S], H, W, Q_CUT, wrap=args.wrap)
     dt = time.perf_counter() - t0
     return {"value": S / dt, "unit": "spectra/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"first {S} of {Q} TX queries of the workload, {N} Gaussians, {W}x{H}, "
@@ -622,7 +640,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc, m, tx_np, shape = make_inputs(args.workload, rank)
+    sc, m, tx_np, shape = make_inputs(args.workload, rank, args.channels)
     N, H, W, Q = shape
     prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
     ds = api.DeviceScene.from_host(sc, dev)
@@ -631,11 +649,11 @@ def main():
     tune_ms = None
     if args.tile == "auto":
         from paper_2506_12787_b300 import autotune
-        (tw, th), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT)
+        (tw, th), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
     else:
         tw, th = (int(v) for v in args.tile.split("x"))
     args.tile = f"{tw}x{th}"
-    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    grid = api.make_grid(H, W, tw, th, Q_CUT, wrap=args.wrap)
     stream = torch.cuda.Stream(device=dev)
     fw = BatchedForward(ds, dm, grid, Q, dev)
     with torch.cuda.stream(stream):
@@ -731,10 +749,12 @@ def main():
     peaks, peak_src = measured_peaks()
     dom = max(stage, key=stage.get)
     if dom == "render":
-        E = count_in_cutoff(fw.rec, H, W, Q_CUT)
+        E = count_in_cutoff(fw.rec, H, W, Q_CUT, wrap=args.wrap)
+        # two channels: one more FMA per evaluation (the imaginary weight)
+        fl_eval = RAST_FLOP_PER_EVAL + 2 * (args.channels - 1)
         fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
         roof = {"kernel": "render_kernel", "bound": "alu",
-                "achieved": RAST_FLOP_PER_EVAL * E / (stage["render"] * 1e-3) / 1e12,
+                "achieved": fl_eval * E / (stage["render"] * 1e-3) / 1e12,
                 "peak": fp32_peak, "unit": "TFLOP/s",
                 "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
                 "evals_in_cutoff": E}

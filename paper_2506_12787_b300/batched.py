@@ -21,7 +21,7 @@ import torch
 
 from . import _lib
 from .api import (DeviceMLP, DeviceScene, _p, _stream, tiles_of, wrf_bin, wrf_deform_project,
-                  wrf_render, wrf_status_read)
+                  wrf_render, wrf_render_complex, wrf_status_read, alloc_records)
 
 
 class BatchedForward:
@@ -34,14 +34,17 @@ class BatchedForward:
         n = scene.n
         self.T = tiles_of(grid)
         self._mc = mlp.c()
-        self.rec = torch.empty((self.Q, n, 8), dtype=torch.float32, device=self.device)
+        self.channels = scene.channels
+        self.rec = alloc_records(self.Q, n, self.channels, self.device)
         self.dws = torch.empty(max(256, L.wrf_deform_workspace_size(n, self.Q, C.byref(self._mc))),
                                dtype=torch.uint8, device=self.device)
         self.bws = torch.empty(max(256, L.wrf_bin_workspace_size(n, self.Q, C.byref(grid))),
                                dtype=torch.uint8, device=self.device)
         self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
         self.offs = torch.empty(self.Q * self.T + 1, dtype=torch.int32, device=self.device)
-        self.out = torch.empty((self.Q, grid.H, grid.W), dtype=torch.float32, device=self.device)
+        # one channel: spectra [Q,H,W]; two: [Q,2,H,W] = magnitude, phase
+        shape = (self.Q, grid.H, grid.W) if self.channels == 1 else (self.Q, 2, grid.H, grid.W)
+        self.out = torch.empty(shape, dtype=torch.float32, device=self.device)
         self.cap = 0
         self.gids = None
         self._alloc_keys(int(key_capacity))
@@ -65,7 +68,8 @@ class BatchedForward:
                 n_keys=self.n_keys, offsets=self.offs, ws=self.bws, stream=stream)
 
     def render(self, stream=None, out=None):
-        return wrf_render(self.rec, self.gids, self.offs, self.n_keys, self.cap, self.scene.n,
+        render = wrf_render_complex if self.channels == 2 else wrf_render
+        return render(self.rec, self.gids, self.offs, self.n_keys, self.cap, self.scene.n,
                           self.Q, self.grid, out=self.out if out is None else out, stream=stream)
 
     def run(self, tx, stream=None, out=None):

@@ -162,9 +162,12 @@ __device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float 
         tx1 = g.ntx - 1;
         return true;
     }
-    const long long c0 = static_cast<long long>(lo), c1 = static_cast<long long>(hi);
-    const int a = static_cast<int>(((c0 % g.W) + g.W) % g.W);
-    const int b = static_cast<int>(((c1 % g.W) + g.W) % g.W);
+    // columns modulo W (|column| < 2^24 for any footprint the rasteriser can
+    // use, so 32-bit integers are exact)
+    const int c0 = static_cast<int>(lo), c1 = static_cast<int>(hi);
+    int a = c0 % g.W, b = c1 % g.W;
+    if (a < 0) a += g.W;
+    if (b < 0) b += g.W;
     if (a <= b) {
         tx0 = a / g.tw;
         tx1 = b / g.tw;
@@ -220,13 +223,20 @@ __device__ __forceinline__ float weight_im(const GaussParams &p) {
     return p.amp_im / (1.f + expf(-p.op));
 }
 
+// Number of tiles a record's footprint rectangle covers.
+__device__ __forceinline__ uint32_t record_tiles(const float4 &r0, const float4 &r1,
+                                                 const GridView &g) {
+    int a, b, a2, b2, c, d;
+    if (!tile_rect(r0.x, r0.y, r1.z, r1.w, g, a, b, a2, b2, c, d)) return 0u;
+    return static_cast<uint32_t>(tile_cols(a, b, a2, b2) * (d - c + 1));
+}
+
 // Deform a Gaussian by its residual (Eq. 12) and project it to a record:
 // centre, log2(e)/2-scaled inverse covariance of R(th) diag(s1^2, s2^2) R^T,
-// weight sigmoid(a) * amp (Sec. 4.1) and footprint half-widths; returns the
-// number of tiles its footprint rectangle covers.
-__device__ __forceinline__ uint32_t project_params(const GaussParams &p, float d0, float d1,
-                                                   float d2, float d3, float d4,
-                                                   const GridView &g, float4 &r0, float4 &r1) {
+// weight sigmoid(a) * amp (Sec. 4.1) and footprint half-widths.
+__device__ __forceinline__ void project_geom(const GaussParams &p, float d0, float d1, float d2,
+                                             float d3, float d4, const GridView &g, float4 &r0,
+                                             float4 &r1) {
     float mx = p.mx + d0, my = p.my + d1;
     float th = p.rot + d2;
     float l1 = p.ls1 + d3, l2 = p.ls2 + d4;
@@ -241,16 +251,16 @@ __device__ __forceinline__ uint32_t project_params(const GaussParams &p, float d
     float rx = sqrtf(g.q_cut * sxx), ry = sqrtf(g.q_cut * syy);
     r0 = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
     r1 = make_float4(C * kHalfLog2e, w, rx, ry);
-    int a, b, a2, b2, c, d;
-    if (!tile_rect(mx, my, rx, ry, g, a, b, a2, b2, c, d)) return 0u;
-    return static_cast<uint32_t>(tile_cols(a, b, a2, b2) * (d - c + 1));
 }
 
-__device__ __forceinline__ uint32_t project_one(const SceneView &s, int n, float d0, float d1,
-                                                float d2, float d3, float d4, const GridView &g,
-                                                float4 &r0, float4 &r1) {
-    return project_params(load_params(s, n), d0, d1, d2, d3, d4, g, r0, r1);
+// project_geom, returning the number of tiles the footprint covers.
+__device__ __forceinline__ uint32_t project_params(const GaussParams &p, float d0, float d1,
+                                                   float d2, float d3, float d4,
+                                                   const GridView &g, float4 &r0, float4 &r1) {
+    project_geom(p, d0, d1, d2, d3, d4, g, r0, r1);
+    return record_tiles(r0, r1, g);
 }
+
 
 // ------------------------------------------------------ positional encoding
 // Eq. 15 applies sin and cos to 2^k pi x for k up to L-1 (2^9 pi at L = 10):

@@ -100,11 +100,11 @@ __global__ void __launch_bounds__(128) mlp_f32_kernel(SceneView s, MlpView m, Gr
         int n = static_cast<int>(row % s.n);
         float4 a, b;
         const GaussParams p = load_params(s, n);
-        uint32_t c = project_params(p, o[0], o[1], o[2], o[3], o[4], g, a, b);
+        project_geom(p, o[0], o[1], o[2], o[3], o[4], g, a, b);
         rec[2 * row] = a;
         rec[2 * row + 1] = b;
         if (rec_im) rec_im[row] = weight_im(p);
-        if (count) count[row] = c;
+        if (count) count[row] = record_tiles(a, b, g);
     }
 }
 

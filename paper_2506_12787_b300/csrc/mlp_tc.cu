@@ -440,11 +440,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 dst[4] = d4;
             } else {
                 float4 r0, r1;
-                uint32_t c = project_params(pcur, d0, d1, d2, d3, d4, a.g, r0, r1);
+                project_geom(pcur, d0, d1, d2, d3, d4, a.g, r0, r1);
                 a.rec[2 * row] = r0;
                 a.rec[2 * row + 1] = r1;
                 if (a.rec_im) a.rec_im[row] = weight_im(pcur);
-                if (a.count) a.count[row] = c;
+                if (a.count) a.count[row] = record_tiles(r0, r1, a.g);
             }
         }
         named_bar(1 + wg, 128);  // TMEM columns, A tile and V image are free again

@@ -19,15 +19,15 @@ __global__ void project_kernel(SceneView s, const float *resid, int Q, GridView 
         }
         float4 a, b;
         const GaussParams p = load_params(s, n);
-        uint32_t c = project_params(p, d[0], d[1], d[2], d[3], d[4], g, a, b);
+        project_geom(p, d[0], d[1], d[2], d[3], d[4], g, a, b);
         rec[2 * r] = a;
         rec[2 * r + 1] = b;
         if (rec_im) rec_im[r] = weight_im(p);
-        if (count) count[r] = c;
+        if (count) count[r] = record_tiles(a, b, g);
     }
 }
 
-// Chain rule of project_one for one row: from dL/d(mx, my, A, B, C, w) to
+// Chain rule of project_geom for one row: from dL/d(mx, my, A, B, C, w) to
 // dL/d(dx, dy, drot, dls1, dls2) and dL/d(opacity_logit, amp).
 //   A = c^2 i1 + s^2 i2, B = cs (i1 - i2), C = s^2 i1 + c^2 i2, i_k = e^{-2 l_k}
 //   dA/dth = -2cs(i1-i2), dB/dth = (c^2-s^2)(i1-i2), dC/dth = 2cs(i1-i2)

@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(kThreads) rssi_kernel(RssiArgs a) {
     if (tid < N) {
         float4 r0, r1;
         const GaussParams p = load_params(a.s, tid);
-        project_params(p, dout[tid][0], dout[tid][1], dout[tid][2], dout[tid][3], dout[tid][4],
-                       a.g, r0, r1);
+        project_geom(p, dout[tid][0], dout[tid][1], dout[tid][2], dout[tid][3], dout[tid][4], a.g,
+                     r0, r1);
         recs[tid][0] = r0;
         recs[tid][1] = r1;
         wims[tid] = weight_im(p);

@@ -111,6 +111,16 @@ def make_mlp(*, L_mean: int = 6, L_tx: int = 10, hidden: int = 128,
     return MLP(Ws, bs, L_mean, L_tx)
 
 
+def complex_amplitudes(scene: Scene, *, seed: int = 0) -> Scene:
+    """Copy of a scene with two-channel amplitudes amp * (cos phi, sin phi),
+    phi ~ U[-pi, pi) (real and imaginary response)."""
+    g = rng(seed + 5000)
+    ph = g.uniform(-math.pi, math.pi, size=scene.amp.shape[0])
+    a = scene.amp.astype(np.float64)
+    amp = np.stack([a * np.cos(ph), a * np.sin(ph)], 1).astype(np.float32)
+    return Scene(scene.mean, scene.log_scale, scene.rot, scene.opacity_logit, amp)
+
+
 def zero_mlp(L_mean: int = 6, L_tx: int = 10, hidden: int = 128,
              n_hidden: int = 4, out: int = 5) -> MLP:
     dims = mlp_dims(L_mean, L_tx, hidden, n_hidden, out)
