@@ -121,6 +121,65 @@ def complex_amplitudes(scene: Scene, *, seed: int = 0) -> Scene:
     return Scene(scene.mean, scene.log_scale, scene.rot, scene.opacity_logit, amp)
 
 
+@dataclasses.dataclass
+class PaperScene:
+    """Primitives of the paper's head, structure of arrays, FP32.
+
+    mu:         [N,2] raw angular centre (u, v) before the tanh map
+    chol:       [N,3] Cholesky entries (l1, l2, l3) of Sigma (pixels)
+    attn_logit: [N]   pre-sigmoid attenuation a
+    psi:        [N,2] complex response (re, im)
+    """
+    mu: np.ndarray
+    chol: np.ndarray
+    attn_logit: np.ndarray
+    psi: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+
+def make_paper_scene(n: int, H: int, W: int, *, ls_mean: float = math.log(3.0),
+                     ls_std: float = 0.3, seed: int = 0) -> PaperScene:
+    """Centres uniform over the map (u = atanh(2x/W - 1)), diagonal Cholesky
+    entries exp(N(ls_mean, ls_std^2)) pixels, off-diagonal N(0, 0.5^2) pixels,
+    attenuation logit N(0,1), response |psi| ~ U(0,1) with a uniform phase."""
+    g = rng(seed + 7000)
+    x = g.uniform(0.0, W, size=n)
+    y = g.uniform(0.0, H, size=n)
+    u = np.arctanh(np.clip(2.0 * x / W - 1.0, -0.999999, 0.999999))
+    v = np.arctanh(np.clip(2.0 * y / H - 1.0, -0.999999, 0.999999))
+    l1 = np.exp(g.normal(ls_mean, ls_std, size=n))
+    l3 = np.exp(g.normal(ls_mean, ls_std, size=n))
+    l2 = g.normal(0.0, 0.5, size=n)
+    a = g.normal(0.0, 1.0, size=n)
+    r = g.uniform(0.0, 1.0, size=n)
+    ph = g.uniform(-math.pi, math.pi, size=n)
+    f = np.float32
+    return PaperScene(np.stack([u, v], 1).astype(f), np.stack([l1, l2, l3], 1).astype(f),
+                      a.astype(f), np.stack([r * np.cos(ph), r * np.sin(ph)], 1).astype(f))
+
+
+def make_paper_mlp(*, L_mean: int = 10, L_tx: int = 6, width: int = 156, n_hidden: int = 8,
+                   skips=(2, 4, 6), gain: float = 0.1, bias_std: float = 0.0,
+                   seed: int = 0) -> MLP:
+    """The paper's deformation network shape: n_hidden layers of `width`, the
+    encoded input concatenated to the activations entering the layers in
+    `skips` (0-based), output 5; Xavier-uniform weights times `gain`."""
+    g = rng(seed + 8000)
+    din = 2 * (2 * L_mean + 1) + 3 * (2 * L_tx + 1)
+    ins = [din] + [width + (din if l in skips else 0) for l in range(1, n_hidden)] + [width]
+    outs = [width] * n_hidden + [5]
+    Ws, bs = [], []
+    for fan_in, fan_out in zip(ins, outs):
+        lim = gain * math.sqrt(6.0 / (fan_in + fan_out))
+        Ws.append(g.uniform(-lim, lim, size=(fan_out, fan_in)).astype(np.float32))
+        bs.append((g.normal(0.0, bias_std, size=fan_out) if bias_std > 0
+                   else np.zeros(fan_out)).astype(np.float32))
+    return MLP(Ws, bs, L_mean, L_tx)
+
+
 def zero_mlp(L_mean: int = 6, L_tx: int = 10, hidden: int = 128,
              n_hidden: int = 4, out: int = 5) -> MLP:
     dims = mlp_dims(L_mean, L_tx, hidden, n_hidden, out)
