@@ -45,6 +45,9 @@ WORKLOADS = {
     "train": (20000, 90, 360, 64, math.log(3.0), 0.3),
     # RSSI head (Sec. 7.2): 50 Gaussians, 16 x 16 map, pooled; 4096 TX per step
     "rssi": (50, 16, 16, 4096, math.log(1.5), 0.3),
+    # the paper's own head (Sec. 4.1-4.2, 6.1): tanh centres, Cholesky
+    # covariance, complex response, 8 x 156 network with skips; FP32
+    "paper": (20000, 90, 360, 64, math.log(3.0), 0.3),
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
@@ -125,6 +128,12 @@ def config_of(args, shape, extra=None):
          "parallelism": f"replicas x{args.gpus}", "wrap": bool(args.wrap),
          "channels": args.channels,
          "output": "magnitude and phase [Q,2,H,W]" if args.channels == 2 else "spectra [Q,H,W]"}
+    if args.workload == "paper":
+        c.update({"mlp": "paper head: gamma(81) -> 156 x 8 ReLU -> 5, the encoding concatenated "
+                         "into hidden layers 2, 4, 6 (0-based); FP32 CUDA cores",
+                  "primitive": "tanh-mapped centre, Cholesky covariance, attenuation, complex "
+                               "response (Sec. 4.1)",
+                  "channels": 2, "output": "magnitude and phase [Q,2,H,W]"})
     if extra:
         c.update(extra)
     return c
@@ -236,17 +245,35 @@ def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18, wrap=False):
     return total
 
 
+def paper_inputs(rank):
+    """The paper-head workload: primitives of the paper's parameterisation,
+    its 8 x 156 network (unit-gain weights, small biases), TX in the room."""
+    N, H, W, Q, lsm, lss = WORKLOADS["paper"]
+    sc = synth.make_paper_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
+    m = synth.make_paper_mlp(gain=1.0, bias_std=0.05, seed=0)
+    tx = synth.make_tx(Q, seed=1 + rank)
+    return sc, m, tx, (N, H, W, Q)
+
+
 def run_reference(args):
     """The FP64 CPU oracle as the reference arm, on a bounded sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    sc, m, tx, shape = make_inputs(args.workload, 0, args.channels)
+    if args.workload == "paper":
+        sc, m, tx, shape = paper_inputs(0)
+    else:
+        sc, m, tx, shape = make_inputs(args.workload, 0, args.channels)
     N, H, W, Q = shape
     S = max(1, min(Q, 4 if args.workload != "rssi" else 256))
     if args.workload == "rssi":
         run = oracle.rssi
+    elif args.workload == "paper":
+        from oracle import paper as opaper
+
+        def run(sc_, m_, tx_, H_, W_, q_):
+            return opaper.forward(sc_, m_, tx_, H_, W_, q_)
     else:
         f = oracle.forward_complex if args.channels == 2 else oracle.forward
 
@@ -621,6 +648,162 @@ def run_rssi(args):
     return 0
 
 
+def run_paper(args):
+    """The paper's own head (Sec. 4.1-4.2, 6.1): per step, every (TX, Gaussian)
+    row through the 8 x 156 network (FP32), the projection to two-channel
+    records, binning and the two-channel rasteriser (magnitude and phase).
+    The three stages replay as one CUDA graph."""
+    import ctypes as C
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_12787_b300 import _lib, api
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc, m, tx_np, shape = paper_inputs(rank)
+    N, H, W, Q = shape
+    tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
+    args.tile = f"{tw}x{th}"
+    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    ds, dm = api.DevicePaperScene.from_host(sc, dev), api.DevicePaperMLP.from_host(m, dev)
+    tx = torch.as_tensor(tx_np, dtype=torch.float32, device=dev)
+    L = _lib.load()
+    stream = torch.cuda.Stream(device=dev)
+    r = api.Renderer(grid, dev)
+    with torch.cuda.stream(stream):
+        r.forward_paper(ds, dm, tx, stream=stream)  # sizes the key buffer (host sync)
+    stream.synchronize()
+    cap, last = r.cap, r.last
+    rec, gids, offs, nk = last["rec"], last["gids"], last["offs"], last["n_keys"]
+    n_keys = int(nk.item())
+    pws = r._buf("pws", L.wrf_paper_workspace_size(N, Q))
+    bws = r._buf("bws", L.wrf_bin_workspace_size(N, Q, C.byref(grid)))
+    out = torch.empty((Q, 2, H, W), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        api.wrf_paper_deform_project(ds, dm, grid, tx, rec=rec, ws=pws, stream=stream)
+        if evs:
+            evs[1].record(stream)
+        api.wrf_bin(rec, N, Q, grid, cap, gids=gids, n_keys=nk, offsets=offs, ws=bws,
+                    stream=stream)
+        if evs:
+            evs[2].record(stream)
+        api.wrf_render_complex(rec, gids, offs, nk, cap, N, Q, grid, out=out, stream=stream)
+        if evs:
+            evs[3].record(stream)
+
+    with torch.cuda.stream(stream):
+        step()
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        step()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(1)
+            graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            graph.replay()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_max, _, value = aggregate(sum(step_ms) / 1e3, Q * K, dist if ws > 1 else None)
+    KS = max(3, min(K, 30))
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(KS)]
+    with torch.cuda.stream(stream):
+        for i in range(KS):
+            flush.fill_(i & 255)
+            step(sev[i])
+    torch.cuda.synchronize()
+    stage = {name: statistics.mean(e[j].elapsed_time(e[j + 1]) for e in sev)
+             for j, name in enumerate(("paper_deform_project", "bin", "render_complex"))}
+    clk = clocks.stop()
+    if api.wrf_status_read(stream) != 0:
+        raise RuntimeError("device status set during the paper workload")
+    # end to end: pinned host TX in, pinned host magnitude / phase out, every step
+    hx = torch.as_tensor(tx_np, dtype=torch.float32).pin_memory()
+    hout = torch.empty((Q, 2, H, W), dtype=torch.float32).pin_memory()
+    KE = max(3, min(K, 30))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(KE):
+            tx.copy_(hx, non_blocking=True)
+            graph.replay()
+            hout.copy_(out, non_blocking=True)
+        e1.record(stream)
+    e1.synchronize()
+    _, _, e2e_val = aggregate(e0.elapsed_time(e1) / 1e3, Q * KE, dist if ws > 1 else None)
+    # roofline of the network stage: the factorised network's FLOPs per row
+    # (hidden-to-hidden products of layers 1..7, layer-0 add, output layer)
+    # plus the per-Gaussian and per-query encoding products, over its time
+    peaks, _ = measured_peaks()
+    wd, nh = 156, 8
+    dm_, dt_ = 42, 39
+    fl_row = (nh - 1) * 2 * wd * wd + 2 * wd * 5 + wd
+    fl = Q * N * fl_row + 4 * 2 * wd * (N * dm_ + Q * dt_)
+    fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    roof = {"kernel": "paper_mlp_kernel (+ encoding / weight prep)", "bound": "alu",
+            "achieved": fl / (stage["paper_deform_project"] * 1e-3) / 1e12, "peak": fp32_peak,
+            "unit": "TFLOP/s", "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
+            "flop_per_row": fl_row, "traffic": None, "stage_ms": stage}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
+            "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": config_of(args, shape, {"keys_per_step": n_keys, "cuda_graph": True}),
+            "clocks": clk,
+            "e2e": {"value": e2e_val, "unit": "spectra/s", "h2d_bytes_per_step": 12 * Q,
+                    "d2h_bytes_per_step": 8 * Q * H * W,
+                    "api": "api.wrf_paper_deform_project + wrf_bin + wrf_render_complex graph, "
+                           "pinned host TX in, pinned host magnitude / phase out"},
+            "roofline": roof, "gpu_launches": 10 * K}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import paper as opaper
+        import oracle
+        t0 = time.perf_counter()
+        opaper.forward(sc, m, tx_np[:1], H, W, Q_CUT)
+        t1 = time.perf_counter() - t0
+        S = int(max(1, min(Q, round(args.cpu_seconds / max(t1, 1e-3)))))
+        t0 = time.perf_counter()
+        opaper.forward(sc, m, tx_np[:S], H, W, Q_CUT)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": S / dt, "unit": "spectra/s",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"first {S} of {Q} TX queries, {N} Gaussians, {W}x{H}, "
+                                          f"FP64 numpy network + C oracle render, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -629,6 +812,8 @@ def main():
         return run_rssi(args)
     if args.workload == "train":
         return run_train(args)
+    if args.workload == "paper":
+        return run_paper(args)
     import torch
     import torch.distributed as dist
 

@@ -265,6 +265,61 @@ wrf_status wrf_render_complex(const float *rec, const uint32_t *gids,
                               int64_t key_capacity, int32_t n, int32_t Q, const wrf_grid *grid,
                               float *out, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* The paper's own primitive and deformation head (Sec. 4.1-4.2, Sec. 6.1).
+ * Primitive n, FP32, device, structure of arrays:
+ *   mu[n]         raw angular centre (u, v); the reference centre in pixels
+ *                 is x = W (tanh u + 1) / 2 (azimuth), y = H (tanh v + 1) / 2
+ *                 (elevation);
+ *   chol[n]       Cholesky entries (l1, l2, l3) of the covariance in pixels,
+ *                 Sigma = L L^T with L = [[l1, 0], [l2, l3]] (Sec. 3.2);
+ *                 l1 l3 != 0;
+ *   attn_logit[n] attenuation delta = sigmoid(a);
+ *   psi[n]        complex response (re, im).                                */
+typedef struct {
+    int32_t n;
+    const float *mu;          /* [N][2] device, 8-byte aligned               */
+    const float *chol;        /* [N][3] device                               */
+    const float *attn_logit;  /* [N]    device                               */
+    const float *psi;         /* [N][2] device, 8-byte aligned               */
+} wrf_paper_scene;
+
+/* Deformation network F (Eq. 14) of the paper's head: n_hidden Linear+ReLU
+ * layers of width `width`, the encoded input e = [gamma((x/W, y/H)) with
+ * L_mean bands, gamma((tx - room_min)/room_size) with L_tx bands] (Eq. 15)
+ * entering layer 0 and concatenated after the activations entering hidden
+ * layers 2, 4 and 6 (a skip every two layers), then a Linear output of width
+ * 5 = (dmu_x, dmu_y, dpsi_re, dpsi_im, ddelta).  W[l] is [out][in] row-major
+ * FP32 device with in = dim(e) for l = 0, width + dim(e) for a skip layer,
+ * width otherwise; W[n_hidden] is the output layer [5][width].  The paper's
+ * network: n_hidden 8, width 156, L_mean 10, L_tx 6.
+ * Supported: 1 <= n_hidden <= 8, 1 <= width <= 160, bands in [0, 15].       */
+enum { WRF_PAPER_MAX_LAYERS = 9, WRF_PAPER_MAX_WIDTH = 160 };
+typedef struct {
+    int32_t n_hidden, width;
+    const float *W[WRF_PAPER_MAX_LAYERS];
+    const float *b[WRF_PAPER_MAX_LAYERS];
+    int32_t L_mean, L_tx;
+    float room_min[3], room_size[3];
+} wrf_paper_mlp;
+
+/* Deform + project with the paper's head, in FP32: the frame at TX s is
+ * (mu + dmu, Sigma, psi + dpsi, delta + ddelta) (Eq. 12, no covariance
+ * residual), written as two-channel records (layout above: w = (delta +
+ * ddelta)(psi_re + dpsi_re), the imaginary weights (delta + ddelta)(psi_im +
+ * dpsi_im) after them; the caller allocates Q x N x 9 floats) for wrf_bin
+ * and wrf_render_complex, which give magnitude and phase (Sec. 6.1).
+ *   mlp   NULL: no deformation (Q copies of the reference frame).
+ *   tx    [Q][3] device, TX positions in metres (unused when mlp is NULL).
+ *   rec   device output, 16-byte aligned.
+ *   ws    wrf_paper_workspace_size(N, Q) bytes, 256-byte aligned (the
+ *         per-Gaussian and per-query terms of the layers that read the
+ *         encoding, and padded weight images).                              */
+size_t wrf_paper_workspace_size(int32_t n, int32_t Q);
+wrf_status wrf_paper_deform_project(const wrf_paper_scene *scene, const wrf_paper_mlp *mlp,
+                                    const wrf_grid *grid, const float *tx, int32_t Q, float *rec,
+                                    void *ws, size_t ws_bytes, void *stream);
+
 /* Backward of wrf_render: from dL/dA [Q][H][W] to d_rec [Q][N][6] =
  * dL/d(mx, my, A, B, C, w) where (A, B, C) is the unscaled inverse
  * covariance (Eq. 8).  Per-pixel weights are recomputed from the records

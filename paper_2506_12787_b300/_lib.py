@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libwrf.so")
 WRF_OK, WRF_EINVAL, WRF_ENOSPC, WRF_ECUDA, WRF_ETIMEOUT, WRF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 WRF_FP32, WRF_BF16 = 0, 1
 MAX_LAYERS = 8
+PAPER_MAX_LAYERS, PAPER_MAX_WIDTH = 9, 160
 REC_FLOATS = 8
 
 STATUS_NAMES = {0: "WRF_OK", -1: "WRF_EINVAL", -2: "WRF_ENOSPC", -3: "WRF_ECUDA",
@@ -27,6 +28,7 @@ EXPORTS = (
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
     "wrf_loss_workspace_size", "wrf_loss", "wrf_adam", "wrf_render_complex",
+    "wrf_paper_workspace_size", "wrf_paper_deform_project",
 )
 
 
@@ -47,6 +49,18 @@ class Mlp(C.Structure):
                 ("W", C.c_void_p * MAX_LAYERS), ("b", C.c_void_p * MAX_LAYERS),
                 ("L_mean", C.c_int32), ("L_tx", C.c_int32), ("room_min", C.c_float * 3),
                 ("room_size", C.c_float * 3), ("precision", C.c_int32)]
+
+
+class PaperScene(C.Structure):
+    _fields_ = [("n", C.c_int32), ("mu", C.c_void_p), ("chol", C.c_void_p),
+                ("attn_logit", C.c_void_p), ("psi", C.c_void_p)]
+
+
+class PaperMlp(C.Structure):
+    _fields_ = [("n_hidden", C.c_int32), ("width", C.c_int32),
+                ("W", C.c_void_p * PAPER_MAX_LAYERS), ("b", C.c_void_p * PAPER_MAX_LAYERS),
+                ("L_mean", C.c_int32), ("L_tx", C.c_int32), ("room_min", C.c_float * 3),
+                ("room_size", C.c_float * 3)]
 
 
 class AdamGroup(C.Structure):
@@ -95,6 +109,9 @@ def load(path: str = LIB_PATH):
         "wrf_loss": (I32, [P, P, I32, I32, I32, F, P, P, P, S, P]),
         "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
         "wrf_render_complex": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
+        "wrf_paper_workspace_size": (S, [I32, I32]),
+        "wrf_paper_deform_project": (I32, [C.POINTER(PaperScene), C.POINTER(PaperMlp), gp, P, I32,
+                                           P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)

@@ -20,7 +20,8 @@ from ._lib import WRF_BF16, WRF_FP32, WrfError
 __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
-           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail"]
+           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
+           "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project"]
 
 
 def _p(t):
@@ -173,6 +174,77 @@ def wrf_deform_project(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rec=None, t
     _lib.check(L.wrf_deform_project(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
                                     _p(rec), _p(tile_count), _p(ws), ws.numel(), _stream(stream)))
     return rec, tile_count
+
+
+@dataclasses.dataclass
+class DevicePaperScene:
+    """The paper's primitives on the device (Sec. 4.1): raw angular centres,
+    Cholesky entries, attenuation logits, complex responses (FP32, SoA)."""
+    mu: torch.Tensor          # [N,2]
+    chol: torch.Tensor        # [N,3]
+    attn_logit: torch.Tensor  # [N]
+    psi: torch.Tensor         # [N,2]
+
+    @classmethod
+    def from_host(cls, s, device="cuda"):
+        return cls(*(_f32(getattr(s, k), device) for k in ("mu", "chol", "attn_logit", "psi")))
+
+    @property
+    def n(self) -> int:
+        return int(self.mu.shape[0])
+
+    channels = 2
+
+    def c(self) -> _lib.PaperScene:
+        return _lib.PaperScene(self.n, self.mu.data_ptr(), self.chol.data_ptr(),
+                               self.attn_logit.data_ptr(), self.psi.data_ptr())
+
+
+@dataclasses.dataclass
+class DevicePaperMLP:
+    """The paper's deformation network (Sec. 6.1: hidden layers with a skip
+    every two layers, outputs dmu, dpsi, ddelta), FP32 on the device."""
+    W: list
+    b: list
+    L_mean: int = 10
+    L_tx: int = 6
+    room_min: tuple = (0.0, 0.0, 0.0)
+    room_size: tuple = (5.0, 5.0, 3.0)
+
+    @classmethod
+    def from_host(cls, m, device="cuda"):
+        return cls([_f32(w, device) for w in m.W], [_f32(b, device) for b in m.b], m.L_mean,
+                   m.L_tx, tuple(m.room_min), tuple(m.room_size))
+
+    def c(self) -> _lib.PaperMlp:
+        m = _lib.PaperMlp()
+        m.n_hidden = len(self.W) - 1
+        m.width = int(self.W[0].shape[0])
+        for i, (w, b) in enumerate(zip(self.W, self.b)):
+            m.W[i] = w.data_ptr()
+            m.b[i] = b.data_ptr()
+        m.L_mean, m.L_tx = self.L_mean, self.L_tx
+        for i in range(3):
+            m.room_min[i] = self.room_min[i]
+            m.room_size[i] = self.room_size[i]
+        return m
+
+
+def wrf_paper_deform_project(scene: DevicePaperScene, mlp, grid, tx, rec=None, ws=None,
+                             stream=None):
+    """Two-channel records [Q,N,8] (+ imaginary tail) of the paper's head;
+    mlp None: no deformation."""
+    L = _lib.load()
+    Q, dev = int(tx.shape[0]), scene.mu.device
+    if rec is None:
+        rec = alloc_records(Q, scene.n, 2, dev)
+    if mlp is not None and ws is None:
+        ws = _ws(L.wrf_paper_workspace_size(scene.n, Q), dev)
+    mc = None if mlp is None else mlp.c()
+    _lib.check(L.wrf_paper_deform_project(C.byref(scene.c()), None if mc is None else C.byref(mc),
+                                          C.byref(grid), _p(tx), Q, _p(rec), _p(ws),
+                                          0 if ws is None else ws.numel(), _stream(stream)))
+    return rec
 
 
 def wrf_loss(pred, target, lambda1: float = 0.7, want_grad: bool = True, out=None, d_pred=None,
@@ -379,6 +451,18 @@ class Renderer:
         render = wrf_render_complex if channels == 2 else wrf_render
         out = render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out, stream=stream)
         self.last = dict(rec=rec, gids=gids, offs=offs, n_keys=n_keys, n=n, Q=Q)
+        return out
+
+    def forward_paper(self, scene: DevicePaperScene, mlp, tx, stream=None, out=None):
+        """Magnitude and phase [Q,2,H,W] with the paper's head (Sec. 6.1)."""
+        L = _lib.load()
+        Q = int(tx.shape[0])
+        buf = self._buf("rec", Q * scene.n * 9 * 4)
+        rec = buf[: Q * scene.n * 32].view(torch.float32).view(Q, scene.n, 8)
+        ws = None if mlp is None else self._buf("pws", L.wrf_paper_workspace_size(scene.n, Q))
+        wrf_paper_deform_project(scene, mlp, self.grid, tx, rec=rec, ws=ws, stream=stream)
+        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out, channels=2)
+        self.last["resid"] = None
         return out
 
     def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None):

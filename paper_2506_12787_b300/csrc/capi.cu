@@ -344,6 +344,68 @@ wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *
     return WRF_OK;
 }
 
+size_t wrf_paper_workspace_size(int32_t n, int32_t Q) {
+    return wrf::paper_ws_layout(n < 0 ? 0 : n, Q < 0 ? 0 : Q, nullptr, nullptr);
+}
+
+wrf_status wrf_paper_deform_project(const wrf_paper_scene *scene, const wrf_paper_mlp *mlp,
+                                    const wrf_grid *grid, const float *tx, int32_t Q, float *rec,
+                                    void *ws, size_t ws_bytes, void *stream) {
+    static_assert(WRF_PAPER_MAX_LAYERS == wrf::kPaperMaxLayers, "layer bound");
+    static_assert(WRF_PAPER_MAX_WIDTH == wrf::kPaperMaxWidth, "width bound");
+    wrf_status s;
+    wrf::GridView g{};
+    if (!scene) return fail(WRF_EINVAL, "scene is NULL");
+    if (scene->n < 0) return fail(WRF_EINVAL, "scene.n < 0");
+    if (scene->n > 0 && (!scene->mu || !scene->chol || !scene->attn_logit || !scene->psi))
+        return fail(WRF_EINVAL, "scene array is NULL");
+    if (scene->n > 0 && (!aligned(scene->mu, 8) || !aligned(scene->psi, 8)))
+        return fail(WRF_EINVAL, "scene.mu / psi must be 8-byte aligned");
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "Q < 0");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q must be <= 65535");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    wrf::PaperMlpView mv{};
+    if (mlp) {
+        if (mlp->n_hidden < 1 || mlp->n_hidden > 8)
+            return fail(WRF_EUNSUPPORTED, "n_hidden must be in [1, 8]");
+        if (mlp->width < 1 || mlp->width > WRF_PAPER_MAX_WIDTH)
+            return fail(WRF_EUNSUPPORTED, "width must be in [1, 160]");
+        if (mlp->L_mean < 0 || mlp->L_mean > 15 || mlp->L_tx < 0 || mlp->L_tx > 15)
+            return fail(WRF_EUNSUPPORTED, "frequency bands must be in [0, 15]");
+        for (int l = 0; l <= mlp->n_hidden; ++l)
+            if (!mlp->W[l] || !mlp->b[l]) return fail(WRF_EINVAL, "weight %d is NULL", l);
+        for (int i = 0; i < 3; ++i)
+            if (!(mlp->room_size[i] > 0.f)) return fail(WRF_EINVAL, "room_size must be > 0");
+        if (Q > 0 && !tx) return fail(WRF_EINVAL, "tx is NULL");
+        mv.n_hidden = mlp->n_hidden;
+        mv.width = mlp->width;
+        mv.L_mean = mlp->L_mean;
+        mv.L_tx = mlp->L_tx;
+        for (int i = 0; i < 3; ++i) {
+            mv.room_min[i] = mlp->room_min[i];
+            mv.room_size[i] = mlp->room_size[i];
+        }
+        for (int l = 0; l <= mlp->n_hidden; ++l) {
+            mv.W[l] = mlp->W[l];
+            mv.b[l] = mlp->b[l];
+        }
+    }
+    if (Q == 0 || scene->n == 0) return WRF_OK;
+    if (!rec || !aligned(rec, 16)) return fail(WRF_EINVAL, "rec must be 16-byte aligned");
+    size_t need = wrf::paper_ws_layout(scene->n, Q, nullptr, nullptr);
+    if (mlp && (ws_bytes < need || !ws || !aligned(ws, 256)))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    wrf::PaperWs w{};
+    if (mlp) wrf::paper_ws_layout(scene->n, Q, &w, static_cast<char *>(ws));
+    wrf::PaperSceneView sv{scene->n, scene->mu, scene->chol, scene->attn_logit, scene->psi};
+    cudaError_t e = wrf::launch_paper(sv, mlp ? &mv : nullptr, g, tx, Q, w,
+                                      reinterpret_cast<float4 *>(rec),
+                                      static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "paper head");
+    return WRF_OK;
+}
+
 wrf_status wrf_project(const wrf_scene *scene, const float *resid, int32_t Q,
                        const wrf_grid *grid, float *rec, uint32_t *tile_count, void *stream) {
     wrf_status s;

@@ -62,6 +62,25 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
 cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
                            float4 *rec, uint32_t *count, cudaStream_t st);
 
+// The paper's primitive and deformation head (paper.cu).
+constexpr int kPaperMaxWidth = 160;
+constexpr int kPaperMaxLayers = 9;  // <= 8 hidden + output
+struct PaperSceneView {
+    int n;
+    const float *mu, *chol, *attn_logit, *psi;
+};
+struct PaperMlpView {
+    int n_hidden, width, L_mean, L_tx;
+    float room_min[3], room_size[3];
+    const float *W[kPaperMaxLayers], *b[kPaperMaxLayers];
+};
+struct PaperWs {
+    float *U, *V, *Wt, *bh, *Wo;
+};
+size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base);
+cudaError_t launch_paper(const PaperSceneView &s, const PaperMlpView *m, const GridView &g,
+                         const float *tx, int Q, const PaperWs &ws, float4 *rec, cudaStream_t st);
+
 // Training protocol (train.cu): Eq. 16 loss with SSIM, and Adam.
 size_t loss_ws_layout(int Q, int H, int W, float **coef, float **part);
 cudaError_t launch_loss(const float *pred, const float *target, int Q, int H, int W, float lam,

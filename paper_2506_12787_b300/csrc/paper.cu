@@ -1,0 +1,354 @@
+// The paper's own primitive and deformation head (Sec. 4.1-4.2, Sec. 6.1).
+//
+// Primitive n: raw angular centre (u, v) normalised by the hyperbolic map
+// (x = W (tanh u + 1) / 2 on the [0, 2 pi] azimuth axis, y = H (tanh v + 1) / 2
+// on the [0, pi/2] elevation axis), covariance Sigma = L L^T from its Cholesky
+// entries L = [[l1, 0], [l2, l3]] (Sec. 3.2), attenuation delta = sigmoid(a),
+// complex response psi = (re, im).  The deformation network F (Eq. 14) maps
+// [gamma(x/W, y/H), gamma(s)] to residuals (dmu_x, dmu_y, dpsi_re, dpsi_im,
+// ddelta); the frame at s is (mu + dmu, Sigma, psi + dpsi, delta + ddelta)
+// (Eq. 12, no covariance residual), rendered per channel with the weight
+// (delta + ddelta) (psi_c + dpsi_c) (Eq. 13) by the two-channel rasteriser.
+//
+// Network: n_hidden Linear+ReLU layers of width <= 160 (the paper: 8 x 156),
+// the encoded input concatenated to the activations entering hidden layers 2,
+// 4 and 6 (0-based: a skip every two layers), a Linear output of width 5.  A
+// layer whose input holds the encoding splits exactly into
+//   W [h; gamma(mu_n); gamma(s_q)] + b = W_h h + U[n] + V[q],
+// U[n] = W_mu gamma(mu_n) once per Gaussian, V[q] = W_s gamma(s_q) + b once per
+// query (prep kernels), so a row pays only the hidden-to-hidden products.
+// Those run as a register-tiled FP32 product: a CTA holds 64 rows of one
+// query, activations transposed ([input][row]) in shared memory, thread t the
+// 4 x 8 output tile rows 4 (t % 16) .., columns 8 (t / 16) .. (320 threads over
+// 64 x 160), weights staged 32 inputs (20 KB) at a time (two CTAs per SM); each output sums its
+// add-term then w_k h_k in ascending k.  The epilogue evaluates the output
+// layer and the projection and writes the records (w = real weight) and the
+// imaginary weights after them.
+#include "kernels.h"
+
+namespace wrf {
+
+namespace {
+
+constexpr int kPW = kPaperMaxWidth;   // padded width (160)
+constexpr int kRows = 64;             // rows per CTA
+constexpr int kThreads = 320;         // 16 row groups x 20 column groups
+constexpr int kPitch = kRows + 4;     // floats per input of the transposed activations
+constexpr int kKC = 32;               // weight rows (inputs) staged per pass (two CTAs per SM)
+constexpr int kEnc = 4;               // layers with the encoding in their input: 0, 2, 4, 6
+
+__host__ __device__ inline bool is_skip(int l) { return l == 2 || l == 4 || l == 6; }
+// index of an encoding layer among {0, 2, 4, 6}
+__host__ __device__ inline int enc_index(int l) { return l / 2; }
+
+struct PaperView {
+    int n;
+    const float *mu, *chol, *attn, *psi;
+};
+
+struct PaperNet {
+    int n_hidden, width, dm, dt, L_mean, L_tx;
+    float room_min[3], room_size[3];
+    const float *W[kPaperMaxLayers], *b[kPaperMaxLayers];
+};
+
+// (tanh u + 1) / 2 as an unevaluated sum hi + lo (Fast2Sum of 1 + tanh u,
+// |tanh u| <= 1; halving is exact), the encoding's input on the unit square.
+__device__ __forceinline__ PeArg unit_centre(float u) {
+    const float t = tanhf(u);
+    const float s = __fadd_rn(1.f, t);
+    const float e = __fadd_rn(__fsub_rn(1.f, s), t);
+    return PeArg{0.5f * s, 0.5f * e};
+}
+
+// Reference centre in pixels: x = W (tanh u + 1) / 2, y = H (tanh v + 1) / 2.
+__device__ __forceinline__ void centre(const PaperView &s, int n, const GridView &g, float &x,
+                                       float &y) {
+    const float2 m = reinterpret_cast<const float2 *>(s.mu)[n];
+    x = static_cast<float>(g.W) * pe_value(unit_centre(m.x));
+    y = static_cast<float>(g.H) * pe_value(unit_centre(m.y));
+}
+
+// gamma(x) of Eq. 15 for a d-vector: [x, sin band 0..L-1 (all d), cos ...].
+__device__ void encode_vec(const PeArg *x, int d, int L, float *out) {
+    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
+    for (int k = 0; k < L; ++k)
+        for (int i = 0; i < d; ++i) {
+            float sn, cs;
+            pe_band(x[i], k, sn, cs);
+            out[d + k * d + i] = sn;
+            out[d + L * d + k * d + i] = cs;
+        }
+}
+
+// Column offset of the mean-encoding block in layer l's input.
+__device__ __forceinline__ int mu_off(const PaperNet &m, int l) { return l == 0 ? 0 : m.width; }
+__device__ __forceinline__ int in_dim(const PaperNet &m, int l) {
+    return (l == 0 ? 0 : m.width) + (l == 0 || is_skip(l) ? m.dm + m.dt : 0);
+}
+
+// U[e][n][j] for the encoding layers, 32 Gaussians per block, thread = j.
+__global__ void __launch_bounds__(kPW) paper_mean_kernel(PaperView s, PaperNet m, GridView g,
+                                                         float *U) {
+    __shared__ float gam[32][2 * (2 * 15 + 1)];
+    const int n0 = blockIdx.x * 32;
+    if (threadIdx.x < 32 && n0 + threadIdx.x < s.n) {
+        const float2 mu = reinterpret_cast<const float2 *>(s.mu)[n0 + threadIdx.x];
+        const PeArg a[2] = {unit_centre(mu.x), unit_centre(mu.y)};
+        encode_vec(a, 2, m.L_mean, gam[threadIdx.x]);
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    for (int l = 0; l < m.n_hidden; ++l) {
+        if (l != 0 && !is_skip(l)) continue;
+        float acc[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) acc[r] = 0.f;
+        if (j < m.width) {
+            const float *wr = m.W[l] + static_cast<size_t>(j) * in_dim(m, l) + mu_off(m, l);
+            for (int k = 0; k < m.dm; ++k) {
+                const float w = __ldg(wr + k);
+#pragma unroll
+                for (int r = 0; r < 32; ++r) acc[r] = fmaf(w, gam[r][k], acc[r]);
+            }
+        }
+        float *Ue = U + static_cast<size_t>(enc_index(l)) * s.n * kPW;
+        for (int r = 0; r < 32 && n0 + r < s.n; ++r) Ue[static_cast<size_t>(n0 + r) * kPW + j] = acc[r];
+    }
+}
+
+// V[e][q][j] = W_s gamma(s_q) + b for the encoding layers, one query per block.
+__global__ void __launch_bounds__(kPW) paper_tx_kernel(PaperNet m, const float *tx, int Q, float *V) {
+    __shared__ float gam[3 * (2 * 15 + 1)];
+    const int q = blockIdx.x;
+    if (threadIdx.x == 0) {
+        PeArg a[3];
+        for (int c = 0; c < 3; ++c) a[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
+        encode_vec(a, 3, m.L_tx, gam);
+    }
+    __syncthreads();
+    const int j = threadIdx.x;
+    for (int l = 0; l < m.n_hidden; ++l) {
+        if (l != 0 && !is_skip(l)) continue;
+        float acc = 0.f;
+        if (j < m.width) {
+            const float *wr = m.W[l] + static_cast<size_t>(j) * in_dim(m, l) + mu_off(m, l) + m.dm;
+            for (int k = 0; k < m.dt; ++k) acc = fmaf(__ldg(wr + k), gam[k], acc);
+            acc += m.b[l][j];
+        }
+        V[(static_cast<size_t>(enc_index(l)) * Q + q) * kPW + j] = acc;
+    }
+}
+
+// Transposed, zero-padded hidden-to-hidden weights Wt[l][k][j] (l = 1 ..
+// n_hidden-1), biases of the layers without the encoding, output layer
+// Wo[k][8].
+__global__ void paper_weights_kernel(PaperNet m, float *Wt, float *bh, float *Wo) {
+    const long long per = static_cast<long long>(kPW) * kPW;
+    const long long total = (kPaperMaxLayers - 1) * per + kPaperMaxLayers * kPW + kPW * 8;
+    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (i < (kPaperMaxLayers - 1) * per) {
+            const int l = 1 + static_cast<int>(i / per);
+            const int k = static_cast<int>((i % per) / kPW), j = static_cast<int>(i % kPW);
+            float v = 0.f;
+            if (l < m.n_hidden && k < m.width && j < m.width)
+                v = m.W[l][static_cast<size_t>(j) * in_dim(m, l) + k];
+            Wt[i] = v;
+        } else if (i < (kPaperMaxLayers - 1) * per + kPaperMaxLayers * kPW) {
+            const long long e = i - (kPaperMaxLayers - 1) * per;
+            const int l = static_cast<int>(e / kPW), j = static_cast<int>(e % kPW);
+            bh[e] = (l > 0 && l < m.n_hidden && !is_skip(l) && j < m.width) ? m.b[l][j] : 0.f;
+        } else {
+            const long long e = i - (kPaperMaxLayers - 1) * per - kPaperMaxLayers * kPW;
+            const int k = static_cast<int>(e / 8), o = static_cast<int>(e % 8);
+            Wo[e] = (k < m.width && o < WRF_OUT) ? m.W[m.n_hidden][static_cast<size_t>(o) * m.width + k]
+                                                 : 0.f;
+        }
+    }
+}
+
+struct PaperArgs {
+    PaperView s;
+    PaperNet m;
+    GridView g;
+    int Q, tpq;
+    const float *U, *V, *Wt, *bh, *Wo;
+    int deform;  // 0: no network (residuals 0)
+    float4 *rec;
+    float *rec_im;
+};
+
+__global__ void __launch_bounds__(kThreads, 2) paper_mlp_kernel(PaperArgs a) {
+    extern __shared__ __align__(16) float smem[];
+    float *wbuf = smem;                                  // [kKC][kPW]
+    float *hin = smem + kKC * kPW, *hout = hin + kPW * kPitch;
+    __shared__ float dout[kRows][8];
+    const int tid = threadIdx.x, q = blockIdx.y;
+    const int n0 = blockIdx.x * kRows;
+    const int N = a.s.n;
+    const int rg = tid % 16, cg = tid / 16;
+    const PaperNet &m = a.m;
+    if (a.deform) {
+        // layer 0: h = relu(U0[n] + V0[q])
+        const float *U0 = a.U, *V0 = a.V + static_cast<size_t>(q) * kPW;
+        for (int e = tid; e < kRows * kPW; e += kThreads) {
+            const int r = e / kPW, j = e % kPW, n = n0 + r;
+            hin[j * kPitch + r] =
+                n < N ? fmaxf(__ldg(U0 + static_cast<size_t>(n) * kPW + j) + __ldg(V0 + j), 0.f) : 0.f;
+        }
+        for (int l = 1; l < m.n_hidden; ++l) {
+            float acc[4][8];
+            if (is_skip(l)) {
+                const float *Ul = a.U + static_cast<size_t>(enc_index(l)) * N * kPW;
+                const float *Vl = a.V + (static_cast<size_t>(enc_index(l)) * a.Q + q) * kPW;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int n = min(n0 + 4 * rg + r, N - 1);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        acc[r][c] = __ldg(Ul + static_cast<size_t>(n) * kPW + 8 * cg + c) +
+                                    __ldg(Vl + 8 * cg + c);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float bv = a.bh[l * kPW + 8 * cg + c];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) acc[r][c] = bv;
+                }
+            }
+            const float4 *wl = reinterpret_cast<const float4 *>(
+                a.Wt + static_cast<size_t>(l - 1) * kPW * kPW);
+            for (int k0 = 0; k0 < kPW; k0 += kKC) {
+                __syncthreads();  // the previous chunk (or layer outputs) is done with
+                for (int i = tid; i < kKC * kPW / 4; i += kThreads)
+                    reinterpret_cast<float4 *>(wbuf)[i] = __ldg(wl + k0 * (kPW / 4) + i);
+                __syncthreads();
+#pragma unroll 4
+                for (int k = 0; k < kKC; ++k) {
+                    const float4 hv = *reinterpret_cast<const float4 *>(hin + (k0 + k) * kPitch + 4 * rg);
+                    const float4 wa = *reinterpret_cast<const float4 *>(wbuf + k * kPW + 8 * cg);
+                    const float4 wb = *reinterpret_cast<const float4 *>(wbuf + k * kPW + 8 * cg + 4);
+                    const float h[4] = {hv.x, hv.y, hv.z, hv.w};
+                    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(w[c], h[r], acc[r][c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                *reinterpret_cast<float4 *>(hout + (8 * cg + c) * kPitch + 4 * rg) =
+                    make_float4(fmaxf(acc[0][c], 0.f), fmaxf(acc[1][c], 0.f), fmaxf(acc[2][c], 0.f),
+                                fmaxf(acc[3][c], 0.f));
+            float *t = hin;
+            hin = hout;
+            hout = t;
+        }
+        __syncthreads();
+        // output layer: thread (row, output) = (tid / 5, tid % 5)
+        for (int i = tid; i < kPW * 8; i += kThreads) wbuf[i] = a.Wo[i];
+        __syncthreads();
+        {
+            const int r = tid / WRF_OUT, o = tid % WRF_OUT;
+            float acc = m.b[m.n_hidden][o];
+            for (int k = 0; k < kPW; ++k) acc = fmaf(wbuf[k * 8 + o], hin[k * kPitch + r], acc);
+            dout[r][o] = acc;
+        }
+    } else if (tid < kRows * WRF_OUT) {
+        dout[tid / WRF_OUT][tid % WRF_OUT] = 0.f;
+    }
+    __syncthreads();
+    // projection (Eq. 12-13 with the paper's primitive), one thread per row
+    if (tid < kRows && n0 + tid < N) {
+        const int n = n0 + tid;
+        float x, y;
+        centre(a.s, n, a.g, x, y);
+        const float mx = x + dout[tid][0], my = y + dout[tid][1];
+        const float *L = a.s.chol + static_cast<size_t>(n) * 3;
+        const float l1 = L[0], l2 = L[1], l3 = L[2];
+        const float sxx = l1 * l1, sxy = l1 * l2, syy = fmaf(l2, l2, l3 * l3);
+        const float det = (l1 * l3) * (l1 * l3);
+        const float inv = 1.f / det;
+        const float A = syy * inv, B = -sxy * inv, C = sxx * inv;
+        const float delta = 1.f / (1.f + expf(-a.s.attn[n])) + dout[tid][4];
+        const float2 ps = reinterpret_cast<const float2 *>(a.s.psi)[n];
+        const float rx = sqrtf(a.g.q_cut * sxx), ry = sqrtf(a.g.q_cut * syy);
+        const size_t row = static_cast<size_t>(q) * N + n;
+        a.rec[2 * row] = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
+        a.rec[2 * row + 1] = make_float4(C * kHalfLog2e, delta * (ps.x + dout[tid][2]), rx, ry);
+        a.rec_im[row] = delta * (ps.y + dout[tid][3]);
+    }
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+}  // namespace
+
+size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char *p = base ? base + off : nullptr;
+        off = align256(off + bytes);
+        return reinterpret_cast<float *>(p);
+    };
+    PaperWs w{};
+    w.U = take(static_cast<size_t>(kEnc) * (n > 0 ? n : 1) * kPW * 4);
+    w.V = take(static_cast<size_t>(kEnc) * (Q > 0 ? Q : 1) * kPW * 4);
+    w.Wt = take(static_cast<size_t>(kPaperMaxLayers - 1) * kPW * kPW * 4);
+    w.bh = take(static_cast<size_t>(kPaperMaxLayers) * kPW * 4);
+    w.Wo = take(static_cast<size_t>(kPW) * 8 * 4);
+    if (ws) *ws = w;
+    return off;
+}
+
+cudaError_t launch_paper(const PaperSceneView &sv, const PaperMlpView *mv, const GridView &g,
+                         const float *tx, int Q, const PaperWs &ws, float4 *rec, cudaStream_t st) {
+    const long long rows = static_cast<long long>(Q) * sv.n;
+    if (rows == 0) return cudaSuccess;
+    PaperArgs a{};
+    a.s = PaperView{sv.n, sv.mu, sv.chol, sv.attn_logit, sv.psi};
+    a.g = g;
+    a.Q = Q;
+    a.tpq = (sv.n + kRows - 1) / kRows;
+    a.rec = rec;
+    a.rec_im = reinterpret_cast<float *>(rec + 2 * rows);
+    a.deform = mv != nullptr;
+    if (mv) {
+        PaperNet &m = a.m;
+        m.n_hidden = mv->n_hidden;
+        m.width = mv->width;
+        m.L_mean = mv->L_mean;
+        m.L_tx = mv->L_tx;
+        m.dm = 2 * (2 * mv->L_mean + 1);
+        m.dt = 3 * (2 * mv->L_tx + 1);
+        for (int i = 0; i < 3; ++i) {
+            m.room_min[i] = mv->room_min[i];
+            m.room_size[i] = mv->room_size[i];
+        }
+        for (int l = 0; l <= mv->n_hidden; ++l) {
+            m.W[l] = mv->W[l];
+            m.b[l] = mv->b[l];
+        }
+        a.U = ws.U;
+        a.V = ws.V;
+        a.Wt = ws.Wt;
+        a.bh = ws.bh;
+        a.Wo = ws.Wo;
+        paper_mean_kernel<<<(sv.n + 31) / 32, kPW, 0, st>>>(a.s, m, g, ws.U);
+        paper_tx_kernel<<<Q, kPW, 0, st>>>(m, tx, Q, ws.V);
+        paper_weights_kernel<<<148 * 4, 256, 0, st>>>(m, ws.Wt, ws.bh, ws.Wo);
+    }
+    const size_t smem = (static_cast<size_t>(kKC) * kPW + 2 * kPW * kPitch) * 4;
+    cudaError_t e = cudaFuncSetAttribute(paper_mlp_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    dim3 grid(a.tpq, Q);
+    paper_mlp_kernel<<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace wrf

@@ -64,6 +64,32 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert st == _lib.WRF_EUNSUPPORTED  # hidden width 100
 
 
+def test_paper_head_host_validation(lib):
+    """The paper head's entry point checks its network shape on the host."""
+    from paper_2506_12787_b300 import _lib
+    g = _lib.Grid(90, 360, 16, 16, 9.0)
+    s = _lib.PaperScene(10, None, None, None, None)
+    assert lib.wrf_paper_deform_project(C.byref(s), None, C.byref(g), None, 1, None, None, 0,
+                                        None) == _lib.WRF_EINVAL  # NULL arrays
+    s = _lib.PaperScene(0, None, None, None, None)
+    m = _lib.PaperMlp()
+    m.n_hidden, m.width, m.L_mean, m.L_tx = 8, 161, 10, 6
+    assert lib.wrf_paper_deform_project(C.byref(s), C.byref(m), C.byref(g), None, 1, None, None,
+                                        0, None) == _lib.WRF_EUNSUPPORTED
+    m.width, m.n_hidden = 156, 9
+    assert lib.wrf_paper_deform_project(C.byref(s), C.byref(m), C.byref(g), None, 1, None, None,
+                                        0, None) == _lib.WRF_EUNSUPPORTED
+    m.n_hidden = 8
+    assert lib.wrf_paper_deform_project(C.byref(s), C.byref(m), C.byref(g), None, 1, None, None,
+                                        0, None) == _lib.WRF_EINVAL  # NULL weights
+    assert lib.wrf_paper_deform_project(C.byref(s), None, C.byref(g), None, 70000, None, None,
+                                        0, None) == _lib.WRF_EUNSUPPORTED  # Q > 65535
+    # no Gaussians, no deformation: nothing to do
+    assert lib.wrf_paper_deform_project(C.byref(s), None, C.byref(g), None, 4, None, None, 0,
+                                        None) == _lib.WRF_OK
+    assert 0 < lib.wrf_paper_workspace_size(100, 2) < lib.wrf_paper_workspace_size(10000, 64)
+
+
 def test_workspace_sizes_are_monotone(lib):
     from paper_2506_12787_b300 import _lib
     g = _lib.Grid(90, 360, 16, 16, 9.0)

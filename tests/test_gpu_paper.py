@@ -1,0 +1,173 @@
+"""GPU parity of the paper's own head (Sec. 4.1-4.2, Sec. 6.1: tanh-mapped
+angular centres, Cholesky covariance, attenuation and complex response, the
+deformation network with skips every two layers and outputs dmu, dpsi,
+ddelta) against the FP64 oracle, through the C ABI.
+
+Tolerances.  The network runs in FP32 (sums of <= 160 + 237 products per
+output, 9 layers), and the centre enters the encoding through tanhf (a few
+ulp of (tanh u + 1) / 2, i.e. <= ~1e-7 relative, raised by 2^9 pi at the top
+band of L_mean = 10 to ~2e-4 rad of sin / cos).  With unit-gain weights that
+phase error reaches the residuals attenuated by the network, so records
+carry: centres within 2e-3 px, weights within 1e-4 x the largest |w|,
+inverse covariance and footprint radii within FP32 rounding (2e-6 relative;
+no network term), and spectra within 2e-4 x the channel peak (a centre
+error e moves a Gaussian of standard deviation >= 1.5 px by at most
+~0.6 e / 1.5 of its peak) plus the cutoff-band slack."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from helpers import spectrum_error
+from oracle import paper
+from paper_2506_12787_b300 import _lib
+
+pytestmark = pytest.mark.gpu
+
+H, W = 90, 360
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_2506_12787_b300 import api, build
+    build.build()
+    assert torch.cuda.is_available()
+    return api
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=dev())
+
+
+def paper_mlp(seed, width=156, n_hidden=8, move=10.0):
+    """Unit-gain network; the centre outputs scaled so dmu is a few pixels."""
+    m = synth.make_paper_mlp(gain=1.0, bias_std=0.05, width=width, n_hidden=n_hidden, seed=seed)
+    m.W[-1][:2] *= np.float32(move)
+    m.b[-1][:2] *= np.float32(move)
+    return m
+
+
+def gpu_records(api, sc, m, tx, grid):
+    Q, N = tx.shape[0], sc.mu.shape[0]
+    ds = api.DevicePaperScene.from_host(sc, dev())
+    dm = None if m is None else api.DevicePaperMLP.from_host(m, dev())
+    rec = api.wrf_paper_deform_project(ds, dm, grid, T(tx))
+    torch.cuda.synchronize()
+    return rec.cpu().numpy().astype(np.float64), api.record_tail(rec, Q, N).cpu().numpy()
+
+
+def check_records(g, tail, sc, m, tx, q_cut=9.0):
+    Q, N = tx.shape[0], sc.mu.shape[0]
+    resid = paper.residuals(sc, m, tx, H, W) if m is not None else np.zeros((Q, N, 5))
+    pre, pim = paper.project(sc, resid, H, W, q_cut)
+    s = 0.72134752044448170368  # log2(e) / 2, the records' conic scale
+    e_c = float(np.abs(g[..., :2] - pre[..., :2]).max())
+    conic = pre[..., 2:5] * s
+    e_q = float((np.abs(g[..., 2:5] - conic) / np.abs(conic).max(-1, keepdims=True)).max())
+    e_r = float((np.abs(g[..., 6:8] - pre[..., 6:8]) / pre[..., 6:8]).max())
+    wmax = max(float(np.abs(pre[..., 5]).max()), float(np.abs(pim[..., 5]).max()))
+    e_w = max(float(np.abs(g[..., 5] - pre[..., 5]).max()),
+              float(np.abs(tail - pim[..., 5]).max())) / wmax
+    print(f"records: centre {e_c:.2e} px, conic {e_q:.2e}, radii {e_r:.2e}, weight {e_w:.2e} "
+          f"(|dmu| up to {float(np.abs(resid[..., :2]).max()):.2f} px)")
+    assert e_c <= 2e-3 and e_q <= 2e-6 and e_r <= 2e-6 and e_w <= 1e-4
+    return resid
+
+
+def test_paper_records_match_oracle(api):
+    """The paper's network (8 x 156, skips every two layers); N = 1000 = 15 x
+    64 + 40 Gaussians (a ragged last CTA), 3 TX."""
+    sc = synth.make_paper_scene(1000, H, W, seed=1)
+    m = paper_mlp(1)
+    tx = synth.make_tx(3, seed=1)
+    g, tail = gpu_records(api, sc, m, tx, api.make_grid(H, W, 16, 16, 9.0))
+    resid = check_records(g, tail, sc, m, tx)
+    assert float(np.abs(resid[..., :2]).max()) > 1.0  # the centres really move
+
+
+@pytest.mark.parametrize("width,n_hidden", [(100, 3), (160, 1), (17, 5), (156, 7)])
+def test_paper_network_shapes(api, width, n_hidden):
+    """Other widths (padded to 160 inside) and depths (skips at 2, 4, 6 below
+    n_hidden only)."""
+    sc = synth.make_paper_scene(130, H, W, seed=2)
+    m = paper_mlp(2, width=width, n_hidden=n_hidden)
+    tx = synth.make_tx(2, seed=2)
+    g, tail = gpu_records(api, sc, m, tx, api.make_grid(H, W, 16, 16, 9.0))
+    check_records(g, tail, sc, m, tx)
+
+
+def test_paper_no_deformation_records(api):
+    sc = synth.make_paper_scene(77, H, W, seed=3)
+    tx = np.zeros((2, 3))
+    g, tail = gpu_records(api, sc, None, tx, api.make_grid(H, W, 16, 16, 9.0))
+    check_records(g, tail, sc, None, tx)
+    assert np.array_equal(g[0], g[1])
+
+
+def check_spectra(out, sc, m, tx, grid_w, q_cut, wrap, Hs=H, Ws=W, tol=2e-4):
+    mag, ph, re, im, slack, _ = paper.forward(sc, m, tx, Hs, Ws, q_cut, wrap=wrap)
+    gm, gp = out[:, 0].astype(np.float64), out[:, 1].astype(np.float64)
+    ok_re, e_re, _ = spectrum_error(gm * np.cos(gp), re, slack, tol)
+    ok_im, e_im, _ = spectrum_error(gm * np.sin(gp), im, slack, tol)
+    ok_m, e_m, used = spectrum_error(gm, mag, slack, tol)
+    print(f"paper spectra ({grid_w}): re {e_re:.2e}, im {e_im:.2e}, magnitude {e_m:.2e} "
+          f"(x peak; slack px {used})")
+    assert ok_re and ok_im and ok_m
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
+def test_paper_spectra_match_oracle(api, tile):
+    """Magnitude and phase of Eq. 13 with the paper's head, 2000 Gaussians,
+    3 TX, through binning and the two-channel rasteriser."""
+    sc = synth.make_paper_scene(2000, H, W, seed=4)
+    m = paper_mlp(4)
+    tx = synth.make_tx(3, seed=4)
+    r = api.Renderer(api.make_grid(H, W, tile[0], tile[1], 9.0), dev())
+    out = r.forward_paper(api.DevicePaperScene.from_host(sc, dev()),
+                          api.DevicePaperMLP.from_host(m, dev()), T(tx))
+    assert tuple(out.shape) == (3, 2, H, W)
+    check_spectra(out.cpu().numpy(), sc, m, tx, tile, 9.0, False)
+
+
+def test_paper_spectra_wrap_no_deformation(api):
+    """The reference frame alone on a wrapped 40 x 72 grid (ragged tiles)."""
+    Hs, Ws = 40, 72
+    sc = synth.make_paper_scene(300, Hs, Ws, ls_mean=math.log(2.0), seed=5)
+    tx = np.zeros((1, 3))
+    r = api.Renderer(api.make_grid(Hs, Ws, 16, 16, 9.0, wrap=True), dev())
+    out = r.forward_paper(api.DevicePaperScene.from_host(sc, dev()), None, T(tx))
+    check_spectra(out.cpu().numpy(), sc, None, tx, (16, 16), 9.0, True, Hs, Ws)
+
+
+def test_paper_single_gaussian_and_determinism(api):
+    """N = 1 (one CTA row of 64 used) matches the one-primitive closed form's
+    oracle; repeated calls are bit-identical."""
+    sc = synth.make_paper_scene(1, H, W, seed=6)
+    m = paper_mlp(6)
+    tx = synth.make_tx(1, seed=6)
+    g, tail = gpu_records(api, sc, m, tx, api.make_grid(H, W, 16, 16, 9.0))
+    check_records(g, tail, sc, m, tx)
+    sc = synth.make_paper_scene(500, H, W, seed=7)
+    ds, dm = api.DevicePaperScene.from_host(sc, dev()), api.DevicePaperMLP.from_host(m, dev())
+    grid = api.make_grid(H, W, 16, 16, 9.0)
+    a = api.wrf_paper_deform_project(ds, dm, grid, T(synth.make_tx(5, seed=7)))
+    b = api.wrf_paper_deform_project(ds, dm, grid, T(synth.make_tx(5, seed=7)))
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_paper_workspace_too_small(api):
+    sc = synth.make_paper_scene(100, H, W, seed=8)
+    m = paper_mlp(8)
+    ds, dm = api.DevicePaperScene.from_host(sc, dev()), api.DevicePaperMLP.from_host(m, dev())
+    ws = torch.empty(1024, dtype=torch.uint8, device=dev())
+    with pytest.raises(api.WrfError) as e:
+        api.wrf_paper_deform_project(ds, dm, api.make_grid(H, W, 16, 16, 9.0),
+                                     T(synth.make_tx(2, seed=8)), ws=ws)
+    assert e.value.status == _lib.WRF_EINVAL
