@@ -20,7 +20,8 @@
 // Those run as a register-tiled FP32 product: a CTA holds 64 rows of one
 // query, activations transposed ([input][row]) in shared memory, thread t the
 // 4 x 8 output tile rows 4 (t % 16) .., columns 8 (t / 16) .. (320 threads over
-// 64 x 160), weights staged 32 inputs (20 KB) at a time (two CTAs per SM); each output sums its
+// 64 x 160), weights streamed 16 inputs (10 KB) at a time through two cp.async
+// buffers (two CTAs per SM); each output sums its
 // add-term then w_k h_k in ascending k.  The epilogue evaluates the output
 // layer and the projection and writes the records (w = real weight) and the
 // imaginary weights after them.
@@ -34,8 +35,15 @@ constexpr int kPW = kPaperMaxWidth;   // padded width (160)
 constexpr int kRows = 64;             // rows per CTA
 constexpr int kThreads = 320;         // 16 row groups x 20 column groups
 constexpr int kPitch = kRows + 4;     // floats per input of the transposed activations
-constexpr int kKC = 32;               // weight rows (inputs) staged per pass (two CTAs per SM)
+constexpr int kKC = 16;               // weight rows (inputs) per staged chunk (two buffers)
 constexpr int kEnc = 4;               // layers with the encoding in their input: 0, 2, 4, 6
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __host__ __device__ inline bool is_skip(int l) { return l == 2 || l == 4 || l == 6; }
 // index of an encoding layer among {0, 2, 4, 6}
@@ -182,7 +190,7 @@ struct PaperArgs {
 __global__ void __launch_bounds__(kThreads, 2) paper_mlp_kernel(PaperArgs a) {
     extern __shared__ __align__(16) float smem[];
     float *wbuf = smem;                                  // [kKC][kPW]
-    float *hin = smem + kKC * kPW, *hout = hin + kPW * kPitch;
+    float *hin = smem + 2 * kKC * kPW, *hout = hin + kPW * kPitch;
     __shared__ float dout[kRows][8];
     const int tid = threadIdx.x, q = blockIdx.y;
     const int n0 = blockIdx.x * kRows;
@@ -190,66 +198,99 @@ __global__ void __launch_bounds__(kThreads, 2) paper_mlp_kernel(PaperArgs a) {
     const int rg = tid % 16, cg = tid / 16;
     const PaperNet &m = a.m;
     if (a.deform) {
-        // layer 0: h = relu(U0[n] + V0[q])
+        // weight chunks (kKC inputs x 160 outputs) stream through two buffers
+        // with cp.async, one chunk ahead of the products
+        const int nchunk = (m.n_hidden - 1) * (kPW / kKC);
+        auto stage = [&](int s) {
+            const int l = 1 + s / (kPW / kKC), k0 = (s % (kPW / kKC)) * kKC;
+            const float4 *src = reinterpret_cast<const float4 *>(
+                a.Wt + (static_cast<size_t>(l - 1) * kPW + k0) * kPW);
+            float4 *dst = reinterpret_cast<float4 *>(wbuf + (s & 1) * kKC * kPW);
+            for (int i = tid; i < kKC * kPW / 4; i += kThreads) cp_async16(dst + i, src + i);
+            cp_async_commit();
+        };
+        if (nchunk > 0) stage(0);
+        // layer 0: h = relu(U0[n] + V0[q]); lanes take consecutive rows so the
+        // transposed stores are conflict-free, each loading 4 columns
         const float *U0 = a.U, *V0 = a.V + static_cast<size_t>(q) * kPW;
-        for (int e = tid; e < kRows * kPW; e += kThreads) {
-            const int r = e / kPW, j = e % kPW, n = n0 + r;
-            hin[j * kPitch + r] =
-                n < N ? fmaxf(__ldg(U0 + static_cast<size_t>(n) * kPW + j) + __ldg(V0 + j), 0.f) : 0.f;
+        for (int e = tid; e < kRows * kPW / 4; e += kThreads) {
+            const int r = e % kRows, j4 = 4 * (e / kRows), n = n0 + r;
+            float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (n < N) u = __ldg(reinterpret_cast<const float4 *>(U0 + static_cast<size_t>(n) * kPW + j4));
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(V0 + j4));
+            const bool ok = n < N;
+            hin[(j4 + 0) * kPitch + r] = ok ? fmaxf(u.x + v.x, 0.f) : 0.f;
+            hin[(j4 + 1) * kPitch + r] = ok ? fmaxf(u.y + v.y, 0.f) : 0.f;
+            hin[(j4 + 2) * kPitch + r] = ok ? fmaxf(u.z + v.z, 0.f) : 0.f;
+            hin[(j4 + 3) * kPitch + r] = ok ? fmaxf(u.w + v.w, 0.f) : 0.f;
         }
-        for (int l = 1; l < m.n_hidden; ++l) {
-            float acc[4][8];
-            if (is_skip(l)) {
-                const float *Ul = a.U + static_cast<size_t>(enc_index(l)) * N * kPW;
-                const float *Vl = a.V + (static_cast<size_t>(enc_index(l)) * a.Q + q) * kPW;
+        float acc[4][8];
+        for (int s = 0; s < nchunk; ++s) {
+            const int l = 1 + s / (kPW / kKC), kc = s % (kPW / kKC);
+            if (kc == 0) {
+                if (is_skip(l)) {
+                    const float *Ul = a.U + static_cast<size_t>(enc_index(l)) * N * kPW;
+                    const float *Vl = a.V + (static_cast<size_t>(enc_index(l)) * a.Q + q) * kPW;
+                    const float4 va = __ldg(reinterpret_cast<const float4 *>(Vl + 8 * cg));
+                    const float4 vb = __ldg(reinterpret_cast<const float4 *>(Vl + 8 * cg + 4));
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int n = min(n0 + 4 * rg + r, N - 1);
+                    for (int r = 0; r < 4; ++r) {
+                        const int n = min(n0 + 4 * rg + r, N - 1);
+                        const float *ur = Ul + static_cast<size_t>(n) * kPW + 8 * cg;
+                        const float4 ua = __ldg(reinterpret_cast<const float4 *>(ur));
+                        const float4 ub = __ldg(reinterpret_cast<const float4 *>(ur + 4));
+                        acc[r][0] = ua.x + va.x;
+                        acc[r][1] = ua.y + va.y;
+                        acc[r][2] = ua.z + va.z;
+                        acc[r][3] = ua.w + va.w;
+                        acc[r][4] = ub.x + vb.x;
+                        acc[r][5] = ub.y + vb.y;
+                        acc[r][6] = ub.z + vb.z;
+                        acc[r][7] = ub.w + vb.w;
+                    }
+                } else {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        acc[r][c] = __ldg(Ul + static_cast<size_t>(n) * kPW + 8 * cg + c) +
-                                    __ldg(Vl + 8 * cg + c);
-                }
-            } else {
+                    for (int c = 0; c < 8; ++c) {
+                        const float bv = a.bh[l * kPW + 8 * cg + c];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const float bv = a.bh[l * kPW + 8 * cg + c];
-#pragma unroll
-                    for (int r = 0; r < 4; ++r) acc[r][c] = bv;
-                }
-            }
-            const float4 *wl = reinterpret_cast<const float4 *>(
-                a.Wt + static_cast<size_t>(l - 1) * kPW * kPW);
-            for (int k0 = 0; k0 < kPW; k0 += kKC) {
-                __syncthreads();  // the previous chunk (or layer outputs) is done with
-                for (int i = tid; i < kKC * kPW / 4; i += kThreads)
-                    reinterpret_cast<float4 *>(wbuf)[i] = __ldg(wl + k0 * (kPW / 4) + i);
-                __syncthreads();
-#pragma unroll 4
-                for (int k = 0; k < kKC; ++k) {
-                    const float4 hv = *reinterpret_cast<const float4 *>(hin + (k0 + k) * kPitch + 4 * rg);
-                    const float4 wa = *reinterpret_cast<const float4 *>(wbuf + k * kPW + 8 * cg);
-                    const float4 wb = *reinterpret_cast<const float4 *>(wbuf + k * kPW + 8 * cg + 4);
-                    const float h[4] = {hv.x, hv.y, hv.z, hv.w};
-                    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                    for (int r = 0; r < 4; ++r)
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(w[c], h[r], acc[r][c]);
+                        for (int r = 0; r < 4; ++r) acc[r][c] = bv;
+                    }
                 }
             }
+            // chunk s has landed for every thread, and every thread is done
+            // with the buffer the next chunk overwrites (and with the layer
+            // outputs written before this point)
+            cp_async_wait_all();
+            __syncthreads();
+            if (s + 1 < nchunk) stage(s + 1);
+            const float *wb = wbuf + (s & 1) * kKC * kPW;
+            const float *hk = hin + kc * kKC * kPitch;
+#pragma unroll 8
+            for (int k = 0; k < kKC; ++k) {
+                const float4 hv = *reinterpret_cast<const float4 *>(hk + k * kPitch + 4 * rg);
+                const float4 wa = *reinterpret_cast<const float4 *>(wb + k * kPW + 8 * cg);
+                const float4 wc = *reinterpret_cast<const float4 *>(wb + k * kPW + 8 * cg + 4);
+                const float h[4] = {hv.x, hv.y, hv.z, hv.w};
+                const float w[8] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
 #pragma unroll
-            for (int c = 0; c < 8; ++c)
-                *reinterpret_cast<float4 *>(hout + (8 * cg + c) * kPitch + 4 * rg) =
-                    make_float4(fmaxf(acc[0][c], 0.f), fmaxf(acc[1][c], 0.f), fmaxf(acc[2][c], 0.f),
-                                fmaxf(acc[3][c], 0.f));
-            float *t = hin;
-            hin = hout;
-            hout = t;
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(w[c], h[r], acc[r][c]);
+            }
+            if (kc == kPW / kKC - 1) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    *reinterpret_cast<float4 *>(hout + (8 * cg + c) * kPitch + 4 * rg) =
+                        make_float4(fmaxf(acc[0][c], 0.f), fmaxf(acc[1][c], 0.f),
+                                    fmaxf(acc[2][c], 0.f), fmaxf(acc[3][c], 0.f));
+                float *t = hin;
+                hin = hout;
+                hout = t;
+            }
         }
         __syncthreads();
         // output layer: thread (row, output) = (tid / 5, tid % 5)
-        for (int i = tid; i < kPW * 8; i += kThreads) wbuf[i] = a.Wo[i];
+        for (int i = tid; i < kPW * 8; i += kThreads) wbuf[i] = a.Wo[i];  // 2 x 16 x 160 >= 1280
         __syncthreads();
         {
             const int r = tid / WRF_OUT, o = tid % WRF_OUT;
@@ -341,7 +382,7 @@ cudaError_t launch_paper(const PaperSceneView &sv, const PaperMlpView *mv, const
         paper_tx_kernel<<<Q, kPW, 0, st>>>(m, tx, Q, ws.V);
         paper_weights_kernel<<<148 * 4, 256, 0, st>>>(m, ws.Wt, ws.bh, ws.Wo);
     }
-    const size_t smem = (static_cast<size_t>(kKC) * kPW + 2 * kPW * kPitch) * 4;
+    const size_t smem = (static_cast<size_t>(2 * kKC) * kPW + 2 * kPW * kPitch) * 4;
     cudaError_t e = cudaFuncSetAttribute(paper_mlp_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
