@@ -130,7 +130,9 @@ def config_of(args, shape, extra=None):
          "output": "magnitude and phase [Q,2,H,W]" if args.channels == 2 else "spectra [Q,H,W]"}
     if args.workload == "paper":
         c.update({"mlp": "paper head: gamma(81) -> 156 x 8 ReLU -> 5, the encoding concatenated "
-                         "into hidden layers 2, 4, 6 (0-based); FP32 CUDA cores",
+                         "into hidden layers 2, 4, 6 (0-based); " +
+                         ("BF16 tcgen05 / FP32 acc" if args.precision == "bf16"
+                          else "FP32 CUDA cores"),
                   "primitive": "tanh-mapped centre, Cholesky covariance, attenuation, complex "
                                "response (Sec. 4.1)",
                   "channels": 2, "output": "magnitude and phase [Q,2,H,W]"})
@@ -670,7 +672,9 @@ def run_paper(args):
     tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
     args.tile = f"{tw}x{th}"
     grid = api.make_grid(H, W, tw, th, Q_CUT)
-    ds, dm = api.DevicePaperScene.from_host(sc, dev), api.DevicePaperMLP.from_host(m, dev)
+    prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
+    ds = api.DevicePaperScene.from_host(sc, dev)
+    dm = api.DevicePaperMLP.from_host(m, dev, precision=prec)
     tx = torch.as_tensor(tx_np, dtype=torch.float32, device=dev)
     L = _lib.load()
     stream = torch.cuda.Stream(device=dev)
@@ -767,15 +771,20 @@ def run_paper(args):
     fl_row = (nh - 1) * 2 * wd * wd + 2 * wd * 5 + wd
     fl = Q * N * fl_row + 4 * 2 * wd * (N * dm_ + Q * dt_)
     fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-    roof = {"kernel": "paper_mlp_kernel (+ encoding / weight prep)", "bound": "alu",
-            "achieved": fl / (stage["paper_deform_project"] * 1e-3) / 1e12, "peak": fp32_peak,
-            "unit": "TFLOP/s", "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
-            "flop_per_row": fl_row, "traffic": None, "stage_ms": stage}
+    if prec == api.WRF_BF16:
+        roof = {"kernel": "paper_tc_kernel (+ gamma rows / per-query terms / weight panels)",
+                "bound": "tensor", "peak": peaks["bf16_tflops"],
+                "peak_source": "bf16_tflops (measured)"}
+    else:
+        roof = {"kernel": "paper_mlp_kernel (+ encoding / weight prep)", "bound": "alu",
+                "peak": fp32_peak, "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock"}
+    roof.update({"achieved": fl / (stage["paper_deform_project"] * 1e-3) / 1e12,
+                 "unit": "TFLOP/s", "flop_per_row": fl_row, "traffic": None, "stage_ms": stage})
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == api.WRF_BF16 else "f32", "data": "synthetic",
             "config": config_of(args, shape, {"keys_per_step": n_keys, "cuda_graph": True}),
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "spectra/s", "h2d_bytes_per_step": 12 * Q,

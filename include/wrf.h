@@ -293,7 +293,12 @@ typedef struct {
  * FP32 device with in = dim(e) for l = 0, width + dim(e) for a skip layer,
  * width otherwise; W[n_hidden] is the output layer [5][width].  The paper's
  * network: n_hidden 8, width 156, L_mean 10, L_tx 6.
- * Supported: 1 <= n_hidden <= 8, 1 <= width <= 160, bands in [0, 15].       */
+ * Supported: 1 <= n_hidden <= 8, 1 <= width <= 160, bands in [0, 15]
+ * (L_mean <= 15 in FP32, <= 15 with 2(2 L_mean + 1) <= 64 in BF16).
+ * precision = WRF_FP32: every product in FP32 on the CUDA cores.
+ * precision = WRF_BF16: the hidden and output layers on the tcgen05 tensor
+ * cores with BF16 weights, activations and gamma(mean), FP32 accumulation;
+ * the query's part of the encoding, W_s gamma(s) + b, stays FP32.         */
 enum { WRF_PAPER_MAX_LAYERS = 9, WRF_PAPER_MAX_WIDTH = 160 };
 typedef struct {
     int32_t n_hidden, width;
@@ -301,9 +306,10 @@ typedef struct {
     const float *b[WRF_PAPER_MAX_LAYERS];
     int32_t L_mean, L_tx;
     float room_min[3], room_size[3];
+    int32_t precision;           /* WRF_FP32 or WRF_BF16 (see below)          */
 } wrf_paper_mlp;
 
-/* Deform + project with the paper's head, in FP32: the frame at TX s is
+/* Deform + project with the paper's head: the frame at TX s is
  * (mu + dmu, Sigma, psi + dpsi, delta + ddelta) (Eq. 12, no covariance
  * residual), written as two-channel records (layout above: w = (delta +
  * ddelta)(psi_re + dpsi_re), the imaginary weights (delta + ddelta)(psi_im +

@@ -60,7 +60,7 @@ class PaperMlp(C.Structure):
     _fields_ = [("n_hidden", C.c_int32), ("width", C.c_int32),
                 ("W", C.c_void_p * PAPER_MAX_LAYERS), ("b", C.c_void_p * PAPER_MAX_LAYERS),
                 ("L_mean", C.c_int32), ("L_tx", C.c_int32), ("room_min", C.c_float * 3),
-                ("room_size", C.c_float * 3)]
+                ("room_size", C.c_float * 3), ("precision", C.c_int32)]
 
 
 class AdamGroup(C.Structure):

@@ -210,11 +210,12 @@ class DevicePaperMLP:
     L_tx: int = 6
     room_min: tuple = (0.0, 0.0, 0.0)
     room_size: tuple = (5.0, 5.0, 3.0)
+    precision: int = WRF_FP32
 
     @classmethod
-    def from_host(cls, m, device="cuda"):
+    def from_host(cls, m, device="cuda", precision=WRF_FP32):
         return cls([_f32(w, device) for w in m.W], [_f32(b, device) for b in m.b], m.L_mean,
-                   m.L_tx, tuple(m.room_min), tuple(m.room_size))
+                   m.L_tx, tuple(m.room_min), tuple(m.room_size), precision)
 
     def c(self) -> _lib.PaperMlp:
         m = _lib.PaperMlp()
@@ -227,6 +228,7 @@ class DevicePaperMLP:
         for i in range(3):
             m.room_min[i] = self.room_min[i]
             m.room_size[i] = self.room_size[i]
+        m.precision = self.precision
         return m
 
 

@@ -75,11 +75,17 @@ struct PaperMlpView {
     const float *W[kPaperMaxLayers], *b[kPaperMaxLayers];
 };
 struct PaperWs {
-    float *U, *V, *Wt, *bh, *Wo;
+    float *U, *V, *Wt, *bh, *Wo;  // FP32 network (paper.cu)
+    uint16_t *G, *img;            // tensor-core network (paper_tc.cu): BF16 gamma rows, panels
+    float *vec;                   //   per-query FP32 layer terms [Q][8][160]
 };
 size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base);
 cudaError_t launch_paper(const PaperSceneView &s, const PaperMlpView *m, const GridView &g,
                          const float *tx, int Q, const PaperWs &ws, float4 *rec, cudaStream_t st);
+size_t paper_tc_image_bytes(int n_hidden);
+cudaError_t launch_paper_tc(const PaperSceneView &s, const PaperMlpView &m, const GridView &g,
+                            const float *tx, int Q, const PaperWs &ws, float4 *rec, int *status,
+                            cudaStream_t st);
 
 // Training protocol (train.cu): Eq. 16 loss with SSIM, and Adam.
 size_t loss_ws_layout(int Q, int H, int W, float **coef, float **part);

@@ -26,6 +26,7 @@
 // layer and the projection and writes the records (w = real weight) and the
 // imaginary weights after them.
 #include "kernels.h"
+#include "paper.cuh"
 
 namespace wrf {
 
@@ -45,49 +46,11 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-__host__ __device__ inline bool is_skip(int l) { return l == 2 || l == 4 || l == 6; }
-// index of an encoding layer among {0, 2, 4, 6}
-__host__ __device__ inline int enc_index(int l) { return l / 2; }
-
-struct PaperView {
-    int n;
-    const float *mu, *chol, *attn, *psi;
-};
-
 struct PaperNet {
     int n_hidden, width, dm, dt, L_mean, L_tx;
     float room_min[3], room_size[3];
     const float *W[kPaperMaxLayers], *b[kPaperMaxLayers];
 };
-
-// (tanh u + 1) / 2 as an unevaluated sum hi + lo (Fast2Sum of 1 + tanh u,
-// |tanh u| <= 1; halving is exact), the encoding's input on the unit square.
-__device__ __forceinline__ PeArg unit_centre(float u) {
-    const float t = tanhf(u);
-    const float s = __fadd_rn(1.f, t);
-    const float e = __fadd_rn(__fsub_rn(1.f, s), t);
-    return PeArg{0.5f * s, 0.5f * e};
-}
-
-// Reference centre in pixels: x = W (tanh u + 1) / 2, y = H (tanh v + 1) / 2.
-__device__ __forceinline__ void centre(const PaperView &s, int n, const GridView &g, float &x,
-                                       float &y) {
-    const float2 m = reinterpret_cast<const float2 *>(s.mu)[n];
-    x = static_cast<float>(g.W) * pe_value(unit_centre(m.x));
-    y = static_cast<float>(g.H) * pe_value(unit_centre(m.y));
-}
-
-// gamma(x) of Eq. 15 for a d-vector: [x, sin band 0..L-1 (all d), cos ...].
-__device__ void encode_vec(const PeArg *x, int d, int L, float *out) {
-    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
-    for (int k = 0; k < L; ++k)
-        for (int i = 0; i < d; ++i) {
-            float sn, cs;
-            pe_band(x[i], k, sn, cs);
-            out[d + k * d + i] = sn;
-            out[d + L * d + k * d + i] = cs;
-        }
-}
 
 // Column offset of the mean-encoding block in layer l's input.
 __device__ __forceinline__ int mu_off(const PaperNet &m, int l) { return l == 0 ? 0 : m.width; }
@@ -303,25 +266,8 @@ __global__ void __launch_bounds__(kThreads, 2) paper_mlp_kernel(PaperArgs a) {
     }
     __syncthreads();
     // projection (Eq. 12-13 with the paper's primitive), one thread per row
-    if (tid < kRows && n0 + tid < N) {
-        const int n = n0 + tid;
-        float x, y;
-        centre(a.s, n, a.g, x, y);
-        const float mx = x + dout[tid][0], my = y + dout[tid][1];
-        const float *L = a.s.chol + static_cast<size_t>(n) * 3;
-        const float l1 = L[0], l2 = L[1], l3 = L[2];
-        const float sxx = l1 * l1, sxy = l1 * l2, syy = fmaf(l2, l2, l3 * l3);
-        const float det = (l1 * l3) * (l1 * l3);
-        const float inv = 1.f / det;
-        const float A = syy * inv, B = -sxy * inv, C = sxx * inv;
-        const float delta = 1.f / (1.f + expf(-a.s.attn[n])) + dout[tid][4];
-        const float2 ps = reinterpret_cast<const float2 *>(a.s.psi)[n];
-        const float rx = sqrtf(a.g.q_cut * sxx), ry = sqrtf(a.g.q_cut * syy);
-        const size_t row = static_cast<size_t>(q) * N + n;
-        a.rec[2 * row] = make_float4(mx, my, A * kHalfLog2e, B * kHalfLog2e);
-        a.rec[2 * row + 1] = make_float4(C * kHalfLog2e, delta * (ps.x + dout[tid][2]), rx, ry);
-        a.rec_im[row] = delta * (ps.y + dout[tid][3]);
-    }
+    if (tid < kRows && n0 + tid < N)
+        paper_project(a.s, n0 + tid, q, dout[tid], a.g, a.rec, a.rec_im);
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -341,6 +287,9 @@ size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base) {
     w.Wt = take(static_cast<size_t>(kPaperMaxLayers - 1) * kPW * kPW * 4);
     w.bh = take(static_cast<size_t>(kPaperMaxLayers) * kPW * 4);
     w.Wo = take(static_cast<size_t>(kPW) * 8 * 4);
+    w.G = reinterpret_cast<uint16_t *>(take(static_cast<size_t>(n > 0 ? n : 1) * 64 * 2));
+    w.vec = take(static_cast<size_t>(Q > 0 ? Q : 1) * (kPaperMaxLayers - 1) * kPW * 4);
+    w.img = reinterpret_cast<uint16_t *>(take(paper_tc_image_bytes(kPaperMaxLayers - 1)));
     if (ws) *ws = w;
     return off;
 }

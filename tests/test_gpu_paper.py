@@ -172,3 +172,141 @@ def test_paper_workspace_too_small(api):
         api.wrf_paper_deform_project(ds, dm, api.make_grid(H, W, 16, 16, 9.0),
                                      T(synth.make_tx(2, seed=8)), ws=ws)
     assert e.value.status == _lib.WRF_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# Tensor-core network (precision = WRF_BF16): BF16 weights, activations and
+# gamma(mean), FP32 accumulation, the query's encoding term in FP32.
+
+
+def bf16(x):
+    """Round float32 values to the nearest BF16 (ties to even), as float64."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def emulate_paper_bf16(sc, m, tx, Hs=H, Ws=W):
+    """Residuals [Q,N,5] with the tensor-core kernel's rounding points: every
+    product of a BF16 operand pair (activations, gamma(mean) and the weights
+    that multiply them) summed in FP64 and rounded to FP32; the query's term
+    W_s gamma(s) + b in FP32, added in FP32; ReLU, then BF16."""
+    import oracle
+    x0, y0 = paper.centres(sc.mu[:, 0], sc.mu[:, 1], Hs, Ws)
+    gm = bf16(np.stack([oracle.pe(np.array([x / Ws, y / Hs]), m.L_mean) for x, y in zip(x0, y0)]))
+    s = (np.asarray(tx, np.float64) - np.asarray(m.room_min)) / np.asarray(m.room_size)
+    gt = np.stack([oracle.pe(v, m.L_tx) for v in s])
+    dm, width = gm.shape[1], m.W[0].shape[0]
+    Q, N = tx.shape[0], gm.shape[0]
+    h = None
+    for l in range(len(m.W) - 1):
+        Wl = np.asarray(m.W[l], np.float64)
+        if l == 0:
+            z = gm @ bf16(Wl[:, :dm]).T
+            vec = gt @ Wl[:, dm:].T + m.b[l]
+            z = z[None, :, :]
+        elif l in paper.SKIPS:
+            z = h @ bf16(Wl[:, :width]).T + (gm @ bf16(Wl[:, width:width + dm]).T)[None]
+            vec = gt @ Wl[:, width + dm:].T + m.b[l]
+        else:
+            z = h @ bf16(Wl).T
+            vec = np.broadcast_to(np.asarray(m.b[l], np.float64), (Q, width))
+        z = z.astype(np.float32) + vec.astype(np.float32)[:, None, :]
+        h = bf16(np.maximum(z, 0))
+        if h.shape[0] != Q:
+            h = np.broadcast_to(h, (Q, N, width))
+    return (h @ bf16(m.W[-1]).T).astype(np.float32) + np.asarray(m.b[-1], np.float32)
+
+
+def bf16_records(api, sc, m, tx, grid=None):
+    grid = grid or api.make_grid(H, W, 16, 16, 9.0)
+    ds = api.DevicePaperScene.from_host(sc, dev())
+    dm = api.DevicePaperMLP.from_host(m, dev(), precision=api.WRF_BF16)
+    rec = api.wrf_paper_deform_project(ds, dm, grid, T(tx))
+    torch.cuda.synchronize()
+    return rec, rec.cpu().numpy().astype(np.float64), \
+        api.record_tail(rec, tx.shape[0], sc.mu.shape[0]).cpu().numpy()
+
+
+def residuals_from_records(g, tail, sc, Hs=H, Ws=W):
+    """(dmu_x, dmu_y, w_re, w_im) of the GPU records, for comparison."""
+    x0, y0 = paper.centres(sc.mu[:, 0], sc.mu[:, 1], Hs, Ws)
+    return np.stack([g[..., 0] - x0[None], g[..., 1] - y0[None], g[..., 5], tail], -1)
+
+
+def emulated_records(sc, resid, Hs=H, Ws=W):
+    pre, pim = paper.project(sc, resid.astype(np.float64), Hs, Ws, 9.0)
+    x0, y0 = paper.centres(sc.mu[:, 0], sc.mu[:, 1], Hs, Ws)
+    return np.stack([pre[..., 0] - x0[None], pre[..., 1] - y0[None], pre[..., 5], pim[..., 5]], -1)
+
+
+@pytest.mark.parametrize("N,Q", [(1000, 3), (5, 1), (128, 1), (300, 7), (257, 2)])
+def test_paper_bf16_matches_emulation(api, N, Q):
+    """Ragged tiles, a single row, one exact tile, odd tile counts (the last
+    pair of a CTA has one tile)."""
+    sc = synth.make_paper_scene(N, H, W, seed=N)
+    m = paper_mlp(N)
+    tx = synth.make_tx(Q, seed=N)
+    _, g, tail = bf16_records(api, sc, m, tx)
+    got = residuals_from_records(g, tail, sc)
+    want = emulated_records(sc, emulate_paper_bf16(sc, m, tx))
+    scale = np.abs(want).max(axis=(0, 1))
+    rel = np.abs(got - want) / scale
+    ref64 = emulated_records(sc, paper.residuals(sc, m, tx, H, W))
+    e64 = float((np.abs(got - ref64) / scale).max())
+    p50, p99 = np.percentile(rel, [50, 99])
+    print(f"paper bf16 N={N} Q={Q}: vs emulation p50 {p50:.1e} p99 {p99:.1e} max {rel.max():.1e}; "
+          f"vs FP64 oracle {e64:.1e}")
+    # bulk: FP32 accumulation order; a few rows: BF16 rounding flips of an
+    # activation on a rounding boundary, carried through the later layers
+    assert p50 <= 1e-5
+    assert rel.max() <= 2e-2
+
+
+def test_paper_bf16_spectra(api):
+    """Magnitude / phase through binning and the two-channel rasteriser
+    against the oracle's projection and render of the emulated residuals."""
+    sc = synth.make_paper_scene(2000, H, W, seed=11)
+    m = paper_mlp(11)
+    tx = synth.make_tx(3, seed=11)
+    resid = emulate_paper_bf16(sc, m, tx).astype(np.float64)
+    pre, pim = paper.project(sc, resid, H, W, 9.0)
+    import oracle
+    re, s_re = oracle.render(pre, H, W, 9.0)
+    im, s_im = oracle.render(pim, H, W, 9.0)
+    slack = np.maximum(s_re, s_im)
+    r = api.Renderer(api.make_grid(H, W, 32, 8, 9.0), dev())
+    out = r.forward_paper(api.DevicePaperScene.from_host(sc, dev()),
+                          api.DevicePaperMLP.from_host(m, dev(), precision=api.WRF_BF16),
+                          T(tx)).cpu().numpy().astype(np.float64)
+    gm, gp = out[:, 0], out[:, 1]
+    ok_re, e_re, _ = spectrum_error(gm * np.cos(gp), re, slack, 5e-3)
+    ok_im, e_im, _ = spectrum_error(gm * np.sin(gp), im, slack, 5e-3)
+    print(f"paper bf16 spectra vs emulated residuals: re {e_re:.2e}, im {e_im:.2e} (x peak)")
+    assert ok_re and ok_im
+
+
+@pytest.mark.parametrize("width,n_hidden", [(100, 3), (160, 1), (17, 5), (156, 7)])
+def test_paper_bf16_network_shapes(api, width, n_hidden):
+    sc = synth.make_paper_scene(200, H, W, seed=12)
+    m = paper_mlp(12, width=width, n_hidden=n_hidden)
+    tx = synth.make_tx(3, seed=12)
+    _, g, tail = bf16_records(api, sc, m, tx)
+    got = residuals_from_records(g, tail, sc)
+    want = emulated_records(sc, emulate_paper_bf16(sc, m, tx))
+    rel = np.abs(got - want) / np.abs(want).max(axis=(0, 1))
+    print(f"paper bf16 {width} x {n_hidden}: p50 {np.median(rel):.1e} max {rel.max():.1e}")
+    assert np.median(rel) <= 1e-5 and rel.max() <= 2e-2
+
+
+def test_paper_bf16_query_alone_equals_batch_and_repeats(api):
+    """A query's records do not depend on the other queries of the call, and
+    calls repeat bit for bit."""
+    sc = synth.make_paper_scene(700, H, W, seed=13)
+    m = paper_mlp(13)
+    tx = synth.make_tx(5, seed=13)
+    rec, _, _ = bf16_records(api, sc, m, tx)
+    rec2, _, _ = bf16_records(api, sc, m, tx)
+    assert torch.equal(rec, rec2)
+    one, _, _ = bf16_records(api, sc, m, tx[3:4])
+    assert torch.equal(one[0], rec[3])
