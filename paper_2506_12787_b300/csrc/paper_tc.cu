@@ -15,8 +15,11 @@
 // another hidden layer K 0..159.  The encoding part that depends on the
 // query, W_s gamma(s_q), is the same for the 128 rows of a tile: it is
 // computed once per query in FP32 together with the bias (vec[q][l]) and
-// added in the epilogue, like the bias of the other layers.  N = 160 output
-// columns per MMA (M = 128, K = 16 per instruction).
+// added, like the bias of the other layers, by the tensor core: each layer
+// starts with one K = 16 MMA of a selector A (ones in K columns 0 and 1) by
+// a per-warpgroup B image holding the layer's term as BF16 hi + lo, written
+// by the previous epilogue.  N = 160 output columns per MMA (M = 128, K = 16
+// per instruction).
 //
 // The hidden weights (up to 4 panels of 160 rows x 64 K per layer, 20 KB
 // each, 26 panels for the paper's network) do not fit in shared memory
@@ -25,10 +28,11 @@
 // warpgroups consume every panel (their tiles are at most four panels
 // apart), and a slot is refilled once the MMAs of both have completed
 // (tcgen05.commit to the slot's empty barrier, arrival count 2).  Every
-// epilogue reads its row's 160 accumulators from TMEM, adds vec[q][l],
-// applies ReLU and rounds to BF16 into the A tile.  The output layer (N = 16,
-// 5 used) runs on resident weights; its epilogue adds the output bias and
-// projects the Gaussian into its two-channel record.
+// epilogue reads its row's 160 accumulators from TMEM, applies ReLU and
+// rounds to BF16 into the A tile (and writes the next layer's term image).
+// The output layer (N = 16, 5 used, bias by the same selector MMA) runs on
+// resident weights; its epilogue projects the Gaussian into its two-channel
+// record.
 // Every wait is bounded (WRF_ETIMEOUT on the status word).
 #include <cuda_bf16.h>
 
@@ -53,9 +57,12 @@ constexpr uint32_t kOutImg = 3 * kOutPanel;  // K 0..191 (0..159 used)
 constexpr int kGammaK0 = 160;
 constexpr int kGammaCols = 64;
 constexpr uint32_t kTmemCols = 512;          // two accumulators of 160 columns, at 0 and 256
+constexpr uint32_t kTermImg = kPW * 16;      // per-layer term image: 160 rows x 16 B (hi, lo)
+constexpr uint32_t kSelImg = 256;            // selector: two 8 x 16 B core matrices
 
 constexpr size_t tc_smem_bytes() {
-    return 1024 + kWGs * kATile + kRing * kBPanel + kOutImg + (2 * kRing + kWGs + 1) * 8 + 16;
+    return 1024 + kWGs * kATile + kRing * kBPanel + kOutImg + kWGs * kTermImg + kSelImg +
+           (2 * kRing + kWGs + 1) * 8 + 16;
 }
 static_assert(tc_smem_bytes() <= 227 * 1024, "shared memory of one CTA");
 
@@ -203,13 +210,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
     uint8_t *atile0 = base;
     uint8_t *ring = base + kWGs * kATile;
     uint8_t *oimg = ring + kRing * kBPanel;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(oimg + kOutImg);
+    uint8_t *term0 = oimg + kOutImg;         // [kWGs][160 rows x 16 B]
+    uint8_t *sel = term0 + kWGs * kTermImg;   // selector A
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sel + kSelImg);
     uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing;
     uint64_t *wbar = bars + 2 * kRing + kWGs;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(wbar + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid < 16) {
+        // selector: rows 0..7 of core matrix 0 hold (1, 1, 0 ...) in K 0..7,
+        // core matrix 1 (K 8..15) is zero; every 8-row group repeats it
+        const uint32_t one2 = 0x3F803F80u;  // BF16 1.0 twice
+        reinterpret_cast<uint4 *>(sel)[tid] =
+            tid < 8 ? make_uint4(one2, 0u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
     if (tid == 0) {
         for (int i = 0; i < kRing; ++i) {
             mbar_init(&full[i], 1);
@@ -265,6 +281,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
         const int my_row = wq * 32 + lane;
         const bool leader = wt == 0;
         const uint32_t id_h = idesc_bf16(128, kPW), id_o = idesc_bf16(128, 16);
+        uint8_t *term = term0 + wg * kTermImg;
+        const uint64_t d_sel = plain_desc(smem_u32(sel), 128u, 0u);
+        const uint64_t d_term = plain_desc(smem_u32(term), 0u, 128u);
+        // the term image of layer l (vec[q][l], or the output bias when l ==
+        // nh): rows wt and 128 + wt as BF16 hi + lo in K columns 0 and 1
+        auto write_term = [&](int q, int l) {
+            for (int j = wt; j < kPW; j += 128) {
+                float v = 0.f;
+                if (l < a.nh)
+                    v = __ldg(a.vec + (static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + j);
+                else if (j < WRF_OUT)
+                    v = __ldg(a.bout + j);
+                const uint32_t hi = pack_bf16(v, 0.f) & 0xFFFFu;
+                const uint32_t lo = pack_bf16(__fsub_rn(v, __uint_as_float(hi << 16)), 0.f) & 0xFFFFu;
+                *reinterpret_cast<uint4 *>(term + j * 16) = make_uint4(hi | (lo << 16), 0u, 0u, 0u);
+            }
+        };
         uint32_t phase = 0, g = 0;
         wait_or_abort(wbar, 0, abort_flag, a.status);
         for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
@@ -284,14 +317,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                     *reinterpret_cast<uint4 *>(A + a_chunk_off(my_row, kGammaK0 / 8 + c)) = v;
                 }
             }
+            write_term(q, 0);
             fence_async_smem();
             named_bar(1 + wg, 128);
-            const float *vq = a.vec + static_cast<size_t>(q) * (kPaperMaxLayers - 1) * kPW;
             for (int l = 0; l < a.nh; ++l) {
                 if (leader) {
                     tc_fence_after();
                     const int kb = k_begin(l), ke = k_end(l);
-                    uint32_t acc_flag = 0u;
+                    // D = vec[q][l] (hi + lo), then += W_l x
+                    mma_bf16(t_acc, d_sel, d_term, id_h, 0u);
+                    uint32_t acc_flag = 1u;
                     for (int pn = kb / 64; pn <= (ke - 1) / 64; ++pn, ++g) {
                         const int slot = static_cast<int>(g % kRing);
                         wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
@@ -314,19 +349,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                 wait_or_abort(&accb[wg], phase, abort_flag, a.status);
                 phase ^= 1u;
                 tc_fence_after();
-                const float4 *vl = reinterpret_cast<const float4 *>(vq + l * kPW);
+                write_term(q, l + 1);  // the layer-l MMAs that read the image are complete
 #pragma unroll 1
                 for (int c = 0; c < kPW / 32; ++c) {
                     float v[32];
                     tmem_ld32(t_acc + lane_off + c * 32, v);
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const float4 b = __ldg(vl + c * 8 + i);
-                        v[4 * i] += b.x;
-                        v[4 * i + 1] += b.y;
-                        v[4 * i + 2] += b.z;
-                        v[4 * i + 3] += b.w;
-                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         uint4 pk;
@@ -344,12 +371,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
             // output layer: N = 16 (5 used), K 0..159, resident weights
             if (leader) {
                 tc_fence_after();
+                mma_bf16(t_acc, d_sel, d_term, id_o, 0u);  // D = output bias (hi + lo)
 #pragma unroll
                 for (int k = 0; k < kPW; k += 16) {
                     const uint32_t kin = static_cast<uint32_t>((k & 63) >> 4) * 32u;
                     mma_bf16(t_acc, sw128_desc(a_addr + static_cast<uint32_t>(k >> 6) * kAPanel + kin),
                              sw128_desc(o_addr + static_cast<uint32_t>(k >> 6) * kOutPanel + kin), id_o,
-                             k ? 1u : 0u);
+                             1u);
                 }
                 mma_commit(&accb[wg]);
             }
@@ -362,7 +390,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
             if (tv && rv && !*abort_flag) {
                 float d[5];
 #pragma unroll
-                for (int i = 0; i < WRF_OUT; ++i) d[i] = o[i] + __ldg(a.bout + i);
+                for (int i = 0; i < WRF_OUT; ++i) d[i] = o[i];
                 paper_project(a.s, n, q, d, a.g, a.rec, a.rec_im);
             }
             named_bar(1 + wg, 128);  // TMEM columns and the A tile are free again

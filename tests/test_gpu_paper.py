@@ -186,11 +186,19 @@ def bf16(x):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
+def hilo(v):
+    """An FP32 value as the kernel's BF16 pair hi + lo (lo = BF16 of v - hi)."""
+    v = np.asarray(v, np.float32)
+    hi = bf16(v)
+    return hi + bf16((v - hi.astype(np.float32)).astype(np.float32))
+
+
 def emulate_paper_bf16(sc, m, tx, Hs=H, Ws=W):
     """Residuals [Q,N,5] with the tensor-core kernel's rounding points: every
     product of a BF16 operand pair (activations, gamma(mean) and the weights
     that multiply them) summed in FP64 and rounded to FP32; the query's term
-    W_s gamma(s) + b in FP32, added in FP32; ReLU, then BF16."""
+    W_s gamma(s) + b computed in FP32 and entering as BF16 hi + lo (as do the
+    biases); ReLU, then BF16."""
     import oracle
     x0, y0 = paper.centres(sc.mu[:, 0], sc.mu[:, 1], Hs, Ws)
     gm = bf16(np.stack([oracle.pe(np.array([x / Ws, y / Hs]), m.L_mean) for x, y in zip(x0, y0)]))
@@ -211,11 +219,11 @@ def emulate_paper_bf16(sc, m, tx, Hs=H, Ws=W):
         else:
             z = h @ bf16(Wl).T
             vec = np.broadcast_to(np.asarray(m.b[l], np.float64), (Q, width))
-        z = z.astype(np.float32) + vec.astype(np.float32)[:, None, :]
+        z = z.astype(np.float32) + hilo(vec.astype(np.float32)).astype(np.float32)[:, None, :]
         h = bf16(np.maximum(z, 0))
         if h.shape[0] != Q:
             h = np.broadcast_to(h, (Q, N, width))
-    return (h @ bf16(m.W[-1]).T).astype(np.float32) + np.asarray(m.b[-1], np.float32)
+    return (h @ bf16(m.W[-1]).T).astype(np.float32) + hilo(m.b[-1]).astype(np.float32)
 
 
 def bf16_records(api, sc, m, tx, grid=None):
@@ -280,8 +288,12 @@ def test_paper_bf16_spectra(api):
                           api.DevicePaperMLP.from_host(m, dev(), precision=api.WRF_BF16),
                           T(tx)).cpu().numpy().astype(np.float64)
     gm, gp = out[:, 0], out[:, 1]
-    ok_re, e_re, _ = spectrum_error(gm * np.cos(gp), re, slack, 5e-3)
-    ok_im, e_im, _ = spectrum_error(gm * np.sin(gp), im, slack, 5e-3)
+    # flip level: single BF16 rounding flips carried through eight layers move
+    # a record by up to ~5e-3 of its scale (the emulation test's max), i.e.
+    # a centre by up to ~0.05 px at |dmu| ~ 10 px, which bounds the spectrum
+    # difference near 1e-2 x peak rather than at FP32 rounding level
+    ok_re, e_re, _ = spectrum_error(gm * np.cos(gp), re, slack, 1e-2)
+    ok_im, e_im, _ = spectrum_error(gm * np.sin(gp), im, slack, 1e-2)
     print(f"paper bf16 spectra vs emulated residuals: re {e_re:.2e}, im {e_im:.2e} (x peak)")
     assert ok_re and ok_im
 
