@@ -2,37 +2,39 @@
 // tensor cores: BF16 operands, FP32 accumulation in tensor memory.
 //
 // Rows are (query, Gaussian) pairs; a tile is 128 consecutive Gaussians of
-// one query (TMEM lane = row).  A CTA runs two compute warpgroups, each with
-// its own tile, and one producer warp.  Per tile the A operand lives in
-// shared memory as 128 rows x 224 K columns (BF16, K-major, 128-byte
-// swizzle, four 64-column panels):
-//   K 0..159    the previous layer's activations (width <= 160, zero-padded),
-//               rewritten by every epilogue;
-//   K 160..223  gamma(mean_n) of Eq. 15 (42 values, zero-padded), written once
-//               per tile: the encoding part that depends on the Gaussian.
-// Layer l runs over the K range its input holds: layer 0 K 160..223 (the
-// encoding alone), a skip layer K 0..223 (activations and encoding),
-// another hidden layer K 0..159.  The encoding part that depends on the
-// query, W_s gamma(s_q), is the same for the 128 rows of a tile: it is
-// computed once per query in FP32 together with the bias (vec[q][l]) and
-// added, like the bias of the other layers, by the tensor core: each layer
-// starts with one K = 16 MMA of a selector A (ones in K columns 0 and 1) by
-// a per-warpgroup B image holding the layer's term as BF16 hi + lo, written
-// by the previous epilogue.  N = 160 output columns per MMA (M = 128, K = 16
-// per instruction).
+// one query (TMEM lane = row).  A CTA runs two compute groups of eight warps,
+// each group with its own tile (the two warps of a TMEM lane quarter split
+// the 160 columns of every epilogue), and one producer warp.
 //
-// The hidden weights (up to 4 panels of 160 rows x 64 K per layer, 20 KB
-// each, 26 panels for the paper's network) do not fit in shared memory
-// together, so the producer warp streams them with bulk copies through a
-// ring of four panel slots, in the order the layers consume them; both
-// warpgroups consume every panel (their tiles are at most four panels
-// apart), and a slot is refilled once the MMAs of both have completed
-// (tcgen05.commit to the slot's empty barrier, arrival count 2).  Every
-// epilogue reads its row's 160 accumulators from TMEM, applies ReLU and
-// rounds to BF16 into the A tile (and writes the next layer's term image).
-// The output layer (N = 16, 5 used, bias by the same selector MMA) runs on
-// resident weights; its epilogue projects the Gaussian into its two-channel
-// record.
+// A layer's input is split in two operands:
+//   * the previous layer's activations (K 0..159, width <= 160 zero-padded)
+//     stay in tensor memory as BF16 pairs (lane = row, column j = elements
+//     2j, 2j+1): each epilogue reads the FP32 accumulator, applies ReLU,
+//     rounds to BF16 and writes the pairs back (tcgen05.st), where the next
+//     layer's MMAs read their A operand;
+//   * gamma(mean_n) of Eq. 15 (42 values, zero-padded to 64) sits in shared
+//     memory (one 128-byte-swizzled 128 x 64 panel per tile, written once per
+//     tile): the encoding part that depends on the Gaussian, read by layer 0
+//     and by the skip layers.
+// The encoding part that depends on the query, W_s gamma(s_q), is the same
+// for the 128 rows of a tile: it is computed once per query in FP32 together
+// with the bias (vec[q][l]) and added, like the bias of the other layers, by
+// the tensor core: each layer starts with one K = 16 MMA of a selector A
+// (ones in K columns 0 and 1) by a per-group B image holding the layer's term
+// as BF16 hi + lo, written by the previous epilogue.  N = 160 output columns
+// per MMA (M = 128, K = 16 per instruction).
+//
+// The weights arrive as 160-row x 64-K panels (20 KB, 128-byte swizzle):
+// activations K 0..63, 64..127, 128..159 (half used) and the gamma(mean)
+// block, 25 panels for the paper's network in the order the layers consume
+// them.  They do not fit in shared memory together, so the producer warp
+// streams them with bulk copies through a ring of nine slots (two layers and
+// more); both groups consume every panel, a slot is refilled once the MMAs of
+// both have completed (tcgen05.commit to the slot's empty barrier, arrival
+// count 2), and the ring is deep enough for one group to run a layer ahead of
+// the other, so one group's epilogue overlaps the other's MMAs.  The output
+// layer (N = 16, 5 used, bias by the same selector MMA) runs on resident
+// weights; its epilogue projects the Gaussian into its two-channel record.
 // Every wait is bounded (WRF_ETIMEOUT on the status word).
 #include <cuda_bf16.h>
 
@@ -47,31 +49,33 @@ namespace {
 constexpr int kPW = kPaperMaxWidth;          // 160
 constexpr int kTile = 128;
 constexpr int kWGs = 2;
-constexpr int kTcThreads = kWGs * 128 + 32;  // + producer warp
-constexpr uint32_t kAPanel = 128 * 128;      // 128 rows x 64 K x BF16
-constexpr uint32_t kATile = 4 * kAPanel;
-constexpr uint32_t kBPanel = kPW * 128;      // 160 rows x 64 K x BF16
-constexpr int kRing = 4;
+constexpr int kGroup = 256;                  // threads per compute group (8 warps)
+constexpr int kTcThreads = kWGs * kGroup + 32;  // + producer warp
+constexpr uint32_t kGPanel = 128 * 128;      // gamma(mean) A panel: 128 rows x 64 K x BF16
+constexpr uint32_t kBPanel = kPW * 128;      // weight panel: 160 rows x 64 K x BF16
+constexpr int kRing = 9;
 constexpr uint32_t kOutPanel = 16 * 128;     // 16 rows x 64 K x BF16
 constexpr uint32_t kOutImg = 3 * kOutPanel;  // K 0..191 (0..159 used)
-constexpr int kGammaK0 = 160;
 constexpr int kGammaCols = 64;
-constexpr uint32_t kTmemCols = 512;          // two accumulators of 160 columns, at 0 and 256
+constexpr int kGammaPanel = 3;               // panel id of the gamma(mean) block
+// TMEM columns: accumulators at 0 and 256 (160 each), activations (80 BF16
+// pair columns each) at 160 and 416
+constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTermImg = kPW * 16;      // per-layer term image: 160 rows x 16 B (hi, lo)
 constexpr uint32_t kSelImg = 256;            // selector: two 8 x 16 B core matrices
 
 constexpr size_t tc_smem_bytes() {
-    return 1024 + kWGs * kATile + kRing * kBPanel + kOutImg + kWGs * kTermImg + kSelImg +
+    return 1024 + kWGs * kGPanel + kRing * kBPanel + kOutImg + kWGs * kTermImg + kSelImg +
            (2 * kRing + kWGs + 1) * 8 + 16;
 }
 static_assert(tc_smem_bytes() <= 227 * 1024, "shared memory of one CTA");
 
-// K range of layer l's input in A-tile columns.
-__host__ __device__ inline int k_begin(int l) { return l == 0 ? kGammaK0 : 0; }
-__host__ __device__ inline int k_end(int l) {
-    return (l == 0 || is_skip(l)) ? kGammaK0 + kGammaCols : kPW;
+// Panels layer l consumes, in order: activation panels 0, 1, 2 (l >= 1), then
+// the gamma(mean) panel (layer 0 and the skip layers).
+__host__ __device__ inline int panels_of(int l) {
+    return (l == 0 ? 0 : 3) + ((l == 0 || is_skip(l)) ? 1 : 0);
 }
-__host__ __device__ inline int panels_of(int l) { return (k_end(l) - 1) / 64 - k_begin(l) / 64 + 1; }
+__host__ __device__ inline int panel_id(int l, int i) { return l == 0 ? kGammaPanel : i; }
 __host__ __device__ inline int seq_len(int nh) {
     int s = 0;
     for (int l = 0; l < nh; ++l) s += panels_of(l);
@@ -85,18 +89,50 @@ __host__ __device__ inline uint32_t sw128_off(int r, int k) {
                                  (k & 7) * 2);
 }
 
+// A operand from tensor memory (BF16 pairs, lane = row), B from shared memory.
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                            uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 16 / 8 consecutive columns of this warp's 32 lanes from registers.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 struct PaperNetTc {
     int n_hidden, width, dm, dt, L_mean, L_tx;
     float room_min[3], room_size[3];
     const float *W[kPaperMaxLayers], *b[kPaperMaxLayers];
 };
 
-// W_l's input index for A-tile column k (-1: no weight there).
-__device__ inline int input_index(const PaperNetTc &m, int l, int k) {
-    if (l == 0) return (k >= kGammaK0 && k - kGammaK0 < m.dm) ? k - kGammaK0 : -1;
-    if (k < kPW) return k < m.width ? k : -1;
-    if (is_skip(l) && k - kGammaK0 < m.dm) return m.width + (k - kGammaK0);
-    return -1;
+// W_l's input index for column k of panel pid (-1: no weight there).
+__device__ inline int input_index(const PaperNetTc &m, int l, int pid, int k) {
+    if (pid == kGammaPanel) {
+        if (k >= m.dm) return -1;
+        return l == 0 ? k : m.width + k;
+    }
+    const int j = 64 * pid + k;
+    return j < m.width ? j : -1;
 }
 __device__ inline int in_dim_tc(const PaperNetTc &m, int l) {
     return (l == 0 ? 0 : m.width) + (l == 0 || is_skip(l) ? m.dm + m.dt : 0);
@@ -112,19 +148,19 @@ __global__ void paper_tc_weights_kernel(PaperNetTc m, int nseq, uint16_t *wimg, 
         if (i < nseq * per) {
             const int s = static_cast<int>(i / per);
             const int r = static_cast<int>((i % per) / 64), kl = static_cast<int>(i % 64);
-            int l = 0, p = 0, acc = 0;
+            int l = 0, pid = 0, acc = 0;
             for (l = 0; l < m.n_hidden; ++l) {
                 const int np = panels_of(l);
                 if (s < acc + np) {
-                    p = k_begin(l) / 64 + (s - acc);
+                    const int idx = s - acc;
+                    pid = (l == 0 || idx == 3) ? kGammaPanel : idx;
                     break;
                 }
                 acc += np;
             }
-            const int k = 64 * p + kl;
             float v = 0.f;
-            if (k >= k_begin(l) && k < k_end(l) && r < m.width) {
-                const int j = input_index(m, l, k);
+            if (r < m.width) {
+                const int j = input_index(m, l, pid, kl);
                 if (j >= 0) v = m.W[l][static_cast<size_t>(r) * in_dim_tc(m, l) + j];
             }
             const __nv_bfloat16 bv = __float2bfloat16_rn(v);
@@ -198,20 +234,15 @@ struct PaperTcArgs {
     int *status;
 };
 
-__device__ __forceinline__ uint32_t a_chunk_off(int row, int kc) {
-    // 16-byte chunk kc (0..27) of A-tile row `row`
-    return static_cast<uint32_t>((kc >> 3) * kAPanel + row * 128 + (((kc & 7) ^ (row & 7)) << 4));
-}
-
 __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    uint8_t *atile0 = base;
-    uint8_t *ring = base + kWGs * kATile;
+    uint8_t *gp0 = base;                       // [kWGs] gamma(mean) panels
+    uint8_t *ring = base + kWGs * kGPanel;
     uint8_t *oimg = ring + kRing * kBPanel;
-    uint8_t *term0 = oimg + kOutImg;         // [kWGs][160 rows x 16 B]
-    uint8_t *sel = term0 + kWGs * kTermImg;   // selector A
+    uint8_t *term0 = oimg + kOutImg;           // [kWGs][160 rows x 16 B]
+    uint8_t *sel = term0 + kWGs * kTermImg;    // selector A
     uint64_t *bars = reinterpret_cast<uint64_t *>(sel + kSelImg);
     uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing;
     uint64_t *wbar = bars + 2 * kRing + kWGs;
@@ -242,7 +273,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (warp == kWGs * 4) {
+    if (warp == kWGs * (kGroup / 32)) {
         // ---------------------------------------------------- producer warp
         if (lane == 0) {
             mbar_arrive_expect_tx(wbar, kOutImg);
@@ -272,128 +303,149 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
             mbar_wait(wbar, 0, a.status, kWaitLimitNs);
         }
     } else {
-        // ---------------------------------------------- compute warpgroups
-        const int wg = warp >> 2, wq = warp & 3, wt = tid & 127;
-        uint8_t *A = atile0 + wg * kATile;
-        const uint32_t a_addr = smem_u32(A), ring_addr = smem_u32(ring), o_addr = smem_u32(oimg);
+        // ---------------------------------------------- compute groups
+        // group, TMEM lane quarter, column half, thread within the group
+        const int wg = warp / (kGroup / 32), wq = warp & 3, half = (warp >> 2) & 1;
+        const int wt = tid & (kGroup - 1);
+        uint8_t *G = gp0 + wg * kGPanel;
+        const uint32_t g_addr = smem_u32(G), ring_addr = smem_u32(ring), o_addr = smem_u32(oimg);
         const uint32_t t_acc = tmem_base + static_cast<uint32_t>(wg * 256);
+        const uint32_t t_act = t_acc + static_cast<uint32_t>(kPW);
         const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;
         const int my_row = wq * 32 + lane;
-        const bool leader = wt == 0;
+        // the MMA warp of the group: lane 0 issues while lanes 1..31 wait at
+        // the warp's reconvergence point (not on the mbarriers: a diverged
+        // warp spinning there would slow the issuing lane down)
+        const bool mma_warp = wt < 32, leader = wt == 0;
         const uint32_t id_h = idesc_bf16(128, kPW), id_o = idesc_bf16(128, 16);
         uint8_t *term = term0 + wg * kTermImg;
         const uint64_t d_sel = plain_desc(smem_u32(sel), 128u, 0u);
         const uint64_t d_term = plain_desc(smem_u32(term), 0u, 128u);
-        // the term image of layer l (vec[q][l], or the output bias when l ==
-        // nh): rows wt and 128 + wt as BF16 hi + lo in K columns 0 and 1
-        auto write_term = [&](int q, int l) {
-            for (int j = wt; j < kPW; j += 128) {
-                float v = 0.f;
+        // the term of layer l (vec[q][l], or the output bias when l == nh)
+        // for row wt of the image: loaded ahead, written as BF16 hi + lo in K
+        // columns 0 and 1 once the MMAs reading the image have completed
+        auto load_term = [&](int q, int l) {
+            float v = 0.f;
+            if (wt < kPW) {
                 if (l < a.nh)
-                    v = __ldg(a.vec + (static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + j);
-                else if (j < WRF_OUT)
-                    v = __ldg(a.bout + j);
+                    v = __ldg(a.vec + (static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + wt);
+                else if (wt < WRF_OUT)
+                    v = __ldg(a.bout + wt);
+            }
+            return v;
+        };
+        auto write_term = [&](float v) {
+            if (wt < kPW) {
                 const uint32_t hi = pack_bf16(v, 0.f) & 0xFFFFu;
                 const uint32_t lo = pack_bf16(__fsub_rn(v, __uint_as_float(hi << 16)), 0.f) & 0xFFFFu;
-                *reinterpret_cast<uint4 *>(term + j * 16) = make_uint4(hi | (lo << 16), 0u, 0u, 0u);
+                *reinterpret_cast<uint4 *>(term + wt * 16) = make_uint4(hi | (lo << 16), 0u, 0u, 0u);
             }
         };
         uint32_t phase = 0, g = 0;
         wait_or_abort(wbar, 0, abort_flag, a.status);
         for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
-            if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
+            if (wg_bar_any(1 + wg, *abort_flag != 0, kGroup)) break;
             const int tile = 2 * p + wg;
             const bool tv = tile < a.ntiles;
             const int q = tv ? tile / a.tpq : 0;
             const int n = tv ? (tile % a.tpq) * kTile + my_row : a.N;
             const bool rv = n < a.N;
-            // gamma(mean_n) -> A columns 160..223 (chunks 20..27)
+            // gamma(mean_n) -> this tile's panel, 16-byte chunks 4 half .. 4 half + 3
             {
                 const uint4 *src = reinterpret_cast<const uint4 *>(
                     a.G + static_cast<size_t>(rv ? n : 0) * kGammaCols);
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
+                for (int c = 4 * half; c < 4 * half + 4; ++c) {
                     const uint4 v = rv ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
-                    *reinterpret_cast<uint4 *>(A + a_chunk_off(my_row, kGammaK0 / 8 + c)) = v;
+                    *reinterpret_cast<uint4 *>(G + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = v;
                 }
             }
-            write_term(q, 0);
+            write_term(load_term(q, 0));
             fence_async_smem();
-            named_bar(1 + wg, 128);
+            named_bar(1 + wg, kGroup);
             for (int l = 0; l < a.nh; ++l) {
                 if (leader) {
                     tc_fence_after();
-                    const int kb = k_begin(l), ke = k_end(l);
                     // D = vec[q][l] (hi + lo), then += W_l x
                     mma_bf16(t_acc, d_sel, d_term, id_h, 0u);
-                    uint32_t acc_flag = 1u;
-                    for (int pn = kb / 64; pn <= (ke - 1) / 64; ++pn, ++g) {
+                    const int np = panels_of(l);
+                    for (int i = 0; i < np; ++i, ++g) {
                         const int slot = static_cast<int>(g % kRing);
                         wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
                         tc_fence_after();
-                        const int k0 = kb > pn * 64 ? kb : pn * 64;
-                        const int k1 = ke < pn * 64 + 64 ? ke : pn * 64 + 64;
                         const uint32_t b_addr = ring_addr + static_cast<uint32_t>(slot) * kBPanel;
-                        for (int k = k0; k < k1; k += 16) {
-                            const uint32_t kin = static_cast<uint32_t>((k & 63) >> 4) * 32u;
-                            mma_bf16(t_acc, sw128_desc(a_addr + static_cast<uint32_t>(pn) * kAPanel + kin),
-                                     sw128_desc(b_addr + kin), id_h, acc_flag);
-                            acc_flag = 1u;
+                        const int pid = (l == 0 || i == 3) ? kGammaPanel : i;
+                        if (pid == kGammaPanel) {
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u),
+                                         sw128_desc(b_addr + kk * 32u), id_h, 1u);
+                        } else {
+                            // activations K 64 pid .. (K 128..159 for pid 2)
+                            const int nk = pid == 2 ? 2 : 4;
+                            for (int kk = 0; kk < nk; ++kk)
+                                mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>((4 * pid + kk) * 8),
+                                            sw128_desc(b_addr + kk * 32u), id_h, 1u);
                         }
                         mma_commit(&empty[slot]);
                     }
                     mma_commit(&accb[wg]);
-                } else {
-                    g += static_cast<uint32_t>(panels_of(l));
                 }
+                if (mma_warp) __syncwarp();
+                const float tnext = load_term(q, l + 1);  // in flight during the MMAs
                 wait_or_abort(&accb[wg], phase, abort_flag, a.status);
                 phase ^= 1u;
                 tc_fence_after();
-                write_term(q, l + 1);  // the layer-l MMAs that read the image are complete
+                write_term(tnext);  // the layer-l MMAs that read the image are complete
+                // this warp's 80 accumulator columns -> 40 activation columns
 #pragma unroll 1
-                for (int c = 0; c < kPW / 32; ++c) {
+                for (int c = 0; c < 3; ++c) {
+                    const int col = 80 * half + 32 * c;
                     float v[32];
-                    tmem_ld32(t_acc + lane_off + c * 32, v);
+                    uint32_t pk[16];
+                    if (c < 2) {
+                        tmem_ld32(t_acc + lane_off + col, v);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        uint4 pk;
-                        pk.x = pack_bf16_relu(v[8 * j + 0], v[8 * j + 1]);
-                        pk.y = pack_bf16_relu(v[8 * j + 2], v[8 * j + 3]);
-                        pk.z = pack_bf16_relu(v[8 * j + 4], v[8 * j + 5]);
-                        pk.w = pack_bf16_relu(v[8 * j + 6], v[8 * j + 7]);
-                        *reinterpret_cast<uint4 *>(A + a_chunk_off(my_row, c * 4 + j)) = pk;
+                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+                        tmem_st16(t_act + lane_off + col / 2, pk);
+                    } else {
+                        tmem_ld16(t_acc + lane_off + col, v);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+                        tmem_st8(t_act + lane_off + col / 2, pk);
                     }
                 }
+                tmem_wait_st();
                 tc_fence_before();
                 fence_async_smem();
-                named_bar(1 + wg, 128);
+                named_bar(1 + wg, kGroup);
             }
             // output layer: N = 16 (5 used), K 0..159, resident weights
             if (leader) {
                 tc_fence_after();
                 mma_bf16(t_acc, d_sel, d_term, id_o, 0u);  // D = output bias (hi + lo)
 #pragma unroll
-                for (int k = 0; k < kPW; k += 16) {
-                    const uint32_t kin = static_cast<uint32_t>((k & 63) >> 4) * 32u;
-                    mma_bf16(t_acc, sw128_desc(a_addr + static_cast<uint32_t>(k >> 6) * kAPanel + kin),
-                             sw128_desc(o_addr + static_cast<uint32_t>(k >> 6) * kOutPanel + kin), id_o,
-                             1u);
-                }
+                for (int kk = 0; kk < kPW / 16; ++kk)
+                    mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8),
+                                sw128_desc(o_addr + static_cast<uint32_t>(kk >> 2) * kOutPanel +
+                                           static_cast<uint32_t>(kk & 3) * 32u),
+                                id_o, 1u);
                 mma_commit(&accb[wg]);
             }
+            if (mma_warp) __syncwarp();
             wait_or_abort(&accb[wg], phase, abort_flag, a.status);
             phase ^= 1u;
             tc_fence_after();
             float o[16];
             tmem_ld16(t_acc + lane_off, o);
             tc_fence_before();
-            if (tv && rv && !*abort_flag) {
+            if (half == 0 && tv && rv && !*abort_flag) {
                 float d[5];
 #pragma unroll
                 for (int i = 0; i < WRF_OUT; ++i) d[i] = o[i];
                 paper_project(a.s, n, q, d, a.g, a.rec, a.rec_im);
             }
-            named_bar(1 + wg, 128);  // TMEM columns and the A tile are free again
+            named_bar(1 + wg, kGroup);  // TMEM columns and the gamma panel are free again
         }
     }
     tc_fence_before();

@@ -32,15 +32,15 @@ __device__ __forceinline__ void named_bar(int id, int count) {
 }
 // Barrier over the 128 threads of one warpgroup that also ORs `pred` across
 // them, so every thread of the warpgroup takes the same branch afterwards.
-__device__ __forceinline__ bool wg_bar_any(int id, bool pred) {
+__device__ __forceinline__ bool wg_bar_any(int id, bool pred, int count = 128) {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.or.pred q, %2, 128, p;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"(static_cast<uint32_t>(pred)), "r"(id)
+        : "r"(static_cast<uint32_t>(pred)), "r"(id), "r"(count)
         : "memory");
     return r != 0;
 }
