@@ -206,6 +206,16 @@ def measured_peaks():
                 "sm_max_mhz": 2032.0}, "fallback"
 
 
+def alu_peaks(api, stream):
+    """FP32 and MUFU ex2 peaks of this device, measured by the library's probe
+    kernels (wrf_measure_alu_peaks: one-lane fma, two-lane fma.rn.f32x2, ex2),
+    outside every timed region.  The FP32 peak is the larger FMA rate."""
+    fma, fma2, ex2 = api.wrf_measure_alu_peaks(stream)
+    return {"fp32_tflops": max(fma, fma2) / 1e12, "fma_tflops": fma / 1e12,
+            "fma2_tflops": fma2 / 1e12, "ex2_per_s": ex2,
+            "source": "measured on this GPU by wrf_measure_alu_peaks"}
+
+
 def count_in_cutoff(rec, H, W, q_cut, chunk=1 << 18, wrap=False):
     """Number of (pixel, record) pairs with q <= q_cut over all records
     [Q,N,8]: the evaluations the order-free sum needs (Eq. 9), counted per
@@ -605,11 +615,11 @@ def run_rssi(args):
     peaks, _ = measured_peaks()
     nh = len(m.W) - 2
     fl_q = N * (128 + nh * 2 * 128 * 128 + 2 * 128 * 5) + H * W * N * 12
-    fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+    ap = alu_peaks(api, stream)
     t_step = statistics.median(step_ms) * 1e-3
     roof = {"kernel": "rssi_kernel (+ PE / weight prep)", "bound": "alu",
-            "achieved": Q * fl_q / t_step / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
-            "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
+            "achieved": Q * fl_q / t_step / 1e12, "peak": ap["fp32_tflops"], "unit": "TFLOP/s",
+            "peak_source": "FP32 " + ap["source"],
             "flop_per_query": fl_q, "traffic": None}
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": "rssi/s", "value": value, "unit": "rssi/s", "n_gpus": ws, "steps": K,
@@ -770,14 +780,14 @@ def run_paper(args):
     dm_, dt_ = 42, 39
     fl_row = (nh - 1) * 2 * wd * wd + 2 * wd * 5 + wd
     fl = Q * N * fl_row + 4 * 2 * wd * (N * dm_ + Q * dt_)
-    fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
     if prec == api.WRF_BF16:
         roof = {"kernel": "paper_tc_kernel (+ gamma rows / per-query terms / weight panels)",
                 "bound": "tensor", "peak": peaks["bf16_tflops"],
                 "peak_source": "bf16_tflops (measured)"}
     else:
+        ap = alu_peaks(api, stream)
         roof = {"kernel": "paper_mlp_kernel (+ encoding / weight prep)", "bound": "alu",
-                "peak": fp32_peak, "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock"}
+                "peak": ap["fp32_tflops"], "peak_source": "FP32 " + ap["source"]}
     roof.update({"achieved": fl / (stage["paper_deform_project"] * 1e-3) / 1e12,
                  "unit": "TFLOP/s", "flop_per_row": fl_row, "traffic": None, "stage_ms": stage})
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -946,22 +956,28 @@ def main():
         E = count_in_cutoff(fw.rec, H, W, Q_CUT, wrap=args.wrap)
         # two channels: one more FMA per evaluation (the imaginary weight)
         fl_eval = RAST_FLOP_PER_EVAL + 2 * (args.channels - 1)
-        fp32_peak = 148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        ap = alu_peaks(api, stream)
+        t_r = stage["render"] * 1e-3
+        # the two roofs of the order-free sum: FP32 FLOPs and one ex2 per evaluation
+        t_min = max(fl_eval * E / (ap["fp32_tflops"] * 1e12), E / ap["ex2_per_s"])
         roof = {"kernel": "render_kernel", "bound": "alu",
-                "achieved": fl_eval * E / (stage["render"] * 1e-3) / 1e12,
-                "peak": fp32_peak, "unit": "TFLOP/s",
-                "peak_source": "FP32 148 SM x 128 lanes x 2 x max SM clock",
-                "evals_in_cutoff": E}
+                "achieved": fl_eval * E / t_r / 1e12,
+                "peak": ap["fp32_tflops"], "unit": "TFLOP/s",
+                "peak_source": "FP32 " + ap["source"],
+                "evals_in_cutoff": E,
+                "mufu_ex2": {"achieved_per_s": E / t_r, "peak_per_s": ap["ex2_per_s"],
+                             "frac": E / t_r / ap["ex2_per_s"]},
+                "t_min_ms": t_min * 1e3, "frac_of_t_min": t_min / t_r,
+                "alu_peaks": ap}
     elif dom == "deform_project":
         rows = Q * N
-        pk = peaks["bf16_tflops"] if prec == api.WRF_BF16 else \
-            148 * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        pk = peaks["bf16_tflops"] if prec == api.WRF_BF16 else alu_peaks(api, stream)["fp32_tflops"]
         roof = {"kernel": "mlp_tc_kernel" if prec == api.WRF_BF16 else "mlp_f32_kernel",
                 "bound": "tensor" if prec == api.WRF_BF16 else "alu",
                 "achieved": rows * MLP_FLOP_PER_ROW / (stage["deform_project"] * 1e-3) / 1e12,
                 "peak": pk, "unit": "TFLOP/s",
                 "peak_source": f"bf16_tflops ({peak_src})" if prec == api.WRF_BF16 else
-                               "FP32 148 SM x 128 lanes x 2 x max SM clock"}
+                               "FP32 measured on this GPU by wrf_measure_alu_peaks"}
     else:
         nbytes = BIN_BYTES_PER_REC * Q * N + BIN_BYTES_PER_KEY * n_keys + 4 * (Q * fw.T + 1)
         roof = {"kernel": "bin (count+scan+scatter)", "bound": "hbm",

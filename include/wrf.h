@@ -326,6 +326,15 @@ wrf_status wrf_paper_deform_project(const wrf_paper_scene *scene, const wrf_pape
                                     const wrf_grid *grid, const float *tx, int32_t Q, float *rec,
                                     void *ws, size_t ws_bytes, void *stream);
 
+/* Measurement helper (no paper counterpart): the device's FP32 FMA rate in
+ * FLOP/s with one-lane fma and with two-lane fma.rn.f32x2, and its MUFU ex2
+ * rate in results per second, each timed with CUDA events over one launch of
+ * 8 x SMs x 1024 threads (after one warm-up launch) on `stream`.  These are
+ * the denominators of the rooflines of the CUDA-core kernels.  Blocks the
+ * calling thread until the probes finish.                                  */
+wrf_status wrf_measure_alu_peaks(double *fma_flops, double *fma2_flops, double *ex2_per_s,
+                                 void *stream);
+
 /* Backward of wrf_render: from dL/dA [Q][H][W] to d_rec [Q][N][6] =
  * dL/d(mx, my, A, B, C, w) where (A, B, C) is the unscaled inverse
  * covariance (Eq. 8).  Per-pixel weights are recomputed from the records

@@ -28,7 +28,7 @@ EXPORTS = (
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
     "wrf_loss_workspace_size", "wrf_loss", "wrf_adam", "wrf_render_complex",
-    "wrf_paper_workspace_size", "wrf_paper_deform_project",
+    "wrf_paper_workspace_size", "wrf_paper_deform_project", "wrf_measure_alu_peaks",
 )
 
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH):
         "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
         "wrf_render_complex": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
         "wrf_paper_workspace_size": (S, [I32, I32]),
+        "wrf_measure_alu_peaks": (I32, [C.POINTER(C.c_double)] * 3 + [P]),
         "wrf_paper_deform_project": (I32, [C.POINTER(PaperScene), C.POINTER(PaperMlp), gp, P, I32,
                                            P, P, S, P]),
     }

@@ -21,7 +21,8 @@ __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
            "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
-           "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project"]
+           "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project",
+           "wrf_measure_alu_peaks"]
 
 
 def _p(t):
@@ -247,6 +248,15 @@ def wrf_paper_deform_project(scene: DevicePaperScene, mlp, grid, tx, rec=None, w
                                           C.byref(grid), _p(tx), Q, _p(rec), _p(ws),
                                           0 if ws is None else ws.numel(), _stream(stream)))
     return rec
+
+
+def wrf_measure_alu_peaks(stream=None):
+    """(FP32 FLOP/s with fma, FP32 FLOP/s with fma.rn.f32x2, MUFU ex2 per second)
+    of the current device, measured by the library's probe kernels."""
+    L = _lib.load()
+    out = [C.c_double(0.0) for _ in range(3)]
+    _lib.check(L.wrf_measure_alu_peaks(*(C.byref(o) for o in out), _stream(stream)))
+    return tuple(o.value for o in out)
 
 
 def wrf_loss(pred, target, lambda1: float = 0.7, want_grad: bool = True, out=None, d_pred=None,

@@ -344,6 +344,18 @@ wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *
     return WRF_OK;
 }
 
+wrf_status wrf_measure_alu_peaks(double *fma_flops, double *fma2_flops, double *ex2_per_s,
+                                 void *stream) {
+    if (!fma_flops || !fma2_flops || !ex2_per_s) return fail(WRF_EINVAL, "output is NULL");
+    double r[3] = {0, 0, 0};
+    cudaError_t e = wrf::measure_alu_peaks(r, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "peak probes");
+    *fma_flops = r[0];
+    *fma2_flops = r[1];
+    *ex2_per_s = r[2];
+    return WRF_OK;
+}
+
 size_t wrf_paper_workspace_size(int32_t n, int32_t Q) {
     return wrf::paper_ws_layout(n < 0 ? 0 : n, Q < 0 ? 0 : Q, nullptr, nullptr);
 }

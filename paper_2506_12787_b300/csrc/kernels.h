@@ -62,6 +62,9 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
 cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
                            float4 *rec, uint32_t *count, cudaStream_t st);
 
+// FP32 FMA (one- and two-lane) and MUFU ex2 rate probes (peaks.cu): out3 = FLOP/s, FLOP/s, ex2/s.
+cudaError_t measure_alu_peaks(double *out3, cudaStream_t st);
+
 // The paper's primitive and deformation head (paper.cu).
 constexpr int kPaperMaxWidth = 160;
 constexpr int kPaperMaxLayers = 9;  // <= 8 hidden + output
