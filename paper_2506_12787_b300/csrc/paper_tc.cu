@@ -199,28 +199,27 @@ __global__ void paper_tc_gamma_kernel(PaperView s, int L_mean, int dm, uint16_t 
 }
 
 // vec[q][l][j] (FP32): W_s gamma(s_q) + b for the layers whose input holds
-// the encoding, b for the others, zero past the width.
+// the encoding, b for the others, zero past the width; one block per (q, l).
 __global__ void __launch_bounds__(kPW) paper_tc_vec_kernel(PaperNetTc m, const float *tx, float *vec) {
     __shared__ float gam[3 * (2 * 15 + 1)];
-    const int q = blockIdx.x, j = threadIdx.x;
-    if (j == 0) {
+    const int q = blockIdx.x, l = blockIdx.y, j = threadIdx.x;
+    const bool enc = l < m.n_hidden && (l == 0 || is_skip(l));
+    if (enc && j == 0) {
         PeArg a[3];
         for (int c = 0; c < 3; ++c) a[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
         encode_vec(a, 3, m.L_tx, gam);
     }
     __syncthreads();
-    for (int l = 0; l < kPaperMaxLayers - 1; ++l) {
-        float acc = 0.f;
-        if (l < m.n_hidden && j < m.width) {
-            if (l == 0 || is_skip(l)) {
-                const float *wr = m.W[l] + static_cast<size_t>(j) * in_dim_tc(m, l) +
-                                  (l == 0 ? 0 : m.width) + m.dm;
-                for (int k = 0; k < m.dt; ++k) acc = fmaf(__ldg(wr + k), gam[k], acc);
-            }
-            acc += m.b[l][j];
+    float acc = 0.f;
+    if (l < m.n_hidden && j < m.width) {
+        if (enc) {
+            const float *wr = m.W[l] + static_cast<size_t>(j) * in_dim_tc(m, l) +
+                              (l == 0 ? 0 : m.width) + m.dm;
+            for (int k = 0; k < m.dt; ++k) acc = fmaf(__ldg(wr + k), gam[k], acc);
         }
-        vec[(static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + j] = acc;
+        acc += m.b[l][j];
     }
+    vec[(static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + j] = acc;
 }
 
 struct PaperTcArgs {
@@ -489,7 +488,7 @@ cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, co
     uint16_t *oimg = ws.img + static_cast<size_t>(nseq) * kBPanel / 2;
     paper_tc_weights_kernel<<<148 * 2, 256, 0, st>>>(m, nseq, wimg, oimg);
     paper_tc_gamma_kernel<<<(sv.n + 127) / 128, 128, 0, st>>>(s, m.L_mean, m.dm, ws.G);
-    paper_tc_vec_kernel<<<Q, kPW, 0, st>>>(m, tx, ws.vec);
+    paper_tc_vec_kernel<<<dim3(Q, kPaperMaxLayers - 1), kPW, 0, st>>>(m, tx, ws.vec);
     PaperTcArgs a{};
     a.s = s;
     a.g = g;
