@@ -322,3 +322,37 @@ def test_paper_bf16_query_alone_equals_batch_and_repeats(api):
     assert torch.equal(rec, rec2)
     one, _, _ = bf16_records(api, sc, m, tx[3:4])
     assert torch.equal(one[0], rec[3])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_paper_workload_full_size_sampled(api, precision):
+    """The bench's paper workload as the bench launches it (20,000 Gaussians,
+    64 TX, 360x90, tile 32x8, unit-gain network with small biases): two whole
+    queries of the batch against the oracle -- the FP64 head for FP32, the
+    projection and render of the BF16-emulated residuals for BF16."""
+    import math as _m
+    import oracle
+    sc = synth.make_paper_scene(20000, H, W, ls_mean=_m.log(3.0), ls_std=0.3, seed=0)
+    m = synth.make_paper_mlp(gain=1.0, bias_std=0.05, seed=0)
+    tx = synth.make_tx(64, seed=1)
+    prec = api.WRF_BF16 if precision == "bf16" else api.WRF_FP32
+    r = api.Renderer(api.make_grid(H, W, 32, 8, 9.0), dev())
+    out = r.forward_paper(api.DevicePaperScene.from_host(sc, dev()),
+                          api.DevicePaperMLP.from_host(m, dev(), precision=prec), T(tx))
+    torch.cuda.synchronize()
+    picks = [0, 37]
+    g = out.cpu().numpy()[picks].astype(np.float64)
+    if precision == "fp32":
+        mag, ph, re, im, slack, _ = paper.forward(sc, m, tx[picks], H, W, 9.0)
+        tol = 1e-4
+    else:
+        resid = emulate_paper_bf16(sc, m, tx[picks]).astype(np.float64)
+        pre, pim = paper.project(sc, resid, H, W, 9.0)
+        re, s_re = oracle.render(pre, H, W, 9.0)
+        im, s_im = oracle.render(pim, H, W, 9.0)
+        slack = np.maximum(s_re, s_im)
+        tol = 1e-2
+    ok_re, e_re, _ = spectrum_error(g[:, 0] * np.cos(g[:, 1]), re, slack, tol)
+    ok_im, e_im, _ = spectrum_error(g[:, 0] * np.sin(g[:, 1]), im, slack, tol)
+    print(f"paper workload {precision}, queries {picks}: re {e_re:.2e}, im {e_im:.2e} (x peak)")
+    assert ok_re and ok_im
