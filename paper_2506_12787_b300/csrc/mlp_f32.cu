@@ -1,103 +1,147 @@
 // Deformation MLP on the CUDA cores in FP32 (Sec. 4.2, Eq. 14).
 //
-// One CTA takes 32 (query, Gaussian) rows.  Activations live in shared
-// memory column-major ([unit][row]) so that lane = row reads them without
-// bank conflicts; warp w produces hidden units 32w..32w+31 for all 32 rows,
-// reading the transposed weights as warp-uniform float4 broadcasts.
-// Layer 1 starts from ReLU(U[n] + V[q]) (see prep.cu).  The epilogue either
-// stores the residual row or deforms and projects the Gaussian in place.
+// A CTA takes ROWS consecutive (query, Gaussian) rows (64, or 32 for small
+// problems so that more SMs take part).  Activations live in shared memory
+// transposed ([unit][row], padded pitch), and thread t computes a 4-row x
+// 8-unit register tile of every hidden layer: rows 4 (t % (ROWS/4)) .., units
+// 8 (t / (ROWS/4)) ..; per input k it reads one float4 of activations and two
+// float4 of weights for 32 FMAs.  The transposed weights ([k][unit]) stream
+// through two shared buffers of 16 inputs each with cp.async, one chunk
+// ahead of the products.  Every output sums its bias, then w_k h_k in
+// ascending k.  Layer 1 starts from ReLU(U[n] + V[q]) (see prep.cu).  The
+// epilogue evaluates the output layer and either stores the residual row or
+// deforms and projects the Gaussian.
 #include "kernels.h"
 
 namespace wrf {
 
 namespace {
 
-constexpr int kRows = 32;
+constexpr int kH = WRF_HIDDEN;  // 128
+constexpr int kKC = 16;         // inputs per staged weight chunk
 
-__global__ void __launch_bounds__(128) mlp_f32_kernel(SceneView s, MlpView m, GridView g, int Q,
-                                                      DeformWs ws, int mode, float *resid,
-                                                      float4 *rec, uint32_t *count,
-                                                      float *rec_im) {
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int ROWS>
+struct F32Cfg {
+    static constexpr int RG = ROWS / 4;          // row groups
+    static constexpr int THREADS = RG * (kH / 8);  // x 16 unit groups
+    static constexpr int PITCH = ROWS + 4;       // floats per unit of the activations
+    static constexpr size_t smem = (static_cast<size_t>(2 * kKC) * kH + 2 * kH * PITCH + kH * 8) * 4;
+};
+
+template <int ROWS>
+__global__ void __launch_bounds__(F32Cfg<ROWS>::THREADS) mlp_f32_kernel(
+    SceneView s, MlpView m, GridView g, int Q, DeformWs ws, int mode, float *resid, float4 *rec,
+    uint32_t *count, float *rec_im) {
+    using C = F32Cfg<ROWS>;
+    constexpr int T = C::THREADS, P = C::PITCH;
     extern __shared__ __align__(16) float smem[];
-    float *act0 = smem;                                   // [128][32]
-    float *act1 = act0 + WRF_HIDDEN * kRows;              // [128][32]
-    float *wt = act1 + WRF_HIDDEN * kRows;                // [128][128]
-    float *wo = wt + WRF_HIDDEN * WRF_HIDDEN;             // [128][8]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *wbuf = smem;                       // [2][kKC][kH]
+    float *hin = wbuf + 2 * kKC * kH;         // [kH][P]
+    float *hout = hin + kH * P;               // [kH][P]
+    float *wo = hout + kH * P;                // [kH][8]
+    __shared__ float dout[ROWS][8];
+    const int tid = threadIdx.x;
+    const int rg = tid % C::RG, cg = tid / C::RG;
     const long long rows = static_cast<long long>(Q) * s.n;
-    const long long r0 = static_cast<long long>(blockIdx.x) * kRows;
-
-    // Layer 1: h1 = ReLU(U[n] + V[q]).  Lane = row; warp w fills units
-    // 32w..32w+31 (each lane walks its own row of U, so the 128-byte line is
-    // reused from L1 across the 32 iterations).
-    {
-        const long long row = r0 + lane;
-        const bool ok = row < rows;
-        const int q = ok ? static_cast<int>(row / s.n) : 0;
-        const int n = ok ? static_cast<int>(row % s.n) : 0;
-        const float *u = ws.U + static_cast<size_t>(n) * WRF_HIDDEN + warp * 32;
-        const float *v = ws.V + static_cast<size_t>(q) * WRF_HIDDEN + warp * 32;
-        for (int jj = 0; jj < 32; ++jj)
-            act0[(warp * 32 + jj) * kRows + lane] = ok ? fmaxf(u[jj] + v[jj], 0.f) : 0.f;
-    }
-    for (int i = threadIdx.x; i < WRF_HIDDEN * 8 / 4; i += blockDim.x)
+    const long long r0 = static_cast<long long>(blockIdx.x) * ROWS;
+    const int nh = m.n_layers - 2;
+    const int nchunk = nh * (kH / kKC);
+    auto stage = [&](int c) {
+        const int l = c / (kH / kKC), k0 = (c % (kH / kKC)) * kKC;
+        const float4 *src = reinterpret_cast<const float4 *>(
+            ws.wt_f32 + (static_cast<size_t>(l) * kH + k0) * kH);
+        float4 *dst = reinterpret_cast<float4 *>(wbuf + (c & 1) * kKC * kH);
+        for (int i = tid; i < kKC * kH / 4; i += T) cp_async16(dst + i, src + i);
+        cp_async_commit();
+    };
+    if (nchunk > 0) stage(0);
+    for (int i = tid; i < kH * 8 / 4; i += T)
         reinterpret_cast<float4 *>(wo)[i] = reinterpret_cast<const float4 *>(ws.wo_f32)[i];
-
-    float *in = act0, *out = act1;
-    for (int l = 0; l < m.n_layers - 2; ++l) {
-        __syncthreads();  // previous layer's activations and weight reads done
-        const float4 *src = reinterpret_cast<const float4 *>(ws.wt_f32 +
-                                                             static_cast<size_t>(l) * WRF_HIDDEN *
-                                                                 WRF_HIDDEN);
-        for (int i = threadIdx.x; i < WRF_HIDDEN * WRF_HIDDEN / 4; i += blockDim.x)
-            reinterpret_cast<float4 *>(wt)[i] = src[i];
-        __syncthreads();
-        float acc[32];
-        const float *bl = m.bh[l] + warp * 32;
+    // layer 1: h = ReLU(U[n] + V[q]); lanes take consecutive rows (conflict-
+    // free transposed stores), each loading 4 units
+    for (int e = tid; e < ROWS * kH / 4; e += T) {
+        const int r = e % ROWS, j4 = 4 * (e / ROWS);
+        const long long row = r0 + r;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < rows) {
+            const int q = static_cast<int>(row / s.n), n = static_cast<int>(row % s.n);
+            const float4 u = __ldg(reinterpret_cast<const float4 *>(ws.U + static_cast<size_t>(n) * kH + j4));
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(ws.V + static_cast<size_t>(q) * kH + j4));
+            h = make_float4(fmaxf(u.x + v.x, 0.f), fmaxf(u.y + v.y, 0.f), fmaxf(u.z + v.z, 0.f),
+                            fmaxf(u.w + v.w, 0.f));
+        }
+        hin[(j4 + 0) * P + r] = h.x;
+        hin[(j4 + 1) * P + r] = h.y;
+        hin[(j4 + 2) * P + r] = h.z;
+        hin[(j4 + 3) * P + r] = h.w;
+    }
+    float acc[4][8];
+    for (int c = 0; c < nchunk; ++c) {
+        const int l = c / (kH / kKC), kc = c % (kH / kKC);
+        if (kc == 0) {
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) acc[jj] = bl[jj];
-#pragma unroll 2
-        for (int k = 0; k < WRF_HIDDEN; ++k) {
-            float h = in[k * kRows + lane];
-            const float4 *wk = reinterpret_cast<const float4 *>(wt + k * WRF_HIDDEN + warp * 32);
+            for (int j = 0; j < 8; ++j) {
+                const float bv = __ldg(m.bh[l] + 8 * cg + j);
 #pragma unroll
-            for (int v4 = 0; v4 < 8; ++v4) {
-                float4 w = wk[v4];
-                acc[4 * v4 + 0] = fmaf(w.x, h, acc[4 * v4 + 0]);
-                acc[4 * v4 + 1] = fmaf(w.y, h, acc[4 * v4 + 1]);
-                acc[4 * v4 + 2] = fmaf(w.z, h, acc[4 * v4 + 2]);
-                acc[4 * v4 + 3] = fmaf(w.w, h, acc[4 * v4 + 3]);
+                for (int r = 0; r < 4; ++r) acc[r][j] = bv;
             }
         }
+        // chunk c has landed for every thread, every thread is done with the
+        // buffer the next chunk overwrites and with the previous layer
+        cp_async_wait_all();
+        __syncthreads();
+        if (c + 1 < nchunk) stage(c + 1);
+        const float *wb = wbuf + (c & 1) * kKC * kH;
+        const float *hk = hin + kc * kKC * P;
+#pragma unroll 8
+        for (int k = 0; k < kKC; ++k) {
+            const float4 hv = *reinterpret_cast<const float4 *>(hk + k * P + 4 * rg);
+            const float4 wa = *reinterpret_cast<const float4 *>(wb + k * kH + 8 * cg);
+            const float4 wc = *reinterpret_cast<const float4 *>(wb + k * kH + 8 * cg + 4);
+            const float h[4] = {hv.x, hv.y, hv.z, hv.w};
+            const float w[8] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) out[(warp * 32 + jj) * kRows + lane] = fmaxf(acc[jj], 0.f);
-        float *t = in;
-        in = out;
-        out = t;
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[r][j] = fmaf(w[j], h[r], acc[r][j]);
+        }
+        if (kc == kH / kKC - 1) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4 *>(hout + (8 * cg + j) * P + 4 * rg) =
+                    make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f),
+                                fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+            float *t = hin;
+            hin = hout;
+            hout = t;
+        }
     }
     __syncthreads();
-    if (warp != 0) return;
-    const long long row = r0 + lane;
-    if (row >= rows) return;
-    float o[WRF_OUT];
-#pragma unroll
-    for (int j = 0; j < WRF_OUT; ++j) o[j] = m.bo[j];
-    for (int k = 0; k < WRF_HIDDEN; ++k) {
-        float h = in[k * kRows + lane];
-        float4 w0 = reinterpret_cast<const float4 *>(wo + k * 8)[0];
-        float w4 = wo[k * 8 + 4];
-        o[0] = fmaf(w0.x, h, o[0]);
-        o[1] = fmaf(w0.y, h, o[1]);
-        o[2] = fmaf(w0.z, h, o[2]);
-        o[3] = fmaf(w0.w, h, o[3]);
-        o[4] = fmaf(w4, h, o[4]);
+    // output layer: (row, output) pairs over the threads
+    for (int i = tid; i < ROWS * WRF_OUT; i += T) {
+        const int r = i / WRF_OUT, o = i % WRF_OUT;
+        float a = __ldg(m.bo + o);
+        for (int k = 0; k < kH; ++k) a = fmaf(wo[k * 8 + o], hin[k * P + r], a);
+        dout[r][o] = a;
     }
+    __syncthreads();
+    if (tid >= ROWS) return;
+    const long long row = r0 + tid;
+    if (row >= rows) return;
+    const float *o = dout[tid];
     if (mode == 0) {
         float *dst = resid + row * WRF_OUT;
 #pragma unroll
         for (int j = 0; j < WRF_OUT; ++j) dst[j] = o[j];
     } else {
-        int n = static_cast<int>(row % s.n);
+        const int n = static_cast<int>(row % s.n);
         float4 a, b;
         const GaussParams p = load_params(s, n);
         project_geom(p, o[0], o[1], o[2], o[3], o[4], g, a, b);
@@ -108,24 +152,35 @@ __global__ void __launch_bounds__(128) mlp_f32_kernel(SceneView s, MlpView m, Gr
     }
 }
 
+template <int ROWS>
+cudaError_t launch_rows(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                        const DeformWs &ws, int mode, float *resid, float4 *rec, uint32_t *count,
+                        float *rec_im, long long rows, cudaStream_t st) {
+    using C = F32Cfg<ROWS>;
+    cudaError_t e = cudaFuncSetAttribute(mlp_f32_kernel<ROWS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(C::smem));
+    if (e != cudaSuccess) return e;
+    const long long blocks = (rows + ROWS - 1) / ROWS;
+    mlp_f32_kernel<ROWS><<<static_cast<unsigned>(blocks), C::THREADS, C::smem, st>>>(
+        s, m, g, Q, ws, mode, resid, rec, count, rec_im);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                            const DeformWs &ws, int mode, float *resid, float4 *rec,
                            uint32_t *count, cudaStream_t st) {
-    long long rows = static_cast<long long>(Q) * s.n;
+    const long long rows = static_cast<long long>(Q) * s.n;
     if (rows == 0) return cudaSuccess;
-    size_t smem = (2 * WRF_HIDDEN * kRows + WRF_HIDDEN * WRF_HIDDEN + WRF_HIDDEN * 8) * 4;
-    cudaError_t e = cudaFuncSetAttribute(mlp_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    long long blocks = (rows + kRows - 1) / kRows;
     // two channels: the imaginary weights follow the Q x N records
     float *rec_im = (mode == 1 && s.channels == 2) ? reinterpret_cast<float *>(rec + 2 * rows)
                                                    : nullptr;
-    mlp_f32_kernel<<<static_cast<unsigned>(blocks), 128, smem, st>>>(s, m, g, Q, ws, mode, resid,
-                                                                     rec, count, rec_im);
-    return cudaGetLastError();
+    // small problems: 32-row CTAs so that more SMs take part
+    if (rows < 148LL * 64 * 4)
+        return launch_rows<32>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, rows, st);
+    return launch_rows<64>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, rows, st);
 }
 
 }  // namespace wrf
