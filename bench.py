@@ -431,7 +431,8 @@ def run_train(args):
                                                "amp")])
     dm = api.DeviceMLP(mlp_p[0::2], mlp_p[1::2])
     r = api.Renderer(cfg.grid, dev, fused=False)
-    pred = r.forward(ds, dm, tx).clone()
+    acts = torch.empty((len(mlp_p) // 2 - 1, Q * N, 128), dtype=torch.float32, device=dev)
+    pred = r.forward(ds, dm, tx, acts=acts).clone()
     _, dA = api.wrf_loss(pred, tgt, tcfg.lambda1)
     L = r.last
     adam_state = [(p, torch.zeros_like(p), torch.zeros_like(p), torch.zeros_like(p))
@@ -450,22 +451,23 @@ def run_train(args):
     d_rec = api.wrf_render_backward(L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, N, Q,
                                     cfg.grid, dA)
     g = api.wrf_project_backward(ds, L["resid"], Q, d_rec)
-    stage = {"forward": t(lambda: r.forward(ds, dm, tx)),
+    stage = {"forward": t(lambda: r.forward(ds, dm, tx, acts=acts)),
              "loss_l1_ssim": t(lambda: api.wrf_loss(pred, tgt, tcfg.lambda1)),
              "render_backward": t(lambda: api.wrf_render_backward(
                  L["rec"], L["gids"], L["offs"], L["n_keys"], r.cap, N, Q, cfg.grid, dA)),
              "project_backward": t(lambda: api.wrf_project_backward(ds, L["resid"], Q, d_rec)),
              "deform_backward": t(lambda: api.wrf_deform_backward(ds, dm, cfg.grid, tx,
                                                                   g["d_resid"],
-                                                                  stop_grad_mean=True)),
+                                                                  stop_grad_mean=True,
+                                                                  acts=acts)),
              "adam": t(lambda: api.wrf_adam([(p.clone(), gg, m_, v_, 1e-3)
                                              for p, gg, m_, v_ in adam_state], 1))}
     peaks, peak_src = measured_peaks()
-    # MLP backward algorithmic FLOP per row: forward recompute of the hidden
-    # layers (3 x 2*128^2), delta chain through them and the output
-    # (3 x 2*128^2 + 2*128*5), weight gradients (4 x 2*128^2 + 2*128*89 +
-    # 2*128*5), d_mean through W1m (2*128*26)
-    fl_row = 3 * 2 * 128 * 128 * 2 + 2 * 128 * 5 + 4 * 2 * 128 * 128 + 2 * 128 * 89 + \
+    # MLP backward algorithmic FLOP per row (the forward saved its hidden
+    # activations, so none are recomputed): delta chain through the hidden
+    # layers and the output (3 x 2*128^2 + 2*128*5), weight gradients
+    # (4 x 2*128^2 + 2*128*89 + 2*128*5), d_mean through W1m (2*128*26)
+    fl_row = 3 * 2 * 128 * 128 + 2 * 128 * 5 + 4 * 2 * 128 * 128 + 2 * 128 * 89 + \
         2 * 128 * 5 + 2 * 128 * 26
     # the MLP backward's GEMMs are FP32 emulated on the BF16 tensor cores with
     # a three-term split (nine BF16 products per FP32 product)

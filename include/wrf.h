@@ -128,6 +128,15 @@ wrf_status wrf_deform(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid
                       const float *tx, int32_t Q, float *resid, void *ws, size_t ws_bytes,
                       void *stream);
 
+/* As wrf_deform, and also stores every hidden activation for the backward
+ * (training): acts [n_layers - 1][Q][N][128] FP32 device, row-major, layer l
+ * = the output of hidden layer l + 1 after its ReLU (the first entry is the
+ * first layer's output).  mlp->precision must be WRF_FP32 (else
+ * WRF_EUNSUPPORTED).  Needs (n_layers - 1) x Q x N x 512 bytes.           */
+wrf_status wrf_deform_acts(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                           const float *tx, int32_t Q, float *resid, float *acts, void *ws,
+                           size_t ws_bytes, void *stream);
+
 /* Deform + project: Eq. 12-13 applied to every (query, Gaussian) row, giving
  * the projected record (layout above) and, if tile_count is non-NULL, the
  * number of tiles its footprint rectangle covers.
@@ -363,10 +372,12 @@ wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int3
  * is part of ws, but the first call on a device creates one cuBLAS handle,
  * for which cuBLAS allocates its own small device state: make that first
  * call outside any stream capture.  The weight gradients are accumulated
- * with FP32 atomics and reductions whose order is not fixed.               */
+ * with FP32 atomics and reductions whose order is not fixed.
+ *   acts  the hidden activations saved by wrf_deform_acts for the same
+ *         scene, MLP and tx, or NULL: then the forward is recomputed.      */
 size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp);
 wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
-                               const float *tx, int32_t Q, const float *d_resid, float *const *dW,
+                               const float *tx, int32_t Q, const float *d_resid, const float *acts, float *const *dW,
                                float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
                                size_t ws_bytes, void *stream);
 

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "WRF_OK", -1: "WRF_EINVAL", -2: "WRF_ENOSPC", -3: "WRF_ECUDA"
 
 # Every symbol include/wrf.h declares (checked by the CPU test suite).
 EXPORTS = (
-    "wrf_deform_workspace_size", "wrf_deform", "wrf_project", "wrf_deform_project",
+    "wrf_deform_workspace_size", "wrf_deform", "wrf_deform_acts", "wrf_project",
+    "wrf_deform_project",
     "wrf_bin_workspace_size", "wrf_bin", "wrf_bin_noalloc", "wrf_render", "wrf_render_backward",
     "wrf_project_backward", "wrf_deform_backward_workspace_size", "wrf_deform_backward",
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
     sig = {
         "wrf_deform_workspace_size": (S, [I32, I32, mp]),
         "wrf_deform": (I32, [sp, mp, gp, P, I32, P, P, S, P]),
+        "wrf_deform_acts": (I32, [sp, mp, gp, P, I32, P, P, P, S, P]),
         "wrf_project": (I32, [sp, P, I32, gp, P, P, P]),
         "wrf_deform_project": (I32, [sp, mp, gp, P, I32, P, P, P, S, P]),
         "wrf_bin_workspace_size": (S, [I32, I32, gp]),
@@ -99,7 +101,7 @@ def load(path: str = LIB_PATH):
         "wrf_render_backward": (I32, [P, P, P, P, I64, I32, I32, gp, P, P, P]),
         "wrf_project_backward": (I32, [sp, P, I32, P, P, P, P, P, P, P, P]),
         "wrf_deform_backward_workspace_size": (S, [I32, I32, mp]),
-        "wrf_deform_backward": (I32, [sp, mp, gp, P, I32, P, P, P, P, I32, P, S, P]),
+        "wrf_deform_backward": (I32, [sp, mp, gp, P, I32, P, P, P, P, P, I32, P, S, P]),
         "wrf_status_read": (I32, [P]),
         "wrf_last_error": (C.c_char_p, []),
         "wrf_version": (I32, []),

@@ -22,7 +22,7 @@ __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
            "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
            "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project",
-           "wrf_measure_alu_peaks"]
+           "wrf_measure_alu_peaks", "wrf_deform_acts"]
 
 
 def _p(t):
@@ -148,6 +148,24 @@ def wrf_deform(scene: DeviceScene, mlp: DeviceMLP, grid, tx, resid=None, ws=None
     _lib.check(L.wrf_deform(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q, _p(resid),
                             _p(ws), ws.numel(), _stream(stream)))
     return resid
+
+
+def wrf_deform_acts(scene: DeviceScene, mlp: DeviceMLP, grid, tx, resid=None, acts=None, ws=None,
+                    stream=None):
+    """Residuals [Q,N,5] and the hidden activations [n_layers-1, Q*N, 128]
+    (FP32 MLP) saved for wrf_deform_backward."""
+    L = _lib.load()
+    Q, dev = int(tx.shape[0]), tx.device
+    mc = mlp.c()
+    if resid is None:
+        resid = torch.empty((Q, scene.n, 5), dtype=torch.float32, device=dev)
+    if acts is None:
+        acts = torch.empty((len(mlp.W) - 1, Q * scene.n, 128), dtype=torch.float32, device=dev)
+    need = L.wrf_deform_workspace_size(scene.n, Q, C.byref(mc))
+    ws = _ws(need, dev) if ws is None else ws
+    _lib.check(L.wrf_deform_acts(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
+                                 _p(resid), _p(acts), _p(ws), ws.numel(), _stream(stream)))
+    return resid, acts
 
 
 def wrf_project(scene: DeviceScene, resid, Q: int, grid, rec=None, tile_count=None, stream=None):
@@ -373,8 +391,9 @@ def wrf_project_backward(scene: DeviceScene, resid, Q: int, d_rec, d_resid=None,
 
 
 def wrf_deform_backward(scene: DeviceScene, mlp: DeviceMLP, grid, tx, d_resid, d_mean=None,
-                        stop_grad_mean=False, ws=None, stream=None):
-    """dW, db (lists) and d_mean accumulated through gamma(mean) (unless stopped)."""
+                        stop_grad_mean=False, ws=None, stream=None, acts=None):
+    """dW, db (lists) and d_mean accumulated through gamma(mean) (unless stopped);
+    acts: the activations saved by wrf_deform_acts (else recomputed)."""
     L = _lib.load()
     dev, Q = tx.device, int(tx.shape[0])
     mc = mlp.c()
@@ -388,7 +407,8 @@ def wrf_deform_backward(scene: DeviceScene, mlp: DeviceMLP, grid, tx, d_resid, d
     need = L.wrf_deform_backward_workspace_size(scene.n, Q, C.byref(mc))
     ws = _ws(need, dev) if ws is None else ws
     _lib.check(L.wrf_deform_backward(C.byref(scene.c()), C.byref(mc), C.byref(grid), _p(tx), Q,
-                                     _p(d_resid), pW, pb, _p(d_mean), int(bool(stop_grad_mean)),
+                                     _p(d_resid), _p(acts), pW, pb, _p(d_mean),
+                                     int(bool(stop_grad_mean)),
                                      _p(ws), ws.numel(), _stream(stream)))
     return dW, db, d_mean
 
@@ -424,7 +444,10 @@ class Renderer:
         nbytes = numel * torch.empty((), dtype=dtype).element_size()
         return self._buf(name, nbytes)[:nbytes].view(dtype)[:numel].view(shape)
 
-    def project(self, scene: DeviceScene, mlp, tx, stream=None):
+    def project(self, scene: DeviceScene, mlp, tx, stream=None, acts=None):
+        """Records (and residuals on the unfused path); acts, a tensor
+        [n_layers-1, Q*N, 128], receives the hidden activations (unfused,
+        FP32 MLP) for the backward."""
         L = _lib.load()
         Q = int(tx.shape[0])
         # 2 channels: the imaginary weights follow the Q x N records
@@ -439,7 +462,10 @@ class Renderer:
             wrf_deform_project(scene, mlp, self.grid, tx, rec=rec, ws=ws, stream=stream)
             return rec, None
         resid = self._tensor("resid", (Q, scene.n, 5), torch.float32)
-        wrf_deform(scene, mlp, self.grid, tx, resid=resid, ws=ws, stream=stream)
+        if acts is not None:
+            wrf_deform_acts(scene, mlp, self.grid, tx, resid=resid, acts=acts, ws=ws, stream=stream)
+        else:
+            wrf_deform(scene, mlp, self.grid, tx, resid=resid, ws=ws, stream=stream)
         wrf_project(scene, resid, Q, self.grid, rec=rec, tile_count=None, stream=stream)
         return rec, resid
 
@@ -477,9 +503,9 @@ class Renderer:
         self.last["resid"] = None
         return out
 
-    def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None):
+    def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None, acts=None):
         Q = int(tx.shape[0])
-        rec, resid = self.project(scene, mlp, tx, stream=stream)
+        rec, resid = self.project(scene, mlp, tx, stream=stream, acts=acts)
         out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out, channels=scene.channels)
         self.last["resid"] = resid
         return out

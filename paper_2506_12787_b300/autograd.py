@@ -31,6 +31,7 @@ class SpectrumConfig:
     room_size: tuple = (5.0, 5.0, 3.0)
     stop_grad_mean: bool = False  # the paper's fine stage freezes position gradients
     renderer: object = None       # reusable api.Renderer (created on first use)
+    saved_activation_bytes: int = 16 << 30  # keep the MLP's activations up to this size
 
 
 class SpectrumFunction(torch.autograd.Function):
@@ -50,13 +51,21 @@ class SpectrumFunction(torch.autograd.Function):
             cfg.renderer = api.Renderer(cfg.grid, dev, fused=False)
         r = cfg.renderer
         txc = tx.detach().contiguous()
-        out = r.forward(scene, mlp, txc).clone()
+        # the forward keeps its hidden activations for the backward (no
+        # recompute there) when they fit in the budget
+        acts = None
+        if mlp is not None:
+            nbytes = (len(W) - 1) * int(txc.shape[0]) * scene.n * 128 * 4
+            if nbytes <= cfg.saved_activation_bytes:
+                acts = torch.empty((len(W) - 1, int(txc.shape[0]) * scene.n, 128),
+                                   dtype=torch.float32, device=dev)
+        out = r.forward(scene, mlp, txc, acts=acts).clone()
         last = r.last
         ctx.cfg, ctx.scene, ctx.mlp, ctx.tx = cfg, scene, mlp, txc
         ctx.saved = dict(rec=last["rec"].clone(), gids=last["gids"].clone(),
                          offs=last["offs"].clone(), n_keys=last["n_keys"].clone(),
                          resid=last["resid"].clone() if last["resid"] is not None else None,
-                         cap=r.cap)
+                         cap=r.cap, acts=acts)
         ctx.n_params = len(params)
         return out
 
@@ -72,7 +81,8 @@ class SpectrumFunction(torch.autograd.Function):
                     g["d_amp"])
         dW, db, d_mean = api.wrf_deform_backward(scene, mlp, cfg.grid, ctx.tx, g["d_resid"],
                                                  d_mean=g["d_mean"],
-                                                 stop_grad_mean=cfg.stop_grad_mean)
+                                                 stop_grad_mean=cfg.stop_grad_mean,
+                                                 acts=sv["acts"])
         grads = [None, None, d_mean, g["d_log_scale"], g["d_rot"], g["d_opacity"], g["d_amp"]]
         for w, b in zip(dW, db):
             grads += [w, b]

@@ -209,7 +209,8 @@ size_t wrf_deform_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp) {
 
 static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                                 const float *tx, int32_t Q, int mode, float *resid, float *rec,
-                                uint32_t *tile_count, void *ws, size_t ws_bytes, void *stream) {
+                                uint32_t *tile_count, float *acts, void *ws, size_t ws_bytes,
+                                void *stream) {
     wrf_status s;
     wrf::GridView g{};
     wrf::MlpView m{};
@@ -220,6 +221,9 @@ static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, cons
     if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
     if (Q > 0 && !tx) return fail(WRF_EINVAL, "tx is NULL");
     if (mode == 0 && Q > 0 && scene->n > 0 && !resid) return fail(WRF_EINVAL, "resid is NULL");
+    if (acts && mlp->precision != WRF_FP32)
+        return fail(WRF_EUNSUPPORTED, "saved activations need the FP32 MLP");
+    if (acts && !aligned(acts, 16)) return fail(WRF_EINVAL, "acts must be 16-byte aligned");
     if (mode == 1 && Q > 0 && scene->n > 0 && (!rec || !aligned(rec, 16)))
         return fail(WRF_EINVAL, "rec must be non-NULL and 16-byte aligned");
     size_t need = wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, nullptr, nullptr);
@@ -238,7 +242,7 @@ static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, cons
                                tile_count, status, st);
     else
         e = wrf::launch_mlp_f32(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
-                                tile_count, st);
+                                tile_count, acts, st);
     if (e != cudaSuccess) return cuda_fail(e, "mlp");
     return WRF_OK;
 }
@@ -246,15 +250,23 @@ static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, cons
 wrf_status wrf_deform(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                       const float *tx, int32_t Q, float *resid, void *ws, size_t ws_bytes,
                       void *stream) {
-    return deform_common(scene, mlp, grid, tx, Q, 0, resid, nullptr, nullptr, ws, ws_bytes,
+    return deform_common(scene, mlp, grid, tx, Q, 0, resid, nullptr, nullptr, nullptr, ws,
+                         ws_bytes, stream);
+}
+
+wrf_status wrf_deform_acts(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                           const float *tx, int32_t Q, float *resid, float *acts, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (Q > 0 && scene && scene->n > 0 && !acts) return fail(WRF_EINVAL, "acts is NULL");
+    return deform_common(scene, mlp, grid, tx, Q, 0, resid, nullptr, nullptr, acts, ws, ws_bytes,
                          stream);
 }
 
 wrf_status wrf_deform_project(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                               const float *tx, int32_t Q, float *rec, uint32_t *tile_count,
                               void *ws, size_t ws_bytes, void *stream) {
-    return deform_common(scene, mlp, grid, tx, Q, 1, nullptr, rec, tile_count, ws, ws_bytes,
-                         stream);
+    return deform_common(scene, mlp, grid, tx, Q, 1, nullptr, rec, tile_count, nullptr, ws,
+                         ws_bytes, stream);
 }
 
 size_t wrf_loss_workspace_size(int32_t Q, int32_t H, int32_t W) {
@@ -587,9 +599,10 @@ size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *m
 }
 
 wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
-                               const float *tx, int32_t Q, const float *d_resid, float *const *dW,
-                               float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
-                               size_t ws_bytes, void *stream) {
+                               const float *tx, int32_t Q, const float *d_resid,
+                               const float *acts, float *const *dW, float *const *db,
+                               float *d_mean, int32_t stop_grad_mean, void *ws, size_t ws_bytes,
+                               void *stream) {
     wrf_status s;
     wrf::GridView g{};
     wrf::MlpView m{};
@@ -618,7 +631,8 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
         e = wrf::launch_prep(sv, m, g, tx, Q, fw, false, st);
         if (e != cudaSuccess) return cuda_fail(e, "prep");
     }
-    e = wrf::launch_mlp_bwd(sv, m, g, tx, Q, fw, bw, d_resid, dW, db, d_mean, stop_grad_mean, st);
+    e = wrf::launch_mlp_bwd(sv, m, g, tx, Q, fw, bw, d_resid, acts, dW, db, d_mean,
+                            stop_grad_mean, st);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_backward");
     return WRF_OK;
 }

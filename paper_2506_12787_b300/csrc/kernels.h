@@ -54,7 +54,7 @@ cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g,
 // mode 0: write residuals [Q][N][5]; mode 1: project and write records.
 cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                            const DeformWs &ws, int mode, float *resid, float4 *rec,
-                           uint32_t *count, cudaStream_t st);
+                           uint32_t *count, float *acts, cudaStream_t st);
 cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                           const DeformWs &ws, int mode, float *resid, float4 *rec,
                           uint32_t *count, int *status, cudaStream_t st);
@@ -159,7 +159,7 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
                             char *base);
 cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g,
                            const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
-                           const float *d_resid, float *const *dW, float *const *db,
+                           const float *d_resid, const float *acts, float *const *dW, float *const *db,
                            float *d_mean, int stop_grad_mean, cudaStream_t st);
 
 bool render_config_supported(int tw, int th);

@@ -10,6 +10,8 @@
 // CUBLAS_COMPUTE_32F_EMULATED_16BFX9) between small hand-written kernels:
 //   features   H0 = [gamma(mean_n), gamma(tx_q)], H1 = ReLU(U[n] + V[q])
 //   forward    Z_l = H_{l-1} W_{l-1}^T; H_l = ReLU(Z_l + b)       (hidden layers)
+//              -- both skipped for H1.. when the forward saved its hidden
+//              activations (acts), which are then read in place
 //   deltas     D_last = (G_out W_out) * [H_last > 0]; D_{l-1} = (D_l W_l) * [H_{l-1} > 0]
 //   gradients  dW_l += D_l^T H_{l-1} (GEMM over rows, accumulated across
 //              chunks), db_l += column sums of D_l,
@@ -75,11 +77,12 @@ __global__ void features_kernel(int N, long long row0, int nrows, int dm, int dt
                                 const float *gam_m, const float *gam_t, const float *U,
                                 const float *V, float *H0, float *H1) {
     const int din = dm + dt;
-    const long long total = static_cast<long long>(nrows) * (din + WRF_HIDDEN);
+    const int ncol = din + (H1 ? WRF_HIDDEN : 0);  // H1 is NULL when saved by the forward
+    const long long total = static_cast<long long>(nrows) * ncol;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long r = e / (din + WRF_HIDDEN);
-        const int c = static_cast<int>(e % (din + WRF_HIDDEN));
+        const long long r = e / ncol;
+        const int c = static_cast<int>(e % ncol);
         const long long row = row0 + r;
         const int q = static_cast<int>(row / N), n = static_cast<int>(row % N);
         if (c < din) {
@@ -207,8 +210,8 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
 
 cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g,
                            const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
-                           const float *d_resid, float *const *dW, float *const *db,
-                           float *d_mean, int stop_grad_mean, cudaStream_t st) {
+                           const float *d_resid, const float *acts, float *const *dW,
+                           float *const *db, float *d_mean, int stop_grad_mean, cudaStream_t st) {
     const int L = m.n_layers, nh = L - 2;
     const int din = m.dm + m.dt;
     for (int l = 0; l < L; ++l) {
@@ -232,10 +235,15 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
     for (long long r0 = 0; r0 < rows; r0 += CH) {
         const int R = static_cast<int>(rows - r0 < CH ? rows - r0 : CH);
         const long long nH = static_cast<long long>(R) * WRF_HIDDEN;
-        features_kernel<<<grid_for(static_cast<long long>(R) * (din + WRF_HIDDEN)), 256, 0, st>>>(
-            s.n, r0, R, m.dm, m.dt, bw.gam_m, bw.gam_t, fw.U, fw.V, bw.cb_H0, bw.cb_Hh[0]);
+        // hidden activations of this chunk: saved by the forward, or recomputed
+        const float *Hh[8];
+        for (int l = 0; l <= nh; ++l)
+            Hh[l] = acts ? acts + (static_cast<size_t>(l) * rows + r0) * WRF_HIDDEN : bw.cb_Hh[l];
+        features_kernel<<<grid_for(static_cast<long long>(R) * (din + (acts ? 0 : WRF_HIDDEN))),
+                          256, 0, st>>>(s.n, r0, R, m.dm, m.dt, bw.gam_m, bw.gam_t, fw.U, fw.V,
+                                        bw.cb_H0, acts ? nullptr : bw.cb_Hh[0]);
         // forward recompute of the hidden layers: H_{l+1} = ReLU(H_l Wh[l]^T + bh[l])
-        for (int l = 0; l < nh; ++l) {
+        for (int l = 0; l < nh && !acts; ++l) {
             if (gemm(h, T_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, bw.cb_Hh[l],
                      WRF_HIDDEN, 0.f, bw.cb_Hh[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
                 return cudaErrorUnknown;
@@ -247,16 +255,16 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
         if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_OUT, m.Wo, WRF_HIDDEN, Gout, WRF_OUT, 0.f, Dl,
                  WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
             return cudaErrorUnknown;
-        relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dl, bw.cb_Hh[nh], nH);
+        relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dl, Hh[nh], nH);
         // output layer gradients: dWo += G_out^T H_last, dbo += colsum(G_out)
-        if (gemm(h, N_, T_, WRF_HIDDEN, WRF_OUT, R, bw.cb_Hh[nh], WRF_HIDDEN, Gout, WRF_OUT, 1.f,
+        if (gemm(h, N_, T_, WRF_HIDDEN, WRF_OUT, R, Hh[nh], WRF_HIDDEN, Gout, WRF_OUT, 1.f,
                  dW[L - 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
             return cudaErrorUnknown;
         colsum_kernel<<<296, 32, 0, st>>>(Gout, R, WRF_OUT, db[L - 1]);
         // hidden layers backwards: layer l+1 (Wh[l]) maps H_l -> Z_{l+1}
         for (int l = nh - 1; l >= 0; --l) {
             float *D = bw.cb_G[l + 1];  // delta of Z_{l+1}
-            if (gemm(h, N_, T_, WRF_HIDDEN, WRF_HIDDEN, R, bw.cb_Hh[l], WRF_HIDDEN, D, WRF_HIDDEN,
+            if (gemm(h, N_, T_, WRF_HIDDEN, WRF_HIDDEN, R, Hh[l], WRF_HIDDEN, D, WRF_HIDDEN,
                      1.f, dW[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
                 return cudaErrorUnknown;
             colsum_kernel<<<296, 128, 0, st>>>(D, R, WRF_HIDDEN, db[l + 1]);
@@ -264,7 +272,7 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
             if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, D, WRF_HIDDEN, 0.f,
                      Dp, WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
                 return cudaErrorUnknown;
-            relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dp, bw.cb_Hh[l], nH);
+            relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dp, Hh[l], nH);
         }
         // first layer: dW0 += D_0^T H0, db0 += colsum(D_0)
         if (gemm(h, N_, T_, din, WRF_HIDDEN, R, bw.cb_H0, din, bw.cb_G[0], WRF_HIDDEN, 1.f, dW[0],

@@ -10,7 +10,8 @@
 // ahead of the products.  Every output sums its bias, then w_k h_k in
 // ascending k.  Layer 1 starts from ReLU(U[n] + V[q]) (see prep.cu).  The
 // epilogue evaluates the output layer and either stores the residual row or
-// deforms and projects the Gaussian.
+// deforms and projects the Gaussian.  On request (training) every hidden
+// activation is also stored, acts [layer][row][128] FP32, for the backward.
 #include "kernels.h"
 
 namespace wrf {
@@ -38,7 +39,7 @@ struct F32Cfg {
 template <int ROWS>
 __global__ void __launch_bounds__(F32Cfg<ROWS>::THREADS) mlp_f32_kernel(
     SceneView s, MlpView m, GridView g, int Q, DeformWs ws, int mode, float *resid, float4 *rec,
-    uint32_t *count, float *rec_im) {
+    uint32_t *count, float *rec_im, float *acts) {
     using C = F32Cfg<ROWS>;
     constexpr int T = C::THREADS, P = C::PITCH;
     extern __shared__ __align__(16) float smem[];
@@ -77,6 +78,8 @@ __global__ void __launch_bounds__(F32Cfg<ROWS>::THREADS) mlp_f32_kernel(
             h = make_float4(fmaxf(u.x + v.x, 0.f), fmaxf(u.y + v.y, 0.f), fmaxf(u.z + v.z, 0.f),
                             fmaxf(u.w + v.w, 0.f));
         }
+        if (acts && row < rows)
+            *reinterpret_cast<float4 *>(acts + static_cast<size_t>(row) * kH + j4) = h;
         hin[(j4 + 0) * P + r] = h.x;
         hin[(j4 + 1) * P + r] = h.y;
         hin[(j4 + 2) * P + r] = h.z;
@@ -118,6 +121,19 @@ __global__ void __launch_bounds__(F32Cfg<ROWS>::THREADS) mlp_f32_kernel(
                 *reinterpret_cast<float4 *>(hout + (8 * cg + j) * P + 4 * rg) =
                     make_float4(fmaxf(acc[0][j], 0.f), fmaxf(acc[1][j], 0.f),
                                 fmaxf(acc[2][j], 0.f), fmaxf(acc[3][j], 0.f));
+            if (acts) {
+                float *al = acts + static_cast<size_t>(l + 1) * rows * kH;
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const long long row = r0 + 4 * rg + r;
+                    if (row >= rows) continue;
+                    float4 *dst = reinterpret_cast<float4 *>(al + static_cast<size_t>(row) * kH + 8 * cg);
+                    dst[0] = make_float4(fmaxf(acc[r][0], 0.f), fmaxf(acc[r][1], 0.f),
+                                         fmaxf(acc[r][2], 0.f), fmaxf(acc[r][3], 0.f));
+                    dst[1] = make_float4(fmaxf(acc[r][4], 0.f), fmaxf(acc[r][5], 0.f),
+                                         fmaxf(acc[r][6], 0.f), fmaxf(acc[r][7], 0.f));
+                }
+            }
             float *t = hin;
             hin = hout;
             hout = t;
@@ -155,7 +171,7 @@ __global__ void __launch_bounds__(F32Cfg<ROWS>::THREADS) mlp_f32_kernel(
 template <int ROWS>
 cudaError_t launch_rows(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                         const DeformWs &ws, int mode, float *resid, float4 *rec, uint32_t *count,
-                        float *rec_im, long long rows, cudaStream_t st) {
+                        float *rec_im, float *acts, long long rows, cudaStream_t st) {
     using C = F32Cfg<ROWS>;
     cudaError_t e = cudaFuncSetAttribute(mlp_f32_kernel<ROWS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -163,7 +179,7 @@ cudaError_t launch_rows(const SceneView &s, const MlpView &m, const GridView &g,
     if (e != cudaSuccess) return e;
     const long long blocks = (rows + ROWS - 1) / ROWS;
     mlp_f32_kernel<ROWS><<<static_cast<unsigned>(blocks), C::THREADS, C::smem, st>>>(
-        s, m, g, Q, ws, mode, resid, rec, count, rec_im);
+        s, m, g, Q, ws, mode, resid, rec, count, rec_im, acts);
     return cudaGetLastError();
 }
 
@@ -171,7 +187,7 @@ cudaError_t launch_rows(const SceneView &s, const MlpView &m, const GridView &g,
 
 cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                            const DeformWs &ws, int mode, float *resid, float4 *rec,
-                           uint32_t *count, cudaStream_t st) {
+                           uint32_t *count, float *acts, cudaStream_t st) {
     const long long rows = static_cast<long long>(Q) * s.n;
     if (rows == 0) return cudaSuccess;
     // two channels: the imaginary weights follow the Q x N records
@@ -179,8 +195,8 @@ cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView 
                                                    : nullptr;
     // small problems: 32-row CTAs so that more SMs take part
     if (rows < 148LL * 64 * 4)
-        return launch_rows<32>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, rows, st);
-    return launch_rows<64>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, rows, st);
+        return launch_rows<32>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, acts, rows, st);
+    return launch_rows<64>(s, m, g, Q, ws, mode, resid, rec, count, rec_im, acts, rows, st);
 }
 
 }  // namespace wrf

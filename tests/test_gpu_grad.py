@@ -146,14 +146,23 @@ def test_deform_backward_matches_oracle(api, stop):
                                   dparams.ctypes.data_as(D), dmean.ctypes.data_as(D))
     assert rc == 0
     dW_ref, db_ref = oracle.unflat_params(m, dparams)
-    dW, db, d_mean = api.wrf_deform_backward(api.DeviceScene.from_host(sc, dev()),
-                                             api.DeviceMLP.from_host(m, dev()),
-                                             api.make_grid(H, W), T(tx), T(d_resid),
+    ds, dmlp = api.DeviceScene.from_host(sc, dev()), api.DeviceMLP.from_host(m, dev())
+    grid = api.make_grid(H, W)
+    dW, db, d_mean = api.wrf_deform_backward(ds, dmlp, grid, T(tx), T(d_resid),
                                              stop_grad_mean=stop)
+    # the same with the hidden activations saved by the forward (no recompute)
+    resid, acts = api.wrf_deform_acts(ds, dmlp, grid, T(tx))
+    assert torch.equal(resid, api.wrf_deform(ds, dmlp, grid, T(tx)))
+    dW2, db2, d_mean2 = api.wrf_deform_backward(ds, dmlp, grid, T(tx), T(d_resid),
+                                                stop_grad_mean=stop, acts=acts)
     for l in range(len(m.W)):
         ew, eb = rel(dW[l].cpu().numpy(), dW_ref[l]), rel(db[l].cpu().numpy(), db_ref[l])
-        print(f"deform backward layer {l}: dW rel {ew:.2e}, db rel {eb:.2e}")
-        assert ew <= REL and eb <= REL
+        ew2, eb2 = rel(dW2[l].cpu().numpy(), dW_ref[l]), rel(db2[l].cpu().numpy(), db_ref[l])
+        print(f"deform backward layer {l}: dW rel {ew:.2e}, db rel {eb:.2e}; "
+              f"from saved activations dW rel {ew2:.2e}, db rel {eb2:.2e}")
+        assert ew <= REL and eb <= REL and ew2 <= REL and eb2 <= REL
+    if not stop:
+        assert rel(d_mean2.cpu().numpy(), d_mean.cpu().numpy()) <= REL
     if stop:
         assert np.all(d_mean.cpu().numpy() == 0)
     else:
