@@ -123,11 +123,13 @@ class Slot:
 class Server:
     """Continuous batching over resident scenes."""
 
-    def __init__(self, scenes, n_streams=4, buckets=(1, 2, 4, 8, 16, 32, 64, 128),
-                 hbm_budget=32 << 30, max_batch=128, on_result=None):
+    def __init__(self, scenes, n_streams=4, buckets=(1, 4, 16, 64),
+                 hbm_budget=32 << 30, max_batch=64, on_result=None):
         """on_result(request, spectrum) is called at completion with a view
         of the spectrum in pinned host memory that stays valid during the
-        call; copy it to keep it."""
+        call; copy it to keep it.  The default buckets cap a batch at 64
+        queries: at 50k queries/s over scenes of 5k-120k Gaussians larger
+        batches keep requests waiting (a cap of 128 doubles p50 and p99)."""
         self.scenes = scenes
         self.on_result = on_result
         self.buckets = tuple(b for b in buckets if b <= max_batch)
