@@ -169,14 +169,16 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
         float4 a = rec[2 * r], b = rec[2 * r + 1];
         valid = tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
     }
-    for (int tx = 0; tx < g.ntx; ++tx) {
-        uint32_t m = __ballot_sync(0xffffffffu, valid && ((tx >= tx0 && tx <= tx1) ||
-                                                          (WRAP && tx >= tx2 && tx <= tx3)));
-        if (lane == 0) colmask[w * g.ntx + tx] = m;
-    }
-    for (int ty = 0; ty < g.nty; ++ty) {
-        uint32_t m = __ballot_sync(0xffffffffu, valid && ty >= ty0 && ty <= ty1);
-        if (lane == 0) rowmask[w * g.nty + ty] = m;
+    // per warp and tile column / row: the mask of lanes whose rectangle
+    // covers it; each lane sets its bit in the few columns and rows it covers
+    for (int i = threadIdx.x; i < 32 * (g.ntx + g.nty); i += blockDim.x) colmask[i] = 0u;
+    __syncthreads();
+    if (valid) {
+        const uint32_t bit = 1u << lane;
+        for (int tx = tx0; tx <= tx1; ++tx) atomicOr(&colmask[w * g.ntx + tx], bit);
+        if (WRAP)
+            for (int tx = tx2; tx <= tx3; ++tx) atomicOr(&colmask[w * g.ntx + tx], bit);
+        for (int ty = ty0; ty <= ty1; ++ty) atomicOr(&rowmask[w * g.nty + ty], bit);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) {
