@@ -75,7 +75,6 @@ static_assert(tc_smem_bytes() <= 227 * 1024, "shared memory of one CTA");
 __host__ __device__ inline int panels_of(int l) {
     return (l == 0 ? 0 : 3) + ((l == 0 || is_skip(l)) ? 1 : 0);
 }
-__host__ __device__ inline int panel_id(int l, int i) { return l == 0 ? kGammaPanel : i; }
 __host__ __device__ inline int seq_len(int nh) {
     int s = 0;
     for (int l = 0; l < nh; ++l) s += panels_of(l);
