@@ -291,4 +291,26 @@ __device__ __forceinline__ void pe_band(PeArg x, int k, float &s, float &c) {
     sincospif(red, &s, &c);
 }
 
+// gamma(x) of Eq. 15 for a d-vector, written to out[d(2L+1)] in the order
+// [x, sin band 0 (all d), ..., sin band L-1, cos band 0, ..., cos band L-1].
+__device__ inline void pe_encode(const PeArg *x, int d, int L, float *out) {
+    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
+    for (int k = 0; k < L; ++k)
+        for (int i = 0; i < d; ++i) {
+            float s, c;
+            pe_band(x[i], k, s, c);
+            out[d + k * d + i] = s;
+            out[d + L * d + k * d + i] = c;
+        }
+}
+
+// ------------------------------------------------------------ cp.async
+// 16-byte global -> shared copy (L2 only), its commit and a wait for all.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 }  // namespace wrf

@@ -43,17 +43,6 @@ constexpr size_t kCublasWs = size_t(32) << 20;
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-// gamma(x) of Eq. 15 (same feature order and phase reduction as prep.cu).
-__device__ void encode_row(const PeArg *x, int d, int L, float *out) {
-    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
-    for (int k = 0; k < L; ++k)
-        for (int i = 0; i < d; ++i) {
-            float s, c;
-            pe_band(x[i], k, s, c);
-            out[d + k * d + i] = s;
-            out[d + L * d + k * d + i] = c;
-        }
-}
 
 __global__ void gamma_tables_kernel(SceneView s, MlpView m, GridView g, const float *tx, int Q,
                                     float *gam_m, float *gam_t) {
@@ -62,12 +51,12 @@ __global__ void gamma_tables_kernel(SceneView s, MlpView m, GridView g, const fl
         const float2 mu = reinterpret_cast<const float2 *>(s.mean)[i];
         const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
                             pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
-        encode_row(x, 2, m.L_mean, gam_m + static_cast<size_t>(i) * m.dm);
+        pe_encode(x, 2, m.L_mean, gam_m + static_cast<size_t>(i) * m.dm);
     } else if (i < s.n + Q) {
         const int q = i - s.n;
         PeArg x[3];
         for (int c = 0; c < 3; ++c) x[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
-        encode_row(x, 3, m.L_tx, gam_t + static_cast<size_t>(q) * m.dt);
+        pe_encode(x, 3, m.L_tx, gam_t + static_cast<size_t>(q) * m.dt);
     }
 }
 

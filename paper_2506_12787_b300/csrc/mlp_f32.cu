@@ -21,12 +21,6 @@ namespace {
 constexpr int kH = WRF_HIDDEN;  // 128
 constexpr int kKC = 16;         // inputs per staged weight chunk
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <int ROWS>
 struct F32Cfg {

@@ -39,12 +39,6 @@ constexpr int kPitch = kRows + 4;     // floats per input of the transposed acti
 constexpr int kKC = 16;               // weight rows (inputs) per staged chunk (two buffers)
 constexpr int kEnc = 4;               // layers with the encoding in their input: 0, 2, 4, 6
 
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 struct PaperNet {
     int n_hidden, width, dm, dt, L_mean, L_tx;
@@ -66,7 +60,7 @@ __global__ void __launch_bounds__(kPW) paper_mean_kernel(PaperView s, PaperNet m
     if (threadIdx.x < 32 && n0 + threadIdx.x < s.n) {
         const float2 mu = reinterpret_cast<const float2 *>(s.mu)[n0 + threadIdx.x];
         const PeArg a[2] = {unit_centre(mu.x), unit_centre(mu.y)};
-        encode_vec(a, 2, m.L_mean, gam[threadIdx.x]);
+        pe_encode(a, 2, m.L_mean, gam[threadIdx.x]);
     }
     __syncthreads();
     const int j = threadIdx.x;
@@ -95,7 +89,7 @@ __global__ void __launch_bounds__(kPW) paper_tx_kernel(PaperNet m, const float *
     if (threadIdx.x == 0) {
         PeArg a[3];
         for (int c = 0; c < 3; ++c) a[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
-        encode_vec(a, 3, m.L_tx, gam);
+        pe_encode(a, 3, m.L_tx, gam);
     }
     __syncthreads();
     const int j = threadIdx.x;

@@ -1,6 +1,7 @@
 // Pieces of the paper's primitive and head (Sec. 4.1-4.2) shared by the FP32
-// and the tensor-core network kernels: the skip layout, the tanh centre map,
-// the encoding of Eq. 15 and the projection to two-channel records.
+// and the tensor-core network kernels: the skip layout, the tanh centre map
+// and the projection to two-channel records (the encoding of Eq. 15 is
+// pe_encode in common.cuh).
 #pragma once
 #include "common.cuh"
 
@@ -33,17 +34,6 @@ __device__ __forceinline__ void centre(const PaperView &s, int n, const GridView
     y = static_cast<float>(g.H) * pe_value(unit_centre(m.y));
 }
 
-// gamma(x) of Eq. 15 for a d-vector: [x, sin band 0..L-1 (all d), cos ...].
-__device__ inline void encode_vec(const PeArg *x, int d, int L, float *out) {
-    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
-    for (int k = 0; k < L; ++k)
-        for (int i = 0; i < d; ++i) {
-            float sn, cs;
-            pe_band(x[i], k, sn, cs);
-            out[d + k * d + i] = sn;
-            out[d + L * d + k * d + i] = cs;
-        }
-}
 
 // Record of Gaussian n for query q (Eq. 12-13 with the paper's primitive):
 // centre x0 + dmu, inverse of Sigma = L L^T (scaled by log2(e)/2), real

@@ -188,7 +188,7 @@ __global__ void paper_tc_gamma_kernel(PaperView s, int L_mean, int dm, uint16_t 
     const float2 mu = reinterpret_cast<const float2 *>(s.mu)[n];
     const PeArg a[2] = {unit_centre(mu.x), unit_centre(mu.y)};
     float gam[2 * (2 * 15 + 1)];
-    encode_vec(a, 2, L_mean, gam);
+    pe_encode(a, 2, L_mean, gam);
     uint32_t *dst = reinterpret_cast<uint32_t *>(G + static_cast<size_t>(n) * kGammaCols);
     for (int i = 0; i < kGammaCols / 2; ++i) {
         const float x0 = 2 * i < dm ? gam[2 * i] : 0.f;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(kPW) paper_tc_vec_kernel(PaperNetTc m, const f
     if (enc && j == 0) {
         PeArg a[3];
         for (int c = 0; c < 3; ++c) a[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
-        encode_vec(a, 3, m.L_tx, gam);
+        pe_encode(a, 3, m.L_tx, gam);
     }
     __syncthreads();
     float acc = 0.f;

@@ -21,18 +21,6 @@ namespace {
 constexpr int kMaxPe = 3 * (2 * 15 + 1);  // d(2L+1) for d <= 3, L <= 15
 constexpr size_t kW1ImageBytes = WRF_HIDDEN * 128;  // 128 rows x 64 BF16 columns
 
-// gamma(x) of Eq. 15 for a d-vector, written to out[d(2L+1)] in the order
-// [x, sin band 0 (all d), ..., sin band L-1, cos band 0, ..., cos band L-1].
-__device__ void encode(const PeArg *x, int d, int L, float *out) {
-    for (int i = 0; i < d; ++i) out[i] = pe_value(x[i]);
-    for (int k = 0; k < L; ++k)
-        for (int i = 0; i < d; ++i) {
-            float s, c;
-            pe_band(x[i], k, s, c);
-            out[d + k * d + i] = s;
-            out[d + L * d + k * d + i] = c;
-        }
-}
 
 // Per-Gaussian part of layer 1 for 32 Gaussians per block.  FP32 path:
 // U[n][j] = W0[j, :dm] . gamma(mean_n), thread j owns column j.  BF16 path:
@@ -49,7 +37,7 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
             float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
             const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
                                 pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
-            encode(x, 2, m.L_mean, gam[threadIdx.x]);
+            pe_encode(x, 2, m.L_mean, gam[threadIdx.x]);
         }
     }
     __syncthreads();
