@@ -162,16 +162,25 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
     const int c = blockIdx.x, q = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int id = c * kBinChunk + threadIdx.x;
-    int tx0 = 0, tx1 = -1, tx2 = 1, tx3 = 0, ty0 = 0, ty1 = -1;
-    bool valid = false;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (id < n) {
-        size_t r = static_cast<size_t>(q) * n + id;
-        float4 a = rec[2 * r], b = rec[2 * r + 1];
-        valid = tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
+        const size_t r = static_cast<size_t>(q) * n + id;
+        a = rec[2 * r];
+        b = rec[2 * r + 1];
     }
+    // this chunk's start in every tile list of the query, loaded while the
+    // records are in flight
+    const size_t ebase = static_cast<size_t>(q) * g.T * C + c;
+    const uint32_t b0 = threadIdx.x < g.T ? excl[ebase + static_cast<size_t>(threadIdx.x) * C] : 0u;
+    int tx0 = 0, tx1 = -1, tx2 = 1, tx3 = 0, ty0 = 0, ty1 = -1;
+    const bool valid =
+        id < n && tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
     // per warp and tile column / row: the mask of lanes whose rectangle
     // covers it; each lane sets its bit in the few columns and rows it covers
     for (int i = threadIdx.x; i < 32 * (g.ntx + g.nty); i += blockDim.x) colmask[i] = 0u;
+    if (threadIdx.x < g.T) base[threadIdx.x] = b0;
+    for (int t = threadIdx.x + blockDim.x; t < g.T; t += blockDim.x)
+        base[t] = excl[ebase + static_cast<size_t>(t) * C];
     __syncthreads();
     if (valid) {
         const uint32_t bit = 1u << lane;
@@ -188,7 +197,6 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
             woff[ww * g.T + t] = static_cast<uint16_t>(run);
             run += __popc(colmask[ww * g.ntx + tx] & rowmask[ww * g.nty + ty]);
         }
-        base[t] = excl[(static_cast<size_t>(q) * g.T + t) * C + c];
     }
     __syncthreads();
     if (!valid || *n_keys > cap) return;
@@ -196,8 +204,8 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
     for (int ty = ty0; ty <= ty1; ++ty) {
         uint32_t rm = rowmask[w * g.nty + ty];
         for (int part = 0; part < (WRAP ? 2 : 1); ++part) {
-            const int a = part == 0 ? tx0 : tx2, b = part == 0 ? tx1 : tx3;
-            for (int tx = a; tx <= b; ++tx) {
+            const int lo = part == 0 ? tx0 : tx2, hi = part == 0 ? tx1 : tx3;
+            for (int tx = lo; tx <= hi; ++tx) {
                 int t = ty * g.ntx + tx;
                 uint32_t mk = colmask[w * g.ntx + tx] & rm;
                 const uint32_t pos = base[t] + woff[w * g.T + t] + __popc(mk & below);

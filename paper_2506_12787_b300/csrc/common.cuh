@@ -132,6 +132,10 @@ __device__ __forceinline__ bool tile_rect(float mx, float my, float rx, float ry
                   : tile_rect_t<false>(mx, my, rx, ry, g, tx0, tx1, tx2, tx3, ty0, ty1);
 }
 
+// a / t for a >= 0 and a tile size t that is a power of two (every
+// supported tile shape is: 8, 16 or 32 wide, 8 or 16 high).
+__device__ __forceinline__ int tile_of(int a, int t) { return a >> (__ffs(t) - 1); }
+
 template <bool WRAP>
 __device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float ry,
                                             const GridView &g, int &tx0, int &tx1, int &tx2,
@@ -143,16 +147,16 @@ __device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float 
     if (!(yhi >= 0.f) || !(ylo <= hm)) return false;
     const float ay = ceilf(fmaxf(ylo, 0.f)), by = floorf(fminf(yhi, hm));
     if (ay > by) return false;
-    ty0 = static_cast<int>(ay) / g.th;
-    ty1 = static_cast<int>(by) / g.th;
+    ty0 = tile_of(static_cast<int>(ay), g.th);
+    ty1 = tile_of(static_cast<int>(by), g.th);
     const float xlo = __fsub_rn(mx, rx), xhi = __fadd_rn(mx, rx);
     if (!WRAP) {
         const float wm = static_cast<float>(g.W - 1);
         if (!(xhi >= 0.f) || !(xlo <= wm)) return false;
         const float ax = ceilf(fmaxf(xlo, 0.f)), bx = floorf(fminf(xhi, wm));
         if (ax > bx) return false;
-        tx0 = static_cast<int>(ax) / g.tw;
-        tx1 = static_cast<int>(bx) / g.tw;
+        tx0 = tile_of(static_cast<int>(ax), g.tw);
+        tx1 = tile_of(static_cast<int>(bx), g.tw);
         return true;
     }
     const float lo = ceilf(xlo), hi = floorf(xhi);
@@ -169,11 +173,11 @@ __device__ __forceinline__ bool tile_rect_t(float mx, float my, float rx, float 
     if (a < 0) a += g.W;
     if (b < 0) b += g.W;
     if (a <= b) {
-        tx0 = a / g.tw;
-        tx1 = b / g.tw;
+        tx0 = tile_of(a, g.tw);
+        tx1 = tile_of(b, g.tw);
         return true;
     }
-    const int ta = a / g.tw, tb = b / g.tw;
+    const int ta = tile_of(a, g.tw), tb = tile_of(b, g.tw);
     tx0 = 0;
     if (ta <= tb) {  // both pieces of the wrapped footprint meet in one tile
         tx1 = g.ntx - 1;
