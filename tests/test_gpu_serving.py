@@ -96,7 +96,8 @@ def test_continuous_batching_beats_plain(env):
     plain.prepare()
     pl, _ = serving.run_stream(plain, arr, lambda i: txs[i], window_s=win, drain_s=1.0,
                                warmup_s=0.1)
-    print(f"continuous: {cb}\nplain: {pl}")
+    print(f"continuous: {cb}\nplain: {pl}\nrequests held behind a batch in flight: {srv.holds}")
     assert cb["unserved"] == 0
+    assert srv.holds > 0  # the hold-while-busy policy was exercised
     assert cb["spectra_per_s"] > pl["spectra_per_s"]
     assert pl["p99_ms"] is None or cb["p99_ms"] < pl["p99_ms"]
