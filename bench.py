@@ -332,9 +332,9 @@ def error_vs_oracle(gpu, ref, slack, tol):
 
 def cpu_baseline(args, sc, m, tx, shape, gpu_out=None, tol=None):
     """The FP64 oracle on the host cores over a bounded sample of the
-    workload's queries (sized from a timed warm batch of up to 8 queries to
-    ~args.cpu_seconds: one query alone runs several times slower per query,
-    its rows being too few to keep every core busy);
+    workload's queries (sized from a timed warm batch of up to 32 queries to
+    ~args.cpu_seconds: small batches run slower per query, their rows being
+    too few to keep every core busy);
     with gpu_out (the step's spectra on the device) also the GPU's error
     against the oracle on that sample."""
     import oracle
@@ -342,7 +342,7 @@ def cpu_baseline(args, sc, m, tx, shape, gpu_out=None, tol=None):
     N, H, W, Q = shape
     fwd = oracle.forward_complex if args.channels == 2 else oracle.forward
     fwd(sc, m, tx[:1], H, W, Q_CUT, wrap=args.wrap)  # builds and pages in the oracle
-    s0 = min(Q, 8)
+    s0 = min(Q, 32)
     t0 = time.perf_counter()
     fwd(sc, m, tx[:s0], H, W, Q_CUT, wrap=args.wrap)  # a warm batch sizes the sample
     t1 = (time.perf_counter() - t0) / s0
@@ -384,10 +384,10 @@ def run_serving(args, dev):
     txs = synth.make_tx(len(arr), seed=9)
     out = {"config": f"Poisson {args.rate:.0f} q/s over 8 resident scenes {list(sizes)}, "
                      f"{dur:.0f} s measured after {warm:.0f} s warm-up, BF16 MLP, 360x90"}
-    # batches of at most 64 queries: at 50k q/s a cap of 128 raises p50 and p99
-    # (requests wait on larger batches), 32 or finer buckets lengthen the tail;
-    # a scene with a batch in flight holds its new requests for the next one
-    srv = serving.Server(scenes, n_streams=4, buckets=(1, 4, 16, 64), max_batch=64)
+    # a scene with a batch in flight holds its new requests for the next one;
+    # batches of at most 32 queries on 8 streams (caps of 48-96 keep requests
+    # waiting longer, a cap of 16 saturates in bursts)
+    srv = serving.Server(scenes, n_streams=8, buckets=(1, 4, 8, 16, 32), max_batch=32)
     srv.prepare()
     cb, _ = serving.run_stream(srv, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
                                warmup_s=warm)

@@ -9,9 +9,10 @@ requests that arrive while other batches are on the GPU are admitted as
 slots free up, so work of several scenes and batches overlaps on the device.
 While one of a scene's batches is on the GPU, the scene's new requests are
 held back (unless they already fill the largest bucket) and go out together
-when it completes: fewer, larger batches contend less for the device, which
-at 50k queries/s over the 8-scene mix halves p50 and p99 against launching
-every waiting request at once.
+when it completes: fewer, larger batches contend less for the device.  At
+50k queries/s over the 8-scene mix this took p50 / p99 from 28 / 39 ms
+(every waiting request launched at once, batches of up to 64) to 13 / 23 ms,
+and with the cap lowered to 32 to about 5 / 11 ms.
 Slots are created on demand and admitted by memory: the device bytes of all
 slots together stay within an HBM budget.  A request completes when its
 batch's spectra are back in pinned host memory, where they are handed to the
@@ -129,13 +130,14 @@ class Slot:
 class Server:
     """Continuous batching over resident scenes."""
 
-    def __init__(self, scenes, n_streams=4, buckets=(1, 4, 16, 64),
-                 hbm_budget=32 << 30, max_batch=64, on_result=None, hold_while_busy=True):
+    def __init__(self, scenes, n_streams=8, buckets=(1, 4, 8, 16, 32),
+                 hbm_budget=32 << 30, max_batch=32, on_result=None, hold_while_busy=True):
         """on_result(request, spectrum) is called at completion with a view
         of the spectrum in pinned host memory that stays valid during the
-        call; copy it to keep it.  The default buckets cap a batch at 64
-        queries: at 50k queries/s over scenes of 5k-120k Gaussians larger
-        batches keep requests waiting (a cap of 128 raises p50 and p99).
+        call; copy it to keep it.  The default buckets cap a batch at 32
+        queries: with hold_while_busy, at 50k queries/s over scenes of
+        5k-120k Gaussians, caps of 48, 64 and 96 kept requests waiting longer
+        (p50 10, 13, 15 ms) and a cap of 16 ran into saturation bursts.
         hold_while_busy: a scene with a batch in flight launches another
         only once its queue fills the largest bucket."""
         self.scenes = scenes
