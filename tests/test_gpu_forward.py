@@ -243,3 +243,22 @@ def test_query_alone_equals_query_in_batch(api):
     for q in (0, 4, 8):
         alone = api.Renderer(grid, dev()).forward(ds, m, tx[q:q + 1])
         assert torch.equal(alone[0], batch[q])
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_zero_queries(api, precision):
+    """Q = 0 through the whole path (deform + project, bin, render): empty
+    spectra, no device error; the next non-empty call is unaffected."""
+    H, W = 90, 360
+    prec = api.WRF_BF16 if precision == "bf16" else api.WRF_FP32
+    ds = api.DeviceScene.from_host(synth.make_scene(300, H, W, seed=4), dev())
+    m = api.DeviceMLP.from_host(synth.make_mlp(seed=4), dev(), precision=prec)
+    r = api.Renderer(api.make_grid(H, W, 16, 16, 9.0), dev())
+    out = r.forward(ds, m, T(np.zeros((0, 3), np.float32)))
+    torch.cuda.synchronize()
+    assert tuple(out.shape) == (0, H, W)
+    assert api.wrf_status_read() == 0
+    tx = T(synth.make_tx(2, seed=4))
+    again = r.forward(ds, m, tx)
+    ref = api.Renderer(api.make_grid(H, W, 16, 16, 9.0), dev()).forward(ds, m, tx)
+    assert torch.equal(again, ref)
