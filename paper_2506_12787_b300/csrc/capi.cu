@@ -478,7 +478,13 @@ wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
     size_t need = wrf::bin_ws_layout(n, Q, g, nullptr, nullptr);
     if (ws_bytes < need || !ws || !aligned(ws, 256))
         return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
-    if (Q == 0) return WRF_OK;
+    if (Q == 0) {  // no keys: the count and the one CSR entry are still written
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        cudaError_t e = cudaMemsetAsync(n_keys_out, 0, sizeof(int64_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tile_offsets, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "bin (Q = 0)");
+        return WRF_OK;
+    }
     wrf::BinWs w{};
     wrf::bin_ws_layout(n, Q, g, &w, static_cast<char *>(ws));
     cudaError_t e = wrf::launch_bin(reinterpret_cast<const float4 *>(rec), n, Q, g, gids,

@@ -254,6 +254,10 @@ def test_zero_queries(api, precision):
     ds = api.DeviceScene.from_host(synth.make_scene(300, H, W, seed=4), dev())
     m = api.DeviceMLP.from_host(synth.make_mlp(seed=4), dev(), precision=prec)
     r = api.Renderer(api.make_grid(H, W, 16, 16, 9.0), dev())
+    # the key count and offsets must be written even with nothing to bin:
+    # poison the renderer's buffers so a missing write shows
+    r._buf("nk", 256).fill_(0xFF)
+    r._buf("offs", 256).fill_(0xFF)
     out = r.forward(ds, m, T(np.zeros((0, 3), np.float32)))
     torch.cuda.synchronize()
     assert tuple(out.shape) == (0, H, W)
