@@ -20,8 +20,9 @@ import ctypes as C
 import torch
 
 from . import _lib
-from .api import (DeviceMLP, DeviceScene, _p, _stream, tiles_of, wrf_bin, wrf_deform_project,
-                  wrf_render, wrf_render_complex, wrf_status_read, alloc_records)
+from .api import (DeviceMLP, DevicePaperScene, DeviceScene, _p, _stream, tiles_of, wrf_bin,
+                  wrf_deform_project, wrf_paper_deform_project, wrf_render, wrf_render_complex,
+                  wrf_status_read, alloc_records)
 
 
 class BatchedForward:
@@ -111,6 +112,45 @@ class BatchedForward:
         with torch.cuda.graph(g, stream=s):
             self.run(tx, s, out)
         return g
+
+
+class PaperForward(BatchedForward):
+    """BatchedForward for the paper's own head (Sec. 4.1-4.2, 6.1): the
+    tanh-mapped, Cholesky-parameterised scene (DevicePaperScene) through the
+    skip network (DevicePaperMLP, or None for no deformation) into
+    two-channel records, then the same binning and the two-channel render;
+    out [Q,2,H,W] = magnitude, phase.  Same buffers, key-capacity protocol
+    and graph capture as BatchedForward, so HostPipeline drives it too."""
+
+    def __init__(self, scene: DevicePaperScene, mlp, grid, Q: int, device="cuda",
+                 key_capacity: int = 0, margin: float = 1.25):
+        self.scene, self.mlp, self.grid, self.Q = scene, mlp, grid, int(Q)
+        self.device = torch.device(device)
+        self.margin = margin
+        L = _lib.load()
+        n = scene.n
+        self.T = tiles_of(grid)
+        self.channels = 2
+        self.rec = alloc_records(self.Q, n, 2, self.device)
+        self.dws = None if mlp is None else torch.empty(
+            max(256, L.wrf_paper_workspace_size(n, self.Q)), dtype=torch.uint8, device=self.device)
+        self.bws = torch.empty(max(256, L.wrf_bin_workspace_size(n, self.Q, C.byref(grid))),
+                               dtype=torch.uint8, device=self.device)
+        self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.offs = torch.empty(self.Q * self.T + 1, dtype=torch.int32, device=self.device)
+        self.out = torch.empty((self.Q, 2, grid.H, grid.W), dtype=torch.float32,
+                               device=self.device)
+        self.cap = 0
+        self.gids = None
+        self._alloc_keys(int(key_capacity))
+
+    # kernels one run() launches: the network's four (weight images or
+    # panels, encodings, per-query terms, network), binning's five, render
+    launches_per_run = 10
+
+    def deform_project(self, tx, stream=None):
+        wrf_paper_deform_project(self.scene, self.mlp, self.grid, tx, rec=self.rec, ws=self.dws,
+                                 stream=stream)
 
 
 class HostPipeline:

@@ -356,3 +356,30 @@ def test_paper_workload_full_size_sampled(api, precision):
     ok_im, e_im, _ = spectrum_error(g[:, 0] * np.sin(g[:, 1]), im, slack, tol)
     print(f"paper workload {precision}, queries {picks}: re {e_re:.2e}, im {e_im:.2e} (x peak)")
     assert ok_re and ok_im
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_paper_host_pipeline_matches_forward_paper(api, precision):
+    """HostPipeline over PaperForward (TX from pinned host memory, magnitude /
+    phase back to pinned host memory, copies overlapped) returns exactly the
+    output of Renderer.forward_paper for alternating TX batches."""
+    from paper_2506_12787_b300.batched import HostPipeline, PaperForward
+    H, W, N, Q = 90, 360, 2000, 8
+    prec = _lib.WRF_BF16 if precision == "bf16" else _lib.WRF_FP32
+    sc = synth.make_paper_scene(N, H, W, seed=21)
+    ds = api.DevicePaperScene.from_host(sc, dev())
+    dm = api.DevicePaperMLP.from_host(paper_mlp(21), dev(), precision=prec)
+    grid = api.make_grid(H, W, 32, 8, 9.0)
+    txs = [synth.make_tx(Q, seed=50 + i) for i in range(2)]
+    ref = [api.Renderer(grid, dev()).forward_paper(ds, dm, T(t)).cpu().numpy() for t in txs]
+    fw = PaperForward(ds, dm, grid, Q, dev())
+    for t in txs:  # key capacity for both batches
+        fw.reserve(T(t))
+    pipe = HostPipeline(fw)
+    hosts = [torch.as_tensor(t).pin_memory() for t in txs]
+    for i in range(6):
+        out = pipe.step(hosts[i % 2])
+        if i >= 4:  # steps 4 and 5 land in different ring slots
+            pipe.sync()
+            assert np.array_equal(out.numpy(), ref[i % 2])
+    fw.check()
