@@ -87,6 +87,8 @@ wrf_status check_grid(const wrf_grid *g, wrf::GridView *v) {
     if (!g) return fail(WRF_EINVAL, "grid is NULL");
     if (g->H < 1 || g->W < 1 || g->H > 65536 || g->W > 65536)
         return fail(WRF_EINVAL, "grid H/W out of range");
+    // every supported shape is a power of two on both axes: the device code
+    // takes tile indices by shift (tile_of)
     if (!wrf::render_config_supported(g->tile_w, g->tile_h))
         return fail(WRF_EUNSUPPORTED, "tile %dx%d not supported", g->tile_w, g->tile_h);
     if (!(g->q_cut > 0.f)) return fail(WRF_EINVAL, "q_cut must be > 0 (or +inf)");
