@@ -54,7 +54,7 @@ MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output
 # ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, tile_w, tile_h)
 NCU_TRAFFIC = {
     ("render_kernel", 20000, 256, 90, 360, 32, 8): 263.144192e6 + 28.133632e6,
-    ("mlp_tc_kernel", 20000, 256, 90, 360, 32, 8): 2.128896e6 + 103.981312e6,
+    ("mlp_tc_kernel", 20000, 256, 90, 360, 32, 8): 2.130432e6 + 104.015360e6,
 }
 RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
 BIN_BYTES_PER_REC = 32   # each record read once
