@@ -36,11 +36,23 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
     const int c = blockIdx.x, q = blockIdx.y;
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
-    for (int i = 0; i < kBinChunk / 256; ++i) {
-        int id = c * kBinChunk + i * 256 + threadIdx.x;
+    // all of this thread's records are requested before any is used
+    constexpr int kPer = kBinChunk / 256;
+    float4 ra[kPer], rb[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int id = c * kBinChunk + i * 256 + threadIdx.x;
+        if (id < n) {
+            const size_t r = static_cast<size_t>(q) * n + id;
+            ra[i] = rec[2 * r];
+            rb[i] = rec[2 * r + 1];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int id = c * kBinChunk + i * 256 + threadIdx.x;
         if (id >= n) break;
-        size_t r = static_cast<size_t>(q) * n + id;
-        float4 a = rec[2 * r], b = rec[2 * r + 1];
+        const float4 a = ra[i], b = rb[i];
         int tx0, tx1, tx2, tx3, ty0, ty1;
         if (!tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1)) continue;
         // with wrap a tile is rendered with the Gaussian's image nearest to
