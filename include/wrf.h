@@ -181,7 +181,9 @@ wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
  * library holds on every device that loads it until the process exits.
  *   - Calls whose scratch need (wrf_bin_workspace_size) exceeds 4 MiB are
  *     rejected with WRF_EINVAL before any work is queued; at 16 x 16 tiles
- *     on a 360 x 90 grid that admits Q * ceil(N / 1024) up to about 7,500.
+ *     on a 360 x 90 grid (138 tiles, so binning chunks of 512 Gaussians;
+ *     grids of more than 256 tiles use chunks of 1024) that admits
+ *     Q * ceil(N / 512) up to about 7,500.
  *   - The function allocates nothing (no cudaMalloc, cudaFree or allocating
  *     library call).  Its first call on a device looks the array's device
  *     address up once (cudaGetSymbolAddress); make that first call outside

@@ -8,7 +8,7 @@
 // them in (q, t, n) order without ever sorting on n.
 //
 // Three steps, each bound by memory traffic:
-//   1. count   - per (query, chunk of 1024 Gaussians): smem histogram of the
+//   1. count   - per (query, chunk of 512 or 1024 Gaussians): smem histogram of the
 //                tiles its rectangles cover -> counts[q][t][chunk]
 //   2. scan    - exclusive prefix sum over the flattened [q][t][chunk] array
 //                (reduce / scan-of-block-sums / down-sweep); the entry of
@@ -29,7 +29,7 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;  // 4096
 
-template <bool WRAP>
+template <bool WRAP, int CHUNK>
 __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n, GridView g,
                                                         int C, uint32_t *counts, int *status) {
     extern __shared__ uint32_t hist[];
@@ -37,11 +37,11 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
     // all of this thread's records are requested before any is used
-    constexpr int kPer = kBinChunk / 256;
+    constexpr int kPer = CHUNK / 256;
     float4 ra[kPer], rb[kPer];
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-        const int id = c * kBinChunk + i * 256 + threadIdx.x;
+        const int id = c * CHUNK + i * 256 + threadIdx.x;
         if (id < n) {
             const size_t r = static_cast<size_t>(q) * n + id;
             ra[i] = rec[2 * r];
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
     }
 #pragma unroll
     for (int i = 0; i < kPer; ++i) {
-        const int id = c * kBinChunk + i * 256 + threadIdx.x;
+        const int id = c * CHUNK + i * 256 + threadIdx.x;
         if (id >= n) break;
         const float4 a = ra[i], b = rb[i];
         int tx0, tx1, tx2, tx3, ty0, ty1;
@@ -161,19 +161,21 @@ __global__ void __launch_bounds__(kScanThreads) scan_down_kernel(
     if (blockIdx.x == 0 && threadIdx.x == 0) offsets[QT] = static_cast<uint32_t>(*n_keys);
 }
 
-template <bool WRAP>
-__global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec, int n, GridView g,
+// CHUNK Gaussians per (query, chunk) CTA, one per thread
+template <bool WRAP, int CHUNK>
+__global__ void __launch_bounds__(CHUNK, 2048 / CHUNK) bin_scatter_kernel(const float4 *rec, int n, GridView g,
                                                            int C, const uint32_t *excl,
                                                            uint32_t *gids, long long cap,
                                                            const long long *n_keys) {
     extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *colmask = sm;                               // [32][ntx]
-    uint32_t *rowmask = colmask + 32 * g.ntx;             // [32][nty]
-    uint32_t *base = rowmask + 32 * g.nty;                // [T]
-    uint16_t *woff = reinterpret_cast<uint16_t *>(base + g.T);  // [32][T]
+    constexpr int kScatterWarps = CHUNK / 32;
+    uint32_t *colmask = sm;                                        // [warps][ntx]
+    uint32_t *rowmask = colmask + kScatterWarps * g.ntx;           // [warps][nty]
+    uint32_t *base = rowmask + kScatterWarps * g.nty;              // [T]
+    uint16_t *woff = reinterpret_cast<uint16_t *>(base + g.T);     // [warps][T]
     const int c = blockIdx.x, q = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int id = c * kBinChunk + threadIdx.x;
+    const int id = c * CHUNK + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (id < n) {
         const size_t r = static_cast<size_t>(q) * n + id;
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
         id < n && tile_rect_t<WRAP>(a.x, a.y, b.z, b.w, g, tx0, tx1, tx2, tx3, ty0, ty1);
     // per warp and tile column / row: the mask of lanes whose rectangle
     // covers it; each lane sets its bit in the few columns and rows it covers
-    for (int i = threadIdx.x; i < 32 * (g.ntx + g.nty); i += blockDim.x) colmask[i] = 0u;
+    for (int i = threadIdx.x; i < kScatterWarps * (g.ntx + g.nty); i += blockDim.x) colmask[i] = 0u;
     if (threadIdx.x < g.T) base[threadIdx.x] = b0;
     for (int t = threadIdx.x + blockDim.x; t < g.T; t += blockDim.x)
         base[t] = excl[ebase + static_cast<size_t>(t) * C];
@@ -205,7 +207,7 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) {
         int tx = t % g.ntx, ty = t / g.ntx;
         uint32_t run = 0;
-        for (int ww = 0; ww < 32; ++ww) {
+        for (int ww = 0; ww < kScatterWarps; ++ww) {
             woff[ww * g.T + t] = static_cast<uint16_t>(run);
             run += __popc(colmask[ww * g.ntx + tx] & rowmask[ww * g.nty + ty]);
         }
@@ -229,16 +231,50 @@ __global__ void __launch_bounds__(1024, 2) bin_scatter_kernel(const float4 *rec,
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
+// Gaussians per binning chunk: 512 for grids of up to 256 tiles (a shorter
+// per-tile walk over the chunk's warps, four CTAs per SM), 1024 above (the
+// per-(query, tile, chunk) counts, which the scan reads and writes, grow with
+// the tile count over the chunk size).
+inline int bin_chunk(const GridView &g) { return g.T <= 256 ? 512 : 1024; }
+
 size_t scatter_smem(const GridView &g) {
-    return static_cast<size_t>(32) * (g.ntx + g.nty) * 4 + static_cast<size_t>(g.T) * 4 +
-           static_cast<size_t>(32) * g.T * 2;
+    const size_t warps = static_cast<size_t>(bin_chunk(g) / 32);
+    return warps * (g.ntx + g.nty) * 4 + static_cast<size_t>(g.T) * 4 + warps * g.T * 2;
+}
+
+template <int CHUNK>
+cudaError_t launch_count_scatter(int phase, const float4 *rec, int n, int Q, const GridView &g,
+                                 uint32_t *gids, long long cap, const long long *n_keys,
+                                 const BinWs &ws, int *status, cudaStream_t st) {
+    dim3 grid(ws.C, Q);
+    if (phase == 0) {
+        auto kern = g.wrap ? bin_count_kernel<true, CHUNK> : bin_count_kernel<false, CHUNK>;
+        kern<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts, status);
+        return cudaGetLastError();
+    }
+    const size_t smem = scatter_smem(g);
+    auto kern = g.wrap ? bin_scatter_kernel<true, CHUNK> : bin_scatter_kernel<false, CHUNK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    kern<<<grid, CHUNK, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap, n_keys);
+    return cudaGetLastError();
+}
+
+cudaError_t count_scatter(int phase, const float4 *rec, int n, int Q, const GridView &g,
+                          uint32_t *gids, long long cap, const long long *n_keys, const BinWs &ws,
+                          int *status, cudaStream_t st) {
+    return bin_chunk(g) == 512
+               ? launch_count_scatter<512>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status, st)
+               : launch_count_scatter<1024>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
 }
 
 }  // namespace
 
 size_t bin_ws_layout(int n, int Q, const GridView &g, BinWs *ws, char *base) {
     BinWs w{};
-    w.C = n > 0 ? (n + kBinChunk - 1) / kBinChunk : 1;
+    const int chunk = bin_chunk(g);
+    w.C = n > 0 ? (n + chunk - 1) / chunk : 1;
     w.M = static_cast<long long>(Q) * g.T * w.C;
     w.nblocks = static_cast<int>((w.M + kScanBlock - 1) / kScanBlock);
     if (w.nblocks < 1) w.nblocks = 1;
@@ -258,13 +294,8 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
                        int *status, cudaStream_t st) {
     if (Q == 0) return cudaSuccess;
     if (n > 0) {
-        dim3 grid(ws.C, Q);
-        if (g.wrap)
-            bin_count_kernel<true><<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts,
-                                                               status);
-        else
-            bin_count_kernel<false><<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts,
-                                                                status);
+        cudaError_t e = count_scatter(0, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
+        if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = cudaMemsetAsync(ws.chunk_counts, 0, static_cast<size_t>(ws.M) * 4, st);
         if (e != cudaSuccess) return e;
@@ -275,13 +306,8 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
                                                          ws.C, offsets,
                                                          static_cast<long long>(Q) * g.T, n_keys);
     if (n > 0) {
-        size_t smem = scatter_smem(g);
-        auto kern = g.wrap ? bin_scatter_kernel<true> : bin_scatter_kernel<false>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(smem));
+        cudaError_t e = count_scatter(1, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
         if (e != cudaSuccess) return e;
-        dim3 grid(ws.C, Q);
-        kern<<<grid, 1024, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap, n_keys);
     }
     return cudaGetLastError();
 }

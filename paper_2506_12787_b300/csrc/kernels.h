@@ -116,11 +116,10 @@ cudaError_t launch_rssi(const SceneView &s, const MlpView &m, const GridView &g,
 struct BinWs {
     uint32_t *chunk_counts;  // [Q][T][C]
     unsigned long long *block_sums;
-    int C;                   // chunks of kBinChunk Gaussians per query
+    int C;                   // chunks of Gaussians per query (512 or 1024 each)
     long long M;             // Q*T*C
     int nblocks;
 };
-constexpr int kBinChunk = 1024;
 size_t bin_ws_layout(int n, int Q, const GridView &g, BinWs *ws, char *base);
 cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint32_t *gids,
                        long long cap, long long *n_keys, uint32_t *offsets, const BinWs &ws,
