@@ -544,11 +544,11 @@ def run_train(args):
                        "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
             # this library's kernels only (cuBLAS GEMM kernels not counted):
-            # forward: PE x2, weights, MLP, project, bin x5, render (11); loss: 3;
-            # backward: render, project, gamma tables, then per row chunk of up
-            # to 1M rows features, 3 bias-ReLU, 4 ReLU masks, 5 column sums
-            # (13); Adam: 1
-            "gpu_launches": K * (11 + 3 + 3 + 13 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
+            # forward: prep, MLP, project, bin x5, render (9); loss: 3;
+            # backward: render, project, prep, gamma tables (4), then per row
+            # chunk of up to 1M rows features, 4 ReLU masks, 5 column sums
+            # (10, the hidden activations saved by the forward); Adam: 1
+            "gpu_launches": K * (9 + 3 + 4 + 10 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
@@ -696,7 +696,7 @@ def run_rssi(args):
                     "d2h_bytes_per_step": 4 * Q,
                     "api": "api.wrf_rssi graph with pinned host TX in and pinned host RSSI out"},
             "roofline": roof,
-            "gpu_launches": K * 4}
+            "gpu_launches": K * 2}  # prep, fused RSSI kernel
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()

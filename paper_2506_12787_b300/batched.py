@@ -50,9 +50,10 @@ class BatchedForward:
         self.gids = None
         self._alloc_keys(int(key_capacity))
 
-    # kernels one run() launches: PE(mean), PE(tx), weight images, MLP;
-    # bin count, scan reduce, scan top, scan down-sweep, scatter; render
-    launches_per_run = 10
+    # kernels one run() launches: prep (encodings, per-query terms and
+    # weight images in one launch), MLP; bin count, scan reduce, scan top,
+    # scan down-sweep, scatter; render
+    launches_per_run = 8
 
     def _alloc_keys(self, cap: int):
         cap = max(int(cap), 1024)

@@ -26,10 +26,10 @@ constexpr size_t kW1ImageBytes = WRF_HIDDEN * 128;  // 128 rows x 64 BF16 column
 // U[n][j] = W0[j, :dm] . gamma(mean_n), thread j owns column j.  BF16 path:
 // the row gamma(mean_n) itself in BF16, zero-padded to k1 columns, which the
 // tensor-core kernel multiplies by the W1m image.
-__global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, GridView g,
-                                                      float *U, uint16_t *G, int k1) {
+__device__ __forceinline__ void pe_mean_block(int blk, const SceneView &s, const MlpView &m,
+                                              const GridView &g, float *U, uint16_t *G, int k1) {
     __shared__ float gam[32][kMaxPe];
-    const int n0 = blockIdx.x * 32;
+    const int n0 = blk * 32;
     const int din = m.dm + m.dt;
     if (threadIdx.x < 32) {
         int n = n0 + threadIdx.x;
@@ -70,9 +70,10 @@ __global__ void __launch_bounds__(128) pe_mean_kernel(SceneView s, MlpView m, Gr
 // V[q][j] for 4 queries per block: the 4 x dt features of Eq. 15 are
 // computed one per thread, then thread j forms output column j of each query.
 constexpr int kTxPerBlock = 4;
-__global__ void __launch_bounds__(128) pe_tx_kernel(MlpView m, const float *tx, int Q, float *V) {
+__device__ __forceinline__ void pe_tx_block(int blk, const MlpView &m, const float *tx, int Q,
+                                            float *V) {
     __shared__ float gam[kTxPerBlock][kMaxPe];
-    const int q0 = blockIdx.x * kTxPerBlock;
+    const int q0 = blk * kTxPerBlock;
     const int din = m.dm + m.dt;
     const int L = m.L_tx;
     for (int e = threadIdx.x; e < kTxPerBlock * m.dt; e += blockDim.x) {
@@ -121,7 +122,8 @@ __device__ __forceinline__ uint32_t sw128_offset(int n, int k, int rows) {
 // layer: FP32 transposes and BF16 swizzled images.  The BF16 image starts
 // with W1m = W0[:, :dm] as a 128 x 64 K-major image (columns >= dm zero) and
 // ends with the bias image and the four bias selectors (layout in kernels.h).
-__global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
+__device__ __forceinline__ void weights_block(int blk, int nblk, const MlpView &m,
+                                              const DeformWs &ws, int want_bf16) {
     const int nh = m.n_layers - 2;
     const long long per = WRF_HIDDEN * WRF_HIDDEN;
     const long long w1 = want_bf16 ? WRF_HIDDEN * 64 : 0;
@@ -130,8 +132,8 @@ __global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
     char *img = reinterpret_cast<char *>(ws.w_bf16);
     const int din = m.dm + m.dt;
     const size_t aug_off = kW1ImageBytes + static_cast<size_t>(nh) * per * 2 + 16 * WRF_HIDDEN * 2;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long i = blk * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(nblk) * blockDim.x) {
         if (i >= mats) {
             // bias image (1024 elements), then selectors (4 x 128 elements)
             const int e = static_cast<int>(i - mats);
@@ -185,6 +187,29 @@ __global__ void weights_kernel(MlpView m, DeformWs ws, int want_bf16) {
     }
 }
 
+// The three independent preparation jobs in one launch, so that they run
+// side by side: blocks [0, nb_mean) encode 32 Gaussians each, the next nb_tx
+// blocks 4 queries each, the rest build the weight images (grid-stride).
+// Every block runs exactly one job, so each job's barriers see all 128
+// threads of its block.
+__global__ void __launch_bounds__(128) prep_kernel(SceneView s, MlpView m, GridView g,
+                                                   const float *tx, int Q, DeformWs ws,
+                                                   int want_bf16, int k1, int nb_mean,
+                                                   int nb_tx) {
+    int b = blockIdx.x;
+    if (b < nb_mean) {
+        pe_mean_block(b, s, m, g, ws.U, want_bf16 ? ws.G : nullptr, k1);
+        return;
+    }
+    b -= nb_mean;
+    if (b < nb_tx) {
+        pe_tx_block(b, m, tx, Q, ws.V);
+        return;
+    }
+    b -= nb_tx;
+    weights_block(b, static_cast<int>(gridDim.x) - nb_mean - nb_tx, m, ws, want_bf16);
+}
+
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 }  // namespace
@@ -212,16 +237,18 @@ size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
 
 cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
                         int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st) {
-    if (s.n > 0)
-        pe_mean_kernel<<<(s.n + 31) / 32, 128, 0, st>>>(s, m, g, ws.U, want_bf16 ? ws.G : nullptr,
-                                                        mlp_k1(m.dm));
-    if (Q > 0) pe_tx_kernel<<<(Q + kTxPerBlock - 1) / kTxPerBlock, 128, 0, st>>>(m, tx, Q, ws.V);
-    long long total = (want_bf16 ? WRF_HIDDEN * 64 : 0) +
-                      static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
-                      16 * WRF_HIDDEN + (want_bf16 ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
-    int blocks = static_cast<int>((total + 255) / 256);
-    if (blocks > 1184) blocks = 1184;
-    weights_kernel<<<blocks, 256, 0, st>>>(m, ws, want_bf16 ? 1 : 0);
+    const int nb_mean = s.n > 0 ? (s.n + 31) / 32 : 0;
+    const int nb_tx = Q > 0 ? (Q + kTxPerBlock - 1) / kTxPerBlock : 0;
+    const long long total = (want_bf16 ? WRF_HIDDEN * 64 : 0) +
+                            static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
+                            16 * WRF_HIDDEN +
+                            (want_bf16 ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
+    long long nb_w = (total + 127) / 128;
+    if (nb_w > 2368) nb_w = 2368;
+    const long long blocks = nb_mean + nb_tx + nb_w;
+    if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
+    prep_kernel<<<static_cast<unsigned>(blocks), 128, 0, st>>>(
+        s, m, g, tx, Q, ws, want_bf16 ? 1 : 0, mlp_k1(m.dm), nb_mean, nb_tx);
     return cudaGetLastError();
 }
 
