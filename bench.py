@@ -866,7 +866,7 @@ def run_paper(args):
                     "api": "batched.HostPipeline over batched.PaperForward (pinned host TX in, "
                            "pinned host magnitude / phase out, copies overlapped with the next "
                            "step)"},
-            "roofline": roof, "gpu_launches": PaperForward.launches_per_run * K}
+            "roofline": roof, "gpu_launches": pfw.launches_per_run * K}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import paper as opaper
         import oracle

@@ -144,10 +144,14 @@ class PaperForward(BatchedForward):
         self.cap = 0
         self.gids = None
         self._alloc_keys(int(key_capacity))
+        net = 1 if mlp is None else (2 if mlp.precision == _lib.WRF_BF16 else 4)
+        self.launches_per_run = net + 6
 
-    # kernels one run() launches: the network's four (weight images or
-    # panels, encodings, per-query terms, network), binning's five, render
-    launches_per_run = 10
+    # kernels one run() launches, set in __init__: the network's (tensor
+    # cores: one prep launch and the network; FP32: encodings, per-query
+    # terms, weights and the network; no network: the projection alone),
+    # binning's five, render
+    launches_per_run = 8
 
     def deform_project(self, tx, stream=None):
         wrf_paper_deform_project(self.scene, self.mlp, self.grid, tx, rec=self.rec, ws=self.dws,

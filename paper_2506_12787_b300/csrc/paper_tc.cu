@@ -139,11 +139,12 @@ __device__ inline int in_dim_tc(const PaperNetTc &m, int l) {
 
 // BF16 panels of every hidden layer in consumption order, and the output
 // layer's three panels (rows = output units, K-major, 128-byte swizzle).
-__global__ void paper_tc_weights_kernel(PaperNetTc m, int nseq, uint16_t *wimg, uint16_t *oimg) {
+__device__ __forceinline__ void paper_tc_weights_block(int blk, int nblk, const PaperNetTc &m,
+                                                       int nseq, uint16_t *wimg, uint16_t *oimg) {
     const long long per = static_cast<long long>(kPW) * 64;
     const long long total = nseq * per + 3LL * 16 * 64;
-    for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
-         i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    for (long long i = blk * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(nblk) * blockDim.x) {
         if (i < nseq * per) {
             const int s = static_cast<int>(i / per);
             const int r = static_cast<int>((i % per) / 64), kl = static_cast<int>(i % 64);
@@ -182,8 +183,9 @@ __global__ void paper_tc_weights_kernel(PaperNetTc m, int nseq, uint16_t *wimg, 
 
 // gamma(mean_n) rows [N][64] BF16 (42 values of Eq. 15 at L_mean = 10, zeros
 // after them): the encoding input on the unit square (tanh u + 1) / 2.
-__global__ void paper_tc_gamma_kernel(PaperView s, int L_mean, int dm, uint16_t *G) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void paper_tc_gamma_block(int blk, const PaperView &s, int L_mean,
+                                                     int dm, uint16_t *G) {
+    const int n = blk * blockDim.x + threadIdx.x;
     if (n >= s.n) return;
     const float2 mu = reinterpret_cast<const float2 *>(s.mu)[n];
     const PeArg a[2] = {unit_centre(mu.x), unit_centre(mu.y)};
@@ -199,9 +201,10 @@ __global__ void paper_tc_gamma_kernel(PaperView s, int L_mean, int dm, uint16_t 
 
 // vec[q][l][j] (FP32): W_s gamma(s_q) + b for the layers whose input holds
 // the encoding, b for the others, zero past the width; one block per (q, l).
-__global__ void __launch_bounds__(kPW) paper_tc_vec_kernel(PaperNetTc m, const float *tx, float *vec) {
+__device__ __forceinline__ void paper_tc_vec_block(int q, int l, const PaperNetTc &m,
+                                                   const float *tx, float *vec) {
     __shared__ float gam[3 * (2 * 15 + 1)];
-    const int q = blockIdx.x, l = blockIdx.y, j = threadIdx.x;
+    const int j = threadIdx.x;
     const bool enc = l < m.n_hidden && (l == 0 || is_skip(l));
     if (enc && j == 0) {
         PeArg a[3];
@@ -219,6 +222,30 @@ __global__ void __launch_bounds__(kPW) paper_tc_vec_kernel(PaperNetTc m, const f
         acc += m.b[l][j];
     }
     vec[(static_cast<size_t>(q) * (kPaperMaxLayers - 1) + l) * kPW + j] = acc;
+}
+
+// The three independent preparation jobs of the network in one launch of
+// kPW-thread blocks, so that they run side by side: blocks [0, nb_vec) form
+// vec for one (query, layer) each, the next nb_gamma blocks encode kPW
+// Gaussians each, the rest build the weight panels (grid-stride).  Every
+// block runs exactly one job, so the vec job's barrier sees all its threads.
+__global__ void __launch_bounds__(kPW) paper_tc_prep_kernel(PaperNetTc m, int nseq, uint16_t *wimg,
+                                                            uint16_t *oimg, PaperView s,
+                                                            uint16_t *G, const float *tx,
+                                                            float *vec, int nb_vec, int nb_gamma) {
+    int b = blockIdx.x;
+    if (b < nb_vec) {
+        paper_tc_vec_block(b / (kPaperMaxLayers - 1), b % (kPaperMaxLayers - 1), m, tx, vec);
+        return;
+    }
+    b -= nb_vec;
+    if (b < nb_gamma) {
+        paper_tc_gamma_block(b, s, m.L_mean, m.dm, G);
+        return;
+    }
+    b -= nb_gamma;
+    paper_tc_weights_block(b, static_cast<int>(gridDim.x) - nb_vec - nb_gamma, m, nseq, wimg,
+                           oimg);
 }
 
 struct PaperTcArgs {
@@ -485,9 +512,13 @@ cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, co
     const int nseq = seq_len(m.n_hidden);
     uint16_t *wimg = ws.img;
     uint16_t *oimg = ws.img + static_cast<size_t>(nseq) * kBPanel / 2;
-    paper_tc_weights_kernel<<<148 * 2, 256, 0, st>>>(m, nseq, wimg, oimg);
-    paper_tc_gamma_kernel<<<(sv.n + 127) / 128, 128, 0, st>>>(s, m.L_mean, m.dm, ws.G);
-    paper_tc_vec_kernel<<<dim3(Q, kPaperMaxLayers - 1), kPW, 0, st>>>(m, tx, ws.vec);
+    {
+        const int nb_vec = Q * (kPaperMaxLayers - 1);
+        const int nb_gamma = (sv.n + kPW - 1) / kPW;
+        const int nb_w = 148 * 4;  // 592 x 160 threads, about the 296 x 256 of a separate launch
+        paper_tc_prep_kernel<<<nb_vec + nb_gamma + nb_w, kPW, 0, st>>>(
+            m, nseq, wimg, oimg, s, ws.G, tx, ws.vec, nb_vec, nb_gamma);
+    }
     PaperTcArgs a{};
     a.s = s;
     a.g = g;
