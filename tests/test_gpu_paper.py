@@ -358,7 +358,7 @@ def test_paper_workload_full_size_sampled(api, precision):
     assert ok_re and ok_im
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "none"])
 def test_paper_host_pipeline_matches_forward_paper(api, precision):
     """HostPipeline over PaperForward (TX from pinned host memory, magnitude /
     phase back to pinned host memory, copies overlapped) returns exactly the
@@ -368,11 +368,13 @@ def test_paper_host_pipeline_matches_forward_paper(api, precision):
     prec = _lib.WRF_BF16 if precision == "bf16" else _lib.WRF_FP32
     sc = synth.make_paper_scene(N, H, W, seed=21)
     ds = api.DevicePaperScene.from_host(sc, dev())
-    dm = api.DevicePaperMLP.from_host(paper_mlp(21), dev(), precision=prec)
+    dm = None if precision == "none" else api.DevicePaperMLP.from_host(paper_mlp(21), dev(),
+                                                                        precision=prec)
     grid = api.make_grid(H, W, 32, 8, 9.0)
     txs = [synth.make_tx(Q, seed=50 + i) for i in range(2)]
     ref = [api.Renderer(grid, dev()).forward_paper(ds, dm, T(t)).cpu().numpy() for t in txs]
     fw = PaperForward(ds, dm, grid, Q, dev())
+    assert fw.launches_per_run == {"fp32": 10, "bf16": 8, "none": 7}[precision]
     for t in txs:  # key capacity for both batches
         fw.reserve(T(t))
     pipe = HostPipeline(fw)
