@@ -1071,6 +1071,12 @@ def main():
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (ncu)"
     roof["stage_ms"] = stage
+    # the sort (binning) against HBM on every workload, whichever stage dominates
+    bin_bytes = BIN_BYTES_PER_REC * Q * N + BIN_BYTES_PER_KEY * n_keys + 4 * (Q * fw.T + 1)
+    binning = {"keys": int(n_keys), "algorithmic_bytes": int(bin_bytes),
+               "achieved": bin_bytes / (stage["bin"] * 1e-3) / 1e9, "unit": "GB/s",
+               "peak": peaks["hbm_gbs"], "peak_source": f"hbm_gbs ({peak_src})"}
+    binning["frac"] = binning["achieved"] / binning["peak"]
 
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
@@ -1086,7 +1092,7 @@ def main():
                            "copies overlapped with the next step)",
                     "l2": "no flush; each step writes 164 MB of records + 33 MB of spectra"},
             "gpu_launches": fw.launches_per_run * K,
-            "roofline": roof}
+            "roofline": roof, "binning": binning}
     if args.serving and ws == 1 and args.workload == "batched":
         line["serving"] = run_serving(args, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
