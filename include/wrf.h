@@ -25,7 +25,10 @@
  *   - Spectrum layout: FP32 [Q][H][W] row-major; row y = elevation index,
  *     column x = azimuth index (Sec. 3.1, Eq. 5: 90 rows x 360 columns at
  *     1 degree).  Pixel (x, y) is sampled at integer coordinates (x, y).
- *   - One channel (C = 1) is supported: the scalar signal response.
+ *   - Channels: one (C = 1, the scalar signal response) everywhere; two
+ *     (real and imaginary amplitude, Sec. 6.1) for the forward calls, with
+ *     wrf_render_complex giving magnitude and phase.  The backward calls take
+ *     one channel.
  */
 #ifndef WRF_H
 #define WRF_H
@@ -186,8 +189,10 @@ wrf_status wrf_bin(const float *rec, int32_t n, int32_t Q, const wrf_grid *grid,
  *     Q * ceil(N / 512) up to about 7,500.
  *   - The function allocates nothing (no cudaMalloc, cudaFree or allocating
  *     library call).  Its first call on a device looks the array's device
- *     address up once (cudaGetSymbolAddress); make that first call outside
- *     any stream capture.
+ *     address up once (cudaGetSymbolAddress) and caches it with the context's
+ *     id; make that first call outside any stream capture.  After a device
+ *     reset the next call looks the address up again in the new context
+ *     (again outside capture).
  *   - Every call shares the one array: calls that may run at the same time
  *     on the GPU (different streams, or overlapping work on one device)
  *     race on it.  Serialise them.  The array keeps the last call's

@@ -5,6 +5,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cuda.h>
+
 #include <mutex>
 
 #include "kernels.h"
@@ -27,18 +29,69 @@ wrf_status cuda_fail(cudaError_t e, const char *where) {
     return fail(WRF_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-// Device address of g_status for the current device (looked up once per
-// device; the first call on a device should happen outside stream capture).
-int *status_ptr() {
-    static int *ptrs[64] = {nullptr};
+// Device address of a __device__ symbol in the current device's context,
+// cached per device together with the context it was looked up in: after a
+// device reset (a new primary context, where the module and its symbols may
+// sit elsewhere) the address is looked up again.  The first lookup in a
+// context should happen outside stream capture.  Returns the CUDA error.
+struct SymbolCache {
+    void *ptr[64] = {nullptr};
+    unsigned long long ctx_id[64] = {0};  // unique id of the context (never reused)
+    std::mutex mu;
+};
+
+cudaError_t symbol_ptr(SymbolCache &c, const void *symbol, void **out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-        ptrs[dev] = static_cast<int *>(p);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    // make the device's primary context current (initialises it if needed)
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return e;
+    // the driver calls are fetched through the runtime, so the library has
+    // no link-time dependency on the driver library
+    using GetCurrentFn = CUresult (*)(CUcontext *);
+    using GetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(c.mu);
+        if (!get_current || !get_id) {
+            void *f0 = nullptr, *f1 = nullptr;
+            cudaDriverEntryPointQueryResult r0, r1;
+            if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault,
+                                                 &r0) != cudaSuccess ||
+                cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault,
+                                                 &r1) != cudaSuccess ||
+                r0 != cudaDriverEntryPointSuccess || r1 != cudaDriverEntryPointSuccess)
+                return cudaErrorSymbolNotFound;
+            get_current = reinterpret_cast<GetCurrentFn>(f0);
+            get_id = reinterpret_cast<GetIdFn>(f1);
+        }
     }
-    return ptrs[dev];
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return cudaErrorDeviceUninitialized;
+    std::lock_guard<std::mutex> lock(c.mu);
+    if (!c.ptr[dev] || c.ctx_id[dev] != id) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, symbol);
+        if (e != cudaSuccess) return e;
+        c.ptr[dev] = p;
+        c.ctx_id[dev] = id;
+    }
+    *out = c.ptr[dev];
+    return cudaSuccess;
+}
+
+// Device address of g_status for the current device, or NULL.
+int *status_ptr() {
+    static SymbolCache cache;
+    void *p = nullptr;
+    if (symbol_ptr(cache, reinterpret_cast<const void *>(&g_status), &p) != cudaSuccess)
+        return nullptr;
+    return static_cast<int *>(p);
 }
 
 // Scratch for wrf_bin_noalloc: a fixed array in device memory that exists on
@@ -48,25 +101,12 @@ int *status_ptr() {
 constexpr size_t kBinScratchBytes = size_t(4) << 20;  // 4 MiB
 __device__ __align__(256) unsigned char g_bin_scratch[kBinScratchBytes];
 
-// Device address of g_bin_scratch on the current device, looked up on the
-// first call per device (the first wrf_bin_noalloc call on a device should
-// therefore come before any stream capture).  Returns the CUDA error.
+// Device address of g_bin_scratch on the current device (see symbol_ptr: the
+// first wrf_bin_noalloc call in a context should come before any stream
+// capture).  Returns the CUDA error.
 cudaError_t bin_scratch_ptr(void **out) {
-    static void *ptrs[64] = {nullptr};
-    static std::mutex mu;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!ptrs[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_bin_scratch);
-        if (e != cudaSuccess) return e;
-        ptrs[dev] = p;
-    }
-    *out = ptrs[dev];
-    return cudaSuccess;
+    static SymbolCache cache;
+    return symbol_ptr(cache, reinterpret_cast<const void *>(g_bin_scratch), out);
 }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }

@@ -33,3 +33,36 @@ def spectrum_error(gpu, ref, slack, rel_tol):
         worst = max(worst, float(np.maximum(d - slack[q], 0.0).max()) / peak)
     return ok, worst, used
 
+
+
+def grad_error(gpu, ref, rel=1e-3, floor=1e-3):
+    """Element-wise gradient check of one parameter group:
+    |g - g_ref| <= rel * |g_ref| + floor * max|g_ref| for every element (the
+    floor keeps the bound defined where a component is ~0).  Returns (ok,
+    worst ratio |g - g_ref| / bound (<= 1 passes), flat index of the worst
+    element, its GPU value, its oracle value)."""
+    a = np.asarray(gpu, np.float64).ravel()
+    b = np.asarray(ref, np.float64).ravel()
+    assert a.shape == b.shape, (a.shape, b.shape)
+    if b.size == 0:
+        return True, 0.0, -1, 0.0, 0.0
+    bound = rel * np.abs(b) + floor * float(np.abs(b).max())
+    d = np.abs(a - b)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(bound > 0, d / np.where(bound > 0, bound, 1.0), np.where(d > 0, np.inf, 0.0))
+    i = int(np.argmax(ratio))
+    worst = float(ratio[i])
+    return bool(worst <= 1.0), worst, i, float(a[i]), float(b[i])
+
+
+def check_grads(named, tag, rel=1e-3, floor=1e-3):
+    """Runs grad_error over (name, gpu, ref) groups, prints each group's worst
+    element and returns the worst ratio over all groups (<= 1 passes)."""
+    worst = 0.0
+    for name, a, b in named:
+        ok, r, i, ga, gb = grad_error(a, b, rel, floor)
+        print(f"{tag} {name}: worst element {i}: gpu {ga:.6e} oracle {gb:.6e} "
+              f"(|diff| / bound = {r:.2e})")
+        worst = max(worst, r)
+    print(f"{tag}: worst over all groups {worst:.2e} (<= 1 passes)")
+    return worst

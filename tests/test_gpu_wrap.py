@@ -1,7 +1,8 @@
 """GPU parity of the azimuth-wrap option (0 and W columns the same
 direction) against the FP64 oracle: wrapped tile lists bit-exact, spectra
 within 1e-4 x peak (FP32 MLP) or 2e-3 x peak (BF16 MLP) plus the cutoff-band
-slack, gradients within 1e-3 relative, the RSSI head with wrap, and the
+slack, gradients element by element within 1e-3 relative (floor 1e-3 of
+the group's largest component), the RSSI head with wrap, and the
 reported limit (a footprint as wide as W - tile width)."""
 import math
 
@@ -11,7 +12,7 @@ import torch
 
 import oracle
 import synth
-from helpers import oracle_proj_to_records, spectrum_error
+from helpers import check_grads, oracle_proj_to_records, spectrum_error
 from paper_2506_12787_b300 import _lib
 
 pytestmark = pytest.mark.gpu
@@ -98,18 +99,18 @@ def test_wrapped_gradients(api):
     out.backward(T(dA))
     ref = oracle.grad(sc, m, tx, H, W, 9.0, dA, wrap=True)
     names = ["d_mean", "d_log_scale", "d_rot", "d_opacity", "d_amp"]
-    worst = 0.0
+    grp = []
     for k, lv in zip(names, leaves):
-        a = lv.grad.cpu().numpy().ravel()
-        b = ref[k].ravel()
-        e = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-        print(f"wrap grad {k}: rel {e:.2e}")
-        worst = max(worst, e)
-    for p, rW in zip(ps[0::2], ref["d_W"]):
-        a, b = p.grad.cpu().numpy().ravel(), rW.ravel()
-        worst = max(worst, float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)))
-    print(f"wrap grad worst rel {worst:.2e}")
-    assert worst <= 1e-3
+        a = lv.grad.cpu().numpy()
+        if a.ndim == 2:
+            grp += [(f"{k}[:,{c}]", a[:, c], ref[k][:, c]) for c in range(a.shape[1])]
+        else:
+            grp.append((k, a, ref[k]))
+    for l, (p, rW) in enumerate(zip(ps[0::2], ref["d_W"])):
+        grp.append((f"d_W[{l}]", p.grad.cpu().numpy(), rW))
+    for l, (p, rb) in enumerate(zip(ps[1::2], ref["d_b"])):
+        grp.append((f"d_b[{l}]", p.grad.cpu().numpy(), rb))
+    assert check_grads(grp, "wrap grad") <= 1.0
 
 
 def test_wrapped_rssi(api):

@@ -71,3 +71,38 @@ def test_noalloc_matches_wrf_bin_twice(lib):
         assert torch.equal(off, off0), call
         assert torch.equal(gids[:k], gids0[:k]), call
     assert api.wrf_status_read() == 0
+
+
+@pytest.mark.gpu
+def test_noalloc_allocates_nothing(lib):
+    """After a first (warm-up) call, further calls change neither torch's
+    allocator statistics nor the device's free memory."""
+    import torch
+    from paper_2506_12787_b300 import _lib, api
+    H, W, Q, N = 90, 360, 4, 3000
+    dev = torch.device("cuda:0")
+    rec = torch.as_tensor(synth.random_rects_records(Q, N, H, W, r_max=30, seed=32), device=dev)
+    g = api.make_grid(H, W, 16, 16, 9.0)
+    T = api.tiles_of(g)
+    cap = Q * N * 40
+    gids = torch.zeros(cap, dtype=torch.int32, device=dev)
+    nk = torch.zeros(1, dtype=torch.int64, device=dev)
+    off = torch.zeros(Q * T + 1, dtype=torch.int32, device=dev)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def call():
+        _lib.check(lib.wrf_bin_noalloc(C.c_void_p(rec.data_ptr()), N, Q, C.byref(g),
+                                       C.c_void_p(gids.data_ptr()), cap,
+                                       C.c_void_p(nk.data_ptr()), C.c_void_p(off.data_ptr()),
+                                       stream))
+        torch.cuda.synchronize()
+
+    call()  # warm-up: the first call in a context looks up the scratch address
+    alloc0 = torch.cuda.memory_allocated(dev)
+    free0, _ = torch.cuda.mem_get_info(dev)
+    for _ in range(3):
+        call()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert torch.cuda.memory_allocated(dev) == alloc0
+    assert free1 == free0, (free0, free1)
+    assert int(nk.item()) > 0
