@@ -17,6 +17,8 @@ Function -> paper:
   render        Sec. 4.1 Eq. 9, Sec. 4.2 Eq. 13 (order-free truncated sum)
   bin_f32       tile lists, Sec. 4.1 ("spectrum domain partitioned into tiles")
   grad          derivatives of the above (Sec. 4.4 training by back-propagation)
+  mlp_grad      the MLP part of grad, with the slack of ReLU decisions that an FP32
+                forward may take either way
   wrap          optional azimuth periodicity (0 and W columns the same direction:
                 every sum runs over the images mx + m W of each Gaussian, the tile
                 lists cover columns modulo W)
@@ -82,6 +84,9 @@ def lib():
         L.or_project_grad.restype = None
         L.or_mlp_grad.argtypes = [C.c_int, D, C.c_int, C.c_int, C.c_int, D, C.c_int, C.c_int, D,
                                   D, C.c_int, I, D, D, C.c_int, D, D]
+        L.or_mlp_grad_slack.argtypes = [C.c_int, D, C.c_int, C.c_int, C.c_int, D, C.c_int,
+                                        C.c_int, D, D, C.c_int, I, D, D, C.c_int, C.c_double, D,
+                                        D, D, D]
         L.or_num_threads.argtypes = []
         _lib = L
     return _lib
@@ -244,13 +249,54 @@ def bin_f32(rec32, H: int, W: int, tw: int, th: int, cap: int | None = None, wra
     return counts, gids[: int(nk.value)], offsets, int(nk.value)
 
 
+# ReLU decisions whose pre-activation lies within this fraction of the
+# magnitude of its terms (|b| + sum |W a|) of zero: an FP32 evaluation of the
+# same row may take them either way (its rounding error is ~1e-6 of that
+# magnitude), so both gradients are correct; mlp_grad reports the slack.
+RELU_BAND = 4e-6
+
+
+def mlp_grad(scene, mlp, tx, H: int, W: int, d_resid, stop_grad_mean: bool = False,
+             band: float = RELU_BAND):
+    """FP64 back-propagation through F_theta (Eq. 14-15) of dL/d(resid)
+    [Q,N,5]: returns (dW list, db list, d_mean [N,2] through gamma(mean),
+    slack dict).  slack holds, per gradient element, the summed absolute
+    change when one ambiguous ReLU decision (|z| <= band * magnitude) is
+    taken the other way: d_W, d_b (lists) and d_mean; "decisions" counts
+    them (0 with band = 0)."""
+    tx = np.atleast_2d(tx)
+    Q = tx.shape[0]
+    dims, params = flat_params(mlp)
+    params, ppar = _d(params)
+    N = int(np.asarray(scene.mean).shape[0])
+    dparams = np.zeros_like(params)
+    sl = np.zeros_like(params)
+    dmean = np.zeros((N, 2))
+    dmean_sl = np.zeros((N, 2))
+    mean, pm = _d(scene.mean)
+    txd, pt = _d(tx)
+    rmin, prm = _d(mlp.room_min)
+    rsz, prs = _d(mlp.room_size)
+    dr, pdr = _d(d_resid)
+    rc = lib().or_mlp_grad_slack(N, pm, H, W, Q, pt, mlp.L_mean, mlp.L_tx, prm, prs, len(mlp.W),
+                                 dims.ctypes.data_as(I), ppar, pdr, int(stop_grad_mean),
+                                 float(band), dparams.ctypes.data_as(D), dmean.ctypes.data_as(D),
+                                 sl.ctypes.data_as(D), dmean_sl.ctypes.data_as(D))
+    if rc != 0:
+        raise ValueError(f"or_mlp_grad_slack failed ({rc})")
+    dW, db = unflat_params(mlp, dparams)
+    sW, sb = unflat_params(mlp, sl)
+    return dW, db, dmean, dict(d_W=sW, d_b=sb, d_mean=dmean_sl)
+
+
 def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool = False,
          wrap: bool = False):
     """Analytic FP64 gradient of L given dL/dA [Q,H,W].
 
     Returns a dict with d_mean [N,2], d_log_scale [N,2], d_rot [N],
     d_opacity [N], d_amp [N], d_W (list), d_b (list), d_resid [Q,N,5] and
-    d_proj [Q,N,6]."""
+    d_proj [Q,N,6]; with an MLP also "slack": the ambiguous-ReLU slack of
+    d_W, d_b and d_mean (see mlp_grad)."""
     tx = np.atleast_2d(tx)
     Q = tx.shape[0]
     resid = deform(scene, mlp, tx, H, W) if mlp is not None else None
@@ -273,22 +319,9 @@ def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool 
     out = dict(d_mean=d_mean, d_log_scale=d_ls, d_rot=d_rot, d_opacity=d_op, d_amp=d_amp,
                d_resid=dresid, d_proj=dproj)
     if mlp is not None:
-        dims, params = flat_params(mlp)
-        params, ppar = _d(params)
-        dparams = np.zeros_like(params)
-        dmean_mlp = np.zeros((N, 2))
-        mean, pm = _d(scene.mean)
-        txd, pt = _d(tx)
-        rmin, prm = _d(mlp.room_min)
-        rsz, prs = _d(mlp.room_size)
-        rc = lib().or_mlp_grad(N, pm, H, W, Q, pt, mlp.L_mean, mlp.L_tx, prm, prs, len(mlp.W),
-                               dims.ctypes.data_as(I), ppar, dresid.ctypes.data_as(D),
-                               int(stop_grad_mean), dparams.ctypes.data_as(D),
-                               dmean_mlp.ctypes.data_as(D))
-        if rc != 0:
-            raise ValueError(f"or_mlp_grad failed ({rc})")
+        dW, db, dmean_mlp, slack = mlp_grad(scene, mlp, tx, H, W, dresid, stop_grad_mean)
         out["d_mean"] = d_mean + dmean_mlp
         out["d_mean_direct"] = d_mean
-        dW, db = unflat_params(mlp, dparams)
         out["d_W"], out["d_b"] = dW, db
+        out["slack"] = slack
     return out

@@ -453,14 +453,85 @@ void or_project_grad(int N, const double *log_scale, const double *rot,
     }
 }
 
+/* Back-propagation of one row through F_theta (Sec. 4.4: every parameter is
+ * fitted by gradient descent).  `pre` holds the row's pre-activations from
+ * or_mlp_row.  The ReLU decision of hidden unit j of layer l is z > 0, except
+ * for the one unit (flip_l, flip_j), if flip_l >= 0, whose decision is taken
+ * the other way round (its activation then counts as 0: it lies within
+ * rounding of zero).  Adds the row's parameter gradient into gp (params
+ * layout) and, unless stop_grad_mean is set, the derivative through
+ * gamma(mean) into gm[2]. */
+static void row_backward(const double *in, const double *pre, int n_layers, const int *dims,
+                         const double *params, const size_t *off, const double *dres,
+                         int flip_l, int flip_j, int stop_grad_mean, const double *mu, int H,
+                         int W, int L_mean, double *gp, double *gm)
+{
+    double delta[OR_MAX_WIDTH], prev[OR_MAX_WIDTH], act[OR_MAX_WIDTH];
+    int dl = dims[n_layers];
+    memcpy(delta, dres, sizeof(double) * dl);
+    for (int l = n_layers - 1; l >= 0; --l) {
+        int din = dims[l], dout = dims[l + 1];
+        const double *Wl = params + off[l];
+        double *gW = gp + off[l], *gb = gW + (size_t)dout * din;
+        /* input activation of layer l: ReLU of layer l-1's pre-activation */
+        if (l == 0) memcpy(act, in, sizeof(double) * din);
+        else
+            for (int k = 0; k < din; ++k) {
+                double z = pre[(size_t)(l - 1) * OR_MAX_WIDTH + k];
+                int on = z > 0.0;
+                if (l - 1 == flip_l && k == flip_j) { on = !on; z = 0.0; }
+                act[k] = on ? z : 0.0;
+            }
+        for (int j = 0; j < dout; ++j) {
+            gb[j] += delta[j];
+            for (int k = 0; k < din; ++k) gW[(size_t)j * din + k] += delta[j] * act[k];
+        }
+        for (int k = 0; k < din; ++k) {
+            double sum = 0.0;
+            for (int j = 0; j < dout; ++j) sum += Wl[(size_t)j * din + k] * delta[j];
+            prev[k] = sum;
+        }
+        if (l > 0)
+            for (int k = 0; k < din; ++k) {
+                int on = pre[(size_t)(l - 1) * OR_MAX_WIDTH + k] > 0.0;
+                if (l - 1 == flip_l && k == flip_j) on = !on;
+                delta[k] = on ? prev[k] : 0.0;
+            }
+        else
+            memcpy(delta, prev, sizeof(double) * din);
+    }
+    if (!stop_grad_mean) {
+        /* delta now holds dL/d(input features); the first dm belong to gamma(mean). */
+        for (int i = 0; i < 2; ++i) {
+            double g = delta[i];
+            for (int k = 0; k < L_mean; ++k) {
+                double f = ldexp(M_PI, k);
+                g += delta[2 + k * 2 + i] * f * cos(f * mu[i]);
+                g -= delta[2 + L_mean * 2 + k * 2 + i] * f * sin(f * mu[i]);
+            }
+            gm[i] += g / (i == 0 ? W : H);
+        }
+    }
+}
+
 /* Back-propagation through F_theta for every row: accumulates d_params
  * (same layout as params) and, unless stop_grad_mean is set, adds the
  * derivative through gamma(mean) to d_mean [N,2] (the paper freezes position
- * gradients in its fine stage, Sec. 4.4; the flag reproduces that). */
-int or_mlp_grad(int N, const double *mean, int H, int W, int Q, const double *tx, int L_mean,
-                int L_tx, const double *room_min, const double *room_size, int n_layers,
-                const int *dims, const double *params, const double *dresid, int stop_grad_mean,
-                double *d_params, double *d_mean)
+ * gradients in its fine stage, Sec. 4.4; the flag reproduces that).
+ *
+ * Ambiguous ReLU decisions: a hidden pre-activation z with
+ * |z| <= band * (|b_j| + sum_k |W_jk a_k|) lies within the rounding error of
+ * an FP32 evaluation of the same row, so an FP32 forward may take its ReLU
+ * decision either way and both gradients are correct.  If slack is non-NULL
+ * (params layout, and dmean_slack [N,2]) it receives, summed over every such
+ * decision of every row, the absolute change of each gradient element when
+ * that one decision is taken the other way (band = 0: no ambiguous
+ * decision, zero slack). */
+int or_mlp_grad_slack(int N, const double *mean, int H, int W, int Q, const double *tx,
+                      int L_mean, int L_tx, const double *room_min, const double *room_size,
+                      int n_layers, const int *dims, const double *params, const double *dresid,
+                      int stop_grad_mean, double band, double *d_params, double *d_mean,
+                      double *slack, double *dmean_slack)
 {
     if (n_layers < 1 || n_layers > OR_MAX_LAYERS) return OR_EINVAL;
     size_t P = param_count(n_layers, dims);
@@ -470,8 +541,12 @@ int or_mlp_grad(int N, const double *mean, int H, int W, int Q, const double *tx
 #endif
     double *part = calloc((size_t)nthreads * P, sizeof(double));
     double *dmp = calloc((size_t)nthreads * 2 * N, sizeof(double));
-    if (!part || !dmp) { free(part); free(dmp); return OR_EINVAL; }
-    int dm = 2 * (2 * L_mean + 1);
+    double *spart = slack ? calloc((size_t)nthreads * P, sizeof(double)) : NULL;
+    double *smp = slack ? calloc((size_t)nthreads * 2 * N, sizeof(double)) : NULL;
+    if (!part || !dmp || (slack && (!spart || !smp))) {
+        free(part); free(dmp); free(spart); free(smp);
+        return OR_EINVAL;
+    }
 #pragma omp parallel
     {
         int tid = 0;
@@ -481,8 +556,9 @@ int or_mlp_grad(int N, const double *mean, int H, int W, int Q, const double *tx
         double *gp = part + (size_t)tid * P;
         double *gm = dmp + (size_t)tid * 2 * N;
         double *pre = malloc(sizeof(double) * OR_MAX_LAYERS * OR_MAX_WIDTH);
-        double in[OR_MAX_WIDTH], outv[OR_MAX_WIDTH], delta[OR_MAX_WIDTH], prev[OR_MAX_WIDTH];
-        double act[OR_MAX_WIDTH];
+        double *rowA = slack ? malloc(sizeof(double) * P) : NULL;
+        double *rowB = slack ? malloc(sizeof(double) * P) : NULL;
+        double in[OR_MAX_WIDTH], outv[OR_MAX_WIDTH], a[OR_MAX_WIDTH];
         size_t off[OR_MAX_LAYERS + 1];
         off[0] = 0;
         for (int l = 0; l < n_layers; ++l)
@@ -490,62 +566,96 @@ int or_mlp_grad(int N, const double *mean, int H, int W, int Q, const double *tx
 #pragma omp for schedule(static)
         for (long long r = 0; r < (long long)N * Q; ++r) {
             int q = (int)(r / N), n = (int)(r % N);
+            double mu[2] = {mean[2 * n] / W, mean[2 * n + 1] / H};
             mlp_input(mean + 2 * (size_t)n, H, W, tx + 3 * (size_t)q, L_mean, L_tx, room_min,
                       room_size, in);
             or_mlp_row(in, n_layers, dims, params, outv, pre);
-            int dl = dims[n_layers];
-            memcpy(delta, dresid + (size_t)r * dl, sizeof(double) * dl);
-            for (int l = n_layers - 1; l >= 0; --l) {
+            const double *dres = dresid + (size_t)r * dims[n_layers];
+            /* ambiguous ReLU decisions of this row */
+            int nflip = 0;
+            if (slack && band > 0.0) {
+                memcpy(a, in, sizeof(double) * dims[0]);
+                for (int l = 0; l + 1 < n_layers; ++l) {
+                    int din = dims[l], dout = dims[l + 1];
+                    const double *Wl = params + off[l], *bl = Wl + (size_t)dout * din;
+                    for (int j = 0; j < dout; ++j) {
+                        double mag = fabs(bl[j]);
+                        for (int k = 0; k < din; ++k) mag += fabs(Wl[(size_t)j * din + k] * a[k]);
+                        if (fabs(pre[(size_t)l * OR_MAX_WIDTH + j]) <= band * mag) ++nflip;
+                    }
+                    for (int j = 0; j < dout; ++j) {
+                        double z = pre[(size_t)l * OR_MAX_WIDTH + j];
+                        a[j] = z > 0.0 ? z : 0.0;
+                    }
+                }
+            }
+            if (nflip == 0) {
+                row_backward(in, pre, n_layers, dims, params, off, dres, -1, -1, stop_grad_mean,
+                             mu, H, W, L_mean, gp, gm + 2 * n);
+                continue;
+            }
+            double gmA[2] = {0.0, 0.0}, gmB[2];
+            memset(rowA, 0, sizeof(double) * P);
+            row_backward(in, pre, n_layers, dims, params, off, dres, -1, -1, stop_grad_mean, mu,
+                         H, W, L_mean, rowA, gmA);
+            double *sp = spart + (size_t)tid * P, *sm = smp + (size_t)tid * 2 * N;
+            memcpy(a, in, sizeof(double) * dims[0]);
+            for (int l = 0; l + 1 < n_layers; ++l) {
                 int din = dims[l], dout = dims[l + 1];
-                const double *Wl = params + off[l];
-                double *gW = gp + off[l], *gb = gW + (size_t)dout * din;
-                /* input activation of layer l */
-                if (l == 0) memcpy(act, in, sizeof(double) * din);
-                else
-                    for (int k = 0; k < din; ++k) {
-                        double z = pre[(size_t)(l - 1) * OR_MAX_WIDTH + k];
-                        act[k] = z > 0.0 ? z : 0.0;
-                    }
+                const double *Wl = params + off[l], *bl = Wl + (size_t)dout * din;
                 for (int j = 0; j < dout; ++j) {
-                    gb[j] += delta[j];
-                    for (int k = 0; k < din; ++k) gW[(size_t)j * din + k] += delta[j] * act[k];
+                    double mag = fabs(bl[j]);
+                    for (int k = 0; k < din; ++k) mag += fabs(Wl[(size_t)j * din + k] * a[k]);
+                    if (!(fabs(pre[(size_t)l * OR_MAX_WIDTH + j]) <= band * mag)) continue;
+                    memset(rowB, 0, sizeof(double) * P);
+                    gmB[0] = gmB[1] = 0.0;
+                    row_backward(in, pre, n_layers, dims, params, off, dres, l, j,
+                                 stop_grad_mean, mu, H, W, L_mean, rowB, gmB);
+                    for (size_t i = 0; i < P; ++i) sp[i] += fabs(rowB[i] - rowA[i]);
+                    sm[2 * n] += fabs(gmB[0] - gmA[0]);
+                    sm[2 * n + 1] += fabs(gmB[1] - gmA[1]);
                 }
-                for (int k = 0; k < din; ++k) {
-                    double s = 0.0;
-                    for (int j = 0; j < dout; ++j) s += Wl[(size_t)j * din + k] * delta[j];
-                    prev[k] = s;
-                }
-                if (l > 0)
-                    for (int k = 0; k < din; ++k)
-                        delta[k] = pre[(size_t)(l - 1) * OR_MAX_WIDTH + k] > 0.0 ? prev[k] : 0.0;
-                else
-                    memcpy(delta, prev, sizeof(double) * din);
-            }
-            if (!stop_grad_mean) {
-                /* delta now holds dL/d(input features); the first dm belong to gamma(mean). */
-                double mu[2] = {mean[2 * n] / W, mean[2 * n + 1] / H};
-                for (int i = 0; i < 2; ++i) {
-                    double g = delta[i];
-                    for (int k = 0; k < L_mean; ++k) {
-                        double f = ldexp(M_PI, k);
-                        g += delta[2 + k * 2 + i] * f * cos(f * mu[i]);
-                        g -= delta[2 + L_mean * 2 + k * 2 + i] * f * sin(f * mu[i]);
-                    }
-                    gm[2 * n + i] += g / (i == 0 ? W : H);
+                for (int j = 0; j < dout; ++j) {
+                    double z = pre[(size_t)l * OR_MAX_WIDTH + j];
+                    a[j] = z > 0.0 ? z : 0.0;
                 }
             }
-            (void)dm;
+            for (size_t i = 0; i < P; ++i) gp[i] += rowA[i];
+            gm[2 * n] += gmA[0];
+            gm[2 * n + 1] += gmA[1];
         }
         free(pre);
+        free(rowA);
+        free(rowB);
     }
     memset(d_params, 0, sizeof(double) * P);
     for (int t = 0; t < nthreads; ++t)
         for (size_t i = 0; i < P; ++i) d_params[i] += part[(size_t)t * P + i];
     for (int t = 0; t < nthreads; ++t)
         for (int i = 0; i < 2 * N; ++i) d_mean[i] += dmp[(size_t)t * 2 * N + i];
+    if (slack) {
+        memset(slack, 0, sizeof(double) * P);
+        for (int t = 0; t < nthreads; ++t)
+            for (size_t i = 0; i < P; ++i) slack[i] += spart[(size_t)t * P + i];
+        if (dmean_slack)
+            for (int t = 0; t < nthreads; ++t)
+                for (int i = 0; i < 2 * N; ++i) dmean_slack[i] += smp[(size_t)t * 2 * N + i];
+    }
     free(part);
     free(dmp);
+    free(spart);
+    free(smp);
     return OR_OK;
+}
+
+int or_mlp_grad(int N, const double *mean, int H, int W, int Q, const double *tx, int L_mean,
+                int L_tx, const double *room_min, const double *room_size, int n_layers,
+                const int *dims, const double *params, const double *dresid, int stop_grad_mean,
+                double *d_params, double *d_mean)
+{
+    return or_mlp_grad_slack(N, mean, H, W, Q, tx, L_mean, L_tx, room_min, room_size, n_layers,
+                             dims, params, dresid, stop_grad_mean, 0.0, d_params, d_mean, NULL,
+                             NULL);
 }
 
 /* Number of OpenMP threads the oracle runs with (reported by benchmarks). */

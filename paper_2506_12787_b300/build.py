@@ -54,7 +54,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(c))
     if jobs or _stale(OUT, objs):
-        cmd = [NVCC] + ARCH + ["-shared", "-o", OUT + ".tmp"] + objs + ["-lcuda", "-lcublas"]
+        cmd = [NVCC] + ARCH + ["-shared", "-o", OUT + ".tmp"] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

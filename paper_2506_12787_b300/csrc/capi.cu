@@ -680,7 +680,7 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
         if (e != cudaSuccess) return cuda_fail(e, "prep");
     }
     e = wrf::launch_mlp_bwd(sv, m, g, tx, Q, fw, bw, d_resid, acts, dW, db, d_mean,
-                            stop_grad_mean, st);
+                            stop_grad_mean, status_ptr(), st);
     if (e != cudaSuccess) return cuda_fail(e, "mlp_backward");
     return WRF_OK;
 }

@@ -143,23 +143,26 @@ cudaError_t launch_project_bwd(const SceneView &s, const float *resid, int Q, co
                                float *d_resid, float *d_mean, float *d_ls, float *d_rot,
                                float *d_op, float *d_amp, cudaStream_t st);
 
-// MLP backward (row chunks; see mlp_bwd.cu).
+// MLP backward on the tensor cores (mlp_bwd.cu).
 struct DeformBwdWs {
-    float *cb_H0;       // [chunk][din]  first-layer inputs
-    float *cb_Hh[7];    // [chunk][128]  hidden activations (inputs of layers 1..L-1)
-    float *cb_G[8];     // [chunk][128]  pre-activation gradients of layers 0..L-2
-    float *dgm;         // [chunk][dm]   dL/dgamma(mean)
-    float *gam_m;       // [N][dm] gamma(mean)
-    float *gam_t;       // [Q][dt] gamma(tx)
-    char *cublas_ws;    // GEMM workspace handed to cuBLAS
-    size_t cublas_ws_bytes;
+    char *wimg;          // BF16 hi / lo W^T panels of the hidden layers
+    char *gimg;          // BF16 hi / lo gamma(mean) tiles (two term images)
+    long long gterm;     // bytes per term image
+    float *gam_t;        // [Q][dt] gamma(tx) in FP32
+    float *pdw, *pdb, *pdwo, *pdw0;  // per-CTA partial sums
+    float *tilesum;      // [Q * tiles per query][128] per-tile sums of D_0
+    float *colsum;       // [Q][128]
+    float *acts;         // recomputed hidden activations of a chunk of queries
+    float *resid;        // the recompute's residuals (unused)
+    float *d0;           // [chunk rows][128] D_0, for the gradient through gamma(mean)
+    int qc;              // queries per chunk
 };
 size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, DeformBwdWs *bw,
                             char *base);
 cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g,
                            const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
                            const float *d_resid, const float *acts, float *const *dW, float *const *db,
-                           float *d_mean, int stop_grad_mean, cudaStream_t st);
+                           float *d_mean, int stop_grad_mean, int *status, cudaStream_t st);
 
 bool render_config_supported(int tw, int th);
 

@@ -1,124 +1,693 @@
 // Back-propagation through the deformation MLP (Sec. 4.2 Eq. 14-15; the
-// paper fits all parameters by gradient descent, Sec. 4.4).
+// paper fits all parameters by gradient descent, Sec. 4.4), on the
+// 5th-generation tensor cores.
 //
-// Given dL/d(resid) for every (query, Gaussian) row, produces dL/dW and
-// dL/db of every layer and, unless positions are stop-gradded (the paper's
-// fine stage, Sec. 4.4), the derivative through gamma(mean) added into
-// d_mean.  Every step over rows is a dense product, so rows are processed in
-// chunks of up to kChunk as plain GEMMs (cuBLAS, FP32 inputs and outputs computed
-// on the tensor cores with the three-term BF16 split of FP32,
-// CUBLAS_COMPUTE_32F_EMULATED_16BFX9) between small hand-written kernels:
-//   features   H0 = [gamma(mean_n), gamma(tx_q)], H1 = ReLU(U[n] + V[q])
-//   forward    Z_l = H_{l-1} W_{l-1}^T; H_l = ReLU(Z_l + b)       (hidden layers)
-//              -- both skipped for H1.. when the forward saved its hidden
-//              activations (acts), which are then read in place
-//   deltas     D_last = (G_out W_out) * [H_last > 0]; D_{l-1} = (D_l W_l) * [H_{l-1} > 0]
-//   gradients  dW_l += D_l^T H_{l-1} (GEMM over rows, accumulated across
-//              chunks), db_l += column sums of D_l,
-//              dgamma(mean) = D_1 W0m -> d_mean through d gamma / d mean.
-// All matrices are row-major [rows][width]; cuBLAS sees them column-major
-// transposed.  The GEMM workspace comes from the caller's workspace; one
-// cuBLAS handle per device is created on the first call.
-#include <cublas_v2.h>
-
-#include <mutex>
+// Notation: layer l maps H_l -> Z_l, H_{l+1} = ReLU(Z_l); H_0 = [gamma(mean_n),
+// gamma(tx_q)] (Eq. 15), the output layer is l = L-1 and D_l = dL/dZ_l:
+//   D_{L-1} = d_resid,   dW_l += D_l^T H_l,   db_l += sum_rows D_l,
+//   D_{l-1} = (D_l W_l) * [H_l > 0].
+// The forward's hidden activations H_1 .. H_{L-1} are read from `acts`
+// (saved by wrf_deform_acts, or recomputed here by the FP32 forward kernel in
+// chunks of queries).
+//
+// Tiles and layouts.  A tile is 64 consecutive Gaussians (rows) of one query.
+// TMEM lanes are hidden units, not rows: everything a row-sum or a mask needs
+// is then thread-local.  Per tile and layer:
+//   * D_l^T is a 128-unit x 64-row shared tile (K-major, 128-byte swizzle:
+//     unit u's 64 rows in one 128-byte line), written by thread u;
+//   * H_l is a 64-row x 128-unit shared tile (row-major, two 64-unit swizzle
+//     atoms), written by thread u from a coalesced column load;
+//   * delta:  D_{l-1}^T = W_l^T D_l^T   (M = 128 units, N = 64 rows, K = 128):
+//             A = W_l^T panels (K-major), B = the D^T tile read MN-major;
+//   * weight gradient:  dW_l += D_l^T H_l   (M = 128 out units, N = 128 in
+//             units, K = 64 rows): A = the D^T tile (K-major), B = the H tile
+//             (MN-major), accumulated in TMEM over many tiles;
+//   * the epilogue (thread u = TMEM lane u) reads its unit's 64 deltas,
+//     applies the ReLU mask of H_l (bits kept from the load), sums them into
+//     db, and writes D_{l-1}^T back to the tile.
+// The output layer (K = 5) runs on the CUDA cores in FP32: D_{L-2} =
+// (d_resid W_{L-1}) * mask, dW_{L-1} and db_{L-1} in registers.  Layer 0: the
+// gamma(mean) part of dW_0 is one more MMA (A = D_0^T, B = a 64-row x 64-
+// feature tile of gamma(mean) rows); the gamma(tx) part is rank one per
+// query, gamma(tx_q) x (sum over the query's rows of D_0), and db_0 is that
+// row sum: per-tile column sums are stored and reduced per query at the end.
+//
+// Precision.  Every FP32 operand x is split into BF16 hi = bf16(x) and lo =
+// bf16(x - hi); each product is hi*hi + hi*lo + lo*hi (relative error ~2^-17
+// of |a||b|), accumulated in FP32 by the tensor core.  The weight gradients
+// sum over a million rows: each CTA's TMEM accumulators are added into an
+// FP32 partial in global memory every kFlush tile pairs (a bounded number of
+// tensor-core accumulations per FP32 value), and the partials of all CTAs are
+// reduced in a fixed order.
+//
+// A CTA runs two compute warpgroups (a tile each) that share the three dW
+// accumulators, and one producer warp that streams the hidden layers' W^T
+// panels (16 KB each, 4 per layer) through a ring of shared slots with bulk
+// copies; a slot is refilled once both warpgroups' MMAs reading it are done.
+// A model with more than three hidden layers runs in passes of at most three
+// weight-gradient layers (the delta chain is recomputed from the top in each).
+#include <cuda_bf16.h>
 
 #include "kernels.h"
+#include "tc.cuh"
 
 namespace wrf {
 
 namespace {
 
-// Rows per chunk: large chunks keep the launch count low and the weight-
-// gradient GEMMs (a reduction over the chunk's rows) long; the buffers take
-// ~8.2 KB per row of the chunk (1M rows: 8.6 GB of workspace).
-constexpr long long kChunk = 1 << 20;
+constexpr int kR = 64;                    // rows per tile
+constexpr int kWG = 2;                    // compute warpgroups
+constexpr int kThreads = kWG * 128 + 32;  // + producer warp
+constexpr int kRing = 5;                  // weight panel slots
+constexpr uint32_t kPanel = 128 * 128;    // W^T panel: 128 rows x 64 K x BF16
+constexpr uint32_t kDt = 128 * 128;       // D^T tile, one term: 128 units x 64 rows x BF16
+constexpr uint32_t kHt = 64 * 256;        // H tile, one term: 64 rows x 128 units x BF16
+constexpr uint32_t kGt = 64 * 128;        // gamma(mean) tile, one term: 64 rows x 64 features
+constexpr uint32_t kHAtom = 64 * 128;     // bytes per 64-unit swizzle atom of the H tile
+constexpr int kSlots = 3;                 // dW accumulators (hidden layers per pass)
+constexpr int kFlush = 8;                 // tile pairs between flushes of the accumulators
+constexpr int kGp = 8;                    // floats per staged d_resid row
+constexpr int kGammaF = 64;               // gamma(mean) features per row, zero-padded
+constexpr uint32_t kTmemCols = 512;       // 3 x 128 dW + 2 x 64 delta
+constexpr int kMaxGrid = 256;             // CTAs with partial-sum slots
 
-// Rows per chunk for a problem of Q x n rows.
-inline long long chunk_rows(int n, int Q) {
-    const long long rows = static_cast<long long>(Q) * n;
-    return rows < kChunk ? (rows > 0 ? rows : 1) : kChunk;
+constexpr size_t smem_bytes() {
+    return 1024 + kRing * kPanel + kWG * (2 * kDt + 2 * kHt) + kWG * kR * kGp * 4 +
+           8 * WRF_HIDDEN * 4 + (2 * kRing + 2 * kWG) * 8 + 16;
 }
-constexpr size_t kCublasWs = size_t(32) << 20;
+static_assert(smem_bytes() <= 227 * 1024, "shared memory of one CTA");
 
-inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+// Shared-memory descriptor with both byte offsets (MN-major operands: lbo =
+// stride between 64-element swizzle atoms along M/N, sbo = stride between
+// 8-row groups along K), 128-byte swizzle.
+__device__ __forceinline__ uint64_t sw128_desc_lbo(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+    d |= static_cast<uint64_t>(1) << 46;
+    d |= static_cast<uint64_t>(2) << 61;
+    return d;
+}
+// kind::f16 instruction descriptor with B read MN-major (A K-major).
+__host__ __device__ constexpr uint32_t idesc_bf16_bmn(int M, int N) {
+    return idesc_bf16(M, N) | (1u << 16);
+}
 
+// BF16 hi / lo of a pair (x0 in the low half).
+__device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
+    hi = pack_bf16(x0, x1);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xFFFF0000u);
+    lo = pack_bf16(__fsub_rn(x0, h0), __fsub_rn(x1, h1));
+}
+__device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(h)));
+    hi = *reinterpret_cast<const uint16_t *>(&h);
+    lo = *reinterpret_cast<const uint16_t *>(&l);
+}
 
-__global__ void gamma_tables_kernel(SceneView s, MlpView m, GridView g, const float *tx, int Q,
-                                    float *gam_m, float *gam_t) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < s.n) {
-        const float2 mu = reinterpret_cast<const float2 *>(s.mean)[i];
-        const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
-                            pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
-        pe_encode(x, 2, m.L_mean, gam_m + static_cast<size_t>(i) * m.dm);
-    } else if (i < s.n + Q) {
-        const int q = i - s.n;
-        PeArg x[3];
-        for (int c = 0; c < 3; ++c) x[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
-        pe_encode(x, 3, m.L_tx, gam_t + static_cast<size_t>(q) * m.dt);
+// Byte offset of (row r, unit u) in the H tile: two 64-unit atoms (kHAtom
+// apart), 8-row groups of 1024 bytes, 16-byte chunks XOR r % 8.
+__device__ __forceinline__ uint32_t ht_off(int r, int u) {
+    return static_cast<uint32_t>((u >> 6) * kHAtom + (r >> 3) * 1024 + (r & 7) * 128 +
+                                 ((((u & 63) >> 3) ^ (r & 7)) << 4) + (u & 7) * 2);
+}
+// Byte offset of (row m, column k < 64) in a K-major 128-byte-swizzled panel.
+__host__ __device__ inline uint32_t panel_off(int m, int k) {
+    return static_cast<uint32_t>((m >> 3) * 1024 + (m & 7) * 128 + ((((k >> 3) ^ (m & 7))) << 4) +
+                                 (k & 7) * 2);
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+        "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+        "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+        "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+struct BwdArgs {
+    int N, Qc, tpq, ntiles, npairs;
+    int nh;                 // hidden layers (W_1 .. W_nh)
+    int lo, hi;             // hidden layers whose dW this pass accumulates (none if hi < lo)
+    int dlo;                // lowest layer of the delta chain this pass (>= 1)
+    int first_pass, last_pass;
+    int dm;
+    const float *acts;      // [L-1][Qc N][128]; acts + (l-1) stride = H_l
+    long long act_stride;
+    const float *dres;      // [Qc N][5]
+    const float *Wo;        // [5][128]
+    const uint8_t *wimg;    // W^T panels [nh][4][kPanel]
+    const uint8_t *gimg;    // gamma(mean) tiles [2 terms][Npad / 64][kGt]
+    long long gterm;        // bytes per term image
+    float *pdw;             // [grid][kSlots][128][128]
+    float *pdb;             // [grid][kWG][8][128]  db of hidden layer l at [l]
+    float *pdwo;            // [grid][kWG][8][128]  rows 0..4 dW_out, row 5 db_out (lanes < 5)
+    float *pdw0;            // [grid][kWG][64][128] dW_0 gamma(mean) part, [feature][unit]
+    float *tilesum;         // [ntiles][128]
+    float *d0;              // [Qc N][128] or NULL
+    int *status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint8_t *ring = base;
+    uint8_t *tiles = ring + kRing * kPanel;                       // [kWG][Dt 2 terms, Ht 2 terms]
+    float *gstage = reinterpret_cast<float *>(tiles + kWG * (2 * kDt + 2 * kHt));  // [kWG][kR][kGp]
+    float *wo_s = gstage + kWG * kR * kGp;                        // [8][128]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(wo_s + 8 * WRF_HIDDEN);
+    uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing,
+             *gbar = bars + 2 * kRing + kWG;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kRing + 2 * kWG);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int i = 0; i < kRing; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kWG);
+        }
+        for (int i = 0; i < kWG; ++i) {
+            mbar_init(&accb[i], 1);
+            mbar_init(&gbar[i], 1);
+        }
+        fence_mbar_init();
+        *abort_flag = 0;
+    }
+    for (int i = tid; i < 8 * WRF_HIDDEN; i += blockDim.x)
+        wo_s[i] = i < WRF_OUT * WRF_HIDDEN ? a.Wo[i] : 0.f;
+    if (warp == 0) tmem_alloc(tmem_slot, kTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int rounds = blockIdx.x < a.npairs
+                           ? (a.npairs - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x
+                           : 0;
+    const bool have_dw = a.hi >= a.lo;
+
+    if (warp == kWG * 4) {
+        // ------------------------------------------------------ producer warp
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int r = 0; r < rounds && ok; ++r)
+                for (int l = a.nh; l >= a.dlo && ok; --l)
+                    for (int p = 0; p < 4; ++p) {
+                        const int slot = static_cast<int>(g % kRing);
+                        if (g >= kRing &&
+                            !wait_or_abort(&empty[slot], ((g / kRing) - 1) & 1u, abort_flag,
+                                           a.status)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&full[slot], kPanel);
+                        bulk_g2s(ring + slot * kPanel,
+                                 a.wimg + (static_cast<size_t>(l - 1) * 4 + p) * kPanel, kPanel,
+                                 &full[slot]);
+                        ++g;
+                    }
+            // copies still in flight land before the CTA exits (bounded waits)
+            for (uint32_t i = 0; i < kRing && i < g; ++i) {
+                const uint32_t gg = g - 1 - i;
+                mbar_wait(&full[gg % kRing], (gg / kRing) & 1u, a.status, kWaitLimitNs);
+            }
+        }
+    } else {
+        // ---------------------------------------------------- compute groups
+        const int wg = warp >> 2, wq = warp & 3;
+        const int u = tid & 127;  // hidden unit = TMEM lane
+        const bool leader = u == 0, mma_warp = u < 32;
+        uint8_t *Dt = tiles + wg * (2 * kDt + 2 * kHt);
+        uint8_t *Ht = Dt + 2 * kDt;
+        float *gs = gstage + wg * kR * kGp;
+        const uint32_t dt_a = smem_u32(Dt), ht_a = smem_u32(Ht), ring_a = smem_u32(ring);
+        const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;
+        const uint32_t t_dw = tmem_base;                                   // + 128 s
+        const uint32_t t_dl = tmem_base + 384u + static_cast<uint32_t>(64 * wg);
+        const uint32_t id_dw = idesc_bf16_bmn(128, 128), id_dl = idesc_bf16_bmn(128, 64);
+
+        // zero this warpgroup's half (64 columns) of every dW accumulator
+        auto zero_dw = [&]() {
+            uint32_t z[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) z[i] = 0u;
+            for (int s = 0; s < kSlots; ++s)
+                for (int c = 0; c < 2; ++c)
+                    tmem_st32(t_dw + lane_off + static_cast<uint32_t>(128 * s + 64 * wg + 32 * c), z);
+            tmem_wait_st();
+        };
+        // add this warpgroup's half of every dW accumulator of the pass into
+        // the CTA's FP32 partial, then zero it
+        auto flush_dw = [&]() {
+            float *pd = a.pdw + static_cast<size_t>(blockIdx.x) * kSlots * 128 * 128;
+            for (int s = 0; s <= a.hi - a.lo; ++s)
+                for (int c = 0; c < 2; ++c) {
+                    float v[32];
+                    tmem_ld32(t_dw + lane_off + static_cast<uint32_t>(128 * s + 64 * wg + 32 * c), v);
+                    float4 *dst = reinterpret_cast<float4 *>(
+                        pd + (static_cast<size_t>(s) * 128 + u) * 128 + 64 * wg + 32 * c);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        float4 o = dst[j];
+                        o.x += v[4 * j];
+                        o.y += v[4 * j + 1];
+                        o.z += v[4 * j + 2];
+                        o.w += v[4 * j + 3];
+                        dst[j] = o;
+                    }
+                }
+            zero_dw();
+        };
+        if (have_dw) zero_dw();
+        float wo[WRF_OUT];
+#pragma unroll
+        for (int o = 0; o < WRF_OUT; ++o) wo[o] = wo_s[o * WRF_HIDDEN + u];
+        float db_acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) db_acc[i] = 0.f;
+        float dwo[WRF_OUT] = {0.f, 0.f, 0.f, 0.f, 0.f}, dbo = 0.f;
+        uint32_t g = 0, phase = 0, gphase = 0;
+        tc_fence_before();
+        named_bar(1, kWG * 128);
+        tc_fence_after();
+
+        // this unit's column of an activation tile: h[r] = H[row0 + r][u]
+        auto load_col = [&](const float *H, long long row0, int nvalid, float *h) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r)
+                h[r] = r < nvalid ? __ldg(H + (row0 + r) * WRF_HIDDEN + u) : 0.f;
+        };
+        // D^T row u of the tile from 64 FP32 values: hi and lo terms
+        auto write_dt = [&](const float *d) {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                uint4 h4, l4;
+                split2(d[8 * c + 0], d[8 * c + 1], h4.x, l4.x);
+                split2(d[8 * c + 2], d[8 * c + 3], h4.y, l4.y);
+                split2(d[8 * c + 4], d[8 * c + 5], h4.z, l4.z);
+                split2(d[8 * c + 6], d[8 * c + 7], h4.w, l4.w);
+                const uint32_t off = static_cast<uint32_t>(u * 128 + ((c ^ (u & 7)) << 4));
+                *reinterpret_cast<uint4 *>(Dt + off) = h4;
+                *reinterpret_cast<uint4 *>(Dt + kDt + off) = l4;
+            }
+        };
+
+        for (int round = 0; round < rounds; ++round) {
+            if (wg_bar_any(1, *abort_flag != 0, kWG * 128)) break;
+            const int p = static_cast<int>(blockIdx.x) + round * static_cast<int>(gridDim.x);
+            const int tile = 2 * p + wg;
+            const bool tv = tile < a.ntiles;
+            const int q = tv ? tile / a.tpq : 0;
+            const int n0 = tv ? (tile % a.tpq) * kR : 0;
+            const int nvalid = tv ? min(kR, a.N - n0) : 0;
+            const long long row0 = static_cast<long long>(q) * a.N + n0;
+
+            // ---- output layer (K = 5) on the CUDA cores
+            for (int e = u; e < kR * WRF_OUT; e += 128) {
+                const int r = e / WRF_OUT, o = e % WRF_OUT;
+                gs[r * kGp + o] = r < nvalid ? __ldg(a.dres + (row0 + r) * WRF_OUT + o) : 0.f;
+            }
+            float h[kR], d[kR];
+            load_col(a.acts + static_cast<size_t>(a.nh) * a.act_stride, row0, nvalid, h);
+            named_bar(2 + wg, 128);
+            float dsum = 0.f;
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const float4 g0 = *reinterpret_cast<const float4 *>(gs + r * kGp);
+                const float g4 = gs[r * kGp + 4];
+                if (a.first_pass) {
+                    dwo[0] = fmaf(g0.x, h[r], dwo[0]);
+                    dwo[1] = fmaf(g0.y, h[r], dwo[1]);
+                    dwo[2] = fmaf(g0.z, h[r], dwo[2]);
+                    dwo[3] = fmaf(g0.w, h[r], dwo[3]);
+                    dwo[4] = fmaf(g4, h[r], dwo[4]);
+                }
+                float dv = g0.x * wo[0];
+                dv = fmaf(g0.y, wo[1], dv);
+                dv = fmaf(g0.z, wo[2], dv);
+                dv = fmaf(g0.w, wo[3], dv);
+                dv = fmaf(g4, wo[4], dv);
+                d[r] = h[r] > 0.f ? dv : 0.f;
+                dsum += d[r];
+            }
+            if (a.first_pass && u < WRF_OUT)
+                for (int r = 0; r < kR; ++r) dbo += gs[r * kGp + u];
+#pragma unroll
+            for (int i = 1; i < 8; ++i)
+                if (i == a.nh && i >= a.lo && i <= a.hi) db_acc[i] += dsum;
+            write_dt(d);
+
+            // ---- hidden layers l = nh .. dlo: delta chain and dW
+            for (int l = a.nh; l >= a.dlo; --l) {
+                load_col(a.acts + static_cast<size_t>(l - 1) * a.act_stride, row0, nvalid, h);
+                uint64_t mask = 0;
+#pragma unroll
+                for (int r = 0; r < kR; ++r)
+                    if (h[r] > 0.f) mask |= 1ull << r;
+                const bool dw_here = l >= a.lo && l <= a.hi;
+                if (dw_here) {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) {
+                        uint16_t hh, hl;
+                        split1(h[r], hh, hl);
+                        const uint32_t off = ht_off(r, u);
+                        *reinterpret_cast<uint16_t *>(Ht + off) = hh;
+                        *reinterpret_cast<uint16_t *>(Ht + kHt + off) = hl;
+                    }
+                }
+                fence_async_smem();
+                tc_fence_before();
+                named_bar(2 + wg, 128);
+                if (leader) {
+                    tc_fence_after();
+                    if (dw_here) {
+                        const uint32_t acc = t_dw + static_cast<uint32_t>(128 * (a.hi - l));
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ah = sw128_desc(dt_a + kk * 32u);
+                            const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
+                            const uint64_t bh = sw128_desc_lbo(ht_a + kk * 2048u, kHAtom, 1024u);
+                            const uint64_t bl = sw128_desc_lbo(ht_a + kHt + kk * 2048u, kHAtom, 1024u);
+                            mma_bf16(acc, ah, bh, id_dw, 1u);
+                            mma_bf16(acc, ah, bl, id_dw, 1u);
+                            mma_bf16(acc, al, bh, id_dw, 1u);
+                        }
+                    }
+                    // D_{l-1}^T = W_l^T D_l^T: panels (hi, K 0-63), (hi, K 64-127),
+                    // (lo, K 0-63), (lo, K 64-127)
+                    for (int pn = 0; pn < 4; ++pn, ++g) {
+                        const int slot = static_cast<int>(g % kRing);
+                        wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
+                        tc_fence_after();
+                        const uint32_t wa = ring_a + static_cast<uint32_t>(slot) * kPanel;
+#pragma unroll
+                        for (int k4 = 0; k4 < 4; ++k4) {
+                            const int kk = (pn & 1) * 4 + k4;
+                            const uint64_t aw = sw128_desc(wa + k4 * 32u);
+                            const uint64_t bh = sw128_desc_lbo(dt_a + kk * 2048u, kHAtom, 1024u);
+                            if (pn < 2) {
+                                const uint64_t bl =
+                                    sw128_desc_lbo(dt_a + kDt + kk * 2048u, kHAtom, 1024u);
+                                mma_bf16(t_dl, aw, bh, id_dl, (pn == 0 && k4 == 0) ? 0u : 1u);
+                                mma_bf16(t_dl, aw, bl, id_dl, 1u);
+                            } else {
+                                mma_bf16(t_dl, aw, bh, id_dl, 1u);
+                            }
+                        }
+                        mma_commit(&empty[slot]);
+                    }
+                    mma_commit(&accb[wg]);
+                }
+                if (mma_warp) __syncwarp();
+                wait_or_abort(&accb[wg], phase, abort_flag, a.status);
+                phase ^= 1u;
+                tc_fence_after();
+                // epilogue: D_{l-1}^T row u = mask * (W_l^T D_l^T) row u
+                tmem_ld64(t_dl + lane_off, d);
+                dsum = 0.f;
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    d[r] = ((mask >> r) & 1ull) ? d[r] : 0.f;
+                    dsum += d[r];
+                }
+#pragma unroll
+                for (int i = 1; i < 8; ++i)
+                    if (i == l - 1 && i >= a.lo && i <= a.hi) db_acc[i] += dsum;
+                if (l - 1 >= a.dlo || a.last_pass) write_dt(d);
+                tc_fence_before();
+            }
+
+            // ---- layer 0: the gamma(mean) part of dW_0 and per-tile sums of D_0
+            if (a.last_pass) {
+                if (tv) a.tilesum[static_cast<size_t>(tile) * WRF_HIDDEN + u] = dsum;
+                if (a.d0) {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r)
+                        if (r < nvalid) a.d0[(row0 + r) * WRF_HIDDEN + u] = d[r];
+                }
+                if (leader) {
+                    // the gamma(mean) rows of the tile replace the H tile (the
+                    // MMAs that read it have completed)
+                    const size_t t0 = static_cast<size_t>(tv ? n0 / kR : 0) * kGt;
+                    mbar_arrive_expect_tx(&gbar[wg], 2 * kGt);
+                    bulk_g2s(Ht, a.gimg + t0, kGt, &gbar[wg]);
+                    bulk_g2s(Ht + kGt, a.gimg + a.gterm + t0, kGt, &gbar[wg]);
+                }
+                fence_async_smem();
+                tc_fence_before();
+                named_bar(2 + wg, 128);
+                if (leader) {
+                    wait_or_abort(&gbar[wg], gphase, abort_flag, a.status);
+                    tc_fence_after();
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ah = sw128_desc(dt_a + kk * 32u);
+                        const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
+                        const uint64_t bh = sw128_desc_lbo(ht_a + kk * 2048u, kHAtom, 1024u);
+                        const uint64_t bl = sw128_desc_lbo(ht_a + kGt + kk * 2048u, kHAtom, 1024u);
+                        mma_bf16(t_dl, ah, bh, id_dl, kk == 0 ? 0u : 1u);
+                        mma_bf16(t_dl, ah, bl, id_dl, 1u);
+                        mma_bf16(t_dl, al, bh, id_dl, 1u);
+                    }
+                    mma_commit(&accb[wg]);
+                }
+                gphase ^= 1u;
+                if (mma_warp) __syncwarp();
+                wait_or_abort(&accb[wg], phase, abort_flag, a.status);
+                phase ^= 1u;
+                tc_fence_after();
+                tmem_ld64(t_dl + lane_off, d);
+                tc_fence_before();
+                if (!*abort_flag) {
+                    float *pw = a.pdw0 + (static_cast<size_t>(blockIdx.x) * kWG + wg) * kGammaF * 128;
+#pragma unroll
+                    for (int f = 0; f < kGammaF; ++f)
+                        if (f < a.dm) pw[f * 128 + u] += d[f];
+                }
+            }
+            named_bar(2 + wg, 128);  // tiles and TMEM columns are free for the next round
+            if (have_dw && ((round + 1) % kFlush == 0 || round + 1 == rounds)) {
+                named_bar(1, kWG * 128);  // every MMA into the dW accumulators is complete
+                tc_fence_after();
+                if (!*abort_flag) flush_dw();
+                tc_fence_before();
+                named_bar(1, kWG * 128);
+                tc_fence_after();
+            }
+        }
+        // per-thread sums of this warpgroup
+        if (!*abort_flag) {
+            const size_t cw = static_cast<size_t>(blockIdx.x) * kWG + wg;
+#pragma unroll
+            for (int l = 1; l < 8; ++l)
+                if (l >= a.lo && l <= a.hi) a.pdb[(cw * 8 + l) * 128 + u] += db_acc[l];
+            if (a.first_pass) {
+                for (int o = 0; o < WRF_OUT; ++o) a.pdwo[(cw * 8 + o) * 128 + u] += dwo[o];
+                if (u < WRF_OUT) a.pdwo[(cw * 8 + 5) * 128 + u] += dbo;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTmemCols);
     }
 }
 
-// H0[r] = [gamma(mean_n), gamma(tx_q)], H1[r] = ReLU(U[n] + V[q]) for the
-// chunk's rows (row = row0 + r, q = row / N, n = row % N).
-__global__ void features_kernel(int N, long long row0, int nrows, int dm, int dt,
-                                const float *gam_m, const float *gam_t, const float *U,
-                                const float *V, float *H0, float *H1) {
-    const int din = dm + dt;
-    const int ncol = din + (H1 ? WRF_HIDDEN : 0);  // H1 is NULL when saved by the forward
-    const long long total = static_cast<long long>(nrows) * ncol;
+// ------------------------------------------------------------ preparation
+// Jobs in one launch: [0, nb_w) W^T panels of the hidden layers (element
+// grid-stride), then one thread per gamma(mean) row (BF16 hi and lo images,
+// pre-swizzled for the MN-major B operand: 8-row groups of 1024 bytes,
+// 16-byte chunks XOR row % 8), then one thread per query for gamma(tx) in FP32.
+__global__ void __launch_bounds__(128) bwd_prep_kernel(SceneView s, MlpView m, GridView g,
+                                                       const float *tx, int Q, int nb_w,
+                                                       int nb_g, uint8_t *wimg, uint8_t *gimg,
+                                                       long long gterm, int npad, float *gam_t) {
+    int b = blockIdx.x;
+    if (b < nb_w) {
+        const long long total = static_cast<long long>(m.n_layers - 2) * 4 * 128 * 64;
+        for (long long i = b * 128LL + threadIdx.x; i < total; i += 128LL * nb_w) {
+            const int l = static_cast<int>(i / (4 * 128 * 64));  // hidden layer l+1
+            const int pn = static_cast<int>((i / (128 * 64)) % 4);
+            const int mrow = static_cast<int>((i / 64) % 128), k = static_cast<int>(i % 64);
+            const int o = (pn & 1) * 64 + k;  // W[o][mrow] at (row mrow, K o)
+            const float w = m.Wh[l][o * WRF_HIDDEN + mrow];
+            uint16_t hi, lo;
+            split1(w, hi, lo);
+            *reinterpret_cast<uint16_t *>(wimg + (static_cast<size_t>(l) * 4 + pn) * kPanel +
+                                          panel_off(mrow, k)) = (pn < 2) ? hi : lo;
+        }
+        return;
+    }
+    b -= nb_w;
+    if (b < nb_g) {
+        const int n = b * 128 + threadIdx.x;
+        if (n >= npad) return;
+        float gam[kGammaF];
+#pragma unroll
+        for (int f = 0; f < kGammaF; ++f) gam[f] = 0.f;
+        if (n < s.n) {
+            const float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
+            const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
+                                pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
+            pe_encode(x, 2, m.L_mean, gam);
+        }
+        const size_t tbase = static_cast<size_t>(n >> 6) * kGt;
+        const int r = n & 63;
+        for (int c = 0; c < kGammaF / 8; ++c) {
+            uint4 h4, l4;
+            split2(gam[8 * c + 0], gam[8 * c + 1], h4.x, l4.x);
+            split2(gam[8 * c + 2], gam[8 * c + 3], h4.y, l4.y);
+            split2(gam[8 * c + 4], gam[8 * c + 5], h4.z, l4.z);
+            split2(gam[8 * c + 6], gam[8 * c + 7], h4.w, l4.w);
+            const size_t off =
+                tbase + static_cast<size_t>((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
+            *reinterpret_cast<uint4 *>(gimg + off) = h4;
+            *reinterpret_cast<uint4 *>(gimg + gterm + off) = l4;
+        }
+        return;
+    }
+    b -= nb_g;
+    const int q = b * 128 + threadIdx.x;
+    if (q >= Q) return;
+    PeArg x[3];
+    for (int c = 0; c < 3; ++c) x[c] = pe_arg(tx[3 * q + c], m.room_min[c], m.room_size[c]);
+    pe_encode(x, 3, m.L_tx, gam_t + static_cast<size_t>(q) * m.dt);
+}
+
+// ------------------------------------------------------------ reductions
+// The caller's gradient arrays, by value (device pointers).
+struct GradPtrs {
+    float *dW[WRF_MAX_LAYERS];
+    float *db[WRF_MAX_LAYERS];
+};
+
+// Partials of all CTAs into the caller's gradients, in a fixed order (one
+// thread per output element): hidden dW and db of the pass, the output layer
+// (first pass) and the gamma(mean) part of dW_0 (last pass).
+__global__ void bwd_reduce_kernel(MlpView m, int grid, int lo, int hi, int first, int last,
+                                  const float *pdw, const float *pdb, const float *pdwo,
+                                  const float *pdw0, GradPtrs gp) {
+    float *const *dW = gp.dW;
+    float *const *db = gp.db;
+    const int nslot = hi >= lo ? hi - lo + 1 : 0;
+    const long long n_dw = static_cast<long long>(nslot) * 128 * 128;
+    const long long n_db = static_cast<long long>(nslot) * 128;
+    const long long n_o = first ? 6 * 128 : 0;
+    const long long n_0 = last ? static_cast<long long>(m.dm) * 128 : 0;
+    const long long total = n_dw + n_db + n_o + n_0;
+    const int din = m.dm + m.dt;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
-        const long long r = e / ncol;
-        const int c = static_cast<int>(e % ncol);
-        const long long row = row0 + r;
-        const int q = static_cast<int>(row / N), n = static_cast<int>(row % N);
-        if (c < din) {
-            H0[r * din + c] = c < dm ? gam_m[static_cast<size_t>(n) * dm + c]
-                                     : gam_t[static_cast<size_t>(q) * dt + (c - dm)];
-        } else {
-            const int j = c - din;
-            H1[r * WRF_HIDDEN + j] = fmaxf(U[static_cast<size_t>(n) * WRF_HIDDEN + j] +
-                                               V[static_cast<size_t>(q) * WRF_HIDDEN + j],
-                                           0.f);
+        if (e < n_dw) {
+            const int s = static_cast<int>(e / (128 * 128));
+            const int oi = static_cast<int>(e % (128 * 128));
+            float acc = 0.f;
+            for (int c = 0; c < grid; ++c) acc += pdw[(static_cast<size_t>(c) * kSlots + s) * 128 * 128 + oi];
+            dW[hi - s][oi] += acc;  // W_l is [128 out][128 in]
+            continue;
+        }
+        long long f = e - n_dw;
+        if (f < n_db) {
+            const int l = lo + static_cast<int>(f / 128), uu = static_cast<int>(f % 128);
+            float acc = 0.f;
+            for (int c = 0; c < grid * kWG; ++c) acc += pdb[(static_cast<size_t>(c) * 8 + l) * 128 + uu];
+            db[l][uu] += acc;
+            continue;
+        }
+        f -= n_db;
+        if (f < n_o) {
+            const int o = static_cast<int>(f / 128), uu = static_cast<int>(f % 128);
+            if (o == 5 && uu >= WRF_OUT) continue;
+            float acc = 0.f;
+            for (int c = 0; c < grid * kWG; ++c) acc += pdwo[(static_cast<size_t>(c) * 8 + o) * 128 + uu];
+            const int L = m.n_layers;
+            if (o < WRF_OUT)
+                dW[L - 1][o * WRF_HIDDEN + uu] += acc;
+            else
+                db[L - 1][uu] += acc;
+            continue;
+        }
+        f -= n_o;
+        {
+            const int ft = static_cast<int>(f / 128), uu = static_cast<int>(f % 128);
+            float acc = 0.f;
+            for (int c = 0; c < grid * kWG; ++c)
+                acc += pdw0[(static_cast<size_t>(c) * kGammaF + ft) * 128 + uu];
+            dW[0][static_cast<size_t>(uu) * din + ft] += acc;
         }
     }
 }
 
-// Z = ReLU(Z + b) in place, Z [nrows][128].
-__global__ void bias_relu_kernel(float *Z, const float *b, long long n) {
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<long long>(gridDim.x) * blockDim.x)
-        Z[e] = fmaxf(Z[e] + b[e & (WRF_HIDDEN - 1)], 0.f);
+// Per-query sums of D_0 over the query's tiles: colsum[q][u] (fixed order).
+__global__ void bwd_colsum_kernel(const float *tilesum, int Qc, int tpq, float *colsum) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= Qc * 128) return;
+    const int q = i / 128, uu = i % 128;
+    float acc = 0.f;
+    for (int t = 0; t < tpq; ++t) acc += tilesum[(static_cast<size_t>(q) * tpq + t) * 128 + uu];
+    colsum[i] = acc;
 }
 
-// D = D * [H > 0] in place.
-__global__ void relu_mask_kernel(float *D, const float *H, long long n) {
-    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
-         e += static_cast<long long>(gridDim.x) * blockDim.x)
-        if (!(H[e] > 0.f)) D[e] = 0.f;
+// The gamma(tx) part of dW_0 (rank one per query) and db_0:
+// dW_0[u][dm + f] += sum_q colsum[q][u] gamma(tx_q)[f];  db_0[u] += sum_q colsum[q][u].
+__global__ void bwd_tx_part_kernel(MlpView m, int Qc, const float *colsum, const float *gam_t,
+                                   float *dW0, float *db0) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int din = m.dm + m.dt;
+    if (i >= 128 * (m.dt + 1)) return;
+    const int uu = i % 128, f = i / 128;
+    float acc = 0.f;
+    if (f < m.dt) {
+        for (int q = 0; q < Qc; ++q)
+            acc = fmaf(colsum[q * 128 + uu], gam_t[static_cast<size_t>(q) * m.dt + f], acc);
+        dW0[static_cast<size_t>(uu) * din + m.dm + f] += acc;
+    } else {
+        for (int q = 0; q < Qc; ++q) acc += colsum[q * 128 + uu];
+        db0[uu] += acc;
+    }
 }
 
-// db[j] += sum_r D[r][j] for D [nrows][width]: each block sums a slice of
-// rows per column, one atomic add per (block, column).
-__global__ void colsum_kernel(const float *D, int nrows, int width, float *db) {
-    const int j = threadIdx.x;
-    if (j >= width) return;
-    const int rows_per = (nrows + gridDim.x - 1) / gridDim.x;
-    const int r0 = blockIdx.x * rows_per, r1 = min(nrows, r0 + rows_per);
-    float s = 0.f;
-    for (int r = r0; r < r1; ++r) s += D[static_cast<size_t>(r) * width + j];
-    if (r1 > r0) atomicAdd(db + j, s);
-}
-
-// d_mean[n] += dgamma(mean_n) . d gamma / d (mean / (W, H)) / (W, H).
-__global__ void dmean_kernel(SceneView s, MlpView m, GridView g, int N, long long row0, int nrows,
-                             const float *dgm, float *d_mean) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= nrows) return;
-    const long long row = row0 + r;
-    const int n = static_cast<int>(row % N);
+// d_mean[n] += dgamma(mean_n) . d gamma / d (mean / (W, H)) / (W, H), with
+// dgamma(mean) = D_0 W_0[:, :dm] for every row of the chunk (FP32, one thread
+// per row; W_0's gamma(mean) columns staged in shared memory).
+__global__ void __launch_bounds__(128) bwd_dmean_kernel(SceneView s, MlpView m, GridView g,
+                                                        int N, long long rows, const float *d0,
+                                                        float *d_mean) {
+    __shared__ float w0m[62 * WRF_HIDDEN];  // [feature][unit]
+    const int din = m.dm + m.dt;
+    for (int i = threadIdx.x; i < m.dm * WRF_HIDDEN; i += blockDim.x) {
+        const int f = i / WRF_HIDDEN, j = i % WRF_HIDDEN;
+        w0m[i] = m.W0[static_cast<size_t>(j) * din + f];
+    }
+    __syncthreads();
+    const long long r = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    if (r >= rows) return;
+    const int n = static_cast<int>(r % N);
+    float dg[62];
+    for (int f = 0; f < m.dm; ++f) dg[f] = 0.f;
+    const float4 *row = reinterpret_cast<const float4 *>(d0 + r * WRF_HIDDEN);
+    for (int j4 = 0; j4 < WRF_HIDDEN / 4; ++j4) {
+        const float4 v = row[j4];
+        for (int f = 0; f < m.dm; ++f) {
+            const float *w = w0m + f * WRF_HIDDEN + 4 * j4;
+            dg[f] = fmaf(v.x, w[0], fmaf(v.y, w[1], fmaf(v.z, w[2], fmaf(v.w, w[3], dg[f]))));
+        }
+    }
     const float2 mu = reinterpret_cast<const float2 *>(s.mean)[n];
     const PeArg x[2] = {pe_arg(mu.x, 0.f, static_cast<float>(g.W)),
                         pe_arg(mu.y, 0.f, static_cast<float>(g.H))};
@@ -126,48 +695,38 @@ __global__ void dmean_kernel(SceneView s, MlpView m, GridView g, int N, long lon
     float gx[2] = {0.f, 0.f};
     for (int f = 0; f < m.dm; ++f) {
         const int i = f % 2, grp = f / 2;
-        float dg = 1.f;
+        float dgv = 1.f;
         if (grp >= 1) {
             const int k = (grp - 1) % Lm;
             float sn, cs;
             pe_band(x[i], k, sn, cs);
             const float w = ldexpf(3.14159265358979f, k);
-            dg = grp <= Lm ? w * cs : -w * sn;
+            dgv = grp <= Lm ? w * cs : -w * sn;
         }
-        gx[i] = fmaf(dgm[static_cast<size_t>(r) * m.dm + f], dg, gx[i]);
+        gx[i] = fmaf(dg[f], dgv, gx[i]);
     }
     atomicAdd(d_mean + 2 * n, gx[0] / static_cast<float>(g.W));
     atomicAdd(d_mean + 2 * n + 1, gx[1] / static_cast<float>(g.H));
 }
 
-int grid_for(long long n) {
-    long long b = (n + 255) / 256;
-    return static_cast<int>(b > 148 * 16 ? 148 * 16 : (b < 1 ? 1 : b));
+inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Queries per launch: everything when the forward saved its activations and
+// positions are stop-gradded; otherwise chunks whose recomputed activations
+// and D_0 rows fit in about 1 GiB.
+constexpr size_t kChunkBudget = size_t(1) << 30;
+inline int chunk_queries(int n, int Q, int n_layers) {
+    const size_t per_q = static_cast<size_t>(n > 0 ? n : 1) * WRF_HIDDEN * 4 * n_layers;
+    size_t qc = kChunkBudget / per_q;
+    if (qc < 1) qc = 1;
+    return static_cast<int>(qc < static_cast<size_t>(Q) ? qc : Q);
 }
 
-// One cuBLAS handle per device, created on first use.
-cublasHandle_t handle_for_device() {
-    static cublasHandle_t handles[64] = {nullptr};
-    static std::mutex mu;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!handles[dev]) {
-        cublasHandle_t h = nullptr;
-        if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-        handles[dev] = h;
-    }
-    return handles[dev];
-}
-
-// C^T (m x n) = opA(A) (m x k) * opB(B) (k x n) in cuBLAS column-major terms
-// (a row-major [rows][width] matrix is a column-major [width][rows] one).
-cublasStatus_t gemm(cublasHandle_t h, cublasOperation_t ta, cublasOperation_t tb, int m, int n,
-                    int k, const float *A, int lda, const float *B, int ldb, float beta, float *C,
-                    int ldc) {
-    const float alpha = 1.f;
-    return cublasGemmEx(h, ta, tb, m, n, k, &alpha, A, CUDA_R_32F, lda, B, CUDA_R_32F, ldb, &beta, C,
-                        CUDA_R_32F, ldc, CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+inline int grid_size() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
 }
 
 }  // namespace
@@ -178,21 +737,31 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
     auto take = [&](size_t bytes) {
         char *p = base ? base + off : nullptr;
         off = align256(off + bytes);
-        return reinterpret_cast<float *>(p);
+        return p;
     };
     DeformBwdWs w{};
-    const int din = m.dm + m.dt;
-    const int L = m.n_layers;
-    const size_t C = static_cast<size_t>(chunk_rows(n, Q));
-    w.cb_H0 = take(C * din * 4);
-    for (int l = 0; l < L - 1; ++l) w.cb_Hh[l] = take(C * WRF_HIDDEN * 4);
-    for (int l = 0; l < L - 1; ++l) w.cb_G[l] = take(C * WRF_HIDDEN * 4);
-    w.cb_G[L - 1] = nullptr;  // the output layer's delta is d_resid itself
-    w.dgm = take(C * m.dm * 4);
-    w.gam_m = take(static_cast<size_t>(n) * m.dm * 4);
-    w.gam_t = take(static_cast<size_t>(Q) * m.dt * 4);
-    w.cublas_ws = reinterpret_cast<char *>(take(kCublasWs));
-    w.cublas_ws_bytes = kCublasWs;
+    const int nh = m.n_layers - 2 > 0 ? m.n_layers - 2 : 0;
+    const int qc = chunk_queries(n, Q > 0 ? Q : 1, m.n_layers);
+    const int npad = ((n > 0 ? n : 1) + kR - 1) / kR * kR;
+    const size_t grid = kMaxGrid;
+    w.wimg = take(static_cast<size_t>(nh > 0 ? nh : 1) * 4 * kPanel);
+    w.gterm = static_cast<long long>(npad) * 128;
+    w.gimg = take(2 * static_cast<size_t>(w.gterm));
+    w.gam_t = reinterpret_cast<float *>(take(static_cast<size_t>(Q > 0 ? Q : 1) * m.dt * 4));
+    w.pdw = reinterpret_cast<float *>(take(grid * kSlots * 128 * 128 * 4));
+    w.pdb = reinterpret_cast<float *>(take(grid * kWG * 8 * 128 * 4));
+    w.pdwo = reinterpret_cast<float *>(take(grid * kWG * 8 * 128 * 4));
+    w.pdw0 = reinterpret_cast<float *>(take(grid * kWG * kGammaF * 128 * 4));
+    const size_t tpq = static_cast<size_t>(npad / kR);
+    const size_t qall = static_cast<size_t>(Q > 0 ? Q : 1);
+    w.tilesum = reinterpret_cast<float *>(take(qall * tpq * 128 * 4));
+    w.colsum = reinterpret_cast<float *>(take(qall * 128 * 4));
+    const size_t chunk_rows = static_cast<size_t>(qc) * (n > 0 ? n : 1);
+    w.acts = reinterpret_cast<float *>(
+        take(static_cast<size_t>(m.n_layers - 1) * chunk_rows * WRF_HIDDEN * 4));
+    w.resid = reinterpret_cast<float *>(take(chunk_rows * WRF_OUT * 4));
+    w.d0 = reinterpret_cast<float *>(take(chunk_rows * WRF_HIDDEN * 4));
+    w.qc = qc;
     if (bw) *bw = w;
     return off;
 }
@@ -200,7 +769,8 @@ size_t deform_bwd_ws_layout(int n, int Q, const MlpView &m, DeformWs *fw, Deform
 cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView &g,
                            const float *tx, int Q, const DeformWs &fw, const DeformBwdWs &bw,
                            const float *d_resid, const float *acts, float *const *dW,
-                           float *const *db, float *d_mean, int stop_grad_mean, cudaStream_t st) {
+                           float *const *db, float *d_mean, int stop_grad_mean, int *status,
+                           cudaStream_t st) {
     const int L = m.n_layers, nh = L - 2;
     const int din = m.dm + m.dt;
     for (int l = 0; l < L; ++l) {
@@ -212,69 +782,101 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
     }
     const long long rows = static_cast<long long>(Q) * s.n;
     if (rows == 0) return cudaGetLastError();
-    cublasHandle_t h = handle_for_device();
-    if (!h) return cudaErrorUnknown;
-    if (cublasSetStream(h, st) != CUBLAS_STATUS_SUCCESS ||
-        cublasSetWorkspace(h, bw.cublas_ws, bw.cublas_ws_bytes) != CUBLAS_STATUS_SUCCESS)
-        return cudaErrorUnknown;
-    gamma_tables_kernel<<<static_cast<int>((s.n + Q + 127) / 128), 128, 0, st>>>(
-        s, m, g, tx, Q, bw.gam_m, bw.gam_t);
-    const cublasOperation_t N_ = CUBLAS_OP_N, T_ = CUBLAS_OP_T;
-    const long long CH = chunk_rows(s.n, Q);
-    for (long long r0 = 0; r0 < rows; r0 += CH) {
-        const int R = static_cast<int>(rows - r0 < CH ? rows - r0 : CH);
-        const long long nH = static_cast<long long>(R) * WRF_HIDDEN;
-        // hidden activations of this chunk: saved by the forward, or recomputed
-        const float *Hh[8];
-        for (int l = 0; l <= nh; ++l)
-            Hh[l] = acts ? acts + (static_cast<size_t>(l) * rows + r0) * WRF_HIDDEN : bw.cb_Hh[l];
-        features_kernel<<<grid_for(static_cast<long long>(R) * (din + (acts ? 0 : WRF_HIDDEN))),
-                          256, 0, st>>>(s.n, r0, R, m.dm, m.dt, bw.gam_m, bw.gam_t, fw.U, fw.V,
-                                        bw.cb_H0, acts ? nullptr : bw.cb_Hh[0]);
-        // forward recompute of the hidden layers: H_{l+1} = ReLU(H_l Wh[l]^T + bh[l])
-        for (int l = 0; l < nh && !acts; ++l) {
-            if (gemm(h, T_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, bw.cb_Hh[l],
-                     WRF_HIDDEN, 0.f, bw.cb_Hh[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
-            bias_relu_kernel<<<grid_for(nH), 256, 0, st>>>(bw.cb_Hh[l + 1], m.bh[l], nH);
+    if (m.dm > kGammaF || m.dm > 62) return cudaErrorInvalidValue;
+    const int N = s.n;
+    const int npad = (N + kR - 1) / kR * kR;
+    {
+        const int nb_w = nh > 0 ? 256 : 0;
+        const int nb_g = (npad + 127) / 128;
+        const int nb_t = (Q + 127) / 128;
+        bwd_prep_kernel<<<nb_w + nb_g + nb_t, 128, 0, st>>>(
+            s, m, g, tx, Q, nb_w, nb_g, reinterpret_cast<uint8_t *>(bw.wimg),
+            reinterpret_cast<uint8_t *>(bw.gimg), bw.gterm, npad, bw.gam_t);
+    }
+    cudaError_t e = cudaFuncSetAttribute(mlp_bwd_tc_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem_bytes()));
+    if (e != cudaSuccess) return e;
+    int sms = grid_size();
+    if (sms > kMaxGrid) sms = kMaxGrid;
+    GradPtrs gp{};
+    for (int l = 0; l < L; ++l) {
+        gp.dW[l] = dW[l];
+        gp.db[l] = db[l];
+    }
+    const int tpq = npad / kR;
+    // passes of at most kSlots weight-gradient layers, from the top
+    int npass = nh > 0 ? (nh + kSlots - 1) / kSlots : 1;
+    // queries per launch
+    const bool need_chunks = !acts || !stop_grad_mean;
+    const int qc = need_chunks ? bw.qc : Q;
+    const size_t pdw_bytes = static_cast<size_t>(kMaxGrid) * kSlots * 128 * 128 * 4;
+    const size_t small_bytes = static_cast<size_t>(kMaxGrid) * kWG * 8 * 128 * 4;
+    const size_t pdw0_bytes = static_cast<size_t>(kMaxGrid) * kWG * kGammaF * 128 * 4;
+    for (int q0 = 0; q0 < Q; q0 += qc) {
+        const int Qc = Q - q0 < qc ? Q - q0 : qc;
+        const long long crows = static_cast<long long>(Qc) * N;
+        const float *cacts = acts ? acts + static_cast<size_t>(q0) * N * WRF_HIDDEN : bw.acts;
+        const long long astride = acts ? rows * WRF_HIDDEN : crows * WRF_HIDDEN;
+        if (!acts) {
+            // recompute this chunk's hidden activations with the FP32 forward
+            DeformWs cw = fw;
+            cw.V = fw.V + static_cast<size_t>(q0) * WRF_HIDDEN;
+            e = launch_mlp_f32(s, m, g, Qc, cw, 0, bw.resid, nullptr, nullptr, bw.acts, st);
+            if (e != cudaSuccess) return e;
         }
-        const float *Gout = d_resid + r0 * WRF_OUT;
-        // delta of the last hidden layer: (G_out W_out) * [H_last > 0]
-        float *Dl = bw.cb_G[nh];
-        if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_OUT, m.Wo, WRF_HIDDEN, Gout, WRF_OUT, 0.f, Dl,
-                 WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
-            return cudaErrorUnknown;
-        relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dl, Hh[nh], nH);
-        // output layer gradients: dWo += G_out^T H_last, dbo += colsum(G_out)
-        if (gemm(h, N_, T_, WRF_HIDDEN, WRF_OUT, R, Hh[nh], WRF_HIDDEN, Gout, WRF_OUT, 1.f,
-                 dW[L - 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
-            return cudaErrorUnknown;
-        colsum_kernel<<<296, 32, 0, st>>>(Gout, R, WRF_OUT, db[L - 1]);
-        // hidden layers backwards: layer l+1 (Wh[l]) maps H_l -> Z_{l+1}
-        for (int l = nh - 1; l >= 0; --l) {
-            float *D = bw.cb_G[l + 1];  // delta of Z_{l+1}
-            if (gemm(h, N_, T_, WRF_HIDDEN, WRF_HIDDEN, R, Hh[l], WRF_HIDDEN, D, WRF_HIDDEN,
-                     1.f, dW[l + 1], WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
-            colsum_kernel<<<296, 128, 0, st>>>(D, R, WRF_HIDDEN, db[l + 1]);
-            float *Dp = bw.cb_G[l];  // delta of Z_l = (D Wh[l]) * [H_l > 0]
-            if (gemm(h, N_, N_, WRF_HIDDEN, R, WRF_HIDDEN, m.Wh[l], WRF_HIDDEN, D, WRF_HIDDEN, 0.f,
-                     Dp, WRF_HIDDEN) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
-            relu_mask_kernel<<<grid_for(nH), 256, 0, st>>>(Dp, Hh[l], nH);
+        const int ntiles = Qc * tpq;
+        const int npairs = (ntiles + 1) / 2;
+        const int grid = npairs < sms ? npairs : sms;
+        for (int pass = 0; pass < npass; ++pass) {
+            BwdArgs a{};
+            a.N = N;
+            a.Qc = Qc;
+            a.tpq = tpq;
+            a.ntiles = ntiles;
+            a.npairs = npairs;
+            a.nh = nh;
+            a.hi = nh - pass * kSlots;
+            a.lo = a.hi - kSlots + 1 > 1 ? a.hi - kSlots + 1 : 1;
+            if (nh == 0) {
+                a.hi = 0;
+                a.lo = 1;
+            }
+            a.first_pass = pass == 0;
+            a.last_pass = pass == npass - 1;
+            a.dlo = a.last_pass ? 1 : a.lo;
+            a.dm = m.dm;
+            a.acts = cacts;
+            a.act_stride = astride;
+            a.dres = d_resid + static_cast<size_t>(q0) * N * WRF_OUT;
+            a.Wo = m.Wo;
+            a.wimg = reinterpret_cast<const uint8_t *>(bw.wimg);
+            a.gimg = reinterpret_cast<const uint8_t *>(bw.gimg);
+            a.gterm = bw.gterm;
+            a.pdw = bw.pdw;
+            a.pdb = bw.pdb;
+            a.pdwo = bw.pdwo;
+            a.pdw0 = bw.pdw0;
+            a.tilesum = bw.tilesum;
+            a.d0 = (!stop_grad_mean && a.last_pass) ? bw.d0 : nullptr;
+            a.status = status;
+            if ((e = cudaMemsetAsync(bw.pdw, 0, pdw_bytes, st)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(bw.pdb, 0, small_bytes, st)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(bw.pdwo, 0, small_bytes, st)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(bw.pdw0, 0, pdw0_bytes, st)) != cudaSuccess) return e;
+            mlp_bwd_tc_kernel<<<grid, kThreads, smem_bytes(), st>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            bwd_reduce_kernel<<<256, 256, 0, st>>>(m, grid, a.lo, a.hi, a.first_pass, a.last_pass,
+                                                   bw.pdw, bw.pdb, bw.pdwo, bw.pdw0, gp);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        // first layer: dW0 += D_0^T H0, db0 += colsum(D_0)
-        if (gemm(h, N_, T_, din, WRF_HIDDEN, R, bw.cb_H0, din, bw.cb_G[0], WRF_HIDDEN, 1.f, dW[0],
-                 din) != CUBLAS_STATUS_SUCCESS)
-            return cudaErrorUnknown;
-        colsum_kernel<<<296, 128, 0, st>>>(bw.cb_G[0], R, WRF_HIDDEN, db[0]);
-        if (!stop_grad_mean) {
-            // dgamma(mean) [R][dm] = D_0 W0[:, :dm]
-            if (gemm(h, N_, N_, m.dm, R, WRF_HIDDEN, m.W0, din, bw.cb_G[0], WRF_HIDDEN, 0.f,
-                     bw.dgm, m.dm) != CUBLAS_STATUS_SUCCESS)
-                return cudaErrorUnknown;
-            dmean_kernel<<<(R + 127) / 128, 128, 0, st>>>(s, m, g, s.n, r0, R, bw.dgm, d_mean);
-        }
+        bwd_colsum_kernel<<<(Qc * 128 + 255) / 256, 256, 0, st>>>(bw.tilesum, Qc, tpq, bw.colsum);
+        bwd_tx_part_kernel<<<(128 * (m.dt + 1) + 255) / 256, 256, 0, st>>>(
+            m, Qc, bw.colsum, bw.gam_t + static_cast<size_t>(q0) * m.dt, dW[0], db[0]);
+        if (!stop_grad_mean)
+            bwd_dmean_kernel<<<static_cast<unsigned>((crows + 127) / 128), 128, 0, st>>>(
+                s, m, g, N, crows, bw.d0, d_mean);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }

@@ -35,18 +35,21 @@ def spectrum_error(gpu, ref, slack, rel_tol):
 
 
 
-def grad_error(gpu, ref, rel=1e-3, floor=1e-3):
+def grad_error(gpu, ref, rel=1e-3, floor=1e-3, slack=None):
     """Element-wise gradient check of one parameter group:
-    |g - g_ref| <= rel * |g_ref| + floor * max|g_ref| for every element (the
-    floor keeps the bound defined where a component is ~0).  Returns (ok,
-    worst ratio |g - g_ref| / bound (<= 1 passes), flat index of the worst
-    element, its GPU value, its oracle value)."""
+    |g - g_ref| <= rel * |g_ref| + floor * max|g_ref| (+ slack) for every
+    element (the floor keeps the bound defined where a component is ~0; the
+    oracle's slack covers ReLU decisions an FP32 forward may take either
+    way).  Returns (ok, worst ratio |g - g_ref| / bound (<= 1 passes), flat
+    index of the worst element, its GPU value, its oracle value)."""
     a = np.asarray(gpu, np.float64).ravel()
     b = np.asarray(ref, np.float64).ravel()
     assert a.shape == b.shape, (a.shape, b.shape)
     if b.size == 0:
         return True, 0.0, -1, 0.0, 0.0
     bound = rel * np.abs(b) + floor * float(np.abs(b).max())
+    if slack is not None:
+        bound = bound + np.asarray(slack, np.float64).ravel()
     d = np.abs(a - b)
     with np.errstate(divide="ignore", invalid="ignore"):
         ratio = np.where(bound > 0, d / np.where(bound > 0, bound, 1.0), np.where(d > 0, np.inf, 0.0))
@@ -56,11 +59,14 @@ def grad_error(gpu, ref, rel=1e-3, floor=1e-3):
 
 
 def check_grads(named, tag, rel=1e-3, floor=1e-3):
-    """Runs grad_error over (name, gpu, ref) groups, prints each group's worst
-    element and returns the worst ratio over all groups (<= 1 passes)."""
+    """Runs grad_error over (name, gpu, ref[, slack]) groups, prints each
+    group's worst element and returns the worst ratio over all groups (<= 1
+    passes)."""
     worst = 0.0
-    for name, a, b in named:
-        ok, r, i, ga, gb = grad_error(a, b, rel, floor)
+    for entry in named:
+        name, a, b = entry[:3]
+        sl = entry[3] if len(entry) > 3 else None
+        ok, r, i, ga, gb = grad_error(a, b, rel, floor, sl)
         print(f"{tag} {name}: worst element {i}: gpu {ga:.6e} oracle {gb:.6e} "
               f"(|diff| / bound = {r:.2e})")
         worst = max(worst, r)

@@ -129,10 +129,11 @@ def _stage_grads(api, stage, seed=3):
         else:
             grp.append((k, a, ref[k]))
     if fine:
+        sl = ref["slack"]  # ReLU decisions an FP32 forward may take either way
         for l, (p, r) in enumerate(zip(ps[0::2], ref["d_W"])):
-            grp.append((f"d_W[{l}]", p.grad.cpu().numpy(), r))
+            grp.append((f"d_W[{l}]", p.grad.cpu().numpy(), r, sl["d_W"][l]))
         for l, (p, r) in enumerate(zip(ps[1::2], ref["d_b"])):
-            grp.append((f"d_b[{l}]", p.grad.cpu().numpy(), r))
+            grp.append((f"d_b[{l}]", p.grad.cpu().numpy(), r, sl["d_b"][l]))
     return check_grads(grp, stage)
 
 

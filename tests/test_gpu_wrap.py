@@ -106,10 +106,11 @@ def test_wrapped_gradients(api):
             grp += [(f"{k}[:,{c}]", a[:, c], ref[k][:, c]) for c in range(a.shape[1])]
         else:
             grp.append((k, a, ref[k]))
+    sl = ref["slack"]  # ReLU decisions an FP32 forward may take either way
     for l, (p, rW) in enumerate(zip(ps[0::2], ref["d_W"])):
-        grp.append((f"d_W[{l}]", p.grad.cpu().numpy(), rW))
+        grp.append((f"d_W[{l}]", p.grad.cpu().numpy(), rW, sl["d_W"][l]))
     for l, (p, rb) in enumerate(zip(ps[1::2], ref["d_b"])):
-        grp.append((f"d_b[{l}]", p.grad.cpu().numpy(), rb))
+        grp.append((f"d_b[{l}]", p.grad.cpu().numpy(), rb, sl["d_b"][l]))
     assert check_grads(grp, "wrap grad") <= 1.0
 
 

@@ -371,6 +371,83 @@ def test_stop_grad_mean_drops_only_the_encoding_path():
         np.testing.assert_array_equal(a, b)
 
 
+def _numpy_mlp_backward(m, x, g_out, masks):
+    """Independent dense numpy back-propagation of one row with the ReLU
+    decisions given explicitly (masks[l]: the on/off pattern of the units of
+    hidden layer l); an 'off' unit contributes activation 0."""
+    L = len(m.W)
+    acts = [np.asarray(x, np.float64)]
+    h = acts[0]
+    for l in range(L - 1):
+        z = m.W[l].astype(np.float64) @ h + m.b[l]
+        h = np.where(masks[l], z, 0.0)
+        acts.append(h)
+    d = np.asarray(g_out, np.float64)
+    dW, db = [None] * L, [None] * L
+    for l in range(L - 1, -1, -1):
+        dW[l] = np.outer(d, acts[l])
+        db[l] = d.copy()
+        if l > 0:
+            d = (m.W[l].astype(np.float64).T @ d) * masks[l - 1]
+    return dW, db
+
+
+def test_relu_slack_is_zero_without_ambiguous_decisions():
+    """Biases of +10 put every hidden pre-activation far above zero: no ReLU
+    decision is ambiguous and the slack is exactly zero."""
+    H, W = 16, 32
+    sc = synth.make_scene(30, H, W, seed=21)
+    m = synth.make_mlp(gain=0.3, seed=21)
+    m.b = [np.full_like(b, 10.0) for b in m.b]
+    tx = synth.make_tx(2, seed=21)
+    dr = synth.rng(21).normal(size=(2, 30, 5))
+    _, _, _, sl = oracle.mlp_grad(sc, m, tx, H, W, dr)
+    assert all(float(np.abs(a).max()) == 0.0 for a in sl["d_W"] + sl["d_b"])
+    assert float(np.abs(sl["d_mean"]).max()) == 0.0
+
+
+def test_relu_slack_equals_the_flipped_decision():
+    """One row whose hidden unit j of the second layer is put exactly at zero
+    pre-activation (by its bias): the slack of every parameter equals the
+    absolute difference between the dense numpy back-propagations with that
+    unit on and off, and the gradient itself is one of the two."""
+    H, W = 16, 32
+    sc = synth.make_scene(1, H, W, seed=22)
+    m = synth.make_mlp(gain=1.0, bias_std=0.05, n_hidden=3, seed=22)
+    m.W = [w.astype(np.float64) for w in m.W]
+    m.b = [b.astype(np.float64) for b in m.b]
+    tx = synth.make_tx(1, seed=22)
+    mu = sc.mean[0].astype(np.float64) / np.array([W, H])
+    s = (tx[0] - np.array(m.room_min)) / np.array(m.room_size)
+    x = np.concatenate([oracle.pe(mu, m.L_mean), oracle.pe(s, m.L_tx)])
+    h0 = np.maximum(m.W[0] @ x + m.b[0], 0.0)
+    z1 = m.W[1] @ h0 + m.b[1]
+    j = int(np.argmax(np.abs(z1)))
+    m.b[1][j] = 0.0
+    m.b[1][j] = -float(m.W[1][j] @ h0)      # z1[j] = 0 up to rounding
+    masks = []
+    h = x
+    for l in range(len(m.W) - 1):
+        z = m.W[l] @ h + m.b[l]
+        masks.append(z > 0.0)
+        h = np.maximum(z, 0.0)
+    dr = synth.rng(22).normal(size=(1, 1, 5))
+    dW, db, _, sl = oracle.mlp_grad(sc, m, tx, H, W, dr, stop_grad_mean=True)
+    on = [mk.copy() for mk in masks]
+    off = [mk.copy() for mk in masks]
+    on[1][j], off[1][j] = True, False
+    dW_on, db_on = _numpy_mlp_backward(m, x, dr[0, 0], on)
+    dW_off, db_off = _numpy_mlp_backward(m, x, dr[0, 0], off)
+    close = lambda a, b: all(np.allclose(x, y, rtol=1e-9, atol=1e-12) for x, y in zip(a, b))
+    assert close(dW, dW_on) or close(dW, dW_off)  # either decision at z = 0
+    for l in range(len(m.W)):
+        np.testing.assert_allclose(sl["d_W"][l], np.abs(dW_on[l] - dW_off[l]), rtol=1e-9,
+                                   atol=1e-12)
+        np.testing.assert_allclose(sl["d_b"][l], np.abs(db_on[l] - db_off[l]), rtol=1e-9,
+                                   atol=1e-12)
+    assert float(np.abs(sl["d_W"][0]).max()) > 0.0  # the flip reaches the first layer
+
+
 # ---------------------------------------------------------------- rssi ----
 @pytest.mark.parametrize("sigma", [1.5, 2.5])
 def test_rssi_closed_form(sigma):
