@@ -519,18 +519,18 @@ def run_train(args):
                                              for p, gg, m_, v_ in adam_state], 1))}
     peaks, peak_src = measured_peaks()
     # MLP backward algorithmic FLOP per row (the forward saved its hidden
-    # activations, so none are recomputed): delta chain through the hidden
-    # layers and the output (3 x 2*128^2 + 2*128*5), weight gradients
-    # (4 x 2*128^2 + 2*128*89 + 2*128*5), d_mean through W1m (2*128*26)
-    fl_row = 3 * 2 * 128 * 128 + 2 * 128 * 5 + 4 * 2 * 128 * 128 + 2 * 128 * 89 + \
-        2 * 128 * 5 + 2 * 128 * 26
-    # the MLP backward's GEMMs are FP32 emulated on the BF16 tensor cores with
-    # a three-term split (nine BF16 products per FP32 product)
-    roof = {"kernel": "wrf_deform_backward (cuBLAS FP32-emulated GEMMs + elementwise kernels)",
+    # activations; positions are stop-gradded in the fine stage): the delta
+    # chain through the output layer and the hidden 128 x 128 layers, and the
+    # weight gradients of every layer
+    nh = len(mlp_p) // 2 - 2
+    fl_row = 2 * 128 * 5 + nh * 2 * 128 * 128 + nh * 2 * 128 * 128 + 2 * 128 * 89 + 2 * 128 * 5
+    # its products run on the BF16 tensor cores with every FP32 operand split
+    # into BF16 hi + lo: three BF16 products (hi hi, hi lo, lo hi) per FP32 one
+    roof = {"kernel": "mlp_bwd_tc_kernel (wrf_deform_backward: tcgen05, BF16 hi/lo split)",
             "bound": "tensor",
             "achieved": Q * N * fl_row / (stage["deform_backward"] * 1e-3) / 1e12,
-            "peak": peaks["bf16_tflops"] / 9.0, "unit": "TFLOP/s",
-            "peak_source": f"bf16_tflops ({peak_src}) / 9 (FP32 as 3xBF16 split)",
+            "peak": peaks["bf16_tflops"] / 3.0, "unit": "TFLOP/s",
+            "peak_source": f"bf16_tflops ({peak_src}) / 3 (three BF16 products per FP32 product)",
             "traffic": None, "stage_ms": stage}
     roof["frac"] = roof["achieved"] / roof["peak"]
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": K,
@@ -543,12 +543,11 @@ def run_train(args):
                        "l2": "256 MB buffer rewritten between timed steps",
                        "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
-            # this library's kernels only (cuBLAS GEMM kernels not counted):
-            # forward: prep, MLP, project, bin x5, render (9); loss: 3;
-            # backward: render, project, prep, gamma tables (4), then per row
-            # chunk of up to 1M rows features, 4 ReLU masks, 5 column sums
-            # (10, the hidden activations saved by the forward); Adam: 1
-            "gpu_launches": K * (9 + 3 + 4 + 10 * ((Q * N + (1 << 20) - 1) // (1 << 20)) + 1)}
+            # this library's kernels: anneal noise (1); forward: prep, MLP,
+            # project, bin x5, render (9); loss: 3; backward: render, project
+            # (2), MLP: prep, backward preparation, the tensor-core kernel, its
+            # reduction, the per-query sums and the gamma(tx) part (6); Adam: 1
+            "gpu_launches": K * (1 + 9 + 3 + 2 + 6 + 1)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()

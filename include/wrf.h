@@ -248,6 +248,22 @@ typedef struct {
 wrf_status wrf_adam(const wrf_adam_group *groups, int32_t n_groups, int32_t step, float beta1,
                     float beta2, float eps, void *stream);
 
+/* Anneal smoothing of the fine stage (Sec. 4.4, Eq. 17-18): the MLP's TX
+ * input at fine-stage iteration i carries the noise
+ *   n_i = gamma N3(0,1) (2 / cbrt(N_s)) (1 - i / tau)   for i < tau, else 0
+ * on the position normalised to the room's unit cube, i.e. room_size * n_i
+ * in metres:
+ *   tx_out[q] = tx[idx[q]] + room_size * normals[q] * gamma (2 / cbrt(N_s)) (1 - i / tau).
+ *   tx       [n_positions][3] device, the training positions (metres).
+ *   idx      [Q] device row indices into tx (the minibatch), or NULL (row q).
+ *   normals  [Q][3] device N(0,1) draws (the caller's generator).
+ *   room_size host float[3] (> 0); gamma >= 0 (Table I: 1); tau >= 1 (Table I:
+ *            10k); iter >= 0; n_positions = N_s.
+ *   tx_out   [Q][3] device output.                                          */
+wrf_status wrf_anneal_tx(const float *tx, const int32_t *idx, int32_t n_positions,
+                         const float *normals, int32_t Q, int32_t iter, float gamma, int32_t tau,
+                         const float room_size[3], float *tx_out, void *stream);
+
 /* RSSI head (Sec. 7.2): for each query the map of wrf_deform_project +
  * wrf_render, reduced by a global average pool of its magnitude,
  *   rssi[q] = (1 / (H W)) sum_pixels |A_q(pixel)|

@@ -30,6 +30,7 @@ EXPORTS = (
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
     "wrf_loss_workspace_size", "wrf_loss", "wrf_adam", "wrf_render_complex",
     "wrf_paper_workspace_size", "wrf_paper_deform_project", "wrf_measure_alu_peaks",
+    "wrf_anneal_tx",
 )
 
 
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
         "wrf_loss": (I32, [P, P, I32, I32, I32, F, P, P, P, S, P]),
         "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
         "wrf_render_complex": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
+        "wrf_anneal_tx": (I32, [P, P, I32, P, I32, I32, F, I32, C.POINTER(C.c_float), P, P]),
         "wrf_paper_workspace_size": (S, [I32, I32]),
         "wrf_measure_alu_peaks": (I32, [C.POINTER(C.c_double)] * 3 + [P]),
         "wrf_paper_deform_project": (I32, [C.POINTER(PaperScene), C.POINTER(PaperMlp), gp, P, I32,

@@ -22,7 +22,7 @@ __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
            "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
            "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project",
-           "wrf_measure_alu_peaks", "wrf_deform_acts"]
+           "wrf_measure_alu_peaks", "wrf_deform_acts", "wrf_anneal_tx"]
 
 
 def _p(t):
@@ -306,6 +306,23 @@ def wrf_adam(groups, step: int, beta1: float = 0.9, beta2: float = 0.999, eps: f
         arr[i] = _lib.AdamGroup(_p(p), _p(g), _p(m), _p(v), p.numel(), float(lr))
     _lib.check(L.wrf_adam(arr, len(groups), int(step), float(beta1), float(beta2), float(eps),
                           _stream(stream)))
+
+
+def wrf_anneal_tx(tx, normals, iteration: int, gamma: float, tau: int, room_size, idx=None,
+                  n_positions=None, out=None, stream=None):
+    """Eq. 17-18: TX positions (tx[idx] or tx) plus the anneal-smoothing noise
+    of fine-stage iteration `iteration`, in metres ([Q,3] FP32 device)."""
+    L = _lib.load()
+    Q = int(normals.shape[0])
+    if out is None:
+        out = torch.empty((Q, 3), dtype=torch.float32, device=normals.device)
+    if idx is not None:
+        idx = idx.to(device=normals.device, dtype=torch.int32).contiguous()
+    ns = int(tx.shape[0]) if n_positions is None else int(n_positions)
+    room = (C.c_float * 3)(*[float(v) for v in room_size])
+    _lib.check(L.wrf_anneal_tx(_p(tx), _p(idx), ns, _p(normals), Q, int(iteration), float(gamma),
+                               int(tau), room, _p(out), _stream(stream)))
+    return out
 
 
 def wrf_rssi(scene: DeviceScene, mlp: DeviceMLP, grid, tx, rssi=None, map_out=None, ws=None,

@@ -355,6 +355,22 @@ wrf_status wrf_adam(const wrf_adam_group *groups, int32_t n_groups, int32_t step
     return WRF_OK;
 }
 
+wrf_status wrf_anneal_tx(const float *tx, const int32_t *idx, int32_t n_positions,
+                         const float *normals, int32_t Q, int32_t iter, float gamma, int32_t tau,
+                         const float room_size[3], float *tx_out, void *stream) {
+    if (Q < 0 || n_positions < 1 || tau < 1 || iter < 0)
+        return fail(WRF_EINVAL, "anneal: Q >= 0, n_positions >= 1, tau >= 1, iter >= 0");
+    if (!room_size || !(room_size[0] > 0.f && room_size[1] > 0.f && room_size[2] > 0.f))
+        return fail(WRF_EINVAL, "anneal: room_size must be > 0");
+    if (!(gamma >= 0.f)) return fail(WRF_EINVAL, "anneal: gamma >= 0");
+    if (Q == 0) return WRF_OK;
+    if (!tx || !normals || !tx_out) return fail(WRF_EINVAL, "anneal: NULL pointer");
+    cudaError_t e = wrf::launch_anneal(tx, idx, normals, Q, iter, n_positions, gamma, tau,
+                                       room_size, tx_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "anneal");
+    return WRF_OK;
+}
+
 wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                     const float *tx, int32_t Q, float *rssi, float *map, void *ws,
                     size_t ws_bytes, void *stream) {

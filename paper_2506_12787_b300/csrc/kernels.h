@@ -104,6 +104,9 @@ struct AdamGroup {
 constexpr int kAdamGroups = 32;
 cudaError_t launch_adam(const AdamGroup *groups, int n, int step, float beta1, float beta2,
                         float eps, cudaStream_t st);
+cudaError_t launch_anneal(const float *tx, const int *idx, const float *normals, int Q, int iter,
+                          int n_pos, float gamma, int tau, const float *room_size, float *out,
+                          cudaStream_t st);
 
 // RSSI head: one CTA per query, whole path fused (rssi.cu); U, V and the
 // FP32 weight images come from launch_prep(..., want_bf16 = false).

@@ -15,13 +15,13 @@
 // is then thread-local.  Per tile and layer:
 //   * D_l^T is a 128-unit x 64-row shared tile (K-major, 128-byte swizzle:
 //     unit u's 64 rows in one 128-byte line), written by thread u;
-//   * H_l is a 64-row x 128-unit shared tile (row-major, two 64-unit swizzle
-//     atoms), written by thread u from a coalesced column load;
+//   * H_l^T is a 128-unit x 64-row shared tile laid out like D^T, written by
+//     thread u from a coalesced column load;
 //   * delta:  D_{l-1}^T = W_l^T D_l^T   (M = 128 units, N = 64 rows, K = 128):
 //             A = W_l^T panels (K-major), B = the D^T tile read MN-major;
-//   * weight gradient:  dW_l += D_l^T H_l   (M = 128 out units, N = 128 in
-//             units, K = 64 rows): A = the D^T tile (K-major), B = the H tile
-//             (MN-major), accumulated in TMEM over many tiles;
+//   * weight gradient:  dW_l^T += H_l^T D_l   (M = 128 in units, N = 128 out
+//             units, K = 64 rows): A = the H^T tile, B = the D^T tile (both
+//             K-major), accumulated in TMEM over many tiles;
 //   * the epilogue (thread u = TMEM lane u) reads its unit's 64 deltas,
 //     applies the ReLU mask of H_l (bits kept from the load), sums them into
 //     db, and writes D_{l-1}^T back to the tile.
@@ -61,9 +61,9 @@ constexpr int kThreads = kWG * 128 + 32;  // + producer warp
 constexpr int kRing = 5;                  // weight panel slots
 constexpr uint32_t kPanel = 128 * 128;    // W^T panel: 128 rows x 64 K x BF16
 constexpr uint32_t kDt = 128 * 128;       // D^T tile, one term: 128 units x 64 rows x BF16
-constexpr uint32_t kHt = 64 * 256;        // H tile, one term: 64 rows x 128 units x BF16
+constexpr uint32_t kHt = 128 * 128;       // H^T tile, one term: 128 units x 64 rows x BF16
 constexpr uint32_t kGt = 64 * 128;        // gamma(mean) tile, one term: 64 rows x 64 features
-constexpr uint32_t kHAtom = 64 * 128;     // bytes per 64-unit swizzle atom of the H tile
+constexpr uint32_t kMnLbo = 8192;         // MN-major B with N = 64: one swizzle atom, LBO unused
 constexpr int kSlots = 3;                 // dW accumulators (hidden layers per pass)
 constexpr int kFlush = 8;                 // tile pairs between flushes of the accumulators
 constexpr int kGp = 8;                    // floats per staged d_resid row
@@ -73,7 +73,7 @@ constexpr int kMaxGrid = 256;             // CTAs with partial-sum slots
 
 constexpr size_t smem_bytes() {
     return 1024 + kRing * kPanel + kWG * (2 * kDt + 2 * kHt) + kWG * kR * kGp * 4 +
-           8 * WRF_HIDDEN * 4 + (2 * kRing + 2 * kWG) * 8 + 16;
+           8 * WRF_HIDDEN * 4 + (2 * kRing + kWG) * 8 + 16;
 }
 static_assert(smem_bytes() <= 227 * 1024, "shared memory of one CTA");
 
@@ -107,12 +107,6 @@ __device__ __forceinline__ void split1(float x, uint16_t &hi, uint16_t &lo) {
     lo = *reinterpret_cast<const uint16_t *>(&l);
 }
 
-// Byte offset of (row r, unit u) in the H tile: two 64-unit atoms (kHAtom
-// apart), 8-row groups of 1024 bytes, 16-byte chunks XOR r % 8.
-__device__ __forceinline__ uint32_t ht_off(int r, int u) {
-    return static_cast<uint32_t>((u >> 6) * kHAtom + (r >> 3) * 1024 + (r & 7) * 128 +
-                                 ((((u & 63) >> 3) ^ (r & 7)) << 4) + (u & 7) * 2);
-}
 // Byte offset of (row m, column k < 64) in a K-major 128-byte-swizzled panel.
 __host__ __device__ inline uint32_t panel_off(int m, int k) {
     return static_cast<uint32_t>((m >> 3) * 1024 + (m & 7) * 128 + ((((k >> 3) ^ (m & 7))) << 4) +
@@ -158,6 +152,9 @@ struct BwdArgs {
     int *status;
 };
 
+// 9 warps: the SM's four register sub-files hold up to 3 warps each, so at
+// most 168 registers per thread; a single 64-float column buffer (prefetch)
+// keeps the kernel within that.
 __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -167,9 +164,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
     float *gstage = reinterpret_cast<float *>(tiles + kWG * (2 * kDt + 2 * kHt));  // [kWG][kR][kGp]
     float *wo_s = gstage + kWG * kR * kGp;                        // [8][128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(wo_s + 8 * WRF_HIDDEN);
-    uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing,
-             *gbar = bars + 2 * kRing + kWG;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kRing + 2 * kWG);
+    uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kRing + kWG);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -178,10 +174,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kWG);
         }
-        for (int i = 0; i < kWG; ++i) {
-            mbar_init(&accb[i], 1);
-            mbar_init(&gbar[i], 1);
-        }
+        for (int i = 0; i < kWG; ++i) mbar_init(&accb[i], 1);
         fence_mbar_init();
         *abort_flag = 0;
     }
@@ -197,28 +190,48 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                            ? (a.npairs - static_cast<int>(blockIdx.x) + gridDim.x - 1) / gridDim.x
                            : 0;
     const bool have_dw = a.hi >= a.lo;
+    // per round, in order: W^T panels of the delta layers nh .. dlo (4 each),
+    // then (last pass) the gamma(mean) tiles of the two warpgroups' tiles
 
     if (warp == kWG * 4) {
         // ------------------------------------------------------ producer warp
         if (lane == 0) {
             uint32_t g = 0;
             bool ok = true;
-            for (int r = 0; r < rounds && ok; ++r)
+            auto acquire = [&](int &slot) {
+                slot = static_cast<int>(g % kRing);
+                if (g >= kRing &&
+                    !wait_or_abort(&empty[slot], ((g / kRing) - 1) & 1u, abort_flag, a.status))
+                    return false;
+                return true;
+            };
+            for (int r = 0; r < rounds && ok; ++r) {
                 for (int l = a.nh; l >= a.dlo && ok; --l)
                     for (int p = 0; p < 4; ++p) {
-                        const int slot = static_cast<int>(g % kRing);
-                        if (g >= kRing &&
-                            !wait_or_abort(&empty[slot], ((g / kRing) - 1) & 1u, abort_flag,
-                                           a.status)) {
-                            ok = false;
-                            break;
-                        }
+                        int slot;
+                        if (!(ok = acquire(slot))) break;
                         mbar_arrive_expect_tx(&full[slot], kPanel);
                         bulk_g2s(ring + slot * kPanel,
                                  a.wimg + (static_cast<size_t>(l - 1) * 4 + p) * kPanel, kPanel,
                                  &full[slot]);
                         ++g;
                     }
+                if (!a.last_pass) continue;
+                const int pr = static_cast<int>(blockIdx.x) + r * static_cast<int>(gridDim.x);
+                for (int w2 = 0; w2 < kWG && ok; ++w2) {
+                    int slot;
+                    if (!(ok = acquire(slot))) break;
+                    const int tile = 2 * pr + w2;
+                    // a warpgroup without a tile this round multiplies zeros: any
+                    // gamma tile will do
+                    const size_t t0 =
+                        static_cast<size_t>(tile < a.ntiles ? (tile % a.tpq) : 0) * kGt;
+                    mbar_arrive_expect_tx(&full[slot], 2 * kGt);
+                    bulk_g2s(ring + slot * kPanel, a.gimg + t0, kGt, &full[slot]);
+                    bulk_g2s(ring + slot * kPanel + kGt, a.gimg + a.gterm + t0, kGt, &full[slot]);
+                    ++g;
+                }
+            }
             // copies still in flight land before the CTA exits (bounded waits)
             for (uint32_t i = 0; i < kRing && i < g; ++i) {
                 const uint32_t gg = g - 1 - i;
@@ -237,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
         const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;
         const uint32_t t_dw = tmem_base;                                   // + 128 s
         const uint32_t t_dl = tmem_base + 384u + static_cast<uint32_t>(64 * wg);
-        const uint32_t id_dw = idesc_bf16_bmn(128, 128), id_dl = idesc_bf16_bmn(128, 64);
+        const uint32_t id_dw = idesc_bf16(128, 128), id_dl = idesc_bf16_bmn(128, 64);
 
         // zero this warpgroup's half (64 columns) of every dW accumulator
         auto zero_dw = [&]() {
@@ -272,100 +285,157 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
             zero_dw();
         };
         if (have_dw) zero_dw();
-        float wo[WRF_OUT];
-#pragma unroll
-        for (int o = 0; o < WRF_OUT; ++o) wo[o] = wo_s[o * WRF_HIDDEN + u];
         float db_acc[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) db_acc[i] = 0.f;
         float dwo[WRF_OUT] = {0.f, 0.f, 0.f, 0.f, 0.f}, dbo = 0.f;
-        uint32_t g = 0, phase = 0, gphase = 0;
+        uint32_t g = 0, phase = 0;
         tc_fence_before();
         named_bar(1, kWG * 128);
         tc_fence_after();
 
+        struct TileRef {
+            int tile, q, n0, nvalid;
+            bool tv;
+            long long row0;
+        };
+        auto tile_at = [&](int round) {
+            TileRef t{};
+            const int p = static_cast<int>(blockIdx.x) + round * static_cast<int>(gridDim.x);
+            t.tile = 2 * p + wg;
+            t.tv = round < rounds && t.tile < a.ntiles;
+            t.q = t.tv ? t.tile / a.tpq : 0;
+            t.n0 = t.tv ? (t.tile % a.tpq) * kR : 0;
+            t.nvalid = t.tv ? min(kR, a.N - t.n0) : 0;
+            t.row0 = static_cast<long long>(t.q) * a.N + t.n0;
+            return t;
+        };
         // this unit's column of an activation tile: h[r] = H[row0 + r][u]
-        auto load_col = [&](const float *H, long long row0, int nvalid, float *h) {
+        auto load_col = [&](const float *H, const TileRef &t, float *h) {
 #pragma unroll
             for (int r = 0; r < kR; ++r)
-                h[r] = r < nvalid ? __ldg(H + (row0 + r) * WRF_HIDDEN + u) : 0.f;
+                h[r] = r < t.nvalid ? __ldg(H + (t.row0 + r) * WRF_HIDDEN + u) : 0.f;
         };
-        // D^T row u of the tile from 64 FP32 values: hi and lo terms
-        auto write_dt = [&](const float *d) {
+        // this thread's share of the tile's d_resid rows (kR x 5 values)
+        auto load_g = [&](const TileRef &t, float *gp) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
+            for (int k = 0; k < 3; ++k) {
+                const int e = u + 128 * k, r = e / WRF_OUT;
+                gp[k] = (e < kR * WRF_OUT && r < t.nvalid) ? __ldg(a.dres + t.row0 * WRF_OUT + e)
+                                                           : 0.f;
+            }
+        };
+        // rows 16 qt .. 16 qt + 15 of D^T row u (hi and lo terms)
+        auto write_dt_q = [&](const float *t, int qt) {
+#pragma unroll
+            for (int c4 = 0; c4 < 2; ++c4) {
+                const int c = 2 * qt + c4;
                 uint4 h4, l4;
-                split2(d[8 * c + 0], d[8 * c + 1], h4.x, l4.x);
-                split2(d[8 * c + 2], d[8 * c + 3], h4.y, l4.y);
-                split2(d[8 * c + 4], d[8 * c + 5], h4.z, l4.z);
-                split2(d[8 * c + 6], d[8 * c + 7], h4.w, l4.w);
+                split2(t[8 * c4 + 0], t[8 * c4 + 1], h4.x, l4.x);
+                split2(t[8 * c4 + 2], t[8 * c4 + 3], h4.y, l4.y);
+                split2(t[8 * c4 + 4], t[8 * c4 + 5], h4.z, l4.z);
+                split2(t[8 * c4 + 6], t[8 * c4 + 7], h4.w, l4.w);
                 const uint32_t off = static_cast<uint32_t>(u * 128 + ((c ^ (u & 7)) << 4));
                 *reinterpret_cast<uint4 *>(Dt + off) = h4;
                 *reinterpret_cast<uint4 *>(Dt + kDt + off) = l4;
             }
         };
+        auto write_d0_q = [&](const float *t, int qt, const TileRef &ti) {
+            if (!a.d0) return;
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                if (16 * qt + r < ti.nvalid)
+                    a.d0[(ti.row0 + 16 * qt + r) * WRF_HIDDEN + u] = t[r];
+        };
 
+        // h: one 64-row column of activations, always the next one needed
+        // (loaded a step ahead); gacc: the gamma(mean) part of dW_0 for
+        // features < 32 (the rest, when L_mean > 7, read-modify-written per tile)
+        float h[kR], gpre[3], gacc[32];
+#pragma unroll
+        for (int f = 0; f < 32; ++f) gacc[f] = 0.f;
+        {
+            const TileRef t0 = tile_at(0);
+            load_col(a.acts + static_cast<size_t>(a.nh) * a.act_stride, t0, h);
+            load_g(t0, gpre);
+        }
         for (int round = 0; round < rounds; ++round) {
-            if (wg_bar_any(1, *abort_flag != 0, kWG * 128)) break;
-            const int p = static_cast<int>(blockIdx.x) + round * static_cast<int>(gridDim.x);
-            const int tile = 2 * p + wg;
-            const bool tv = tile < a.ntiles;
-            const int q = tv ? tile / a.tpq : 0;
-            const int n0 = tv ? (tile % a.tpq) * kR : 0;
-            const int nvalid = tv ? min(kR, a.N - n0) : 0;
-            const long long row0 = static_cast<long long>(q) * a.N + n0;
-
-            // ---- output layer (K = 5) on the CUDA cores
-            for (int e = u; e < kR * WRF_OUT; e += 128) {
-                const int r = e / WRF_OUT, o = e % WRF_OUT;
-                gs[r * kGp + o] = r < nvalid ? __ldg(a.dres + (row0 + r) * WRF_OUT + o) : 0.f;
+            const TileRef ti = tile_at(round), tn = tile_at(round + 1);
+            // ---- output layer (K = 5) on the CUDA cores; h = H_{nh+1}
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int e = u + 128 * k;
+                if (e < kR * WRF_OUT) gs[(e / WRF_OUT) * kGp + e % WRF_OUT] = gpre[k];
             }
-            float h[kR], d[kR];
-            load_col(a.acts + static_cast<size_t>(a.nh) * a.act_stride, row0, nvalid, h);
             named_bar(2 + wg, 128);
-            float dsum = 0.f;
+            // what this step needs from h: the ReLU mask and dW of the output layer
+            uint64_t mask_o = 0;
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const float4 g0 = *reinterpret_cast<const float4 *>(gs + r * kGp);
-                const float g4 = gs[r * kGp + 4];
+                if (h[r] > 0.f) mask_o |= 1ull << r;
                 if (a.first_pass) {
+                    const float4 g0 = *reinterpret_cast<const float4 *>(gs + r * kGp);
+                    const float g4 = gs[r * kGp + 4];
                     dwo[0] = fmaf(g0.x, h[r], dwo[0]);
                     dwo[1] = fmaf(g0.y, h[r], dwo[1]);
                     dwo[2] = fmaf(g0.z, h[r], dwo[2]);
                     dwo[3] = fmaf(g0.w, h[r], dwo[3]);
                     dwo[4] = fmaf(g4, h[r], dwo[4]);
                 }
-                float dv = g0.x * wo[0];
-                dv = fmaf(g0.y, wo[1], dv);
-                dv = fmaf(g0.z, wo[2], dv);
-                dv = fmaf(g0.w, wo[3], dv);
-                dv = fmaf(g4, wo[4], dv);
-                d[r] = h[r] > 0.f ? dv : 0.f;
-                dsum += d[r];
+            }
+            // the first delta layer's activations, in flight during the rest of the step
+            if (a.nh >= a.dlo) {
+                load_col(a.acts + static_cast<size_t>(a.nh - 1) * a.act_stride, ti, h);
+            } else {
+                // no delta layer: the next round's inputs
+                load_col(a.acts + static_cast<size_t>(a.nh) * a.act_stride, tn, h);
+                load_g(tn, gpre);
+            }
+            float dsum = 0.f;
+#pragma unroll
+            for (int qt = 0; qt < 4; ++qt) {
+                float t[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const int rr = 16 * qt + r;
+                    const float4 g0 = *reinterpret_cast<const float4 *>(gs + rr * kGp);
+                    const float g4 = gs[rr * kGp + 4];
+                    float dv = g0.x * wo_s[u];
+                    dv = fmaf(g0.y, wo_s[WRF_HIDDEN + u], dv);
+                    dv = fmaf(g0.z, wo_s[2 * WRF_HIDDEN + u], dv);
+                    dv = fmaf(g0.w, wo_s[3 * WRF_HIDDEN + u], dv);
+                    dv = fmaf(g4, wo_s[4 * WRF_HIDDEN + u], dv);
+                    t[r] = ((mask_o >> rr) & 1ull) ? dv : 0.f;
+                    dsum += t[r];
+                }
+                if (a.nh == 0) write_d0_q(t, qt, ti);
+                write_dt_q(t, qt);
             }
             if (a.first_pass && u < WRF_OUT)
                 for (int r = 0; r < kR; ++r) dbo += gs[r * kGp + u];
 #pragma unroll
             for (int i = 1; i < 8; ++i)
                 if (i == a.nh && i >= a.lo && i <= a.hi) db_acc[i] += dsum;
-            write_dt(d);
 
-            // ---- hidden layers l = nh .. dlo: delta chain and dW
+            // ---- hidden layers l = nh .. dlo: delta chain and dW; d = H_l
             for (int l = a.nh; l >= a.dlo; --l) {
-                load_col(a.acts + static_cast<size_t>(l - 1) * a.act_stride, row0, nvalid, h);
                 uint64_t mask = 0;
 #pragma unroll
                 for (int r = 0; r < kR; ++r)
                     if (h[r] > 0.f) mask |= 1ull << r;
                 const bool dw_here = l >= a.lo && l <= a.hi;
                 if (dw_here) {
+                    // H_l^T row u (64 rows of unit u), hi and lo terms
 #pragma unroll
-                    for (int r = 0; r < kR; ++r) {
-                        uint16_t hh, hl;
-                        split1(h[r], hh, hl);
-                        const uint32_t off = ht_off(r, u);
-                        *reinterpret_cast<uint16_t *>(Ht + off) = hh;
-                        *reinterpret_cast<uint16_t *>(Ht + kHt + off) = hl;
+                    for (int c = 0; c < 8; ++c) {
+                        uint4 h4, l4;
+                        split2(h[8 * c + 0], h[8 * c + 1], h4.x, l4.x);
+                        split2(h[8 * c + 2], h[8 * c + 3], h4.y, l4.y);
+                        split2(h[8 * c + 4], h[8 * c + 5], h4.z, l4.z);
+                        split2(h[8 * c + 6], h[8 * c + 7], h4.w, l4.w);
+                        const uint32_t off = static_cast<uint32_t>(u * 128 + ((c ^ (u & 7)) << 4));
+                        *reinterpret_cast<uint4 *>(Ht + off) = h4;
+                        *reinterpret_cast<uint4 *>(Ht + kHt + off) = l4;
                     }
                 }
                 fence_async_smem();
@@ -374,13 +444,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                 if (leader) {
                     tc_fence_after();
                     if (dw_here) {
+                        // dW_l^T += H_l^T D_l (lanes = input units, columns = output units)
                         const uint32_t acc = t_dw + static_cast<uint32_t>(128 * (a.hi - l));
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ah = sw128_desc(dt_a + kk * 32u);
-                            const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
-                            const uint64_t bh = sw128_desc_lbo(ht_a + kk * 2048u, kHAtom, 1024u);
-                            const uint64_t bl = sw128_desc_lbo(ht_a + kHt + kk * 2048u, kHAtom, 1024u);
+                            const uint64_t ah = sw128_desc(ht_a + kk * 32u);
+                            const uint64_t al = sw128_desc(ht_a + kHt + kk * 32u);
+                            const uint64_t bh = sw128_desc(dt_a + kk * 32u);
+                            const uint64_t bl = sw128_desc(dt_a + kDt + kk * 32u);
                             mma_bf16(acc, ah, bh, id_dw, 1u);
                             mma_bf16(acc, ah, bl, id_dw, 1u);
                             mma_bf16(acc, al, bh, id_dw, 1u);
@@ -397,10 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                         for (int k4 = 0; k4 < 4; ++k4) {
                             const int kk = (pn & 1) * 4 + k4;
                             const uint64_t aw = sw128_desc(wa + k4 * 32u);
-                            const uint64_t bh = sw128_desc_lbo(dt_a + kk * 2048u, kHAtom, 1024u);
+                            const uint64_t bh = sw128_desc_lbo(dt_a + kk * 2048u, kMnLbo, 1024u);
                             if (pn < 2) {
                                 const uint64_t bl =
-                                    sw128_desc_lbo(dt_a + kDt + kk * 2048u, kHAtom, 1024u);
+                                    sw128_desc_lbo(dt_a + kDt + kk * 2048u, kMnLbo, 1024u);
                                 mma_bf16(t_dl, aw, bh, id_dl, (pn == 0 && k4 == 0) ? 0u : 1u);
                                 mma_bf16(t_dl, aw, bl, id_dl, 1u);
                             } else {
@@ -412,80 +483,107 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                     mma_commit(&accb[wg]);
                 }
                 if (mma_warp) __syncwarp();
+                // in flight during the MMAs and the epilogue: the next layer's
+                // activations, or the next round's inputs after the last layer
+                if (l - 1 >= a.dlo) {
+                    load_col(a.acts + static_cast<size_t>(l - 2) * a.act_stride, ti, h);
+                } else {
+                    load_col(a.acts + static_cast<size_t>(a.nh) * a.act_stride, tn, h);
+                    load_g(tn, gpre);
+                }
                 wait_or_abort(&accb[wg], phase, abort_flag, a.status);
                 phase ^= 1u;
                 tc_fence_after();
                 // epilogue: D_{l-1}^T row u = mask * (W_l^T D_l^T) row u
-                tmem_ld64(t_dl + lane_off, d);
                 dsum = 0.f;
 #pragma unroll
-                for (int r = 0; r < kR; ++r) {
-                    d[r] = ((mask >> r) & 1ull) ? d[r] : 0.f;
-                    dsum += d[r];
+                for (int qt = 0; qt < 4; ++qt) {
+                    float t[16];
+                    tmem_ld16(t_dl + lane_off + static_cast<uint32_t>(16 * qt), t);
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        t[r] = ((mask >> (16 * qt + r)) & 1ull) ? t[r] : 0.f;
+                        dsum += t[r];
+                    }
+                    if (l - 1 == 0) write_d0_q(t, qt, ti);
+                    if (l - 1 >= a.dlo || a.last_pass) write_dt_q(t, qt);
                 }
 #pragma unroll
                 for (int i = 1; i < 8; ++i)
                     if (i == l - 1 && i >= a.lo && i <= a.hi) db_acc[i] += dsum;
-                if (l - 1 >= a.dlo || a.last_pass) write_dt(d);
                 tc_fence_before();
             }
 
             // ---- layer 0: the gamma(mean) part of dW_0 and per-tile sums of D_0
             if (a.last_pass) {
-                if (tv) a.tilesum[static_cast<size_t>(tile) * WRF_HIDDEN + u] = dsum;
-                if (a.d0) {
-#pragma unroll
-                    for (int r = 0; r < kR; ++r)
-                        if (r < nvalid) a.d0[(row0 + r) * WRF_HIDDEN + u] = d[r];
-                }
-                if (leader) {
-                    // the gamma(mean) rows of the tile replace the H tile (the
-                    // MMAs that read it have completed)
-                    const size_t t0 = static_cast<size_t>(tv ? n0 / kR : 0) * kGt;
-                    mbar_arrive_expect_tx(&gbar[wg], 2 * kGt);
-                    bulk_g2s(Ht, a.gimg + t0, kGt, &gbar[wg]);
-                    bulk_g2s(Ht + kGt, a.gimg + a.gterm + t0, kGt, &gbar[wg]);
-                }
+                if (ti.tv) a.tilesum[static_cast<size_t>(ti.tile) * WRF_HIDDEN + u] = dsum;
                 fence_async_smem();
                 tc_fence_before();
                 named_bar(2 + wg, 128);
                 if (leader) {
-                    wait_or_abort(&gbar[wg], gphase, abort_flag, a.status);
-                    tc_fence_after();
+                    for (int w2 = 0; w2 < kWG; ++w2, ++g) {
+                        const int slot = static_cast<int>(g % kRing);
+                        wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
+                        if (w2 != wg) {
+                            mbar_arrive(&empty[slot]);  // the other warpgroup's tile
+                            continue;
+                        }
+                        tc_fence_after();
+                        const uint32_t ga = ring_a + static_cast<uint32_t>(slot) * kPanel;
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t ah = sw128_desc(dt_a + kk * 32u);
-                        const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
-                        const uint64_t bh = sw128_desc_lbo(ht_a + kk * 2048u, kHAtom, 1024u);
-                        const uint64_t bl = sw128_desc_lbo(ht_a + kGt + kk * 2048u, kHAtom, 1024u);
-                        mma_bf16(t_dl, ah, bh, id_dl, kk == 0 ? 0u : 1u);
-                        mma_bf16(t_dl, ah, bl, id_dl, 1u);
-                        mma_bf16(t_dl, al, bh, id_dl, 1u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            const uint64_t ah = sw128_desc(dt_a + kk * 32u);
+                            const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
+                            const uint64_t bh = sw128_desc_lbo(ga + kk * 2048u, kMnLbo, 1024u);
+                            const uint64_t bl = sw128_desc_lbo(ga + kGt + kk * 2048u, kMnLbo, 1024u);
+                            mma_bf16(t_dl, ah, bh, id_dl, kk == 0 ? 0u : 1u);
+                            mma_bf16(t_dl, ah, bl, id_dl, 1u);
+                            mma_bf16(t_dl, al, bh, id_dl, 1u);
+                        }
+                        mma_commit(&empty[slot]);
                     }
                     mma_commit(&accb[wg]);
                 }
-                gphase ^= 1u;
                 if (mma_warp) __syncwarp();
                 wait_or_abort(&accb[wg], phase, abort_flag, a.status);
                 phase ^= 1u;
                 tc_fence_after();
-                tmem_ld64(t_dl + lane_off, d);
-                tc_fence_before();
-                if (!*abort_flag) {
-                    float *pw = a.pdw0 + (static_cast<size_t>(blockIdx.x) * kWG + wg) * kGammaF * 128;
 #pragma unroll
-                    for (int f = 0; f < kGammaF; ++f)
-                        if (f < a.dm) pw[f * 128 + u] += d[f];
+                for (int qt = 0; qt < 2; ++qt) {
+                    float t[16];
+                    tmem_ld16(t_dl + lane_off + static_cast<uint32_t>(16 * qt), t);
+#pragma unroll
+                    for (int f = 0; f < 16; ++f) gacc[16 * qt + f] += t[f];
                 }
+                if (a.dm > 32) {
+                    float *pw =
+                        a.pdw0 + (static_cast<size_t>(blockIdx.x) * kWG + wg) * kGammaF * 128;
+                    for (int qt = 2; qt < 4; ++qt) {
+                        float t[16];
+                        tmem_ld16(t_dl + lane_off + static_cast<uint32_t>(16 * qt), t);
+                        if (!*abort_flag) {
+#pragma unroll
+                            for (int f = 0; f < 16; ++f)
+                                if (16 * qt + f < a.dm) pw[(16 * qt + f) * 128 + u] += t[f];
+                        }
+                    }
+                }
+                tc_fence_before();
             }
             named_bar(2 + wg, 128);  // tiles and TMEM columns are free for the next round
-            if (have_dw && ((round + 1) % kFlush == 0 || round + 1 == rounds)) {
-                named_bar(1, kWG * 128);  // every MMA into the dW accumulators is complete
+            // Every kFlush rounds both warpgroups meet: the dW accumulators are
+            // added into the CTA's partial, and a timed-out wait anywhere (after
+            // which every wait returns at once) ends the loop for all threads
+            // together.
+            if ((round + 1) % kFlush == 0 || round + 1 == rounds) {
+                // every MMA into the dW accumulators is complete past this point
+                const bool stop = wg_bar_any(1, *abort_flag != 0, kWG * 128);
                 tc_fence_after();
-                if (!*abort_flag) flush_dw();
+                if (!stop && have_dw) flush_dw();
                 tc_fence_before();
                 named_bar(1, kWG * 128);
                 tc_fence_after();
+                if (stop) break;
             }
         }
         // per-thread sums of this warpgroup
@@ -497,6 +595,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
             if (a.first_pass) {
                 for (int o = 0; o < WRF_OUT; ++o) a.pdwo[(cw * 8 + o) * 128 + u] += dwo[o];
                 if (u < WRF_OUT) a.pdwo[(cw * 8 + 5) * 128 + u] += dbo;
+            }
+            if (a.last_pass) {
+                float *pw = a.pdw0 + cw * kGammaF * 128;
+#pragma unroll
+                for (int f = 0; f < 32; ++f)
+                    if (f < a.dm) pw[f * 128 + u] += gacc[f];
             }
         }
     }
@@ -598,7 +702,8 @@ __global__ void bwd_reduce_kernel(MlpView m, int grid, int lo, int hi, int first
             const int oi = static_cast<int>(e % (128 * 128));
             float acc = 0.f;
             for (int c = 0; c < grid; ++c) acc += pdw[(static_cast<size_t>(c) * kSlots + s) * 128 * 128 + oi];
-            dW[hi - s][oi] += acc;  // W_l is [128 out][128 in]
+            // the partial holds dW_l^T [128 in][128 out]; W_l is [128 out][128 in]
+            dW[hi - s][(oi % 128) * 128 + oi / 128] += acc;
             continue;
         }
         long long f = e - n_dw;

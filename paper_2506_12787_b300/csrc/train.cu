@@ -18,6 +18,8 @@
 //      per-map SSIM.
 // Adam (the paper trains with PyTorch's Adam, learning rates in Table I):
 // one launch updates up to kAdamGroups parameter tensors.
+// Anneal smoothing (Eq. 17-18): the fine stage's noisy TX positions, gathered
+// from the training set in the same launch.
 #include "kernels.h"
 
 namespace wrf {
@@ -256,7 +258,33 @@ __global__ void adam_kernel(AdamArgs a) {
     }
 }
 
+// Eq. 17-18 anneal smoothing of the MLP's TX input: for row q,
+// out[q] = tx[idx[q]] + room_size * normals[q] * gamma (2 / cbrt(N_s)) (1 - i / tau)
+// while i < tau, else tx[idx[q]] (idx NULL: row q itself).
+__global__ void anneal_kernel(const float *tx, const int *idx, const float *normals, int Q,
+                              int iter, int n_pos, float gamma, int tau, float rx, float ry,
+                              float rz, float *out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
+    const int src = idx ? idx[q] : q;
+    const float scale = iter < tau ? gamma * (2.f / cbrtf(static_cast<float>(n_pos))) *
+                                         (1.f - static_cast<float>(iter) / static_cast<float>(tau))
+                                   : 0.f;
+    const float room[3] = {rx, ry, rz};
+    for (int c = 0; c < 3; ++c)
+        out[3 * q + c] = fmaf(room[c] * normals[3 * q + c], scale, tx[3 * src + c]);
+}
+
 }  // namespace
+
+cudaError_t launch_anneal(const float *tx, const int *idx, const float *normals, int Q, int iter,
+                          int n_pos, float gamma, int tau, const float *room_size, float *out,
+                          cudaStream_t st) {
+    if (Q == 0) return cudaSuccess;
+    anneal_kernel<<<(Q + 127) / 128, 128, 0, st>>>(tx, idx, normals, Q, iter, n_pos, gamma, tau,
+                                                   room_size[0], room_size[1], room_size[2], out);
+    return cudaGetLastError();
+}
 
 size_t loss_ws_layout(int Q, int H, int W, float **coef, float **part) {
     const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;

@@ -21,7 +21,6 @@ Random draws come from a torch.Generator the caller seeds, or are passed in.
 from __future__ import annotations
 
 import dataclasses
-import math
 
 import torch
 
@@ -45,13 +44,6 @@ class TrainConfig:
     eps: float = 1e-8
 
 
-def anneal_noise(normals: torch.Tensor, i: int, n_positions: int, gamma: float, tau: int):
-    """Eq. 18 on the unit-cube position: normals [..., 3] are N3(0,1) draws."""
-    if i >= tau:
-        return torch.zeros_like(normals)
-    return normals * (gamma * (2.0 / n_positions ** (1.0 / 3.0)) * (1.0 - i / tau))
-
-
 class Trainer:
     """Coarse-to-fine fitting of a scene and its deformation MLP to measured
     spectra (Sec. 4.4).
@@ -68,7 +60,6 @@ class Trainer:
         self.spec, self.cfg = spec, cfg
         self.tx_train, self.targets = tx_train, targets
         self.gen = generator
-        self.room_size = torch.tensor(spec.room_size, dtype=torch.float32, device=tx_train.device)
         self.state = {id(p): [torch.zeros_like(p), torch.zeros_like(p), 0]
                       for p in list(self.g.values()) + self.mlp}
         self.it = 0
@@ -77,13 +68,21 @@ class Trainer:
     def coarse(self) -> bool:
         return self.it < self.cfg.coarse_iters
 
-    def noise(self, Qb: int, normals=None):
-        """Metres added to the MLP's TX input at this fine-stage iteration."""
+    def noisy_tx(self, idx, normals=None):
+        """The MLP's TX input at this fine-stage iteration: the training
+        positions idx plus the Eq. 18 noise (wrf_anneal_tx), in metres."""
         if normals is None:
-            normals = torch.randn(Qb, 3, generator=self.gen).to(self.tx_train.device)
+            normals = torch.randn(int(idx.numel()), 3, generator=self.gen)
+        normals = normals.to(device=self.tx_train.device, dtype=torch.float32).contiguous()
         i = self.it - self.cfg.coarse_iters
-        return anneal_noise(normals, i, self.tx_train.shape[0], self.cfg.gamma,
-                            self.cfg.tau) * self.room_size
+        return api.wrf_anneal_tx(self.tx_train, normals, i, self.cfg.gamma, self.cfg.tau,
+                                 self.spec.room_size, idx=idx)
+
+    def noise(self, Qb: int, normals=None):
+        """Metres added to the MLP's TX input at this fine-stage iteration
+        (the noisy positions of rows 0 .. Qb-1 minus the positions)."""
+        idx = torch.arange(Qb, device=self.tx_train.device)
+        return self.noisy_tx(idx, normals) - self.tx_train[:Qb]
 
     def step(self, idx=None, normals=None):
         """One iteration; idx [B] (training positions) and normals [B,3] may be
@@ -92,10 +91,9 @@ class Trainer:
         if idx is None:
             idx = torch.randint(self.tx_train.shape[0], (c.batch,), generator=self.gen)
         idx = idx.to(self.tx_train.device)
-        tx, tgt = self.tx_train[idx], self.targets[idx]
+        tgt = self.targets[idx]
         coarse = self.coarse
-        if not coarse:
-            tx = tx + self.noise(int(idx.numel()), normals)
+        tx = self.noisy_tx(idx, normals) if not coarse else self.tx_train[idx]
         self.spec.stop_grad_mean = not coarse
         leaves = {k: v.detach().requires_grad_(coarse or k != "mean") for k, v in self.g.items()}
         params = [] if coarse else [p.detach().requires_grad_() for p in self.mlp]

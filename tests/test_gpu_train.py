@@ -177,7 +177,8 @@ def test_trainer_stages_and_noise(api):
         tr.it = it
         want = otrain.anneal_noise(z, it - 3, 24, 1.0, 10) * room
         got = tr.noise(8, T(z)).cpu().numpy()
-        assert np.allclose(got, want, rtol=1e-6, atol=1e-7)
+        # (tx + noise) - tx in FP32: a rounding of positions of a few metres
+        assert np.allclose(got, want, rtol=1e-6, atol=1e-6)
     tr.it = 3
     mean0 = gauss["mean"].clone()
     ls0 = gauss["log_scale"].clone()
@@ -186,6 +187,26 @@ def test_trainer_stages_and_noise(api):
     assert torch.equal(gauss["mean"], mean0), "fine stage moved the positions"
     assert not torch.equal(gauss["log_scale"], ls0)
     assert not all(torch.equal(a, b) for a, b in zip(mlp, mlp0))
+
+
+@pytest.mark.parametrize("it", [0, 1, 4999, 9999, 10000, 12000])
+def test_anneal_tx_matches_oracle(api, it):
+    """wrf_anneal_tx (Eq. 17-18): the minibatch of training positions plus
+    room_size * n_i, against the oracle's schedule; after tau the positions
+    come back unchanged (bit for bit)."""
+    rng = np.random.default_rng(it)
+    tx_np = synth.make_tx(40, seed=11)
+    idx = rng.integers(0, 40, 64)
+    z = rng.normal(size=(64, 3))
+    room = np.array([5.0, 5.0, 3.0])
+    out = api.wrf_anneal_tx(T(tx_np), T(z), it, 1.0, 10000, room, idx=torch.as_tensor(idx))
+    got = out.cpu().numpy().astype(np.float64)
+    want = tx_np[idx].astype(np.float64) + otrain.anneal_noise(z, it, 40, 1.0, 10000) * room
+    err = np.abs(got - want).max()
+    print(f"anneal iteration {it}: max |tx_out - oracle| {err:.2e} m")
+    assert err <= 1e-6
+    if it >= 10000:
+        assert np.array_equal(got, tx_np[idx].astype(np.float32).astype(np.float64))
 
 
 def test_training_reduces_the_loss(api):
