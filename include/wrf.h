@@ -203,6 +203,61 @@ wrf_status wrf_bin_noalloc(const float *rec, int32_t n, int32_t Q, const wrf_gri
                            uint32_t *gids, int64_t key_capacity, int64_t *n_keys_out,
                            uint32_t *tile_offsets, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Multi-scene batches.  Each scene is its own reference frame G^0 with its
+ * own deformation network (Sec. 4.2); a batch may hold queries of several
+ * resident scenes, and one launch sequence serves all of them:
+ *   wrf_multi_set_prepare (once)  ->  per batch: wrf_deform_project_multi,
+ *   wrf_bin_multi, wrf_render_multi.
+ * A query's records, tile lists and spectrum are exactly those of a
+ * single-scene launch of that query (wrf_deform_project with BF16, wrf_bin,
+ * wrf_render), whatever else the batch holds.
+ * Scenes: 1 <= S <= 16, one channel each; every network BF16 (tensor
+ * cores) with the same n_layers, bands and room (their weights differ).    */
+enum { WRF_MAX_SCENES = 16 };
+
+/* The prepared scene set: per scene the BF16 gamma(mean) rows and weight
+ * images of the tensor-core network, and a device table of the scenes, in
+ * `set` (device, 256-byte aligned, wrf_multi_set_size bytes).  The scenes'
+ * and networks' arrays must stay valid and unchanged while the set is used
+ * (prepare again after changing weights). */
+size_t wrf_multi_set_size(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S);
+wrf_status wrf_multi_set_prepare(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,
+                                 const wrf_grid *grid, void *set, size_t set_bytes,
+                                 void *stream);
+
+/* Deform + project a batch of Q queries: query q is TX position tx[q] in
+ * scene scene_of[q] (device int32 [Q]; an index outside [0, S) gives the
+ * query no Gaussians: it renders zeros).  Writes query_base (device int64
+ * [Q+1]): query q's records are rows query_base[q] .. query_base[q+1]-1 of
+ * rec (device, 16-byte aligned, room for rec_capacity records of 8 floats),
+ * in the order of its scene's Gaussians.  The offsets are computed on the
+ * device, so a captured graph serves any mix of scenes.  If the batch needs
+ * more than rec_capacity records, every query is emptied (no records) and
+ * the status word records WRF_ENOSPC.  scenes / mlps / S: the host arrays
+ * the set was prepared from.  ws: wrf_multi_workspace_size(Q) bytes.     */
+size_t wrf_multi_workspace_size(int32_t Q);
+wrf_status wrf_deform_project_multi(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,
+                                    const void *set, const int32_t *scene_of, const float *tx,
+                                    int32_t Q, const wrf_grid *grid, float *rec,
+                                    int64_t rec_capacity, int64_t *query_base, void *ws,
+                                    size_t ws_bytes, void *stream);
+
+/* wrf_bin over a multi-scene batch: query q's records are rows
+ * query_base[q] .. query_base[q+1]-1 of rec (at most n_max of them: the
+ * largest scene); gids index those rows (0 = query_base[q]).  Workspace:
+ * wrf_bin_workspace_size(n_max, Q, grid).  Other arguments as wrf_bin.     */
+wrf_status wrf_bin_multi(const float *rec, const int64_t *query_base, int32_t n_max, int32_t Q,
+                         const wrf_grid *grid, uint32_t *gids, int64_t key_capacity,
+                         int64_t *n_keys_out, uint32_t *tile_offsets, void *ws, size_t ws_bytes,
+                         void *stream);
+
+/* wrf_render over a multi-scene batch (records located by query_base). */
+wrf_status wrf_render_multi(const float *rec, const int64_t *query_base, const uint32_t *gids,
+                            const uint32_t *tile_offsets, const int64_t *n_keys,
+                            int64_t key_capacity, int32_t Q, const wrf_grid *grid, float *spectra,
+                            void *stream);
+
 /* Rasterisation, Eq. 9 / Eq. 13: A_q(y, x) = sum over the Gaussians listed
  * for the pixel's tile, ascending n, of [q <= q_cut] w exp(-q/2).  No depth
  * order, no transmittance, no clamping (order-free accumulation).

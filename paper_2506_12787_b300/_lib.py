@@ -30,7 +30,8 @@ EXPORTS = (
     "wrf_status_read", "wrf_last_error", "wrf_version", "wrf_selftest_wait", "wrf_rssi",
     "wrf_loss_workspace_size", "wrf_loss", "wrf_adam", "wrf_render_complex",
     "wrf_paper_workspace_size", "wrf_paper_deform_project", "wrf_measure_alu_peaks",
-    "wrf_anneal_tx",
+    "wrf_anneal_tx", "wrf_multi_set_size", "wrf_multi_set_prepare", "wrf_multi_workspace_size",
+    "wrf_deform_project_multi", "wrf_bin_multi", "wrf_render_multi",
 )
 
 
@@ -113,6 +114,12 @@ def load(path: str = LIB_PATH):
         "wrf_adam": (I32, [C.POINTER(AdamGroup), I32, I32, F, F, F, P]),
         "wrf_render_complex": (I32, [P, P, P, P, I64, I32, I32, gp, P, P]),
         "wrf_anneal_tx": (I32, [P, P, I32, P, I32, I32, F, I32, C.POINTER(C.c_float), P, P]),
+        "wrf_multi_set_size": (S, [sp, mp, I32]),
+        "wrf_multi_set_prepare": (I32, [sp, mp, I32, gp, P, S, P]),
+        "wrf_multi_workspace_size": (S, [I32]),
+        "wrf_deform_project_multi": (I32, [sp, mp, I32, P, P, P, I32, gp, P, I64, P, P, S, P]),
+        "wrf_bin_multi": (I32, [P, P, I32, I32, gp, P, I64, P, P, P, S, P]),
+        "wrf_render_multi": (I32, [P, P, P, P, P, I64, I32, gp, P, P]),
         "wrf_paper_workspace_size": (S, [I32, I32]),
         "wrf_measure_alu_peaks": (I32, [C.POINTER(C.c_double)] * 3 + [P]),
         "wrf_paper_deform_project": (I32, [C.POINTER(PaperScene), C.POINTER(PaperMlp), gp, P, I32,

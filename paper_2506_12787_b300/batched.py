@@ -158,6 +158,122 @@ class PaperForward(BatchedForward):
                                  stream=stream)
 
 
+class MultiSceneForward:
+    """One launch sequence over a batch of up to Q queries of several
+    resident scenes (each its own Gaussians and BF16 deformation network).
+
+    The scene set is prepared once (per-scene gamma(mean) rows and weight
+    images on the device); a batch is the device buffers scene_of [Q]
+    (int32; -1 for an unused slot, which renders zeros) and tx [Q,3].  The
+    record offsets of the queries are computed on the device, so one captured
+    graph serves every mix of scenes.  A query's spectrum equals the spectrum
+    of the same query run alone through BatchedForward of its scene."""
+
+    # kernels one run() launches: setup, per-query term, MLP; binning's five;
+    # render
+    launches_per_run = 9
+
+    def __init__(self, scenes, mlps, grid, Q: int, device="cuda", key_capacity: int = 0,
+                 margin: float = 1.25, rec_capacity: int | None = None):
+        assert len(scenes) == len(mlps) and 1 <= len(scenes) <= 16
+        self.scenes, self.mlps, self.grid, self.Q = list(scenes), list(mlps), grid, int(Q)
+        self.device = torch.device(device)
+        self.margin = margin
+        L = _lib.load()
+        S = len(scenes)
+        self.S = S
+        self._sc = (_lib.Scene * S)(*[sc.c() for sc in scenes])
+        self._mc = (_lib.Mlp * S)(*[m.c() for m in mlps])
+        nset = L.wrf_multi_set_size(self._sc, self._mc, S)
+        if nset == 0:
+            raise _lib.WrfError(_lib.WRF_EINVAL, L.wrf_last_error().decode())
+        self.set = torch.empty(nset, dtype=torch.uint8, device=self.device)
+        _lib.check(L.wrf_multi_set_prepare(self._sc, self._mc, S, C.byref(grid),
+                                           _p(self.set), nset, _stream(None)))
+        self.n_max = max(sc.n for sc in scenes)
+        self.rec_cap = int(rec_capacity) if rec_capacity is not None else self.Q * self.n_max
+        self.rec = torch.empty((max(self.rec_cap, 1), 8), dtype=torch.float32, device=self.device)
+        self.qbase = torch.zeros(self.Q + 1, dtype=torch.int64, device=self.device)
+        self.scene_of = torch.full((self.Q,), -1, dtype=torch.int32, device=self.device)
+        self.tx = torch.zeros((self.Q, 3), dtype=torch.float32, device=self.device)
+        self.mws = torch.empty(max(256, L.wrf_multi_workspace_size(self.Q)), dtype=torch.uint8,
+                               device=self.device)
+        self.bws = torch.empty(max(256, L.wrf_bin_workspace_size(self.n_max, self.Q,
+                                                                 C.byref(grid))),
+                               dtype=torch.uint8, device=self.device)
+        self.T = tiles_of(grid)
+        self.n_keys = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.offs = torch.empty(self.Q * self.T + 1, dtype=torch.int32, device=self.device)
+        self.out = torch.empty((self.Q, grid.H, grid.W), dtype=torch.float32, device=self.device)
+        self.cap = 0
+        self.gids = None
+        self._alloc_keys(int(key_capacity))
+
+    def _alloc_keys(self, cap: int):
+        cap = max(int(cap), 1024)
+        if cap > self.cap:
+            self.gids = torch.empty(cap, dtype=torch.int32, device=self.device)
+            self.cap = cap
+
+    def set_batch(self, scene_of, tx):
+        """Copy a batch (scene indices [<=Q], TX [<=Q,3]) into the device
+        buffers; slots past it are unused (-1)."""
+        k = int(len(scene_of))
+        self.scene_of.fill_(-1)
+        self.scene_of[:k].copy_(torch.as_tensor(scene_of, dtype=torch.int32), non_blocking=True)
+        self.tx[:k].copy_(torch.as_tensor(tx, dtype=torch.float32), non_blocking=True)
+
+    def run(self, stream=None, out=None):
+        """Enqueue one forward of the batch in scene_of / tx on `stream`."""
+        L = _lib.load()
+        st = _stream(stream)
+        _lib.check(L.wrf_deform_project_multi(
+            self._sc, self._mc, self.S, _p(self.set), _p(self.scene_of), _p(self.tx), self.Q,
+            C.byref(self.grid), _p(self.rec), self.rec_cap, _p(self.qbase), _p(self.mws),
+            self.mws.numel(), st))
+        _lib.check(L.wrf_bin_multi(_p(self.rec), _p(self.qbase), self.n_max, self.Q,
+                                   C.byref(self.grid), _p(self.gids), self.cap, _p(self.n_keys),
+                                   _p(self.offs), _p(self.bws), self.bws.numel(), st))
+        out = self.out if out is None else out
+        _lib.check(L.wrf_render_multi(_p(self.rec), _p(self.qbase), _p(self.gids), _p(self.offs),
+                                      _p(self.n_keys), self.cap, self.Q, C.byref(self.grid),
+                                      _p(out), st))
+        return out
+
+    def reserve(self, stream=None) -> int:
+        """Run the current batch once and grow the key capacity to the
+        count it needs times the margin."""
+        self.run(stream)
+        st = stream or torch.cuda.current_stream()
+        st.synchronize()
+        need = int(self.n_keys.item())
+        wrf_status_read(stream)
+        if need > self.cap:
+            self._alloc_keys(int(need * self.margin) + 1024)
+            self.run(stream)
+            st.synchronize()
+        return need
+
+    def check(self, stream=None):
+        s = wrf_status_read(stream)
+        if s != 0:
+            raise _lib.WrfError(s, f"device status (n_keys={int(self.n_keys.item())}, "
+                                   f"capacity={self.cap})")
+
+    def graph(self, stream=None, out=None):
+        """Capture run() into a CUDA graph: it reads whatever batch scene_of /
+        tx hold at replay."""
+        g = torch.cuda.CUDAGraph()
+        s = stream or torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.run(s, out)
+        torch.cuda.current_stream().wait_stream(s)
+        with torch.cuda.graph(g, stream=s):
+            self.run(s, out)
+        return g
+
+
 class HostPipeline:
     """Spectra for TX batches held in host memory, with the copies overlapped
     with compute: step i's TX upload and forward run on the compute stream

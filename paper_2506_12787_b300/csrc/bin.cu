@@ -29,11 +29,28 @@ constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanBlock = kScanThreads * kScanItems;  // 4096
 
+// Records of query q: n per query at q n, or (multi-scene batches, qbase
+// non-NULL) qbase[q+1] - qbase[q] starting at qbase[q].
+__device__ __forceinline__ void query_records(const long long *qbase, int n, int q, int &nq,
+                                              size_t &base) {
+    if (qbase) {
+        const long long b0 = qbase[q];
+        nq = static_cast<int>(qbase[q + 1] - b0);
+        base = static_cast<size_t>(b0);
+    } else {
+        nq = n;
+        base = static_cast<size_t>(q) * n;
+    }
+}
+
 template <bool WRAP, int CHUNK>
 __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n, GridView g,
-                                                        int C, uint32_t *counts, int *status) {
+                                                        int C, uint32_t *counts, int *status,
+                                                        const long long *qbase) {
     extern __shared__ uint32_t hist[];
     const int c = blockIdx.x, q = blockIdx.y;
+    size_t qb;
+    query_records(qbase, n, q, n, qb);
     for (int t = threadIdx.x; t < g.T; t += blockDim.x) hist[t] = 0;
     __syncthreads();
     // all of this thread's records are requested before any is used
@@ -43,7 +60,7 @@ __global__ void __launch_bounds__(256) bin_count_kernel(const float4 *rec, int n
     for (int i = 0; i < kPer; ++i) {
         const int id = c * CHUNK + i * 256 + threadIdx.x;
         if (id < n) {
-            const size_t r = static_cast<size_t>(q) * n + id;
+            const size_t r = qb + id;
             ra[i] = rec[2 * r];
             rb[i] = rec[2 * r + 1];
         }
@@ -166,7 +183,8 @@ template <bool WRAP, int CHUNK>
 __global__ void __launch_bounds__(CHUNK, 2048 / CHUNK) bin_scatter_kernel(const float4 *rec, int n, GridView g,
                                                            int C, const uint32_t *excl,
                                                            uint32_t *gids, long long cap,
-                                                           const long long *n_keys) {
+                                                           const long long *n_keys,
+                                                           const long long *qbase) {
     extern __shared__ __align__(16) uint32_t sm[];
     constexpr int kScatterWarps = CHUNK / 32;
     uint32_t *colmask = sm;                                        // [warps][ntx]
@@ -174,11 +192,13 @@ __global__ void __launch_bounds__(CHUNK, 2048 / CHUNK) bin_scatter_kernel(const 
     uint32_t *base = rowmask + kScatterWarps * g.nty;              // [T]
     uint16_t *woff = reinterpret_cast<uint16_t *>(base + g.T);     // [warps][T]
     const int c = blockIdx.x, q = blockIdx.y;
+    size_t qb;
+    query_records(qbase, n, q, n, qb);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int id = c * CHUNK + threadIdx.x;
     float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
     if (id < n) {
-        const size_t r = static_cast<size_t>(q) * n + id;
+        const size_t r = qb + id;
         a = rec[2 * r];
         b = rec[2 * r + 1];
     }
@@ -245,11 +265,12 @@ size_t scatter_smem(const GridView &g) {
 template <int CHUNK>
 cudaError_t launch_count_scatter(int phase, const float4 *rec, int n, int Q, const GridView &g,
                                  uint32_t *gids, long long cap, const long long *n_keys,
-                                 const BinWs &ws, int *status, cudaStream_t st) {
+                                 const BinWs &ws, int *status, const long long *qbase,
+                                 cudaStream_t st) {
     dim3 grid(ws.C, Q);
     if (phase == 0) {
         auto kern = g.wrap ? bin_count_kernel<true, CHUNK> : bin_count_kernel<false, CHUNK>;
-        kern<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts, status);
+        kern<<<grid, 256, g.T * 4, st>>>(rec, n, g, ws.C, ws.chunk_counts, status, qbase);
         return cudaGetLastError();
     }
     const size_t smem = scatter_smem(g);
@@ -257,16 +278,18 @@ cudaError_t launch_count_scatter(int phase, const float4 *rec, int n, int Q, con
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<grid, CHUNK, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap, n_keys);
+    kern<<<grid, CHUNK, smem, st>>>(rec, n, g, ws.C, ws.chunk_counts, gids, cap, n_keys, qbase);
     return cudaGetLastError();
 }
 
 cudaError_t count_scatter(int phase, const float4 *rec, int n, int Q, const GridView &g,
                           uint32_t *gids, long long cap, const long long *n_keys, const BinWs &ws,
-                          int *status, cudaStream_t st) {
+                          int *status, const long long *qbase, cudaStream_t st) {
     return bin_chunk(g) == 512
-               ? launch_count_scatter<512>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status, st)
-               : launch_count_scatter<1024>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
+               ? launch_count_scatter<512>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status,
+                                           qbase, st)
+               : launch_count_scatter<1024>(phase, rec, n, Q, g, gids, cap, n_keys, ws, status,
+                                            qbase, st);
 }
 
 }  // namespace
@@ -291,10 +314,10 @@ bool bin_grid_supported(const GridView &g) { return scatter_smem(g) <= 200 * 102
 
 cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint32_t *gids,
                        long long cap, long long *n_keys, uint32_t *offsets, const BinWs &ws,
-                       int *status, cudaStream_t st) {
+                       int *status, cudaStream_t st, const long long *qbase) {
     if (Q == 0) return cudaSuccess;
     if (n > 0) {
-        cudaError_t e = count_scatter(0, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
+        cudaError_t e = count_scatter(0, rec, n, Q, g, gids, cap, n_keys, ws, status, qbase, st);
         if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = cudaMemsetAsync(ws.chunk_counts, 0, static_cast<size_t>(ws.M) * 4, st);
@@ -306,7 +329,7 @@ cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint3
                                                          ws.C, offsets,
                                                          static_cast<long long>(Q) * g.T, n_keys);
     if (n > 0) {
-        cudaError_t e = count_scatter(1, rec, n, Q, g, gids, cap, n_keys, ws, status, st);
+        cudaError_t e = count_scatter(1, rec, n, Q, g, gids, cap, n_keys, ws, status, qbase, st);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();

@@ -574,6 +574,162 @@ wrf_status wrf_bin_noalloc(const float *rec, int32_t n, int32_t Q, const wrf_gri
                    kBinScratchBytes, stream);
 }
 
+// ------------------------------------------------------ multi-scene batches
+static wrf_status check_multi(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,
+                              wrf::SceneView *sv, wrf::MlpView *mv) {
+    if (!scenes || !mlps) return fail(WRF_EINVAL, "scenes / mlps is NULL");
+    if (S < 1 || S > wrf::kMaxScenes)
+        return fail(WRF_EUNSUPPORTED, "multi-scene: 1 <= S <= %d scenes", wrf::kMaxScenes);
+    wrf_status s;
+    for (int i = 0; i < S; ++i) {
+        if ((s = check_scene(&scenes[i])) != WRF_OK) return s;
+        if (scenes[i].channels != 1)
+            return fail(WRF_EUNSUPPORTED, "multi-scene: one channel per scene");
+        if ((s = check_mlp(&mlps[i], &mv[i])) != WRF_OK) return s;
+        if (mlps[i].precision != WRF_BF16)
+            return fail(WRF_EUNSUPPORTED, "multi-scene: BF16 tensor-core MLPs");
+        const wrf_mlp &a = mlps[0], &b = mlps[i];
+        bool same = a.n_layers == b.n_layers && a.L_mean == b.L_mean && a.L_tx == b.L_tx;
+        for (int k = 0; k < 3; ++k)
+            same = same && a.room_min[k] == b.room_min[k] && a.room_size[k] == b.room_size[k];
+        if (!same)
+            return fail(WRF_EUNSUPPORTED,
+                        "multi-scene: every scene's MLP has the same layers, bands and room");
+        sv[i] = view(&scenes[i]);
+    }
+    return WRF_OK;
+}
+
+size_t wrf_multi_set_size(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S) {
+    wrf::SceneView sv[wrf::kMaxScenes];
+    wrf::MlpView mv[wrf::kMaxScenes];
+    if (check_multi(scenes, mlps, S, sv, mv) != WRF_OK) return 0;
+    return wrf::multi_set_layout(sv, S, mlps[0].n_layers, wrf::mlp_k1(mv[0].dm), nullptr,
+                                 nullptr);
+}
+
+wrf_status wrf_multi_set_prepare(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,
+                                 const wrf_grid *grid, void *set, size_t set_bytes,
+                                 void *stream) {
+    wrf::SceneView sv[wrf::kMaxScenes];
+    wrf::MlpView mv[wrf::kMaxScenes];
+    wrf::GridView g{};
+    wrf_status s;
+    if ((s = check_multi(scenes, mlps, S, sv, mv)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    const size_t need = wrf::multi_set_layout(sv, S, mlps[0].n_layers, wrf::mlp_k1(mv[0].dm),
+                                              nullptr, nullptr);
+    if (!set || set_bytes < need || !aligned(set, 256))
+        return fail(WRF_EINVAL, "scene set: need %zu bytes, 256-byte aligned", need);
+    wrf::MultiSet ms{};
+    wrf::multi_set_layout(sv, S, mlps[0].n_layers, wrf::mlp_k1(mv[0].dm), &ms,
+                          static_cast<char *>(set));
+    cudaError_t e = wrf::launch_multi_prepare(sv, mv, S, g, ms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "multi-scene prepare");
+    return WRF_OK;
+}
+
+size_t wrf_multi_workspace_size(int32_t Q) {
+    return wrf::multi_ws_layout(Q < 0 ? 0 : Q, nullptr, nullptr);
+}
+
+wrf_status wrf_deform_project_multi(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,
+                                    const void *set, const int32_t *scene_of, const float *tx,
+                                    int32_t Q, const wrf_grid *grid, float *rec,
+                                    int64_t rec_capacity, int64_t *query_base, void *ws,
+                                    size_t ws_bytes, void *stream) {
+    wrf::SceneView sv[wrf::kMaxScenes];
+    wrf::MlpView mv[wrf::kMaxScenes];
+    wrf::GridView g{};
+    wrf_status s;
+    if ((s = check_multi(scenes, mlps, S, sv, mv)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0 || Q > 65535) return fail(WRF_EUNSUPPORTED, "multi-scene: 0 <= Q <= 65535");
+    if (rec_capacity < 0) return fail(WRF_EINVAL, "rec_capacity < 0");
+    if (!query_base) return fail(WRF_EINVAL, "query_base is NULL");
+    if (Q == 0) {
+        cudaError_t e = cudaMemsetAsync(query_base, 0, sizeof(int64_t),
+                                        static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return cuda_fail(e, "multi-scene (Q = 0)");
+        return WRF_OK;
+    }
+    if (!set || !aligned(set, 256) || !scene_of || !tx)
+        return fail(WRF_EINVAL, "set / scene_of / tx is NULL (or set not 256-byte aligned)");
+    if (rec_capacity > 0 && (!rec || !aligned(rec, 16)))
+        return fail(WRF_EINVAL, "rec must be non-NULL and 16-byte aligned");
+    const size_t need = wrf::multi_ws_layout(Q, nullptr, nullptr);
+    if (!ws || ws_bytes < need || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    wrf::MultiSet ms{};
+    wrf::multi_set_layout(sv, S, mlps[0].n_layers, wrf::mlp_k1(mv[0].dm), &ms,
+                          static_cast<char *>(const_cast<void *>(set)));
+    wrf::MultiWs w{};
+    wrf::multi_ws_layout(Q, &w, static_cast<char *>(ws));
+    cudaError_t e = wrf::launch_deform_project_multi(
+        ms, S, mv[0], g, scene_of, tx, Q, reinterpret_cast<float4 *>(rec), rec_capacity,
+        reinterpret_cast<long long *>(query_base), w, status_ptr(),
+        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "deform_project_multi");
+    return WRF_OK;
+}
+
+wrf_status wrf_bin_multi(const float *rec, const int64_t *query_base, int32_t n_max, int32_t Q,
+                         const wrf_grid *grid, uint32_t *gids, int64_t key_capacity,
+                         int64_t *n_keys_out, uint32_t *tile_offsets, void *ws, size_t ws_bytes,
+                         void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (n_max < 0 || Q < 0 || key_capacity < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (!rows_ok(n_max, Q)) return fail(WRF_EUNSUPPORTED, "Q*n_max must be < 2^31");
+    if (!n_keys_out || !tile_offsets) return fail(WRF_EINVAL, "n_keys_out / tile_offsets NULL");
+    if (Q > 0 && !query_base) return fail(WRF_EINVAL, "query_base is NULL");
+    if (n_max > 0 && Q > 0 && (!rec || !aligned(rec, 16))) return fail(WRF_EINVAL, "rec alignment");
+    if (key_capacity > 0 && !gids) return fail(WRF_EINVAL, "gids is NULL");
+    size_t need = wrf::bin_ws_layout(n_max, Q, g, nullptr, nullptr);
+    if (ws_bytes < need || !ws || !aligned(ws, 256))
+        return fail(WRF_EINVAL, "workspace: need %zu bytes, 256-byte aligned", need);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (Q == 0) {
+        cudaError_t e = cudaMemsetAsync(n_keys_out, 0, sizeof(int64_t), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tile_offsets, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return cuda_fail(e, "bin_multi (Q = 0)");
+        return WRF_OK;
+    }
+    wrf::BinWs w{};
+    wrf::bin_ws_layout(n_max, Q, g, &w, static_cast<char *>(ws));
+    cudaError_t e = wrf::launch_bin(reinterpret_cast<const float4 *>(rec), n_max, Q, g, gids,
+                                    key_capacity, reinterpret_cast<long long *>(n_keys_out),
+                                    tile_offsets, w, status_ptr(), st,
+                                    reinterpret_cast<const long long *>(query_base));
+    if (e != cudaSuccess) return cuda_fail(e, "bin_multi");
+    return WRF_OK;
+}
+
+wrf_status wrf_render_multi(const float *rec, const int64_t *query_base, const uint32_t *gids,
+                            const uint32_t *tile_offsets, const int64_t *n_keys,
+                            int64_t key_capacity, int32_t Q, const wrf_grid *grid, float *spectra,
+                            void *stream) {
+    wrf_status s;
+    wrf::GridView g{};
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 0) return fail(WRF_EINVAL, "negative size");
+    if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
+    if (Q == 0) return WRF_OK;
+    if (!query_base || !tile_offsets || !n_keys || !spectra)
+        return fail(WRF_EINVAL, "NULL pointer");
+    if (!aligned(spectra, 16) || (rec && !aligned(rec, 16)))
+        return fail(WRF_EINVAL, "spectra / rec must be 16-byte aligned");
+    cudaError_t e = wrf::launch_render(reinterpret_cast<const float4 *>(rec), gids, tile_offsets,
+                                       reinterpret_cast<const long long *>(n_keys), key_capacity,
+                                       0, Q, g, spectra, status_ptr(),
+                                       static_cast<cudaStream_t>(stream),
+                                       reinterpret_cast<const long long *>(query_base));
+    if (e != cudaSuccess) return cuda_fail(e, "render_multi");
+    return WRF_OK;
+}
+
 wrf_status wrf_render(const float *rec, const uint32_t *gids, const uint32_t *tile_offsets,
                       const int64_t *n_keys, int64_t key_capacity, int32_t n, int32_t Q,
                       const wrf_grid *grid, float *spectra, void *stream) {

@@ -48,6 +48,17 @@ inline __host__ __device__ int mlp_k1(int dm) { return dm <= 32 ? 32 : 64; }
 
 size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base);
 
+// A resident scene of a multi-scene batch: its Gaussians, its BF16
+// gamma(mean) rows and weight images (prepared once), and its first layer in
+// FP32 (for the per-query term).
+struct SceneEntry {
+    SceneView s;
+    const uint16_t *G;       // [n][k1]
+    const uint16_t *w_img;   // W1m, hidden layers, output, bias image, selectors
+    const float *W0, *b0;
+};
+constexpr int kMaxScenes = 16;
+
 cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
                         int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st);
 
@@ -58,6 +69,30 @@ cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView 
 cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                           const DeformWs &ws, int mode, float *resid, float4 *rec,
                           uint32_t *count, int *status, cudaStream_t st);
+
+// Multi-scene batches (multi.cu): query q of scene scene_of[q] (-1: none).
+struct MultiSet {           // a prepared scene set (caller-owned device memory)
+    SceneEntry *table;      // [kMaxScenes]
+    float *wt_scratch, *wo_scratch;
+    uint16_t *G[kMaxScenes], *img[kMaxScenes];
+};
+struct MultiWs {            // per-batch scratch
+    int *tstart;            // [Q+1] 128-row MLP tile ranges
+    float *V;               // [Q][128] per-query layer-1 terms
+};
+size_t multi_set_layout(const SceneView *s, int S, int n_layers, int k1, MultiSet *ms, char *base);
+cudaError_t launch_multi_prepare(const SceneView *s, const MlpView *m, int S, const GridView &g,
+                                 const MultiSet &ms, cudaStream_t st);
+size_t multi_ws_layout(int Q, MultiWs *mw, char *base);
+cudaError_t launch_deform_project_multi(const MultiSet &ms, int S, const MlpView &m,
+                                        const GridView &g, const int *scene_of, const float *tx,
+                                        int Q, float4 *rec, long long rec_capacity,
+                                        long long *qbase, const MultiWs &w, int *status,
+                                        cudaStream_t st);
+cudaError_t launch_mlp_tc_multi(const SceneEntry *table, const MlpView &m, const GridView &g,
+                                int Q, const int *scene_of, const long long *qbase,
+                                const int *tstart, const float *V, float4 *rec, int *status,
+                                cudaStream_t st);
 
 cudaError_t launch_project(const SceneView &s, const float *resid, int Q, const GridView &g,
                            float4 *rec, uint32_t *count, cudaStream_t st);
@@ -124,14 +159,17 @@ struct BinWs {
     int nblocks;
 };
 size_t bin_ws_layout(int n, int Q, const GridView &g, BinWs *ws, char *base);
+// qbase (multi-scene batches, else NULL): query q's records start at
+// qbase[q] and number qbase[q+1] - qbase[q] (<= n, the chunked maximum).
 cudaError_t launch_bin(const float4 *rec, int n, int Q, const GridView &g, uint32_t *gids,
                        long long cap, long long *n_keys, uint32_t *offsets, const BinWs &ws,
-                       int *status, cudaStream_t st);
+                       int *status, cudaStream_t st, const long long *qbase = nullptr);
 
 // Rasteriser.
 cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                           const long long *n_keys, long long cap, int n, int Q,
-                          const GridView &g, float *out, int *status, cudaStream_t st);
+                          const GridView &g, float *out, int *status, cudaStream_t st,
+                          const long long *qbase = nullptr);
 // Two channels (records followed by [Q][N] imaginary weights): out
 // [Q][2][H][W] = magnitude, phase.
 cudaError_t launch_render_complex(const float4 *rec, const uint32_t *gids,

@@ -66,6 +66,13 @@ struct TcArgs {
     uint32_t *count;
     float *rec_im;           // two channels: imaginary weights after the records
     int *status;
+    // multi-scene batches (MULTI): query q belongs to scene scene_of[q] of the
+    // table; its records start at qbase[q]; its 128-row tiles are
+    // tstart[q] .. tstart[q+1]-1 of the launch (tstart[Q] tiles in all)
+    const SceneEntry *table;
+    const int *scene_of;
+    const long long *qbase;
+    const int *tstart;
 };
 
 constexpr size_t smem_bytes(int nh) {
@@ -74,6 +81,49 @@ constexpr size_t smem_bytes(int nh) {
 }
 static_assert(smem_bytes(3) <= 227 * 1024, "shared memory of one CTA");
 
+// The tile of a launch: query q, Gaussians n0 .. n0+127 of its scene, the
+// scene's Gaussians and gamma(mean) rows, and where its records go.
+struct TcTile {
+    int q, n0, nq;
+    long long rbase;  // record index of (q, Gaussian 0)
+    SceneView s;
+    const uint16_t *G;
+};
+
+// Query of tile t (MULTI): the last q with tstart[q] <= t.
+__device__ __forceinline__ int tile_query(const int *tstart, int Q, int t) {
+    int lo = 0, hi = Q - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tstart + mid) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <bool MULTI>
+__device__ __forceinline__ TcTile tile_info(const TcArgs &a, int tile) {
+    TcTile t;
+    if (!MULTI) {
+        t.q = tile / a.tpq;
+        t.n0 = (tile % a.tpq) * kTileRows;
+        t.nq = a.N;
+        t.rbase = static_cast<long long>(t.q) * a.N;
+        t.s = a.s;
+        t.G = a.G;
+    } else {
+        t.q = tile_query(a.tstart, a.Q, tile);
+        t.n0 = (tile - __ldg(a.tstart + t.q)) * kTileRows;
+        const SceneEntry &e = a.table[__ldg(a.scene_of + t.q)];
+        t.s = e.s;
+        t.nq = e.s.n;
+        t.rbase = __ldg(a.qbase + t.q);
+        t.G = e.G;
+    }
+    return t;
+}
+
+template <bool MULTI>
 __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned base (128-byte swizzle atoms must be 1024-aligned)
@@ -103,16 +153,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    if (tid == 0) {
-        mbar_arrive_expect_tx(&bars[0], w_bytes);
-        const uint8_t *src = reinterpret_cast<const uint8_t *>(a.w_img);
-        for (uint32_t off = 0; off < w_bytes; off += 16384u) {
-            uint32_t len = w_bytes - off < 16384u ? w_bytes - off : 16384u;
-            bulk_g2s(wsm + off, src + off, len, &bars[0]);
+    // the weights (and bias images) into shared memory; every thread waits
+    uint32_t wphase = 0;
+    auto load_weights = [&](const uint16_t *img) {
+        if (tid == 0) {
+            mbar_arrive_expect_tx(&bars[0], w_bytes);
+            const uint8_t *src = reinterpret_cast<const uint8_t *>(img);
+            for (uint32_t off = 0; off < w_bytes; off += 16384u) {
+                uint32_t len = w_bytes - off < 16384u ? w_bytes - off : 16384u;
+                bulk_g2s(wsm + off, src + off, len, &bars[0]);
+            }
         }
-    }
-    wait_or_abort(&bars[0], 0, abort_flag, a.status);
-    __syncthreads();
+        wait_or_abort(&bars[0], wphase, abort_flag, a.status);
+        wphase ^= 1u;
+        __syncthreads();
+    };
+    if (!MULTI) load_weights(a.w_img);
 
     uint64_t *mbar = &bars[1 + wg];
     uint32_t phase = 0;
@@ -139,26 +195,26 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     uint4 gpre[8];
     float vpre = 0.f;     // this thread's column of V[q] for the next tile
     GaussParams ppre{};  // this thread's Gaussian for the next tile (projection epilogue)
-    auto load_g = [&](int tile) {
-        const int nb = tile % a.tpq;
-        const int n = nb * kTileRows + my_row;
-        const bool ok = tile < a.ntiles && n < a.N;
-        if (tile < a.ntiles) vpre = __ldg(a.V + static_cast<size_t>(tile / a.tpq) * 128 + wt);
-        if (ok && a.mode == 1) ppre = load_params(a.s, n);
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.G + static_cast<size_t>(ok ? n : 0) * a.k1);
+    auto load_g = [&](int tile, bool have) {
+        if (!have) return;
+        const TcTile ti = tile_info<MULTI>(a, tile);
+        const int n = ti.n0 + my_row;
+        const bool ok = n < ti.nq;
+        vpre = __ldg(a.V + static_cast<size_t>(ti.q) * 128 + wt);
+        if (ok && a.mode == 1) ppre = load_params(ti.s, n);
+        const uint4 *src =
+            reinterpret_cast<const uint4 *>(ti.G + static_cast<size_t>(ok ? n : 0) * a.k1);
 #pragma unroll
         for (int c = 0; c < 8; ++c)
             gpre[c] = (ok && c < nch) ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
     };
-    int tile = blockIdx.x * kWG + wg;
-    load_g(tile);
 
-    for (; tile < a.ntiles; tile += stride) {
-        // uniform per warpgroup: a timed-out wait anywhere ends the loop for
-        // all 128 threads together (no thread is left at a named barrier)
-        if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
-        const int q = tile / a.tpq;
-        const int n = (tile % a.tpq) * kTileRows + my_row;
+    // one tile: layer 1 from the prefetched operands, the hidden layers, the
+    // output layer and its epilogue; prefetches tile `next` (if has_next)
+    auto run_tile = [&](int tile, int next, bool has_next) {
+        const TcTile ti = tile_info<MULTI>(a, tile);
+        const int q = ti.q;
+        const int n = ti.n0 + my_row;
         // ---- layer 1 operand: gamma(mean_n) row -> A columns 0..k1-1
 #pragma unroll
         for (int c = 0; c < 8; ++c)
@@ -173,7 +229,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 make_uint4(hi | (lo << 16), 0u, 0u, 0u);
         }
         const GaussParams pcur = ppre;
-        load_g(tile + stride);
+        load_g(next, has_next);
         fence_async_smem();
         named_bar(1 + wg, 128);
 
@@ -244,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         float o[16];
         tmem_ld16(t_acc + lane_off, o);
         tc_fence_before();
-        if (n < a.N && !*abort_flag) {
-            const long long row = static_cast<long long>(q) * a.N + n;
+        if (n < ti.nq && !*abort_flag) {
+            const long long row = ti.rbase + n;
             const float d0 = o[0], d1 = o[1], d2 = o[2], d3 = o[3], d4 = o[4];
             if (a.mode == 0) {
                 float *dst = a.resid + row * WRF_OUT;
@@ -264,6 +320,46 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             }
         }
         named_bar(1 + wg, 128);  // TMEM columns, A tile and V image are free again
+    };
+
+    if (!MULTI) {
+        int tile = blockIdx.x * kWG + wg;
+        load_g(tile, tile < a.ntiles);
+        for (; tile < a.ntiles; tile += stride) {
+            // uniform per warpgroup: a timed-out wait anywhere ends the loop for
+            // all 128 threads together (no thread is left at a named barrier)
+            if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
+            run_tile(tile, tile + stride, tile + stride < a.ntiles);
+        }
+    } else {
+        // a contiguous range of tiles per CTA, in segments of one scene: the
+        // scene's weights are loaded at a segment start (all threads wait),
+        // then the warpgroups take the segment's tiles in turn
+        const int ntiles = __ldg(a.tstart + a.Q);
+        const int t0 = static_cast<int>(static_cast<long long>(ntiles) * blockIdx.x / gridDim.x);
+        const int t1 =
+            static_cast<int>(static_cast<long long>(ntiles) * (blockIdx.x + 1) / gridDim.x);
+        int cur = -1;
+        for (int seg = t0; seg < t1;) {
+            int q = tile_query(a.tstart, a.Q, seg);
+            const int sc = __ldg(a.scene_of + q);
+            while (q + 1 < a.Q && __ldg(a.scene_of + q + 1) == sc) ++q;
+            const int seg_end = min(t1, __ldg(a.tstart + q + 1));
+            if (sc != cur) {
+                // uniform over the CTA: a timed-out wait ends the loop for all
+                if (wg_bar_any(4, *abort_flag != 0, kThreads)) break;
+                load_weights(a.table[sc].w_img);
+                cur = sc;
+            }
+            int tile = seg + wg;
+            load_g(tile, tile < seg_end);
+            for (; tile < seg_end; tile += kWG) {
+                if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
+                run_tile(tile, tile + kWG, tile + kWG < seg_end);
+            }
+            seg = seg_end;
+            __syncthreads();  // every warpgroup is done with the segment's weights
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -303,7 +399,8 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
     a.rec_im = (mode == 1 && s.channels == 2) ? reinterpret_cast<float *>(rec + 2 * rows) : nullptr;
     a.status = status;
     const size_t smem = smem_bytes(nh);
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
@@ -311,7 +408,40 @@ cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int grid = (a.ntiles + kWG - 1) / kWG;
     if (grid > sms) grid = sms;
-    mlp_tc_kernel<<<grid, kThreads, smem, st>>>(a);
+    mlp_tc_kernel<false><<<grid, kThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_tc_multi(const SceneEntry *table, const MlpView &m, const GridView &g,
+                                int Q, const int *scene_of, const long long *qbase,
+                                const int *tstart, const float *V, float4 *rec, int *status,
+                                cudaStream_t st) {
+    if (Q == 0) return cudaSuccess;
+    const int nh = m.n_layers - 2;
+    if (nh < 0 || nh > 3 || m.dm > 64) return cudaErrorInvalidValue;
+    TcArgs a{};
+    a.g = g;
+    a.V = V;
+    a.nh = nh;
+    a.k1 = mlp_k1(m.dm);
+    a.Q = Q;
+    a.mode = 1;
+    a.rec = rec;
+    a.status = status;
+    a.table = table;
+    a.scene_of = scene_of;
+    a.qbase = qbase;
+    a.tstart = tstart;
+    const size_t smem = smem_bytes(nh);
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // persistent: the tile count is on the device (it depends on the batch)
+    mlp_tc_kernel<true><<<sms, kThreads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,8 @@ template <int TW, int TH, int CH, bool WRAP>
 __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
-    GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im) {
+    GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im,
+    const long long *__restrict__ qbase) {
     constexpr int NT = TW * TH / 2, B = NT, NW = NT / 32;
     constexpr int NSX = TW / 8;  // warp blocks of 8 x 8 pixels: NSX across, TH/8 down
     static_assert(NW == NSX * (TH / 8), "one 8x8 pixel block per warp");
@@ -104,7 +105,8 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     }
     const int total = static_cast<int>(s1 - s0);
     const int nb = (total + B - 1) / B;
-    const float4 *qrec = rec + static_cast<size_t>(q) * n * 2;
+    // records of this query (multi-scene batches: at qbase[q])
+    const float4 *qrec = rec + (qbase ? static_cast<size_t>(qbase[q]) : static_cast<size_t>(q) * n) * 2;
     const float *qim = CH == 2 ? rec_im + static_cast<size_t>(q) * n : nullptr;
     float wim0 = 0.f, wim1 = 0.f;  // imaginary weights of this thread's record, per buffer
 
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
 template <int TW, int TH, int CH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
-                       float *out, int *status, cudaStream_t st) {
+                       float *out, int *status, cudaStream_t st, const long long *qbase) {
     const size_t smem = FwdSmem<TW * TH / 2, TH>::bytes;
     auto kern = g.wrap ? render_kernel<TW, TH, CH, true> : render_kernel<TW, TH, CH, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -340,20 +342,20 @@ cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *
     const float *rec_im =
         CH == 2 ? reinterpret_cast<const float *>(rec + 2 * static_cast<size_t>(Q) * n) : nullptr;
     kern<<<grid, TW * TH / 2, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                          -g.q_cut * kHalfLog2e, out, status, rec_im);
+                                          -g.q_cut * kHalfLog2e, out, status, rec_im, qbase);
     return cudaGetLastError();
 }
 
 template <int CH>
 cudaError_t launch_any(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
-                       float *out, int *status, cudaStream_t st) {
+                       float *out, int *status, cudaStream_t st, const long long *qb) {
     if (Q == 0) return cudaSuccess;
-    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
-    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    if (g.tw == 8 && g.th == 8) return launch_fwd<8, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qb);
+    if (g.tw == 16 && g.th == 8) return launch_fwd<16, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qb);
+    if (g.tw == 16 && g.th == 16) return launch_fwd<16, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qb);
+    if (g.tw == 32 && g.th == 8) return launch_fwd<32, 8, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qb);
+    if (g.tw == 32 && g.th == 16) return launch_fwd<32, 16, CH>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qb);
     return cudaErrorInvalidValue;
 }
 
@@ -376,15 +378,16 @@ bool render_config_supported(int tw, int th) {
 
 cudaError_t launch_render(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
                           const long long *n_keys, long long cap, int n, int Q,
-                          const GridView &g, float *out, int *status, cudaStream_t st) {
-    return launch_any<1>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+                          const GridView &g, float *out, int *status, cudaStream_t st,
+                          const long long *qbase) {
+    return launch_any<1>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, qbase);
 }
 
 cudaError_t launch_render_complex(const float4 *rec, const uint32_t *gids,
                                   const uint32_t *offsets, const long long *n_keys, long long cap,
                                   int n, int Q, const GridView &g, float *out, int *status,
                                   cudaStream_t st) {
-    return launch_any<2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st);
+    return launch_any<2>(rec, gids, offsets, n_keys, cap, n, Q, g, out, status, st, nullptr);
 }
 
 cudaError_t launch_render_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *offsets,
