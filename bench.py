@@ -48,6 +48,9 @@ WORKLOADS = {
     # the paper's own head (Sec. 4.1-4.2, 6.1): tanh centres, Cholesky
     # covariance, complex response, 8 x 156 network with skips; FP32
     "paper": (20000, 90, 360, 64, math.log(3.0), 0.3),
+    # 256 TX per step over the 8 serving scenes (5k..120k Gaussians), one
+    # multi-scene launch sequence per step (mean N shown here)
+    "mixed": (41875, 90, 360, 256, math.log(3.0), 0.3),
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
@@ -81,6 +84,11 @@ def parse():
     p.add_argument("--rate", type=float, default=50000.0, help="serving arrivals per second")
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--serve-warmup", type=float, default=1.0)
+    p.add_argument("--serve-sweep", type=lambda v: [float(x) for x in v.split(",") if x],
+                   default=[2000.0, 10000.0, 25000.0],
+                   help="arrival rates of the serving sweep (q/s, comma-separated)")
+    p.add_argument("--sweep-seconds", type=float, default=3.0)
+    p.add_argument("--sweep-warmup", type=float, default=0.5)
     return p.parse_args()
 
 
@@ -386,39 +394,163 @@ def cpu_baseline(args, sc, m, tx, shape, gpu_out=None, tol=None):
 
 def run_serving(args, dev):
     """Serving workload: Poisson stream (mean args.rate queries/s) of single
-    TX queries over 8 resident scenes (5k..120k Gaussians, 360x90), scene
-    uniform per query; continuous batching vs one query per launch on the
-    same arrivals.  Latency = arrival -> spectrum in pinned host memory."""
+    TX queries over 8 resident scenes (5k..120k Gaussians, 360x90, each scene
+    with its own deformation network), scene uniform per query.  Arms on the
+    same arrivals: continuous batching across scenes (multi-scene launches),
+    continuous batching per scene, and the plain path (one query per launch:
+    a captured one-query forward of its scene, up to 8 in flight on 8
+    streams); then a sweep of arrival rates (shorter windows) for the
+    cross-scene server and the plain path.  Latency = arrival -> spectrum in
+    pinned host memory."""
     from paper_2506_12787_b300 import api, serving
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
     grid = api.make_grid(90, 360, 16, 16, Q_CUT)
-    mlp = synth.make_mlp(seed=0)
-    scenes = [serving.ResidentScene(i, synth.make_scene(n, 90, 360, seed=200 + i), mlp, grid, dev)
+    scenes = [serving.ResidentScene(i, synth.make_scene(n, 90, 360, seed=200 + i),
+                                    synth.make_mlp(seed=300 + i), grid, dev)
               for i, n in enumerate(sizes)]
-    warm, dur = args.serve_warmup, args.serve_seconds
-    t, sc = synth.poisson_arrivals(args.rate, warm + dur, len(sizes), seed=0)
-    arr = list(zip(t.tolist(), sc.tolist()))
-    txs = synth.make_tx(len(arr), seed=9)
-    out = {"config": f"Poisson {args.rate:.0f} q/s over 8 resident scenes {list(sizes)}, "
-                     f"{dur:.0f} s measured after {warm:.0f} s warm-up, BF16 MLP, 360x90"}
-    # a scene with a batch in flight holds its new requests for the next one;
-    # batches of at most 32 queries on 8 streams (caps of 48-96 keep requests
-    # waiting longer, a cap of 16 saturates in bursts)
-    srv = serving.Server(scenes, n_streams=8, buckets=(1, 4, 8, 16, 32), max_batch=32)
-    srv.prepare()
-    cb, _ = serving.run_stream(srv, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
-                               warmup_s=warm)
-    cb["overflow_reruns"] = srv.overflows
-    cb["policy"] = "hold a scene's new requests while one of its batches is in flight"
-    plain = serving.PlainServer(scenes)
-    plain.prepare()
-    pl, _ = serving.run_stream(plain, arr, lambda i: txs[i], window_s=warm + dur, drain_s=1.0,
-                               warmup_s=warm)
-    for d in (cb, pl):
+    out = {}
+
+    def arrivals(rate, total, seed):
+        t, sc = synth.poisson_arrivals(rate, total, len(sizes), seed=seed)
+        return list(zip(t.tolist(), sc.tolist()))
+
+    def finish(d):
         # p99 over all offered requests is undefined once >1% were never served
         d["p99_ms_all"] = d["p99_ms"] if d["unserved"] <= 0.01 * max(1, d["offered"]) else None
-    out["continuous"], out["plain"] = cb, pl
+        return d
+
+    mixed = serving.MixedServer(scenes, n_streams=8, buckets=(8, 16, 32), max_inflight=8)
+    mixed.prepare()
+    per_scene = serving.Server(scenes, n_streams=8, buckets=(1, 4, 8, 16, 32), max_batch=32)
+    per_scene.prepare()
+    plain = serving.PlainServer(scenes, n_streams=8)
+    plain.prepare()
+
+    warm, dur = args.serve_warmup, args.serve_seconds
+    arr = arrivals(args.rate, warm + dur, 0)
+    txs = synth.make_tx(len(arr), seed=9)
+    out["config"] = (f"Poisson {args.rate:.0f} q/s over 8 resident scenes {list(sizes)} (each "
+                     f"its own BF16 network), {dur:.0f} s measured after {warm:.0f} s warm-up, "
+                     "360x90")
+    cb, _ = serving.run_stream(mixed, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
+                               warmup_s=warm)
+    cb["overflow_reruns"] = mixed.overflows
+    cb["policy"] = ("batches across scenes (one multi-scene launch sequence each), up to 32 "
+                    "queries, at most 8 in flight on 8 streams")
+    out["continuous"] = finish(cb)
+    ps, _ = serving.run_stream(per_scene, arr, lambda i: txs[i], window_s=warm + dur,
+                               drain_s=5.0, warmup_s=warm)
+    ps["overflow_reruns"] = per_scene.overflows
+    ps["policy"] = ("batches per scene, up to 32 queries on 8 streams; a scene with a batch in "
+                    "flight holds its new requests for the next one")
+    out["continuous_per_scene"] = finish(ps)
+    pl, _ = serving.run_stream(plain, arr, lambda i: txs[i], window_s=warm + dur, drain_s=1.0,
+                               warmup_s=warm)
+    pl["policy"] = "one query per launch (captured graph), up to 8 in flight on 8 streams"
+    out["plain"] = finish(pl)
+    # rate sweep: shorter windows, the cross-scene server vs the plain path
+    sweep = []
+    for k, rate in enumerate(args.serve_sweep):
+        a2 = arrivals(rate, args.sweep_warmup + args.sweep_seconds, 10 + k)
+        t2 = synth.make_tx(len(a2), seed=20 + k)
+        row = {"rate": rate}
+        for name, srv in (("continuous", mixed), ("plain", plain)):
+            st, _ = serving.run_stream(srv, a2, lambda i: t2[i],
+                                       window_s=args.sweep_warmup + args.sweep_seconds,
+                                       drain_s=2.0, warmup_s=args.sweep_warmup)
+            st = finish(st)
+            row[name] = {k2: st[k2] for k2 in ("spectra_per_s", "p50_ms", "p99_ms", "p99_ms_all",
+                                               "unserved", "offered")}
+        sweep.append(row)
+    out["rate_sweep"] = {"seconds": args.sweep_seconds, "warmup_s": args.sweep_warmup,
+                         "rows": sweep}
     return out
+
+
+def run_mixed(args):
+    """Mixed-scene batches: 256 TX positions per step over the 8 resident
+    scenes of the serving configuration (5k..120k Gaussians, each with its own
+    BF16 network, scene uniform per query, queries ordered by scene), one
+    multi-scene launch sequence per step replayed from one CUDA graph."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_12787_b300 import api
+    from paper_2506_12787_b300.batched import MultiSceneForward
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
+    H, W, Q = 90, 360, 256
+    tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
+    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    hosts = [synth.make_scene(n, H, W, seed=200 + i) for i, n in enumerate(sizes)]
+    mlps = [synth.make_mlp(seed=300 + i) for i in range(len(sizes))]
+    ds = [api.DeviceScene.from_host(h, dev) for h in hosts]
+    dm = [api.DeviceMLP.from_host(m, dev, precision=api.WRF_BF16) for m in mlps]
+    g = synth.rng(40 + rank)
+    scene_of = np.sort(g.integers(0, len(sizes), Q)).astype(np.int32)
+    tx_np = synth.make_tx(Q, seed=41 + rank)
+    mf = MultiSceneForward(ds, dm, grid, Q, dev)
+    mf.set_batch(scene_of, tx_np)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        n_keys = mf.reserve(stream)
+        mf.check(stream)
+        graph = mf.graph(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            graph.replay()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    time.sleep(0.3)
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(K):
+            flush.fill_(i & 255)
+            ev[i][0].record(stream)
+            graph.replay()
+            ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    total_max, _, value = aggregate(total_s, Q * K, dist if ws > 1 else None)
+    out = mf.out.cpu().numpy()
+    n_mean = float(np.mean([sizes[s] for s in scene_of]))
+    line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"mixed: {Q} TX per step over 8 resident scenes "
+                                   f"{list(sizes)} (each its own BF16 network; mean "
+                                   f"{n_mean:.0f} Gaussians per query), 360x90, one multi-scene "
+                                   "launch sequence per step (CUDA graph)",
+                       "queries_per_step": Q, "tile": f"{tw}x{th}",
+                       "queries_per_scene": np.bincount(scene_of, minlength=len(sizes)).tolist(),
+                       "keys_per_step": n_keys,
+                       "l2": "256 MB buffer rewritten between timed steps"},
+            "clocks": clk, "gpu_launches": K * MultiSceneForward.launches_per_run}
+    if rank == 0:
+        # the stated error: a sample of queries (one per scene present) vs the oracle
+        import oracle
+        idx = [int(np.argmax(scene_of == s)) for s in sorted(set(scene_of.tolist()))]
+        refs, slacks = [], []
+        for q in idx:
+            A, slack, _, _ = oracle.forward(hosts[scene_of[q]], mlps[scene_of[q]],
+                                            tx_np[q:q + 1], H, W, Q_CUT)
+            refs.append(A[0])
+            slacks.append(slack[0])
+        line["error_vs_oracle"] = error_vs_oracle(out[idx], np.stack(refs), np.stack(slacks),
+                                                  2e-3)
+        print(json.dumps(line), flush=True)
 
 
 def run_train(args):
@@ -910,6 +1042,8 @@ def main():
         return run_train(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
     import torch
     import torch.distributed as dist
 

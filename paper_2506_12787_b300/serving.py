@@ -19,8 +19,14 @@ batch's spectra are back in pinned host memory, where they are handed to the
 caller's on_result callback; its latency is measured from arrival to the poll
 that sees the batch's completion event.
 
-``PlainServer`` is the baseline: one query per launch, in arrival order, on
-one stream.
+``MixedServer`` batches across scenes: a slot is one multi-scene forward
+(batched.MultiSceneForward) of up to Q queries of any of the resident scenes,
+captured once as a CUDA graph; the oldest waiting requests, whatever their
+scenes, leave together as one launch sequence.
+
+``PlainServer`` is the baseline: one query per launch (a graph-captured
+one-query forward of its scene), in arrival order, with up to K queries in
+flight on K streams.
 
 The spectrum of a query does not depend on the other queries of its batch
 (every stage treats queries independently), so a result served in a mix
@@ -37,7 +43,7 @@ import numpy as np
 import torch
 
 from . import api
-from .batched import BatchedForward
+from .batched import BatchedForward, MultiSceneForward
 
 
 @dataclasses.dataclass
@@ -272,53 +278,83 @@ class Server:
     def pending(self):
         return sum(len(q) for q in self.queues.values()) + sum(len(s.reqs) for s in self.inflight)
 
+    def reset(self):
+        """Drop every waiting request and forget the batches in flight (after
+        the device has finished them): the server is idle again."""
+        torch.cuda.synchronize()
+        self.queues.clear()
+        for s in self.inflight:
+            s.reqs, s.busy = [], False
+        self.inflight = []
+
 
 class PlainServer:
-    """Baseline: one query per launch, in arrival order, on one stream."""
+    """Baseline: one query per launch, in arrival order.  Each launch is the
+    replay of a captured one-query forward of the request's scene; up to
+    n_streams queries are in flight, one per stream (with n_streams = 1 and
+    graph = False: one eager query at a time)."""
 
-    def __init__(self, scenes, on_result=None):
+    def __init__(self, scenes, on_result=None, n_streams=8, graph=True):
         self.scenes = scenes
         self.on_result = on_result
-        self.stream = torch.cuda.Stream()
-        self.slots = {}
+        self.graph = graph
+        self.streams = [torch.cuda.Stream() for _ in range(max(1, n_streams))]
+        self.slots = {}   # (scene, stream index) -> PlainSlot
+        self.free = collections.deque()
         self.queue = collections.deque()
         self.completed = []
-        self.inflight = None
+        self.inflight = []
 
     def prepare(self):
-        for sid, rs in enumerate(self.scenes):
-            self.slots[sid] = PlainSlot(rs, self.stream)
+        for k, st in enumerate(self.streams):
+            for sid, rs in enumerate(self.scenes):
+                self.slots[(sid, k)] = PlainSlot(rs, st, self.graph)
+            self.free.append(k)
         torch.cuda.synchronize()
 
     def submit(self, req):
         self.queue.append(req)
 
     def poll(self):
-        if self.inflight is not None and self.inflight.done.query():
-            s = self.inflight
-            now = time.perf_counter()
-            r = s.req
-            r.t_done = now
-            if self.on_result is not None:
-                self.on_result(r, s.out_host.numpy()[0])
-            self.completed.append(r)
-            self.inflight = None
+        still = []
+        for s, k in self.inflight:
+            if s.done.query():
+                now = time.perf_counter()
+                r = s.req
+                r.t_done = now
+                if self.on_result is not None:
+                    self.on_result(r, s.out_host.numpy()[0])
+                self.completed.append(r)
+                self.free.append(k)
+            else:
+                still.append((s, k))
+        self.inflight = still
 
     def schedule(self):
-        if self.inflight is None and self.queue:
+        while self.free and self.queue:
             r = self.queue.popleft()
-            s = self.slots[r.scene]
+            k = self.free.popleft()
+            s = self.slots[(r.scene, k)]
             s.launch(r)
-            self.inflight = s
+            self.inflight.append((s, k))
 
     def pending(self):
-        return len(self.queue) + (1 if self.inflight is not None else 0)
+        return len(self.queue) + len(self.inflight)
+
+    def reset(self):
+        """Drop every waiting request and forget the queries in flight."""
+        torch.cuda.synchronize()
+        self.queue.clear()
+        for _, k in self.inflight:
+            self.free.append(k)
+        self.inflight = []
 
 
 class PlainSlot:
-    """One-query forward through the public calls, launched eagerly."""
+    """One-query forward of one scene on one stream (graph-captured, or
+    eager through the public calls)."""
 
-    def __init__(self, rs, stream):
+    def __init__(self, rs, stream, graph=True):
         self.rs, self.stream = rs, stream
         self.fw = BatchedForward(rs.scene, rs.mlp, rs.grid, 1, rs.device,
                                  key_capacity=int(rs.keys_per_query * 2) + 4096)
@@ -326,6 +362,7 @@ class PlainSlot:
         self.tx_host = torch.zeros((1, 3), dtype=torch.float32).pin_memory()
         self.out_host = torch.empty((1, rs.grid.H, rs.grid.W), dtype=torch.float32).pin_memory()
         self.done = torch.cuda.Event()
+        self.g = self.fw.graph(self.tx_dev, stream) if graph else None
         self.req = None
 
     def launch(self, r):
@@ -333,9 +370,158 @@ class PlainSlot:
         self.tx_host.numpy()[0] = r.tx
         with torch.cuda.stream(self.stream):
             self.tx_dev.copy_(self.tx_host, non_blocking=True)
-            self.fw.run(self.tx_dev, self.stream)
+            if self.g is not None:
+                self.g.replay()
+            else:
+                self.fw.run(self.tx_dev, self.stream)
             self.out_host.copy_(self.fw.out, non_blocking=True)
             self.done.record(self.stream)
+
+
+class MixedSlot:
+    """Device buffers + captured graph of one multi-scene forward of up to Q
+    queries, with pinned host staging for its inputs and outputs."""
+
+    def __init__(self, scenes, Q: int, stream, margin=1.6):
+        self.Q, self.stream = Q, stream
+        rs0 = scenes[0]
+        dev = rs0.device
+        cap = int(max(rs.keys_per_query for rs in scenes) * Q * margin) + 4096
+        self.fw = MultiSceneForward([rs.scene for rs in scenes], [rs.mlp for rs in scenes],
+                                    rs0.grid, Q, dev, key_capacity=cap)
+        self.scene_host = torch.full((Q,), -1, dtype=torch.int32).pin_memory()
+        self.tx_host = torch.zeros((Q, 3), dtype=torch.float32).pin_memory()
+        self.out_ring = [torch.empty((Q, rs0.grid.H, rs0.grid.W), dtype=torch.float32).pin_memory()
+                         for _ in range(2)]
+        self.nbatch = 0
+        self.out_host = self.out_ring[0]
+        self.nk_host = torch.zeros(1, dtype=torch.int64).pin_memory()
+        self.done = torch.cuda.Event()
+        self.graph = self.fw.graph(stream)
+        self.reqs = []
+        self.busy = False
+        self.nbytes = sum(int(t.numel() * t.element_size()) for t in
+                          (self.fw.rec, self.fw.gids, self.fw.offs, self.fw.out, self.fw.bws,
+                           self.fw.mws, self.fw.qbase))
+
+    def launch(self, reqs):
+        # the scenes in order: a CTA of the MLP reloads weights per scene run
+        reqs = sorted(reqs, key=lambda r: r.scene)
+        self.reqs = reqs
+        self.busy = True
+        k = len(reqs)
+        sc = self.scene_host.numpy()
+        sc[:k] = [r.scene for r in reqs]
+        sc[k:] = -1
+        self.tx_host.numpy()[:k] = np.stack([r.tx for r in reqs]).astype(np.float32)
+        self.out_host = self.out_ring[self.nbatch & 1]
+        self.nbatch += 1
+        with torch.cuda.stream(self.stream):
+            self.fw.scene_of.copy_(self.scene_host, non_blocking=True)
+            self.fw.tx.copy_(self.tx_host, non_blocking=True)
+            self.graph.replay()
+            self.out_host[:k].copy_(self.fw.out[:k], non_blocking=True)
+            self.nk_host.copy_(self.fw.n_keys, non_blocking=True)
+            self.done.record(self.stream)
+
+    def rerun_eager(self):
+        """After a key-capacity overflow: grow the capacity, rerun without
+        the graph (synchronously) and recapture for later batches."""
+        need = int(self.nk_host.item())
+        api.wrf_status_read(self.stream)
+        self.fw._alloc_keys(int(need * 1.5) + 4096)
+        k = len(self.reqs)
+        with torch.cuda.stream(self.stream):
+            self.fw.run(self.stream)
+            self.out_host[:k].copy_(self.fw.out[:k], non_blocking=True)
+        self.stream.synchronize()
+        self.graph = self.fw.graph(self.stream)
+
+
+class MixedServer:
+    """Continuous batching across scenes: whenever a slot is free, the oldest
+    waiting requests (any scenes, up to the largest bucket) leave together as
+    one multi-scene launch sequence.  With max_inflight batches on the GPU,
+    new requests wait for one to complete, so batches grow with the load."""
+
+    def __init__(self, scenes, n_streams=8, buckets=(8, 16, 32), max_inflight=8,
+                 hbm_budget=32 << 30, on_result=None):
+        self.scenes = scenes
+        self.on_result = on_result
+        self.buckets = tuple(sorted(buckets))
+        self.max_inflight = max_inflight
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.next_stream = 0
+        self.budget = int(hbm_budget)
+        self.used = 0
+        self.slots = []
+        self.queue = collections.deque()
+        self.inflight = []
+        self.completed = []
+        self.overflows = 0
+
+    def prepare(self, per_bucket=None):
+        """Create and capture the slots ahead of time: per bucket one per
+        stream (as many as the HBM budget admits)."""
+        for b in self.buckets:
+            for _ in range(per_bucket or len(self.streams)):
+                st = self.streams[self.next_stream % len(self.streams)]
+                s = MixedSlot(self.scenes, b, st)
+                if self.used + s.nbytes > self.budget and self.slots:
+                    del s
+                    break
+                self.next_stream += 1
+                self.used += s.nbytes
+                self.slots.append(s)
+        torch.cuda.synchronize()
+
+    def submit(self, req: Request):
+        self.queue.append(req)
+
+    def poll(self):
+        now = None
+        still = []
+        for s in self.inflight:
+            if s.done.query():
+                now = now or time.perf_counter()
+                if int(s.nk_host.item()) > s.fw.cap:
+                    self.overflows += 1
+                    s.rerun_eager()
+                    now = time.perf_counter()
+                out = s.out_host.numpy()
+                for i, r in enumerate(s.reqs):
+                    r.t_done = now
+                    if self.on_result is not None:
+                        self.on_result(r, out[i])
+                self.completed.extend(s.reqs)
+                s.reqs = []
+                s.busy = False
+            else:
+                still.append(s)
+        self.inflight = still
+
+    def schedule(self):
+        while self.queue and len(self.inflight) < self.max_inflight:
+            free = [x for x in self.slots if not x.busy]
+            if not free:
+                return
+            n = len(self.queue)
+            fit = [x for x in free if x.Q >= n]
+            s = min(fit, key=lambda x: x.Q) if fit else max(free, key=lambda x: x.Q)
+            take = [self.queue.popleft() for _ in range(min(s.Q, n))]
+            s.launch(take)
+            self.inflight.append(s)
+
+    def pending(self):
+        return len(self.queue) + sum(len(s.reqs) for s in self.inflight)
+
+    def reset(self):
+        """Drop every waiting request and forget the batches in flight."""
+        torch.cuda.synchronize()
+        self.queue.clear()
+        for s in self.inflight:
+            s.reqs, s.busy = [], False
+        self.inflight = []
 
 
 def run_stream(server, arrivals, tx_of, window_s, drain_s=2.0, warmup_s=0.0):
@@ -383,6 +569,9 @@ def _run_stream(server, arrivals, tx_of, window_s, drain_s, warmup_s):
     torch.cuda.synchronize()
     server.poll()
     t_end = time.perf_counter()
+    # requests still waiting after the drain are counted unserved; the server
+    # starts the next run idle
+    server.reset()
     done = [r for r in reqs if r.t_done > 0]
     meas = [r for r in done if r.t_arrival - t0 >= warmup_s]
     lat = np.array([r.t_done - r.t_arrival for r in meas]) * 1e3

@@ -1,12 +1,13 @@
-"""Continuous-batching server (resident scenes, HBM-budget admission, K
-streams) against the plain one-query-per-launch path.
+"""Continuous-batching servers (resident scenes, each with its own
+deformation network; per-scene batches with HBM-budget admission, or batches
+that mix scenes in one multi-scene launch) against the plain
+one-query-per-launch path (graph-captured, several queries in flight).
 
-Checks: a query served inside a mixed batch equals the same query rendered
-alone (within 1e-6 x peak; the path is deterministic per query); served
-spectra match the FP64 oracle at the BF16-MLP tolerance (2e-3 x peak);
-admission under a tiny HBM budget still serves everything; and continuous
-batching beats the plain path in spectra/s and p99 latency at the same
-offered load.
+Checks: a query served inside a batch equals the same query rendered alone
+(within 1e-6 x peak per-scene; bit for bit in mixed batches); served spectra
+match the FP64 oracle at the BF16-MLP tolerance (2e-3 x peak); admission
+under a tiny HBM budget still serves everything; and continuous batching
+beats the plain path in spectra/s and p99 latency at the same offered load.
 """
 import numpy as np
 import pytest
@@ -29,9 +30,9 @@ def env():
     dev = torch.device("cuda:0")
     grid = api.make_grid(H, W, 16, 16, 9.0)
     hosts = [synth.make_scene(n, H, W, seed=100 + i) for i, n in enumerate(SIZES)]
-    mlp = synth.make_mlp(seed=7)
-    scenes = [serving.ResidentScene(i, hosts[i], mlp, grid, dev) for i in range(len(SIZES))]
-    return api, serving, scenes, hosts, mlp, grid, dev
+    mlps = [synth.make_mlp(seed=7 + i) for i in range(len(SIZES))]
+    scenes = [serving.ResidentScene(i, hosts[i], mlps[i], grid, dev) for i in range(len(SIZES))]
+    return api, serving, scenes, hosts, mlps, grid, dev
 
 
 def arrivals(rate, dur, seed):
@@ -40,7 +41,7 @@ def arrivals(rate, dur, seed):
 
 
 def test_served_equals_alone_and_matches_oracle(env):
-    api, serving, scenes, hosts, mlp, grid, dev = env
+    api, serving, scenes, hosts, mlps, grid, dev = env
     srv = serving.Server(scenes, n_streams=3, buckets=(1, 4, 16, 64),
                          on_result=serving.keep_results)
     arr = arrivals(4000.0, 0.25, seed=1)
@@ -62,14 +63,40 @@ def test_served_equals_alone_and_matches_oracle(env):
     print(f"alone vs in the mix: max |diff| / peak = {worst:.2e}")
     # oracle parity of a few served results
     for r in done[:3]:
-        A, slack, _, _ = oracle.forward(hosts[r.scene], mlp, r.tx[None], H, W, 9.0)
+        A, slack, _, _ = oracle.forward(hosts[r.scene], mlps[r.scene], r.tx[None], H, W, 9.0)
         ok, err, _ = spectrum_error(r.result[None], A, slack, 2e-3)
         print(f"served query {r.rid} (scene {r.scene}) vs oracle: err/peak {err:.2e}")
         assert ok
 
 
+def test_mixed_batches_equal_alone_and_match_oracle(env):
+    """Batches that mix scenes: every served spectrum is bit-identical to the
+    same query run alone through its scene's single-scene forward."""
+    api, serving, scenes, hosts, mlps, grid, dev = env
+    srv = serving.MixedServer(scenes, n_streams=3, buckets=(4, 16), max_inflight=2,
+                              on_result=serving.keep_results)
+    srv.prepare(per_bucket=2)
+    arr = arrivals(6000.0, 0.25, seed=4)
+    txs = synth.make_tx(len(arr), seed=14)
+    stats, done = serving.run_stream(srv, arr, lambda i: txs[i], window_s=0.25, drain_s=10.0)
+    assert stats["unserved"] == 0 and len(done) == len(arr)
+    print(f"mixed: served {len(done)}: p50 {stats['p50_ms']:.3f} ms p99 {stats['p99_ms']:.3f} ms")
+    from paper_2506_12787_b300.batched import BatchedForward
+    for r in done[:: max(1, len(done) // 12)]:
+        rs = scenes[r.scene]
+        fw = BatchedForward(rs.scene, rs.mlp, grid, 1, dev)
+        tx = torch.as_tensor(r.tx[None], device=dev)
+        fw.reserve(tx)
+        assert np.array_equal(fw.out[0].cpu().numpy(), r.result), r.rid
+    for r in done[:3]:
+        A, slack, _, _ = oracle.forward(hosts[r.scene], mlps[r.scene], r.tx[None], H, W, 9.0)
+        ok, err, _ = spectrum_error(r.result[None], A, slack, 2e-3)
+        print(f"mixed-served query {r.rid} (scene {r.scene}) vs oracle: err/peak {err:.2e}")
+        assert ok
+
+
 def test_admission_under_small_budget(env):
-    api, serving, scenes, hosts, mlp, grid, dev = env
+    api, serving, scenes, hosts, mlps, grid, dev = env
     srv = serving.Server(scenes, n_streams=2, buckets=(1, 4, 16), hbm_budget=1)
     arr = arrivals(3000.0, 0.2, seed=2)
     txs = synth.make_tx(len(arr), seed=12)
@@ -84,7 +111,7 @@ def test_admission_under_small_budget(env):
 
 
 def test_continuous_batching_beats_plain(env):
-    api, serving, scenes, hosts, mlp, grid, dev = env
+    api, serving, scenes, hosts, mlps, grid, dev = env
     rate, win = 20000.0, 0.6
     arr = arrivals(rate, win, seed=3)
     txs = synth.make_tx(len(arr), seed=13)
@@ -92,12 +119,18 @@ def test_continuous_batching_beats_plain(env):
     srv.prepare()
     cb, _ = serving.run_stream(srv, arr, lambda i: txs[i], window_s=win, drain_s=5.0,
                                warmup_s=0.1)
-    plain = serving.PlainServer(scenes)
+    mixed = serving.MixedServer(scenes, n_streams=4)
+    mixed.prepare(per_bucket=4)
+    mx, _ = serving.run_stream(mixed, arr, lambda i: txs[i], window_s=win, drain_s=5.0,
+                               warmup_s=0.1)
+    plain = serving.PlainServer(scenes, n_streams=4)
     plain.prepare()
     pl, _ = serving.run_stream(plain, arr, lambda i: txs[i], window_s=win, drain_s=1.0,
                                warmup_s=0.1)
-    print(f"continuous: {cb}\nplain: {pl}\nrequests held behind a batch in flight: {srv.holds}")
-    assert cb["unserved"] == 0
+    print(f"continuous per scene: {cb}\ncontinuous mixed: {mx}\nplain (graphs, 4 streams): {pl}"
+          f"\nrequests held behind a batch in flight: {srv.holds}")
+    assert cb["unserved"] == 0 and mx["unserved"] == 0
     assert srv.holds > 0  # the hold-while-busy policy was exercised
-    assert cb["spectra_per_s"] > pl["spectra_per_s"]
-    assert pl["p99_ms"] is None or cb["p99_ms"] < pl["p99_ms"]
+    for c in (cb, mx):
+        assert c["spectra_per_s"] > pl["spectra_per_s"]
+        assert pl["p99_ms"] is None or c["p99_ms"] < pl["p99_ms"]
