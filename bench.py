@@ -71,7 +71,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
-    p.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    p.add_argument("--precision", default=None, choices=["bf16", "bf16x3", "fp32"],
+                   help="network precision (default: bf16; the paper workload: bf16x3, the "
+                        "three-product BF16 network held to the FP32 tolerance)")
     p.add_argument("--tile", default="auto", help="WxH, or auto (autotuned, cached)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU-oracle time of the cpu_baseline sample")
@@ -89,7 +91,10 @@ def parse():
                    help="arrival rates of the serving sweep (q/s, comma-separated)")
     p.add_argument("--sweep-seconds", type=float, default=3.0)
     p.add_argument("--sweep-warmup", type=float, default=0.5)
-    return p.parse_args()
+    args = p.parse_args()
+    if args.precision is None:
+        args.precision = "bf16x3" if args.workload == "paper" else "bf16"
+    return args
 
 
 def dist_env():
@@ -139,8 +144,10 @@ def config_of(args, shape, extra=None):
     if args.workload == "paper":
         c.update({"mlp": "paper head: gamma(81) -> 156 x 8 ReLU -> 5, the encoding concatenated "
                          "into hidden layers 2, 4, 6 (0-based); " +
-                         ("BF16 tcgen05 / FP32 acc" if args.precision == "bf16"
-                          else "FP32 CUDA cores"),
+                         {"bf16": "BF16 tcgen05 / FP32 acc",
+                          "bf16x3": "BF16 hi + lo operands, three tcgen05 products per "
+                                    "multiply / FP32 acc"}.get(args.precision,
+                                                               "FP32 CUDA cores"),
                   "primitive": "tanh-mapped centre, Cholesky covariance, attenuation, complex "
                                "response (Sec. 4.1)",
                   "channels": 2, "output": "magnitude and phase [Q,2,H,W]"})
@@ -870,7 +877,7 @@ def run_paper(args):
     tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
     args.tile = f"{tw}x{th}"
     grid = api.make_grid(H, W, tw, th, Q_CUT)
-    prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
+    prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[args.precision]
     ds = api.DevicePaperScene.from_host(sc, dev)
     dm = api.DevicePaperMLP.from_host(m, dev, precision=prec)
     tx = torch.as_tensor(tx_np, dtype=torch.float32, device=dev)
@@ -979,6 +986,12 @@ def run_paper(args):
         roof = {"kernel": "paper_tc_kernel (+ gamma rows / per-query terms / weight panels)",
                 "bound": "tensor", "peak": peaks["bf16_tflops"],
                 "peak_source": "bf16_tflops (measured)"}
+    elif prec == api.WRF_BF16X3:
+        roof = {"kernel": "paper_tc_kernel, three-product BF16 (+ gamma rows / per-query terms / "
+                          "weight panels)",
+                "bound": "tensor", "peak": peaks["bf16_tflops"] / 3.0,
+                "peak_source": "bf16_tflops (measured) / 3 (three BF16 products per FP32 "
+                               "product)"}
     else:
         ap = alu_peaks(api, stream)
         roof = {"kernel": "paper_mlp_kernel (+ encoding / weight prep)", "bound": "alu",
@@ -989,7 +1002,8 @@ def run_paper(args):
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if prec == api.WRF_BF16 else "f32", "data": "synthetic",
+            "dtype": {api.WRF_BF16: "bf16", api.WRF_BF16X3: "bf16x3"}.get(prec, "f32"),
+            "data": "synthetic",
             "config": config_of(args, shape, {"keys_per_step": n_keys, "cuda_graph": True}),
             "clocks": clk,
             "e2e": {"value": e2e_val, "unit": "spectra/s", "h2d_bytes_per_step": pipe.h2d_bytes,
@@ -1013,12 +1027,12 @@ def run_paper(args):
                                 "sample": f"first {S} of {Q} TX queries, {N} Gaussians, {W}x{H}, "
                                           f"FP64 numpy network + C oracle render, {dt:.1f} s"}
         # the stated error against the FP64 oracle on the same sample: the FP32
-        # network at 1e-4 x peak; the BF16 network carries BF16 rounding through
-        # eight layers (its parity is asserted against an emulation of those
-        # roundings in the tests), so no FP64 tolerance is claimed for it
+        # and the three-product BF16 networks at 1e-4 x peak; the BF16 network
+        # carries BF16 rounding of weights and activations (2^-9 relative)
+        # through eight layers, stated at 1.5e-2 x peak (measured ~7e-3)
         import numpy as np
         g = out[:S].float().cpu().numpy()
-        tol = 1e-4 if prec == api.WRF_FP32 else None
+        tol = 1.5e-2 if prec == api.WRF_BF16 else 1e-4
         e_re = error_vs_oracle(g[:, 0] * np.cos(g[:, 1]), re, slack, tol or 0.0)
         e_im = error_vs_oracle(g[:, 0] * np.sin(g[:, 1]), im, slack, tol or 0.0)
         err = max(e_re, e_im, key=lambda e: e["max_abs_over_peak"])
@@ -1214,7 +1228,8 @@ def main():
     line = {"metric": "spectra/s", "value": value, "unit": "spectra/s", "n_gpus": ws,
             "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16" if prec == api.WRF_BF16 else "f32", "data": "synthetic",
+            "dtype": {api.WRF_BF16: "bf16", api.WRF_BF16X3: "bf16x3"}.get(prec, "f32"),
+            "data": "synthetic",
             "config": config_of(args, shape, {"keys_per_step": n_keys,
                                               "cuda_graph": bool(args.graph),
                                               "autotune_ms_per_step": tune_ms}),

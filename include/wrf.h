@@ -49,7 +49,11 @@ typedef enum {
     WRF_EUNSUPPORTED = -5  /* valid request outside what the kernels implement   */
 } wrf_status;
 
-enum { WRF_FP32 = 0, WRF_BF16 = 1 };
+/* Network precision.  WRF_BF16X3 (the paper's head only): every FP32
+ * operand split into BF16 hi + lo = bf16(x) + bf16(x - bf16(x)) and every
+ * product taken as hi hi + hi lo + lo hi on the tensor cores with FP32
+ * accumulation (relative error ~2^-17 per product). */
+enum { WRF_FP32 = 0, WRF_BF16 = 1, WRF_BF16X3 = 2 };
 enum { WRF_MAX_LAYERS = 8, WRF_HIDDEN = 128, WRF_OUT = 5 };
 
 /* Reference-frame Gaussians G^0 (Sec. 4.2, Eq. 10-12), structure of arrays,
@@ -385,7 +389,10 @@ typedef struct {
  * precision = WRF_FP32: every product in FP32 on the CUDA cores.
  * precision = WRF_BF16: the hidden and output layers on the tcgen05 tensor
  * cores with BF16 weights, activations and gamma(mean), FP32 accumulation;
- * the query's part of the encoding, W_s gamma(s) + b, stays FP32.         */
+ * the query's part of the encoding, W_s gamma(s) + b, stays FP32.
+ * precision = WRF_BF16X3: the same on the tensor cores with weights,
+ * activations and gamma(mean) each as BF16 hi + lo and three products per
+ * multiply (FP32-level results at about three times the tensor work).     */
 enum { WRF_PAPER_MAX_LAYERS = 9, WRF_PAPER_MAX_WIDTH = 160 };
 typedef struct {
     int32_t n_hidden, width;

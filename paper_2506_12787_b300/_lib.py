@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwrf.so")
 
 WRF_OK, WRF_EINVAL, WRF_ENOSPC, WRF_ECUDA, WRF_ETIMEOUT, WRF_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
-WRF_FP32, WRF_BF16 = 0, 1
+WRF_FP32, WRF_BF16, WRF_BF16X3 = 0, 1, 2
 MAX_LAYERS = 8
 PAPER_MAX_LAYERS, PAPER_MAX_WIDTH = 9, 160
 REC_FLOATS = 8

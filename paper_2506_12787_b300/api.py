@@ -15,12 +15,12 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import WRF_BF16, WRF_FP32, WrfError
+from ._lib import WRF_BF16, WRF_BF16X3, WRF_FP32, WrfError
 
 __all__ = ["DeviceScene", "DeviceMLP", "make_grid", "wrf_deform", "wrf_project",
            "wrf_deform_project", "wrf_bin", "wrf_render", "wrf_render_backward",
            "wrf_project_backward", "wrf_deform_backward", "wrf_status_read", "tiles_of",
-           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
+           "Renderer", "WrfError", "WRF_FP32", "WRF_BF16", "WRF_BF16X3", "wrf_rssi", "wrf_loss", "wrf_adam", "wrf_render_complex", "alloc_records", "record_tail",
            "DevicePaperScene", "DevicePaperMLP", "wrf_paper_deform_project",
            "wrf_measure_alu_peaks", "wrf_deform_acts", "wrf_anneal_tx"]
 

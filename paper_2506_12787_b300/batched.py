@@ -144,7 +144,8 @@ class PaperForward(BatchedForward):
         self.cap = 0
         self.gids = None
         self._alloc_keys(int(key_capacity))
-        net = 1 if mlp is None else (2 if mlp.precision == _lib.WRF_BF16 else 4)
+        net = 1 if mlp is None else (2 if mlp.precision in (_lib.WRF_BF16, _lib.WRF_BF16X3)
+                                     else 4)
         self.launches_per_run = net + 6
 
     # kernels one run() launches, set in __init__: the network's (tensor

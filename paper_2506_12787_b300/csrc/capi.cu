@@ -460,11 +460,13 @@ wrf_status wrf_paper_deform_project(const wrf_paper_scene *scene, const wrf_pape
         for (int i = 0; i < 3; ++i)
             if (!(mlp->room_size[i] > 0.f)) return fail(WRF_EINVAL, "room_size must be > 0");
         if (Q > 0 && !tx) return fail(WRF_EINVAL, "tx is NULL");
-        if (mlp->precision != WRF_FP32 && mlp->precision != WRF_BF16)
+        if (mlp->precision != WRF_FP32 && mlp->precision != WRF_BF16 &&
+            mlp->precision != WRF_BF16X3)
             return fail(WRF_EINVAL, "unknown precision");
-        if (mlp->precision == WRF_BF16 && 2 * (2 * mlp->L_mean + 1) > 64)
+        const bool tc = mlp->precision == WRF_BF16 || mlp->precision == WRF_BF16X3;
+        if (tc && 2 * (2 * mlp->L_mean + 1) > 64)
             return fail(WRF_EUNSUPPORTED, "BF16 path: 2(2 L_mean + 1) must be <= 64");
-        if (mlp->precision == WRF_BF16 && Q > 0 && scene->n > 0 &&
+        if (tc && Q > 0 && scene->n > 0 &&
             (static_cast<long long>(Q) * ((scene->n + 127) / 128) >= (1ll << 30)))
             return fail(WRF_EUNSUPPORTED, "too many tiles");
         mv.n_hidden = mlp->n_hidden;
@@ -489,9 +491,9 @@ wrf_status wrf_paper_deform_project(const wrf_paper_scene *scene, const wrf_pape
     if (mlp) wrf::paper_ws_layout(scene->n, Q, &w, static_cast<char *>(ws));
     wrf::PaperSceneView sv{scene->n, scene->mu, scene->chol, scene->attn_logit, scene->psi};
     cudaError_t e;
-    if (mlp && mlp->precision == WRF_BF16)
+    if (mlp && (mlp->precision == WRF_BF16 || mlp->precision == WRF_BF16X3))
         e = wrf::launch_paper_tc(sv, mv, g, tx, Q, w, reinterpret_cast<float4 *>(rec), status_ptr(),
-                                 static_cast<cudaStream_t>(stream));
+                                 mlp->precision, static_cast<cudaStream_t>(stream));
     else
         e = wrf::launch_paper(sv, mlp ? &mv : nullptr, g, tx, Q, w,
                               reinterpret_cast<float4 *>(rec), static_cast<cudaStream_t>(stream));

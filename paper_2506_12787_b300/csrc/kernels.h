@@ -121,9 +121,10 @@ size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base);
 cudaError_t launch_paper(const PaperSceneView &s, const PaperMlpView *m, const GridView &g,
                          const float *tx, int Q, const PaperWs &ws, float4 *rec, cudaStream_t st);
 size_t paper_tc_image_bytes(int n_hidden);
+// precision WRF_BF16 or WRF_BF16X3 (three BF16 products per FP32 product)
 cudaError_t launch_paper_tc(const PaperSceneView &s, const PaperMlpView &m, const GridView &g,
                             const float *tx, int Q, const PaperWs &ws, float4 *rec, int *status,
-                            cudaStream_t st);
+                            int precision, cudaStream_t st);
 
 // Training protocol (train.cu): Eq. 16 loss with SSIM, and Adam.
 size_t loss_ws_layout(int Q, int H, int W, float **coef, float **part);

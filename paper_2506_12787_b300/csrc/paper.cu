@@ -281,7 +281,8 @@ size_t paper_ws_layout(int n, int Q, PaperWs *ws, char *base) {
     w.Wt = take(static_cast<size_t>(kPaperMaxLayers - 1) * kPW * kPW * 4);
     w.bh = take(static_cast<size_t>(kPaperMaxLayers) * kPW * 4);
     w.Wo = take(static_cast<size_t>(kPW) * 8 * 4);
-    w.G = reinterpret_cast<uint16_t *>(take(static_cast<size_t>(n > 0 ? n : 1) * 64 * 2));
+    // BF16 gamma(mean) rows [N][64], then (three-product precision) their remainders
+    w.G = reinterpret_cast<uint16_t *>(take(static_cast<size_t>(n > 0 ? n : 1) * 64 * 2 * 2));
     w.vec = take(static_cast<size_t>(Q > 0 ? Q : 1) * (kPaperMaxLayers - 1) * kPW * 4);
     w.img = reinterpret_cast<uint16_t *>(take(paper_tc_image_bytes(kPaperMaxLayers - 1)));
     if (ws) *ws = w;

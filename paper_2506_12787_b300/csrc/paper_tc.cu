@@ -48,27 +48,38 @@ namespace {
 
 constexpr int kPW = kPaperMaxWidth;          // 160
 constexpr int kTile = 128;
-constexpr int kWGs = 2;
 constexpr int kGroup = 256;                  // threads per compute group (8 warps)
-constexpr int kTcThreads = kWGs * kGroup + 32;  // + producer warp
 constexpr uint32_t kGPanel = 128 * 128;      // gamma(mean) A panel: 128 rows x 64 K x BF16
 constexpr uint32_t kBPanel = kPW * 128;      // weight panel: 160 rows x 64 K x BF16
-constexpr int kRing = 9;
 constexpr uint32_t kOutPanel = 16 * 128;     // 16 rows x 64 K x BF16
 constexpr uint32_t kOutImg = 3 * kOutPanel;  // K 0..191 (0..159 used)
 constexpr int kGammaCols = 64;
 constexpr int kGammaPanel = 3;               // panel id of the gamma(mean) block
-// TMEM columns: accumulators at 0 and 256 (160 each), activations (80 BF16
-// pair columns each) at 160 and 416
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kTermImg = kPW * 16;      // per-layer term image: 160 rows x 16 B (hi, lo)
 constexpr uint32_t kSelImg = 256;            // selector: two 8 x 16 B core matrices
 
-constexpr size_t tc_smem_bytes() {
-    return 1024 + kWGs * kGPanel + kRing * kBPanel + kOutImg + kWGs * kTermImg + kSelImg +
-           (2 * kRing + kWGs + 1) * 8 + 16;
-}
-static_assert(tc_smem_bytes() <= 227 * 1024, "shared memory of one CTA");
+// Precision X: 1 = BF16 operands; 3 = every FP32 operand (weights,
+// activations, gamma(mean)) as BF16 hi + lo and each product as the three
+// BF16 products hi hi + hi lo + lo hi.
+//   X = 1: two compute groups (two tiles per CTA); TMEM: accumulators at 0
+//          and 256 (160 columns each), BF16 activation pairs (80 columns) at
+//          160 and 416; a ring of nine weight panels.
+//   X = 3: one compute group; TMEM: accumulator at 0 (160 columns),
+//          activation hi pairs at 160, lo pairs at 240; every weight panel
+//          comes as a hi and a lo panel; a ring of eight panels.
+template <int X>
+struct TcCfg {
+    static constexpr int WGs = X == 3 ? 1 : 2;
+    static constexpr int Terms = X == 3 ? 2 : 1;
+    static constexpr int Threads = WGs * kGroup + 32;  // + producer warp
+    static constexpr int Ring = X == 3 ? 8 : 9;
+    static constexpr size_t smem = 1024 + WGs * Terms * kGPanel + Ring * kBPanel +
+                                   Terms * kOutImg + WGs * kTermImg + kSelImg +
+                                   (2 * Ring + WGs + 1) * 8 + 16;
+};
+static_assert(TcCfg<1>::smem <= 227 * 1024, "shared memory of one CTA");
+static_assert(TcCfg<3>::smem <= 227 * 1024, "shared memory of one CTA");
 
 // Panels layer l consumes, in order: activation panels 0, 1, 2 (l >= 1), then
 // the gamma(mean) panel (layer 0 and the skip layers).
@@ -139,8 +150,22 @@ __device__ inline int in_dim_tc(const PaperNetTc &m, int l) {
 
 // BF16 panels of every hidden layer in consumption order, and the output
 // layer's three panels (rows = output units, K-major, 128-byte swizzle).
+// terms = 2: panel s of the sequence becomes physical panels 2s (hi) and
+// 2s + 1 (lo = BF16 of the remainder), the output image its three hi panels
+// then its three lo panels.
+__device__ __forceinline__ void store_terms(uint16_t *img, size_t hi_index, size_t lo_index,
+                                            float v, int terms) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    img[hi_index] = *reinterpret_cast<const uint16_t *>(&h);
+    if (terms == 2) {
+        const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(h)));
+        img[lo_index] = *reinterpret_cast<const uint16_t *>(&l);
+    }
+}
+
 __device__ __forceinline__ void paper_tc_weights_block(int blk, int nblk, const PaperNetTc &m,
-                                                       int nseq, uint16_t *wimg, uint16_t *oimg) {
+                                                       int nseq, uint16_t *wimg, uint16_t *oimg,
+                                                       int terms) {
     const long long per = static_cast<long long>(kPW) * 64;
     const long long total = nseq * per + 3LL * 16 * 64;
     for (long long i = blk * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
@@ -163,9 +188,9 @@ __device__ __forceinline__ void paper_tc_weights_block(int blk, int nblk, const 
                 const int j = input_index(m, l, pid, kl);
                 if (j >= 0) v = m.W[l][static_cast<size_t>(r) * in_dim_tc(m, l) + j];
             }
-            const __nv_bfloat16 bv = __float2bfloat16_rn(v);
-            wimg[(static_cast<size_t>(s) * kBPanel + sw128_off(r, kl)) / 2] =
-                *reinterpret_cast<const uint16_t *>(&bv);
+            const size_t o = sw128_off(r, kl) / 2;
+            store_terms(wimg, static_cast<size_t>(terms * s) * kBPanel / 2 + o,
+                        static_cast<size_t>(terms * s + 1) * kBPanel / 2 + o, v, terms);
         } else {
             const long long e = i - nseq * per;
             const int p = static_cast<int>(e / (16 * 64));
@@ -174,9 +199,8 @@ __device__ __forceinline__ void paper_tc_weights_block(int blk, int nblk, const 
             const float v = (r < WRF_OUT && k < m.width)
                                 ? m.W[m.n_hidden][static_cast<size_t>(r) * m.width + k]
                                 : 0.f;
-            const __nv_bfloat16 bv = __float2bfloat16_rn(v);
-            oimg[(static_cast<size_t>(p) * kOutPanel + sw128_off(r, kl)) / 2] =
-                *reinterpret_cast<const uint16_t *>(&bv);
+            const size_t o = (static_cast<size_t>(p) * kOutPanel + sw128_off(r, kl)) / 2;
+            store_terms(oimg, o, o + kOutImg / 2, v, terms);
         }
     }
 }
@@ -184,7 +208,7 @@ __device__ __forceinline__ void paper_tc_weights_block(int blk, int nblk, const 
 // gamma(mean_n) rows [N][64] BF16 (42 values of Eq. 15 at L_mean = 10, zeros
 // after them): the encoding input on the unit square (tanh u + 1) / 2.
 __device__ __forceinline__ void paper_tc_gamma_block(int blk, const PaperView &s, int L_mean,
-                                                     int dm, uint16_t *G) {
+                                                     int dm, uint16_t *G, int terms) {
     const int n = blk * blockDim.x + threadIdx.x;
     if (n >= s.n) return;
     const float2 mu = reinterpret_cast<const float2 *>(s.mu)[n];
@@ -192,10 +216,16 @@ __device__ __forceinline__ void paper_tc_gamma_block(int blk, const PaperView &s
     float gam[2 * (2 * 15 + 1)];
     pe_encode(a, 2, L_mean, gam);
     uint32_t *dst = reinterpret_cast<uint32_t *>(G + static_cast<size_t>(n) * kGammaCols);
+    // terms = 2: the lo rows [N][64] follow the hi rows
+    uint32_t *dlo = reinterpret_cast<uint32_t *>(G + (static_cast<size_t>(s.n) + n) * kGammaCols);
     for (int i = 0; i < kGammaCols / 2; ++i) {
         const float x0 = 2 * i < dm ? gam[2 * i] : 0.f;
         const float x1 = 2 * i + 1 < dm ? gam[2 * i + 1] : 0.f;
-        dst[i] = pack_bf16(x0, x1);
+        const uint32_t h = pack_bf16(x0, x1);
+        dst[i] = h;
+        if (terms == 2)
+            dlo[i] = pack_bf16(__fsub_rn(x0, __uint_as_float(h << 16)),
+                               __fsub_rn(x1, __uint_as_float(h & 0xFFFF0000u)));
     }
 }
 
@@ -232,7 +262,8 @@ __device__ __forceinline__ void paper_tc_vec_block(int q, int l, const PaperNetT
 __global__ void __launch_bounds__(kPW) paper_tc_prep_kernel(PaperNetTc m, int nseq, uint16_t *wimg,
                                                             uint16_t *oimg, PaperView s,
                                                             uint16_t *G, const float *tx,
-                                                            float *vec, int nb_vec, int nb_gamma) {
+                                                            float *vec, int nb_vec, int nb_gamma,
+                                                            int terms) {
     int b = blockIdx.x;
     if (b < nb_vec) {
         paper_tc_vec_block(b / (kPaperMaxLayers - 1), b % (kPaperMaxLayers - 1), m, tx, vec);
@@ -240,12 +271,12 @@ __global__ void __launch_bounds__(kPW) paper_tc_prep_kernel(PaperNetTc m, int ns
     }
     b -= nb_vec;
     if (b < nb_gamma) {
-        paper_tc_gamma_block(b, s, m.L_mean, m.dm, G);
+        paper_tc_gamma_block(b, s, m.L_mean, m.dm, G, terms);
         return;
     }
     b -= nb_gamma;
     paper_tc_weights_block(b, static_cast<int>(gridDim.x) - nb_vec - nb_gamma, m, nseq, wimg,
-                           oimg);
+                           oimg, terms);
 }
 
 struct PaperTcArgs {
@@ -253,20 +284,23 @@ struct PaperTcArgs {
     GridView g;
     const uint16_t *G, *wimg, *oimg;
     const float *vec, *bout;
-    int nh, nseq, Q, N, tpq, ntiles, npairs;
+    int nh, nseq, Q, N, tpq, ntiles;
     float4 *rec;
     float *rec_im;
     int *status;
 };
 
-__global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) {
+template <int X>
+__global__ void __launch_bounds__(TcCfg<X>::Threads, 1) paper_tc_kernel(PaperTcArgs a) {
+    using Cfg = TcCfg<X>;
+    constexpr int kWGs = Cfg::WGs, kRing = Cfg::Ring, kTerms = Cfg::Terms;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-    uint8_t *gp0 = base;                       // [kWGs] gamma(mean) panels
-    uint8_t *ring = base + kWGs * kGPanel;
-    uint8_t *oimg = ring + kRing * kBPanel;
-    uint8_t *term0 = oimg + kOutImg;           // [kWGs][160 rows x 16 B]
+    uint8_t *gp0 = base;                       // [kWGs][kTerms] gamma(mean) panels
+    uint8_t *ring = base + kWGs * kTerms * kGPanel;
+    uint8_t *oimg = ring + kRing * kBPanel;    // [kTerms] output images
+    uint8_t *term0 = oimg + kTerms * kOutImg;  // [kWGs][160 rows x 16 B]
     uint8_t *sel = term0 + kWGs * kTermImg;    // selector A
     uint64_t *bars = reinterpret_cast<uint64_t *>(sel + kSelImg);
     uint64_t *full = bars, *empty = bars + kRing, *accb = bars + 2 * kRing;
@@ -297,16 +331,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    const int rounds_total = (a.ntiles + kWGs - 1) / kWGs;  // tiles per round: one per group
 
     if (warp == kWGs * (kGroup / 32)) {
         // ---------------------------------------------------- producer warp
         if (lane == 0) {
-            mbar_arrive_expect_tx(wbar, kOutImg);
-            bulk_g2s(oimg, a.oimg, kOutImg, wbar);
+            mbar_arrive_expect_tx(wbar, kTerms * kOutImg);
+            bulk_g2s(oimg, a.oimg, kTerms * kOutImg, wbar);
             uint32_t g = 0;  // panels issued
             bool ok = true;
-            for (int p = blockIdx.x; p < a.npairs && ok; p += gridDim.x) {
-                for (int s = 0; s < a.nseq; ++s) {
+            for (int p = blockIdx.x; p < rounds_total && ok; p += gridDim.x) {
+                for (int s = 0; s < kTerms * a.nseq; ++s) {
                     const int slot = static_cast<int>(g % kRing);
                     if (g >= kRing &&
                         !wait_or_abort(&empty[slot], ((g / kRing) - 1) & 1u, abort_flag, a.status)) {
@@ -332,10 +367,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
         // group, TMEM lane quarter, column half, thread within the group
         const int wg = warp / (kGroup / 32), wq = warp & 3, half = (warp >> 2) & 1;
         const int wt = tid & (kGroup - 1);
-        uint8_t *G = gp0 + wg * kGPanel;
+        uint8_t *G = gp0 + wg * kTerms * kGPanel;
         const uint32_t g_addr = smem_u32(G), ring_addr = smem_u32(ring), o_addr = smem_u32(oimg);
         const uint32_t t_acc = tmem_base + static_cast<uint32_t>(wg * 256);
-        const uint32_t t_act = t_acc + static_cast<uint32_t>(kPW);
+        const uint32_t t_act = t_acc + static_cast<uint32_t>(kPW);      // hi pairs (80 columns)
+        const uint32_t t_lo = t_act + static_cast<uint32_t>(kPW / 2);   // lo pairs (X = 3)
         const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;
         const int my_row = wq * 32 + lane;
         // the MMA warp of the group: lane 0 issues while lanes 1..31 wait at
@@ -366,23 +402,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                 *reinterpret_cast<uint4 *>(term + wt * 16) = make_uint4(hi | (lo << 16), 0u, 0u, 0u);
             }
         };
+        // MMAs of one weight panel (hi, and lo when X = 3) at K offsets
+        // 0 .. nk-1 of 16: A from tensor memory (activation pairs from
+        // column a_col) or from the gamma(mean) panel in shared memory
+        auto panel_mmas = [&](uint32_t bh, uint32_t bl, bool gamma, int a_col, int nk) {
+            for (int kk = 0; kk < nk; ++kk) {
+                const uint64_t dbh = sw128_desc(bh + kk * 32u);
+                if (gamma) {
+                    mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u), dbh, id_h, 1u);
+                    if (X == 3) {
+                        mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u), sw128_desc(bl + kk * 32u),
+                                 id_h, 1u);
+                        mma_bf16(t_acc, sw128_desc(g_addr + kGPanel + kk * 32u), dbh, id_h, 1u);
+                    }
+                } else {
+                    const uint32_t col = static_cast<uint32_t>((a_col + kk) * 8);
+                    mma_bf16_ts(t_acc, t_act + col, dbh, id_h, 1u);
+                    if (X == 3) {
+                        mma_bf16_ts(t_acc, t_act + col, sw128_desc(bl + kk * 32u), id_h, 1u);
+                        mma_bf16_ts(t_acc, t_lo + col, dbh, id_h, 1u);
+                    }
+                }
+            }
+        };
         uint32_t phase = 0, g = 0;
         wait_or_abort(wbar, 0, abort_flag, a.status);
-        for (int p = blockIdx.x; p < a.npairs; p += gridDim.x) {
+        for (int p = blockIdx.x; p < rounds_total; p += gridDim.x) {
             if (wg_bar_any(1 + wg, *abort_flag != 0, kGroup)) break;
-            const int tile = 2 * p + wg;
+            const int tile = kWGs * p + wg;
             const bool tv = tile < a.ntiles;
             const int q = tv ? tile / a.tpq : 0;
             const int n = tv ? (tile % a.tpq) * kTile + my_row : a.N;
             const bool rv = n < a.N;
-            // gamma(mean_n) -> this tile's panel, 16-byte chunks 4 half .. 4 half + 3
-            {
+            // gamma(mean_n) -> this tile's panel(s), 16-byte chunks 4 half .. 4 half + 3
+            for (int t = 0; t < kTerms; ++t) {
                 const uint4 *src = reinterpret_cast<const uint4 *>(
-                    a.G + static_cast<size_t>(rv ? n : 0) * kGammaCols);
+                    a.G + (static_cast<size_t>(t) * a.N + (rv ? n : 0)) * kGammaCols);
 #pragma unroll
                 for (int c = 4 * half; c < 4 * half + 4; ++c) {
                     const uint4 v = rv ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
-                    *reinterpret_cast<uint4 *>(G + my_row * 128 + ((c ^ (my_row & 7)) << 4)) = v;
+                    *reinterpret_cast<uint4 *>(G + t * kGPanel + my_row * 128 +
+                                               ((c ^ (my_row & 7)) << 4)) = v;
                 }
             }
             write_term(load_term(q, 0));
@@ -394,25 +454,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                     // D = vec[q][l] (hi + lo), then += W_l x
                     mma_bf16(t_acc, d_sel, d_term, id_h, 0u);
                     const int np = panels_of(l);
-                    for (int i = 0; i < np; ++i, ++g) {
-                        const int slot = static_cast<int>(g % kRing);
-                        wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
-                        tc_fence_after();
-                        const uint32_t b_addr = ring_addr + static_cast<uint32_t>(slot) * kBPanel;
+                    for (int i = 0; i < np; ++i) {
                         const int pid = (l == 0 || i == 3) ? kGammaPanel : i;
+                        uint32_t b_addr[2];
+                        int slots[2];
+                        for (int t = 0; t < kTerms; ++t, ++g) {
+                            slots[t] = static_cast<int>(g % kRing);
+                            wait_or_abort(&full[slots[t]], (g / kRing) & 1u, abort_flag, a.status);
+                            b_addr[t] = ring_addr + static_cast<uint32_t>(slots[t]) * kBPanel;
+                        }
+                        tc_fence_after();
                         if (pid == kGammaPanel) {
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u),
-                                         sw128_desc(b_addr + kk * 32u), id_h, 1u);
+                            panel_mmas(b_addr[0], b_addr[kTerms - 1], true, 0, 4);
                         } else {
                             // activations K 64 pid .. (K 128..159 for pid 2)
-                            const int nk = pid == 2 ? 2 : 4;
-                            for (int kk = 0; kk < nk; ++kk)
-                                mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>((4 * pid + kk) * 8),
-                                            sw128_desc(b_addr + kk * 32u), id_h, 1u);
+                            panel_mmas(b_addr[0], b_addr[kTerms - 1], false, 4 * pid,
+                                       pid == 2 ? 2 : 4);
                         }
-                        mma_commit(&empty[slot]);
+                        for (int t = 0; t < kTerms; ++t) mma_commit(&empty[slots[t]]);
                     }
                     mma_commit(&accb[wg]);
                 }
@@ -423,21 +482,33 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                 tc_fence_after();
                 write_term(tnext);  // the layer-l MMAs that read the image are complete
                 // this warp's 80 accumulator columns -> 40 activation columns
+                // (and, X = 3, 40 columns of the BF16 remainders)
 #pragma unroll 1
                 for (int c = 0; c < 3; ++c) {
                     const int col = 80 * half + 32 * c;
+                    const int nv = c < 2 ? 32 : 16;
                     float v[32];
-                    uint32_t pk[16];
-                    if (c < 2) {
+                    uint32_t pk[16], pl[16];
+                    if (c < 2)
                         tmem_ld32(t_acc + lane_off + col, v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
-                        tmem_st16(t_act + lane_off + col / 2, pk);
-                    } else {
+                    else
                         tmem_ld16(t_acc + lane_off + col, v);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+                    for (int j = 0; j < 16; ++j) {
+                        if (2 * j >= nv) break;
+                        pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+                        if (X == 3) {
+                            const float r0 = fmaxf(v[2 * j], 0.f), r1 = fmaxf(v[2 * j + 1], 0.f);
+                            pl[j] = pack_bf16(__fsub_rn(r0, __uint_as_float(pk[j] << 16)),
+                                              __fsub_rn(r1, __uint_as_float(pk[j] & 0xFFFF0000u)));
+                        }
+                    }
+                    if (c < 2) {
+                        tmem_st16(t_act + lane_off + col / 2, pk);
+                        if (X == 3) tmem_st16(t_lo + lane_off + col / 2, pl);
+                    } else {
                         tmem_st8(t_act + lane_off + col / 2, pk);
+                        if (X == 3) tmem_st8(t_lo + lane_off + col / 2, pl);
                     }
                 }
                 tmem_wait_st();
@@ -450,11 +521,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
                 tc_fence_after();
                 mma_bf16(t_acc, d_sel, d_term, id_o, 0u);  // D = output bias (hi + lo)
 #pragma unroll
-                for (int kk = 0; kk < kPW / 16; ++kk)
-                    mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8),
-                                sw128_desc(o_addr + static_cast<uint32_t>(kk >> 2) * kOutPanel +
-                                           static_cast<uint32_t>(kk & 3) * 32u),
-                                id_o, 1u);
+                for (int kk = 0; kk < kPW / 16; ++kk) {
+                    const uint32_t ob = o_addr + static_cast<uint32_t>(kk >> 2) * kOutPanel +
+                                        static_cast<uint32_t>(kk & 3) * 32u;
+                    mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8), sw128_desc(ob), id_o, 1u);
+                    if (X == 3) {
+                        mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8),
+                                    sw128_desc(ob + kOutImg), id_o, 1u);
+                        mma_bf16_ts(t_acc, t_lo + static_cast<uint32_t>(kk * 8), sw128_desc(ob),
+                                    id_o, 1u);
+                    }
+                }
                 mma_commit(&accb[wg]);
             }
             if (mma_warp) __syncwarp();
@@ -484,12 +561,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) paper_tc_kernel(PaperTcArgs a) 
 }  // namespace
 
 size_t paper_tc_image_bytes(int n_hidden) {
-    return static_cast<size_t>(seq_len(n_hidden)) * kBPanel + kOutImg;
+    // room for the hi and lo images (three-product precision)
+    return 2 * (static_cast<size_t>(seq_len(n_hidden)) * kBPanel + kOutImg);
 }
 
-cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, const GridView &g,
-                            const float *tx, int Q, const PaperWs &ws, float4 *rec, int *status,
-                            cudaStream_t st) {
+namespace {
+
+template <int X>
+cudaError_t launch_paper_tc_x(const PaperSceneView &sv, const PaperMlpView &mv, const GridView &g,
+                              const float *tx, int Q, const PaperWs &ws, float4 *rec, int *status,
+                              cudaStream_t st) {
+    using Cfg = TcCfg<X>;
     const long long rows = static_cast<long long>(Q) * sv.n;
     if (rows == 0) return cudaSuccess;
     PaperNetTc m{};
@@ -511,13 +593,13 @@ cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, co
     PaperView s{sv.n, sv.mu, sv.chol, sv.attn_logit, sv.psi};
     const int nseq = seq_len(m.n_hidden);
     uint16_t *wimg = ws.img;
-    uint16_t *oimg = ws.img + static_cast<size_t>(nseq) * kBPanel / 2;
+    uint16_t *oimg = ws.img + static_cast<size_t>(Cfg::Terms * nseq) * kBPanel / 2;
     {
         const int nb_vec = Q * (kPaperMaxLayers - 1);
         const int nb_gamma = (sv.n + kPW - 1) / kPW;
         const int nb_w = 148 * 4;  // 592 x 160 threads, about the 296 x 256 of a separate launch
         paper_tc_prep_kernel<<<nb_vec + nb_gamma + nb_w, kPW, 0, st>>>(
-            m, nseq, wimg, oimg, s, ws.G, tx, ws.vec, nb_vec, nb_gamma);
+            m, nseq, wimg, oimg, s, ws.G, tx, ws.vec, nb_vec, nb_gamma, Cfg::Terms);
     }
     PaperTcArgs a{};
     a.s = s;
@@ -535,20 +617,31 @@ cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, co
     const long long nt = static_cast<long long>(a.tpq) * Q;
     if (nt >= (1ll << 30)) return cudaErrorInvalidValue;
     a.ntiles = static_cast<int>(nt);
-    a.npairs = (a.ntiles + 1) / 2;
     a.rec = rec;
     a.rec_im = reinterpret_cast<float *>(rec + 2 * rows);
     a.status = status;
-    const size_t smem = tc_smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(paper_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = Cfg::smem;
+    cudaError_t e = cudaFuncSetAttribute(paper_tc_kernel<X>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int grid = a.npairs < sms ? a.npairs : sms;
-    paper_tc_kernel<<<grid, kTcThreads, smem, st>>>(a);
+    const int rounds = (a.ntiles + Cfg::WGs - 1) / Cfg::WGs;
+    const int grid = rounds < sms ? rounds : sms;
+    paper_tc_kernel<X><<<grid, Cfg::Threads, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_paper_tc(const PaperSceneView &sv, const PaperMlpView &mv, const GridView &g,
+                            const float *tx, int Q, const PaperWs &ws, float4 *rec, int *status,
+                            int precision, cudaStream_t st) {
+    return precision == WRF_BF16X3
+               ? launch_paper_tc_x<3>(sv, mv, g, tx, Q, ws, rec, status, st)
+               : launch_paper_tc_x<1>(sv, mv, g, tx, Q, ws, rec, status, st);
 }
 
 }  // namespace wrf

@@ -324,25 +324,26 @@ def test_paper_bf16_query_alone_equals_batch_and_repeats(api):
     assert torch.equal(one[0], rec[3])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
 def test_paper_workload_full_size_sampled(api, precision):
     """The bench's paper workload as the bench launches it (20,000 Gaussians,
     64 TX, 360x90, tile 32x8, unit-gain network with small biases): two whole
-    queries of the batch against the oracle -- the FP64 head for FP32, the
+    queries of the batch against the oracle -- the FP64 head for FP32 and for
+    the three-product BF16 network (both held to 1e-4 x peak), the
     projection and render of the BF16-emulated residuals for BF16."""
     import math as _m
     import oracle
     sc = synth.make_paper_scene(20000, H, W, ls_mean=_m.log(3.0), ls_std=0.3, seed=0)
     m = synth.make_paper_mlp(gain=1.0, bias_std=0.05, seed=0)
     tx = synth.make_tx(64, seed=1)
-    prec = api.WRF_BF16 if precision == "bf16" else api.WRF_FP32
+    prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[precision]
     r = api.Renderer(api.make_grid(H, W, 32, 8, 9.0), dev())
     out = r.forward_paper(api.DevicePaperScene.from_host(sc, dev()),
                           api.DevicePaperMLP.from_host(m, dev(), precision=prec), T(tx))
     torch.cuda.synchronize()
     picks = [0, 37]
     g = out.cpu().numpy()[picks].astype(np.float64)
-    if precision == "fp32":
+    if precision in ("fp32", "bf16x3"):
         mag, ph, re, im, slack, _ = paper.forward(sc, m, tx[picks], H, W, 9.0)
         tol = 1e-4
     else:
@@ -356,6 +357,43 @@ def test_paper_workload_full_size_sampled(api, precision):
     ok_im, e_im, _ = spectrum_error(g[:, 0] * np.sin(g[:, 1]), im, slack, tol)
     print(f"paper workload {precision}, queries {picks}: re {e_re:.2e}, im {e_im:.2e} (x peak)")
     assert ok_re and ok_im
+
+
+@pytest.mark.parametrize("N,Q", [(1000, 3), (5, 1), (300, 7)])
+@pytest.mark.parametrize("shape", [(156, 8), (100, 3), (17, 5)])
+def test_paper_bf16x3_records_match_oracle(api, N, Q, shape):
+    """Three-product BF16 network: records against the FP64 head (centres,
+    weights) at the FP32 path's bound, for ragged / single-row / odd tile
+    counts and several network shapes."""
+    width, n_hidden = shape
+    sc = synth.make_paper_scene(N, H, W, seed=N + width)
+    m = paper_mlp(N, width=width, n_hidden=n_hidden)
+    tx = synth.make_tx(Q, seed=N)
+    ds = api.DevicePaperScene.from_host(sc, dev())
+    dm = api.DevicePaperMLP.from_host(m, dev(), precision=api.WRF_BF16X3)
+    rec = api.wrf_paper_deform_project(ds, dm, api.make_grid(H, W, 16, 16, 9.0), T(tx))
+    torch.cuda.synchronize()
+    g = rec.cpu().numpy().astype(np.float64)
+    tail = api.record_tail(rec, Q, N).cpu().numpy()
+    got = residuals_from_records(g, tail, sc)
+    want = emulated_records(sc, paper.residuals(sc, m, tx, H, W))
+    scale = np.abs(want).max(axis=(0, 1))
+    rel = float((np.abs(got - want) / scale).max())
+    print(f"paper bf16x3 N={N} Q={Q} {width}x{n_hidden}: records vs FP64 oracle {rel:.1e}")
+    assert rel <= 1e-4
+
+
+def test_paper_bf16x3_query_alone_equals_batch(api):
+    sc = synth.make_paper_scene(700, H, W, seed=14)
+    m = paper_mlp(14)
+    tx = synth.make_tx(5, seed=14)
+    ds = api.DevicePaperScene.from_host(sc, dev())
+    dm = api.DevicePaperMLP.from_host(m, dev(), precision=api.WRF_BF16X3)
+    grid = api.make_grid(H, W, 16, 16, 9.0)
+    rec = api.wrf_paper_deform_project(ds, dm, grid, T(tx)).clone()
+    one = api.wrf_paper_deform_project(ds, dm, grid, T(tx[2:3]))
+    torch.cuda.synchronize()
+    assert torch.equal(one[0], rec[2])
 
 
 @pytest.mark.parametrize("precision", ["fp32", "bf16", "none"])
