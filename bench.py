@@ -56,8 +56,8 @@ Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
 # ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, tile_w, tile_h)
 NCU_TRAFFIC = {
-    ("render_kernel", 20000, 256, 90, 360, 32, 8): 263.165184e6 + 28.148992e6,
-    ("mlp_tc_kernel", 20000, 256, 90, 360, 32, 8): 2.130432e6 + 104.015360e6,
+    ("render_kernel", 20000, 256, 90, 360, "32x8p2b1"): 263.165184e6 + 28.148992e6,
+    ("mlp_tc_kernel", 20000, 256, 90, 360, "32x8p2b1"): 2.130432e6 + 104.015360e6,
 }
 RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
 BIN_BYTES_PER_REC = 32   # each record read once
@@ -74,7 +74,9 @@ def parse():
     p.add_argument("--precision", default=None, choices=["bf16", "bf16x3", "fp32"],
                    help="network precision (default: bf16; the paper workload: bf16x3, the "
                         "three-product BF16 network held to the FP32 tolerance)")
-    p.add_argument("--tile", default="auto", help="WxH, or auto (autotuned, cached)")
+    p.add_argument("--tile", default="auto",
+                   help="rasteriser configuration WxH or WxHpPXbBF (tile, pixels per thread, "
+                        "records per thread per batch), or auto (autotuned, cached)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU-oracle time of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -129,6 +131,15 @@ def make_inputs(workload, rank, channels=1):
     m = synth.make_mlp(seed=0)
     tx = synth.make_tx(Q, seed=1 + rank)
     return sc, m, tx, (N, H, W, Q)
+
+
+def launch_cfg(args, default):
+    """The rasteriser configuration (tile_w, tile_h, px_per_thread,
+    batch_factor): --tile WxH or WxHpPXbBF, else the workload's default."""
+    from paper_2506_12787_b300 import autotune
+    cfg = default if args.tile == "auto" else autotune.parse_config(args.tile)
+    args.tile = autotune.config_name(*cfg)
+    return cfg
 
 
 def config_of(args, shape, extra=None):
@@ -492,8 +503,8 @@ def run_mixed(args):
     dev = torch.device("cuda", local)
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
     H, W, Q = 90, 360, 256
-    tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
-    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    tw, th, px, bf = launch_cfg(args, (32, 8, 2, 1))
+    grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
     hosts = [synth.make_scene(n, H, W, seed=200 + i) for i, n in enumerate(sizes)]
     mlps = [synth.make_mlp(seed=300 + i) for i in range(len(sizes))]
     ds = [api.DeviceScene.from_host(h, dev) for h in hosts]
@@ -580,8 +591,8 @@ def run_train(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = make_inputs("train", rank)
     N, H, W, Q = shape
-    tw, th = (16, 16) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
-    cfg = SpectrumConfig(api.make_grid(H, W, tw, th, Q_CUT))
+    tw, th, px, bf = launch_cfg(args, (16, 16, 2, 1))
+    cfg = SpectrumConfig(api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf))
     tx = torch.as_tensor(tx_np, device=dev)
     tgt_scene = synth.jitter_means(sc, 2.0, seed=4)
     ds_t = api.DeviceScene.from_host(tgt_scene, dev)
@@ -874,9 +885,8 @@ def run_paper(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = paper_inputs(rank)
     N, H, W, Q = shape
-    tw, th = (32, 8) if args.tile == "auto" else (int(v) for v in args.tile.split("x"))
-    args.tile = f"{tw}x{th}"
-    grid = api.make_grid(H, W, tw, th, Q_CUT)
+    tw, th, px, bf = launch_cfg(args, (32, 8, 2, 1))
+    grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
     prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[args.precision]
     ds = api.DevicePaperScene.from_host(sc, dev)
     dm = api.DevicePaperMLP.from_host(m, dev, precision=prec)
@@ -1076,13 +1086,13 @@ def main():
     dm = api.DeviceMLP.from_host(m, dev, precision=prec)
     tx = torch.as_tensor(tx_np, device=dev)
     tune_ms = None
+    from paper_2506_12787_b300 import autotune
     if args.tile == "auto":
-        from paper_2506_12787_b300 import autotune
-        (tw, th), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
+        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
+        args.tile = autotune.config_name(tw, th, px, bf)
     else:
-        tw, th = (int(v) for v in args.tile.split("x"))
-    args.tile = f"{tw}x{th}"
-    grid = api.make_grid(H, W, tw, th, Q_CUT, wrap=args.wrap)
+        tw, th, px, bf = launch_cfg(args, None)
+    grid = autotune.make_grid(H, W, (tw, th, px, bf), Q_CUT, wrap=args.wrap)
     stream = torch.cuda.Stream(device=dev)
     fw = BatchedForward(ds, dm, grid, Q, dev)
     with torch.cuda.stream(stream):
@@ -1213,7 +1223,7 @@ def main():
     # one ncu capture of this kernel on this exact workload and tile shape
     # (profiles/render_batched.txt, profiles/mlp_tc_batched.txt); null for any
     # other configuration
-    tkey = (roof["kernel"], N, Q, H, W, tw, th)
+    tkey = (roof["kernel"], N, Q, H, W, autotune.config_name(tw, th, px, bf))
     roof["traffic"] = NCU_TRAFFIC.get(tkey)
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (ncu)"

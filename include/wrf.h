@@ -101,12 +101,24 @@ typedef struct {
  * rendered with the image nearest to it; this needs q_cut finite and every
  * footprint narrower than W - tile_w pixels (2 rx < W - tile_w), else the
  * device status word records WRF_EUNSUPPORTED.  wrap_x = 0: a flat plane
- * clipped at the edges. */
+ * clipped at the edges.
+ * Rasteriser knobs (they change how the work is laid out, not the result
+ * beyond FP32 summation order, which they keep: each pixel sums its
+ * Gaussians in the same ascending order whatever the knobs):
+ *   px_per_thread  pixels one thread accumulates: 2 (default) or 4 (needs
+ *                  tile_w >= 16);
+ *   batch_factor   Gaussian records each thread stages per shared-memory
+ *                  batch: 1 (default) or 2 (a batch then holds 2 x threads
+ *                  records).
+ * 0 selects the default.  wrf_render_complex supports the defaults only
+ * (else WRF_EUNSUPPORTED). */
 typedef struct {
     int32_t H, W;
     int32_t tile_w, tile_h;
     float q_cut;
     int32_t wrap_x;
+    int32_t px_per_thread;
+    int32_t batch_factor;
 } wrf_grid;
 
 /* Projected record of one deformed Gaussian for one query: 8 floats, 32-byte

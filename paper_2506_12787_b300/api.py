@@ -122,9 +122,13 @@ class DeviceMLP:
         return m
 
 
-def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0, wrap=False) -> _lib.Grid:
-    """Spectrum grid; wrap=True makes the azimuth axis periodic (0 = 360 degrees)."""
-    return _lib.Grid(H, W, tile_w, tile_h, float(q_cut), int(bool(wrap)))
+def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0, wrap=False, px_per_thread=0,
+              batch_factor=0) -> _lib.Grid:
+    """Spectrum grid; wrap=True makes the azimuth axis periodic (0 = 360 degrees).
+    px_per_thread (2 or 4) and batch_factor (1 or 2) are the rasteriser's layout
+    knobs (0 = default 2 and 1)."""
+    return _lib.Grid(H, W, tile_w, tile_h, float(q_cut), int(bool(wrap)), int(px_per_thread),
+                     int(batch_factor))
 
 
 def tiles_of(grid) -> int:

@@ -144,6 +144,12 @@ wrf_status check_grid(const wrf_grid *g, wrf::GridView *v) {
     if (g->wrap_x && !(g->q_cut < INFINITY)) return fail(WRF_EINVAL, "wrap_x needs a finite q_cut");
     v->wrap = g->wrap_x;
     if (v->T > 3000) return fail(WRF_EUNSUPPORTED, "more than 3000 tiles");
+    v->px = g->px_per_thread ? g->px_per_thread : 2;
+    v->bpt = g->batch_factor ? g->batch_factor : 1;
+    if (v->px != 2 && v->px != 4) return fail(WRF_EUNSUPPORTED, "px_per_thread must be 2 or 4");
+    if (v->bpt != 1 && v->bpt != 2) return fail(WRF_EUNSUPPORTED, "batch_factor must be 1 or 2");
+    if (v->px == 4 && g->tile_w < 16)
+        return fail(WRF_EUNSUPPORTED, "px_per_thread 4 needs tile_w >= 16");
     return WRF_OK;
 }
 
@@ -759,6 +765,8 @@ wrf_status wrf_render_complex(const float *rec, const uint32_t *gids,
     wrf_status s;
     wrf::GridView g{};
     if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (g.px != 2 || g.bpt != 1)
+        return fail(WRF_EUNSUPPORTED, "render_complex takes the default rasteriser knobs only");
     if (n < 0 || Q < 0) return fail(WRF_EINVAL, "negative size");
     if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
     if (Q == 0) return WRF_OK;

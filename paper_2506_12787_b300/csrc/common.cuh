@@ -21,6 +21,8 @@ struct GridView {
     int H, W, tw, th, ntx, nty, T;
     float q_cut;
     int wrap;  // azimuth wrap: columns 0 and W are the same direction
+    int px;    // rasteriser: pixels per thread (2 or 4)
+    int bpt;   // rasteriser: Gaussian records per thread in a staged batch (1 or 2)
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

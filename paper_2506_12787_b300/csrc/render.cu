@@ -52,10 +52,10 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 
 // Shared-memory carve-up of the forward kernel for a tile with NT threads
-// (two pixels each) and TH rows: a batch holds B = NT records, one per thread.
-template <int NT, int TH>
+// and TH rows: a batch holds B = BF x NT records, BF per thread.
+template <int NT, int TH, int BF>
 struct FwdSmem {
-    static constexpr int B = NT, NW = NT / 32, RS = B + 1;  // RS: bank spread
+    static constexpr int B = NT * BF, NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
     static constexpr size_t rowc = raw + 2 * B * 32;           // [TH/2][RS] float4, row pairs
     static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float4 (c3, c3, w, 0)
@@ -67,16 +67,22 @@ struct FwdSmem {
 // CH = 1: one channel, out [Q][H][W].  CH = 2: real and imaginary channels
 // (weights w from the records, w_im from rec_im [Q][N]) summed with one ex2
 // per pixel and Gaussian, out [Q][2][H][W] = magnitude, phase (Sec. 6.1).
-template <int TW, int TH, int CH, bool WRAP>
-__global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
+// PX: pixels per thread, 2 (rows y, y + 4 of an 8 x 8 warp block) or 4 (also
+// columns x + 8: a 16 x 8 warp block; one row-pair entry serves both
+// columns).  BF: records per thread in a staged batch (the batch holds
+// BF x threads Gaussians).
+template <int TW, int TH, int CH, bool WRAP, int PX, int BF>
+__global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im,
     const long long *__restrict__ qbase) {
-    constexpr int NT = TW * TH / 2, B = NT, NW = NT / 32;
-    constexpr int NSX = TW / 8;  // warp blocks of 8 x 8 pixels: NSX across, TH/8 down
-    static_assert(NW == NSX * (TH / 8), "one 8x8 pixel block per warp");
-    using L = FwdSmem<NT, TH>;
+    constexpr int NT = TW * TH / PX, B = NT * BF, NW = NT / 32;
+    constexpr int BW = 4 * PX;   // warp block width: 8 or 16 columns
+    constexpr int NSX = TW / BW;  // warp blocks of BW x 8 pixels: NSX across, TH/8 down
+    static_assert(NW == NSX * (TH / 8), "one warp block per warp");
+    static_assert(CH == 1 || (PX == 2 && BF == 1), "two channels: two pixels, one record each");
+    using L = FwdSmem<NT, TH, BF>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
     float4 *rowc = reinterpret_cast<float4 *>(smem + L::rowc);
@@ -91,9 +97,9 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.x, q = blockIdx.y;
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
-    // this thread's pixels (tile-local): column pxl, rows pyl and pyl + 4;
-    // lx = the column's offset from the tile centre
-    const int pxl = (warp % NSX) * 8 + (lane & 7);
+    // this thread's pixels (tile-local): column pxl (and pxl + 8 when PX = 4),
+    // rows pyl and pyl + 4; lx = the column's offset from the tile centre
+    const int pxl = (warp % NSX) * BW + (lane & 7);
     const int pyl = (warp / NSX) * 8 + (lane >> 3);
     const float lx = static_cast<float>(pxl - TW / 2);
     const float xcen = static_cast<float>(x0 + TW / 2), ycen = static_cast<float>(y0 + TH / 2);
@@ -120,17 +126,25 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     }
     __syncthreads();
     for (int b = 0; b < 2 && b < nb; ++b) {
-        if (tid < total - b * B) {
-            const uint32_t gid = gids[s0 + b * B + tid];
-            bulk_g2s(raw + (b * B + tid) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
-            if (CH == 2) (b == 0 ? wim0 : wim1) = qim[gid];
+#pragma unroll
+        for (int k = 0; k < BF; ++k) {
+            const int i = tid + k * NT;
+            if (i < total - b * B) {
+                const uint32_t gid = gids[s0 + b * B + i];
+                bulk_g2s(raw + (b * B + i) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
+                if (CH == 2) (b == 0 ? wim0 : wim1) = qim[gid];
+            }
         }
     }
-    // this thread's Gaussian id of batch b + 2, loaded one batch early so the
-    // copy is issued without waiting on the index load
-    uint32_t gnext = tid < total - 2 * B ? gids[s0 + 2 * B + tid] : 0u;
+    // this thread's Gaussian ids of batch b + 2, loaded one batch early so the
+    // copies are issued without waiting on the index loads
+    uint32_t gnext[BF];
+#pragma unroll
+    for (int k = 0; k < BF; ++k)
+        gnext[k] = tid + k * NT < total - 2 * B ? gids[s0 + 2 * B + tid + k * NT] : 0u;
 
     float acc0 = 0.f, acc1 = 0.f, acc0i = 0.f, acc1i = 0.f;
+    float acc2 = 0.f, acc3 = 0.f;  // PX = 4: column pxl + 8, rows pyl and pyl + 4
     uint16_t *mylist = lists + warp * B;
     int b = 0;
     for (; b < nb; ++b) {
@@ -145,8 +159,11 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
         //   dx = lx - ux, dy = ly - uy, u = centre - tile centre,
         //   -q' = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
         // and the mask of 8x8 warp blocks its footprint rectangle touches.
-        if (tid < cnt) {
-            const float4 r0 = raw[(buf * B + tid) * 2], r1 = raw[(buf * B + tid) * 2 + 1];
+#pragma unroll
+        for (int k = 0; k < BF; ++k) {
+            const int ri = tid + k * NT;  // the record this thread sets up
+            if (ri >= cnt) break;
+            const float4 r0 = raw[(buf * B + ri) * 2], r1 = raw[(buf * B + ri) * 2 + 1];
             // with azimuth wrap, the image of the Gaussian nearest to this tile
             const float mx = WRAP ? nearest_image_x(r0.x, xcen, g) : r0.x;
             const float ux = mx - xcen, uy = r0.y - ycen;
@@ -159,32 +176,39 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             for (int pr = 0; pr < TH / 2; ++pr) {
                 const float ly0 = static_cast<float>((pr >> 2) * 8 + (pr & 3) - TH / 2);
                 const float ly1 = ly0 + 4.f;
-                rowc[pr * L::RS + tid] =
+                rowc[pr * L::RS + ri] =
                     make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
                                 fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[tid] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim1 : wim0) : 0.f);
+            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim1 : wim0) : 0.f);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
             const float ylo = ceilf(__fsub_rn(r0.y, r1.w)) - static_cast<float>(y0);
             const float yhi = floorf(__fadd_rn(r0.y, r1.w)) - static_cast<float>(y0);
             if (xhi >= 0.f && xlo <= TW - 1.f && yhi >= 0.f && ylo <= TH - 1.f) {
-                const int bx0 = static_cast<int>(fmaxf(xlo, 0.f)) >> 3;
-                const int bx1 = static_cast<int>(fminf(xhi, TW - 1.f)) >> 3;
+                const int bx0 = static_cast<int>(fmaxf(xlo, 0.f)) / BW;
+                const int bx1 = static_cast<int>(fminf(xhi, TW - 1.f)) / BW;
                 const int by0 = static_cast<int>(fmaxf(ylo, 0.f)) >> 3;
                 const int by1 = static_cast<int>(fminf(yhi, TH - 1.f)) >> 3;
                 const uint32_t row = (2u << bx1) - (1u << bx0);
                 for (int by = by0; by <= by1; ++by) mk |= row << (by * NSX);
             }
-            mask[tid] = mk;
+            mask[ri] = mk;
         }
         __syncthreads();
         // raw[buf] is consumed: the copies of batch b+2 can land there now
-        if (b + 2 < nb && tid < total - (b + 2) * B) {
-            bulk_g2s(raw + (buf * B + tid) * 2, qrec + 2 * static_cast<size_t>(gnext), 32, &bar[buf]);
-            if (CH == 2) (buf ? wim1 : wim0) = qim[gnext];
-            if (tid < total - (b + 3) * B) gnext = gids[s0 + (b + 3) * B + tid];
+        if (b + 2 < nb) {
+#pragma unroll
+            for (int k = 0; k < BF; ++k) {
+                const int i = tid + k * NT;
+                if (i < total - (b + 2) * B) {
+                    bulk_g2s(raw + (buf * B + i) * 2, qrec + 2 * static_cast<size_t>(gnext[k]), 32,
+                             &bar[buf]);
+                    if (CH == 2) (buf ? wim1 : wim0) = qim[gnext[k]];
+                    if (i < total - (b + 3) * B) gnext[k] = gids[s0 + (b + 3) * B + i];
+                }
+            }
         }
         // ---- this warp's list: records touching its block, ascending index
         int m = 0;
@@ -202,9 +226,10 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             rowc + ((pyl >> 3) * 4 + (pyl & 3)) * L::RS);
         const char *gcb = reinterpret_cast<const char *>(gcoef);
         const float2 lx2 = make_float2(lx, lx);
+        const float2 lxb = make_float2(lx + 8.f, lx + 8.f);  // PX = 4: the second column
         // unrolled 8 deep at 32 x 8 tiles (0.5 % faster there), 4 elsewhere
         // (8 spills a register at 16 x 16)
-        constexpr int kUnroll = (TW == 32 && TH == 8) ? 8 : 4;
+        constexpr int kUnroll = (TW == 32 && TH == 8 && PX == 2) ? 8 : 4;
 #pragma unroll kUnroll
         for (int j = 0; j < m; ++j) {
             const int o = mylist[j];  // = record index * 16
@@ -215,6 +240,12 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
             if (CH == 1) {
                 if (nq.x >= ncut) acc0 = fmaf(cw.z, ex2_approx(nq.x), acc0);
                 if (nq.y >= ncut) acc1 = fmaf(cw.z, ex2_approx(nq.y), acc1);
+                if (PX == 4) {
+                    const float2 tb = fma2(make_float2(cw.x, cw.y), lxb, make_float2(ab.z, ab.w));
+                    const float2 nqb = fma2(tb, lxb, make_float2(ab.x, ab.y));
+                    if (nqb.x >= ncut) acc2 = fmaf(cw.z, ex2_approx(nqb.x), acc2);
+                    if (nqb.y >= ncut) acc3 = fmaf(cw.z, ex2_approx(nqb.y), acc3);
+                }
             } else {
                 if (nq.x >= ncut) {
                     const float e = ex2_approx(nq.x);
@@ -240,6 +271,10 @@ __global__ void __launch_bounds__(TW *TH / 2, 2048 / (TW * TH)) render_kernel(
     if (CH == 1) {
         stile[pyl][pxl] = acc0;
         stile[pyl + 4][pxl] = acc1;
+        if (PX == 4) {
+            stile[pyl][pxl + 8] = acc2;
+            stile[pyl + 4][pxl + 8] = acc3;
+        }
     } else {
         // magnitude and phase of re + i im (arg 0 = 0)
         stile[pyl][pxl] = sqrtf(fmaf(acc0, acc0, acc0i * acc0i));
@@ -328,12 +363,13 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     }
 }
 
-template <int TW, int TH, int CH>
-cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
-                       const long long *n_keys, long long cap, int n, int Q, const GridView &g,
-                       float *out, int *status, cudaStream_t st, const long long *qbase) {
-    const size_t smem = FwdSmem<TW * TH / 2, TH>::bytes;
-    auto kern = g.wrap ? render_kernel<TW, TH, CH, true> : render_kernel<TW, TH, CH, false>;
+template <int TW, int TH, int CH, int PX, int BF>
+cudaError_t launch_fwd_x(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
+                         const long long *n_keys, long long cap, int n, int Q, const GridView &g,
+                         float *out, int *status, cudaStream_t st, const long long *qbase) {
+    const size_t smem = FwdSmem<TW * TH / PX, TH, BF>::bytes;
+    auto kern = g.wrap ? render_kernel<TW, TH, CH, true, PX, BF>
+                       : render_kernel<TW, TH, CH, false, PX, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
@@ -341,9 +377,31 @@ cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *
     // two channels: the imaginary weights follow the Q x N records
     const float *rec_im =
         CH == 2 ? reinterpret_cast<const float *>(rec + 2 * static_cast<size_t>(Q) * n) : nullptr;
-    kern<<<grid, TW * TH / 2, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                          -g.q_cut * kHalfLog2e, out, status, rec_im, qbase);
+    kern<<<grid, TW * TH / PX, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
+                                           -g.q_cut * kHalfLog2e, out, status, rec_im, qbase);
     return cudaGetLastError();
+}
+
+// The rasteriser's knobs (pixels per thread, records per thread per batch):
+// every combination for one channel (PX = 4 needs tiles at least 16 wide);
+// two channels take the default (2, 1) only.
+template <int TW, int TH, int CH>
+cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
+                       const long long *n_keys, long long cap, int n, int Q, const GridView &g,
+                       float *out, int *status, cudaStream_t st, const long long *qbase) {
+    if (g.px == 2 && g.bpt == 1)
+        return launch_fwd_x<TW, TH, CH, 2, 1>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+    if constexpr (CH == 1) {
+        if (g.px == 2 && g.bpt == 2)
+            return launch_fwd_x<TW, TH, 1, 2, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+        if constexpr (TW >= 16) {
+            if (g.px == 4 && g.bpt == 1)
+                return launch_fwd_x<TW, TH, 1, 4, 1>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+            if (g.px == 4 && g.bpt == 2)
+                return launch_fwd_x<TW, TH, 1, 4, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+        }
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int CH>

@@ -64,6 +64,36 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert st == _lib.WRF_EUNSUPPORTED  # hidden width 100
 
 
+def test_rasteriser_knob_validation(lib):
+    """Pixels per thread 2 or 4 (4 needs tiles >= 16 wide), records per thread
+    1 or 2; 0 picks the default; the complex renderer takes the defaults only."""
+    from paper_2506_12787_b300 import _lib, autotune
+    def render(g):
+        return lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None)
+    for px, bf, want in [(3, 0, _lib.WRF_EUNSUPPORTED), (0, 3, _lib.WRF_EUNSUPPORTED),
+                         (1, 1, _lib.WRF_EUNSUPPORTED), (4, 2, _lib.WRF_EINVAL),
+                         (0, 0, _lib.WRF_EINVAL), (2, 1, _lib.WRF_EINVAL)]:
+        # WRF_EINVAL: the knobs pass and the NULL outputs are caught next
+        assert render(_lib.Grid(90, 360, 16, 16, 9.0, 0, px, bf)) == want, (px, bf)
+    assert render(_lib.Grid(90, 360, 8, 8, 9.0, 0, 4, 1)) == _lib.WRF_EUNSUPPORTED
+    assert b"tile_w" in lib.wrf_last_error()
+    g = _lib.Grid(90, 360, 16, 16, 9.0, 0, 4, 1)
+    assert lib.wrf_render_complex(None, None, None, None, 0, 0, 1, C.byref(g), None,
+                                  None) == _lib.WRF_EUNSUPPORTED
+    # the autotuner's search space is exactly the supported combinations
+    sp = autotune.space()
+    assert len(sp) == 5 * 4 - 2 and len(set(sp)) == len(sp)
+    for tw, th, px, bf in sp:
+        assert render(_lib.Grid(90, 360, tw, th, 9.0, 0, px, bf)) == _lib.WRF_EINVAL
+    assert sorted({autotune.batch_records(*c) for c in sp}) == [32, 64, 128, 256, 512]
+    assert autotune.parse_config("32x8") == (32, 8, 2, 1)
+    assert autotune.parse_config("16x16p4b2") == (16, 16, 4, 2)
+    assert autotune.config_name(*autotune.parse_config("32x16p2b2")) == "32x16p2b2"
+    k1 = autotune.workload_key(20000, 90, 360, 256, 1, 9.0)
+    k2 = autotune.workload_key(20000, 90, 360, 256, 1, 9.0, candidates=sp[:3])
+    assert k1 != k2  # the key names the search space
+
+
 def test_paper_head_host_validation(lib):
     """The paper head's entry point checks its network shape on the host."""
     from paper_2506_12787_b300 import _lib
