@@ -4,10 +4,12 @@
 // Forward: one CTA per (tile, query), one thread per two pixels; warp w owns
 // an 8 x 8 pixel block of the tile and lane l the pixels (l % 8, l / 8) and
 // (l % 8, l / 8 + 4) of it.  The tile's Gaussian list (ascending id) is
-// streamed through shared memory in batches of one record per thread: every
-// thread issues one 32-byte cp.async.bulk (TMA bulk copy), completion is
-// counted in bytes on an mbarrier, and two landing buffers alternate so the
-// next batch is in flight while the current one is evaluated.  Once per
+// streamed through shared memory in batches of one record per thread (or
+// two, a launch knob): every thread copies its own records with two 16-byte
+// cp.async each into its own slots of two landing buffers that alternate, so
+// the batch after next is in flight while the current one is evaluated, and
+// waits for its own copies only (cp.async.wait_group; the thread that copies
+// a record is the one that sets it up).  Once per
 // (tile, Gaussian) a thread turns the record into the polynomial
 //   -q'(lx, ly) = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
 // in the pixel's offset (lx, ly) from the tile centre (q' = q log2(e)/2), and
@@ -89,8 +91,6 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     float4 *gcoef = reinterpret_cast<float4 *>(smem + L::gc);
     uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int abort_flag;
     __shared__ __align__(16) float stile[TH][TW];
     __shared__ __align__(16) float stile_im[CH == 2 ? TH : 1][CH == 2 ? TW : 1];
 
@@ -104,11 +104,11 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     const float lx = static_cast<float>(pxl - TW / 2);
     const float xcen = static_cast<float>(x0 + TW / 2), ycen = static_cast<float>(y0 + TH / 2);
 
-    uint32_t s0 = 0, s1 = 0;
-    if (*n_keys <= cap) {
-        s0 = offs[static_cast<size_t>(q) * g.T + t];
-        s1 = offs[static_cast<size_t>(q) * g.T + t + 1];
-    }
+    // the offsets array always has Q x T + 1 entries, so both loads are
+    // issued together with the key count; an overflowed binning renders zero
+    uint32_t s0 = offs[static_cast<size_t>(q) * g.T + t];
+    uint32_t s1 = offs[static_cast<size_t>(q) * g.T + t + 1];
+    if (*n_keys > cap) s0 = s1 = 0;
     const int total = static_cast<int>(s1 - s0);
     const int nb = (total + B - 1) / B;
     // records of this query (multi-scene batches: at qbase[q])
@@ -116,25 +116,21 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     const float *qim = CH == 2 ? rec_im + static_cast<size_t>(q) * n : nullptr;
     float wim0 = 0.f, wim1 = 0.f;  // imaginary weights of this thread's record, per buffer
 
-    if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        fence_mbar_init();
-        abort_flag = 0;
-        for (int b = 0; b < 2 && b < nb; ++b)
-            mbar_arrive_expect_tx(&bar[b], static_cast<uint32_t>(min(B, total - b * B)) * 32u);
-    }
-    __syncthreads();
-    for (int b = 0; b < 2 && b < nb; ++b) {
+    // batches 0 and 1 in flight; one commit group per batch, empty or not,
+    // so "all but the newest group done" always means "this batch landed"
+    for (int b = 0; b < 2; ++b) {
 #pragma unroll
         for (int k = 0; k < BF; ++k) {
             const int i = tid + k * NT;
             if (i < total - b * B) {
                 const uint32_t gid = gids[s0 + b * B + i];
-                bulk_g2s(raw + (b * B + i) * 2, qrec + 2 * static_cast<size_t>(gid), 32, &bar[b]);
+                const float4 *src = qrec + 2 * static_cast<size_t>(gid);
+                cp_async16(raw + (b * B + i) * 2, src);
+                cp_async16(raw + (b * B + i) * 2 + 1, src + 1);
                 if (CH == 2) (b == 0 ? wim0 : wim1) = qim[gid];
             }
         }
+        cp_async_commit();
     }
     // this thread's Gaussian ids of batch b + 2, loaded one batch early so the
     // copies are issued without waiting on the index loads
@@ -150,10 +146,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     for (; b < nb; ++b) {
         const int buf = b & 1;
         const int cnt = min(B, total - b * B);
-        if (!mbar_wait(&bar[buf], (b >> 1) & 1, status)) abort_flag = 1;
-        if (tid == 0 && b + 2 < nb)
-            mbar_arrive_expect_tx(&bar[buf],
-                                  static_cast<uint32_t>(min(B, total - (b + 2) * B)) * 32u);
+        cp_async_wait_pending<1>();  // this thread's records of batch b
         // ---- per-record set-up, once per (tile, Gaussian):
         // -q'(p) for p = tile centre + (lx, ly) as a polynomial in lx, ly:
         //   dx = lx - ux, dy = ly - uy, u = centre - tile centre,
@@ -197,22 +190,27 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             mask[ri] = mk;
         }
         __syncthreads();
-        // raw[buf] is consumed: the copies of batch b+2 can land there now
-        if (b + 2 < nb) {
+        // this thread's slots of raw[buf] are consumed (it set them up
+        // itself): the copies of batch b+2 can land there now
 #pragma unroll
-            for (int k = 0; k < BF; ++k) {
-                const int i = tid + k * NT;
-                if (i < total - (b + 2) * B) {
-                    bulk_g2s(raw + (buf * B + i) * 2, qrec + 2 * static_cast<size_t>(gnext[k]), 32,
-                             &bar[buf]);
-                    if (CH == 2) (buf ? wim1 : wim0) = qim[gnext[k]];
-                    if (i < total - (b + 3) * B) gnext[k] = gids[s0 + (b + 3) * B + i];
-                }
+        for (int k = 0; k < BF; ++k) {
+            const int i = tid + k * NT;
+            if (i < total - (b + 2) * B) {
+                const float4 *src = qrec + 2 * static_cast<size_t>(gnext[k]);
+                cp_async16(raw + (buf * B + i) * 2, src);
+                cp_async16(raw + (buf * B + i) * 2 + 1, src + 1);
+                if (CH == 2) (buf ? wim1 : wim0) = qim[gnext[k]];
+                if (i < total - (b + 3) * B) gnext[k] = gids[s0 + (b + 3) * B + i];
             }
         }
+        cp_async_commit();
         // ---- this warp's list: records touching its block, ascending index
+        // (the mask loads of all rounds are independent: unrolled, they
+        // overlap)
         int m = 0;
-        for (int base = 0; base < cnt; base += 32) {
+#pragma unroll
+        for (int base = 0; base < B; base += 32) {
+            if (base >= cnt) break;
             const int i = base + lane;
             const bool hit = i < cnt && ((mask[i] >> warp) & 1u);
             const uint32_t bal = __ballot_sync(0xffffffffu, hit);
@@ -260,14 +258,8 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             }
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
-        if (abort_flag) break;
     }
-    if (abort_flag) {
-        // drain copies still in flight (bounded waits) before the CTA exits
-        for (int bb = b; bb < nb && bb <= b + 2; ++bb)
-            mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
-        return;
-    }
+    cp_async_wait_all();  // nothing may be in flight when the CTA exits
     if (CH == 1) {
         stile[pyl][pxl] = acc0;
         stile[pyl + 4][pxl] = acc1;
