@@ -183,6 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
     // K 0..7 and meet the selector's zero core matrix); A = selector p
     const uint64_t d_bias = plain_desc(aug_addr, 0u, 128u);
     const uint64_t d_vimg = plain_desc(smem_u32(vimg), 0u, 128u);
+    // descriptor bases; each MMA advances them by a constant (desc_adv)
+    const uint64_t d_a = sw128_desc(a_addr), d_w1 = sw128_desc(w1_addr);
+    const uint64_t d_wh = sw128_desc(wh_addr), d_sel = plain_desc(sel_addr, 128u, 0u);
     const uint32_t t_acc = tmem_base + static_cast<uint32_t>(wg * 128);
     const uint32_t lane_off = static_cast<uint32_t>(wq * 32) << 16;  // TMEM lane field
     const int my_row = wq * 32 + lane;                               // row within the tile
@@ -239,19 +242,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
                 tc_fence_after();
                 if (l == 0) {
                     // D = V[q] (hi + lo), then += W1m gamma(mean)
-                    mma_bf16(t_acc, plain_desc(sel_addr, 128u, 0u), d_vimg, id128, 0u);
-                    for (int k = 0; k < (a.k1 >> 4); ++k)
-                        mma_bf16(t_acc, sw128_desc(a_addr + k * 32u), sw128_desc(w1_addr + k * 32u),
-                                 id128, 1u);
+                    mma_bf16(t_acc, d_sel, d_vimg, id128, 0u);
+                    mma_bf16(t_acc, d_a, d_w1, id128, 1u);
+                    mma_bf16(t_acc, desc_adv(d_a, 32u), desc_adv(d_w1, 32u), id128, 1u);
+                    if (a.k1 == 64) {
+                        mma_bf16(t_acc, desc_adv(d_a, 64u), desc_adv(d_w1, 64u), id128, 1u);
+                        mma_bf16(t_acc, desc_adv(d_a, 96u), desc_adv(d_w1, 96u), id128, 1u);
+                    }
                 } else {
                     // D = b_l (hi + lo, selector pair l-1), then += W_l h
-                    mma_bf16(t_acc, plain_desc(sel_addr + (l - 1) * 256u, 128u, 0u), d_bias, id128,
-                             0u);
-                    const uint32_t wl = wh_addr + (l - 1) * kLayerBytes;
+                    mma_bf16(t_acc, desc_adv(d_sel, (l - 1) * 256u), d_bias, id128, 0u);
+                    const uint64_t d_wl = desc_adv(d_wh, (l - 1) * kLayerBytes);
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const uint32_t koff = (k >> 2) * 16384u + (k & 3) * 32u;
-                        mma_bf16(t_acc, sw128_desc(a_addr + koff), sw128_desc(wl + koff), id128, 1u);
+                        mma_bf16(t_acc, desc_adv(d_a, koff), desc_adv(d_wl, koff), id128, 1u);
                     }
                 }
                 mma_commit(mbar);
@@ -283,14 +288,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
         // ---- output layer (N = 16, columns 0..4 used), into the same columns
         if (leader) {
             tc_fence_after();
-            const uint32_t wo = wh_addr + a.nh * kLayerBytes;
+            const uint64_t d_wo = desc_adv(d_wh, a.nh * kLayerBytes);
             // D = b_out (selector pair 3), then += W_out h
-            mma_bf16(t_acc, plain_desc(sel_addr + 3 * 256u, 128u, 0u), d_bias, id16, 0u);
+            mma_bf16(t_acc, desc_adv(d_sel, 3 * 256u), d_bias, id16, 0u);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 const uint32_t ka = (k >> 2) * 16384u + (k & 3) * 32u;
                 const uint32_t kb = (k >> 2) * 2048u + (k & 3) * 32u;
-                mma_bf16(t_acc, sw128_desc(a_addr + ka), sw128_desc(wo + kb), id16, 1u);
+                mma_bf16(t_acc, desc_adv(d_a, ka), desc_adv(d_wo, kb), id16, 1u);
             }
             mma_commit(mbar);
         }
