@@ -431,12 +431,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                     if (dw_here) {
                         // dW_l^T += H_l^T D_l (lanes = input units, columns = output units)
                         const uint32_t acc = t_dw + static_cast<uint32_t>(128 * (a.hi - l));
+                        const uint64_t dh = sw128_desc(ht_a), dd = sw128_desc(dt_a);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ah = sw128_desc(ht_a + kk * 32u);
-                            const uint64_t al = sw128_desc(ht_a + kHt + kk * 32u);
-                            const uint64_t bh = sw128_desc(dt_a + kk * 32u);
-                            const uint64_t bl = sw128_desc(dt_a + kDt + kk * 32u);
+                            const uint32_t ko = kk * 32u;
+                            const uint64_t ah = desc_adv(dh, ko), al = desc_adv(dh, kHt + ko);
+                            const uint64_t bh = desc_adv(dd, ko), bl = desc_adv(dd, kDt + ko);
                             mma_bf16(acc, ah, bh, id_dw, 1u);
                             mma_bf16(acc, ah, bl, id_dw, 1u);
                             mma_bf16(acc, al, bh, id_dw, 1u);
@@ -449,14 +449,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                         wait_or_abort(&full[slot], (g / kRing) & 1u, abort_flag, a.status);
                         tc_fence_after();
                         const uint32_t wa = ring_a + static_cast<uint32_t>(slot) * kPanel;
+                        const uint64_t dwa = sw128_desc(wa);
+                        const uint64_t dmn = sw128_desc_lbo(dt_a, kMnLbo, 1024u);
 #pragma unroll
                         for (int k4 = 0; k4 < 4; ++k4) {
                             const int kk = (pn & 1) * 4 + k4;
-                            const uint64_t aw = sw128_desc(wa + k4 * 32u);
-                            const uint64_t bh = sw128_desc_lbo(dt_a + kk * 2048u, kMnLbo, 1024u);
+                            const uint64_t aw = desc_adv(dwa, k4 * 32u);
+                            const uint64_t bh = desc_adv(dmn, kk * 2048u);
                             if (pn < 2) {
-                                const uint64_t bl =
-                                    sw128_desc_lbo(dt_a + kDt + kk * 2048u, kMnLbo, 1024u);
+                                const uint64_t bl = desc_adv(dmn, kDt + kk * 2048u);
                                 mma_bf16(t_dl, aw, bh, id_dl, (pn == 0 && k4 == 0) ? 0u : 1u);
                                 mma_bf16(t_dl, aw, bl, id_dl, 1u);
                             } else {
@@ -515,12 +516,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                         }
                         tc_fence_after();
                         const uint32_t ga = ring_a + static_cast<uint32_t>(slot) * kPanel;
+                        const uint64_t dd = sw128_desc(dt_a), dg = sw128_desc_lbo(ga, kMnLbo, 1024u);
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ah = sw128_desc(dt_a + kk * 32u);
-                            const uint64_t al = sw128_desc(dt_a + kDt + kk * 32u);
-                            const uint64_t bh = sw128_desc_lbo(ga + kk * 2048u, kMnLbo, 1024u);
-                            const uint64_t bl = sw128_desc_lbo(ga + kGt + kk * 2048u, kMnLbo, 1024u);
+                            const uint64_t ah = desc_adv(dd, kk * 32u), al = desc_adv(dd, kDt + kk * 32u);
+                            const uint64_t bh = desc_adv(dg, kk * 2048u);
+                            const uint64_t bl = desc_adv(dg, kGt + kk * 2048u);
                             mma_bf16(t_dl, ah, bh, id_dl, kk == 0 ? 0u : 1u);
                             mma_bf16(t_dl, ah, bl, id_dl, 1u);
                             mma_bf16(t_dl, al, bh, id_dl, 1u);

@@ -376,21 +376,25 @@ __global__ void __launch_bounds__(TcCfg<X>::Threads, 1) paper_tc_kernel(PaperTcA
         // MMAs of one weight panel (hi, and lo when X = 3) at K offsets
         // 0 .. nk-1 of 16: A from tensor memory (activation pairs from
         // column a_col) or from the gamma(mean) panel in shared memory
+        // (descriptors advanced from their bases by one add per MMA)
+        const uint64_t d_g = sw128_desc(g_addr);
         auto panel_mmas = [&](uint32_t bh, uint32_t bl, bool gamma, int a_col, int nk) {
+            const uint64_t dbh0 = sw128_desc(bh), dbl0 = sw128_desc(bl);
             for (int kk = 0; kk < nk; ++kk) {
-                const uint64_t dbh = sw128_desc(bh + kk * 32u);
+                const uint32_t ko = static_cast<uint32_t>(kk) * 32u;
+                const uint64_t dbh = desc_adv(dbh0, ko);
                 if (gamma) {
-                    mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u), dbh, id_h, 1u);
+                    const uint64_t dg = desc_adv(d_g, ko);
+                    mma_bf16(t_acc, dg, dbh, id_h, 1u);
                     if (X == 3) {
-                        mma_bf16(t_acc, sw128_desc(g_addr + kk * 32u), sw128_desc(bl + kk * 32u),
-                                 id_h, 1u);
-                        mma_bf16(t_acc, sw128_desc(g_addr + kGPanel + kk * 32u), dbh, id_h, 1u);
+                        mma_bf16(t_acc, dg, desc_adv(dbl0, ko), id_h, 1u);
+                        mma_bf16(t_acc, desc_adv(d_g, kGPanel + ko), dbh, id_h, 1u);
                     }
                 } else {
                     const uint32_t col = static_cast<uint32_t>((a_col + kk) * 8);
                     mma_bf16_ts(t_acc, t_act + col, dbh, id_h, 1u);
                     if (X == 3) {
-                        mma_bf16_ts(t_acc, t_act + col, sw128_desc(bl + kk * 32u), id_h, 1u);
+                        mma_bf16_ts(t_acc, t_act + col, desc_adv(dbl0, ko), id_h, 1u);
                         mma_bf16_ts(t_acc, t_lo + col, dbh, id_h, 1u);
                     }
                 }
@@ -491,16 +495,17 @@ __global__ void __launch_bounds__(TcCfg<X>::Threads, 1) paper_tc_kernel(PaperTcA
             if (leader) {
                 tc_fence_after();
                 mma_bf16(t_acc, d_sel, d_term, id_o, 0u);  // D = output bias (hi + lo)
+                const uint64_t d_o = sw128_desc(o_addr);
 #pragma unroll
                 for (int kk = 0; kk < kPW / 16; ++kk) {
-                    const uint32_t ob = o_addr + static_cast<uint32_t>(kk >> 2) * kOutPanel +
+                    const uint32_t oo = static_cast<uint32_t>(kk >> 2) * kOutPanel +
                                         static_cast<uint32_t>(kk & 3) * 32u;
-                    mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8), sw128_desc(ob), id_o, 1u);
+                    const uint64_t dob = desc_adv(d_o, oo);
+                    mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8), dob, id_o, 1u);
                     if (X == 3) {
                         mma_bf16_ts(t_acc, t_act + static_cast<uint32_t>(kk * 8),
-                                    sw128_desc(ob + kOutImg), id_o, 1u);
-                        mma_bf16_ts(t_acc, t_lo + static_cast<uint32_t>(kk * 8), sw128_desc(ob),
-                                    id_o, 1u);
+                                    desc_adv(d_o, oo + kOutImg), id_o, 1u);
+                        mma_bf16_ts(t_acc, t_lo + static_cast<uint32_t>(kk * 8), dob, id_o, 1u);
                     }
                 }
                 mma_commit(&accb[wg]);
