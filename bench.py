@@ -56,8 +56,8 @@ Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
 # ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, tile_w, tile_h)
 NCU_TRAFFIC = {
-    ("render_kernel", 20000, 256, 90, 360, "32x8p2b1"): 263.165184e6 + 28.148992e6,
-    ("mlp_tc_kernel", 20000, 256, 90, 360, "32x8p2b1"): 2.130432e6 + 104.015360e6,
+    ("render_kernel", 20000, 256, 90, 360, "32x16p4b1"): 227.556864e6 + 26.882048e6,
+    ("mlp_tc_kernel", 20000, 256, 90, 360, "32x16p4b1"): 2.129664e6 + 103.977984e6,
 }
 RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
 BIN_BYTES_PER_REC = 32   # each record read once
