@@ -54,7 +54,8 @@ WORKLOADS = {
 }
 Q_CUT = 9.0
 MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output layers
-# ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, tile_w, tile_h)
+# ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, rasteriser configuration);
+# captured on the flat one-channel grid only
 NCU_TRAFFIC = {
     ("render_kernel", 20000, 256, 90, 360, "32x16p4b1"): 227.556864e6 + 26.882048e6,
     ("mlp_tc_kernel", 20000, 256, 90, 360, "32x16p4b1"): 2.129664e6 + 103.977984e6,
@@ -1088,7 +1089,10 @@ def main():
     tune_ms = None
     from paper_2506_12787_b300 import autotune
     if args.tile == "auto":
-        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
+        # two channels: the complex rasteriser takes the default knobs only
+        cand = None if args.channels == 1 else [c for c in autotune.space() if c[2:] == (2, 1)]
+        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap,
+                                                  candidates=cand)
         args.tile = autotune.config_name(tw, th, px, bf)
     else:
         tw, th, px, bf = launch_cfg(args, None)
@@ -1223,7 +1227,8 @@ def main():
     # one ncu capture of this kernel on this exact workload and tile shape
     # (profiles/render_batched.txt, profiles/mlp_tc_batched.txt); null for any
     # other configuration
-    tkey = (roof["kernel"], N, Q, H, W, autotune.config_name(tw, th, px, bf))
+    tkey = (roof["kernel"], N, Q, H, W, autotune.config_name(tw, th, px, bf)) \
+        if not args.wrap and args.channels == 1 else None
     roof["traffic"] = NCU_TRAFFIC.get(tkey)
     if roof["traffic"] is not None:
         roof["traffic_unit"] = "bytes per launch (ncu)"

@@ -11,8 +11,9 @@
  *   - Pointers named *device* are CUDA device pointers; they are owned by the
  *     caller and must stay valid until the work queued on `stream` finishes.
  *     Scratch space is passed in as `ws` (size from the matching
- *     *_workspace_size call), 256-byte aligned; the forward calls allocate
- *     no device memory (see wrf_deform_backward for its cuBLAS handle).
+ *     *_workspace_size call), 256-byte aligned; no call on the path
+ *     allocates device memory (only the wrf_measure_alu_peaks diagnostic
+ *     does, a 4-byte sink).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *     only enqueues work and returns; nothing synchronises the host.
  *   - Argument errors are detected on the host and returned before any work
@@ -465,11 +466,14 @@ wrf_status wrf_project_backward(const wrf_scene *scene, const float *resid, int3
  * unless stop_grad_mean is non-zero, adds the derivative through
  * gamma(mean) into d_mean [N][2] (the paper freezes position gradients in
  * its fine stage; the flag reproduces that).  The dense products over rows
- * run as cuBLAS GEMMs (FP32 emulated on the tensor cores); their workspace
- * is part of ws, but the first call on a device creates one cuBLAS handle,
- * for which cuBLAS allocates its own small device state: make that first
- * call outside any stream capture.  The weight gradients are accumulated
- * with FP32 atomics and reductions whose order is not fixed.
+ * (the delta chain D_{l-1} = (D_l W_l) * [H_l > 0] and the weight gradients
+ * D_l^T H_l) run on the tcgen05 tensor cores with every FP32 operand split
+ * into BF16 hi + lo and three products hi*hi + hi*lo + lo*hi (relative error
+ * ~2^-17 of |a||b|), FP32 accumulation; the output layer (5 units) runs on
+ * the CUDA cores in FP32.  The weight and bias gradients are reduced in a
+ * fixed order (bit-reproducible); d_mean is accumulated with FP32 atomics
+ * over queries (order not fixed).  A bounded device-side wait that runs out
+ * records WRF_ETIMEOUT and leaves the outputs undefined.
  *   acts  the hidden activations saved by wrf_deform_acts for the same
  *         scene, MLP and tx, or NULL: then the forward is recomputed.      */
 size_t wrf_deform_backward_workspace_size(int32_t n, int32_t Q, const wrf_mlp *mlp);
