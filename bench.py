@@ -886,7 +886,7 @@ def run_paper(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = paper_inputs(rank)
     N, H, W, Q = shape
-    tw, th, px, bf = launch_cfg(args, (32, 8, 2, 1))
+    tw, th, px, bf = launch_cfg(args, (32, 16, 4, 1))
     grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
     prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[args.precision]
     ds = api.DevicePaperScene.from_host(sc, dev)
@@ -1089,10 +1089,7 @@ def main():
     tune_ms = None
     from paper_2506_12787_b300 import autotune
     if args.tile == "auto":
-        # two channels: the complex rasteriser takes the default knobs only
-        cand = None if args.channels == 1 else [c for c in autotune.space() if c[2:] == (2, 1)]
-        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap,
-                                                  candidates=cand)
+        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
         args.tile = autotune.config_name(tw, th, px, bf)
     else:
         tw, th, px, bf = launch_cfg(args, None)

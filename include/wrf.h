@@ -111,8 +111,8 @@ typedef struct {
  *   batch_factor   Gaussian records each thread stages per shared-memory
  *                  batch: 1 (default) or 2 (a batch then holds 2 x threads
  *                  records).
- * 0 selects the default.  wrf_render_complex supports the defaults only
- * (else WRF_EUNSUPPORTED). */
+ * 0 selects the default.  Both renderers (wrf_render, wrf_render_complex)
+ * take every combination. */
 typedef struct {
     int32_t H, W;
     int32_t tile_w, tile_h;

@@ -9,8 +9,8 @@ The rasteriser has three independent knobs:
   * records per thread per shared-memory batch (1 or 2), so a staged batch
     holds (tile pixels / pixels per thread) x that many Gaussians: 32 to 512
     depending on the other two knobs.
-For a workload (scene size N, grid H x W, queries per launch Q, MLP
-precision, cutoff, wrap) every combination in the search space is tried: a
+For a workload (scene size N and channels, grid H x W, queries per launch
+Q, MLP precision, cutoff, wrap) every combination in the search space is tried: a
 BatchedForward is built, its key capacity reserved, the step captured as a
 CUDA graph and replayed a few times; the combination with the smallest mean
 replay time (CUDA events on the launching stream) wins.  Results persist in a
@@ -64,8 +64,8 @@ def make_grid(H, W, cfg, q_cut, wrap=False):
     return api.make_grid(H, W, tw, th, q_cut, wrap, px_per_thread=px, batch_factor=bf)
 
 
-def workload_key(n, H, W, Q, precision, q_cut, wrap=False, candidates=None):
-    key = f"n{n}_h{H}_w{W}_q{Q}_p{precision}_c{q_cut:g}" + ("_wrap" if wrap else "")
+def workload_key(n, H, W, Q, precision, q_cut, wrap=False, candidates=None, channels=1):
+    key = f"n{n}_h{H}_w{W}_q{Q}_p{precision}_c{q_cut:g}_ch{channels}" + ("_wrap" if wrap else "")
     cand = space() if candidates is None else candidates
     sig = hashlib.sha1(",".join(config_name(*c) for c in sorted(cand)).encode()).hexdigest()[:10]
     return f"{key}_s{sig}"
@@ -101,7 +101,7 @@ def tune(scene: api.DeviceScene, mlp: api.DeviceMLP, H: int, W: int, tx, q_cut=9
     tx: device tensor [Q,3] of representative TX positions."""
     Q = int(tx.shape[0])
     cand = space() if candidates is None else [tuple(c) for c in candidates]
-    key = workload_key(scene.n, H, W, Q, mlp.precision, q_cut, wrap, cand)
+    key = workload_key(scene.n, H, W, Q, mlp.precision, q_cut, wrap, cand, scene.channels)
     cache = _load(cache_path)
     if key in cache:
         e = cache[key]

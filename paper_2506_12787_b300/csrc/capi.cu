@@ -765,8 +765,6 @@ wrf_status wrf_render_complex(const float *rec, const uint32_t *gids,
     wrf_status s;
     wrf::GridView g{};
     if ((s = check_grid(grid, &g)) != WRF_OK) return s;
-    if (g.px != 2 || g.bpt != 1)
-        return fail(WRF_EUNSUPPORTED, "render_complex takes the default rasteriser knobs only");
     if (n < 0 || Q < 0) return fail(WRF_EINVAL, "negative size");
     if (Q > 65535) return fail(WRF_EUNSUPPORTED, "Q > 65535 per call");
     if (Q == 0) return WRF_OK;

@@ -83,7 +83,6 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     constexpr int BW = 4 * PX;   // warp block width: 8 or 16 columns
     constexpr int NSX = TW / BW;  // warp blocks of BW x 8 pixels: NSX across, TH/8 down
     static_assert(NW == NSX * (TH / 8), "one warp block per warp");
-    static_assert(CH == 1 || (PX == 2 && BF == 1), "two channels: two pixels, one record each");
     using L = FwdSmem<NT, TH, BF>;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
@@ -114,10 +113,14 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     // records of this query (multi-scene batches: at qbase[q])
     const float4 *qrec = rec + (qbase ? static_cast<size_t>(qbase[q]) : static_cast<size_t>(q) * n) * 2;
     const float *qim = CH == 2 ? rec_im + static_cast<size_t>(q) * n : nullptr;
-    float wim0 = 0.f, wim1 = 0.f;  // imaginary weights of this thread's record, per buffer
+    // imaginary weights of this thread's records, per landing buffer
+    float wim[2][BF];
+#pragma unroll
+    for (int k = 0; k < BF; ++k) wim[0][k] = wim[1][k] = 0.f;
 
     // batches 0 and 1 in flight; one commit group per batch, empty or not,
     // so "all but the newest group done" always means "this batch landed"
+#pragma unroll
     for (int b = 0; b < 2; ++b) {
 #pragma unroll
         for (int k = 0; k < BF; ++k) {
@@ -127,7 +130,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                 const float4 *src = qrec + 2 * static_cast<size_t>(gid);
                 cp_async16(raw + (b * B + i) * 2, src);
                 cp_async16(raw + (b * B + i) * 2 + 1, src + 1);
-                if (CH == 2) (b == 0 ? wim0 : wim1) = qim[gid];
+                if (CH == 2) wim[b][k] = qim[gid];
             }
         }
         cp_async_commit();
@@ -140,7 +143,8 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
         gnext[k] = tid + k * NT < total - 2 * B ? gids[s0 + 2 * B + tid + k * NT] : 0u;
 
     float acc0 = 0.f, acc1 = 0.f, acc0i = 0.f, acc1i = 0.f;
-    float acc2 = 0.f, acc3 = 0.f;  // PX = 4: column pxl + 8, rows pyl and pyl + 4
+    // PX = 4: column pxl + 8, rows pyl and pyl + 4
+    float acc2 = 0.f, acc3 = 0.f, acc2i = 0.f, acc3i = 0.f;
     uint16_t *mylist = lists + warp * B;
     int b = 0;
     for (; b < nb; ++b) {
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                     make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
                                 fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim1 : wim0) : 0.f);
+            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim[1][k] : wim[0][k]) : 0.f);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
@@ -199,7 +203,10 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                 const float4 *src = qrec + 2 * static_cast<size_t>(gnext[k]);
                 cp_async16(raw + (buf * B + i) * 2, src);
                 cp_async16(raw + (buf * B + i) * 2 + 1, src + 1);
-                if (CH == 2) (buf ? wim1 : wim0) = qim[gnext[k]];
+                if (CH == 2) {
+                    if (buf) wim[1][k] = qim[gnext[k]];
+                    else wim[0][k] = qim[gnext[k]];
+                }
                 if (i < total - (b + 3) * B) gnext[k] = gids[s0 + (b + 3) * B + i];
             }
         }
@@ -255,6 +262,20 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                     acc1 = fmaf(cw.z, e, acc1);
                     acc1i = fmaf(cw.w, e, acc1i);
                 }
+                if (PX == 4) {
+                    const float2 tb = fma2(make_float2(cw.x, cw.y), lxb, make_float2(ab.z, ab.w));
+                    const float2 nqb = fma2(tb, lxb, make_float2(ab.x, ab.y));
+                    if (nqb.x >= ncut) {
+                        const float e = ex2_approx(nqb.x);
+                        acc2 = fmaf(cw.z, e, acc2);
+                        acc2i = fmaf(cw.w, e, acc2i);
+                    }
+                    if (nqb.y >= ncut) {
+                        const float e = ex2_approx(nqb.y);
+                        acc3 = fmaf(cw.z, e, acc3);
+                        acc3i = fmaf(cw.w, e, acc3i);
+                    }
+                }
             }
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
@@ -273,6 +294,12 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
         stile[pyl + 4][pxl] = sqrtf(fmaf(acc1, acc1, acc1i * acc1i));
         stile_im[pyl][pxl] = atan2f(acc0i, acc0);
         stile_im[pyl + 4][pxl] = atan2f(acc1i, acc1);
+        if (PX == 4) {
+            stile[pyl][pxl + 8] = sqrtf(fmaf(acc2, acc2, acc2i * acc2i));
+            stile[pyl + 4][pxl + 8] = sqrtf(fmaf(acc3, acc3, acc3i * acc3i));
+            stile_im[pyl][pxl + 8] = atan2f(acc2i, acc2);
+            stile_im[pyl + 4][pxl + 8] = atan2f(acc3i, acc3);
+        }
     }
     __syncthreads();
     const size_t plane = static_cast<size_t>(g.H) * g.W;
@@ -375,23 +402,20 @@ cudaError_t launch_fwd_x(const float4 *rec, const uint32_t *gids, const uint32_t
 }
 
 // The rasteriser's knobs (pixels per thread, records per thread per batch):
-// every combination for one channel (PX = 4 needs tiles at least 16 wide);
-// two channels take the default (2, 1) only.
+// every combination (PX = 4 needs tiles at least 16 wide).
 template <int TW, int TH, int CH>
 cudaError_t launch_fwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        float *out, int *status, cudaStream_t st, const long long *qbase) {
     if (g.px == 2 && g.bpt == 1)
         return launch_fwd_x<TW, TH, CH, 2, 1>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
-    if constexpr (CH == 1) {
-        if (g.px == 2 && g.bpt == 2)
-            return launch_fwd_x<TW, TH, 1, 2, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
-        if constexpr (TW >= 16) {
-            if (g.px == 4 && g.bpt == 1)
-                return launch_fwd_x<TW, TH, 1, 4, 1>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
-            if (g.px == 4 && g.bpt == 2)
-                return launch_fwd_x<TW, TH, 1, 4, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
-        }
+    if (g.px == 2 && g.bpt == 2)
+        return launch_fwd_x<TW, TH, CH, 2, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+    if constexpr (TW >= 16) {
+        if (g.px == 4 && g.bpt == 1)
+            return launch_fwd_x<TW, TH, CH, 4, 1>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
+        if (g.px == 4 && g.bpt == 2)
+            return launch_fwd_x<TW, TH, CH, 4, 2>(rec, gids, offs, n_keys, cap, n, Q, g, out, status, st, qbase);
     }
     return cudaErrorInvalidValue;
 }

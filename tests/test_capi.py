@@ -66,7 +66,7 @@ def test_host_validation_rejects_bad_arguments(lib):
 
 def test_rasteriser_knob_validation(lib):
     """Pixels per thread 2 or 4 (4 needs tiles >= 16 wide), records per thread
-    1 or 2; 0 picks the default; the complex renderer takes the defaults only."""
+    1 or 2; 0 picks the default; both renderers take every combination."""
     from paper_2506_12787_b300 import _lib, autotune
     def render(g):
         return lib.wrf_render(None, None, None, None, 0, 0, 1, C.byref(g), None, None)
@@ -77,9 +77,9 @@ def test_rasteriser_knob_validation(lib):
         assert render(_lib.Grid(90, 360, 16, 16, 9.0, 0, px, bf)) == want, (px, bf)
     assert render(_lib.Grid(90, 360, 8, 8, 9.0, 0, 4, 1)) == _lib.WRF_EUNSUPPORTED
     assert b"tile_w" in lib.wrf_last_error()
-    g = _lib.Grid(90, 360, 16, 16, 9.0, 0, 4, 1)
+    g = _lib.Grid(90, 360, 16, 16, 9.0, 0, 4, 1)  # knobs pass; the NULL outputs do not
     assert lib.wrf_render_complex(None, None, None, None, 0, 0, 1, C.byref(g), None,
-                                  None) == _lib.WRF_EUNSUPPORTED
+                                  None) == _lib.WRF_EINVAL
     # the autotuner's search space is exactly the supported combinations
     sp = autotune.space()
     assert len(sp) == 5 * 4 - 2 and len(set(sp)) == len(sp)
