@@ -16,6 +16,11 @@
  *     does, a 4-byte sink).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
  *     only enqueues work and returns; nothing synchronises the host.
+ *   - Host buffers: every array argument is a device pointer.  A caller with
+ *     TX positions and spectra in host memory copies them around the calls
+ *     with cudaMemcpyAsync on the same stream (pinned host memory keeps the
+ *     copies asynchronous); the Python package's batched.HostPipeline is that
+ *     end-to-end path, overlapping one step's copies with the next step.
  *   - Argument errors are detected on the host and returned before any work
  *     is queued (WRF_EINVAL / WRF_EUNSUPPORTED).  A failed launch returns
  *     WRF_ECUDA.  Conditions only the device can see (key-capacity overflow,
