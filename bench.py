@@ -421,9 +421,11 @@ def run_serving(args, dev):
     streams); then a sweep of arrival rates (shorter windows) for the
     cross-scene server and the plain path.  Latency = arrival -> spectrum in
     pinned host memory."""
-    from paper_2506_12787_b300 import api, serving
+    from paper_2506_12787_b300 import api, autotune, serving
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
-    grid = api.make_grid(90, 360, 16, 16, Q_CUT)
+    # the rasteriser configuration of the batched run (autotuned or given)
+    cfg = autotune.parse_config(args.tile) if args.tile != "auto" else (32, 16, 4, 1)
+    grid = autotune.make_grid(90, 360, cfg, Q_CUT)
     scenes = [serving.ResidentScene(i, synth.make_scene(n, 90, 360, seed=200 + i),
                                     synth.make_mlp(seed=300 + i), grid, dev)
               for i, n in enumerate(sizes)]
@@ -450,7 +452,7 @@ def run_serving(args, dev):
     txs = synth.make_tx(len(arr), seed=9)
     out["config"] = (f"Poisson {args.rate:.0f} q/s over 8 resident scenes {list(sizes)} (each "
                      f"its own BF16 network), {dur:.0f} s measured after {warm:.0f} s warm-up, "
-                     "360x90")
+                     f"360x90, rasteriser {autotune.config_name(*cfg)}")
     cb, _ = serving.run_stream(mixed, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
                                warmup_s=warm)
     cb["overflow_reruns"] = mixed.overflows
@@ -504,7 +506,7 @@ def run_mixed(args):
     dev = torch.device("cuda", local)
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
     H, W, Q = 90, 360, 256
-    tw, th, px, bf = launch_cfg(args, (32, 8, 2, 1))
+    tw, th, px, bf = launch_cfg(args, (32, 16, 4, 1))
     grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
     hosts = [synth.make_scene(n, H, W, seed=200 + i) for i, n in enumerate(sizes)]
     mlps = [synth.make_mlp(seed=300 + i) for i in range(len(sizes))]
@@ -552,7 +554,7 @@ def run_mixed(args):
                                    f"{list(sizes)} (each its own BF16 network; mean "
                                    f"{n_mean:.0f} Gaussians per query), 360x90, one multi-scene "
                                    "launch sequence per step (CUDA graph)",
-                       "queries_per_step": Q, "tile": f"{tw}x{th}",
+                       "queries_per_step": Q, "tile": args.tile,
                        "queries_per_scene": np.bincount(scene_of, minlength=len(sizes)).tolist(),
                        "keys_per_step": n_keys,
                        "l2": "256 MB buffer rewritten between timed steps"},
@@ -690,7 +692,7 @@ def run_train(args):
             "config": {"workload": f"train: {N} Gaussians, {Q} TX per step, {W}x{H}, fine stage "
                                    "of Sec. 4.4: anneal noise, forward (FP32 MLP), Eq. 16 loss "
                                    "(L1 + SSIM), backward, Adam", "gaussians": N,
-                       "queries_per_step": Q, "tile": f"{tw}x{th}",
+                       "queries_per_step": Q, "tile": args.tile,
                        "l2": "256 MB buffer rewritten between timed steps",
                        "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
