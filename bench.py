@@ -136,7 +136,8 @@ def make_inputs(workload, rank, channels=1):
 
 def launch_cfg(args, default):
     """The rasteriser configuration (tile_w, tile_h, px_per_thread,
-    batch_factor): --tile WxH or WxHpPXbBF, else the workload's default."""
+    batch_factor, tma_staging): --tile WxH or WxHpPXbBF[t], else the
+    workload's default."""
     from paper_2506_12787_b300 import autotune
     cfg = default if args.tile == "auto" else autotune.parse_config(args.tile)
     args.tile = autotune.config_name(*cfg)
@@ -424,7 +425,7 @@ def run_serving(args, dev):
     from paper_2506_12787_b300 import api, autotune, serving
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
     # the rasteriser configuration of the batched run (autotuned or given)
-    cfg = autotune.parse_config(args.tile) if args.tile != "auto" else (32, 16, 4, 1)
+    cfg = autotune.parse_config(args.tile) if args.tile != "auto" else (32, 16, 4, 1, 0)
     grid = autotune.make_grid(90, 360, cfg, Q_CUT)
     scenes = [serving.ResidentScene(i, synth.make_scene(n, 90, 360, seed=200 + i),
                                     synth.make_mlp(seed=300 + i), grid, dev)
@@ -496,7 +497,7 @@ def run_mixed(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2506_12787_b300 import api
+    from paper_2506_12787_b300 import api, autotune
     from paper_2506_12787_b300.batched import MultiSceneForward
 
     ws, rank, local = dist_env()
@@ -506,8 +507,7 @@ def run_mixed(args):
     dev = torch.device("cuda", local)
     sizes = synth.CONFIGS["serving_8scenes"]["scene_sizes"]
     H, W, Q = 90, 360, 256
-    tw, th, px, bf = launch_cfg(args, (32, 16, 4, 1))
-    grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
+    grid = autotune.make_grid(H, W, launch_cfg(args, (32, 16, 4, 1, 0)), Q_CUT)
     hosts = [synth.make_scene(n, H, W, seed=200 + i) for i, n in enumerate(sizes)]
     mlps = [synth.make_mlp(seed=300 + i) for i in range(len(sizes))]
     ds = [api.DeviceScene.from_host(h, dev) for h in hosts]
@@ -583,7 +583,7 @@ def run_train(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2506_12787_b300 import api
+    from paper_2506_12787_b300 import api, autotune
     from paper_2506_12787_b300.autograd import SpectrumConfig
     from paper_2506_12787_b300.train import Trainer, TrainConfig
 
@@ -594,8 +594,7 @@ def run_train(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = make_inputs("train", rank)
     N, H, W, Q = shape
-    tw, th, px, bf = launch_cfg(args, (16, 16, 2, 1))
-    cfg = SpectrumConfig(api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf))
+    cfg = SpectrumConfig(autotune.make_grid(H, W, launch_cfg(args, (16, 16, 2, 1, 0)), Q_CUT))
     tx = torch.as_tensor(tx_np, device=dev)
     tgt_scene = synth.jitter_means(sc, 2.0, seed=4)
     ds_t = api.DeviceScene.from_host(tgt_scene, dev)
@@ -879,7 +878,7 @@ def run_paper(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2506_12787_b300 import _lib, api
+    from paper_2506_12787_b300 import _lib, api, autotune
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -888,8 +887,7 @@ def run_paper(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = paper_inputs(rank)
     N, H, W, Q = shape
-    tw, th, px, bf = launch_cfg(args, (32, 16, 4, 1))
-    grid = api.make_grid(H, W, tw, th, Q_CUT, px_per_thread=px, batch_factor=bf)
+    grid = autotune.make_grid(H, W, launch_cfg(args, (32, 16, 4, 1, 0)), Q_CUT)
     prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[args.precision]
     ds = api.DevicePaperScene.from_host(sc, dev)
     dm = api.DevicePaperMLP.from_host(m, dev, precision=prec)
@@ -1091,11 +1089,11 @@ def main():
     tune_ms = None
     from paper_2506_12787_b300 import autotune
     if args.tile == "auto":
-        (tw, th, px, bf), tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
-        args.tile = autotune.config_name(tw, th, px, bf)
+        rcfg, tune_ms = autotune.tune(ds, dm, H, W, tx, Q_CUT, wrap=args.wrap)
+        args.tile = autotune.config_name(*rcfg)
     else:
-        tw, th, px, bf = launch_cfg(args, None)
-    grid = autotune.make_grid(H, W, (tw, th, px, bf), Q_CUT, wrap=args.wrap)
+        rcfg = launch_cfg(args, None)
+    grid = autotune.make_grid(H, W, rcfg, Q_CUT, wrap=args.wrap)
     stream = torch.cuda.Stream(device=dev)
     fw = BatchedForward(ds, dm, grid, Q, dev)
     with torch.cuda.stream(stream):
@@ -1226,7 +1224,7 @@ def main():
     # one ncu capture of this kernel on this exact workload and tile shape
     # (profiles/render_batched.txt, profiles/mlp_tc_batched.txt); null for any
     # other configuration
-    tkey = (roof["kernel"], N, Q, H, W, autotune.config_name(tw, th, px, bf)) \
+    tkey = (roof["kernel"], N, Q, H, W, autotune.config_name(*rcfg)) \
         if not args.wrap and args.channels == 1 else None
     roof["traffic"] = NCU_TRAFFIC.get(tkey)
     if roof["traffic"] is not None:

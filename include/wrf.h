@@ -115,7 +115,12 @@ typedef struct {
  *                  tile_w >= 16);
  *   batch_factor   Gaussian records each thread stages per shared-memory
  *                  batch: 1 (default) or 2 (a batch then holds 2 x threads
- *                  records).
+ *                  records);
+ *   tma_staging    how the records reach shared memory: 0 (default) each
+ *                  thread copies the records it sets up with cp.async; 1 TMA
+ *                  gathers (cp.async.bulk.tensor tile::gather4, four records
+ *                  per copy, completion on an mbarrier).  The same bytes land
+ *                  in the same slots either way.
  * 0 selects the default.  Both renderers (wrf_render, wrf_render_complex)
  * take every combination. */
 typedef struct {
@@ -125,6 +130,7 @@ typedef struct {
     int32_t wrap_x;
     int32_t px_per_thread;
     int32_t batch_factor;
+    int32_t tma_staging;
 } wrf_grid;
 
 /* Projected record of one deformed Gaussian for one query: 8 floats, 32-byte

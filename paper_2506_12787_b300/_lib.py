@@ -74,7 +74,8 @@ class AdamGroup(C.Structure):
 class Grid(C.Structure):
     _fields_ = [("H", C.c_int32), ("W", C.c_int32), ("tile_w", C.c_int32),
                 ("tile_h", C.c_int32), ("q_cut", C.c_float), ("wrap_x", C.c_int32),
-                ("px_per_thread", C.c_int32), ("batch_factor", C.c_int32)]
+                ("px_per_thread", C.c_int32), ("batch_factor", C.c_int32),
+                ("tma_staging", C.c_int32)]
 
 
 _lib = None

@@ -123,12 +123,12 @@ class DeviceMLP:
 
 
 def make_grid(H=90, W=360, tile_w=16, tile_h=16, q_cut=9.0, wrap=False, px_per_thread=0,
-              batch_factor=0) -> _lib.Grid:
+              batch_factor=0, tma_staging=0) -> _lib.Grid:
     """Spectrum grid; wrap=True makes the azimuth axis periodic (0 = 360 degrees).
-    px_per_thread (2 or 4) and batch_factor (1 or 2) are the rasteriser's layout
-    knobs (0 = default 2 and 1)."""
+    px_per_thread (2 or 4), batch_factor (1 or 2) and tma_staging (0: per-thread
+    cp.async, 1: TMA gathers) are the rasteriser's launch knobs (0 = defaults)."""
     return _lib.Grid(H, W, tile_w, tile_h, float(q_cut), int(bool(wrap)), int(px_per_thread),
-                     int(batch_factor))
+                     int(batch_factor), int(tma_staging))
 
 
 def tiles_of(grid) -> int:

@@ -8,7 +8,9 @@ The rasteriser has three independent knobs:
     the threads per tile;
   * records per thread per shared-memory batch (1 or 2), so a staged batch
     holds (tile pixels / pixels per thread) x that many Gaussians: 32 to 512
-    depending on the other two knobs.
+    depending on the other two knobs;
+  * how the records are staged: per-thread cp.async, or TMA gathers of four
+    records per copy.
 For a workload (scene size N and channels, grid H x W, queries per launch
 Q, MLP precision, cutoff, wrap) every combination in the search space is tried: a
 BatchedForward is built, its key capacity reserved, the step captured as a
@@ -32,36 +34,39 @@ from .batched import BatchedForward
 TILE_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 8), (32, 16))
 PX_PER_THREAD = (2, 4)
 BATCH_FACTORS = (1, 2)
+STAGINGS = (0, 1)  # 0: per-thread cp.async, 1: TMA gathers
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "autotune_cache.json")
 
 
-def space(shapes=TILE_SHAPES, pxs=PX_PER_THREAD, bfs=BATCH_FACTORS):
-    """Every supported (tile_w, tile_h, px_per_thread, batch_factor)."""
-    return [(tw, th, px, bf) for tw, th in shapes for px in pxs for bf in bfs
-            if not (px == 4 and tw < 16)]
+def space(shapes=TILE_SHAPES, pxs=PX_PER_THREAD, bfs=BATCH_FACTORS, stagings=STAGINGS):
+    """Every supported (tile_w, tile_h, px_per_thread, batch_factor, tma)."""
+    return [(tw, th, px, bf, tma) for tw, th in shapes for px in pxs for bf in bfs
+            for tma in stagings if not (px == 4 and tw < 16)]
 
 
-def batch_records(tw, th, px, bf):
+def batch_records(tw, th, px, bf, tma=0):
     """Gaussians one staged shared-memory batch holds."""
     return tw * th // px * bf
 
 
-def config_name(tw, th, px=2, bf=1):
-    return f"{tw}x{th}p{px}b{bf}"
+def config_name(tw, th, px=2, bf=1, tma=0):
+    return f"{tw}x{th}p{px}b{bf}" + ("t" if tma else "")
 
 
 def parse_config(s: str):
-    """'32x8' (default knobs) or '32x8p4b2' -> (tile_w, tile_h, px, bf)."""
-    m = re.fullmatch(r"(\d+)x(\d+)(?:p(\d))?(?:b(\d))?", s.strip())
+    """'32x8' (default knobs), '32x8p4b2' or '32x8p4b2t' (TMA staging) ->
+    (tile_w, tile_h, px, bf, tma)."""
+    m = re.fullmatch(r"(\d+)x(\d+)(?:p(\d))?(?:b(\d))?(t?)", s.strip())
     if not m:
-        raise ValueError(f"bad launch configuration {s!r}: want WxH or WxHpPXbBF")
+        raise ValueError(f"bad launch configuration {s!r}: want WxH or WxHpPXbBF[t]")
     tw, th = int(m.group(1)), int(m.group(2))
-    return tw, th, int(m.group(3) or 2), int(m.group(4) or 1)
+    return tw, th, int(m.group(3) or 2), int(m.group(4) or 1), 1 if m.group(5) else 0
 
 
 def make_grid(H, W, cfg, q_cut, wrap=False):
-    tw, th, px, bf = cfg
-    return api.make_grid(H, W, tw, th, q_cut, wrap, px_per_thread=px, batch_factor=bf)
+    tw, th, px, bf, tma = (tuple(cfg) + (0,))[:5]
+    return api.make_grid(H, W, tw, th, q_cut, wrap, px_per_thread=px, batch_factor=bf,
+                         tma_staging=tma)
 
 
 def workload_key(n, H, W, Q, precision, q_cut, wrap=False, candidates=None, channels=1):
@@ -96,7 +101,7 @@ def _load(path):
 
 def tune(scene: api.DeviceScene, mlp: api.DeviceMLP, H: int, W: int, tx, q_cut=9.0, reps=5,
          cache_path: str | None = DEFAULT_CACHE, candidates=None, verbose=False, wrap=False):
-    """Best (tile_w, tile_h, px_per_thread, batch_factor) for this workload and
+    """Best (tile_w, tile_h, px_per_thread, batch_factor, tma) for this workload and
     the timings of every candidate (ms per step, keyed by config_name).
     tx: device tensor [Q,3] of representative TX positions."""
     Q = int(tx.shape[0])

@@ -150,6 +150,9 @@ wrf_status check_grid(const wrf_grid *g, wrf::GridView *v) {
     if (v->bpt != 1 && v->bpt != 2) return fail(WRF_EUNSUPPORTED, "batch_factor must be 1 or 2");
     if (v->px == 4 && g->tile_w < 16)
         return fail(WRF_EUNSUPPORTED, "px_per_thread 4 needs tile_w >= 16");
+    if (g->tma_staging != 0 && g->tma_staging != 1)
+        return fail(WRF_EINVAL, "tma_staging must be 0 or 1");
+    v->tma = g->tma_staging;
     return WRF_OK;
 }
 

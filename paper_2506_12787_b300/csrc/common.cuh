@@ -23,6 +23,7 @@ struct GridView {
     int wrap;  // azimuth wrap: columns 0 and W are the same direction
     int px;    // rasteriser: pixels per thread (2 or 4)
     int bpt;   // rasteriser: Gaussian records per thread in a staged batch (1 or 2)
+    int tma;   // rasteriser: records staged by TMA gathers (1) or per-thread cp.async (0)
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {

@@ -32,6 +32,11 @@
 // its bounding box inside the tile, recomputes exp(-q/2) and accumulates
 // dL/d(mx, my, A, B, C, w), then adds them to the per-(query, Gaussian)
 // gradient with atomics (a Gaussian spans several tiles).
+#include <cuda.h>
+
+#include <cstring>
+#include <mutex>
+
 #include "kernels.h"
 
 namespace wrf {
@@ -53,6 +58,19 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+// TMA gather of four 32-byte records (rows r0..r3 of the record tensor map,
+// 8 FP32 columns from column 0) into 128 contiguous bytes of shared memory,
+// completion counted in bytes on `bar`.  dst 128-byte aligned.
+__device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, int r0, int r1,
+                                            int r2, int r3, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Shared-memory carve-up of the forward kernel for a tile with NT threads
 // and TH rows: a batch holds B = BF x NT records, BF per thread.
 template <int NT, int TH, int BF>
@@ -63,7 +81,8 @@ struct FwdSmem {
     static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float4 (c3, c3, w, 0)
     static constexpr size_t mask = gc + B * 16;                // [B] u32, warp blocks touched
     static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
-    static constexpr size_t bytes = lists + NW * B * 2;
+    static constexpr size_t wim = lists + NW * B * 2;          // [2][B] f32, imaginary weights
+    static constexpr size_t bytes = wim + 2 * B * 4;
 };
 
 // CH = 1: one channel, out [Q][H][W].  CH = 2: real and imaginary channels
@@ -73,13 +92,21 @@ struct FwdSmem {
 // columns x + 8: a 16 x 8 warp block; one row-pair entry serves both
 // columns).  BF: records per thread in a staged batch (the batch holds
 // BF x threads Gaussians).
-template <int TW, int TH, int CH, bool WRAP, int PX, int BF>
+// TMA: record staging by TMA gathers (one cp.async.bulk.tensor tile::gather4
+// of four records per issuing thread, completion counted in bytes on one
+// mbarrier per landing buffer, bounded waits) or, with TMA = false, by
+// per-thread cp.async (each thread copies the records it sets up itself,
+// completion by cp.async.wait_group).  Both stage the same bytes in the same
+// slots; the rest of the kernel is shared.
+template <int TW, int TH, int CH, bool WRAP, int PX, int BF, bool TMA>
 __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im,
-    const long long *__restrict__ qbase) {
+    const long long *__restrict__ qbase, const __grid_constant__ CUtensorMap rmap) {
     constexpr int NT = TW * TH / PX, B = NT * BF, NW = NT / 32;
+    constexpr int NG = B / 4;  // four-record gathers per full batch
+    static_assert(NG <= NT, "one gather per thread at most");
     constexpr int BW = 4 * PX;   // warp block width: 8 or 16 columns
     constexpr int NSX = TW / BW;  // warp blocks of BW x 8 pixels: NSX across, TH/8 down
     static_assert(NW == NSX * (TH / 8), "one warp block per warp");
@@ -90,6 +117,9 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     float4 *gcoef = reinterpret_cast<float4 *>(smem + L::gc);
     uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
+    float *wim_s = reinterpret_cast<float *>(smem + L::wim);  // two channels: [2][B]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int abort_flag;
     __shared__ __align__(16) float stile[TH][TW];
     __shared__ __align__(16) float stile_im[CH == 2 ? TH : 1][CH == 2 ? TW : 1];
 
@@ -110,37 +140,92 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     if (*n_keys > cap) s0 = s1 = 0;
     const int total = static_cast<int>(s1 - s0);
     const int nb = (total + B - 1) / B;
-    // records of this query (multi-scene batches: at qbase[q])
-    const float4 *qrec = rec + (qbase ? static_cast<size_t>(qbase[q]) : static_cast<size_t>(q) * n) * 2;
+    // records of this query (multi-scene batches: at qbase[q]): rows from rb
+    const long long rb = qbase ? qbase[q] : static_cast<long long>(q) * n;
+    const float4 *qrec = rec + static_cast<size_t>(rb) * 2;
     const float *qim = CH == 2 ? rec_im + static_cast<size_t>(q) * n : nullptr;
-    // imaginary weights of this thread's records, per landing buffer
-    float wim[2][BF];
-#pragma unroll
-    for (int k = 0; k < BF; ++k) wim[0][k] = wim[1][k] = 0.f;
 
-    // batches 0 and 1 in flight; one commit group per batch, empty or not,
-    // so "all but the newest group done" always means "this batch landed"
+    // Thread g < NG gathers records 4g .. 4g+3 of a batch; gq holds their
+    // Gaussian ids, loaded one batch before the gather is issued (a group
+    // past the batch's end repeats its first id: the bytes land in unused
+    // slots).
+    uint32_t gq[4] = {0u, 0u, 0u, 0u};
+    auto load_group = [&](int bb) {
+        const int cnt = min(B, total - bb * B), i0 = 4 * tid;
+        if (tid < NG && i0 < cnt) {
+            const uint32_t *src = gids + s0 + bb * B + i0;
+            gq[0] = src[0];
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
+            for (int j = 1; j < 4; ++j) gq[j] = i0 + j < cnt ? src[j] : gq[0];
+        }
+    };
+    auto gather = [&](int bb) {
+        const int buf = bb & 1, cnt = min(B, total - bb * B);
+        if (4 * tid < cnt) {
+            tma_gather4(raw + (buf * B + 4 * tid) * 2, &rmap, static_cast<int>(rb + gq[0]),
+                        static_cast<int>(rb + gq[1]), static_cast<int>(rb + gq[2]),
+                        static_cast<int>(rb + gq[3]), &bar[buf]);
+            if (CH == 2) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (4 * tid + j < cnt) wim_s[buf * B + 4 * tid + j] = qim[gq[j]];
+            }
+        }
+    };
+    auto batch_bytes = [&](int bb) {
+        return static_cast<uint32_t>((min(B, total - bb * B) + 3) / 4) * 128u;
+    };
+    // cp.async staging: this thread's records of batch bb (their ids in
+    // gnext, loaded one batch early), one commit group per batch slot, empty
+    // or not, so "all but the newest group done" always means "this batch
+    // landed"
+    uint32_t gnext[BF];
+    auto load_own = [&](int bb) {
 #pragma unroll
         for (int k = 0; k < BF; ++k) {
             const int i = tid + k * NT;
-            if (i < total - b * B) {
-                const uint32_t gid = gids[s0 + b * B + i];
-                const float4 *src = qrec + 2 * static_cast<size_t>(gid);
-                cp_async16(raw + (b * B + i) * 2, src);
-                cp_async16(raw + (b * B + i) * 2 + 1, src + 1);
-                if (CH == 2) wim[b][k] = qim[gid];
+            gnext[k] = i < total - bb * B ? gids[s0 + bb * B + i] : 0u;
+        }
+    };
+    auto copy_own = [&](int bb) {
+        const int buf = bb & 1;
+#pragma unroll
+        for (int k = 0; k < BF; ++k) {
+            const int i = tid + k * NT;
+            if (i < total - bb * B) {
+                const float4 *src = qrec + 2 * static_cast<size_t>(gnext[k]);
+                cp_async16(raw + (buf * B + i) * 2, src);
+                cp_async16(raw + (buf * B + i) * 2 + 1, src + 1);
+                if (CH == 2) wim_s[buf * B + i] = qim[gnext[k]];
             }
         }
         cp_async_commit();
+    };
+
+    if (TMA) {
+        if (tid == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+            for (int bb = 0; bb < 2 && bb < nb; ++bb)
+                mbar_arrive_expect_tx(&bar[bb], batch_bytes(bb));
+        }
+        load_group(0);
+        __syncthreads();
+        if (nb > 0) gather(0);
+        load_group(1);
+        if (nb > 1) gather(1);
+        load_group(2);  // ids of batch 2, gathered after batch 0 is set up
+        if (CH == 2) __syncthreads();  // the imaginary weights of batches 0 and 1
+    } else {
+        load_own(0);
+        copy_own(0);
+        load_own(1);
+        copy_own(1);
+        load_own(2);
     }
-    // this thread's Gaussian ids of batch b + 2, loaded one batch early so the
-    // copies are issued without waiting on the index loads
-    uint32_t gnext[BF];
-#pragma unroll
-    for (int k = 0; k < BF; ++k)
-        gnext[k] = tid + k * NT < total - 2 * B ? gids[s0 + 2 * B + tid + k * NT] : 0u;
+    if (tid == 0) abort_flag = 0;
+    __syncthreads();
 
     float acc0 = 0.f, acc1 = 0.f, acc0i = 0.f, acc1i = 0.f;
     // PX = 4: column pxl + 8, rows pyl and pyl + 4
@@ -150,7 +235,12 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     for (; b < nb; ++b) {
         const int buf = b & 1;
         const int cnt = min(B, total - b * B);
-        cp_async_wait_pending<1>();  // this thread's records of batch b
+        if (TMA) {
+            if (!mbar_wait(&bar[buf], (b >> 1) & 1, status)) abort_flag = 1;
+            if (tid == 0 && b + 2 < nb) mbar_arrive_expect_tx(&bar[buf], batch_bytes(b + 2));
+        } else {
+            cp_async_wait_pending<1>();  // this thread's records of batch b
+        }
         // ---- per-record set-up, once per (tile, Gaussian):
         // -q'(p) for p = tile centre + (lx, ly) as a polynomial in lx, ly:
         //   dx = lx - ux, dy = ly - uy, u = centre - tile centre,
@@ -177,7 +267,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                     make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
                                 fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? (buf ? wim[1][k] : wim[0][k]) : 0.f);
+            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? wim_s[buf * B + ri] : 0.f);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
@@ -194,23 +284,16 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             mask[ri] = mk;
         }
         __syncthreads();
-        // this thread's slots of raw[buf] are consumed (it set them up
-        // itself): the copies of batch b+2 can land there now
-#pragma unroll
-        for (int k = 0; k < BF; ++k) {
-            const int i = tid + k * NT;
-            if (i < total - (b + 2) * B) {
-                const float4 *src = qrec + 2 * static_cast<size_t>(gnext[k]);
-                cp_async16(raw + (buf * B + i) * 2, src);
-                cp_async16(raw + (buf * B + i) * 2 + 1, src + 1);
-                if (CH == 2) {
-                    if (buf) wim[1][k] = qim[gnext[k]];
-                    else wim[0][k] = qim[gnext[k]];
-                }
-                if (i < total - (b + 3) * B) gnext[k] = gids[s0 + (b + 3) * B + i];
+        // raw[buf] is consumed: the copies of batch b+2 can land there now
+        if (TMA) {
+            if (b + 2 < nb) {
+                gather(b + 2);
+                load_group(b + 3);
             }
+        } else {
+            copy_own(b + 2);  // (commits an empty group past the last batch)
+            load_own(b + 3);
         }
-        cp_async_commit();
         // ---- this warp's list: records touching its block, ascending index
         // (the mask loads of all rounds are independent: unrolled, they
         // overlap)
@@ -279,8 +362,15 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             }
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
+        if (abort_flag) break;
     }
-    cp_async_wait_all();  // nothing may be in flight when the CTA exits
+    if (!TMA) cp_async_wait_all();  // nothing may be in flight when the CTA exits
+    if (abort_flag) {
+        // drain gathers still in flight (bounded waits) before the CTA exits
+        for (int bb = b; bb < nb && bb <= b + 2; ++bb)
+            mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
+        return;
+    }
     if (CH == 1) {
         stile[pyl][pxl] = acc0;
         stile[pyl + 4][pxl] = acc1;
@@ -382,22 +472,68 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     }
 }
 
+// The record tensor map: rows of 8 FP32 (32 bytes), a box of one row (the
+// gather's shape).  cuTensorMapEncodeTiled is fetched from the driver at the
+// first use (the library does not link libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &r) == cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+cudaError_t record_map(const float4 *rec, unsigned long long rows, CUtensorMap *m) {
+    std::memset(m, 0, sizeof(*m));
+    if (!rec || rows == 0) return cudaSuccess;  // no records: the map is never used
+    EncodeTiledFn f = encode_tiled();
+    if (!f) return cudaErrorSymbolNotFound;
+    const cuuint64_t dims[2] = {8, rows};
+    const cuuint64_t strides[1] = {32};
+    const cuuint32_t box[2] = {8, 1};
+    const cuuint32_t elem[2] = {1, 1};
+    const CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float4 *>(rec), dims,
+                         strides, box, elem, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int TW, int TH, int CH, int PX, int BF>
 cudaError_t launch_fwd_x(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                          const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                          float *out, int *status, cudaStream_t st, const long long *qbase) {
     const size_t smem = FwdSmem<TW * TH / PX, TH, BF>::bytes;
-    auto kern = g.wrap ? render_kernel<TW, TH, CH, true, PX, BF>
-                       : render_kernel<TW, TH, CH, false, PX, BF>;
+    auto kern = g.tma ? (g.wrap ? render_kernel<TW, TH, CH, true, PX, BF, true>
+                                : render_kernel<TW, TH, CH, false, PX, BF, true>)
+                      : (g.wrap ? render_kernel<TW, TH, CH, true, PX, BF, false>
+                                : render_kernel<TW, TH, CH, false, PX, BF, false>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
+    // record rows the gathers may address: Q x n, or (multi-scene batches,
+    // rows from the device-side query bases) up to the int32 row limit
+    const unsigned long long rows =
+        qbase ? 0x7fffffffull : static_cast<unsigned long long>(Q) * static_cast<unsigned>(n);
+    if (rows > 0x7fffffffull) return cudaErrorInvalidValue;
+    CUtensorMap rmap;  // used by the TMA staging only
+    if ((e = record_map(g.tma ? rec : nullptr, rows, &rmap)) != cudaSuccess) return e;
     dim3 grid(g.T, Q);
     // two channels: the imaginary weights follow the Q x N records
     const float *rec_im =
         CH == 2 ? reinterpret_cast<const float *>(rec + 2 * static_cast<size_t>(Q) * n) : nullptr;
     kern<<<grid, TW * TH / PX, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                           -g.q_cut * kHalfLog2e, out, status, rec_im, qbase);
+                                           -g.q_cut * kHalfLog2e, out, status, rec_im, qbase,
+                                           rmap);
     return cudaGetLastError();
 }
 

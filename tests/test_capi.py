@@ -80,15 +80,21 @@ def test_rasteriser_knob_validation(lib):
     g = _lib.Grid(90, 360, 16, 16, 9.0, 0, 4, 1)  # knobs pass; the NULL outputs do not
     assert lib.wrf_render_complex(None, None, None, None, 0, 0, 1, C.byref(g), None,
                                   None) == _lib.WRF_EINVAL
+    assert render(_lib.Grid(90, 360, 16, 16, 9.0, 0, 2, 1, 2)) == _lib.WRF_EINVAL
+    assert b"tma_staging" in lib.wrf_last_error()
     # the autotuner's search space is exactly the supported combinations
     sp = autotune.space()
-    assert len(sp) == 5 * 4 - 2 and len(set(sp)) == len(sp)
-    for tw, th, px, bf in sp:
-        assert render(_lib.Grid(90, 360, tw, th, 9.0, 0, px, bf)) == _lib.WRF_EINVAL
+    assert len(sp) == 2 * (5 * 4 - 2) and len(set(sp)) == len(sp)
+    for tw, th, px, bf, tma in sp:
+        # every combination passes validation (the NULL outputs are caught next)
+        assert render(_lib.Grid(90, 360, tw, th, 9.0, 0, px, bf, tma)) == _lib.WRF_EINVAL
+        assert b"NULL" in lib.wrf_last_error()
     assert sorted({autotune.batch_records(*c) for c in sp}) == [32, 64, 128, 256, 512]
-    assert autotune.parse_config("32x8") == (32, 8, 2, 1)
-    assert autotune.parse_config("16x16p4b2") == (16, 16, 4, 2)
-    assert autotune.config_name(*autotune.parse_config("32x16p2b2")) == "32x16p2b2"
+    assert autotune.parse_config("32x8") == (32, 8, 2, 1, 0)
+    assert autotune.parse_config("16x16p4b2") == (16, 16, 4, 2, 0)
+    assert autotune.parse_config("16x16p4b2t") == (16, 16, 4, 2, 1)
+    for name in ("32x16p2b2", "32x16p4b1t"):
+        assert autotune.config_name(*autotune.parse_config(name)) == name
     k1 = autotune.workload_key(20000, 90, 360, 256, 1, 9.0)
     k2 = autotune.workload_key(20000, 90, 360, 256, 1, 9.0, candidates=sp[:3])
     assert k1 != k2  # the key names the search space

@@ -132,25 +132,26 @@ def test_two_channel_rssi_and_backward_limit(api):
     assert e.value.status == _lib.WRF_EUNSUPPORTED
 
 
-@pytest.mark.parametrize("cfg", [(16, 8, 4, 1), (32, 16, 4, 2), (32, 8, 2, 2), (16, 16, 4, 1)],
-                         ids=lambda c: "%dx%dp%db%d" % c)
+@pytest.mark.parametrize("cfg", [(16, 8, 4, 1, 0), (32, 16, 4, 2, 1), (32, 8, 2, 2, 0),
+                                 (16, 16, 4, 1, 1), (32, 16, 4, 1, 1)],
+                         ids=lambda c: "%dx%dp%db%d%s" % (c[:4] + ("t" if c[4] else "",)))
 def test_two_channel_launch_knobs(api, cfg):
     """Every rasteriser knob on the two-channel path: magnitude and phase
     bit-identical to the default knobs of the same tile (the same per-pixel
     arithmetic and order), and the complex value within 1e-4 x peak of the
     oracle (FP32 MLP); one case with azimuth wrap."""
-    tw, th, px, bf = cfg
+    tw, th, px, bf, tma = cfg
     H, W = 90, 360
-    wrap = cfg == (16, 16, 4, 1)
+    wrap = cfg[:4] == (16, 16, 4, 1)
     sc = complex_scene(2500, H, W, 3)
     m = synth.make_mlp(gain=0.1, seed=3)
     tx = synth.make_tx(2, seed=3)
     ds = api.DeviceScene.from_host(sc, dev())
     dm = api.DeviceMLP.from_host(m, dev(), precision=api.WRF_FP32)
     outs = []
-    for p, b in ((px, bf), (2, 1)):
+    for p, b, t in ((px, bf, tma), (2, 1, 0)):
         r = api.Renderer(api.make_grid(H, W, tw, th, 9.0, wrap=wrap, px_per_thread=p,
-                                       batch_factor=b), dev())
+                                       batch_factor=b, tma_staging=t), dev())
         outs.append(r.forward(ds, dm, T(tx)).cpu().numpy())
     assert np.array_equal(outs[0], outs[1])
     check(f"2-channel knobs {cfg} wrap={wrap}", outs[0], sc, m, tx, H, W, 1e-4, wrap=wrap)

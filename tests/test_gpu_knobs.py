@@ -1,6 +1,7 @@
 """GPU parity of the rasteriser's launch knobs (pixels per thread 2 or 4,
-records per thread per shared-memory batch 1 or 2) on every tile shape,
-and of the autotuner that searches them.
+records per thread per shared-memory batch 1 or 2, records staged by
+per-thread cp.async or by TMA gathers) on every tile shape, and of the
+autotuner that searches them.
 
 A pixel's terms are the same FP32 operations whatever the knobs (the same
 row-pair coefficients, the same column offset from the tile centre, the
@@ -90,7 +91,7 @@ def test_knobs_with_azimuth_wrap(api):
     proj = oracle.project(sc, None, 9.0, Q=2)
     A, slack = oracle.render(proj, H, W, 9.0, wrap=True)
     rec32 = oracle_proj_to_records(proj)
-    for cfg in ((32, 8, 4, 2), (16, 16, 4, 1), (32, 16, 2, 2)):
+    for cfg in ((32, 8, 4, 2, 0), (16, 16, 4, 1, 1), (32, 16, 2, 2, 1)):
         out = render(api, rec32, H, W, cfg, wrap=True)
         ok, worst, used = spectrum_error(out, A, slack, 1e-4)
         print(f"wrap {autotune.config_name(*cfg)}: err/peak {worst:.2e}")
@@ -112,7 +113,7 @@ def test_batched_forward_with_knobs(api):
     stream = torch.cuda.Stream()
     outs = {}
     for cfg in ((32, 8, 2, 1), (32, 8, 2, 2), (32, 8, 4, 1), (32, 8, 4, 2), (32, 16, 2, 1),
-                (32, 16, 4, 2)):
+                (32, 16, 4, 2), (32, 16, 4, 1, 1), (32, 8, 2, 2, 1)):
         fw = BatchedForward(ds, dm, autotune.make_grid(H, W, cfg, 9.0), Q, dev())
         with torch.cuda.stream(stream):
             fw.reserve(tx, stream)
@@ -143,7 +144,7 @@ def test_autotune_searches_and_caches(api, tmp_path):
     ds, dm = api.DeviceScene.from_host(sc, dev()), api.DeviceMLP.from_host(m, dev(),
                                                                         precision=api.WRF_BF16)
     tx = T(synth.make_tx(Q, seed=31))
-    cand = [(32, 8, 2, 1), (32, 8, 4, 2), (16, 16, 2, 2), (16, 8, 4, 1)]
+    cand = [(32, 8, 2, 1, 0), (32, 8, 4, 2, 0), (16, 16, 2, 2, 1), (16, 8, 4, 1, 1)]
     path = str(tmp_path / "cache.json")
     best, times = autotune.tune(ds, dm, H, W, tx, 9.0, reps=2, cache_path=path, candidates=cand,
                                 verbose=True)
