@@ -1,15 +1,18 @@
 // Tile rasteriser for the order-free Gaussian sum (Sec. 4.1 Eq. 8-9,
 // Sec. 4.2 Eq. 13) and its backward.
 //
-// Forward: one CTA per (tile, query), one thread per two pixels; warp w owns
-// an 8 x 8 pixel block of the tile and lane l the pixels (l % 8, l / 8) and
-// (l % 8, l / 8 + 4) of it.  The tile's Gaussian list (ascending id) is
-// streamed through shared memory in batches of one record per thread (or
-// two, a launch knob): every thread copies its own records with two 16-byte
-// cp.async each into its own slots of two landing buffers that alternate, so
-// the batch after next is in flight while the current one is evaluated, and
-// waits for its own copies only (cp.async.wait_group; the thread that copies
-// a record is the one that sets it up).  Once per
+// Forward: one CTA per (tile, query), one thread per two pixels (or four, a
+// launch knob); warp w owns an 8 x 8 pixel block of the tile and lane l the
+// pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of it (with four pixels a
+// 16 x 8 block, also the columns + 8).  The tile's Gaussian list (ascending
+// id) is streamed through shared memory in batches of one record per thread
+// (or two, a launch knob) into two landing buffers that alternate, so the
+// batch after next is in flight while the current one is evaluated, by one
+// of two staging paths (a launch knob): every thread copies its own records
+// with two 16-byte cp.async each into its own slots and waits for its own
+// copies only (cp.async.wait_group; the thread that copies a record is the
+// one that sets it up), or TMA gathers (cp.async.bulk.tensor tile::gather4,
+// four records per copy) completing on one mbarrier per buffer.  Once per
 // (tile, Gaussian) a thread turns the record into the polynomial
 //   -q'(lx, ly) = c0 + c1 lx + c2 ly + c3 lx^2 + c4 lx ly + c5 ly^2
 // in the pixel's offset (lx, ly) from the tile centre (q' = q log2(e)/2), and
