@@ -90,9 +90,11 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=10.0)
     p.add_argument("--serve-warmup", type=float, default=1.0)
     p.add_argument("--serve-sweep", type=lambda v: [float(x) for x in v.split(",") if x],
-                   default=[2000.0, 10000.0, 25000.0],
+                   default=[2000.0, 5000.0, 10000.0, 25000.0],
                    help="arrival rates of the serving sweep (q/s, comma-separated)")
     p.add_argument("--sweep-seconds", type=float, default=3.0)
+    p.add_argument("--mixed-buckets", type=lambda v: tuple(int(x) for x in v.split(",") if x),
+                   default=(8, 16, 32), help="batch sizes of the scene-mixing server's slots")
     p.add_argument("--sweep-warmup", type=float, default=0.5)
     args = p.parse_args()
     if args.precision is None:
@@ -441,7 +443,7 @@ def run_serving(args, dev):
         d["p99_ms_all"] = d["p99_ms"] if d["unserved"] <= 0.01 * max(1, d["offered"]) else None
         return d
 
-    mixed = serving.MixedServer(scenes, n_streams=8, buckets=(8, 16, 32), max_inflight=8)
+    mixed = serving.MixedServer(scenes, n_streams=8, buckets=args.mixed_buckets, max_inflight=8)
     mixed.prepare()
     per_scene = serving.Server(scenes, n_streams=8, buckets=(1, 4, 8, 16, 32), max_batch=32)
     per_scene.prepare()
@@ -457,8 +459,8 @@ def run_serving(args, dev):
     cb, _ = serving.run_stream(mixed, arr, lambda i: txs[i], window_s=warm + dur, drain_s=5.0,
                                warmup_s=warm)
     cb["overflow_reruns"] = mixed.overflows
-    cb["policy"] = ("batches across scenes (one multi-scene launch sequence each), up to 32 "
-                    "queries, at most 8 in flight on 8 streams")
+    cb["policy"] = ("batches across scenes (one multi-scene launch sequence each), up to "
+                    f"{max(args.mixed_buckets)} queries, at most 8 in flight on 8 streams")
     out["continuous"] = finish(cb)
     ps, _ = serving.run_stream(per_scene, arr, lambda i: txs[i], window_s=warm + dur,
                                drain_s=5.0, warmup_s=warm)
