@@ -32,14 +32,18 @@ def _scenes(H, W):
             [synth.make_mlp(gain=0.2, bias_std=0.02, seed=80 + i) for i in range(3)])
 
 
-@pytest.mark.parametrize("tile", [(32, 8), (16, 16)])
+@pytest.mark.parametrize("tile", [(32, 8, 2, 1, 0), (16, 16, 2, 1, 0), (32, 16, 4, 1, 1)],
+                         ids=["32x8", "16x16", "32x16p4b1-tma"])
 def test_mixed_batch_equals_each_scene_alone(api, tile):
+    """(The third case stages the records with TMA gathers, whose tensor map
+    spans the int32 row range: rows come from the device-side query bases.)"""
     from paper_2506_12787_b300.batched import BatchedForward, MultiSceneForward
     H, W = 90, 360
     scs, mls = _scenes(H, W)
     ds = [api.DeviceScene.from_host(s, dev()) for s in scs]
     dm = [api.DeviceMLP.from_host(m, dev(), precision=api.WRF_BF16) for m in mls]
-    grid = api.make_grid(H, W, tile[0], tile[1], 9.0)
+    grid = api.make_grid(H, W, tile[0], tile[1], 9.0, px_per_thread=tile[2],
+                         batch_factor=tile[3], tma_staging=tile[4])
     Q = 16
     # unsorted scenes, a repeated scene, and two unused slots
     scene_of = [2, 0, 1, 1, 2, 0, 2, 1, 0, 0, 2, 1, 1, 2]
