@@ -227,8 +227,11 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
         copy_own(1);
         load_own(2);
     }
-    if (tid == 0) abort_flag = 0;
-    __syncthreads();
+    if (TMA) {
+        // (the cp.async path has no bounded wait and so no abort)
+        if (tid == 0) abort_flag = 0;
+        __syncthreads();
+    }
 
     float acc0 = 0.f, acc1 = 0.f, acc0i = 0.f, acc1i = 0.f;
     // PX = 4: column pxl + 8, rows pyl and pyl + 4
@@ -365,10 +368,10 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             }
         }
         __syncthreads();  // coef / mask / lists are rewritten by the next batch
-        if (abort_flag) break;
+        if (TMA && abort_flag) break;
     }
     if (!TMA) cp_async_wait_all();  // nothing may be in flight when the CTA exits
-    if (abort_flag) {
+    if (TMA && abort_flag) {
         // drain gathers still in flight (bounded waits) before the CTA exits
         for (int bb = b; bb < nb && bb <= b + 2; ++bb)
             mbar_wait(&bar[bb & 1], (bb >> 1) & 1, status);
