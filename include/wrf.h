@@ -262,7 +262,9 @@ wrf_status wrf_multi_set_prepare(const wrf_scene *scenes, const wrf_mlp *mlps, i
  * in the order of its scene's Gaussians.  The offsets are computed on the
  * device, so a captured graph serves any mix of scenes.  If the batch needs
  * more than rec_capacity records, every query is emptied (no records) and
- * the status word records WRF_ENOSPC.  scenes / mlps / S: the host arrays
+ * the status word records WRF_ENOSPC.  rec_capacity < 2^31 (record rows are
+ * addressed with 32-bit coordinates; else WRF_EUNSUPPORTED).  wrf_render_multi
+ * reads only rows below query_base[Q].  scenes / mlps / S: the host arrays
  * the set was prepared from.  ws: wrf_multi_workspace_size(Q) bytes.     */
 size_t wrf_multi_workspace_size(int32_t Q);
 wrf_status wrf_deform_project_multi(const wrf_scene *scenes, const wrf_mlp *mlps, int32_t S,

@@ -657,6 +657,8 @@ wrf_status wrf_deform_project_multi(const wrf_scene *scenes, const wrf_mlp *mlps
     if ((s = check_grid(grid, &g)) != WRF_OK) return s;
     if (Q < 0 || Q > 65535) return fail(WRF_EUNSUPPORTED, "multi-scene: 0 <= Q <= 65535");
     if (rec_capacity < 0) return fail(WRF_EINVAL, "rec_capacity < 0");
+    // the rasteriser addresses record rows with 32-bit coordinates
+    if (rec_capacity > 0x7fffffffll) return fail(WRF_EUNSUPPORTED, "rec_capacity >= 2^31");
     if (!query_base) return fail(WRF_EINVAL, "query_base is NULL");
     if (Q == 0) {
         cudaError_t e = cudaMemsetAsync(query_base, 0, sizeof(int64_t),
