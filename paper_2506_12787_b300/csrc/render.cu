@@ -183,6 +183,11 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     // or not, so "all but the newest group done" always means "this batch
     // landed"
     uint32_t gnext[BF];
+    // two channels: the imaginary weights of this thread's records, per
+    // landing buffer (registers; the TMA path keeps them in shared memory)
+    float wim_r[2][BF];
+#pragma unroll
+    for (int k = 0; k < BF; ++k) wim_r[0][k] = wim_r[1][k] = 0.f;
     auto load_own = [&](int bb) {
 #pragma unroll
         for (int k = 0; k < BF; ++k) {
@@ -199,7 +204,10 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                 const float4 *src = qrec + 2 * static_cast<size_t>(gnext[k]);
                 cp_async16(raw + (buf * B + i) * 2, src);
                 cp_async16(raw + (buf * B + i) * 2 + 1, src + 1);
-                if (CH == 2) wim_s[buf * B + i] = qim[gnext[k]];
+                if (CH == 2) {
+                    if (buf) wim_r[1][k] = qim[gnext[k]];
+                    else wim_r[0][k] = qim[gnext[k]];
+                }
             }
         }
         cp_async_commit();
@@ -273,7 +281,9 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                     make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
                                 fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
             }
-            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, CH == 2 ? wim_s[buf * B + ri] : 0.f);
+            const float wi = CH == 2 ? (TMA ? wim_s[buf * B + ri] : (buf ? wim_r[1][k] : wim_r[0][k]))
+                                     : 0.f;
+            gcoef[ri] = make_float4(-r0.z, -r0.z, r1.y, wi);
             uint32_t mk = 0;
             const float xlo = ceilf(__fsub_rn(mx, r1.z)) - static_cast<float>(x0);
             const float xhi = floorf(__fadd_rn(mx, r1.z)) - static_cast<float>(x0);
@@ -321,10 +331,10 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
         const char *gcb = reinterpret_cast<const char *>(gcoef);
         const float2 lx2 = make_float2(lx, lx);
         const float2 lxb = make_float2(lx + 8.f, lx + 8.f);  // PX = 4: the second column
-        // unrolled 8 deep with four pixels per thread (1.3 % faster than 4 at
-        // 32 x 16) and at 32 x 8 tiles with two (0.5 %), 4 elsewhere (8 spills
-        // a register at 16 x 16 with two)
-        constexpr int kUnroll = (PX == 4 || (TW == 32 && TH == 8)) ? 8 : 4;
+        // unrolled 8 deep with four pixels per thread and one channel (1.3 %
+        // faster than 4 at 32 x 16) and at 32 x 8 tiles with two (0.5 %), 4
+        // elsewhere (8 spills a register at 16 x 16 with two)
+        constexpr int kUnroll = ((PX == 4 && CH == 1) || (TW == 32 && TH == 8)) ? 8 : 4;
 #pragma unroll kUnroll
         for (int j = 0; j < m; ++j) {
             const int o = mylist[j];  // = record index * 16
