@@ -74,8 +74,8 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="batched", choices=sorted(WORKLOADS))
     p.add_argument("--precision", default=None, choices=["bf16", "bf16x3", "fp32"],
-                   help="network precision (default: bf16; the paper workload: bf16x3, the "
-                        "three-product BF16 network held to the FP32 tolerance)")
+                   help="network precision (default: bf16; the paper and training workloads: "
+                        "bf16x3, the three-product BF16 network held to the FP32 tolerance)")
     p.add_argument("--tile", default="auto",
                    help="rasteriser configuration WxH or WxHpPXbBF (tile, pixels per thread, "
                         "records per thread per batch), or auto (autotuned, cached)")
@@ -99,7 +99,7 @@ def parse():
     p.add_argument("--sweep-warmup", type=float, default=0.5)
     args = p.parse_args()
     if args.precision is None:
-        args.precision = "bf16x3" if args.workload == "paper" else "bf16"
+        args.precision = "bf16x3" if args.workload in ("paper", "train") else "bf16"
     return args
 
 
@@ -151,8 +151,10 @@ def config_of(args, shape, extra=None):
     N, H, W, Q = shape
     c = {"workload": f"{args.workload}: {N} Gaussians, {W}x{H} FP32 spectrum, {Q} TX per step",
          "gaussians": N, "H": H, "W": W, "queries_per_step": Q,
-         "mlp": "89-128x4-5 ReLU, " + ("BF16 tcgen05 / FP32 acc" if args.precision == "bf16"
-                                       else "FP32 CUDA cores"),
+         "mlp": "89-128x4-5 ReLU, " + {"bf16": "BF16 tcgen05 / FP32 acc",
+                                       "bf16x3": "BF16 hi + lo operands, three tcgen05 products "
+                                                 "per multiply / FP32 acc"}.get(args.precision,
+                                                                                "FP32 CUDA cores"),
          "q_cut": Q_CUT, "tile": args.tile, "l2": "256 MB buffer rewritten between timed steps",
          "parallelism": f"replicas x{args.gpus}", "wrap": bool(args.wrap),
          "channels": args.channels,
@@ -579,7 +581,8 @@ def run_mixed(args):
 
 def run_train(args):
     """Training iteration of Sec. 4.4, fine stage: anneal-smoothed TX positions
-    (Eq. 17-18), forward (FP32 MLP), Eq. 16 loss (L1 + SSIM) against fixed
+    (Eq. 17-18), forward (FP32-level MLP: three BF16 tensor-core products per
+    FP32 product, or FP32 CUDA cores), Eq. 16 loss (L1 + SSIM) against fixed
     targets, backward through the rasteriser, projection and MLP (position
     gradients stopped), Adam update of the Gaussians (positions frozen) and
     the MLP; 20k Gaussians and 64 TX positions per step at 360x90."""
@@ -597,7 +600,12 @@ def run_train(args):
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = make_inputs("train", rank)
     N, H, W, Q = shape
-    cfg = SpectrumConfig(autotune.make_grid(H, W, launch_cfg(args, (16, 16, 2, 1, 0)), Q_CUT))
+    if args.precision == "bf16":
+        raise SystemExit("train: the forward MLP must be FP32-level (--precision bf16x3 or fp32)")
+    prec = api.WRF_BF16X3 if args.precision == "bf16x3" else api.WRF_FP32
+    mlp_txt = ("three-product BF16 tcgen05 MLP" if prec == api.WRF_BF16X3 else "FP32 MLP")
+    cfg = SpectrumConfig(autotune.make_grid(H, W, launch_cfg(args, (16, 16, 2, 1, 0)), Q_CUT),
+                         mlp_precision=prec)
     tx = torch.as_tensor(tx_np, device=dev)
     tgt_scene = synth.jitter_means(sc, 2.0, seed=4)
     ds_t = api.DeviceScene.from_host(tgt_scene, dev)
@@ -639,7 +647,7 @@ def run_train(args):
     # per-stage times of the same step (eager calls, default stream)
     ds = api.DeviceScene(*[gauss[k] for k in ("mean", "log_scale", "rot", "opacity_logit",
                                                "amp")])
-    dm = api.DeviceMLP(mlp_p[0::2], mlp_p[1::2])
+    dm = api.DeviceMLP(mlp_p[0::2], mlp_p[1::2], precision=prec)
     r = api.Renderer(cfg.grid, dev, fused=False)
     acts = torch.empty((len(mlp_p) // 2 - 1, Q * N, 128), dtype=torch.float32, device=dev)
     pred = r.forward(ds, dm, tx, acts=acts).clone()
@@ -692,8 +700,8 @@ def run_train(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * total_max / K, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"train: {N} Gaussians, {Q} TX per step, {W}x{H}, fine stage "
-                                   "of Sec. 4.4: anneal noise, forward (FP32 MLP), Eq. 16 loss "
-                                   "(L1 + SSIM), backward, Adam", "gaussians": N,
+                                   f"of Sec. 4.4: anneal noise, forward ({mlp_txt}), Eq. 16 "
+                                   "loss (L1 + SSIM), backward, Adam", "gaussians": N,
                        "queries_per_step": Q, "tile": args.tile,
                        "l2": "256 MB buffer rewritten between timed steps",
                        "final_loss_eq16": float(loss)},
@@ -1085,7 +1093,7 @@ def main():
     dev = torch.device("cuda", local)
     sc, m, tx_np, shape = make_inputs(args.workload, rank, args.channels)
     N, H, W, Q = shape
-    prec = api.WRF_BF16 if args.precision == "bf16" else api.WRF_FP32
+    prec = {"bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3, "fp32": api.WRF_FP32}[args.precision]
     ds = api.DeviceScene.from_host(sc, dev)
     dm = api.DeviceMLP.from_host(m, dev, precision=prec)
     tx = torch.as_tensor(tx_np, device=dev)
@@ -1210,13 +1218,21 @@ def main():
                 "alu_peaks": ap}
     elif dom == "deform_project":
         rows = Q * N
-        pk = peaks["bf16_tflops"] if prec == api.WRF_BF16 else alu_peaks(api, stream)["fp32_tflops"]
-        roof = {"kernel": "mlp_tc_kernel" if prec == api.WRF_BF16 else "mlp_f32_kernel",
-                "bound": "tensor" if prec == api.WRF_BF16 else "alu",
-                "achieved": rows * MLP_FLOP_PER_ROW / (stage["deform_project"] * 1e-3) / 1e12,
-                "peak": pk, "unit": "TFLOP/s",
-                "peak_source": f"bf16_tflops ({peak_src})" if prec == api.WRF_BF16 else
-                               "FP32 measured on this GPU by wrf_measure_alu_peaks"}
+        ach = rows * MLP_FLOP_PER_ROW / (stage["deform_project"] * 1e-3) / 1e12
+        if prec == api.WRF_BF16:
+            roof = {"kernel": "mlp_tc_kernel", "bound": "tensor", "achieved": ach,
+                    "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "peak_source": f"bf16_tflops ({peak_src})"}
+        elif prec == api.WRF_BF16X3:
+            # FP32-equivalent FLOPs against a third of the BF16 peak (three
+            # BF16 products per FP32 product)
+            roof = {"kernel": "mlp_x3_kernel", "bound": "tensor", "achieved": ach,
+                    "peak": peaks["bf16_tflops"] / 3.0, "unit": "TFLOP/s",
+                    "peak_source": f"bf16_tflops ({peak_src}) / 3"}
+        else:
+            roof = {"kernel": "mlp_f32_kernel", "bound": "alu", "achieved": ach,
+                    "peak": alu_peaks(api, stream)["fp32_tflops"], "unit": "TFLOP/s",
+                    "peak_source": "FP32 measured on this GPU by wrf_measure_alu_peaks"}
     else:
         nbytes = BIN_BYTES_PER_REC * Q * N + BIN_BYTES_PER_KEY * n_keys + 4 * (Q * fw.T + 1)
         roof = {"kernel": "bin (count+scan+scatter)", "bound": "hbm",

@@ -55,10 +55,10 @@ typedef enum {
     WRF_EUNSUPPORTED = -5  /* valid request outside what the kernels implement   */
 } wrf_status;
 
-/* Network precision.  WRF_BF16X3 (the paper's head only): every FP32
- * operand split into BF16 hi + lo = bf16(x) + bf16(x - bf16(x)) and every
- * product taken as hi hi + hi lo + lo hi on the tensor cores with FP32
- * accumulation (relative error ~2^-17 per product). */
+/* Network precision.  WRF_BF16X3: every FP32 operand split into BF16
+ * hi + lo = bf16(x) + bf16(x - bf16(x)) and every product taken as
+ * hi hi + hi lo + lo hi on the tensor cores with FP32 accumulation
+ * (relative error ~2^-17 per product). */
 enum { WRF_FP32 = 0, WRF_BF16 = 1, WRF_BF16X3 = 2 };
 enum { WRF_MAX_LAYERS = 8, WRF_HIDDEN = 128, WRF_OUT = 5 };
 
@@ -85,7 +85,11 @@ typedef struct {
  * Supported: dims[0] = 2(2 L_mean + 1) + 3(2 L_tx + 1), hidden widths 128,
  * 2 <= n_layers <= 8, output width 5.  precision = WRF_BF16 runs the hidden
  * layers on tcgen05 tensor cores with BF16 operands and FP32 accumulation;
- * WRF_FP32 runs everything in FP32 on the CUDA cores. */
+ * WRF_BF16X3 runs the hidden and output layers on the tensor cores with
+ * three BF16 products per FP32 product (FP32-level results; the first
+ * layer stays in FP32 on the CUDA cores); WRF_FP32 runs everything in FP32
+ * on the CUDA cores.  Both tensor-core precisions take n_layers <= 5 (the
+ * weights stay resident in shared memory). */
 typedef struct {
     int32_t n_layers;
     int32_t dims[WRF_MAX_LAYERS + 1];
@@ -93,7 +97,7 @@ typedef struct {
     const float *b[WRF_MAX_LAYERS];
     int32_t L_mean, L_tx;
     float room_min[3], room_size[3];
-    int32_t precision;           /* WRF_FP32 or WRF_BF16                      */
+    int32_t precision;           /* WRF_FP32, WRF_BF16 or WRF_BF16X3          */
 } wrf_mlp;
 
 /* Spectrum grid and tiling.  A Gaussian contributes to pixel p only where
@@ -162,8 +166,8 @@ wrf_status wrf_deform(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid
 /* As wrf_deform, and also stores every hidden activation for the backward
  * (training): acts [n_layers - 1][Q][N][128] FP32 device, row-major, layer l
  * = the output of hidden layer l + 1 after its ReLU (the first entry is the
- * first layer's output).  mlp->precision must be WRF_FP32 (else
- * WRF_EUNSUPPORTED).  Needs (n_layers - 1) x Q x N x 512 bytes.           */
+ * first layer's output).  mlp->precision must be WRF_FP32 or WRF_BF16X3
+ * (else WRF_EUNSUPPORTED).  Needs (n_layers - 1) x Q x N x 512 bytes.     */
 wrf_status wrf_deform_acts(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
                            const float *tx, int32_t Q, float *resid, float *acts, void *ws,
                            size_t ws_bytes, void *stream);

@@ -290,13 +290,14 @@ def mlp_grad(scene, mlp, tx, H: int, W: int, d_resid, stop_grad_mean: bool = Fal
 
 
 def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool = False,
-         wrap: bool = False):
+         wrap: bool = False, band: float = RELU_BAND):
     """Analytic FP64 gradient of L given dL/dA [Q,H,W].
 
     Returns a dict with d_mean [N,2], d_log_scale [N,2], d_rot [N],
     d_opacity [N], d_amp [N], d_W (list), d_b (list), d_resid [Q,N,5] and
     d_proj [Q,N,6]; with an MLP also "slack": the ambiguous-ReLU slack of
-    d_W, d_b and d_mean (see mlp_grad)."""
+    d_W, d_b and d_mean (see mlp_grad; band = the width of the ambiguous
+    zone, as a fraction of a pre-activation's magnitude)."""
     tx = np.atleast_2d(tx)
     Q = tx.shape[0]
     resid = deform(scene, mlp, tx, H, W) if mlp is not None else None
@@ -319,7 +320,8 @@ def grad(scene, mlp, tx, H: int, W: int, q_cut: float, dA, stop_grad_mean: bool 
     out = dict(d_mean=d_mean, d_log_scale=d_ls, d_rot=d_rot, d_opacity=d_op, d_amp=d_amp,
                d_resid=dresid, d_proj=dproj)
     if mlp is not None:
-        dW, db, dmean_mlp, slack = mlp_grad(scene, mlp, tx, H, W, dresid, stop_grad_mean)
+        dW, db, dmean_mlp, slack = mlp_grad(scene, mlp, tx, H, W, dresid, stop_grad_mean,
+                                            band)
         out["d_mean"] = d_mean + dmean_mlp
         out["d_mean_direct"] = d_mean
         out["d_W"], out["d_b"] = dW, db

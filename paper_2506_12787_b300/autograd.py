@@ -32,6 +32,9 @@ class SpectrumConfig:
     stop_grad_mean: bool = False  # the paper's fine stage freezes position gradients
     renderer: object = None       # reusable api.Renderer (created on first use)
     saved_activation_bytes: int = 16 << 30  # keep the MLP's activations up to this size
+    # the forward MLP: api.WRF_FP32 (CUDA cores) or api.WRF_BF16X3 (tensor
+    # cores, three BF16 products per FP32 product: FP32-level results)
+    mlp_precision: int = api.WRF_FP32
 
 
 class SpectrumFunction(torch.autograd.Function):
@@ -46,7 +49,7 @@ class SpectrumFunction(torch.autograd.Function):
             W = [p.detach().contiguous() for p in params[0::2]]
             b = [p.detach().contiguous() for p in params[1::2]]
             mlp = api.DeviceMLP(W, b, cfg.L_mean, cfg.L_tx, tuple(cfg.room_min),
-                                tuple(cfg.room_size), api.WRF_FP32)
+                                tuple(cfg.room_size), cfg.mlp_precision)
         if cfg.renderer is None:
             cfg.renderer = api.Renderer(cfg.grid, dev, fused=False)
         r = cfg.renderer

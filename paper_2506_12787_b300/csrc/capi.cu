@@ -171,10 +171,10 @@ wrf_status check_mlp(const wrf_mlp *m, wrf::MlpView *v) {
         if (!m->W[l] || !m->b[l]) return fail(WRF_EINVAL, "weight %d is NULL", l);
     for (int i = 0; i < 3; ++i)
         if (!(m->room_size[i] > 0.f)) return fail(WRF_EINVAL, "room_size must be > 0");
-    if (m->precision != WRF_FP32 && m->precision != WRF_BF16)
+    if (m->precision != WRF_FP32 && m->precision != WRF_BF16 && m->precision != WRF_BF16X3)
         return fail(WRF_EINVAL, "unknown precision");
-    if (m->precision == WRF_BF16 && m->n_layers > 5)
-        return fail(WRF_EUNSUPPORTED, "BF16 tensor-core path keeps <= 3 hidden layers resident");
+    if (m->precision != WRF_FP32 && m->n_layers > 5)
+        return fail(WRF_EUNSUPPORTED, "tensor-core path keeps <= 3 hidden layers resident");
     v->n_layers = m->n_layers;
     v->dm = dm;
     v->dt = dt;
@@ -272,8 +272,8 @@ static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, cons
     if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
     if (Q > 0 && !tx) return fail(WRF_EINVAL, "tx is NULL");
     if (mode == 0 && Q > 0 && scene->n > 0 && !resid) return fail(WRF_EINVAL, "resid is NULL");
-    if (acts && mlp->precision != WRF_FP32)
-        return fail(WRF_EUNSUPPORTED, "saved activations need the FP32 MLP");
+    if (acts && mlp->precision == WRF_BF16)
+        return fail(WRF_EUNSUPPORTED, "saved activations need the FP32 or BF16X3 MLP");
     if (acts && !aligned(acts, 16)) return fail(WRF_EINVAL, "acts must be 16-byte aligned");
     if (mode == 1 && Q > 0 && scene->n > 0 && (!rec || !aligned(rec, 16)))
         return fail(WRF_EINVAL, "rec must be non-NULL and 16-byte aligned");
@@ -286,11 +286,14 @@ static wrf_status deform_common(const wrf_scene *scene, const wrf_mlp *mlp, cons
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     wrf::SceneView sv = view(scene);
     int *status = status_ptr();
-    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, mlp->precision == WRF_BF16, st);
+    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, mlp->precision, st);
     if (e != cudaSuccess) return cuda_fail(e, "prep");
     if (mlp->precision == WRF_BF16)
         e = wrf::launch_mlp_tc(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
                                tile_count, status, st);
+    else if (mlp->precision == WRF_BF16X3)
+        e = wrf::launch_mlp_x3(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
+                               tile_count, acts, status, st);
     else
         e = wrf::launch_mlp_f32(sv, m, g, Q, w, mode, resid, reinterpret_cast<float4 *>(rec),
                                 tile_count, acts, st);
@@ -416,7 +419,7 @@ wrf_status wrf_rssi(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *
     wrf::deform_ws_layout(scene->n, Q, mlp->n_layers, &w, static_cast<char *>(ws));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     wrf::SceneView sv = view(scene);
-    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, false, st);
+    cudaError_t e = wrf::launch_prep(sv, m, g, tx, Q, w, WRF_FP32, st);
     if (e != cudaSuccess) return cuda_fail(e, "prep");
     e = wrf::launch_rssi(sv, m, g, Q, w, rssi, map, st);
     if (e != cudaSuccess) return cuda_fail(e, "rssi");
@@ -861,7 +864,7 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
     wrf::SceneView sv = view(scene);
     cudaError_t e = cudaSuccess;
     if (Q > 0 && scene->n > 0) {
-        e = wrf::launch_prep(sv, m, g, tx, Q, fw, false, st);
+        e = wrf::launch_prep(sv, m, g, tx, Q, fw, WRF_FP32, st);
         if (e != cudaSuccess) return cuda_fail(e, "prep");
     }
     e = wrf::launch_mlp_bwd(sv, m, g, tx, Q, fw, bw, d_resid, acts, dW, db, d_mean,

@@ -30,6 +30,8 @@ struct DeformWs {
     float *wo_f32;         // output layer transposed [k=128][8] (cols 5..7 zero)
     uint16_t *w_bf16;      // tcgen05 operand images: W1m, hidden layers, output,
                            // bias image, bias selectors
+    uint16_t *w_x3;        // FP32-level tcgen05 images (hi and lo of every weight):
+                           // hidden layers, output layer, bias image, selectors
 };
 
 // Biases enter the tensor-core MLP as one extra K = 16 MMA per layer.  The
@@ -42,6 +44,17 @@ struct DeformWs {
 // K = 8..15), so A_sel(p) B_bias adds hi + lo of pair p to every row.
 constexpr size_t kBiasImageBytes = 2048;
 constexpr size_t kSelImageBytes = 4 * 256;
+
+// The three-product image (precision WRF_BF16X3): per hidden layer four
+// 128 x 64 K-major 128-byte-swizzled panels (hi K 0-63, hi K 64-127, lo K
+// 0-63, lo K 64-127; hi = bf16(w), lo = bf16(w - hi)), the output layer the
+// same way as 16-row panels, then the bias image and the selectors.
+constexpr size_t kX3PanelBytes = 128 * 128;
+constexpr size_t kX3OutPanelBytes = 16 * 128;
+inline __host__ __device__ constexpr size_t mlp_x3_image_bytes(int nh) {
+    return static_cast<size_t>(nh) * 4 * kX3PanelBytes + 4 * kX3OutPanelBytes + kBiasImageBytes +
+           kSelImageBytes;
+}
 
 // K of the tensor-core layer-1 MMA: gamma(mean) width dm padded to 32 or 64.
 inline __host__ __device__ int mlp_k1(int dm) { return dm <= 32 ? 32 : 64; }
@@ -59,8 +72,10 @@ struct SceneEntry {
 };
 constexpr int kMaxScenes = 16;
 
+// images: WRF_FP32 (U, V, FP32 transposes), WRF_BF16 (BF16 gamma(mean) rows
+// instead of U, V, BF16 images) or WRF_BF16X3 (U, V, three-product images)
 cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
-                        int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st);
+                        int Q, const DeformWs &ws, int images, cudaStream_t st);
 
 // mode 0: write residuals [Q][N][5]; mode 1: project and write records.
 cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView &g, int Q,
@@ -69,6 +84,11 @@ cudaError_t launch_mlp_f32(const SceneView &s, const MlpView &m, const GridView 
 cudaError_t launch_mlp_tc(const SceneView &s, const MlpView &m, const GridView &g, int Q,
                           const DeformWs &ws, int mode, float *resid, float4 *rec,
                           uint32_t *count, int *status, cudaStream_t st);
+// FP32-level tensor-core MLP (three BF16 products per FP32 product); acts
+// (or NULL) receives the hidden activations like launch_mlp_f32.
+cudaError_t launch_mlp_x3(const SceneView &s, const MlpView &m, const GridView &g, int Q,
+                          const DeformWs &ws, int mode, float *resid, float4 *rec,
+                          uint32_t *count, float *acts, int *status, cudaStream_t st);
 
 // Multi-scene batches (multi.cu): query q of scene scene_of[q] (-1: none).
 struct MultiSet {           // a prepared scene set (caller-owned device memory)

@@ -194,7 +194,7 @@ cudaError_t launch_multi_prepare(const SceneView *s, const MlpView *m, int S, co
         w.w_bf16 = ms.img[i];
         w.wt_f32 = ms.wt_scratch;  // the FP32 images are not used here
         w.wo_f32 = ms.wo_scratch;
-        cudaError_t e = launch_prep(s[i], m[i], g, nullptr, 0, w, true, st);
+        cudaError_t e = launch_prep(s[i], m[i], g, nullptr, 0, w, WRF_BF16, st);
         if (e != cudaSuccess) return e;
         t.e[i] = SceneEntry{s[i], ms.G[i], ms.img[i], m[i].W0, m[i].b0};
     }

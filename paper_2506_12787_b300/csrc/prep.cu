@@ -8,8 +8,9 @@
 // kernels then start every row from ReLU(U[n] + V[q]).
 //
 // This file also builds the weight images the MLP kernels read: FP32
-// transposed copies for the CUDA-core path and BF16 K-major 128-byte-swizzled
-// operand images for the tcgen05 path.
+// transposed copies for the CUDA-core path, BF16 K-major 128-byte-swizzled
+// operand images for the tcgen05 path, and the hi / lo pairs of the same
+// images for the three-product (FP32-level) tcgen05 path.
 #include <cuda_bf16.h>
 
 #include "kernels.h"
@@ -118,6 +119,28 @@ __device__ __forceinline__ uint32_t sw128_offset(int n, int k, int rows) {
                                  ((kk & 7) << 1));
 }
 
+// Element e of the bias image (e < 1024) or of the four selectors (e >= 1024)
+// at `aug` (layout in kernels.h).
+__device__ __forceinline__ void aug_element(int e, const MlpView &m, int nh, char *aug) {
+    float v = 0.f;
+    if (e < 1024) {
+        const int n = e >> 3, col = e & 7, pair = col >> 1;
+        float b = 0.f;
+        if (pair < 3 && pair < nh) b = m.bh[pair][n];
+        if (pair == 3 && n < WRF_OUT) b = m.bo[n];
+        const float hi = __bfloat162float(__float2bfloat16_rn(b));
+        v = (col & 1) ? b - hi : hi;
+        *reinterpret_cast<__nv_bfloat16 *>(aug + (n >> 3) * 128 + (n & 7) * 16 + col * 2) =
+            __float2bfloat16_rn(v);
+    } else {
+        const int s2 = e - 1024, p = s2 >> 7, within = s2 & 127;  // 128 elements each
+        const int col = within & 7;                                // core 0: rows x 8
+        if (within < 64 && (col >> 1) == p) v = 1.f;
+        *reinterpret_cast<__nv_bfloat16 *>(aug + kBiasImageBytes + p * 256 + within * 2) =
+            __float2bfloat16_rn(v);
+    }
+}
+
 // One thread per (layer, row, col) of every hidden layer and the output
 // layer: FP32 transposes and BF16 swizzled images.  The BF16 image starts
 // with W1m = W0[:, :dm] as a 128 x 64 K-major image (columns >= dm zero) and
@@ -135,25 +158,7 @@ __device__ __forceinline__ void weights_block(int blk, int nblk, const MlpView &
     for (long long i = blk * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<long long>(nblk) * blockDim.x) {
         if (i >= mats) {
-            // bias image (1024 elements), then selectors (4 x 128 elements)
-            const int e = static_cast<int>(i - mats);
-            float v = 0.f;
-            if (e < 1024) {
-                const int n = e >> 3, col = e & 7, pair = col >> 1;
-                float b = 0.f;
-                if (pair < 3 && pair < nh) b = m.bh[pair][n];
-                if (pair == 3 && n < WRF_OUT) b = m.bo[n];
-                const float hi = __bfloat162float(__float2bfloat16_rn(b));
-                v = (col & 1) ? b - hi : hi;
-                *reinterpret_cast<__nv_bfloat16 *>(img + aug_off + (n >> 3) * 128 + (n & 7) * 16 +
-                                                   col * 2) = __float2bfloat16_rn(v);
-            } else {
-                const int s2 = e - 1024, p = s2 >> 7, within = s2 & 127;  // 128 elements each
-                const int col = within & 7;                                // core 0: rows x 8
-                if (within < 64 && (col >> 1) == p) v = 1.f;
-                *reinterpret_cast<__nv_bfloat16 *>(img + aug_off + kBiasImageBytes + p * 256 +
-                                                   within * 2) = __float2bfloat16_rn(v);
-            }
+            aug_element(static_cast<int>(i - mats), m, nh, img + aug_off);
             continue;
         }
         if (i < w1) {
@@ -187,6 +192,46 @@ __device__ __forceinline__ void weights_block(int blk, int nblk, const MlpView &
     }
 }
 
+// The three-product image (layout in kernels.h): one thread per weight
+// writes its hi = bf16(w) into the hi panel and lo = bf16(w - hi) into the
+// lo panel; then the bias image and the selectors.
+__device__ __forceinline__ void weights_block_x3(int blk, int nblk, const MlpView &m,
+                                                 const DeformWs &ws) {
+    const int nh = m.n_layers - 2;
+    const long long per = WRF_HIDDEN * WRF_HIDDEN;
+    const long long mats = nh * per + 16 * WRF_HIDDEN;
+    const long long total = mats + (kBiasImageBytes + kSelImageBytes) / 2;
+    char *img = reinterpret_cast<char *>(ws.w_x3);
+    const size_t out_off = static_cast<size_t>(nh) * 4 * kX3PanelBytes;
+    const size_t aug_off = out_off + 4 * kX3OutPanelBytes;
+    for (long long i = blk * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+         i += static_cast<long long>(nblk) * blockDim.x) {
+        if (i >= mats) {
+            aug_element(static_cast<int>(i - mats), m, nh, img + aug_off);
+            continue;
+        }
+        float v;
+        size_t hi_off, lo_off;
+        if (i < nh * per) {
+            const int l = static_cast<int>(i / per), r = static_cast<int>(i % per);
+            const int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // W[j][k]
+            v = m.Wh[l][r];
+            hi_off = l * 4 * kX3PanelBytes + sw128_offset(j, k, WRF_HIDDEN);
+            lo_off = hi_off + 2 * kX3PanelBytes;
+        } else {
+            const int r = static_cast<int>(i - nh * per);
+            const int j = r / WRF_HIDDEN, k = r % WRF_HIDDEN;  // output row j (< 16)
+            v = j < WRF_OUT ? m.Wo[j * WRF_HIDDEN + k] : 0.f;
+            hi_off = out_off + sw128_offset(j, k, 16);
+            lo_off = hi_off + 2 * kX3OutPanelBytes;
+        }
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        *reinterpret_cast<__nv_bfloat16 *>(img + hi_off) = hi;
+        *reinterpret_cast<__nv_bfloat16 *>(img + lo_off) =
+            __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+}
+
 // The three independent preparation jobs in one launch, so that they run
 // side by side: blocks [0, nb_mean) encode 32 Gaussians each, the next nb_tx
 // blocks 4 queries each, the rest build the weight images (grid-stride).
@@ -194,11 +239,11 @@ __device__ __forceinline__ void weights_block(int blk, int nblk, const MlpView &
 // threads of its block.
 __global__ void __launch_bounds__(128) prep_kernel(SceneView s, MlpView m, GridView g,
                                                    const float *tx, int Q, DeformWs ws,
-                                                   int want_bf16, int k1, int nb_mean,
+                                                   int images, int k1, int nb_mean,
                                                    int nb_tx) {
     int b = blockIdx.x;
     if (b < nb_mean) {
-        pe_mean_block(b, s, m, g, ws.U, want_bf16 ? ws.G : nullptr, k1);
+        pe_mean_block(b, s, m, g, ws.U, images == WRF_BF16 ? ws.G : nullptr, k1);
         return;
     }
     b -= nb_mean;
@@ -207,7 +252,11 @@ __global__ void __launch_bounds__(128) prep_kernel(SceneView s, MlpView m, GridV
         return;
     }
     b -= nb_tx;
-    weights_block(b, static_cast<int>(gridDim.x) - nb_mean - nb_tx, m, ws, want_bf16);
+    const int nblk = static_cast<int>(gridDim.x) - nb_mean - nb_tx;
+    if (images == WRF_BF16X3)
+        weights_block_x3(b, nblk, m, ws);
+    else
+        weights_block(b, nblk, m, ws, images == WRF_BF16);
 }
 
 inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
@@ -231,24 +280,28 @@ size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
     w.w_bf16 = reinterpret_cast<uint16_t *>(
         take(kW1ImageBytes + static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 2 +
              16 * WRF_HIDDEN * 2 + kBiasImageBytes + kSelImageBytes));
+    w.w_x3 = reinterpret_cast<uint16_t *>(take(mlp_x3_image_bytes(nh)));
     if (ws) *ws = w;
     return off;
 }
 
 cudaError_t launch_prep(const SceneView &s, const MlpView &m, const GridView &g, const float *tx,
-                        int Q, const DeformWs &ws, bool want_bf16, cudaStream_t st) {
+                        int Q, const DeformWs &ws, int images, cudaStream_t st) {
+    if (images != WRF_FP32 && images != WRF_BF16 && images != WRF_BF16X3)
+        return cudaErrorInvalidValue;
     const int nb_mean = s.n > 0 ? (s.n + 31) / 32 : 0;
     const int nb_tx = Q > 0 ? (Q + kTxPerBlock - 1) / kTxPerBlock : 0;
-    const long long total = (want_bf16 ? WRF_HIDDEN * 64 : 0) +
+    const bool bf16 = images == WRF_BF16, tc = images != WRF_FP32;
+    const long long total = (bf16 ? WRF_HIDDEN * 64 : 0) +
                             static_cast<long long>(m.n_layers - 2) * WRF_HIDDEN * WRF_HIDDEN +
                             16 * WRF_HIDDEN +
-                            (want_bf16 ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
+                            (tc ? (kBiasImageBytes + kSelImageBytes) / 2 : 0);
     long long nb_w = (total + 127) / 128;
     if (nb_w > 2368) nb_w = 2368;
     const long long blocks = nb_mean + nb_tx + nb_w;
     if (blocks >= (1ll << 31)) return cudaErrorInvalidValue;
     prep_kernel<<<static_cast<unsigned>(blocks), 128, 0, st>>>(
-        s, m, g, tx, Q, ws, want_bf16 ? 1 : 0, mlp_k1(m.dm), nb_mean, nb_tx);
+        s, m, g, tx, Q, ws, images, mlp_k1(m.dm), nb_mean, nb_tx);
     return cudaGetLastError();
 }
 

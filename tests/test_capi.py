@@ -64,6 +64,52 @@ def test_host_validation_rejects_bad_arguments(lib):
     assert st == _lib.WRF_EUNSUPPORTED  # hidden width 100
 
 
+def test_mlp_precision_validation(lib):
+    """Precision codes: FP32, BF16 and BF16X3 accepted; an unknown code is
+    EINVAL; the tensor-core precisions take at most three hidden 128 x 128
+    layers; saved activations need FP32 or BF16X3.  Weight pointers are
+    placeholders: validation never dereferences them."""
+    from paper_2506_12787_b300 import _lib
+
+    def mlp(n_layers, precision):
+        m = _lib.Mlp()
+        m.n_layers = n_layers
+        m.L_mean, m.L_tx = 6, 10
+        dims = [89] + [128] * (n_layers - 1) + [5]
+        for i, d in enumerate(dims):
+            m.dims[i] = d
+        for i in range(n_layers):
+            m.W[i] = m.b[i] = 4096
+        for i in range(3):
+            m.room_size[i] = 1.0
+        m.precision = precision
+        return m
+
+    g = _lib.Grid(90, 360, 16, 16, 9.0)
+    s = _lib.Scene(0, 1, None, None, None, None, None)
+    ws = C.c_void_p(1 << 20)
+    tx = C.c_void_p(4096)
+    acts = C.c_void_p(1 << 16)
+
+    def deform(m, with_acts):
+        need = lib.wrf_deform_workspace_size(0, 1, C.byref(m))
+        if with_acts:
+            return lib.wrf_deform_acts(C.byref(s), C.byref(m), C.byref(g), tx, 1, None, acts,
+                                       ws, need, None)
+        return lib.wrf_deform(C.byref(s), C.byref(m), C.byref(g), tx, 1, None, ws, need, None)
+
+    for p in (_lib.WRF_FP32, _lib.WRF_BF16, _lib.WRF_BF16X3):
+        assert deform(mlp(5, p), False) == _lib.WRF_OK  # N = 0: nothing to launch
+    assert deform(mlp(5, 3), False) == _lib.WRF_EINVAL
+    assert b"precision" in lib.wrf_last_error()
+    assert deform(mlp(6, _lib.WRF_FP32), False) == _lib.WRF_OK
+    for p in (_lib.WRF_BF16, _lib.WRF_BF16X3):
+        assert deform(mlp(6, p), False) == _lib.WRF_EUNSUPPORTED
+    assert deform(mlp(5, _lib.WRF_BF16), True) == _lib.WRF_EUNSUPPORTED
+    assert deform(mlp(5, _lib.WRF_BF16X3), True) == _lib.WRF_OK
+    assert deform(mlp(5, _lib.WRF_FP32), True) == _lib.WRF_OK
+
+
 def test_rasteriser_knob_validation(lib):
     """Pixels per thread 2 or 4 (4 needs tiles >= 16 wide), records per thread
     1 or 2; 0 picks the default; both renderers take every combination."""

@@ -56,14 +56,14 @@ def check(name, out, sc, m, tx, H, W, tol, wrap=False):
     assert ok_re and ok_im and ok_m
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 2e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-4), ("bf16", 2e-3), ("bf16x3", 1e-4)])
 @pytest.mark.parametrize("tile", [(16, 16), (32, 8)])
 def test_two_channel_forward_matches_oracle(api, precision, tol, tile):
     H, W = 90, 360
     sc = complex_scene(2000, H, W, 1)
     m = synth.make_mlp(gain=0.1, seed=1)
     tx = synth.make_tx(3, seed=1)
-    prec = api.WRF_BF16 if precision == "bf16" else api.WRF_FP32
+    prec = {"fp32": api.WRF_FP32, "bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3}[precision]
     r = api.Renderer(api.make_grid(H, W, tile[0], tile[1], 9.0), dev())
     out = r.forward(api.DeviceScene.from_host(sc, dev()),
                     api.DeviceMLP.from_host(m, dev(), precision=prec), T(tx))

@@ -245,12 +245,12 @@ def test_query_alone_equals_query_in_batch(api):
         assert torch.equal(alone[0], batch[q])
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16", "bf16x3"])
 def test_zero_queries(api, precision):
     """Q = 0 through the whole path (deform + project, bin, render): empty
     spectra, no device error; the next non-empty call is unaffected."""
     H, W = 90, 360
-    prec = api.WRF_BF16 if precision == "bf16" else api.WRF_FP32
+    prec = {"fp32": api.WRF_FP32, "bf16": api.WRF_BF16, "bf16x3": api.WRF_BF16X3}[precision]
     ds = api.DeviceScene.from_host(synth.make_scene(300, H, W, seed=4), dev())
     m = api.DeviceMLP.from_host(synth.make_mlp(seed=4), dev(), precision=prec)
     r = api.Renderer(api.make_grid(H, W, 16, 16, 9.0), dev())
