@@ -1,5 +1,6 @@
 // Internal launcher declarations shared by the kernel files and the C ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,7 +24,8 @@ struct MlpView {
 
 // Workspace carve-up for deformation (all offsets 256-byte aligned).
 struct DeformWs {
-    float *U;              // [N][128]  W0[:, :dm] gamma(mean_n)            (FP32 path)
+    float *U;              // [N][128]  W0[:, :dm] gamma(mean_n)            (FP32 path;
+                           // BF16X3: blocked [N/128][32][128][4], see prep.cu)
     uint16_t *G;           // [N][k1]   gamma(mean_n) in BF16, zero-padded  (BF16 path)
     float *V;              // [Q][128]  W0[:, dm:] gamma(tx_q) + b0
     float *wt_f32;         // hidden layers transposed [l][k=128][j=128], FP32
@@ -227,5 +229,12 @@ cudaError_t launch_mlp_bwd(const SceneView &s, const MlpView &m, const GridView 
                            float *d_mean, int stop_grad_mean, int *status, cudaStream_t st);
 
 bool render_config_supported(int tw, int th);
+
+// cuTensorMapEncodeTiled from the driver (NULL if unavailable); render.cu.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled();
 
 }  // namespace wrf

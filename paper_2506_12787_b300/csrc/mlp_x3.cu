@@ -19,15 +19,24 @@
 // layers and output layer as hi and lo panels, the bias image and the
 // selectors; <= 203 KB for three hidden layers) stay resident in shared
 // memory, copied once per CTA with bulk copies.  Per tile:
-//   1. layer 1: thread n reads U[n] (FP32), adds V[q], applies ReLU, stores
-//      the activation row (if requested) and writes its hi / lo pairs;
+//   1. layer 1: thread n reads its row of U (FP32; U is stored in
+//      128-Gaussian blocks of column quads, so the tile's 128 threads read
+//      contiguous 2 KB runs, the next 32 columns in flight while the current
+//      ones convert, the first 32 fetched during the previous tile), adds
+//      V[q], applies ReLU, stores the activations (if requested) and writes
+//      its hi / lo pairs;
 //   2. hidden layer l: bias MMA, then 8 K-steps x 3 products, committed to
 //      an mbarrier; the conversion reads the accumulator (tcgen05.ld),
-//      applies ReLU, stores the activation row (if requested) and writes
-//      the hi / lo pairs of the next layer's A operand (tcgen05.st);
+//      applies ReLU, stores the activations (if requested) and writes the
+//      hi / lo pairs of the next layer's A operand (tcgen05.st);
 //   3. output layer (N = 16, 5 used) the same way, then the residual row or
 //      the deformed and projected record (Eq. 12-13).
+// Saved activations leave through a 2 KB staging area per warp (16 columns
+// of its 32 rows) by TMA tensor stores, asynchronously: the conversion does
+// not wait for the stores, and no thread writes 32 scattered 16-byte pieces.
 // Every wait is bounded (WRF_ETIMEOUT on the status word).
+#include <cstring>
+
 #include "kernels.h"
 #include "tc.cuh"
 
@@ -43,15 +52,20 @@ constexpr uint32_t kOutPanel = static_cast<uint32_t>(kX3OutPanelBytes);  // 16 r
 constexpr uint32_t kWgCols = 256;                // TMEM columns per warpgroup
 constexpr uint32_t kTmemCols = 512;
 
+// activation staging: per warp 32 rows x 16 FP32 columns (2 KB)
+constexpr int kStageCols = 16;
+constexpr size_t kStageBytes = static_cast<size_t>(kThreads) * kStageCols * 4;
+
 constexpr size_t smem_bytes(int nh) {
-    return 1024 + mlp_x3_image_bytes(nh) + kWG * WRF_HIDDEN * 4 + (1 + kWG) * 8 + 16;
+    return 1024 + mlp_x3_image_bytes(nh) + kStageBytes + kWG * WRF_HIDDEN * 4 + (1 + kWG) * 8 +
+           16;
 }
 static_assert(smem_bytes(3) <= 227 * 1024, "shared memory of one CTA");
 
 struct X3Args {
     SceneView s;
     GridView g;
-    const float *U;          // [N][128] FP32 per-Gaussian layer-1 term
+    const float *U;          // FP32 per-Gaussian layer-1 term, blocked [N/128][32][128][4]
     const float *V;          // [Q][128] FP32 per-query layer-1 term (incl. b1)
     const uint16_t *w_img;   // X3 weight image (mlp_x3_image_bytes)
     int nh;                  // hidden 128x128 layers after the first (0..3)
@@ -61,9 +75,29 @@ struct X3Args {
     float4 *rec;
     uint32_t *count;
     float *rec_im;
-    float *acts;             // [nh + 1][Q N][128] or NULL
+    float *acts;             // [nh + 1][Q N][128] (stored through the tensor map) or NULL
     int *status;
 };
+
+// TMA tensor store of a 3-D box from shared memory (bulk group), and the
+// bulk-group waits: `read` until the sources have been read, else until the
+// writes are done.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, const void *src, int x, int y,
+                                             int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y),
+                 "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_all() {
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
 
 // hi / lo BF16 pairs of 32 consecutive FP32 values (ReLU already applied)
 __device__ __forceinline__ void split_pairs(const float *v, uint32_t *hi, uint32_t *lo) {
@@ -76,14 +110,18 @@ __device__ __forceinline__ void split_pairs(const float *v, uint32_t *hi, uint32
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a) {
+// amap: the activations as a 3-D tensor [(nh + 1) Q][N][128] FP32, box 16
+// columns x 32 rows, 64-byte swizzle (used only when a.acts is set).
+__global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a,
+                                                             const __grid_constant__ CUtensorMap amap) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned base (128-byte swizzle atoms must be 1024-aligned)
     const uint32_t raw = smem_u32(smem_raw);
     uint8_t *base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t w_bytes = static_cast<uint32_t>(mlp_x3_image_bytes(a.nh));
     uint8_t *wsm = base;
-    float *vsm0 = reinterpret_cast<float *>(base + w_bytes);                 // [kWG][128]
+    float *stage0 = reinterpret_cast<float *>(base + w_bytes);               // [warp][32][16]
+    float *vsm0 = stage0 + kThreads * kStageCols;                            // [kWG][128]
     uint64_t *bars = reinterpret_cast<uint64_t *>(vsm0 + kWG * WRF_HIDDEN);  // wbar, mbar[kWG]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 1 + kWG);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
@@ -132,17 +170,38 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a) {
     const uint64_t d_bias = plain_desc(aug_addr, 0u, 128u);
     const uint64_t d_sel = plain_desc(aug_addr + static_cast<uint32_t>(kBiasImageBytes), 128u, 0u);
     const int stride = gridDim.x * kWG;
-    const size_t rows = static_cast<size_t>(a.Q) * a.N;
 
-    // converts the accumulator (or, for layer 1, U + V) of this thread's row
-    // into the activation row `act` (if any) and the hi / lo pairs
-    auto store_act = [&](int c, const float *v, float *act) {
-        if (act) {
-            float4 *dst = reinterpret_cast<float4 *>(act) + c * 8;
+    // The activations of a warp's 32 rows: each lane writes 16 values of its
+    // own row into the warp's staging rows (16-byte chunk k of row r at chunk
+    // k ^ ((r >> 1) & 3): the map's 64-byte swizzle, and conflict-free), then
+    // lane 0 stores the 32 x 16 box at (column col0, row n0 + 32 wq, layer
+    // plane z) once the previous box has been read out.  Rows past the
+    // query's N are clipped by the map; a warp without valid rows stores
+    // nothing.
+    float *stage = stage0 + warp * 32 * kStageCols;
+    auto stage_out = [&](const float *v, int z, int n0, int col0, bool any) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        for (int h = 0; h < 2; ++h) {
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                *reinterpret_cast<float4 *>(stage + lane * kStageCols +
+                                            ((k ^ ((lane >> 1) & 3)) << 2)) =
+                    make_float4(v[16 * h + 4 * k], v[16 * h + 4 * k + 1], v[16 * h + 4 * k + 2],
+                                v[16 * h + 4 * k + 3]);
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0 && any) {
+                tma_store_3d(&amap, stage, col0 + 16 * h, n0 + wq * 32, z);
+                bulk_commit();
+            }
         }
+    };
+    // converts 32 activations (columns 32c ..) of this thread's row into the
+    // activation plane z (z < 0: none) and the hi / lo pairs
+    auto store_act = [&](int c, const float *v, int z, int n0, bool any) {
+        if (z >= 0) stage_out(v, z, n0, 32 * c, any);
         uint32_t hi[16], lo[16];
         split_pairs(v, hi, lo);
         tmem_st16(t_hi + lane_off + static_cast<uint32_t>(c * 16), hi);
@@ -168,32 +227,60 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a) {
         mma_commit(mbar);
     };
 
+    // U column quad j4 of this thread's row in 128-Gaussian block b
+    auto u_quad = [&](int b, int j4) {
+        return __ldg(reinterpret_cast<const float4 *>(a.U) +
+                     (static_cast<size_t>(b) * 32 + j4) * kTileRows + my_row);
+    };
+    // operands of the next tile, fetched while the current one finishes: its
+    // V[q] column, its Gaussian (projection epilogue) and U columns 0..31
+    float vpre = 0.f;
     GaussParams ppre{};
+    float4 u0[8];
+    auto prefetch = [&](int t) {
+        const int q = t / a.tpq, n0 = (t % a.tpq) * kTileRows;
+        vpre = __ldg(a.V + static_cast<size_t>(q) * WRF_HIDDEN + wt);
+        if (a.mode == 1 && n0 + my_row < a.N) ppre = load_params(a.s, n0 + my_row);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u0[j] = u_quad(n0 / kTileRows, j);
+    };
     int tile = blockIdx.x * kWG + wg;
+    if (tile < a.ntiles) prefetch(tile);
     for (; tile < a.ntiles; tile += stride) {
         if (wg_bar_any(1 + wg, *abort_flag != 0)) break;
         const int q = tile / a.tpq, n0 = (tile % a.tpq) * kTileRows;
         const int n = n0 + my_row;
         const bool ok = n < a.N;
+        const bool any = wq * 32 < a.N - n0;  // this warp has rows to store
         const size_t row = static_cast<size_t>(q) * a.N + (ok ? n : 0);
-        vsm[wt] = __ldg(a.V + static_cast<size_t>(q) * WRF_HIDDEN + wt);
-        if (ok && a.mode == 1) ppre = load_params(a.s, n);
+        const bool save = a.acts != nullptr;
+        const GaussParams pcur = ppre;
+        vsm[wt] = vpre;
         named_bar(1 + wg, 128);
-        // ---- layer 1: ReLU(U[n] + V[q]), exact FP32
-        const float4 *u4 = reinterpret_cast<const float4 *>(a.U + static_cast<size_t>(ok ? n : 0) * WRF_HIDDEN);
-#pragma unroll 1
-        for (int c = 0; c < 4; ++c) {
-            float v[32];
+        // ---- layer 1: ReLU(U[n] + V[q]), exact FP32; U columns 32(c+1) ..
+        // are in flight while columns 32c .. are converted
+        {
+            float4 ub[2][8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 u = ok ? __ldg(u4 + c * 8 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 b = *reinterpret_cast<const float4 *>(vsm + c * 32 + 4 * j);
-                v[4 * j] = fmaxf(__fadd_rn(u.x, b.x), 0.f);
-                v[4 * j + 1] = fmaxf(__fadd_rn(u.y, b.y), 0.f);
-                v[4 * j + 2] = fmaxf(__fadd_rn(u.z, b.z), 0.f);
-                v[4 * j + 3] = fmaxf(__fadd_rn(u.w, b.w), 0.f);
+            for (int j = 0; j < 8; ++j) ub[0][j] = u0[j];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (c < 3) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) ub[(c + 1) & 1][j] = u_quad(n0 / kTileRows, (c + 1) * 8 + j);
+                }
+                float v[32];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 u = ub[c & 1][j];
+                    const float4 b = *reinterpret_cast<const float4 *>(vsm + c * 32 + 4 * j);
+                    v[4 * j] = fmaxf(__fadd_rn(u.x, b.x), 0.f);
+                    v[4 * j + 1] = fmaxf(__fadd_rn(u.y, b.y), 0.f);
+                    v[4 * j + 2] = fmaxf(__fadd_rn(u.z, b.z), 0.f);
+                    v[4 * j + 3] = fmaxf(__fadd_rn(u.w, b.w), 0.f);
+                }
+                store_act(c, v, save ? q : -1, n0, any);
             }
-            store_act(c, v, a.acts && ok ? a.acts + row * WRF_HIDDEN : nullptr);
         }
         tmem_wait_st();
         tc_fence_before();
@@ -204,22 +291,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a) {
             wait_or_abort(mbar, phase, abort_flag, a.status);
             phase ^= 1u;
             tc_fence_after();
-            float *act = a.acts && ok ? a.acts + (static_cast<size_t>(l + 1) * rows + row) * WRF_HIDDEN
-                                      : nullptr;
+            const int z = save ? (l + 1) * a.Q + q : -1;
 #pragma unroll 1
             for (int c = 0; c < 4; ++c) {
                 float v[32];
                 tmem_ld32(t_acc + lane_off + static_cast<uint32_t>(c * 32), v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) v[j] = fmaxf(v[j], 0.f);
-                store_act(c, v, act);
+                store_act(c, v, z, n0, any);
             }
             tmem_wait_st();
             tc_fence_before();
             named_bar(1 + wg, 128);
         }
-        // ---- output layer
+        // ---- output layer (the next tile's operands load meanwhile)
         if (leader) layer_mmas(true, 0);
+        if (tile + stride < a.ntiles) prefetch(tile + stride);
         wait_or_abort(mbar, phase, abort_flag, a.status);
         phase ^= 1u;
         tc_fence_after();
@@ -233,15 +320,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_x3_kernel(X3Args a) {
                 for (int j = 0; j < WRF_OUT; ++j) dst[j] = o[j];
             } else {
                 float4 r0, r1;
-                project_geom(ppre, o[0], o[1], o[2], o[3], o[4], a.g, r0, r1);
+                project_geom(pcur, o[0], o[1], o[2], o[3], o[4], a.g, r0, r1);
                 a.rec[2 * row] = r0;
                 a.rec[2 * row + 1] = r1;
-                if (a.rec_im) a.rec_im[row] = weight_im(ppre);
+                if (a.rec_im) a.rec_im[row] = weight_im(pcur);
                 if (a.count) a.count[row] = record_tiles(r0, r1, a.g);
             }
         }
         named_bar(1 + wg, 128);  // TMEM columns and the V row are free again
     }
+    if (lane == 0) bulk_wait_all();  // this warp's activation stores are done
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -279,6 +367,23 @@ cudaError_t launch_mlp_x3(const SceneView &s, const MlpView &m, const GridView &
     a.rec_im = (mode == 1 && s.channels == 2) ? reinterpret_cast<float *>(rec + 2 * rows) : nullptr;
     a.acts = acts;
     a.status = status;
+    // the activations as [(nh + 1) Q][N][128], a box of 16 columns x 32 rows
+    CUtensorMap amap;
+    std::memset(&amap, 0, sizeof(amap));
+    if (acts) {
+        EncodeTiledFn f = encode_tiled();
+        if (!f) return cudaErrorSymbolNotFound;
+        const cuuint64_t dims[3] = {WRF_HIDDEN, static_cast<cuuint64_t>(s.n),
+                                    static_cast<cuuint64_t>(nh + 1) * static_cast<cuuint64_t>(Q)};
+        const cuuint64_t strides[2] = {WRF_HIDDEN * 4,
+                                       static_cast<cuuint64_t>(s.n) * WRF_HIDDEN * 4};
+        const cuuint32_t box[3] = {static_cast<cuuint32_t>(kStageCols), 32, 1};
+        const cuuint32_t elem[3] = {1, 1, 1};
+        if (f(&amap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, acts, dims, strides, box, elem,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     const size_t smem = smem_bytes(nh);
     cudaError_t e = cudaFuncSetAttribute(mlp_x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -288,7 +393,7 @@ cudaError_t launch_mlp_x3(const SceneView &s, const MlpView &m, const GridView &
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int grid = (a.ntiles + kWG - 1) / kWG;
     if (grid > sms) grid = sms;
-    mlp_x3_kernel<<<grid, kThreads, smem, st>>>(a);
+    mlp_x3_kernel<<<grid, kThreads, smem, st>>>(a, amap);
     return cudaGetLastError();
 }
 

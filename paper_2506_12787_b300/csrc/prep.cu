@@ -24,11 +24,15 @@ constexpr size_t kW1ImageBytes = WRF_HIDDEN * 128;  // 128 rows x 64 BF16 column
 
 
 // Per-Gaussian part of layer 1 for 32 Gaussians per block.  FP32 path:
-// U[n][j] = W0[j, :dm] . gamma(mean_n), thread j owns column j.  BF16 path:
-// the row gamma(mean_n) itself in BF16, zero-padded to k1 columns, which the
-// tensor-core kernel multiplies by the W1m image.
+// U[n][j] = W0[j, :dm] . gamma(mean_n), thread j owns column j; row-major
+// [N][128], or (blocked, for the three-product tensor-core kernel) in
+// 128-Gaussian blocks of [32 column quads][128 rows][4], so that the 128
+// threads of a tile, one row each, read a column quad as one contiguous
+// 2 KB run.  BF16 path: the row gamma(mean_n) itself in BF16, zero-padded to
+// k1 columns, which the tensor-core kernel multiplies by the W1m image.
 __device__ __forceinline__ void pe_mean_block(int blk, const SceneView &s, const MlpView &m,
-                                              const GridView &g, float *U, uint16_t *G, int k1) {
+                                              const GridView &g, float *U, uint16_t *G, int k1,
+                                              bool blocked) {
     __shared__ float gam[32][kMaxPe];
     const int n0 = blk * 32;
     const int din = m.dm + m.dt;
@@ -64,8 +68,14 @@ __device__ __forceinline__ void pe_mean_block(int blk, const SceneView &s, const
         for (int r = 0; r < 32; ++r) acc[r] = fmaf(w, gam[r][k], acc[r]);
     }
 #pragma unroll
-    for (int r = 0; r < 32; ++r)
-        if (n0 + r < s.n) U[static_cast<size_t>(n0 + r) * WRF_HIDDEN + j] = acc[r];
+    for (int r = 0; r < 32; ++r) {
+        const int n = n0 + r;
+        if (n >= s.n) continue;
+        const size_t at = blocked ? ((static_cast<size_t>(n >> 7) * 32 + (j >> 2)) * 128 +
+                                     (n & 127)) * 4 + (j & 3)
+                                  : static_cast<size_t>(n) * WRF_HIDDEN + j;
+        U[at] = acc[r];
+    }
 }
 
 // V[q][j] for 4 queries per block: the 4 x dt features of Eq. 15 are
@@ -243,7 +253,8 @@ __global__ void __launch_bounds__(128) prep_kernel(SceneView s, MlpView m, GridV
                                                    int nb_tx) {
     int b = blockIdx.x;
     if (b < nb_mean) {
-        pe_mean_block(b, s, m, g, ws.U, images == WRF_BF16 ? ws.G : nullptr, k1);
+        pe_mean_block(b, s, m, g, ws.U, images == WRF_BF16 ? ws.G : nullptr, k1,
+                      images == WRF_BF16X3);
         return;
     }
     b -= nb_mean;
@@ -272,7 +283,8 @@ size_t deform_ws_layout(int n, int Q, int n_layers, DeformWs *ws, char *base) {
     };
     int nh = n_layers - 2 > 0 ? n_layers - 2 : 0;
     DeformWs w{};
-    w.U = reinterpret_cast<float *>(take(static_cast<size_t>(n) * WRF_HIDDEN * 4));
+    // rows rounded up to whole 128-Gaussian blocks (the blocked layout)
+    w.U = reinterpret_cast<float *>(take(static_cast<size_t>((n + 127) & ~127) * WRF_HIDDEN * 4));
     w.G = reinterpret_cast<uint16_t *>(take(static_cast<size_t>(n) * 64 * 2));
     w.V = reinterpret_cast<float *>(take(static_cast<size_t>(Q) * WRF_HIDDEN * 4));
     w.wt_f32 = reinterpret_cast<float *>(take(static_cast<size_t>(nh) * WRF_HIDDEN * WRF_HIDDEN * 4));

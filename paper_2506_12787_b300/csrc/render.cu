@@ -490,25 +490,7 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
 }
 
 // The record tensor map: rows of 8 FP32 (32 bytes), a box of one row (the
-// gather's shape).  cuTensorMapEncodeTiled is fetched from the driver at the
-// first use (the library does not link libcuda).
-using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-EncodeTiledFn encode_tiled() {
-    static std::once_flag once;
-    static EncodeTiledFn fn = nullptr;
-    std::call_once(once, [] {
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult r;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
-                                             &r) == cudaSuccess &&
-            r == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(f);
-    });
-    return fn;
-}
+// gather's shape).
 cudaError_t record_map(const float4 *rec, unsigned long long rows, CUtensorMap *m) {
     std::memset(m, 0, sizeof(*m));
     if (!rec || rows == 0) return cudaSuccess;  // no records: the map is never used
@@ -597,6 +579,22 @@ cudaError_t launch_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled, fetched from the driver at the first use (the
+// library does not link libcuda).
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult r;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &r) == cudaSuccess &&
+            r == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
 
 bool render_config_supported(int tw, int th) {
     return (tw == 8 && th == 8) || (tw == 16 && th == 8) || (tw == 16 && th == 16) ||
