@@ -452,6 +452,8 @@ class Renderer:
         self.cap = int(key_capacity)
         self.fused = fused
         self._ws = {}
+        self._nk_host = None   # pinned key count of a deferred binning
+        self._pending = None   # (event, capacity, stream) of a deferred binning
 
     def _buf(self, name, nbytes):
         b = self._ws.get(name)
@@ -490,9 +492,56 @@ class Renderer:
         wrf_project(scene, resid, Q, self.grid, rec=rec, tile_count=None, stream=stream)
         return rec, resid
 
-    def bin_and_render(self, rec, n, Q, stream=None, out=None, channels=1):
+    def bin_and_render(self, rec, n, Q, stream=None, out=None, channels=1, deferred=False):
+        """Bins and renders.  The key count is read back (a host sync) and the
+        binning repeated with a larger key capacity until the keys fit --
+        unless deferred is set and a capacity is known: then one pass runs with
+        the current capacity, the key count is copied back asynchronously, and
+        the caller must call key_overflow() before using the results (a
+        result with too many keys is all zeros and must be recomputed)."""
         L = _lib.load()
         T = tiles_of(self.grid)
+        if deferred and self.cap > 0:
+            gids = self._tensor("gids", (self.cap,), torch.int32)
+            n_keys = self._tensor("nk", (1,), torch.int64)
+            offs = self._tensor("offs", (Q * T + 1,), torch.int32)
+            bws = self._buf("bws", L.wrf_bin_workspace_size(n, Q, C.byref(self.grid)))
+            wrf_bin(rec, n, Q, self.grid, self.cap, gids=gids, n_keys=n_keys, offsets=offs,
+                    ws=bws, stream=stream)
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            if self._nk_host is None:
+                self._nk_host = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+            with torch.cuda.stream(s):
+                self._nk_host.copy_(n_keys, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
+            self._pending = (ev, self.cap, s)
+        else:
+            gids, n_keys, offs = self._bin_checked(rec, n, Q, T, stream)
+        render = wrf_render_complex if channels == 2 else wrf_render
+        out = render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out, stream=stream)
+        self.last = dict(rec=rec, gids=gids, offs=offs, n_keys=n_keys, n=n, Q=Q)
+        return out
+
+    def key_overflow(self) -> bool:
+        """After a deferred bin_and_render: waits for its key count (the
+        binning only, not the rest of the stream) and returns True if the keys
+        did not fit -- the capacity has then been raised and the results of
+        that call are void."""
+        if self._pending is None:
+            return False
+        ev, cap, s = self._pending
+        self._pending = None
+        ev.synchronize()
+        need = int(self._nk_host[0])
+        if need <= cap:
+            return False
+        wrf_status_read(s)  # clear the recorded overflow
+        self.cap = max(self.cap, int(need * 1.25) + 1024)
+        return True
+
+    def _bin_checked(self, rec, n, Q, T, stream):
+        L = _lib.load()
         if self.cap <= 0:
             self.cap = max(1 << 16, Q * n * 6)
         while True:
@@ -504,13 +553,9 @@ class Renderer:
                     ws=bws, stream=stream)
             need = int(n_keys.item())
             if need <= self.cap:
-                break
+                return gids, n_keys, offs
             wrf_status_read(stream)  # clear the recorded overflow
             self.cap = int(need * 1.25) + 1024
-        render = wrf_render_complex if channels == 2 else wrf_render
-        out = render(rec, gids, offs, n_keys, self.cap, n, Q, self.grid, out=out, stream=stream)
-        self.last = dict(rec=rec, gids=gids, offs=offs, n_keys=n_keys, n=n, Q=Q)
-        return out
 
     def forward_paper(self, scene: DevicePaperScene, mlp, tx, stream=None, out=None):
         """Magnitude and phase [Q,2,H,W] with the paper's head (Sec. 6.1)."""
@@ -524,9 +569,12 @@ class Renderer:
         self.last["resid"] = None
         return out
 
-    def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None, acts=None):
+    def forward(self, scene: DeviceScene, mlp, tx, stream=None, out=None, acts=None,
+                deferred=False):
+        """Spectra [Q,H,W] (deferred: see bin_and_render)."""
         Q = int(tx.shape[0])
         rec, resid = self.project(scene, mlp, tx, stream=stream, acts=acts)
-        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out, channels=scene.channels)
+        out = self.bin_and_render(rec, scene.n, Q, stream=stream, out=out, channels=scene.channels,
+                                  deferred=deferred)
         self.last["resid"] = resid
         return out

@@ -35,6 +35,10 @@ class SpectrumConfig:
     # the forward MLP: api.WRF_FP32 (CUDA cores) or api.WRF_BF16X3 (tensor
     # cores, three BF16 products per FP32 product: FP32-level results)
     mlp_precision: int = api.WRF_FP32
+    # the forward does not wait for the key count (no host sync): the caller
+    # calls renderer.key_overflow() before using the step's results and
+    # recomputes them if it returns True (train.Trainer does)
+    defer_key_check: bool = False
 
 
 class SpectrumFunction(torch.autograd.Function):
@@ -62,7 +66,7 @@ class SpectrumFunction(torch.autograd.Function):
             if nbytes <= cfg.saved_activation_bytes:
                 acts = torch.empty((len(W) - 1, int(txc.shape[0]) * scene.n, 128),
                                    dtype=torch.float32, device=dev)
-        out = r.forward(scene, mlp, txc, acts=acts).clone()
+        out = r.forward(scene, mlp, txc, acts=acts, deferred=cfg.defer_key_check).clone()
         last = r.last
         ctx.cfg, ctx.scene, ctx.mlp, ctx.tx = cfg, scene, mlp, txc
         ctx.saved = dict(rec=last["rec"].clone(), gids=last["gids"].clone(),

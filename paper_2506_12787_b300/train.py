@@ -17,6 +17,11 @@ on across the stages (its step count is the number of updates that parameter
 has had); PyTorch's Adam defaults beta = (0.9, 0.999), eps = 1e-8; the
 minibatch of TX positions drawn uniformly with replacement every iteration.
 Random draws come from a torch.Generator the caller seeds, or are passed in.
+
+A step does not stall the host: host-side draws reach the device through
+pinned staging buffers, and the forward's key count is checked only before
+the Adam update (SpectrumConfig.defer_key_check); a step whose keys did not
+fit is recomputed with the raised capacity before any parameter changes.
 """
 from __future__ import annotations
 
@@ -63,6 +68,33 @@ class Trainer:
         self.state = {id(p): [torch.zeros_like(p), torch.zeros_like(p), 0]
                       for p in list(self.g.values()) + self.mlp}
         self.it = 0
+        spec.defer_key_check = True
+        self._ring = [None] * 4  # pinned staging buffers: (buffer, copy-done event)
+        self._ring_i = 0
+
+    def _upload(self, t):
+        """t on the training device; a host tensor goes through a pinned
+        staging buffer (asynchronous copy; a buffer is reused once its previous
+        copy has finished), so the host does not wait for the device."""
+        dev = self.tx_train.device
+        if t.device == dev or dev.type != "cuda":
+            return t.to(dev)
+        t = t.contiguous()
+        nbytes = t.numel() * t.element_size()
+        slot = self._ring_i % len(self._ring)
+        self._ring_i += 1
+        buf, ev = self._ring[slot] or (None, None)
+        if ev is not None:
+            ev.synchronize()
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(nbytes, 4096), dtype=torch.uint8, pin_memory=True)
+        host = buf[:nbytes].view(t.dtype).view(t.shape)
+        host.copy_(t)
+        out = host.to(dev, non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record()
+        self._ring[slot] = (buf, ev)
+        return out
 
     @property
     def coarse(self) -> bool:
@@ -73,7 +105,7 @@ class Trainer:
         positions idx plus the Eq. 18 noise (wrf_anneal_tx), in metres."""
         if normals is None:
             normals = torch.randn(int(idx.numel()), 3, generator=self.gen)
-        normals = normals.to(device=self.tx_train.device, dtype=torch.float32).contiguous()
+        normals = self._upload(normals.to(torch.float32))
         i = self.it - self.cfg.coarse_iters
         return api.wrf_anneal_tx(self.tx_train, normals, i, self.cfg.gamma, self.cfg.tau,
                                  self.spec.room_size, idx=idx)
@@ -90,9 +122,11 @@ class Trainer:
         c = self.cfg
         if idx is None:
             idx = torch.randint(self.tx_train.shape[0], (c.batch,), generator=self.gen)
-        idx = idx.to(self.tx_train.device)
+        idx = self._upload(idx)
         tgt = self.targets[idx]
         coarse = self.coarse
+        if not coarse and normals is None:
+            normals = torch.randn(int(idx.numel()), 3, generator=self.gen)
         tx = self.noisy_tx(idx, normals) if not coarse else self.tx_train[idx]
         self.spec.stop_grad_mean = not coarse
         leaves = {k: v.detach().requires_grad_(coarse or k != "mean") for k, v in self.g.items()}
@@ -101,6 +135,10 @@ class Trainer:
                              leaves["rot"], leaves["opacity_logit"], leaves["amp"], params)
         loss = spectrum_loss(out, tgt, c.lambda1)
         loss.backward()
+        if self.spec.renderer.key_overflow():
+            # the keys did not fit: recompute with the raised capacity (same
+            # draws) before any parameter changes
+            return self.step(idx=idx, normals=normals)
         groups = []
         for k in GAUSS_FIELDS:
             if leaves[k].grad is not None:
