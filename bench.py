@@ -186,7 +186,7 @@ class ClockSampler:
         try:
             self.p = subprocess.Popen(
                 ["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -213,7 +213,7 @@ class ClockSampler:
         os.unlink(self.f.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        # samples are ~100 ms apart; keep the ones taken under load (the top
+        # samples are ~200 ms apart; keep the ones taken under load (the top
         # half of power draw) -- the timed region is the only sustained load
         def fnum(x):
             try:
