@@ -79,6 +79,9 @@ def parse():
     p.add_argument("--tile", default="auto",
                    help="rasteriser configuration WxH or WxHpPXbBF (tile, pixels per thread, "
                         "records per thread per batch), or auto (autotuned, cached)")
+    p.add_argument("--queries", type=int, default=None,
+                   help="TX positions per step in place of the workload's (a smaller case of "
+                        "the same kernels, e.g. for profiler captures); the line's config says so")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU-oracle time of the cpu_baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -100,6 +103,11 @@ def parse():
     args = p.parse_args()
     if args.precision is None:
         args.precision = "bf16x3" if args.workload in ("paper", "train") else "bf16"
+    if args.queries is not None:
+        if args.queries < 1:
+            p.error("--queries must be >= 1")
+        global QUERIES
+        QUERIES = args.queries
     return args
 
 
@@ -127,8 +135,12 @@ def aggregate(seconds_local, units_local, dist=None):
     return tmax, utot, utot / tmax
 
 
+QUERIES = None  # --queries: TX positions per step in place of the workload's (small cases)
+
+
 def make_inputs(workload, rank, channels=1):
     N, H, W, Q, lsm, lss = WORKLOADS[workload]
+    Q = QUERIES or Q
     sc = synth.make_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
     if channels == 2:
         sc = synth.complex_amplitudes(sc, seed=0)
@@ -294,6 +306,7 @@ def paper_inputs(rank):
     """The paper-head workload: primitives of the paper's parameterisation,
     its 8 x 156 network (unit-gain weights, small biases), TX in the room."""
     N, H, W, Q, lsm, lss = WORKLOADS["paper"]
+    Q = QUERIES or Q
     sc = synth.make_paper_scene(N, H, W, ls_mean=lsm, ls_std=lss, seed=0)
     m = synth.make_paper_mlp(gain=1.0, bias_std=0.05, seed=0)
     tx = synth.make_tx(Q, seed=1 + rank)
