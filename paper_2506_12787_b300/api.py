@@ -513,8 +513,12 @@ class Renderer:
                 self._nk_host = torch.zeros(1, dtype=torch.int64, pin_memory=True)
             with torch.cuda.stream(s):
                 self._nk_host.copy_(n_keys, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s)
+                ev = None
+                if not torch.cuda.is_current_stream_capturing():
+                    # (inside a CUDA-graph capture the caller synchronises
+                    # after the replay instead)
+                    ev = torch.cuda.Event()
+                    ev.record(s)
             self._pending = (ev, self.cap, s)
         else:
             gids, n_keys, offs = self._bin_checked(rec, n, Q, T, stream)
@@ -527,16 +531,29 @@ class Renderer:
         """After a deferred bin_and_render: waits for its key count (the
         binning only, not the rest of the stream) and returns True if the keys
         did not fit -- the capacity has then been raised and the results of
-        that call are void."""
+        that call are void.  (A call captured in a CUDA graph is checked with
+        replayed_key_overflow after each replay.)"""
         if self._pending is None:
             return False
         ev, cap, s = self._pending
         self._pending = None
+        if ev is None:
+            return False
         ev.synchronize()
         need = int(self._nk_host[0])
         if need <= cap:
             return False
         wrf_status_read(s)  # clear the recorded overflow
+        self.cap = max(self.cap, int(need * 1.25) + 1024)
+        return True
+
+    def replayed_key_overflow(self, cap, stream=None) -> bool:
+        """key_overflow for a deferred binning captured in a CUDA graph with
+        key capacity cap, after the caller has synchronised with the replay."""
+        need = int(self._nk_host[0])
+        if need <= cap:
+            return False
+        wrf_status_read(stream)  # clear the recorded overflow
         self.cap = max(self.cap, int(need * 1.25) + 1024)
         return True
 

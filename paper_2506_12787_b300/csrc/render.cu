@@ -430,12 +430,33 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     }
 }
 
+// Backward of the order-free sum (Eq. 9) for one (tile, query): per key
+// (record n of the tile's list) the sums over its in-cutoff pixels of
+//   ge = dL/dA(p) e(p),  e = exp(-q/2):
+//   S0 = sum ge, S1 = sum ge dx, S2 = sum ge dy,
+//   S3 = sum ge dx^2, S4 = sum ge dx dy, S5 = sum ge dy^2,
+// from which dL/dw = S0, dL/dmean = w (Sigma^-1 (S1, S2)) and
+// dL/d(A, B, C) = -w (S3 / 2, S4, S5 / 2) (the conic in record units).
+//
+// Work split: a warp takes 32 keys at a time and cuts them into items of one
+// row of a key's box (within the tile).  Each lane gets a contiguous range of
+// the items (all ranges equal to within one), so the lanes of a warp run
+// equally long instead of as long as the warp's largest box; within a row
+// only the x-interval where the quadratic form can be under the cutoff is
+// visited (solved per row with a margin; the per-pixel test decides).  A
+// lane keeps the sums of its current key in registers (the row terms of S2,
+// S4, S5 folded at each row end) and adds them into the warp's per-key sums
+// in shared memory when it moves to the next key; one lane per key then
+// adds the six gradients to d_rec.
 template <int TW, int TH>
 __global__ void __launch_bounds__(128) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float cut_s, const float *__restrict__ dA, float *__restrict__ d_rec) {
     __shared__ float sg[TH][TW];
+    __shared__ float4 kpar[4][32][3];  // per warp and key: mx, my, A, B | C, 1/A, xa, xb | ya
+    __shared__ int kpre[4][33];        // per warp: item (row) prefix over its 32 keys
+    __shared__ float kacc[4][32][6];   // per warp and key: S0 .. S5
     const int t = blockIdx.x, q = blockIdx.y;
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
     for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
@@ -449,43 +470,132 @@ __global__ void __launch_bounds__(128) render_bwd_kernel(
     const uint32_t s1 = offs[static_cast<size_t>(q) * g.T + t + 1];
     const float inv = 1.f / kHalfLog2e;
     const int xe = min(x0 + TW, g.W) - 1, ye = min(y0 + TH, g.H) - 1;
-    for (uint32_t i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
-        const uint32_t gid = gids[i];
-        const size_t r = static_cast<size_t>(q) * n + gid;
-        float4 r0 = rec[2 * r];
-        const float4 r1 = rec[2 * r + 1];
-        // with azimuth wrap, the image of the Gaussian nearest to this tile
-        r0.x = nearest_image_x(r0.x, static_cast<float>(x0) + 0.5f * TW, g);
-        int xa = max(x0, static_cast<int>(ceilf(fmaxf(r0.x - r1.z, static_cast<float>(x0)))));
-        int xb = min(xe, static_cast<int>(floorf(fminf(r0.x + r1.z, static_cast<float>(xe)))));
-        int ya = max(y0, static_cast<int>(ceilf(fmaxf(r0.y - r1.w, static_cast<float>(y0)))));
-        int yb = min(ye, static_cast<int>(floorf(fminf(r0.y + r1.w, static_cast<float>(ye)))));
-        const float A = r0.z * inv, Bc = r0.w * inv, Cc = r1.x * inv, w = r1.y;
-        float gmx = 0.f, gmy = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, gw = 0.f;
-        for (int y = ya; y <= yb; ++y) {
-            const float dy = static_cast<float>(y) - r0.y;
-            for (int x = xa; x <= xb; ++x) {
-                const float dx = static_cast<float>(x) - r0.x;
-                const float nq = -(dx * fmaf(r0.z, dx, 2.f * r0.w * dy) + r1.x * dy * dy);
-                if (!(nq >= -cut_s)) continue;
-                const float e = ex2_approx(nq);
-                const float gp = sg[y - y0][x - x0];
-                const float ge = gp * e, gwe = ge * w;
-                gw += ge;
-                gmx = fmaf(gwe, fmaf(A, dx, Bc * dy), gmx);
-                gmy = fmaf(gwe, fmaf(Bc, dx, Cc * dy), gmy);
-                gA = fmaf(-0.5f * gwe, dx * dx, gA);
-                gB = fmaf(-gwe, dx * dy, gB);
-                gC = fmaf(-0.5f * gwe, dy * dy, gC);
-            }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4(*par)[3] = kpar[warp];
+    int *pre = kpre[warp];
+    float(*acc)[6] = kacc[warp];
+    for (uint32_t base = s0 + 32u * warp; base < s1; base += 128u) {
+        // ---- this lane's key: its box within the tile and its row count
+        const uint32_t i = base + lane;
+        size_t r = 0;
+        float w = 0.f, A = 0.f, Bc = 0.f, Cc = 0.f;
+        int rows = 0;
+        if (i < s1) {
+            r = static_cast<size_t>(q) * n + gids[i];
+            float4 r0 = rec[2 * r];
+            const float4 r1 = rec[2 * r + 1];
+            // with azimuth wrap, the image of the Gaussian nearest to this tile
+            r0.x = nearest_image_x(r0.x, static_cast<float>(x0) + 0.5f * TW, g);
+            const int xa = max(x0, static_cast<int>(ceilf(fmaxf(r0.x - r1.z, static_cast<float>(x0)))));
+            const int xb = min(xe, static_cast<int>(floorf(fminf(r0.x + r1.z, static_cast<float>(xe)))));
+            const int ya = max(y0, static_cast<int>(ceilf(fmaxf(r0.y - r1.w, static_cast<float>(y0)))));
+            const int yb = min(ye, static_cast<int>(floorf(fminf(r0.y + r1.w, static_cast<float>(ye)))));
+            rows = (xa <= xb && ya <= yb) ? yb - ya + 1 : 0;
+            A = r0.z * inv;
+            Bc = r0.w * inv;
+            Cc = r1.x * inv;
+            w = r1.y;
+            par[lane][0] = r0;
+            par[lane][1] = make_float4(r1.x, 1.f / r0.z, static_cast<float>(xa),
+                                       static_cast<float>(xb));
+            par[lane][2] = make_float4(static_cast<float>(ya), 0.f, 0.f, 0.f);
         }
-        float *o = d_rec + r * 6;
-        atomicAdd(o + 0, gmx);
-        atomicAdd(o + 1, gmy);
-        atomicAdd(o + 2, gA);
-        atomicAdd(o + 3, gB);
-        atomicAdd(o + 4, gC);
-        atomicAdd(o + 5, gw);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) acc[lane][j] = 0.f;
+        int incl = rows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        pre[lane + 1] = incl;
+        if (lane == 0) pre[0] = 0;
+        __syncwarp();
+        // ---- this lane's items [it0, it1): rows of consecutive keys
+        const int it0 = static_cast<int>(static_cast<long long>(total) * lane / 32);
+        const int it1 = static_cast<int>(static_cast<long long>(total) * (lane + 1) / 32);
+        if (it0 < it1) {
+            int k = 0;  // the last key whose items start at or before it0
+            for (int step = 16; step > 0; step >>= 1)
+                if (k + step <= 32 && pre[k + step] <= it0) k += step;
+            int row = it0 - pre[k], nrow = pre[k + 1] - pre[k];
+            float4 p0 = par[k][0], p1 = par[k][1];
+            float yk = par[k][2].x;
+            float S0 = 0.f, S1 = 0.f, S2 = 0.f, S3 = 0.f, S4 = 0.f, S5 = 0.f;
+            for (int it = it0; it < it1; ++it) {
+                if (row == nrow) {
+                    // next key with rows: hand this key's sums to the warp
+                    atomicAdd(&acc[k][0], S0);
+                    atomicAdd(&acc[k][1], S1);
+                    atomicAdd(&acc[k][2], S2);
+                    atomicAdd(&acc[k][3], S3);
+                    atomicAdd(&acc[k][4], S4);
+                    atomicAdd(&acc[k][5], S5);
+                    S0 = S1 = S2 = S3 = S4 = S5 = 0.f;
+                    do {
+                        ++k;
+                    } while (pre[k + 1] == pre[k]);
+                    row = 0;
+                    nrow = pre[k + 1] - pre[k];
+                    p0 = par[k][0];
+                    p1 = par[k][1];
+                    yk = par[k][2].x;
+                }
+                const int y = static_cast<int>(yk) + row;
+                ++row;
+                const float dy = static_cast<float>(y) - p0.y;
+                // x-interval of this row where the form r0.z dx^2 + 2 r0.w dx dy +
+                // r1.x dy^2 can be <= cut_s (margin 1/64 px; the test below decides)
+                const float bq = p0.w * dy;
+                const float disc = fmaf(bq, bq, -p0.z * fmaf(p1.x * dy, dy, -cut_s));
+                if (!(disc >= 0.f)) continue;
+                const float sq = sqrtf(disc);
+                const float xlo = fmaxf(ceilf(p0.x + (-bq - sq) * p1.y - 0.015625f), p1.z);
+                const float xhi = fminf(floorf(p0.x + (-bq + sq) * p1.y + 0.015625f), p1.w);
+                if (!(xlo <= xhi)) continue;
+                const int xl = static_cast<int>(xlo), xh = static_cast<int>(xhi);
+                const float b2 = 2.f * p0.w * dy, c0 = p1.x * dy * dy;
+                const float *grow = &sg[y - y0][0];
+                float R0 = 0.f, R1 = 0.f;  // this row's sums of ge and ge dx
+                float dx = static_cast<float>(xl) - p0.x;
+                for (int x = xl; x <= xh; ++x, dx += 1.f) {
+                    const float nq = -(dx * fmaf(p0.z, dx, b2) + c0);
+                    if (nq >= -cut_s) {
+                        const float ge = grow[x - x0] * ex2_approx(nq);
+                        const float tx = ge * dx;
+                        R0 += ge;
+                        R1 += tx;
+                        S3 = fmaf(tx, dx, S3);
+                    }
+                }
+                S0 += R0;
+                S1 += R1;
+                S2 = fmaf(R0, dy, S2);
+                S4 = fmaf(R1, dy, S4);
+                S5 = fmaf(R0 * dy, dy, S5);
+            }
+            atomicAdd(&acc[k][0], S0);
+            atomicAdd(&acc[k][1], S1);
+            atomicAdd(&acc[k][2], S2);
+            atomicAdd(&acc[k][3], S3);
+            atomicAdd(&acc[k][4], S4);
+            atomicAdd(&acc[k][5], S5);
+        }
+        __syncwarp();
+        // ---- one lane per key: the six gradients of its record
+        if (rows > 0) {
+            const float S0 = acc[lane][0], S1 = acc[lane][1], S2 = acc[lane][2];
+            const float S3 = acc[lane][3], S4 = acc[lane][4], S5 = acc[lane][5];
+            float *o = d_rec + r * 6;
+            atomicAdd(o + 0, w * fmaf(A, S1, Bc * S2));
+            atomicAdd(o + 1, w * fmaf(Bc, S1, Cc * S2));
+            atomicAdd(o + 2, -0.5f * w * S3);
+            atomicAdd(o + 3, -w * S4);
+            atomicAdd(o + 4, -0.5f * w * S5);
+            atomicAdd(o + 5, S0);
+        }
+        __syncwarp();  // par / pre / acc are rewritten for the next 32 keys
     }
 }
 

@@ -59,7 +59,8 @@ class Trainer:
     targets [N_s,H,W] on the device."""
 
     def __init__(self, gauss: dict, mlp_params: list, spec: SpectrumConfig, tx_train, targets,
-                 cfg: TrainConfig = TrainConfig(), generator: torch.Generator | None = None):
+                 cfg: TrainConfig = TrainConfig(), generator: torch.Generator | None = None,
+                 graph: bool = True):
         self.g = {k: gauss[k] for k in GAUSS_FIELDS}
         self.mlp = list(mlp_params)
         self.spec, self.cfg = spec, cfg
@@ -71,6 +72,9 @@ class Trainer:
         spec.defer_key_check = True
         self._ring = [None] * 4  # pinned staging buffers: (buffer, copy-done event)
         self._ring_i = 0
+        self.use_graph = graph and tx_train.device.type == "cuda"
+        self._graphs = {}  # stage (coarse?) -> captured forward + loss + backward
+        self.graph_steps = 0  # steps that replayed a graph
 
     def _upload(self, t):
         """t on the training device; a host tensor goes through a pinned
@@ -118,10 +122,25 @@ class Trainer:
 
     def step(self, idx=None, normals=None):
         """One iteration; idx [B] (training positions) and normals [B,3] may be
-        given, else they are drawn.  Returns the loss (0-dim tensor)."""
+        given, else they are drawn.  Returns the loss (0-dim tensor).
+
+        With graph=True (and a batch of cfg.batch positions on a CUDA
+        device) the forward, the loss and the backward replay a CUDA graph
+        captured once per stage; the anneal noise and the Adam update, whose
+        scalar arguments change every step, run as ordinary launches."""
         c = self.cfg
         if idx is None:
             idx = torch.randint(self.tx_train.shape[0], (c.batch,), generator=self.gen)
+        if not self.coarse and normals is None:
+            normals = torch.randn(int(idx.numel()), 3, generator=self.gen)
+        if self.use_graph and int(idx.numel()) == c.batch:
+            out = self._step_graph(idx, normals)
+            if out is not None:
+                return out
+        return self._step_eager(idx, normals)
+
+    def _step_eager(self, idx, normals):
+        c = self.cfg
         idx = self._upload(idx)
         tgt = self.targets[idx]
         coarse = self.coarse
@@ -138,7 +157,7 @@ class Trainer:
         if self.spec.renderer.key_overflow():
             # the keys did not fit: recompute with the raised capacity (same
             # draws) before any parameter changes
-            return self.step(idx=idx, normals=normals)
+            return self._step_eager(idx, normals)
         groups = []
         for k in GAUSS_FIELDS:
             if leaves[k].grad is not None:
@@ -148,6 +167,84 @@ class Trainer:
         self._adam(groups)
         self.it += 1
         return loss.detach()
+
+    # ---- CUDA-graph path
+    def _capture(self, coarse: bool, st: dict):
+        """Leaves sharing the parameters' storage and a graph of forward +
+        loss + backward over the static inputs st (positions, noise normals,
+        TX, already holding this step's values)."""
+        c, dev = self.cfg, self.tx_train.device
+        self.spec.stop_grad_mean = not coarse
+        leaves = {k: v.detach().requires_grad_(coarse or k != "mean") for k, v in self.g.items()}
+        params = [] if coarse else [p.detach().requires_grad_() for p in self.mlp]
+
+        def body():
+            tx = self.tx_train[st["idx"]] if coarse else st["tx"]
+            out = render_spectra(self.spec, tx, leaves["mean"], leaves["log_scale"],
+                                 leaves["rot"], leaves["opacity_logit"], leaves["amp"], params)
+            loss = spectrum_loss(out, self.targets[st["idx"]], c.lambda1)
+            loss.backward()
+            return loss.detach()
+
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(2):  # warm-up: key capacity, workspaces, pinned buffers
+                body()
+                self.spec.renderer.key_overflow()
+                for v in list(leaves.values()) + params:
+                    v.grad = None
+        torch.cuda.current_stream(dev).wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=side):
+            loss = body()
+        self.spec.renderer._pending = None  # replays are checked with replayed_key_overflow
+        return dict(graph=graph, static=st, leaves=leaves, params=params, loss=loss,
+                    cap=self.spec.renderer.cap, renderer=self.spec.renderer, stream=side)
+
+    def _step_graph(self, idx, normals):
+        coarse = self.coarse
+        if self.spec.renderer is None or self.spec.renderer.cap <= 0:
+            return None  # the first (eager) step sizes the key capacity
+        dev, B = self.tx_train.device, self.cfg.batch
+        gr = self._graphs.get(coarse)
+        if gr is not None and gr["cap"] != self.spec.renderer.cap:
+            gr = None
+        if gr is None:
+            self._graphs.clear()  # one stage at a time holds graph memory
+            st = dict(idx=torch.zeros(B, dtype=torch.int64, device=dev),
+                      normals=torch.zeros(B, 3, dtype=torch.float32, device=dev),
+                      tx=torch.zeros(B, 3, dtype=torch.float32, device=dev))
+        else:
+            st = gr["static"]
+        st["idx"].copy_(self._upload(idx))
+        if not coarse:
+            st["normals"].copy_(self._upload(normals.to(torch.float32)))
+            i = self.it - self.cfg.coarse_iters
+            api.wrf_anneal_tx(self.tx_train, st["normals"], i, self.cfg.gamma, self.cfg.tau,
+                              self.spec.room_size, idx=st["idx"], out=st["tx"])
+        if gr is None:
+            gr = self._graphs[coarse] = self._capture(coarse, st)
+        self.spec.stop_grad_mean = not coarse
+        gr["graph"].replay()
+        torch.cuda.current_stream(self.tx_train.device).synchronize()
+        if gr["renderer"].replayed_key_overflow(gr["cap"], gr["stream"]):
+            # the keys did not fit: the capacity is raised; recapture at the
+            # next step and recompute this one without the graph
+            self._graphs.pop(coarse, None)
+            return None
+        c = self.cfg
+        groups = []
+        for k in GAUSS_FIELDS:
+            lv = gr["leaves"][k]
+            if lv.grad is not None:
+                groups.append((self.g[k], lv.grad, c.lr_gauss))
+        for p, lp in zip(self.mlp, gr["params"]):
+            groups.append((p, lp.grad, c.lr_mlp))
+        self._adam(groups)
+        self.it += 1
+        self.graph_steps += 1
+        return gr["loss"].clone()
 
     def _adam(self, groups):
         # one launch per distinct step count (all equal except around the

@@ -239,3 +239,41 @@ def test_training_reduces_the_loss(api):
     losses = [float(tr.step(idx=torch.arange(32))) for _ in range(40)]
     print(f"loss: first {losses[0]:.4f}, after coarse {losses[19]:.4f}, last {losses[-1]:.4f}")
     assert losses[19] < 0.9 * losses[0] and losses[-1] < losses[0]
+
+
+def test_graph_step_matches_eager_step(api):
+    """The CUDA-graph training step (forward + loss + backward replayed, the
+    anneal noise and Adam launched per step) against the step without graphs
+    on the same draws: 2 coarse and 4 fine iterations, each loss within 1e-3
+    relative (the gradient atomics add in another order, and Adam's first
+    steps move each parameter by about lr whatever the gradient's size), the
+    graphs replayed from the second step on, parameters updated in place."""
+    from paper_2506_12787_b300.autograd import SpectrumConfig
+    from paper_2506_12787_b300.train import Trainer, TrainConfig
+    H, W = 30, 64
+    sc = synth.make_scene(400, H, W, seed=21)
+    m = synth.make_mlp(seed=21)
+    tx_np = synth.make_tx(16, seed=21)
+    tgt, _, _, _ = oracle.forward(synth.jitter_means(sc, 1.0, seed=22), m, tx_np, H, W, 9.0)
+    rng = np.random.default_rng(23)
+    draws = [(torch.as_tensor(rng.integers(0, 16, 8)), torch.as_tensor(rng.normal(size=(8, 3))))
+             for _ in range(6)]
+    runs = []
+    for graph in (True, False):
+        gauss = dict(zip(("mean", "log_scale", "rot", "opacity_logit", "amp"),
+                         [T(a) for a in sc.arrays()]))
+        mlp = []
+        for Wt, b in zip(m.W, m.b):
+            mlp += [T(Wt), T(b)]
+        tr = Trainer(gauss, mlp, SpectrumConfig(api.make_grid(H, W, 16, 16, 9.0)), T(tx_np),
+                     T(tgt), TrainConfig(coarse_iters=2, batch=8, tau=10),
+                     torch.Generator().manual_seed(0), graph=graph)
+        losses = [float(tr.step(idx=i, normals=z)) for i, z in draws]
+        runs.append((losses, tr, gauss, mlp))
+    (lg, trg, gg, mg), (le, tre, ge, me) = runs
+    print("graph losses", lg)
+    print("eager losses", le)
+    assert trg.graph_steps == 5 and tre.graph_steps == 0
+    assert np.allclose(lg, le, rtol=1e-3, atol=0)
+    for a, b in zip(list(gg.values()) + mg, list(ge.values()) + me):
+        assert torch.allclose(a, b, rtol=0, atol=6 * 1.02e-2)
