@@ -22,6 +22,7 @@ A step does not stall the host: host-side draws reach the device through
 pinned staging buffers, and the forward's key count is checked only before
 the Adam update (SpectrumConfig.defer_key_check); a step whose keys did not
 fit is recomputed with the raised capacity before any parameter changes.
+On CUDA the forward and the backward replay captured graphs (Trainer.step).
 """
 from __future__ import annotations
 
@@ -125,9 +126,11 @@ class Trainer:
         given, else they are drawn.  Returns the loss (0-dim tensor).
 
         With graph=True (and a batch of cfg.batch positions on a CUDA
-        device) the forward, the loss and the backward replay a CUDA graph
-        captured once per stage; the anneal noise and the Adam update, whose
-        scalar arguments change every step, run as ordinary launches."""
+        device) the forward with the loss, and the backward, replay two CUDA
+        graphs captured once per stage; the host waits for the forward only
+        (its key count) before launching Adam behind the backward.  The
+        anneal noise and the Adam update, whose scalar arguments change every
+        step, run as ordinary launches."""
         c = self.cfg
         if idx is None:
             idx = torch.randint(self.tx_train.shape[0], (c.batch,), generator=self.gen)
@@ -170,36 +173,40 @@ class Trainer:
 
     # ---- CUDA-graph path
     def _capture(self, coarse: bool, st: dict):
-        """Leaves sharing the parameters' storage and a graph of forward +
-        loss + backward over the static inputs st (positions, noise normals,
-        TX, already holding this step's values)."""
+        """Leaves sharing the parameters' storage and two graphs, forward +
+        loss and backward, over the static inputs st (positions, noise
+        normals, TX, already holding this step's values)."""
         c, dev = self.cfg, self.tx_train.device
         self.spec.stop_grad_mean = not coarse
         leaves = {k: v.detach().requires_grad_(coarse or k != "mean") for k, v in self.g.items()}
         params = [] if coarse else [p.detach().requires_grad_() for p in self.mlp]
 
-        def body():
+        def fwd():
             tx = self.tx_train[st["idx"]] if coarse else st["tx"]
             out = render_spectra(self.spec, tx, leaves["mean"], leaves["log_scale"],
                                  leaves["rot"], leaves["opacity_logit"], leaves["amp"], params)
-            loss = spectrum_loss(out, self.targets[st["idx"]], c.lambda1)
-            loss.backward()
-            return loss.detach()
+            return spectrum_loss(out, self.targets[st["idx"]], c.lambda1)
 
         side = torch.cuda.Stream(device=dev)
         side.wait_stream(torch.cuda.current_stream(dev))
         with torch.cuda.stream(side):
             for _ in range(2):  # warm-up: key capacity, workspaces, pinned buffers
-                body()
+                fwd().backward()
                 self.spec.renderer.key_overflow()
                 for v in list(leaves.values()) + params:
                     v.grad = None
         torch.cuda.current_stream(dev).wait_stream(side)
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=side):
-            loss = body()
+        # two graphs sharing one memory pool: the forward (with the binning's
+        # key count copied to the host) and the backward, so that a step can
+        # check the key count while its backward runs
+        g_fwd, g_bwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_fwd, stream=side):
+            loss = fwd()
+        with torch.cuda.graph(g_bwd, stream=side, pool=g_fwd.pool()):
+            loss.backward()
         self.spec.renderer._pending = None  # replays are checked with replayed_key_overflow
-        return dict(graph=graph, static=st, leaves=leaves, params=params, loss=loss,
+        return dict(g_fwd=g_fwd, g_bwd=g_bwd, fwd_done=torch.cuda.Event(), static=st,
+                    leaves=leaves, params=params, loss=loss.detach(),
                     cap=self.spec.renderer.cap, renderer=self.spec.renderer, stream=side)
 
     def _step_graph(self, idx, normals):
@@ -226,8 +233,10 @@ class Trainer:
         if gr is None:
             gr = self._graphs[coarse] = self._capture(coarse, st)
         self.spec.stop_grad_mean = not coarse
-        gr["graph"].replay()
-        torch.cuda.current_stream(self.tx_train.device).synchronize()
+        gr["g_fwd"].replay()
+        gr["fwd_done"].record()
+        gr["g_bwd"].replay()
+        gr["fwd_done"].synchronize()  # the forward only: the backward keeps running
         if gr["renderer"].replayed_key_overflow(gr["cap"], gr["stream"]):
             # the keys did not fit: the capacity is raised; recapture at the
             # next step and recompute this one without the graph
