@@ -94,6 +94,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_bmn(int M, int N) {
     return idesc_bf16(M, N) | (1u << 16);
 }
 
+// dst[0..3] += (a, b, c, d) at the L2 (a vector atomic whose result is unused).
+__device__ __forceinline__ void red_add_v4(float4 *dst, float a, float b, float c, float d) {
+    atomicAdd(dst, make_float4(a, b, c, d));
+}
+
 // BF16 hi / lo of a pair (x0 in the low half).
 __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_t &lo) {
     hi = pack_bf16(x0, x1);
@@ -257,15 +262,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(BwdArgs a) {
                     tmem_ld32(t_dw + lane_off + static_cast<uint32_t>(128 * s + 64 * wg + 32 * c), v);
                     float4 *dst = reinterpret_cast<float4 *>(
                         pd + (static_cast<size_t>(s) * 128 + u) * 128 + 64 * wg + 32 * c);
+                    // fire-and-forget vector reductions: the CTA owns its
+                    // partial, and one thread's reductions to an address are
+                    // applied in order, so every element is still the sum of
+                    // its flushes in flush order
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        float4 o = dst[j];
-                        o.x += v[4 * j];
-                        o.y += v[4 * j + 1];
-                        o.z += v[4 * j + 2];
-                        o.w += v[4 * j + 3];
-                        dst[j] = o;
-                    }
+                    for (int j = 0; j < 8; ++j)
+                        red_add_v4(dst + j, v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 }
             zero_dw();
         };
