@@ -277,3 +277,65 @@ def test_graph_step_matches_eager_step(api):
     assert np.allclose(lg, le, rtol=1e-3, atol=0)
     for a, b in zip(list(gg.values()) + mg, list(ge.values()) + me):
         assert torch.allclose(a, b, rtol=0, atol=6 * 1.02e-2)
+
+
+def _small_trainer(api, graph, seed=31):
+    from paper_2506_12787_b300.autograd import SpectrumConfig
+    from paper_2506_12787_b300.train import Trainer, TrainConfig
+    H, W = 30, 64
+    sc = synth.make_scene(300, H, W, seed=seed)
+    m = synth.make_mlp(seed=seed)
+    tx_np = synth.make_tx(16, seed=seed)
+    tgt, _, _, _ = oracle.forward(synth.jitter_means(sc, 1.0, seed=seed + 1), m, tx_np, H, W, 9.0)
+    gauss = dict(zip(("mean", "log_scale", "rot", "opacity_logit", "amp"),
+                     [T(a) for a in sc.arrays()]))
+    mlp = []
+    for Wt, b in zip(m.W, m.b):
+        mlp += [T(Wt), T(b)]
+    tr = Trainer(gauss, mlp, SpectrumConfig(api.make_grid(H, W, 16, 16, 9.0)), T(tx_np), T(tgt),
+                 TrainConfig(coarse_iters=1, batch=8, tau=10), torch.Generator().manual_seed(0),
+                 graph=graph)
+    return tr, gauss, mlp
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_key_overflow_recomputes_the_step(api, graph, monkeypatch):
+    """A step whose binning reports more keys than the capacity is
+    recomputed before any parameter changes: forcing one overflow report
+    (graph path: the replay's check; eager path: the deferred check) gives
+    the same losses and parameters as a run without it, the capacity grows,
+    and the graph path captures again and keeps replaying."""
+    from paper_2506_12787_b300 import api as A
+    rng = np.random.default_rng(32)
+    draws = [(torch.as_tensor(rng.integers(0, 16, 8)), torch.as_tensor(rng.normal(size=(8, 3))))
+             for _ in range(4)]
+    ref, gr_ref, mr_ref = _small_trainer(api, graph)
+    want = [float(ref.step(idx=i, normals=z)) for i, z in draws]
+    tr, gg, mg = _small_trainer(api, graph)
+    name = "replayed_key_overflow" if graph else "key_overflow"
+    orig = getattr(A.Renderer, name)
+    calls = {"n": 0}
+
+    def forced(self, *args):
+        calls["n"] += 1
+        real = orig(self, *args)
+        if calls["n"] == 2:  # the second check (a fine-stage step) reports an overflow
+            self.cap = int(self.cap * 1.5) + 1024
+            return True
+        return real
+    monkeypatch.setattr(A.Renderer, name, forced)
+    cap0 = None
+    got = []
+    for k, (i, z) in enumerate(draws):
+        got.append(float(tr.step(idx=i, normals=z)))
+        if k == 0:
+            cap0 = tr.spec.renderer.cap
+    print("losses without / with a forced overflow:", want, got)
+    assert calls["n"] >= 3
+    assert tr.spec.renderer.cap > cap0
+    assert np.allclose(got, want, rtol=1e-3, atol=0)
+    for a, b in zip(list(gg.values()) + mg, list(gr_ref.values()) + mr_ref):
+        assert torch.allclose(a, b, rtol=0, atol=4 * 1.02e-2)
+    assert tr.it == ref.it == len(draws)
+    if graph:
+        assert tr.graph_steps == ref.graph_steps - 1  # the overflowed step ran without the graph
