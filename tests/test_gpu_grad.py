@@ -80,14 +80,20 @@ def compare(g, ref, tag):
     return check_grads(groups_of(g, ref), tag)
 
 
-def test_render_backward_matches_oracle(api):
+@pytest.mark.parametrize("q_cut,tile", [(9.0, (16, 16)), (9.0, (8, 8)), (9.0, (32, 16)),
+                                        (2.0, (16, 16)), (math.inf, (16, 16))])
+def test_render_backward_matches_oracle(api, q_cut, tile):
+    """Every record gradient against the oracle: the usual cutoff over three
+    tile shapes (box rows split over the lanes of a warp), a tight cutoff
+    (many box rows without in-cutoff pixels) and no cutoff (every row of
+    every box in full)."""
     H, W = 90, 360
-    sc = synth.make_scene(600, H, W, ls_std=0.4, seed=40)
+    sc = synth.make_scene(600 if q_cut < math.inf else 200, H, W, ls_std=0.4, seed=40)
     Q = 2
     tx = synth.make_tx(Q, seed=40)
     dA = synth.rng(40).normal(size=(Q, H, W))
-    ref = oracle.grad(sc, None, tx, H, W, 9.0, dA)
-    grid = api.make_grid(H, W, 16, 16, 9.0)
+    ref = oracle.grad(sc, None, tx, H, W, q_cut, dA)
+    grid = api.make_grid(H, W, tile[0], tile[1], q_cut)
     ds = api.DeviceScene.from_host(sc, dev())
     r = api.Renderer(grid, dev())
     r.forward(ds, None, T(tx))
@@ -96,7 +102,8 @@ def test_render_backward_matches_oracle(api):
                                     grid, T(dA)).cpu().numpy()
     names = ["mx", "my", "A", "B", "C", "w"]
     worst = check_grads([(f"d_{nm}", d_rec[..., c], ref["d_proj"][..., c])
-                         for c, nm in enumerate(names)], "render backward")
+                         for c, nm in enumerate(names)],
+                        f"render backward q_cut={q_cut} tile={tile[0]}x{tile[1]}")
     assert worst <= 1.0
 
 
