@@ -657,6 +657,20 @@ def run_train(args):
     clk = clocks.stop()
     total_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     total_max, _, value = aggregate(total_s, Q * K, dist if ws > 1 else None)
+    # e2e: the same steps through the public API (Trainer.step) with the step's
+    # inputs on the host -- the minibatch positions passed as a host tensor and
+    # the anneal normals drawn on the host, both copied in by the step -- and
+    # the loss read back to the host after every step; host clock, the L2
+    # flush between steps inside the timed region
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        flush.fill_(i & 255)
+        float(step())
+    torch.cuda.synchronize()
+    _, _, e2e_val = aggregate(time.perf_counter() - t0, Q * K, dist if ws > 1 else None)
     # per-stage times of the same step (eager calls, default stream)
     ds = api.DeviceScene(*[gauss[k] for k in ("mean", "log_scale", "rot", "opacity_logit",
                                                "amp")])
@@ -719,6 +733,11 @@ def run_train(args):
                        "l2": "256 MB buffer rewritten between timed steps",
                        "final_loss_eq16": float(loss)},
             "clocks": clk, "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": "spectra/s",
+                    "h2d_bytes_per_step": 8 * Q + 12 * Q, "d2h_bytes_per_step": 4,
+                    "api": "train.Trainer.step with host minibatch indices (int64) and host "
+                           "anneal normals (3 x FP32 per position) copied in, the Eq. 16 loss "
+                           "read back to the host every step"},
             # this library's kernels: anneal noise (1); forward: prep, MLP,
             # project, bin x5, render (9); loss: 3; backward: render, project
             # (2), MLP: prep, backward preparation, the tensor-core kernel, its
