@@ -32,8 +32,9 @@
 //   3. output layer (N = 16, 5 used) the same way, then the residual row or
 //      the deformed and projected record (Eq. 12-13).
 // Saved activations leave through a 2 KB staging area per warp (16 columns
-// of its 32 rows) by TMA tensor stores, asynchronously: the conversion does
-// not wait for the stores, and no thread writes 32 scattered 16-byte pieces.
+// of its 32 rows) by TMA tensor stores: the conversion waits only until the
+// previous box has been read out of the staging area, not for the writes,
+// and no thread writes 32 scattered 16-byte pieces.
 // Every wait is bounded (WRF_ETIMEOUT on the status word).
 #include <cstring>
 
