@@ -264,20 +264,34 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(TcArgs a) {
             wait_or_abort(mbar, phase, abort_flag, a.status);
             phase ^= 1u;
             tc_fence_after();
-#pragma unroll 1
-            for (int c = 0; c < 2; ++c) {
-                float v[64];
-                tmem_ld64(t_acc + lane_off + c * 64, v);
+            {
+                // 16 columns at a time; the next chunk's load is in flight
+                // while this one is converted and stored
+                uint32_t ra[16], rb[16];
+                auto convert16 = [&](const uint32_t (&r)[16], int c) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    uint4 p;
-                    p.x = pack_bf16_relu(v[j * 8 + 0], v[j * 8 + 1]);
-                    p.y = pack_bf16_relu(v[j * 8 + 2], v[j * 8 + 3]);
-                    p.z = pack_bf16_relu(v[j * 8 + 4], v[j * 8 + 5]);
-                    p.w = pack_bf16_relu(v[j * 8 + 6], v[j * 8 + 7]);
-                    const int kc = c * 8 + j;  // 16-byte chunk 0..15 along K
-                    *reinterpret_cast<uint4 *>(A + (kc >> 3) * 16384 + my_row * 128 +
-                                               (((kc & 7) ^ (my_row & 7)) << 4)) = p;
+                    for (int j = 0; j < 2; ++j) {
+                        const uint32_t *v = r + j * 8;
+                        uint4 p;
+                        p.x = pack_bf16_relu(__uint_as_float(v[0]), __uint_as_float(v[1]));
+                        p.y = pack_bf16_relu(__uint_as_float(v[2]), __uint_as_float(v[3]));
+                        p.z = pack_bf16_relu(__uint_as_float(v[4]), __uint_as_float(v[5]));
+                        p.w = pack_bf16_relu(__uint_as_float(v[6]), __uint_as_float(v[7]));
+                        const int kc = c * 2 + j;  // 16-byte chunk 0..15 along K
+                        *reinterpret_cast<uint4 *>(A + (kc >> 3) * 16384 + my_row * 128 +
+                                                   (((kc & 7) ^ (my_row & 7)) << 4)) = p;
+                    }
+                };
+                tmem_ld16_issue(t_acc + lane_off, ra);
+                tmem_ld16_wait(ra);
+#pragma unroll
+                for (int c = 0; c < 8; c += 2) {
+                    tmem_ld16_issue(t_acc + lane_off + (c + 1) * 16, rb);
+                    convert16(ra, c);
+                    tmem_ld16_wait(rb);
+                    if (c + 2 < 8) tmem_ld16_issue(t_acc + lane_off + (c + 2) * 16, ra);
+                    convert16(rb, c + 1);
+                    if (c + 2 < 8) tmem_ld16_wait(ra);
                 }
             }
             tc_fence_before();

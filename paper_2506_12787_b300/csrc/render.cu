@@ -31,10 +31,11 @@
 // tile goes through shared memory to float4 stores.
 //
 // Backward: one CTA per (tile, query); the tile's dL/dA is staged in shared
-// memory and each thread takes one Gaussian of the list, walks the pixels of
-// its bounding box inside the tile, recomputes exp(-q/2) and accumulates
-// dL/d(mx, my, A, B, C, w), then adds them to the per-(query, Gaussian)
-// gradient with atomics (a Gaussian spans several tiles).
+// memory, a warp cuts 32 keys of the list into (key, box row) items shared
+// out evenly over its lanes, recomputes exp(-q/2) over each row's in-cutoff
+// span and accumulates dL/d(mx, my, A, B, C, w) per key, then adds them to
+// the per-(query, Gaussian) gradient with atomics (a Gaussian spans several
+// tiles).
 #include <cuda.h>
 
 #include <cstring>
