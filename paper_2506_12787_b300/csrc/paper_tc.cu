@@ -458,32 +458,72 @@ __global__ void __launch_bounds__(TcCfg<X>::Threads, 1) paper_tc_kernel(PaperTcA
                 write_term(tnext);  // the layer-l MMAs that read the image are complete
                 // this warp's 80 accumulator columns -> 40 activation columns
                 // (and, X = 3, 40 columns of the BF16 remainders)
-#pragma unroll 1
-                for (int c = 0; c < 3; ++c) {
-                    const int col = 80 * half + 32 * c;
-                    const int nv = c < 2 ? 32 : 16;
-                    float v[32];
-                    uint32_t pk[16], pl[16];
-                    if (c < 2)
-                        tmem_ld32(t_acc + lane_off + col, v);
-                    else
-                        tmem_ld16(t_acc + lane_off + col, v);
+                if (X == 3) {
+                    // five chunks of 16 columns; the next chunk's load is in flight
+                    // while this one is converted and stored
+                    uint32_t ra[16], rb[16];
+                    auto convert = [&](const uint32_t (&r)[16], int c) {
+                        const int col = 80 * half + 16 * c;
+                        uint32_t pk[8], pl[8];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if (2 * j >= nv) break;
-                        pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
-                        if (X == 3) {
-                            const float r0 = fmaxf(v[2 * j], 0.f), r1 = fmaxf(v[2 * j + 1], 0.f);
-                            pl[j] = pack_bf16(__fsub_rn(r0, __uint_as_float(pk[j] << 16)),
-                                              __fsub_rn(r1, __uint_as_float(pk[j] & 0xFFFF0000u)));
+                        for (int j = 0; j < 8; ++j) {
+                            const float v0 = __uint_as_float(r[2 * j]), v1 = __uint_as_float(r[2 * j + 1]);
+                            pk[j] = pack_bf16_relu(v0, v1);
+                            if (X == 3) {
+                                const float r0 = fmaxf(v0, 0.f), r1 = fmaxf(v1, 0.f);
+                                pl[j] = pack_bf16(__fsub_rn(r0, __uint_as_float(pk[j] << 16)),
+                                                  __fsub_rn(r1, __uint_as_float(pk[j] & 0xFFFF0000u)));
+                            }
                         }
-                    }
-                    if (c < 2) {
-                        tmem_st16(t_act + lane_off + col / 2, pk);
-                        if (X == 3) tmem_st16(t_lo + lane_off + col / 2, pl);
-                    } else {
                         tmem_st8(t_act + lane_off + col / 2, pk);
                         if (X == 3) tmem_st8(t_lo + lane_off + col / 2, pl);
+                    };
+                    const uint32_t c0 = t_acc + lane_off + 80 * half;
+                    tmem_ld16_issue(c0, ra);
+                    tmem_ld16_wait(ra);
+                    tmem_ld16_issue(c0 + 16, rb);
+                    convert(ra, 0);
+                    tmem_ld16_wait(rb);
+                    tmem_ld16_issue(c0 + 32, ra);
+                    convert(rb, 1);
+                    tmem_ld16_wait(ra);
+                    tmem_ld16_issue(c0 + 48, rb);
+                    convert(ra, 2);
+                    tmem_ld16_wait(rb);
+                    tmem_ld16_issue(c0 + 64, ra);
+                    convert(rb, 3);
+                    tmem_ld16_wait(ra);
+                    convert(ra, 4);
+                } else {
+                    // (BF16 alone: one chunk at a time; the overlapped form
+                    // spills registers in this instance)
+#pragma unroll 1
+                    for (int c = 0; c < 3; ++c) {
+                        const int col = 80 * half + 32 * c;
+                        const int nv = c < 2 ? 32 : 16;
+                        float v[32];
+                        uint32_t pk[16], pl[16];
+                        if (c < 2)
+                            tmem_ld32(t_acc + lane_off + col, v);
+                        else
+                            tmem_ld16(t_acc + lane_off + col, v);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (2 * j >= nv) break;
+                            pk[j] = pack_bf16_relu(v[2 * j], v[2 * j + 1]);
+                            if (X == 3) {
+                                const float r0 = fmaxf(v[2 * j], 0.f), r1 = fmaxf(v[2 * j + 1], 0.f);
+                                pl[j] = pack_bf16(__fsub_rn(r0, __uint_as_float(pk[j] << 16)),
+                                                  __fsub_rn(r1, __uint_as_float(pk[j] & 0xFFFF0000u)));
+                            }
+                        }
+                        if (c < 2) {
+                            tmem_st16(t_act + lane_off + col / 2, pk);
+                            if (X == 3) tmem_st16(t_lo + lane_off + col / 2, pl);
+                        } else {
+                            tmem_st8(t_act + lane_off + col / 2, pk);
+                            if (X == 3) tmem_st8(t_lo + lane_off + col / 2, pl);
+                        }
                     }
                 }
                 tmem_wait_st();
