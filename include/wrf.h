@@ -104,7 +104,8 @@ typedef struct {
  * q = d^T Sigma^-1 d <= q_cut (d = p - centre); q_cut = +inf disables the
  * cutoff.  Tiles are tile_w x tile_h pixels, numbered row-major; the last
  * tile row/column may be partial.  Supported tile shapes: 8x8, 16x8, 16x16,
- * 32x8, 32x16 (w x h).
+ * 32x8, 32x16 (w x h); H, W <= 65536 and at most 3000 tiles (else
+ * WRF_EUNSUPPORTED / WRF_EINVAL).
  * wrap_x = 1 makes the azimuth axis periodic (columns 0 and W the same
  * direction, as for a 0-360 degree spectrum): every Gaussian also acts through
  * its images centre + k W, tile lists cover columns modulo W, and each tile is

@@ -107,8 +107,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
     GridView g, float ncut, float *__restrict__ out, int *status, const float *__restrict__ rec_im,
-    const long long *__restrict__ qbase, const __grid_constant__ CUtensorMap rmap,
-    bool tile_major) {
+    const long long *__restrict__ qbase, const __grid_constant__ CUtensorMap rmap) {
     constexpr int NT = TW * TH / PX, B = NT * BF, NW = NT / 32;
     constexpr int NG = B / 4;  // four-record gathers per full batch
     static_assert(NG <= NT, "one gather per thread at most");
@@ -129,7 +128,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     __shared__ __align__(16) float stile_im[CH == 2 ? TH : 1][CH == 2 ? TW : 1];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t = tile_major ? blockIdx.y : blockIdx.x, q = tile_major ? blockIdx.x : blockIdx.y;
+    const int t = blockIdx.y, q = blockIdx.x;  // tile-major launch order
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
     // this thread's pixels (tile-local): column pxl (and pxl + 8 when PX = 4),
     // rows pyl and pyl + 4; lx = the column's offset from the tile centre
@@ -454,13 +453,12 @@ template <int TW, int TH>
 __global__ void __launch_bounds__(128) render_bwd_kernel(
     const float4 *__restrict__ rec, const uint32_t *__restrict__ gids,
     const uint32_t *__restrict__ offs, const long long *__restrict__ n_keys, long long cap, int n,
-    GridView g, float cut_s, const float *__restrict__ dA, float *__restrict__ d_rec,
-    bool tile_major) {
+    GridView g, float cut_s, const float *__restrict__ dA, float *__restrict__ d_rec) {
     __shared__ float sg[TH][TW];
     __shared__ float4 kpar[4][32][3];  // per warp and key: mx, my, A, B | C, 1/A, xa, xb | ya
     __shared__ int kpre[4][33];        // per warp: item (row) prefix over its 32 keys
     __shared__ float kacc[4][32][6];   // per warp and key: S0 .. S5
-    const int t = tile_major ? blockIdx.y : blockIdx.x, q = tile_major ? blockIdx.x : blockIdx.y;
+    const int t = blockIdx.y, q = blockIdx.x;  // tile-major, as the forward
     const int x0 = (t % g.ntx) * TW, y0 = (t / g.ntx) * TH;
     for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
         int y = y0 + i / TW, x = x0 + i % TW;
@@ -639,18 +637,16 @@ cudaError_t launch_fwd_x(const float4 *rec, const uint32_t *gids, const uint32_t
     if (rows > 0x7fffffffull) return cudaErrorInvalidValue;
     CUtensorMap rmap;  // used by the TMA staging only
     if ((e = record_map(g.tma ? rec : nullptr, rows, &rmap)) != cudaSuccess) return e;
-    // CTAs in tile-major order (one tile position for all queries, then the
-    // next: 0.914 -> 0.880 ms on 20k Gaussians x 256 TX, 360 x 90, 32 x 16
-    // tiles), or query-major where the tiles exceed the grid's y limit
-    const bool tile_major = g.T <= 65535;
-    if (!tile_major && Q > 65535) return cudaErrorInvalidValue;
-    const dim3 grid = tile_major ? dim3(Q, g.T) : dim3(g.T, Q);
+    // CTAs in tile-major order: the grid is Q x T, query fastest, so one tile
+    // position runs for all queries, then the next (0.914 -> 0.880 ms on 20k
+    // Gaussians x 256 TX, 360 x 90, 32 x 16 tiles); T <= 3000 (grid check)
+    const dim3 grid(Q, g.T);
     // two channels: the imaginary weights follow the Q x N records
     const float *rec_im =
         CH == 2 ? reinterpret_cast<const float *>(rec + 2 * static_cast<size_t>(Q) * n) : nullptr;
     kern<<<grid, TW * TH / PX, smem, st>>>(rec, gids, offs, n_keys, cap, n, g,
                                            -g.q_cut * kHalfLog2e, out, status, rec_im, qbase,
-                                           rmap, tile_major);
+                                           rmap);
     return cudaGetLastError();
 }
 
@@ -690,11 +686,9 @@ template <int TW, int TH>
 cudaError_t launch_bwd(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                        const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                        const float *dA, float *d_rec, cudaStream_t st) {
-    const bool tile_major = g.T <= 65535;  // as the forward
-    if (!tile_major && Q > 65535) return cudaErrorInvalidValue;
-    const dim3 grid = tile_major ? dim3(Q, g.T) : dim3(g.T, Q);
+    const dim3 grid(Q, g.T);  // tile-major, as the forward
     render_bwd_kernel<TW, TH><<<grid, 128, 0, st>>>(rec, gids, offs, n_keys, cap, n, g,
-                                                    g.q_cut * kHalfLog2e, dA, d_rec, tile_major);
+                                                    g.q_cut * kHalfLog2e, dA, d_rec);
     return cudaGetLastError();
 }
 
