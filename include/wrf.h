@@ -500,6 +500,50 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
                                float *const *db, float *d_mean, int32_t stop_grad_mean, void *ws,
                                size_t ws_bytes, void *stream);
 
+/* Host-to-host forward pipeline (the problem as Sec. 4.1-4.2 state it: the
+ * Gaussian parameters and the network stay on the device, TX positions come
+ * in, spectra go out; Eq. 9 / Eq. 13 per query).  It owns everything a step
+ * needs: records, workspaces, tile lists and two slots of device TX and
+ * spectrum buffers, each slot with a CUDA graph of wrf_deform_project +
+ * wrf_bin + wrf_render (wrf_render_complex for two channels), and its own
+ * two streams.  A step copies its TX positions into pinned staging, uploads
+ * them, replays the slot's graph and copies the spectra back to the caller's
+ * host buffer on the second stream, so one step's read-back overlaps the next
+ * step's compute.  The library allocates at create and at a key-capacity
+ * growth, never in a step otherwise.
+ *   wrf_pipeline_create  scene / mlp / grid as for the calls above (device
+ *                        arrays the caller keeps alive and unchanged until
+ *                        destroy; the structs themselves are copied), Q >= 1
+ *                        queries per step, on the current device.
+ *                        key_margin >= 1: the key capacity is the first
+ *                        step's key count x key_margin + 1024 (0 = 1.25).
+ *   wrf_pipeline_step    tx_host [Q][3] host FP32 (read before the call
+ *                        returns); spectra_host host FP32, [Q][H][W] (one
+ *                        channel) or [Q][2][H][W] (two: magnitude, phase),
+ *                        written when the step completes: it must stay valid
+ *                        until then.  Pinned memory (cudaHostAlloc /
+ *                        cudaHostRegister) keeps the read-back asynchronous.
+ *                        A step first waits (on the host) for the step two
+ *                        before it, which used the same slot.  The first step
+ *                        runs synchronously: it sizes the key capacity and
+ *                        captures the graphs.
+ *   wrf_pipeline_wait    blocks until every enqueued step has completed.
+ *   wrf_pipeline_destroy waits, then frees everything; NULL is a no-op.
+ * A step whose keys did not fit (the device records WRF_ENOSPC) is detected
+ * when its slot is next waited on: the pipeline grows the capacity, captures
+ * its graphs again, recomputes that step synchronously into the same host
+ * buffer and clears the status word, so every completed step holds the
+ * spectra of its own TX positions.  Errors: WRF_EINVAL / WRF_EUNSUPPORTED
+ * (arguments, as the calls above), WRF_ECUDA (a failed CUDA call; the
+ * pipeline should then be destroyed).  One pipeline is used by one host
+ * thread at a time.                                                         */
+typedef struct wrf_pipeline wrf_pipeline;
+wrf_status wrf_pipeline_create(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid,
+                               int32_t Q, float key_margin, wrf_pipeline **out);
+wrf_status wrf_pipeline_step(wrf_pipeline *p, const float *tx_host, float *spectra_host);
+wrf_status wrf_pipeline_wait(wrf_pipeline *p);
+wrf_status wrf_pipeline_destroy(wrf_pipeline *p);
+
 /* Diagnostic of the bounded device-side waits (no paper counterpart): one
  * GPU thread waits, with the same bounded wait the kernels use, on an
  * mbarrier phase that nothing completes.  The wait gives up after limit_ns

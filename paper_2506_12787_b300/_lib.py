@@ -32,6 +32,7 @@ EXPORTS = (
     "wrf_paper_workspace_size", "wrf_paper_deform_project", "wrf_measure_alu_peaks",
     "wrf_anneal_tx", "wrf_multi_set_size", "wrf_multi_set_prepare", "wrf_multi_workspace_size",
     "wrf_deform_project_multi", "wrf_bin_multi", "wrf_render_multi",
+    "wrf_pipeline_create", "wrf_pipeline_step", "wrf_pipeline_wait", "wrf_pipeline_destroy",
 )
 
 
@@ -122,6 +123,10 @@ def load(path: str = LIB_PATH):
         "wrf_deform_project_multi": (I32, [sp, mp, I32, P, P, P, I32, gp, P, I64, P, P, S, P]),
         "wrf_bin_multi": (I32, [P, P, I32, I32, gp, P, I64, P, P, P, S, P]),
         "wrf_render_multi": (I32, [P, P, P, P, P, I64, I32, gp, P, P]),
+        "wrf_pipeline_create": (I32, [sp, mp, gp, I32, F, C.POINTER(P)]),
+        "wrf_pipeline_step": (I32, [P, P, P]),
+        "wrf_pipeline_wait": (I32, [P]),
+        "wrf_pipeline_destroy": (I32, [P]),
         "wrf_paper_workspace_size": (S, [I32, I32]),
         "wrf_measure_alu_peaks": (I32, [C.POINTER(C.c_double)] * 3 + [P]),
         "wrf_paper_deform_project": (I32, [C.POINTER(PaperScene), C.POINTER(PaperMlp), gp, P, I32,

@@ -325,3 +325,57 @@ class HostPipeline:
     def sync(self):
         self.copy.synchronize()
         self.compute.synchronize()
+
+
+class NativePipeline:
+    """The library's host-to-host forward pipeline (wrf_pipeline_*): TX
+    positions in host memory in, spectra in pinned host memory out, every
+    step's upload, graph replay and read-back issued by the library itself
+    (two slots, the read-back of one step overlapping the next step's
+    compute; a step whose keys do not fit is recomputed with a grown
+    capacity).  This class only marshals arguments and keeps the scene and
+    network alive while the pipeline uses them.  ``step`` returns the pinned
+    host tensor the step's spectra land in: valid after ``wait`` or once the
+    step two later has been issued (two buffers alternate)."""
+
+    def __init__(self, scene: DeviceScene, mlp: DeviceMLP, grid, Q: int, key_margin: float = 0.0):
+        self._L = _lib.load()
+        self.scene, self.mlp, self.grid, self.Q = scene, mlp, grid, int(Q)
+        self._sc, self._mc = scene.c(), mlp.c()
+        p = C.c_void_p()
+        _lib.check(self._L.wrf_pipeline_create(C.byref(self._sc), C.byref(self._mc),
+                                               C.byref(grid), self.Q, float(key_margin),
+                                               C.byref(p)))
+        self._p = p
+        shape = (self.Q, grid.H, grid.W) if scene.channels == 1 else (self.Q, 2, grid.H, grid.W)
+        self.out_host = [torch.empty(shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        self.i = 0
+
+    @property
+    def h2d_bytes(self):
+        return self.Q * 3 * 4
+
+    @property
+    def d2h_bytes(self):
+        return int(self.out_host[0].numel()) * 4
+
+    def step(self, tx_host):
+        """Issue one step for tx_host [Q,3] (host FP32, contiguous)."""
+        assert tx_host.device.type == "cpu" and tx_host.dtype == torch.float32
+        assert tuple(tx_host.shape) == (self.Q, 3) and tx_host.is_contiguous()
+        out = self.out_host[self.i & 1]
+        _lib.check(self._L.wrf_pipeline_step(self._p, C.c_void_p(tx_host.data_ptr()),
+                                             C.c_void_p(out.data_ptr())))
+        self.i += 1
+        return out
+
+    def wait(self):
+        _lib.check(self._L.wrf_pipeline_wait(self._p))
+
+    def close(self):
+        if getattr(self, "_p", None) is not None and self._p.value:
+            self._L.wrf_pipeline_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        self.close()

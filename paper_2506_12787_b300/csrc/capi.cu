@@ -874,3 +874,24 @@ wrf_status wrf_deform_backward(const wrf_scene *scene, const wrf_mlp *mlp, const
 }
 
 }  // extern "C"
+
+namespace wrf {
+
+wrf_status check_forward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid, int Q) {
+    wrf_status s;
+    GridView g{};
+    MlpView m{};
+    if ((s = check_scene(scene)) != WRF_OK) return s;
+    if ((s = check_mlp(mlp, &m)) != WRF_OK) return s;
+    if ((s = check_grid(grid, &g)) != WRF_OK) return s;
+    if (Q < 1 || Q > 65535) return fail(WRF_EINVAL, "Q must be in [1, 65535]");
+    if (!rows_ok(scene->n, Q)) return fail(WRF_EUNSUPPORTED, "Q*N must be < 2^31");
+    return WRF_OK;
+}
+
+wrf_status set_error(wrf_status s, const char *where, cudaError_t e) {
+    if (e != cudaSuccess) return fail(s, "%s: %s", where, cudaGetErrorString(e));
+    return fail(s, "%s", where);
+}
+
+}  // namespace wrf

@@ -237,4 +237,13 @@ using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_
                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 EncodeTiledFn encode_tiled();
 
+
+// For the library's host code outside the C ABI file (the forward pipeline):
+// the forward calls' argument checks (scene, network, grid, Q >= 1), and the
+// thread-local message that wrf_last_error returns (with the CUDA error's
+// text when e is not cudaSuccess).  Both return their status argument or
+// the check's result.
+wrf_status check_forward(const wrf_scene *scene, const wrf_mlp *mlp, const wrf_grid *grid, int Q);
+wrf_status set_error(wrf_status s, const char *where, cudaError_t e = cudaSuccess);
+
 }  // namespace wrf

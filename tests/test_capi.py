@@ -189,3 +189,38 @@ def test_product_path_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_pipeline_host_validation(lib):
+    """wrf_pipeline_*: argument errors come back before any CUDA call (no GPU
+    needed); NULL handles are rejected, and destroying NULL is a no-op."""
+    from paper_2506_12787_b300 import _lib
+    m = _lib.Mlp()
+    m.n_layers = 5
+    m.L_mean, m.L_tx = 6, 10
+    for i, d in enumerate([89, 128, 128, 128, 128, 5]):
+        m.dims[i] = d
+    for i in range(5):
+        m.W[i] = m.b[i] = 4096  # placeholders: validation never dereferences them
+    for i in range(3):
+        m.room_size[i] = 1.0
+    m.precision = _lib.WRF_BF16
+    s = _lib.Scene(0, 1, None, None, None, None, None)
+    g = _lib.Grid(90, 360, 32, 16, 9.0)
+    p = C.c_void_p()
+    assert lib.wrf_pipeline_create(C.byref(s), C.byref(m), C.byref(g), 4, 0.0, None) == \
+        _lib.WRF_EINVAL
+    bad = _lib.Grid(90, 360, 12, 16, 9.0)
+    assert lib.wrf_pipeline_create(C.byref(s), C.byref(m), C.byref(bad), 4, 0.0, C.byref(p)) == \
+        _lib.WRF_EUNSUPPORTED
+    assert p.value is None
+    for Q in (0, -1, 70000):
+        assert lib.wrf_pipeline_create(C.byref(s), C.byref(m), C.byref(g), Q, 0.0,
+                                       C.byref(p)) == _lib.WRF_EINVAL
+    for margin in (0.5, -1.0, float("nan")):
+        assert lib.wrf_pipeline_create(C.byref(s), C.byref(m), C.byref(g), 4, margin,
+                                       C.byref(p)) == _lib.WRF_EINVAL
+        assert b"key_margin" in lib.wrf_last_error()
+    assert lib.wrf_pipeline_step(None, None, None) == _lib.WRF_EINVAL
+    assert lib.wrf_pipeline_wait(None) == _lib.WRF_EINVAL
+    assert lib.wrf_pipeline_destroy(None) == _lib.WRF_OK
