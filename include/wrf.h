@@ -13,14 +13,15 @@
  *     Scratch space is passed in as `ws` (size from the matching
  *     *_workspace_size call), 256-byte aligned; no call on the path
  *     allocates device memory (only the wrf_measure_alu_peaks diagnostic
- *     does, a 4-byte sink).
+ *     does, a 4-byte sink, and the host-to-host pipeline, which owns its
+ *     buffers: see wrf_pipeline_create).
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
- *     only enqueues work and returns; nothing synchronises the host.
- *   - Host buffers: every array argument is a device pointer.  A caller with
- *     TX positions and spectra in host memory copies them around the calls
- *     with cudaMemcpyAsync on the same stream (pinned host memory keeps the
- *     copies asynchronous); the Python package's batched.HostPipeline is that
- *     end-to-end path, overlapping one step's copies with the next step.
+ *     only enqueues work and returns; nothing synchronises the host (except
+ *     wrf_status_read and the pipeline's step and wait, as documented).
+ *   - Host buffers: every array argument is a device pointer, except in the
+ *     host-to-host pipeline (wrf_pipeline_*), which takes TX positions and
+ *     returns spectra in host memory, overlapping one step's copies with the
+ *     next step's compute.
  *   - Argument errors are detected on the host and returned before any work
  *     is queued (WRF_EINVAL / WRF_EUNSUPPORTED).  A failed launch returns
  *     WRF_ECUDA.  Conditions only the device can see (key-capacity overflow,
