@@ -76,17 +76,21 @@ __device__ __forceinline__ void tma_gather4(void *dst, const CUtensorMap *map, i
 }
 
 // Shared-memory carve-up of the forward kernel for a tile with NT threads
-// and TH rows: a batch holds B = BF x NT records, BF per thread.
-template <int NT, int TH, int BF>
+// and TH rows: a batch holds B = BF x NT records, BF per thread.  WIM: the
+// staged imaginary weights (two channels with TMA staging; the cp.async path
+// keeps them in registers).  The finished tile is staged in the row-pair
+// area, which is dead once the last batch is evaluated.  Kept small enough
+// for eight CTAs per SM at 32 x 16 tiles with four pixels per thread.
+template <int NT, int TH, int BF, bool WIM>
 struct FwdSmem {
     static constexpr int B = NT * BF, NW = NT / 32, RS = B + 1;  // RS: bank spread
     static constexpr size_t raw = 0;                           // [2][B][2] float4, TMA landing
     static constexpr size_t rowc = raw + 2 * B * 32;           // [TH/2][RS] float4, row pairs
     static constexpr size_t gc = rowc + (TH / 2) * RS * 16;    // [B] float4 (c3, c3, w, 0)
-    static constexpr size_t mask = gc + B * 16;                // [B] u32, warp blocks touched
-    static constexpr size_t lists = mask + B * 4;              // [NW][B] u16, per-warp compaction
+    static constexpr size_t mask = gc + B * 16;                // [B] u8, warp blocks touched
+    static constexpr size_t lists = mask + B;                  // [NW][B] u16, per-warp compaction
     static constexpr size_t wim = lists + NW * B * 2;          // [2][B] f32, imaginary weights
-    static constexpr size_t bytes = wim + 2 * B * 4;
+    static constexpr size_t bytes = wim + (WIM ? 2 * B * 4 : 0);
 };
 
 // CH = 1: one channel, out [Q][H][W].  CH = 2: real and imaginary channels
@@ -114,18 +118,22 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     constexpr int BW = 4 * PX;   // warp block width: 8 or 16 columns
     constexpr int NSX = TW / BW;  // warp blocks of BW x 8 pixels: NSX across, TH/8 down
     static_assert(NW == NSX * (TH / 8), "one warp block per warp");
-    using L = FwdSmem<NT, TH, BF>;
+    using L = FwdSmem<NT, TH, BF, CH == 2 && TMA>;
+    static_assert(NW <= 8, "warp-block masks are 8 bits");
+    static_assert(L::gc - L::rowc >= static_cast<size_t>(CH) * TH * TW * 4,
+                  "the output tile fits in the row-pair area");
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *raw = reinterpret_cast<float4 *>(smem + L::raw);
     float4 *rowc = reinterpret_cast<float4 *>(smem + L::rowc);
     float4 *gcoef = reinterpret_cast<float4 *>(smem + L::gc);
-    uint32_t *mask = reinterpret_cast<uint32_t *>(smem + L::mask);
+    uint8_t *mask = smem + L::mask;
     uint16_t *lists = reinterpret_cast<uint16_t *>(smem + L::lists);
     float *wim_s = reinterpret_cast<float *>(smem + L::wim);  // two channels: [2][B]
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int abort_flag;
-    __shared__ __align__(16) float stile[TH][TW];
-    __shared__ __align__(16) float stile_im[CH == 2 ? TH : 1][CH == 2 ? TW : 1];
+    // the finished tile (and its phase plane), written after the last batch
+    float(*stile)[TW] = reinterpret_cast<float(*)[TW]>(smem + L::rowc);
+    float(*stile_im)[TW] = stile + TH;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int t = blockIdx.y, q = blockIdx.x;  // tile-major launch order
@@ -298,7 +306,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
                 const uint32_t row = (2u << bx1) - (1u << bx0);
                 for (int by = by0; by <= by1; ++by) mk |= row << (by * NSX);
             }
-            mask[ri] = mk;
+            mask[ri] = static_cast<uint8_t>(mk);
         }
         __syncthreads();
         // raw[buf] is consumed: the copies of batch b+2 can land there now
@@ -414,7 +422,7 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
     const bool vec = (g.W & 3) == 0;
     for (int c = 0; c < CH; ++c) {
         float *oq = out + (static_cast<size_t>(q) * CH + c) * plane;
-        float(*st)[TW] = c == 0 ? stile : reinterpret_cast<float(*)[TW]>(stile_im);
+        float(*st)[TW] = c == 0 ? stile : stile_im;
         for (int i = tid; i < TH * TW / 4; i += NT) {
             const int r = i / (TW / 4), c4 = (i % (TW / 4)) * 4;
             const int y = y0 + r, x = x0 + c4;
@@ -622,7 +630,8 @@ template <int TW, int TH, int CH, int PX, int BF>
 cudaError_t launch_fwd_x(const float4 *rec, const uint32_t *gids, const uint32_t *offs,
                          const long long *n_keys, long long cap, int n, int Q, const GridView &g,
                          float *out, int *status, cudaStream_t st, const long long *qbase) {
-    const size_t smem = FwdSmem<TW * TH / PX, TH, BF>::bytes;
+    const size_t smem = g.tma && CH == 2 ? FwdSmem<TW * TH / PX, TH, BF, true>::bytes
+                                         : FwdSmem<TW * TH / PX, TH, BF, false>::bytes;
     auto kern = g.tma ? (g.wrap ? render_kernel<TW, TH, CH, true, PX, BF, true>
                                 : render_kernel<TW, TH, CH, false, PX, BF, true>)
                       : (g.wrap ? render_kernel<TW, TH, CH, true, PX, BF, false>
