@@ -282,13 +282,18 @@ __global__ void __launch_bounds__(TW *TH / PX, 1024 * PX / (TW * TH)) render_ker
             const float c1 = 2.f * h1, c2 = 2.f * h2, c4 = -2.f * r0.w, c5 = -r1.x;
             // per tile row: -q'(lx) = alpha + beta lx + c3 lx^2; entry p of
             // the record holds rows y(p) and y(p) + 4, y(p) = 8 (p / 4) + p % 4
+            // both rows of an entry at once: two-lane FMAs, each lane rounded
+            // like fmaf (alpha = (c5 ly + c2) ly + c0, beta = c4 ly + c1)
+            const float2 c5v = make_float2(c5, c5), c2v = make_float2(c2, c2);
+            const float2 c0v = make_float2(c0, c0), c4v = make_float2(c4, c4);
+            const float2 c1v = make_float2(c1, c1);
 #pragma unroll
             for (int pr = 0; pr < TH / 2; ++pr) {
                 const float ly0 = static_cast<float>((pr >> 2) * 8 + (pr & 3) - TH / 2);
-                const float ly1 = ly0 + 4.f;
-                rowc[pr * L::RS + ri] =
-                    make_float4(fmaf(fmaf(c5, ly0, c2), ly0, c0), fmaf(fmaf(c5, ly1, c2), ly1, c0),
-                                fmaf(c4, ly0, c1), fmaf(c4, ly1, c1));
+                const float2 ly = make_float2(ly0, ly0 + 4.f);
+                const float2 al = fma2(fma2(c5v, ly, c2v), ly, c0v);
+                const float2 be = fma2(c4v, ly, c1v);
+                rowc[pr * L::RS + ri] = make_float4(al.x, al.y, be.x, be.y);
             }
             const float wi = CH == 2 ? (TMA ? wim_s[buf * B + ri] : (buf ? wim_r[1][k] : wim_r[0][k]))
                                      : 0.f;
