@@ -57,7 +57,7 @@ MLP_FLOP_PER_ROW = 3 * 2 * 128 * 128 + 2 * 128 * 5  # factorised hidden + output
 # ncu DRAM traffic per launch, keyed by (kernel, N, Q, H, W, rasteriser configuration);
 # captured on the flat one-channel grid only
 NCU_TRAFFIC = {
-    ("render_kernel", 20000, 256, 90, 360, "32x16p4b1"): 901.98784e6 + 33.107712e6,
+    ("render_kernel", 20000, 256, 90, 360, "32x16p4b1"): 901.725184e6 + 33.142016e6,
     ("mlp_tc_kernel", 20000, 256, 90, 360, "32x16p4b1"): 2.128384e6 + 104.083968e6,
 }
 RAST_FLOP_PER_EVAL = 12  # d (2) + quadratic form (8) + w*e accumulate (2); plus one ex2
