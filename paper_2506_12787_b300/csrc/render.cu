@@ -28,7 +28,8 @@
 // both pixels of a thread.
 // Every pixel adds its contributions in ascending Gaussian id, so a query's
 // spectrum does not depend on the other queries in the launch.  The finished
-// tile goes through shared memory to float4 stores.
+// tile goes through shared memory (the row-pair area, dead by then) to
+// float4 stores.
 //
 // Backward: one CTA per (tile, query); the tile's dL/dA is staged in shared
 // memory, a warp cuts 32 keys of the list into (key, box row) items shared
